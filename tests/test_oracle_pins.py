@@ -1,0 +1,314 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test ties one oracle routine to something other than itself: a direct
+sum written here with NumPy, a closed form, a hand-computed value, an
+invariant between two different routes (EPIC vs correlator + XFFT), or
+brute force on tiny inputs.  None needs a GPU.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2411_17804_gb300 import inputs as I
+
+
+def dft_matrix(n):
+    k = np.arange(n)
+    return np.exp(2j * np.pi * np.outer(k, k) / n)
+
+
+def dft2_direct(g):
+    """F = W g W^T with W[l][j] = exp(+2 pi i l j / N): the definition."""
+    w = dft_matrix(g.shape[0])
+    return w @ g @ w.T
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+def placed_conj_taps(n, anchors, taps):
+    """Aperture illumination g[j] = sum_a conj(w_a[j - anchor_a])."""
+    g = np.zeros((n, n), complex)
+    k = taps.shape[1]
+    for a in range(len(anchors)):
+        x0, y0 = anchors[a]
+        g[y0:y0 + k, x0:x0 + k] += taps[a, :, :, 0] - 1j * taps[a, :, :, 1]
+    return g
+
+
+def checker(n):
+    j = np.arange(n)
+    return (-1.0) ** (j[:, None] + j[None, :])
+
+
+# ---------------------------------------------------------------- FFT pins
+@pytest.mark.parametrize("n", [2, 4, 8, 16])
+def test_fft2d_matches_direct_and_brute_dft(n):
+    rng = np.random.default_rng(n)
+    g = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    f = O.fft2d(g)
+    assert rel(f, dft2_direct(g)) < 1e-12
+    assert rel(f, O.dft2d_brute(g)) < 1e-12
+
+
+@pytest.mark.parametrize("n", [8, 64])
+def test_fft1d_closed_forms(n):
+    k = np.arange(n)
+    for n0 in (0, 1, 3, n - 1):
+        x = np.zeros(n, complex)
+        x[n0] = 1.0
+        assert np.abs(O.fft1d(x) - np.exp(2j * np.pi * n0 * k / n)).max() < 1e-12
+    X = O.fft1d(np.ones(n, complex))
+    assert abs(X[0] - n) < 1e-12 and np.abs(X[1:]).max() < 1e-12
+    # a pure +frequency tone lands in its own bin (sign of the exponent)
+    X = O.fft1d(np.exp(-2j * np.pi * 3 * k / n))
+    assert abs(X[3] - n) < 1e-10 and np.abs(np.delete(X, 3)).max() < 1e-10
+
+
+def test_fft2d_parseval_and_axes():
+    n = 32
+    rng = np.random.default_rng(7)
+    g = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    f = O.fft2d(g)
+    assert abs(np.sum(np.abs(f) ** 2) - n * n * np.sum(np.abs(g) ** 2)) < 1e-9 * np.sum(np.abs(f) ** 2)
+    # a tone along x only lands on row ly = 0 (row-major [y][x])
+    x = np.arange(n)
+    g = np.tile(np.exp(-2j * np.pi * 5 * x / n), (n, 1))
+    f = O.fft2d(g)
+    assert abs(f[0, 5] - n * n) < 1e-8 and np.abs(f).sum() - abs(f[0, 5]) < 1e-7
+
+
+# ------------------------------------------------------------- gridding pin
+def test_grid_hand_computed():
+    n, k = 16, 3
+    anchors = np.array([[2, 5]], np.int32)          # window x 2..4, y 5..7
+    taps = np.zeros((1, k, k, 2), np.float32)
+    taps[0, 0, 1] = (0.5, 0.25)                      # (v=0, u=1) -> cell (y=5, x=3)
+    taps[0, 2, 0] = (-1.0, 2.0)                      # (v=2, u=0) -> cell (y=7, x=2)
+    e = np.array([3, -4], np.int8)                   # E = 3 - 4i
+    g = O.grid(n, anchors, taps, e)
+    # conj(0.5 + 0.25i)(3 - 4i) = 0.5 - 2.75i ; conj(-1 + 2i)(3 - 4i) = -11 - 2i
+    assert g[5, 3] == pytest.approx(0.5 - 2.75j)
+    assert g[7, 2] == pytest.approx(-11 - 2j)
+    mask = np.ones((n, n), bool)
+    mask[5, 3] = mask[7, 2] = False
+    assert np.all(g[mask] == 0)
+
+
+def test_off_grid_is_rejected():
+    anchors = np.array([[14, 3]], np.int32)
+    taps = np.ones((1, 3, 3, 2), np.float32)
+    volt = np.zeros((1, 1, 1, 1, 2), np.int8)
+    with pytest.raises(ValueError):
+        O.epic_image(16, anchors, taps, volt)
+
+
+# --------------------------------------------------------- EPIC chain pins
+def _small_station(n_elem=24, diameter=6.0, n=16, k=3, seed=5):
+    rng = np.random.default_rng(seed)
+    pos = I.disk_layout(n_elem, diameter, 0.6, rng)
+    anchors, taps = I.gaussian_kernel(pos, 2.0, 0.5, n, k)
+    return pos, anchors, taps
+
+
+def test_point_source_at_phase_centre_gives_aperture_power_pattern():
+    n, T = 16, 5
+    pos, anchors, taps = _small_station()
+    ne = len(anchors)
+    A = np.array([5, -3])
+    volt = np.zeros((1, T, 1, ne, 2), np.int8)
+    volt[..., 0], volt[..., 1] = A
+    img = O.epic_image(n, anchors, taps, volt)[0, 0]
+    g = placed_conj_taps(n, anchors, taps)
+    pattern = T * (A @ A) * np.abs(dft2_direct(checker(n) * g)) ** 2
+    assert rel(img, pattern) < 1e-12
+    peak = T * (A @ A) * abs(g.sum()) ** 2                     # closed form
+    assert np.unravel_index(np.argmax(img), img.shape) == (n // 2, n // 2)
+    assert img[n // 2, n // 2] == pytest.approx(peak, rel=1e-12)
+
+
+def _on_cell_station(n):
+    """Elements exactly on distinct cells with 1 x 1 unit taps."""
+    cells = np.array([[x, y] for y in range(n // 4, 3 * n // 4, 2)
+                      for x in range(n // 4, 3 * n // 4, 3)], np.int32)
+    taps = np.zeros((len(cells), 1, 1, 2), np.float32)
+    taps[..., 0] = 1.0
+    return cells, taps
+
+
+@pytest.mark.parametrize("n", [16, 32])
+def test_quarter_turn_source_matches_beamformer_everywhere(n):
+    """A source on pixel (ly, lx) = (N/2, 3N/4): element phases are quarter
+    turns, so the int8 voltages are exact.  EPIC equals the Eq. (BF) power
+    at every pixel direction and peaks on that pixel with T (100 N_e)^2."""
+    cells, taps = _on_cell_station(n)
+    ne, T = len(cells), 3
+    jx = cells[:, 0] - n // 2
+    e = 100 * (-1j) ** jx                                    # exp(-2 pi i s.r / lambda)
+    volt = np.zeros((1, T, 2, ne, 2), np.int8)
+    volt[:, :, 0, :, 0], volt[:, :, 0, :, 1] = e.real, e.imag
+    ey = 1j * e                                              # Y = i X exactly
+    volt[:, :, 1, :, 0], volt[:, :, 1, :, 1] = ey.real, ey.imag
+    img = O.epic_image(n, cells, taps, volt)[0]
+    # Eq. (intra-station BF) with unit weights at every pixel direction:
+    # s.r/lambda = (l - N/2)(j - N/2)/N for r/lambda = (j - N/2) cells of 1/2
+    l = np.arange(n) - n // 2
+    rel_cells = cells - n // 2
+    phase = 2 * np.pi * (np.einsum("x,a->xa", l, rel_cells[:, 0])[None, :, :]
+                         + np.einsum("y,a->ya", l, rel_cells[:, 1])[:, None, :]) / n
+    bf = np.einsum("yxa,a->yx", np.exp(1j * phase), e)
+    assert rel(img[0], T * np.abs(bf) ** 2) < 1e-12
+    # (the 2-cell row spacing makes a grating lobe at ly = 0 of equal height)
+    assert img[0, n // 2, 3 * n // 4] == pytest.approx(img[0].max(), rel=1e-12)
+    assert img[0, n // 2, 3 * n // 4] == pytest.approx(T * (100 * ne) ** 2, rel=1e-12)
+    assert img[0, n // 2 + 1, 3 * n // 4] < 0.9 * img[0].max()
+    # Y = iX:  YY = XX, X conj(Y) = -i |X|^2
+    assert rel(img[1], img[0]) < 1e-12
+    assert np.abs(img[2]).max() < 1e-9 * img[0].max()
+    assert rel(img[3], -img[0]) < 1e-12
+
+
+def test_parseval_per_pixel_sum():
+    """sum_l XX[l] = N^2 sum_t sum_j |G_X[j]|^2."""
+    n = 16
+    pos, anchors, taps = _small_station()
+    volt = I.random_voltages((1, 4, 1, len(anchors), 2), seed=3).numpy()
+    img = O.epic_image(n, anchors, taps, volt)[0, 0]
+    tot = sum(np.sum(np.abs(O.grid(n, anchors, taps, volt[0, t, 0])) ** 2) for t in range(4))
+    assert img.sum() == pytest.approx(n * n * tot, rel=1e-12)
+
+
+def test_epic_sums_samples_and_channels_independently():
+    n = 16
+    pos, anchors, taps = _small_station()
+    volt = I.random_voltages((2, 6, 2, len(anchors), 2), seed=9).numpy()
+    full = O.epic_image(n, anchors, taps, volt)
+    parts = O.epic_image(n, anchors, taps, volt[:, :2]) + O.epic_image(n, anchors, taps, volt[:, 2:])
+    assert rel(full, parts) < 1e-13
+    assert rel(full[1], O.epic_image(n, anchors, taps, volt[1:])[0]) < 1e-14
+
+
+# ---------------------------------------------------------- integer paths
+def _cplx(v):
+    return v[..., 0].astype(np.int64) + 1j * v[..., 1].astype(np.int64)
+
+
+def test_correlator_brute_force_and_symmetries():
+    rng = np.random.default_rng(11)
+    volt = rng.integers(-128, 128, (2, 7, 2, 9, 2)).astype(np.int8)
+    vis = O.correlate(volt)
+    e = volt[..., 0].astype(np.int64), volt[..., 1].astype(np.int64)
+    C, T, P, ne, _ = volt.shape
+    for c in range(C):
+        for a in range(ne):
+            for b in range(a + 1):
+                for p in range(P):
+                    for q in range(P):
+                        ar, ai = e[0][c, :, p, a], e[1][c, :, p, a]
+                        br, bi = e[0][c, :, q, b], e[1][c, :, q, b]
+                        want = (int(np.sum(ar * br + ai * bi)), int(np.sum(ai * br - ar * bi)))
+                        assert tuple(vis[c, a * (a + 1) // 2 + b, p, q]) == want
+    autos = vis[:, [a * (a + 1) // 2 + a for a in range(ne)]]
+    assert np.all(autos[:, :, 0, 0, 1] == 0) and np.all(autos[:, :, 0, 0, 0] >= 0)
+    # V^{pq}_{aa} = conj(V^{qp}_{aa})
+    assert np.all(autos[:, :, 0, 1, 0] == autos[:, :, 1, 0, 0])
+    assert np.all(autos[:, :, 0, 1, 1] == -autos[:, :, 1, 0, 1])
+
+
+def test_correlator_adversarial_extremes():
+    T, ne = 5, 4
+    volt = np.full((1, T, 1, ne, 2), -128, np.int8)
+    vis = O.correlate(volt)
+    assert np.all(vis[..., 0] == T * 2 * 128 * 128) and np.all(vis[..., 1] == 0)
+    volt[..., 1] = 127                                        # E = -128 + 127 i
+    vis = O.correlate(volt)
+    assert np.all(vis[..., 0] == T * (128 * 128 + 127 * 127)) and np.all(vis[..., 1] == 0)
+
+
+def test_beamformer_brute_force():
+    rng = np.random.default_rng(12)
+    volt = rng.integers(-128, 128, (2, 2, 3, 2, 5, 2)).astype(np.int8)
+    w = rng.integers(-127, 128, (2, 3, 2, 5, 2)).astype(np.int8)
+    out = O.beamform(volt, w)
+    want = np.einsum("skpa,sctpa->sctkp", np.conj(_cplx(w)), _cplx(volt))
+    assert np.array_equal(out[..., 0], want.real.astype(np.int64))
+    assert np.array_equal(out[..., 1], want.imag.astype(np.int64))
+
+
+def test_beamformer_steers_onto_its_direction():
+    """Weights built for direction s_k and a plane wave from s_k: every
+    element adds in phase, so |B| = sum_a |w_a||E_a| up to rounding."""
+    rng = np.random.default_rng(2)
+    pos = I.disk_layout(32, 10.0, 0.8, rng)
+    dirs = I.beam_directions(4, 2.0, 10.0)
+    w = I.bf_weights(pos, 2.0, dirs, 1)
+    ph = -2 * np.pi * (dirs[2] @ pos.T) / 2.0
+    e = np.stack([np.round(100 * np.cos(ph)), np.round(100 * np.sin(ph))], -1)
+    volt = e.astype(np.int8)[None, None, None, None]
+    b = O.beamform(volt, w[None])[0, 0, 0, :, 0]
+    mag = np.hypot(b[:, 0], b[:, 1])
+    assert np.argmax(mag) == 2
+    assert mag[2] > 0.99 * 127 * 100 * 32
+
+
+@pytest.mark.parametrize("x,shift,want,sat", [
+    (3, 1, 2, 0), (-3, 1, -2, 0), (2, 1, 1, 0), (1, 1, 1, 0), (-1, 1, -1, 0),
+    (5, 2, 1, 0), (6, 2, 2, 0), (-6, 2, -2, 0), (7, 2, 2, 0), (0, 3, 0, 0),
+    (1000, 2, 127, 1), (-1000, 2, -127, 1), (127, 0, 127, 0), (128, 0, 127, 1),
+    (-128, 0, -127, 1), (508, 2, 127, 0), (510, 2, 127, 1)])
+def test_requant_rounds_half_away_and_saturates(x, shift, want, sat):
+    out, n = O.requant(np.array([x]), shift)
+    assert int(out[0]) == want and n == sat
+
+
+# ------------------------------------------------------------ XFFT pins
+def test_vis_kernel_sum_and_hermitian():
+    pos, anchors, taps = _small_station()
+    taps = taps.copy()
+    taps[..., 1] = 0.1 * np.random.default_rng(4).standard_normal(taps.shape[:-1])
+    for a, b in [(0, 0), (3, 1), (1, 3), (5, 2)]:
+        kab, base = O.vis_kernel(anchors, taps, a, b)
+        t64 = taps.astype(np.float64)
+        ga = t64[a, :, :, 0] - 1j * t64[a, :, :, 1]
+        gb = t64[b, :, :, 0] - 1j * t64[b, :, :, 1]
+        assert kab.sum() == pytest.approx(ga.sum() * np.conj(gb.sum()), rel=1e-12)
+        kba, base2 = O.vis_kernel(anchors, taps, b, a)
+        assert base2 == (-base[0], -base[1])
+        assert np.allclose(kba, np.conj(kab[::-1, ::-1]), atol=1e-15)
+    kaa, _ = O.vis_kernel(anchors, taps, 2, 2)
+    k = taps.shape[1]
+    assert kaa[k - 1, k - 1] == pytest.approx(np.sum(taps[2].astype(np.float64) ** 2), rel=1e-12)
+
+
+@pytest.mark.parametrize("P,cplx_taps", [(1, False), (2, False), (2, True)])
+def test_epic_equals_xfft_of_full_correlation_set(P, cplx_taps):
+    """The invariant: the direct-imaged power equals the FFT image of all
+    correlations (autos included) gridded with the illumination
+    autocorrelation kernel, for every polarisation product."""
+    n = 16
+    pos, anchors, taps = _small_station()
+    if cplx_taps:
+        taps = taps.copy()
+        taps[..., 1] = 0.2 * np.random.default_rng(8).standard_normal(taps.shape[:-1])
+    volt = I.random_voltages((2, 6, P, len(anchors), 2), seed=21).numpy()
+    epic = O.epic_image(n, anchors, taps, volt)
+    ximg = O.xfft_image(n, anchors, taps, O.correlate(volt))
+    assert rel(O.xfft_as_epic_planes(ximg), epic) < 1e-11
+    scale = np.abs(ximg).max()
+    for p in range(P):
+        assert np.abs(ximg[:, p, p].imag).max() < 1e-11 * scale      # autos real
+    if P == 2:
+        assert np.abs(ximg[:, 1, 0] - np.conj(ximg[:, 0, 1])).max() < 1e-11 * scale
+
+
+def test_epic_equals_xfft_with_wrapped_lags():
+    """Apertures wider than N/2 alias the lag grid; the circular wrap keeps
+    the invariant exact."""
+    n = 8
+    anchors = np.array([[0, 0], [5, 1], [2, 5], [4, 4]], np.int32)
+    taps = np.random.default_rng(1).standard_normal((4, 3, 3, 2)).astype(np.float32)
+    volt = I.random_voltages((1, 5, 2, 4, 2), seed=2).numpy()
+    epic = O.epic_image(n, anchors, taps, volt)
+    ximg = O.xfft_image(n, anchors, taps, O.correlate(volt))
+    assert rel(O.xfft_as_epic_planes(ximg), epic) < 1e-11
