@@ -1,0 +1,317 @@
+"""Benchmark of the EPIC hot path on GB300 (one JSON line on rank 0).
+
+A step is one cadence of the EPIC imager of the SKA-low-shaped station
+(256 elements, 2 polarisations, 64 channels, 2048 samples, 64 x 64 grid):
+gridding, the per-sample 2D DFT, squaring and accumulation, through the C ABI
+(hai_epic_image).  value = imaged pixel x channel x pol x sample per second.
+`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
+Multi-GPU: every rank images its own cadence (channels are independent), no
+collective on the data path; value is the sum over ranks / the max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "imaged pix·chan·pol·samples/s"
+UNIT = "pix·chan·pol·samples/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["fp16", "fp32"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--channels", type=int, default=0,
+                    help="image only this many channels (small cases for profiling)")
+    return ap.parse_args()
+
+
+def dist_init(n):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload():
+    from paper_2411_17804_gb300 import inputs as I
+    cfg = I.SKA_LOW_STATION_256
+    pos = I.station_layout(cfg)
+    anchors, taps = I.station_kernel(cfg, pos)
+    return cfg, pos, anchors, taps
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if sm:
+            out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                   "reasons": sorted(reasons), "samples": len(sm)}
+        return out
+
+
+def epic_flops_per_unit(cfg):
+    """Algorithmic FLOP per imaged unit (pixel x channel x pol x sample):
+    radix-2 FFT 5 log2(N^2), gridding 8 N_e K^2 / N^2, squaring and
+    accumulation 8 (XX, YY, XY: 8 FMA per pixel per sample for 2 pols)."""
+    n = cfg.grid_n
+    return 5 * math.log2(n * n) + 8.0 * cfg.n_elem * cfg.ksize ** 2 / (n * n) + 8.0
+
+
+def fp32_alu_peak_tflops(sm_count, sm_mhz):
+    """CUDA-core FP32 peak: SMs x 128 FP32 lanes x 2 FLOP (FMA) x clock."""
+    return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def cpu_baseline(cfg, pos, anchors, taps, n_chan):
+    """FP64 oracle on the host cores over a bounded sample of the workload."""
+    from oracle import oracle as O
+    from paper_2411_17804_gb300 import inputs as I
+    volt = I.station_voltages(cfg, pos, n_chan=n_chan).numpy()
+    t0 = time.perf_counter()
+    O.epic_image(cfg.grid_n, anchors, taps, volt)
+    dt = time.perf_counter() - t0
+    units = cfg.grid_n ** 2 * n_chan * cfg.n_pol * cfg.n_time
+    return {"value": units / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n_chan} of {cfg.n_chan} channels x {cfg.n_time} samples of the cadence "
+                      f"({dt:.1f} s)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    cfg, pos, anchors, taps = workload()
+    steps, warm = args.steps, args.warmup
+    sample_chan = 2
+    from oracle import oracle as O
+    from paper_2411_17804_gb300 import inputs as I
+    volt = I.station_voltages(cfg, pos, n_chan=sample_chan).numpy()
+    for _ in range(warm):
+        O.epic_image(cfg.grid_n, anchors, taps, volt[:, :64])
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        O.epic_image(cfg.grid_n, anchors, taps, volt)
+    dt = (time.perf_counter() - t0) / steps
+    units = cfg.grid_n ** 2 * sample_chan * cfg.n_pol * cfg.n_time
+    v = units / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg.name, "sample": f"{sample_chan} channels x {cfg.n_time} samples per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"{sample_chan} of {cfg.n_chan} channels per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_epic(hai, ctx, lay, volt, img, C, T, prec, steps, warm, flush, ws):
+    import torch
+    st = torch.cuda.current_stream()
+    for _ in range(warm):
+        hai.hai_epic_image(ctx, lay, volt, C, T, prec, img, 0, st)
+    hai.hai_sync(ctx, st)
+    hai.hai_profile_read(ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.add_(1.0)                           # evict L2 between steps
+        ev[i][0].record(st)
+        hai.hai_epic_image(ctx, lay, volt, C, T, prec, img, 0, st)
+        ev[i][1].record(st)
+    torch.cuda.synchronize()
+    barrier(ws)
+    hai.hai_sync(ctx, st)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dom_ms, dom_n, launches = hai.hai_profile_read(ctx)
+    return float(np.sum(step_ms)), dom_ms / max(dom_n, 1), launches
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+    from paper_2411_17804_gb300 import hai
+    torch.cuda.set_device(local)
+    cfg, pos, anchors, taps = workload()
+    if args.channels:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, n_chan=args.channels)
+    C, T, P, n = cfg.n_chan, cfg.n_time, cfg.n_pol, cfg.grid_n
+    prec = hai.HAI_PREC_FP16 if args.prec == "fp16" else hai.HAI_PREC_FP32
+    volt = __import__("paper_2411_17804_gb300.inputs", fromlist=["x"]).station_voltages(
+        cfg, pos, device="cuda")
+    ctx = hai.hai_create(local)
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, P)
+    img = torch.empty((C, lay.n_planes, n, n), device="cuda")
+    flush = torch.zeros(64 * 1024 * 1024, device="cuda")       # 256 MB > L2
+    hai.hai_profile_enable(ctx, True, 4096)
+    units = cfg.units_per_cadence
+
+    clocks = Clocks(local)
+    clocks.start()
+    total_ms, dom_ms, launches = time_epic(hai, ctx, lay, volt, img, C, T, prec, args.steps,
+                                           args.warmup, flush, ws)
+    clk = clocks.stop()
+    total_ms = max_over_ranks(total_ms, ws)
+    ms_step = total_ms / args.steps
+    value = ws * units / (ms_step * 1e-3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    vh = volt.cpu().pin_memory()
+    ih = torch.empty(img.shape, dtype=torch.float32).pin_memory()
+    vd = torch.empty_like(volt)
+    st = torch.cuda.current_stream()
+    for _ in range(2):
+        vd.copy_(vh, non_blocking=True)
+        hai.hai_epic_image(ctx, lay, vd, C, T, prec, img, 0, st)
+        ih.copy_(img, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0 = time.perf_counter()
+    e_steps = max(3, args.steps // 2)
+    for _ in range(e_steps):
+        vd.copy_(vh, non_blocking=True)
+        hai.hai_epic_image(ctx, lay, vd, C, T, prec, img, 0, st)
+        ih.copy_(img, non_blocking=True)
+    torch.cuda.synchronize()
+    e_ms = max_over_ranks((time.perf_counter() - e0) * 1e3 / e_steps, ws)
+    hai.hai_profile_read(ctx)
+
+    # plain FP32 form for comparison (metric: tensor cores vs plain FP32)
+    fp32 = None
+    if prec != hai.HAI_PREC_FP32 and not args.no_fp32_compare:
+        t32, d32, _ = time_epic(hai, ctx, lay, volt, img, C, T, hai.HAI_PREC_FP32, max(3, args.steps // 4),
+                                2, flush, ws)
+        fp32 = {"value": ws * units / (t32 / max(3, args.steps // 4) * 1e-3), "unit": UNIT}
+
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    flop_unit = epic_flops_per_unit(cfg)
+    achieved = flop_unit * units / (dom_ms * 1e-3) / 1e12
+    if prec == hai.HAI_PREC_FP32:
+        peak_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = fp32_alu_peak_tflops(sms, peak_mhz)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "epic_fp32_kernel", "peak_source":
+                f"derived: {sms} SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
+                "flop_per_unit": flop_unit, "kernel_ms": dom_ms}
+    else:
+        roof = None
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == hai.HAI_PREC_FP32 else "f16",
+            "data": "synthetic",
+            "config": {"workload": cfg.name, "elements": cfg.n_elem, "channels": C, "pols": P,
+                       "samples": T, "grid": n, "kernel_taps": cfg.ksize ** 2,
+                       "precision": args.prec, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{ws} (channels independent)"},
+            "e2e": {"value": ws * units / (e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(volt.numel()), "d2h_bytes_per_step": int(img.numel() * 4)},
+            "gpu_launches": int(launches), "clocks": clk, "roofline": roof}
+    if fp32 is not None:
+        line["plain_fp32"] = fp32
+        line["tc_over_fp32"] = value / fp32["value"]
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, pos, anchors, taps, n_chan=16)
+    hai.hai_layout_destroy(lay)
+    hai.hai_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

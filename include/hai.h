@@ -1,0 +1,143 @@
+/*
+ * hai.h -- C ABI of the GB300 hybrid aperture-array imaging library (libhai.so).
+ *
+ * The library implements the data-parallel hot path of the hybrid imaging
+ * architectures of Thyagarajan, "Comparison of Fast, Hybrid Imaging
+ * Architectures for Multi-scale, Hierarchical Aperture Arrays" (PASA):
+ *   - the generic FFT direct imager (EPIC): gridding of element voltages with
+ *     an illumination kernel, a 2D spatial DFT per (channel, sample, pol),
+ *     squaring (polarisation outer product) and accumulation over the cadence
+ *     (Section 5.2, Eq. intra-station EPIC + Eq. intra-station squaring);
+ *   - the comparison paths: the int8 correlator (Eq. intra-station
+ *     visibilities), the correlator + FFT imager (Eq. intra-station XFFT) and
+ *     the pre-correlation voltage beamformer (Eq. intra-station BF).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns hai_status; HAI_OK is 0.  On failure nothing is
+ *     launched and hai_last_error() returns a message (thread-local).
+ *   - Data buffers are owned by the caller and are DEVICE pointers (for
+ *     example torch tensors' data_ptr()) on the context's device, unless a
+ *     parameter says "host".  Opaque objects (context, layout) are owned by
+ *     the library and released with their destroy function.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Work is asynchronous on that stream; errors of the kernels
+ *     themselves surface at hai_sync() or at the next CUDA call.
+ *   - The compute entry points allocate no memory: scratch space is reserved
+ *     when the context or layout is created.
+ *   - Complex values are interleaved (re, im).  int8 voltages hold any value
+ *     in [-128, 127].
+ *   - Image planes: for P = 1 input polarisation one plane (XX); for P = 2
+ *     four planes XX, YY, Re XY, Im XY with XY = sum_t F_X conj(F_Y) (YX is
+ *     conj(XY) and not stored).  Images are row-major [l_y][l_x] with the
+ *     phase centre at pixel (N/2, N/2); pixel l looks along direction cosines
+ *     s = (l - N/2) / (N * cell), cell in wavelengths.  The temporal
+ *     "average" of the paper is returned as the SUM over the T samples.
+ */
+#ifndef HAI_H
+#define HAI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HAI_OK = 0,
+    HAI_ERR_INVALID_ARG = 1,   /* a size, pointer or enum is out of range  */
+    HAI_ERR_OFF_GRID = 2,      /* a gridding kernel tap falls off the grid */
+    HAI_ERR_OVERFLOW_RISK = 3, /* int32 accumulation could overflow        */
+    HAI_ERR_UNSUPPORTED = 4,   /* valid request this build does not cover  */
+    HAI_ERR_CUDA = 5,          /* a CUDA runtime call failed               */
+    HAI_ERR_TIMEOUT = 6,       /* a bounded device wait gave up            */
+    HAI_ERR_NO_MEMORY = 7      /* allocation at create time failed         */
+} hai_status;
+
+typedef enum {
+    HAI_PREC_FP32 = 0,   /* FP32 FFT on CUDA cores                              */
+    HAI_PREC_FP16 = 1    /* FP16 DFT-as-GEMM on tcgen05 tensor cores, FP32 acc.  */
+} hai_precision;
+
+typedef struct hai_ctx hai_ctx;
+typedef struct hai_layout hai_layout;
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int hai_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *hai_last_error(void);
+
+/* Name of a status code. */
+const char *hai_status_string(hai_status s);
+
+/* Create a context on CUDA device `device` (makes it current on this thread).
+ * Reserves the device status word used by bounded device-side waits. */
+hai_status hai_create(int device, hai_ctx **out);
+void hai_destroy(hai_ctx *ctx);
+
+/* Wait for `stream`, then report kernel faults: HAI_ERR_CUDA for a CUDA
+ * error, HAI_ERR_TIMEOUT if a bounded device wait gave up since the last
+ * call (the status word is cleared). */
+hai_status hai_sync(hai_ctx *ctx, void *stream);
+
+/* Profiling.  While enabled, every compute call records a pair of CUDA events
+ * on the caller's stream around its dominant kernel (the first kernels it
+ * launches are the one named in the call's description) and counts every
+ * kernel it launches.  Enabling creates an event pool of `max_records`
+ * pairs; further calls are counted but not timed. */
+hai_status hai_profile_enable(hai_ctx *ctx, int enable, int max_records);
+
+/* Synchronise the recorded events and return the summed duration (ms) of the
+ * timed dominant-kernel launches, their count, and the count of all kernels
+ * launched since the last read; then reset. */
+hai_status hai_profile_read(hai_ctx *ctx, double *dominant_ms, long long *dominant_launches,
+                            long long *total_launches);
+
+/* ---------------------------------------------------------------------------
+ * Station layout and gridding kernel (Eq. intra-station EPIC, the bracket:
+ * G[j] = sum_a conj(W~_a(r_j - r_a)) E_a).
+ * The illumination kernel W~ is an input: every element a carries an anchor
+ * cell (x0, y0) and ksize x ksize complex taps; tap (u, v) weights cell
+ * (x0 + u, y0 + v) of the N x N grid whose cell (N/2, N/2) holds the station
+ * origin.  The taps are used conjugated, as the equation states.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int n_elem;              /* N_e > 0                                       */
+    int grid_n;              /* N: power of two, 16..64 in this build         */
+    int ksize;               /* K >= 1                                        */
+    int n_pol;               /* P: 1 or 2                                     */
+    const int32_t *anchors;  /* host [n_elem][2] (x0, y0), copied             */
+    const float *taps;       /* host [n_elem][K][K][2] indexed [v][u][re,im]   */
+} hai_layout_desc;
+
+/* Copy the layout in and reserve its scratch.  HAI_ERR_OFF_GRID if any tap
+ * cell lies outside [0, N)^2; HAI_ERR_UNSUPPORTED for a grid size this build
+ * has no kernel for. */
+hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *desc, hai_layout **out);
+void hai_layout_destroy(hai_layout *layout);
+
+/* Bounding box of the cells the kernel touches, host int[4] = (x0, y0, x1, y1)
+ * half-open. */
+hai_status hai_layout_box(const hai_layout *layout, int *box);
+
+/* ---------------------------------------------------------------------------
+ * EPIC image: for every channel c the sum over samples t of the polarisation
+ * outer product of the synthesised fields F_{c,t,p}[l] =
+ * sum_j (-1)^(jx+jy) G_{c,t,p}[j] exp(+2 pi i l.j / N)
+ * (Eq. intra-station EPIC, then Eq. intra-station squaring with the temporal
+ * average taken as a sum).
+ *   volt  device int8 [C][T][P][N_e][2]
+ *   img   device float [C][Q][N][N], Q = 1 (P = 1) or 4 (P = 2); overwritten
+ *         (accumulate = 0) or added to (accumulate = 1)
+ *   prec  HAI_PREC_FP32 (CUDA-core FFT) or HAI_PREC_FP16 (tensor cores)
+ * C >= 0, T >= 0 (C = 0 or T = 0: nothing to image; with accumulate = 0 the
+ * image is zeroed). */
+hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *layout, const int8_t *volt,
+                          int C, int T, hai_precision prec, float *img, int accumulate,
+                          void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HAI_H */

@@ -1,0 +1,301 @@
+// EPIC direct imager, FP32 on CUDA cores (Eq. intra-station EPIC followed by
+// the squaring and temporal sum of Eq. intra-station squaring).
+//
+// One CTA sums a contiguous range of the flattened (channel, sample) index.
+// Per group of kSamples samples it
+//   1. stages the int8 voltages of the group in shared memory;
+//   2. row pass: one thread per (sample, pol, box row) gathers the gridded
+//      row sum_a conj(W~) E_a from the layout's gather table and transforms
+//      it along x with an N-point radix-2 FFT held in registers;
+//   3. column pass: one thread per (sample, pol, column) transforms along y,
+//      reading and writing its own column of the same shared buffer;
+//   4. squaring: every thread owns N*N/256 pixels and adds F_X conj(F_Y)
+//      products to register accumulators.
+// Only the kernel's bounding box is transformed, placed at the grid origin.
+// Shifting the input by (bx0, by0) multiplies F by exp(+2 pi i l.b / N), a
+// phase common to both polarisations that cancels in every F_a conj(F_b);
+// the (-1)^(jx+jy) phase-centre factor is an output shift by N/2.
+#include <math.h>
+
+#include "hai_internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kSamples = 2;        // samples per group
+constexpr int kTwN = 64;           // twiddle table resolution
+
+__constant__ float2 c_tw[kTwN / 2];   // exp(+2 pi i m / 64), m < 32
+
+__host__ __device__ constexpr int bitrev(int i, int n) {
+    int r = 0;
+    for (int b = 1; b < n; b <<= 1) r = (r << 1) | ((i & b) ? 1 : 0);
+    return r;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// In-register radix-2 decimation-in-time FFT, X[k] = sum_n x[n] e^{+2 pi i nk/N}.
+template <int N>
+__device__ __forceinline__ void fft_reg(float2 (&x)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const int j = bitrev(i, N);
+        if (i < j) {
+            float2 t = x[i];
+            x[i] = x[j];
+            x[j] = t;
+        }
+    }
+#pragma unroll
+    for (int len = 2; len <= N; len <<= 1) {
+        const int half = len / 2;
+#pragma unroll
+        for (int k = 0; k < half; k++) {
+#pragma unroll
+            for (int s = 0; s < N; s += len) {
+                float2 a = x[s + k], b = x[s + k + half], bw;
+                if (k == 0) {
+                    bw = b;
+                } else if (4 * k == len) {
+                    bw = make_float2(-b.y, b.x);               // times +i
+                } else {
+                    bw = cmul(b, c_tw[k * (kTwN / len)]);
+                }
+                x[s + k] = make_float2(a.x + bw.x, a.y + bw.y);
+                x[s + k + half] = make_float2(a.x - bw.x, a.y - bw.y);
+            }
+        }
+    }
+}
+
+template <int N, int P>
+struct EpicSmem {
+    static constexpr int NP = N + 1;                       // padded row stride
+    static constexpr int kBuf = kSamples * P * N * NP;     // float2 count
+};
+
+// Gridded value of one cell: sum over the cell's gather entries.
+__device__ __forceinline__ float2 grid_cell(int cell, const int32_t *__restrict__ cstart,
+                                            const int32_t *__restrict__ celem,
+                                            const float2 *__restrict__ cw, const char2 *e) {
+    float2 acc = make_float2(0.f, 0.f);
+    const int b = __ldg(cstart + cell), end = __ldg(cstart + cell + 1);
+    for (int i = b; i < end; i++) {
+        const int a = __ldg(celem + i);
+        const float2 w = __ldg(cw + i);
+        const char2 v = e[a];
+        const float er = (float)v.x, ei = (float)v.y;
+        acc.x = fmaf(w.x, er, fmaf(-w.y, ei, acc.x));
+        acc.y = fmaf(w.x, ei, fmaf(w.y, er, acc.y));
+    }
+    return acc;
+}
+
+template <int N, int P>
+__global__ void __launch_bounds__(kThreads, 1)
+epic_fp32_kernel(const int8_t *__restrict__ volt, int C, int T, int ne, long long len,
+                 int box_w, int box_h, const int32_t *__restrict__ cstart,
+                 const int32_t *__restrict__ celem, const float2 *__restrict__ cw,
+                 float *__restrict__ out, int direct, int accumulate) {
+    constexpr int Q = (P == 2) ? 4 : 1;
+    constexpr int NP = EpicSmem<N, P>::NP;
+    constexpr int PIX = N * N / kThreads;
+    static_assert(N * N % kThreads == 0, "pixels per thread");
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *buf = reinterpret_cast<float2 *>(smem);
+    char2 *vs = reinterpret_cast<char2 *>(smem + sizeof(float2) * EpicSmem<N, P>::kBuf);
+
+    const int tid = threadIdx.x;
+    const long long total = (long long)C * T;
+    const long long s0 = (long long)blockIdx.x * len;
+    const long long s1 = min(total, s0 + len);
+    const int sample_elems = P * ne;                 // char2 per sample
+
+    float acc[PIX][Q];
+#pragma unroll
+    for (int m = 0; m < PIX; m++)
+#pragma unroll
+        for (int q = 0; q < Q; q++) acc[m][q] = 0.f;
+
+    int seg = 0;
+    int cur_c = (int)(s0 / T);
+    auto flush = [&](int c, int sgm) {
+        float *dst;
+        if (direct) dst = out + (size_t)c * Q * N * N;
+        else dst = out + ((size_t)blockIdx.x * 2 + sgm) * Q * N * N;
+#pragma unroll
+        for (int m = 0; m < PIX; m++) {
+            const int pix = tid + m * kThreads;
+#pragma unroll
+            for (int q = 0; q < Q; q++) {
+                float v = acc[m][q];
+                if (direct && accumulate) v += dst[(size_t)q * N * N + pix];
+                dst[(size_t)q * N * N + pix] = v;
+                acc[m][q] = 0.f;
+            }
+        }
+    };
+
+    for (long long s = s0; s < s1;) {
+        const int c = (int)(s / T);
+        if (c != cur_c) {
+            flush(cur_c, seg);
+            seg++;
+            cur_c = c;
+        }
+        const long long chan_end = (long long)(c + 1) * T;
+        const int ng = (int)min((long long)kSamples, min(s1, chan_end) - s);
+
+        // 1. stage voltages of the group (contiguous bytes)
+        {
+            const size_t nbytes = (size_t)ng * sample_elems * 2;
+            const int8_t *src = volt + (size_t)s * sample_elems * 2;
+            int8_t *dst = reinterpret_cast<int8_t *>(vs);
+            if ((((uintptr_t)src) & 15) == 0 && (nbytes & 15) == 0) {
+                const int4 *s4 = reinterpret_cast<const int4 *>(src);
+                int4 *d4 = reinterpret_cast<int4 *>(dst);
+                for (size_t i = tid; i < nbytes / 16; i += kThreads) d4[i] = __ldg(s4 + i);
+            } else {
+                for (size_t i = tid; i < nbytes; i += kThreads) dst[i] = src[i];
+            }
+        }
+        __syncthreads();
+
+        // 2. row pass: grid + FFT along x
+        for (int task = tid; task < ng * P * box_h; task += kThreads) {
+            const int g = task / (P * box_h);
+            const int p = (task / box_h) % P;
+            const int y = task % box_h;
+            const char2 *e = vs + (size_t)(g * P + p) * ne;
+            float2 x[N];
+#pragma unroll
+            for (int u = 0; u < N; u++)
+                x[u] = (u < box_w) ? grid_cell(y * box_w + u, cstart, celem, cw, e) : make_float2(0.f, 0.f);
+            fft_reg<N>(x);
+            float2 *row = buf + (size_t)(g * P + p) * N * NP + (size_t)y * NP;
+#pragma unroll
+            for (int k = 0; k < N; k++) row[k] = x[k];
+        }
+        __syncthreads();
+
+        // 3. column pass: FFT along y (rows >= box_h are zero)
+        for (int task = tid; task < ng * P * N; task += kThreads) {
+            const int gp = task / N;
+            const int k = task % N;
+            float2 *col = buf + (size_t)gp * N * NP + k;
+            float2 x[N];
+#pragma unroll
+            for (int r = 0; r < N; r++) x[r] = (r < box_h) ? col[(size_t)r * NP] : make_float2(0.f, 0.f);
+            fft_reg<N>(x);
+#pragma unroll
+            for (int r = 0; r < N; r++) col[(size_t)r * NP] = x[r];
+        }
+        __syncthreads();
+
+        // 4. squaring and accumulation (pixel l reads F at l + N/2 mod N)
+#pragma unroll
+        for (int m = 0; m < PIX; m++) {
+            const int pix = tid + m * kThreads;
+            const int ly = pix / N, lx = pix % N;
+            const int src = ((ly + N / 2) & (N - 1)) * NP + ((lx + N / 2) & (N - 1));
+            for (int g = 0; g < ng; g++) {
+                const float2 fx = buf[(size_t)(g * P) * N * NP + src];
+                acc[m][0] = fmaf(fx.x, fx.x, fmaf(fx.y, fx.y, acc[m][0]));
+                if (P == 2) {
+                    const float2 fy = buf[(size_t)(g * P + 1) * N * NP + src];
+                    acc[m][Q > 1 ? 1 : 0] = fmaf(fy.x, fy.x, fmaf(fy.y, fy.y, acc[m][Q > 1 ? 1 : 0]));
+                    acc[m][Q > 2 ? 2 : 0] = fmaf(fx.x, fy.x, fmaf(fx.y, fy.y, acc[m][Q > 2 ? 2 : 0]));
+                    acc[m][Q > 3 ? 3 : 0] = fmaf(fx.y, fy.x, fmaf(-fx.x, fy.y, acc[m][Q > 3 ? 3 : 0]));
+                }
+            }
+        }
+        __syncthreads();
+        s += ng;
+    }
+    if (s1 > s0) flush(cur_c, seg);
+}
+
+// img[c] = (accumulate ? img[c] : 0) + sum of the partials of channel c, in
+// CTA order.  CTA b covers samples [b*len, (b+1)*len) of the flat index.
+__global__ void epic_reduce_kernel(const float *__restrict__ part, float *__restrict__ img, int C,
+                                   int T, long long len, int plane, int accumulate) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)C * plane) return;
+    const int c = (int)(i / plane);
+    const int off = (int)(i % plane);
+    const int b0 = (int)(((long long)c * T) / len);
+    const int b1 = (int)(((long long)(c + 1) * T - 1) / len);
+    float s = 0.f;
+    for (int b = b0; b <= b1; b++) {
+        const int first = (int)(((long long)b * len) / T);
+        const int sgm = c - first;
+        s += part[((size_t)b * 2 + sgm) * plane + off];
+    }
+    img[i] = accumulate ? img[i] + s : s;
+}
+
+template <int N, int P>
+hai_status launch_n(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
+                    cudaStream_t st) {
+    const size_t smem = sizeof(float2) * EpicSmem<N, P>::kBuf +
+                        ((size_t)kSamples * P * L->n_elem * 2 + 15) / 16 * 16;
+    if (smem > (size_t)L->ctx->smem_optin)
+        return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp32: shared memory need exceeds the device limit");
+    auto kern = epic_fp32_kernel<N, P>;
+    HAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const EpicSplit sp = epic_make_split(C, T, epic_fp32_target_ctas(L->ctx, N));
+    if (!sp.direct && (size_t)sp.n_cta * 2 > L->partial_slots)
+        return hai_fail(HAI_ERR_INVALID_ARG, "epic fp32: partial buffer too small");
+    float *dst = sp.direct ? img : L->d_partials;
+    const int pidx = prof_begin(L->ctx, st);
+    kern<<<sp.n_cta, kThreads, smem, st>>>(volt, C, T, L->n_elem, sp.len, L->box_w, L->box_h,
+                                           L->d_cell_start, L->d_entry_elem, L->d_entry_w, dst,
+                                           sp.direct, accumulate);
+    prof_end(L->ctx, pidx, st);
+    prof_count(L->ctx, 1);
+    HAI_CUDA_TRY(cudaGetLastError());
+    if (!sp.direct) return epic_reduce_launch(L, sp, C, T, img, accumulate, st);
+    return HAI_OK;
+}
+
+}  // namespace
+
+hai_status epic_fp32_init_tables(void) {
+    float2 tw[kTwN / 2];
+    for (int m = 0; m < kTwN / 2; m++) {
+        const double ang = 2.0 * 3.14159265358979323846 * m / kTwN;
+        tw[m] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+    HAI_CUDA_TRY(cudaMemcpyToSymbol(c_tw, tw, sizeof(tw)));
+    return HAI_OK;
+}
+
+int epic_fp32_target_ctas(const hai_ctx *ctx, int) { return ctx->num_sms; }
+
+hai_status epic_reduce_launch(const hai_layout *L, const EpicSplit &sp, int C, int T, float *img,
+                              int accumulate, cudaStream_t st) {
+    const int Q = (L->n_pol == 2) ? 4 : 1;
+    const int plane = Q * L->grid_n * L->grid_n;
+    const long long n = (long long)C * plane;
+    const int threads = 256;
+    epic_reduce_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
+        L->d_partials, img, C, T, sp.len, plane, accumulate);
+    prof_count(L->ctx, 1);
+    HAI_CUDA_TRY(cudaGetLastError());
+    return HAI_OK;
+}
+
+hai_status epic_fp32_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img,
+                            int accumulate, cudaStream_t st) {
+    const int n = L->grid_n, p = L->n_pol;
+    if (n == 16) return p == 2 ? launch_n<16, 2>(L, volt, C, T, img, accumulate, st)
+                               : launch_n<16, 1>(L, volt, C, T, img, accumulate, st);
+    if (n == 32) return p == 2 ? launch_n<32, 2>(L, volt, C, T, img, accumulate, st)
+                               : launch_n<32, 1>(L, volt, C, T, img, accumulate, st);
+    if (n == 64) return p == 2 ? launch_n<64, 2>(L, volt, C, T, img, accumulate, st)
+                               : launch_n<64, 1>(L, volt, C, T, img, accumulate, st);
+    return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp32: grid size");
+}

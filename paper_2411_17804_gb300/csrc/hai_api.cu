@@ -1,0 +1,321 @@
+// Host side of the C ABI: contexts, layouts, argument checks, dispatch.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "hai_internal.h"
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+void hai_set_error(const std::string &msg) { g_last_error = msg; }
+
+hai_status hai_fail(hai_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+hai_status hai_cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return HAI_ERR_CUDA;
+}
+
+// HAI_FAULT is a comma-separated list of sites ("alloc", "launch", "timeout")
+// at which the host wrapper reports a failure without touching the GPU.
+bool hai_fault_injected(const char *site) {
+    const char *env = getenv("HAI_FAULT");
+    if (!env || !*env) return false;
+    std::string s(env);
+    size_t pos = 0;
+    while (pos <= s.size()) {
+        size_t e = s.find(',', pos);
+        if (e == std::string::npos) e = s.size();
+        if (s.compare(pos, e - pos, site) == 0) return true;
+        pos = e + 1;
+    }
+    return false;
+}
+
+extern "C" int hai_version(void) { return 100; }
+
+extern "C" const char *hai_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char *hai_status_string(hai_status s) {
+    switch (s) {
+        case HAI_OK: return "HAI_OK";
+        case HAI_ERR_INVALID_ARG: return "HAI_ERR_INVALID_ARG";
+        case HAI_ERR_OFF_GRID: return "HAI_ERR_OFF_GRID";
+        case HAI_ERR_OVERFLOW_RISK: return "HAI_ERR_OVERFLOW_RISK";
+        case HAI_ERR_UNSUPPORTED: return "HAI_ERR_UNSUPPORTED";
+        case HAI_ERR_CUDA: return "HAI_ERR_CUDA";
+        case HAI_ERR_TIMEOUT: return "HAI_ERR_TIMEOUT";
+        case HAI_ERR_NO_MEMORY: return "HAI_ERR_NO_MEMORY";
+    }
+    return "HAI_ERR_UNKNOWN";
+}
+
+// ------------------------------------------------------------------ context
+hai_status epic_fp32_init_tables(void);
+
+extern "C" hai_status hai_create(int device, hai_ctx **out) {
+    if (!out) return hai_fail(HAI_ERR_INVALID_ARG, "hai_create: out is NULL");
+    *out = nullptr;
+    if (hai_fault_injected("alloc")) return hai_fail(HAI_ERR_NO_MEMORY, "hai_create: injected allocation failure");
+    int ndev = 0;
+    HAI_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return hai_fail(HAI_ERR_INVALID_ARG, "hai_create: no such device");
+    HAI_CUDA_TRY(cudaSetDevice(device));
+    hai_ctx *c = new hai_ctx();
+    c->device = device;
+    cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        if (c->d_status) cudaFree(c->d_status);
+        delete c;
+        return hai_cuda_fail(e, "hai_create");
+    }
+    hai_status s = epic_fp32_init_tables();
+    if (s != HAI_OK) {
+        cudaFree(c->d_status);
+        delete c;
+        return s;
+    }
+    *out = c;
+    return HAI_OK;
+}
+
+static void prof_release(hai_ctx *ctx) {
+    for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+    ctx->prof_ev.clear();
+    ctx->prof_used = 0;
+}
+
+extern "C" void hai_destroy(hai_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    prof_release(ctx);
+    cudaFree(ctx->d_status);
+    delete ctx;
+}
+
+extern "C" hai_status hai_profile_enable(hai_ctx *ctx, int enable, int max_records) {
+    if (!ctx || max_records < 0) return hai_fail(HAI_ERR_INVALID_ARG, "hai_profile_enable: bad argument");
+    HAI_CUDA_TRY(cudaSetDevice(ctx->device));
+    prof_release(ctx);
+    ctx->prof_on = enable ? 1 : 0;
+    ctx->prof_launches = 0;
+    if (enable) {
+        ctx->prof_ev.resize(2 * (size_t)max_records);
+        for (size_t i = 0; i < ctx->prof_ev.size(); i++) {
+            cudaError_t e = cudaEventCreate(&ctx->prof_ev[i]);
+            if (e != cudaSuccess) {
+                ctx->prof_ev.resize(i);
+                prof_release(ctx);
+                ctx->prof_on = 0;
+                return hai_cuda_fail(e, "hai_profile_enable");
+            }
+        }
+    }
+    return HAI_OK;
+}
+
+int prof_begin(hai_ctx *ctx, cudaStream_t st) {
+    if (!ctx->prof_on || 2 * (ctx->prof_used + 1) > ctx->prof_ev.size()) return -1;
+    int idx = (int)ctx->prof_used++;
+    cudaEventRecord(ctx->prof_ev[2 * idx], st);
+    return idx;
+}
+
+void prof_end(hai_ctx *ctx, int idx, cudaStream_t st) {
+    if (idx >= 0) cudaEventRecord(ctx->prof_ev[2 * idx + 1], st);
+}
+
+extern "C" hai_status hai_profile_read(hai_ctx *ctx, double *ms, long long *n_dom, long long *n_all) {
+    if (!ctx || !ms || !n_dom || !n_all) return hai_fail(HAI_ERR_INVALID_ARG, "hai_profile_read: NULL argument");
+    HAI_CUDA_TRY(cudaSetDevice(ctx->device));
+    double tot = 0.0;
+    for (size_t i = 0; i < ctx->prof_used; i++) {
+        HAI_CUDA_TRY(cudaEventSynchronize(ctx->prof_ev[2 * i + 1]));
+        float e = 0.f;
+        HAI_CUDA_TRY(cudaEventElapsedTime(&e, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]));
+        tot += e;
+    }
+    *ms = tot;
+    *n_dom = (long long)ctx->prof_used;
+    *n_all = ctx->prof_launches;
+    ctx->prof_used = 0;
+    ctx->prof_launches = 0;
+    return HAI_OK;
+}
+
+extern "C" hai_status hai_sync(hai_ctx *ctx, void *stream) {
+    if (!ctx) return hai_fail(HAI_ERR_INVALID_ARG, "hai_sync: ctx is NULL");
+    if (hai_fault_injected("timeout")) return hai_fail(HAI_ERR_TIMEOUT, "hai_sync: injected device timeout");
+    HAI_CUDA_TRY(cudaSetDevice(ctx->device));
+    HAI_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned st = 0;
+    HAI_CUDA_TRY(cudaMemcpy(&st, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (st) {
+        HAI_CUDA_TRY(cudaMemset(ctx->d_status, 0, sizeof(unsigned)));
+        if (st & HAI_DEV_TIMEOUT) return hai_fail(HAI_ERR_TIMEOUT, "a bounded device wait gave up");
+        return hai_fail(HAI_ERR_CUDA, "a device-side bounds check fired");
+    }
+    return HAI_OK;
+}
+
+// ------------------------------------------------------------------ layout
+static bool grid_supported(int n) { return n == 16 || n == 32 || n == 64; }
+
+static void layout_free(hai_layout *L) {
+    if (!L) return;
+    cudaFree(L->d_cell_start);
+    cudaFree(L->d_entry_elem);
+    cudaFree(L->d_entry_w);
+    cudaFree(L->d_partials);
+    cudaFree(L->d_tc_tables);
+    delete L;
+}
+
+extern "C" hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *d, hai_layout **out) {
+    if (!ctx || !d || !out) return hai_fail(HAI_ERR_INVALID_ARG, "hai_layout_create: NULL argument");
+    *out = nullptr;
+    if (d->n_elem <= 0 || d->ksize <= 0 || d->grid_n <= 0 || (d->n_pol != 1 && d->n_pol != 2) ||
+        !d->anchors || !d->taps)
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_layout_create: bad descriptor");
+    if ((d->grid_n & (d->grid_n - 1)) != 0)
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_layout_create: grid_n must be a power of two");
+    if (!grid_supported(d->grid_n))
+        return hai_fail(HAI_ERR_UNSUPPORTED, "hai_layout_create: grid_n not supported by this build");
+    const int n = d->grid_n, k = d->ksize, ne = d->n_elem;
+    int bx0 = n, by0 = n, bx1 = 0, by1 = 0;
+    for (int a = 0; a < ne; a++) {
+        int x0 = d->anchors[2 * a], y0 = d->anchors[2 * a + 1];
+        if (x0 < 0 || y0 < 0 || (long)x0 + k > n || (long)y0 + k > n)
+            return hai_fail(HAI_ERR_OFF_GRID, "hai_layout_create: element " + std::to_string(a) +
+                                                  " has taps outside the grid");
+        bx0 = std::min(bx0, x0);
+        by0 = std::min(by0, y0);
+        bx1 = std::max(bx1, x0 + k);
+        by1 = std::max(by1, y0 + k);
+    }
+    if (hai_fault_injected("alloc")) return hai_fail(HAI_ERR_NO_MEMORY, "hai_layout_create: injected allocation failure");
+
+    hai_layout *L = new hai_layout();
+    L->ctx = ctx;
+    L->n_elem = ne;
+    L->grid_n = n;
+    L->ksize = k;
+    L->n_pol = d->n_pol;
+    L->box[0] = bx0; L->box[1] = by0; L->box[2] = bx1; L->box[3] = by1;
+    L->box_w = bx1 - bx0;
+    L->box_h = by1 - by0;
+    L->h_anchors.assign(d->anchors, d->anchors + 2 * (size_t)ne);
+    L->h_taps.assign(d->taps, d->taps + 2 * (size_t)ne * k * k);
+
+    // gather table: cells of the box in row-major order, entries by element
+    const int ncell = L->box_w * L->box_h;
+    std::vector<int32_t> count(ncell + 1, 0);
+    for (int a = 0; a < ne; a++)
+        for (int v = 0; v < k; v++)
+            for (int u = 0; u < k; u++) {
+                int cell = (d->anchors[2 * a + 1] + v - by0) * L->box_w + (d->anchors[2 * a] + u - bx0);
+                count[cell + 1]++;
+            }
+    for (int i = 0; i < ncell; i++) count[i + 1] += count[i];
+    L->nnz = count[ncell];
+    std::vector<int32_t> fill(count.begin(), count.end() - 1);
+    std::vector<int32_t> elem(L->nnz);
+    std::vector<float2> w(L->nnz);
+    for (int a = 0; a < ne; a++)
+        for (int v = 0; v < k; v++)
+            for (int u = 0; u < k; u++) {
+                int cell = (d->anchors[2 * a + 1] + v - by0) * L->box_w + (d->anchors[2 * a] + u - bx0);
+                const float *t = d->taps + (((size_t)a * k + v) * k + u) * 2;
+                int slot = fill[cell]++;
+                elem[slot] = a;
+                w[slot] = make_float2(t[0], -t[1]);   // conj(W~)
+            }
+
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc(&L->d_cell_start, sizeof(int32_t) * (ncell + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&L->d_entry_elem, sizeof(int32_t) * std::max(1, L->nnz));
+    if (e == cudaSuccess) e = cudaMalloc(&L->d_entry_w, sizeof(float2) * std::max(1, L->nnz));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(L->d_cell_start, count.data(), sizeof(int32_t) * (ncell + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(L->d_entry_elem, elem.data(), sizeof(int32_t) * L->nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(L->d_entry_w, w.data(), sizeof(float2) * L->nnz, cudaMemcpyHostToDevice);
+    // partial images of the time split (two channel segments per CTA)
+    const int Q = (L->n_pol == 2) ? 4 : 1;
+    L->partial_slots = epic_partial_slots(epic_fp32_target_ctas(ctx, n));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&L->d_partials, sizeof(float) * L->partial_slots * Q * (size_t)n * n);
+    if (e != cudaSuccess) {
+        layout_free(L);
+        if (e == cudaErrorMemoryAllocation) return hai_cuda_fail(e, "hai_layout_create: allocation");
+        return hai_cuda_fail(e, "hai_layout_create");
+    }
+    *out = L;
+    return HAI_OK;
+}
+
+extern "C" void hai_layout_destroy(hai_layout *L) {
+    if (!L) return;
+    cudaSetDevice(L->ctx->device);
+    layout_free(L);
+}
+
+extern "C" hai_status hai_layout_box(const hai_layout *L, int *box) {
+    if (!L || !box) return hai_fail(HAI_ERR_INVALID_ARG, "hai_layout_box: NULL argument");
+    memcpy(box, L->box, sizeof(L->box));
+    return HAI_OK;
+}
+
+// ------------------------------------------------------------------ EPIC
+EpicSplit epic_make_split(int C, int T, int target_ctas) {
+    EpicSplit sp;
+    if (C >= target_ctas) {
+        sp.direct = 1;
+        sp.n_cta = C;
+        sp.len = T;
+        return sp;
+    }
+    long long total = (long long)C * T;
+    sp.len = (total + target_ctas - 1) / target_ctas;   // <= T since C < target
+    sp.n_cta = (int)((total + sp.len - 1) / sp.len);
+    return sp;
+}
+
+size_t epic_partial_slots(int target_ctas) { return 2 * (size_t)target_ctas; }
+
+extern "C" hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *L, const int8_t *volt, int C,
+                                     int T, hai_precision prec, float *img, int accumulate,
+                                     void *stream) {
+    if (!ctx || !L) return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: NULL ctx or layout");
+    if (L->ctx != ctx) return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: layout of another context");
+    if (C < 0 || T < 0) return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: negative C or T");
+    if (accumulate != 0 && accumulate != 1)
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: accumulate must be 0 or 1");
+    if (prec != HAI_PREC_FP32 && prec != HAI_PREC_FP16)
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: unknown precision");
+    if (C == 0) return HAI_OK;
+    if (!img || (T > 0 && !volt)) return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: NULL buffer");
+    if (hai_fault_injected("launch")) return hai_fail(HAI_ERR_CUDA, "hai_epic_image: injected launch failure");
+    HAI_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int Q = (L->n_pol == 2) ? 4 : 1;
+    if (T == 0) {
+        if (!accumulate)
+            HAI_CUDA_TRY(cudaMemsetAsync(img, 0, sizeof(float) * (size_t)C * Q * L->grid_n * L->grid_n, st));
+        return HAI_OK;
+    }
+    if (prec == HAI_PREC_FP32) return epic_fp32_launch(L, volt, C, T, img, accumulate, st);
+    return hai_fail(HAI_ERR_UNSUPPORTED, "hai_epic_image: FP16 tensor-core path not built yet");
+}

@@ -1,0 +1,81 @@
+// Internal declarations shared by the host API and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hai.h"
+
+// Device status word bits, set by kernels whose bounded waits give up.
+enum : unsigned { HAI_DEV_TIMEOUT = 1u, HAI_DEV_BOUNDS = 2u };
+
+struct hai_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int smem_optin = 0;
+    unsigned *d_status = nullptr;   // device status word
+    // profiling (hai_profile_enable)
+    int prof_on = 0;
+    std::vector<cudaEvent_t> prof_ev;   // pairs: [2i] before, [2i+1] after
+    size_t prof_used = 0;               // pairs recorded
+    long long prof_launches = 0;        // all kernels launched
+};
+
+// Profiling helpers: prof_begin returns the pair index or -1.
+int prof_begin(hai_ctx *ctx, cudaStream_t st);
+void prof_end(hai_ctx *ctx, int idx, cudaStream_t st);
+inline void prof_count(hai_ctx *ctx, int n) { if (ctx->prof_on) ctx->prof_launches += n; }
+
+// Gather table of the gridding step: for every cell of the kernel's bounding
+// box (row-major inside the box) the list of (element, conj tap) pairs.
+struct hai_layout {
+    hai_ctx *ctx = nullptr;
+    int n_elem = 0, grid_n = 0, ksize = 0, n_pol = 0;
+    int box[4] = {0, 0, 0, 0};          // x0, y0, x1, y1 (half-open)
+    int box_w = 0, box_h = 0;
+    int nnz = 0;
+    std::vector<int32_t> h_anchors;     // host copy [n_elem][2]
+    std::vector<float> h_taps;          // host copy [n_elem][K][K][2]
+    int32_t *d_cell_start = nullptr;    // [box_w * box_h + 1]
+    int32_t *d_entry_elem = nullptr;    // [nnz]
+    float2 *d_entry_w = nullptr;        // [nnz] conj(tap)
+    float *d_partials = nullptr;        // EPIC time-split partial images
+    size_t partial_slots = 0;           // capacity in images of [Q][N][N]
+    // tensor-core path tables (fp16 DFT operands); built at create time
+    void *d_tc_tables = nullptr;
+    size_t tc_tables_bytes = 0;
+};
+
+// ---------------------------------------------------------------- errors
+void hai_set_error(const std::string &msg);
+hai_status hai_fail(hai_status s, const std::string &msg);
+hai_status hai_cuda_fail(cudaError_t e, const char *what);
+bool hai_fault_injected(const char *site);   // host-side fault injection
+
+#define HAI_CUDA_TRY(call)                                         \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return hai_cuda_fail(_e, #call);    \
+    } while (0)
+
+// ---------------------------------------------------------------- EPIC split
+// The (channel, sample) space is cut into n_cta contiguous ranges of the
+// flattened index c * T + t; each CTA sums its range per channel segment into
+// a partial image, and epic_reduce adds the partials of each channel in CTA
+// order (deterministic).
+struct EpicSplit {
+    int n_cta = 0;        // CTAs launched
+    long long len = 0;    // samples per CTA (last may be shorter)
+    int direct = 0;       // 1: one CTA per channel writes img directly
+};
+EpicSplit epic_make_split(int C, int T, int target_ctas);
+size_t epic_partial_slots(int target_ctas);
+
+hai_status epic_fp32_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img,
+                            int accumulate, cudaStream_t st);
+int epic_fp32_target_ctas(const hai_ctx *ctx, int grid_n);
+hai_status epic_reduce_launch(const hai_layout *L, const EpicSplit &sp, int C, int T, float *img,
+                              int accumulate, cudaStream_t st);

@@ -1,0 +1,181 @@
+"""Python binding of libhai.so (include/hai.h): argument marshalling only.
+
+Every function keeps the C name and forwards to the C ABI; torch tensors
+provide device memory and streams.  Each step of the imaging path runs in the
+library's CUDA kernels: this module computes nothing, and it raises if the
+library is missing rather than falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+HAI_OK = 0
+STATUS_NAMES = {0: "HAI_OK", 1: "HAI_ERR_INVALID_ARG", 2: "HAI_ERR_OFF_GRID",
+                3: "HAI_ERR_OVERFLOW_RISK", 4: "HAI_ERR_UNSUPPORTED", 5: "HAI_ERR_CUDA",
+                6: "HAI_ERR_TIMEOUT", 7: "HAI_ERR_NO_MEMORY"}
+HAI_PREC_FP32 = 0
+HAI_PREC_FP16 = 1
+
+
+class HaiError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class _LayoutDesc(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int), ("grid_n", ctypes.c_int), ("ksize", ctypes.c_int),
+                ("n_pol", ctypes.c_int), ("anchors", ctypes.c_void_p), ("taps", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+_int = ctypes.c_int
+
+
+def _declare(L):
+    L.hai_version.restype = _int
+    L.hai_last_error.restype = ctypes.c_char_p
+    L.hai_status_string.restype = ctypes.c_char_p
+    L.hai_status_string.argtypes = [_int]
+    L.hai_create.argtypes = [_int, ctypes.POINTER(_vp)]
+    L.hai_destroy.argtypes = [_vp]
+    L.hai_destroy.restype = None
+    L.hai_sync.argtypes = [_vp, _vp]
+    L.hai_layout_create.argtypes = [_vp, ctypes.POINTER(_LayoutDesc), ctypes.POINTER(_vp)]
+    L.hai_layout_destroy.argtypes = [_vp]
+    L.hai_layout_destroy.restype = None
+    L.hai_layout_box.argtypes = [_vp, ctypes.POINTER(_int)]
+    L.hai_epic_image.argtypes = [_vp, _vp, _vp, _int, _int, _int, _vp, _int, _vp]
+    L.hai_profile_enable.argtypes = [_vp, _int, _int]
+    L.hai_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+
+
+def load(build: bool = True):
+    """Load (building first if needed) the in-tree libhai.so."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build else _build.LIBPATH
+            if not os.path.exists(path):
+                raise RuntimeError(f"libhai.so missing at {path}; build it with __graft_entry__.build()")
+            L = ctypes.CDLL(path)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != HAI_OK:
+        raise HaiError(rc, where, load().hai_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _dev_ptr(t, dtype, name, numel=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return t.data_ptr()
+
+
+# ------------------------------------------------------------------ C API
+def hai_version() -> int:
+    return load().hai_version()
+
+
+def hai_status_string(s: int) -> str:
+    return load().hai_status_string(s).decode()
+
+
+def hai_last_error() -> str:
+    return load().hai_last_error().decode()
+
+
+def hai_create(device: int = 0):
+    h = _vp()
+    _check(load().hai_create(device, ctypes.byref(h)), "hai_create")
+    return h
+
+
+def hai_destroy(ctx):
+    load().hai_destroy(ctx)
+
+
+def hai_sync(ctx, stream=None):
+    _check(load().hai_sync(ctx, _stream(stream)), "hai_sync")
+
+
+def hai_profile_enable(ctx, enable: bool = True, max_records: int = 4096):
+    _check(load().hai_profile_enable(ctx, int(enable), max_records), "hai_profile_enable")
+
+
+def hai_profile_read(ctx):
+    """(dominant-kernel ms summed, timed launches, all kernel launches)."""
+    ms, nd, na = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load().hai_profile_read(ctx, ctypes.byref(ms), ctypes.byref(nd), ctypes.byref(na)),
+           "hai_profile_read")
+    return ms.value, nd.value, na.value
+
+
+class Layout:
+    """Handle of a hai_layout plus the sizes the binding checks buffers with."""
+
+    def __init__(self, handle, n_elem, grid_n, ksize, n_pol):
+        self.handle, self.n_elem, self.grid_n, self.ksize, self.n_pol = handle, n_elem, grid_n, ksize, n_pol
+
+    @property
+    def n_planes(self):
+        return 4 if self.n_pol == 2 else 1
+
+
+def hai_layout_create(ctx, anchors, taps, grid_n: int, n_pol: int) -> Layout:
+    anchors = np.ascontiguousarray(anchors, np.int32)
+    taps = np.ascontiguousarray(taps, np.float32)
+    ne, k = anchors.shape[0], taps.shape[1]
+    if anchors.shape != (ne, 2) or taps.shape != (ne, k, k, 2):
+        raise ValueError("anchors must be [n][2] and taps [n][K][K][2]")
+    d = _LayoutDesc(ne, grid_n, k, n_pol, anchors.ctypes.data, taps.ctypes.data)
+    h = _vp()
+    _check(load().hai_layout_create(ctx, ctypes.byref(d), ctypes.byref(h)), "hai_layout_create")
+    return Layout(h, ne, grid_n, k, n_pol)
+
+
+def hai_layout_destroy(layout: Layout):
+    load().hai_layout_destroy(layout.handle)
+
+
+def hai_layout_box(layout: Layout):
+    box = (_int * 4)()
+    _check(load().hai_layout_box(layout.handle, box), "hai_layout_box")
+    return tuple(box)
+
+
+def hai_epic_image(ctx, layout: Layout, volt, C: int, T: int, prec: int, img, accumulate: int = 0,
+                   stream=None):
+    import torch
+    P, ne, n = layout.n_pol, layout.n_elem, layout.grid_n
+    vp = _dev_ptr(volt, torch.int8, "volt", C * T * P * ne * 2) if C * T > 0 else 0
+    ip = _dev_ptr(img, torch.float32, "img", C * layout.n_planes * n * n) if C > 0 else 0
+    _check(load().hai_epic_image(ctx, layout.handle, vp, C, T, prec, ip, accumulate, _stream(stream)),
+           "hai_epic_image")

@@ -1,0 +1,134 @@
+"""GPU parity of the EPIC imager (FP32 path) against the FP64 oracle, through
+the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2411_17804_gb300 import inputs as I
+from tests.helpers import FP32_TOL, rel_err_planes, station
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(hai):
+    c = hai.hai_create(0)
+    yield c
+    hai.hai_destroy(c)
+
+
+def run_epic(hai, ctx, anchors, taps, n, volt, prec, accumulate=0, img=None):
+    C, T, P = volt.shape[:3]
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, P)
+    try:
+        if img is None:
+            img = torch.full((C, lay.n_planes, n, n), float("nan"), device="cuda")
+        hai.hai_epic_image(ctx, lay, volt.cuda().contiguous(), C, T, prec, img, accumulate)
+        hai.hai_sync(ctx)
+        return img.cpu().numpy()
+    finally:
+        hai.hai_layout_destroy(lay)
+
+
+def test_single_station_64_full_size(hai, ctx):
+    cfg = I.SINGLE_STATION_64
+    pos, anchors, taps = station(cfg)
+    volt = I.station_voltages(cfg, pos)
+    got = run_epic(hai, ctx, anchors, taps, cfg.grid_n, volt, hai.HAI_PREC_FP32)
+    want = O.epic_image(cfg.grid_n, anchors, taps, volt.numpy())
+    err = rel_err_planes(got, want)
+    assert err.max() < FP32_TOL, err
+    assert np.abs(got - want).max() / np.abs(want).max() < FP32_TOL
+
+
+@pytest.mark.parametrize("C,T", [(3, 40), (1, 7), (5, 1), (2, 301)])
+def test_ska_station_ragged_splits(hai, ctx, C, T):
+    cfg = I.SKA_LOW_STATION_256
+    pos, anchors, taps = station(cfg)
+    volt = I.station_voltages(cfg, pos, n_chan=C, n_time=T)
+    got = run_epic(hai, ctx, anchors, taps, cfg.grid_n, volt, hai.HAI_PREC_FP32)
+    want = O.epic_image(cfg.grid_n, anchors, taps, volt.numpy())
+    assert rel_err_planes(got, want).max() < FP32_TOL
+
+
+@pytest.mark.parametrize("n,P,ne", [(16, 1, 5), (16, 2, 1), (32, 2, 40), (64, 1, 300)])
+def test_grid_sizes_pols_and_element_counts(hai, ctx, n, P, ne):
+    rng = np.random.default_rng(n + P + ne)
+    k = 3
+    anchors = rng.integers(0, n - k + 1, (ne, 2)).astype(np.int32)
+    taps = rng.standard_normal((ne, k, k, 2)).astype(np.float32)
+    volt = I.random_voltages((2, 9, P, ne, 2), seed=ne)
+    got = run_epic(hai, ctx, anchors, taps, n, volt, hai.HAI_PREC_FP32)
+    want = O.epic_image(n, anchors, taps, volt.numpy())
+    assert rel_err_planes(got, want).max() < FP32_TOL
+
+
+def test_adversarial_extreme_voltages(hai, ctx):
+    cfg = I.SKA_LOW_STATION_256
+    pos, anchors, taps = station(cfg)
+    volt = torch.full((2, 16, 2, len(pos), 2), -128, dtype=torch.int8)
+    volt[:, ::2, 1, :, 1] = 127
+    got = run_epic(hai, ctx, anchors, taps, cfg.grid_n, volt, hai.HAI_PREC_FP32)
+    want = O.epic_image(cfg.grid_n, anchors, taps, volt.numpy())
+    assert rel_err_planes(got, want).max() < FP32_TOL
+
+
+def test_accumulate_and_empty_cadence(hai, ctx):
+    cfg = I.SKA_LOW_STATION_256
+    pos, anchors, taps = station(cfg)
+    volt = I.station_voltages(cfg, pos, n_chan=2, n_time=12)
+    n = cfg.grid_n
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, 2)
+    img = torch.zeros((2, 4, n, n), device="cuda")
+    v = volt.cuda()
+    hai.hai_epic_image(ctx, lay, v[:, :5].contiguous(), 2, 5, hai.HAI_PREC_FP32, img, 0)
+    hai.hai_epic_image(ctx, lay, v[:, 5:].contiguous(), 2, 7, hai.HAI_PREC_FP32, img, 1)
+    hai.hai_sync(ctx)
+    want = O.epic_image(n, anchors, taps, volt.numpy())
+    assert rel_err_planes(img.cpu().numpy(), want).max() < FP32_TOL
+    # T = 0 zeroes the image (accumulate = 0) or leaves it (accumulate = 1)
+    hai.hai_epic_image(ctx, lay, v, 2, 0, hai.HAI_PREC_FP32, img, 1)
+    hai.hai_sync(ctx)
+    assert rel_err_planes(img.cpu().numpy(), want).max() < FP32_TOL
+    hai.hai_epic_image(ctx, lay, v, 2, 0, hai.HAI_PREC_FP32, img, 0)
+    hai.hai_sync(ctx)
+    assert torch.count_nonzero(img).item() == 0
+    hai.hai_layout_destroy(lay)
+
+
+def test_deterministic(hai, ctx):
+    cfg = I.SKA_LOW_STATION_256
+    pos, anchors, taps = station(cfg)
+    volt = I.station_voltages(cfg, pos, n_chan=3, n_time=50)
+    a = run_epic(hai, ctx, anchors, taps, cfg.grid_n, volt, hai.HAI_PREC_FP32)
+    b = run_epic(hai, ctx, anchors, taps, cfg.grid_n, volt, hai.HAI_PREC_FP32)
+    assert np.array_equal(a, b)
+
+
+def test_off_grid_and_bad_args(hai, ctx):
+    anchors = np.array([[62, 3]], np.int32)
+    taps = np.ones((1, 3, 3, 2), np.float32)
+    with pytest.raises(hai.HaiError) as e:
+        hai.hai_layout_create(ctx, anchors, taps, 64, 1)
+    assert e.value.status == 2
+    with pytest.raises(hai.HaiError) as e:
+        hai.hai_layout_create(ctx, np.array([[1, 1]], np.int32), taps, 48, 1)
+    assert e.value.status == 1
+
+
+def test_ska_station_full_size_sampled_channels(hai, ctx):
+    """Full cadence (64 channels x 2048 samples) in the benchmark's launch
+    configuration; the oracle recomputes three channels."""
+    cfg = I.SKA_LOW_STATION_256
+    pos, anchors, taps = station(cfg)
+    volt = I.station_voltages(cfg, pos, device="cuda")
+    n = cfg.grid_n
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, 2)
+    img = torch.empty((cfg.n_chan, 4, n, n), device="cuda")
+    hai.hai_epic_image(ctx, lay, volt, cfg.n_chan, cfg.n_time, hai.HAI_PREC_FP32, img, 0)
+    hai.hai_sync(ctx)
+    hai.hai_layout_destroy(lay)
+    for c in (0, 37, 63):
+        want = O.epic_image(n, anchors, taps, volt[c:c + 1].cpu().numpy())
+        assert rel_err_planes(img[c:c + 1].cpu().numpy(), want).max() < FP32_TOL
