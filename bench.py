@@ -33,7 +33,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["fp16", "fp32"], default="fp32")
+    ap.add_argument("--prec", choices=["fp16", "fp32"], default="fp16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--channels", type=int, default=0,
@@ -136,6 +136,14 @@ def epic_flops_per_unit(cfg):
     return 5 * math.log2(n * n) + 8.0 * cfg.n_elem * cfg.ksize ** 2 / (n * n) + 8.0
 
 
+def tc_mma_flops_per_unit(cfg, box=32):
+    """Executed tensor-core FLOP per imaged unit of the two-stage DFT-as-GEMM:
+    per field 8 (R N C + N^2 R) with the padded box R = C = 32 (real-ified
+    complex products, 8 real FLOP per complex MAC)."""
+    n = cfg.grid_n
+    return 8.0 * (box * n * box + n * n * box) / (n * n)
+
+
 def fp32_alu_peak_tflops(sm_count, sm_mhz):
     """CUDA-core FP32 peak: SMs x 128 FP32 lanes x 2 FLOP (FMA) x clock."""
     return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -148,18 +156,31 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(cfg, pos, anchors, taps, n_chan):
-    """FP64 oracle on the host cores over a bounded sample of the workload."""
+def cpu_baseline(cfg, anchors, taps, volt_host, gpu_img=None):
+    """FP64 oracle on the host cores over a bounded sample of the workload
+    (the first n_chan channels of the cadence).  The oracle's images of that
+    sample also give the per-image error of the GPU images of those channels."""
     from oracle import oracle as O
-    from paper_2411_17804_gb300 import inputs as I
-    volt = I.station_voltages(cfg, pos, n_chan=n_chan).numpy()
+    volt = volt_host
+    n_chan = volt.shape[0]
     t0 = time.perf_counter()
-    O.epic_image(cfg.grid_n, anchors, taps, volt)
+    want = O.epic_image(cfg.grid_n, anchors, taps, volt)
     dt = time.perf_counter() - t0
     units = cfg.grid_n ** 2 * n_chan * cfg.n_pol * cfg.n_time
-    return {"value": units / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"{n_chan} of {cfg.n_chan} channels x {cfg.n_time} samples of the cadence "
-                      f"({dt:.1f} s)"}
+    out = {"value": units / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+           "sample": f"{n_chan} of {cfg.n_chan} channels x {cfg.n_time} samples of the cadence "
+                     f"({dt:.1f} s)"}
+    err = None
+    if gpu_img is not None:
+        got = gpu_img[:n_chan].astype(np.float64)
+        d = np.linalg.norm((got - want).reshape(n_chan, want.shape[1], -1), axis=-1)
+        r = np.linalg.norm(want.reshape(n_chan, want.shape[1], -1), axis=-1)
+        r = np.maximum(r, 1e-3 * r[:, :2].max(axis=1, keepdims=True))
+        e = d / r
+        err = {"metric": "||I_gpu - I_oracle||_F / ||I_oracle||_F per (channel, plane)",
+               "channels": n_chan, "max": float(e.max()), "median": float(np.median(e)),
+               "per_plane_max": [float(x) for x in e.max(axis=0)]}
+    return out, err
 
 
 def run_reference(args, ws, rank):
@@ -277,7 +298,17 @@ def main():
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     flop_unit = epic_flops_per_unit(cfg)
     achieved = flop_unit * units / (dom_ms * 1e-3) / 1e12
-    if prec == hai.HAI_PREC_FP32:
+    if prec == hai.HAI_PREC_FP16:
+        mma_unit = tc_mma_flops_per_unit(cfg)
+        ach = mma_unit * units / (dom_ms * 1e-3) / 1e12
+        pk = float(peaks.get("bf16_tflops", 1900.0))
+        roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "traffic": None, "kernel": "epic_tc_kernel",
+                "peak_source": "of measured: MEASURED_PEAKS bf16_tflops (burst) x fp16/bf16 nominal ratio 1"
+                               if "bf16_tflops" in peaks else "of fallback 1.9 PFLOP/s",
+                "flop_per_unit": mma_unit, "kernel_ms": dom_ms,
+                "fft_equiv_tflops": achieved}
+    elif prec == hai.HAI_PREC_FP32:
         peak_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         peak = fp32_alu_peak_tflops(sms, peak_mhz)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -303,7 +334,11 @@ def main():
         line["plain_fp32"] = fp32
         line["tc_over_fp32"] = value / fp32["value"]
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg, pos, anchors, taps, n_chan=16)
+        hai.hai_epic_image(ctx, lay, volt, C, T, prec, img, 0, st)
+        torch.cuda.synchronize()
+        cb, err = cpu_baseline(cfg, anchors, taps, volt[:min(16, C)].cpu().numpy(), gpu_img=img.cpu().numpy())
+        line["cpu_baseline"] = cb
+        line["image_error_vs_oracle"] = err
     hai.hai_layout_destroy(lay)
     hai.hai_destroy(ctx)
     if rank == 0:

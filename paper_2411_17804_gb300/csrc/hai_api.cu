@@ -257,6 +257,13 @@ extern "C" hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *d, 
     L->partial_slots = epic_partial_slots(epic_fp32_target_ctas(ctx, n));
     if (e == cudaSuccess)
         e = cudaMalloc(&L->d_partials, sizeof(float) * L->partial_slots * Q * (size_t)n * n);
+    if (e == cudaSuccess && epic_tc_supported(L)) {   // DFT operand of the tensor-core path
+        std::vector<uint8_t> tab;
+        epic_tc_build_table(L, count, elem, w, tab, L->tc_ncz);
+        L->tc_tables_bytes = tab.size();
+        e = cudaMalloc(&L->d_tc_tables, tab.size());
+        if (e == cudaSuccess) e = cudaMemcpy(L->d_tc_tables, tab.data(), tab.size(), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         layout_free(L);
         if (e == cudaErrorMemoryAllocation) return hai_cuda_fail(e, "hai_layout_create: allocation");
@@ -317,5 +324,5 @@ extern "C" hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *L, const in
         return HAI_OK;
     }
     if (prec == HAI_PREC_FP32) return epic_fp32_launch(L, volt, C, T, img, accumulate, st);
-    return hai_fail(HAI_ERR_UNSUPPORTED, "hai_epic_image: FP16 tensor-core path not built yet");
+    return epic_tc_launch(L, volt, C, T, img, accumulate, st);
 }

@@ -6,7 +6,7 @@ import torch
 
 from oracle import oracle as O
 from paper_2411_17804_gb300 import inputs as I
-from tests.helpers import FP32_TOL, rel_err_planes, station
+from tests.helpers import FP32_TOL, REDUCED_TOL, rel_err_planes, station
 
 pytestmark = pytest.mark.gpu
 
@@ -132,3 +132,80 @@ def test_ska_station_full_size_sampled_channels(hai, ctx):
     for c in (0, 37, 63):
         want = O.epic_image(n, anchors, taps, volt[c:c + 1].cpu().numpy())
         assert rel_err_planes(img[c:c + 1].cpu().numpy(), want).max() < FP32_TOL
+
+
+# ------------------------------------------------------------------ FP16 tensor-core path
+@pytest.mark.parametrize("C,T", [(3, 40), (1, 7), (5, 1), (2, 301), (1, 2), (4, 33)])
+def test_tc_ska_station_ragged_splits(hai, ctx, C, T):
+    cfg = I.SKA_LOW_STATION_256
+    pos, anchors, taps = station(cfg)
+    volt = I.station_voltages(cfg, pos, n_chan=C, n_time=T)
+    got = run_epic(hai, ctx, anchors, taps, cfg.grid_n, volt, hai.HAI_PREC_FP16)
+    want = O.epic_image(cfg.grid_n, anchors, taps, volt.numpy())
+    err = rel_err_planes(got, want)
+    assert err.max() < REDUCED_TOL, err
+
+
+def test_tc_full_size_sampled_channels(hai, ctx):
+    cfg = I.SKA_LOW_STATION_256
+    pos, anchors, taps = station(cfg)
+    volt = I.station_voltages(cfg, pos, device="cuda")
+    n = cfg.grid_n
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, 2)
+    img = torch.empty((cfg.n_chan, 4, n, n), device="cuda")
+    hai.hai_epic_image(ctx, lay, volt, cfg.n_chan, cfg.n_time, hai.HAI_PREC_FP16, img, 0)
+    hai.hai_sync(ctx)
+    hai.hai_layout_destroy(lay)
+    for c in (0, 31, 63):
+        want = O.epic_image(n, anchors, taps, volt[c:c + 1].cpu().numpy())
+        err = rel_err_planes(img[c:c + 1].cpu().numpy(), want)
+        assert err.max() < REDUCED_TOL, (c, err)
+
+
+def test_tc_adversarial_and_random_taps(hai, ctx):
+    cfg = I.SKA_LOW_STATION_256
+    pos, anchors, taps = station(cfg)
+    volt = torch.full((2, 16, 2, len(pos), 2), -128, dtype=torch.int8)
+    volt[:, ::2, 1, :, 1] = 127
+    got = run_epic(hai, ctx, anchors, taps, cfg.grid_n, volt, hai.HAI_PREC_FP16)
+    want = O.epic_image(cfg.grid_n, anchors, taps, volt.numpy())
+    assert rel_err_planes(got, want).max() < REDUCED_TOL
+    # complex taps, uniform random voltages
+    rng = np.random.default_rng(3)
+    ctaps = taps.copy()
+    ctaps[..., 1] = 0.3 * rng.standard_normal(taps.shape[:-1]).astype(np.float32)
+    volt = I.random_voltages((2, 24, 2, len(pos), 2), seed=77)
+    got = run_epic(hai, ctx, anchors, ctaps, cfg.grid_n, volt, hai.HAI_PREC_FP16)
+    want = O.epic_image(cfg.grid_n, anchors, ctaps, volt.numpy())
+    assert rel_err_planes(got, want).max() < REDUCED_TOL
+
+
+def test_tc_accumulate_and_deterministic(hai, ctx):
+    cfg = I.SKA_LOW_STATION_256
+    pos, anchors, taps = station(cfg)
+    volt = I.station_voltages(cfg, pos, n_chan=2, n_time=20)
+    n = cfg.grid_n
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, 2)
+    img = torch.zeros((2, 4, n, n), device="cuda")
+    v = volt.cuda()
+    hai.hai_epic_image(ctx, lay, v[:, :9].contiguous(), 2, 9, hai.HAI_PREC_FP16, img, 0)
+    hai.hai_epic_image(ctx, lay, v[:, 9:].contiguous(), 2, 11, hai.HAI_PREC_FP16, img, 1)
+    hai.hai_sync(ctx)
+    want = O.epic_image(n, anchors, taps, volt.numpy())
+    assert rel_err_planes(img.cpu().numpy(), want).max() < REDUCED_TOL
+    a = run_epic(hai, ctx, anchors, taps, n, volt, hai.HAI_PREC_FP16)
+    b = run_epic(hai, ctx, anchors, taps, n, volt, hai.HAI_PREC_FP16)
+    assert np.array_equal(a, b)
+    hai.hai_layout_destroy(lay)
+
+
+def test_tc_unsupported_layout_is_reported(hai, ctx):
+    cfg = I.SINGLE_STATION_64
+    pos, anchors, taps = station(cfg)
+    lay = hai.hai_layout_create(ctx, anchors, taps, cfg.grid_n, 1)
+    img = torch.zeros((1, 1, cfg.grid_n, cfg.grid_n), device="cuda")
+    volt = torch.zeros((1, 4, 1, len(pos), 2), dtype=torch.int8, device="cuda")
+    with pytest.raises(hai.HaiError) as e:
+        hai.hai_epic_image(ctx, lay, volt, 1, 4, hai.HAI_PREC_FP16, img, 0)
+    assert e.value.status == 4
+    hai.hai_layout_destroy(lay)
