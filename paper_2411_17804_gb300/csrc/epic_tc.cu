@@ -15,9 +15,10 @@
 // CTA = 16 warps, one CTA per SM, persistent over a contiguous range of the
 // flattened (channel, sample) index, two samples (four fields: 2 samples x
 // 2 pols) per step:
-//   warps 0-6  "front": widen the step's voltages (landed by TMA bulk copies)
-//              to FP32, gather-grid the four fields over the layout's list of
-//              non-empty cells into A1 (fp16, K-major); warps 0-3 then move
+//   warps 0-6  "front": re-pack the step's voltages (landed by TMA bulk
+//              copies) as fp16 per element, gather-grid the four fields over
+//              tiles of the layout's non-empty cells into A1 (fp16, K-major)
+//              with FP32 sums; warps 0-3 then move
 //              stage-1 results from TMEM into the stage-2 operand A2 (fp16,
 //              MN-major), transposing on the way;
 //   warp 7     one thread streams the voltages (TMA) and issues every MMA;
@@ -58,23 +59,28 @@ constexpr uint32_t kOffE = kOffA2 + 4 * kA2Bytes;
 constexpr uint32_t kIdesc1 = tc::idesc_f16(128, 128, 0, 0);
 constexpr uint32_t kIdesc2 = tc::idesc_f16(128, 128, 1, 0);
 
-// Device table written by epic_tc_build_table (byte layout):
+// Device table written by epic_tc_build_table (byte layout).  The non-empty
+// cells of the kernel's box are dealt into tiles of 32 (one per warp lane),
+// sorted by entry count so a tile's lanes run the same number of slots; a
+// tile's entries are stored slot-major, entry (slot k, lane l) at
+// tile_base + 32 k + l, with zero-weight padding.
 //   [0, 16384)         DFT operand B (K-major)
-//   cell offsets       uint32 [ncz]   A1 byte offset of each non-empty cell (field 0)
-//   cell starts        int32 [ncz+1]  entry range of each cell
+//   cell offsets       uint32 [ntile * 32]  A1 byte offset of the lane's cell (field 0),
+//                                           0xffffffff for an unused lane
+//   tile bases         int32 [ntile + 1]    first entry of each tile (slots = diff / 32)
 //   (pad to 16)
-//   entry weights      float2 [nnz]   a + ib = conj(W~)
-//   entry elements     uint16 [nnz]
+//   entry weights      float2 [nent]        a + ib = conj(W~)
+//   entry elements     uint16 [nent]
 struct TableLayout {
-    uint32_t off_cell, off_start, off_w, off_e, bytes;
+    uint32_t off_cell, off_base, off_w, off_e, bytes;
 };
-__host__ __device__ inline TableLayout table_layout(int ncz, int nnz) {
+__host__ __device__ inline TableLayout table_layout(int ntile, int nent) {
     TableLayout t;
     t.off_cell = kOpBytes;
-    t.off_start = t.off_cell + 4u * ncz;
-    t.off_w = (t.off_start + 4u * (ncz + 1) + 15u) & ~15u;
-    t.off_e = t.off_w + 8u * nnz;
-    t.bytes = (t.off_e + 2u * nnz + 15u) & ~15u;
+    t.off_base = t.off_cell + 4u * 32u * ntile;
+    t.off_w = (t.off_base + 4u * (ntile + 1) + 15u) & ~15u;
+    t.off_e = t.off_w + 8u * nent;
+    t.bytes = (t.off_e + 2u * nent + 15u) & ~15u;
     return t;
 }
 
@@ -82,7 +88,7 @@ struct EpicTcParams {
     const int8_t *volt;
     int C, T, ne;
     long long len;
-    int ncz, nnz;
+    int ntile, nent;
     const uint8_t *table;
     float *out;
     int direct, accumulate, use_tma;
@@ -101,16 +107,16 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const EpicTcParams
     const int ne = p.ne;
     const int sample_bytes = 4 * ne;                       // 2 pols x ne x (re, im)
     const uint32_t vstage = (2u * sample_bytes + 15u) & ~15u;
-    const TableLayout tl = table_layout(p.ncz, p.nnz);
+    const TableLayout tl = table_layout(p.ntile, p.nent);
     uint8_t *sB = smem;
     uint8_t *sA1 = smem + kOffA1;
     uint8_t *sA2 = smem + kOffA2;
-    float2 *sE = reinterpret_cast<float2 *>(smem + kOffE);  // [2 buffers][ne][4 fields]
-    const uint32_t off_v = kOffE + 2u * 32u * ne;
+    uint4 *sE = reinterpret_cast<uint4 *>(smem + kOffE);    // [2 buffers][ne] 4 fields as half2
+    const uint32_t off_v = kOffE + 2u * 16u * ne;
     int8_t *sV = reinterpret_cast<int8_t *>(smem + off_v);
     uint8_t *sT = smem + off_v + kStages * vstage;          // copy of the table after B
     const uint32_t *s_cell = reinterpret_cast<const uint32_t *>(sT + tl.off_cell - kOpBytes);
-    const int32_t *s_start = reinterpret_cast<const int32_t *>(sT + tl.off_start - kOpBytes);
+    const int32_t *s_base = reinterpret_cast<const int32_t *>(sT + tl.off_base - kOpBytes);
     const float2 *s_w = reinterpret_cast<const float2 *>(sT + tl.off_w - kOpBytes);
     const uint16_t *s_e = reinterpret_cast<const uint16_t *>(sT + tl.off_e - kOpBytes);
 
@@ -148,7 +154,8 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const EpicTcParams
 
     if (warp < kMmaWarp) {
         // ================================================================ front
-        // voltages of step i -> sE[i & 1] as FP32 [elem][field]; ends with a front barrier
+        // voltages of step i -> sE[i & 1]: per element the four fields as
+        // half2 (int8 values are exact in fp16); ends with a front barrier
         auto stage_volt = [&](int i) {
             const int8_t *V = sV + (i % kStages) * vstage;
             const int nv = pair_valid(i);
@@ -161,44 +168,66 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const EpicTcParams
                 for (int b = tid; b < bytes; b += kFront) dst[b] = src[b];
                 bar_front();
             }
+            // two consecutive elements x four fields per thread
+            uint4 *E = sE + (i & 1) * ne;
             const char2 *v2 = reinterpret_cast<const char2 *>(V);
-            float2 *E = sE + (i & 1) * 4 * ne;
-            for (int k = tid; k < 4 * ne; k += kFront) {           // k = elem * 4 + field
-                const int a = k >> 2, f = k & 3;
-                float2 e = make_float2(0.f, 0.f);                   // fields of a missing sample: 0
-                if (f < 2 * nv) {
-                    const char2 v = v2[f * ne + a];
-                    e = make_float2((float)v.x, (float)v.y);
+            for (int a0 = 2 * tid; a0 < ne; a0 += 2 * kFront) {
+                uint32_t h0[4], h1[4];
+#pragma unroll
+                for (int f = 0; f < 4; f++) {
+                    char2 x = make_char2(0, 0), y = make_char2(0, 0);   // missing sample: 0
+                    if (f < 2 * nv) {
+                        x = v2[f * ne + a0];
+                        if (a0 + 1 < ne) y = v2[f * ne + a0 + 1];
+                    }
+                    h0[f] = tc::pack_half2((float)x.x, (float)x.y);
+                    h1[f] = tc::pack_half2((float)y.x, (float)y.y);
                 }
-                E[k] = e;
+                E[a0] = make_uint4(h0[0], h0[1], h0[2], h0[3]);
+                if (a0 + 1 < ne) E[a0 + 1] = make_uint4(h1[0], h1[1], h1[2], h1[3]);
             }
             bar_front();
         };
-        // gridded values of the four fields: G_f[cell] = sum conj(W~) E_f
+        // gridded values of the four fields: G_f[cell] = sum conj(W~) E_f,
+        // one cell per lane, one tile of 32 cells per warp at a time
         auto grid_pair = [&](int i) {
             uint8_t *A = sA1 + (i & 1) * kOpBytes;
-            const float4 *E = reinterpret_cast<const float4 *>(sE + (i & 1) * 4 * ne);
-            for (int ci = tid; ci < p.ncz; ci += kFront) {
+            const uint4 *E = sE + (i & 1) * ne;
+            for (int t = warp; t < p.ntile; t += kMmaWarp) {
                 float2 g0 = make_float2(0.f, 0.f), g1 = g0, g2 = g0, g3 = g0;
-                const int qe = s_start[ci + 1];
-                for (int q = s_start[ci]; q < qe; q++) {
-                    const float2 w = s_w[q];
-                    const int a = s_e[q];
-                    const float4 e01 = E[2 * a], e23 = E[2 * a + 1];
-                    g0.x = fmaf(w.x, e01.x, fmaf(-w.y, e01.y, g0.x));
-                    g0.y = fmaf(w.x, e01.y, fmaf(w.y, e01.x, g0.y));
-                    g1.x = fmaf(w.x, e01.z, fmaf(-w.y, e01.w, g1.x));
-                    g1.y = fmaf(w.x, e01.w, fmaf(w.y, e01.z, g1.y));
-                    g2.x = fmaf(w.x, e23.x, fmaf(-w.y, e23.y, g2.x));
-                    g2.y = fmaf(w.x, e23.y, fmaf(w.y, e23.x, g2.y));
-                    g3.x = fmaf(w.x, e23.z, fmaf(-w.y, e23.w, g3.x));
-                    g3.y = fmaf(w.x, e23.w, fmaf(w.y, e23.z, g3.y));
+                const int qe = s_base[t + 1];
+                int q = s_base[t] + lane;
+                // software pipeline: slot k+1's weight and voltages load while slot k computes
+                float2 w_n = s_w[q];
+                uint4 e_n = E[s_e[q]];
+                for (; q < qe; q += 32) {
+                    const float2 w = w_n;
+                    const uint4 e = e_n;
+                    if (q + 32 < qe) {
+                        w_n = s_w[q + 32];
+                        e_n = E[s_e[q + 32]];
+                    }
+                    const float2 e0 = __half22float2(*reinterpret_cast<const __half2 *>(&e.x));
+                    const float2 e1 = __half22float2(*reinterpret_cast<const __half2 *>(&e.y));
+                    const float2 e2 = __half22float2(*reinterpret_cast<const __half2 *>(&e.z));
+                    const float2 e3 = __half22float2(*reinterpret_cast<const __half2 *>(&e.w));
+                    g0.x = fmaf(w.x, e0.x, fmaf(-w.y, e0.y, g0.x));
+                    g0.y = fmaf(w.x, e0.y, fmaf(w.y, e0.x, g0.y));
+                    g1.x = fmaf(w.x, e1.x, fmaf(-w.y, e1.y, g1.x));
+                    g1.y = fmaf(w.x, e1.y, fmaf(w.y, e1.x, g1.y));
+                    g2.x = fmaf(w.x, e2.x, fmaf(-w.y, e2.y, g2.x));
+                    g2.y = fmaf(w.x, e2.y, fmaf(w.y, e2.x, g2.y));
+                    g3.x = fmaf(w.x, e3.x, fmaf(-w.y, e3.y, g3.x));
+                    g3.y = fmaf(w.x, e3.y, fmaf(w.y, e3.x, g3.y));
                 }
-                uint8_t *c = A + s_cell[ci];
-                *reinterpret_cast<uint32_t *>(c) = tc::pack_half2(g0.x, g0.y);
-                *reinterpret_cast<uint32_t *>(c + kImgBytes) = tc::pack_half2(g1.x, g1.y);
-                *reinterpret_cast<uint32_t *>(c + 2 * kImgBytes) = tc::pack_half2(g2.x, g2.y);
-                *reinterpret_cast<uint32_t *>(c + 3 * kImgBytes) = tc::pack_half2(g3.x, g3.y);
+                const uint32_t off = s_cell[t * 32 + lane];
+                if (off != 0xffffffffu) {
+                    uint8_t *c = A + off;
+                    *reinterpret_cast<uint32_t *>(c) = tc::pack_half2(g0.x, g0.y);
+                    *reinterpret_cast<uint32_t *>(c + kImgBytes) = tc::pack_half2(g1.x, g1.y);
+                    *reinterpret_cast<uint32_t *>(c + 2 * kImgBytes) = tc::pack_half2(g2.x, g2.y);
+                    *reinterpret_cast<uint32_t *>(c + 3 * kImgBytes) = tc::pack_half2(g3.x, g3.y);
+                }
             }
         };
         auto convert = [&](int i) {               // warps 0-3: field f = warp, row y = lane
@@ -374,9 +403,9 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const EpicTcParams
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-size_t smem_bytes(int ne, int ncz, int nnz) {
+size_t smem_bytes(int ne, int ntile, int nent) {
     const uint32_t vstage = (8u * ne + 15u) & ~15u;
-    return kOffE + 64ull * ne + (size_t)kStages * vstage + (table_layout(ncz, nnz).bytes - kOpBytes);
+    return kOffE + 32ull * ne + (size_t)kStages * vstage + (table_layout(ntile, nent).bytes - kOpBytes);
 }
 
 }  // namespace
@@ -388,22 +417,32 @@ bool epic_tc_supported(const hai_layout *L) {
 // Tables of the tensor-core path: the DFT operand of both stages,
 // B[n][kappa] with n = (out re/im, l) and kappa = (j, in re/im), in the
 // K-major layout (W'[j][l] = (-1)^j exp(+2 pi i l j / 64)); and the gather
-// list of the non-empty cells, ordered like A1's core matrices.
+// tiles of the non-empty cells (see TableLayout).
 void epic_tc_build_table(const hai_layout *L, const std::vector<int32_t> &cstart,
                          const std::vector<int32_t> &elem, const std::vector<float2> &w,
-                         std::vector<uint8_t> &out, int &ncz) {
+                         std::vector<uint8_t> &out, int &ntile, int &nent) {
     std::vector<int> cells;
     for (int y = 0; y < L->box_h; y++)
         for (int x = 0; x < L->box_w; x++)
             if (cstart[y * L->box_w + x + 1] > cstart[y * L->box_w + x]) cells.push_back(y * L->box_w + x);
+    auto count = [&](int c) { return cstart[c + 1] - cstart[c]; };
     auto a1off = [&](int cell) {
         const int y = cell / L->box_w, x = cell % L->box_w;
         return tc::off_kmajor(y, 2 * x, kKs, kMNs);
     };
-    std::sort(cells.begin(), cells.end(), [&](int a, int b) { return a1off(a) < a1off(b); });
-    ncz = (int)cells.size();
-    const int nnz = L->nnz;
-    const TableLayout tl = table_layout(ncz, nnz);
+    std::stable_sort(cells.begin(), cells.end(), [&](int a, int b) {
+        if (count(a) != count(b)) return count(a) > count(b);
+        return a1off(a) < a1off(b);
+    });
+    ntile = ((int)cells.size() + 31) / 32;
+    std::vector<int> base(ntile + 1, 0);
+    for (int t = 0; t < ntile; t++) {
+        int slots = 0;
+        for (int l = 0; l < 32 && t * 32 + l < (int)cells.size(); l++) slots = std::max(slots, count(cells[t * 32 + l]));
+        base[t + 1] = base[t] + 32 * slots;
+    }
+    nent = base[ntile];
+    const TableLayout tl = table_layout(ntile, nent);
     out.assign(tl.bytes, 0);
     for (int n = 0; n < 128; n++)
         for (int kappa = 0; kappa < 2 * kBox; kappa++) {
@@ -416,21 +455,25 @@ void epic_tc_build_table(const hai_layout *L, const std::vector<int32_t> &cstart
             memcpy(&out[tc::off_kmajor(n, kappa, kKs, kMNs)], &hv, 2);
         }
     uint32_t *o_cell = reinterpret_cast<uint32_t *>(&out[tl.off_cell]);
-    int32_t *o_start = reinterpret_cast<int32_t *>(&out[tl.off_start]);
+    int32_t *o_base = reinterpret_cast<int32_t *>(&out[tl.off_base]);
     float2 *o_w = reinterpret_cast<float2 *>(&out[tl.off_w]);
     uint16_t *o_e = reinterpret_cast<uint16_t *>(&out[tl.off_e]);
-    int q = 0;
-    for (int ci = 0; ci < ncz; ci++) {
-        const int cell = cells[ci];
-        o_cell[ci] = a1off(cell);
-        o_start[ci] = q;
-        for (int k = cstart[cell]; k < cstart[cell + 1]; k++, q++) {
-            const float a = w[k].x, b = w[k].y;          // conj(W~) = a + ib
-            o_w[q] = make_float2(a, b);
-            o_e[q] = (uint16_t)elem[k];
+    for (int t = 0; t <= ntile; t++) o_base[t] = base[t];
+    for (int t = 0; t < ntile; t++)
+        for (int l = 0; l < 32; l++) {
+            const int ci = t * 32 + l;
+            if (ci >= (int)cells.size()) {
+                o_cell[ci] = 0xffffffffu;
+                continue;
+            }
+            const int cell = cells[ci];
+            o_cell[ci] = a1off(cell);
+            for (int k = 0; k < count(cell); k++) {
+                const int q = base[t] + 32 * k + l;
+                o_w[q] = w[cstart[cell] + k];                 // conj(W~) = a + ib
+                o_e[q] = (uint16_t)elem[cstart[cell] + k];
+            }
         }
-    }
-    o_start[ncz] = q;
 }
 
 hai_status epic_tc_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
@@ -438,7 +481,7 @@ hai_status epic_tc_launch(const hai_layout *L, const int8_t *volt, int C, int T,
     if (!epic_tc_supported(L) || !L->d_tc_tables)
         return hai_fail(HAI_ERR_UNSUPPORTED,
                         "epic fp16: this build's tensor-core path needs N = 64, 2 pols and a kernel box <= 32 x 32");
-    const size_t smem = smem_bytes(L->n_elem, L->tc_ncz, L->nnz);
+    const size_t smem = smem_bytes(L->n_elem, L->tc_ntile, L->tc_nent);
     if (smem > (size_t)L->ctx->smem_optin)
         return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16: shared memory need exceeds the device limit");
     HAI_CUDA_TRY(cudaFuncSetAttribute(epic_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -451,8 +494,8 @@ hai_status epic_tc_launch(const hai_layout *L, const int8_t *volt, int C, int T,
     p.T = T;
     p.ne = L->n_elem;
     p.len = sp.len;
-    p.ncz = L->tc_ncz;
-    p.nnz = L->nnz;
+    p.ntile = L->tc_ntile;
+    p.nent = L->tc_nent;
     p.table = static_cast<const uint8_t *>(L->d_tc_tables);
     p.out = sp.direct ? img : L->d_partials;
     p.direct = sp.direct;

@@ -259,7 +259,7 @@ extern "C" hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *d, 
         e = cudaMalloc(&L->d_partials, sizeof(float) * L->partial_slots * Q * (size_t)n * n);
     if (e == cudaSuccess && epic_tc_supported(L)) {   // DFT operand of the tensor-core path
         std::vector<uint8_t> tab;
-        epic_tc_build_table(L, count, elem, w, tab, L->tc_ncz);
+        epic_tc_build_table(L, count, elem, w, tab, L->tc_ntile, L->tc_nent);
         L->tc_tables_bytes = tab.size();
         e = cudaMalloc(&L->d_tc_tables, tab.size());
         if (e == cudaSuccess) e = cudaMemcpy(L->d_tc_tables, tab.data(), tab.size(), cudaMemcpyHostToDevice);

@@ -47,7 +47,7 @@ struct hai_layout {
     // tensor-core path tables (fp16 DFT operands); built at create time
     void *d_tc_tables = nullptr;
     size_t tc_tables_bytes = 0;
-    int tc_ncz = 0;                     // non-empty cells of the box
+    int tc_ntile = 0, tc_nent = 0;      // gather tiles of the tensor-core path
 };
 
 // ---------------------------------------------------------------- errors
@@ -83,6 +83,6 @@ hai_status epic_tc_launch(const hai_layout *L, const int8_t *volt, int C, int T,
 bool epic_tc_supported(const hai_layout *L);
 void epic_tc_build_table(const hai_layout *L, const std::vector<int32_t> &cstart,
                          const std::vector<int32_t> &elem, const std::vector<float2> &w,
-                         std::vector<uint8_t> &out, int &ncz);
+                         std::vector<uint8_t> &out, int &ntile, int &nent);
 hai_status epic_reduce_launch(const hai_layout *L, const EpicSplit &sp, int C, int T, float *img,
                               int accumulate, cudaStream_t st);
