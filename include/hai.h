@@ -137,6 +137,36 @@ hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *layout, const int8_t *
                           int C, int T, hai_precision prec, float *img, int accumulate,
                           void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Correlator (Eq. intra-station visibilities): for every element pair a >= b
+ * (autos included) and polarisation pair (p, q),
+ *   V^{pq}_{ab} = sum_t E^p_a(t) conj(E^q_b(t)).
+ *   volt  device int8 [C][T][P][N][2] (the EPIC input layout), N elements
+ *   vis   device int32 [C][N(N+1)/2][P][P][2], baseline index a(a+1)/2 + b;
+ *         overwritten (accumulate = 0) or added to (accumulate = 1)
+ * Results are exact: tensor-core products of the int8 values are summed in
+ * FP32 over blocks of at most 512 samples (every partial sum is an integer
+ * below 2^24) and the blocks in int32.  V^{qp}_{ba} = conj(V^{pq}_{ab}) gives
+ * the upper triangle.  HAI_ERR_OVERFLOW_RISK if T > 65535 (|V| could exceed
+ * 2^31 - 1).  No scratch memory; the context supplies the device. */
+hai_status hai_correlate(hai_ctx *ctx, const int8_t *volt, int C, int T, int N, int P,
+                         int32_t *vis, int accumulate, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Correlator + FFT image (Eq. intra-station XFFT): the visibilities of every
+ * ordered element pair (a, b), autos included, gridded with the
+ * autocorrelation of the two elements' illumination kernels,
+ *   K_ab[d] = sum_j g_a[j + d] conj(g_b[j]),  g = the layout's placed conj taps,
+ * on the circular N x N grid, multiplied by (-1)^(dx+dy) and transformed with
+ * exp(+2 pi i l.d / N).  With this kernel the result equals the EPIC image
+ * of the same voltages (same planes and pixel convention as hai_epic_image).
+ *   vis   device int32 [C][N_e(N_e+1)/2][P][P][2] as written by hai_correlate
+ *   img   device float [C][Q][N][N]; overwritten or added to (accumulate)
+ * The pair (b, a) is the Hermitian mirror of the stored (a, b).  FP32 grid and
+ * FFT; grid sums use atomics, so the last bits may vary between runs. */
+hai_status hai_xfft_image(hai_ctx *ctx, const hai_layout *layout, const int32_t *vis, int C,
+                          float *img, int accumulate, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -174,6 +174,8 @@ static bool grid_supported(int n) { return n == 16 || n == 32 || n == 64; }
 
 static void layout_free(hai_layout *L) {
     if (!L) return;
+    cudaFree(L->d_anchors);
+    cudaFree(L->d_taps);
     cudaFree(L->d_cell_start);
     cudaFree(L->d_entry_elem);
     cudaFree(L->d_entry_w);
@@ -243,6 +245,12 @@ extern "C" hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *d, 
             }
 
     cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc(&L->d_anchors, sizeof(int32_t) * 2 * ne);
+    if (e == cudaSuccess) e = cudaMalloc(&L->d_taps, sizeof(float2) * (size_t)ne * k * k);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(L->d_anchors, d->anchors, sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(L->d_taps, d->taps, sizeof(float2) * (size_t)ne * k * k, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&L->d_cell_start, sizeof(int32_t) * (ncell + 1));
     if (e == cudaSuccess) e = cudaMalloc(&L->d_entry_elem, sizeof(int32_t) * std::max(1, L->nnz));
     if (e == cudaSuccess) e = cudaMalloc(&L->d_entry_w, sizeof(float2) * std::max(1, L->nnz));

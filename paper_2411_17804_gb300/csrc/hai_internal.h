@@ -39,6 +39,8 @@ struct hai_layout {
     int nnz = 0;
     std::vector<int32_t> h_anchors;     // host copy [n_elem][2]
     std::vector<float> h_taps;          // host copy [n_elem][K][K][2]
+    int32_t *d_anchors = nullptr;       // [n_elem][2]
+    float2 *d_taps = nullptr;           // [n_elem][K][K] as given (not conjugated)
     int32_t *d_cell_start = nullptr;    // [box_w * box_h + 1]
     int32_t *d_entry_elem = nullptr;    // [nnz]
     float2 *d_entry_w = nullptr;        // [nnz] conj(tap)

@@ -55,6 +55,8 @@ def _declare(L):
     L.hai_layout_destroy.restype = None
     L.hai_layout_box.argtypes = [_vp, ctypes.POINTER(_int)]
     L.hai_epic_image.argtypes = [_vp, _vp, _vp, _int, _int, _int, _vp, _int, _vp]
+    L.hai_correlate.argtypes = [_vp, _vp, _int, _int, _int, _int, _vp, _int, _vp]
+    L.hai_xfft_image.argtypes = [_vp, _vp, _vp, _int, _vp, _int, _vp]
     L.hai_profile_enable.argtypes = [_vp, _int, _int]
     L.hai_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
@@ -179,3 +181,18 @@ def hai_epic_image(ctx, layout: Layout, volt, C: int, T: int, prec: int, img, ac
     ip = _dev_ptr(img, torch.float32, "img", C * layout.n_planes * n * n) if C > 0 else 0
     _check(load().hai_epic_image(ctx, layout.handle, vp, C, T, prec, ip, accumulate, _stream(stream)),
            "hai_epic_image")
+
+
+def hai_correlate(ctx, volt, C: int, T: int, N: int, P: int, vis, accumulate: int = 0, stream=None):
+    import torch
+    vp = _dev_ptr(volt, torch.int8, "volt", C * T * P * N * 2) if C * T > 0 else 0
+    op = _dev_ptr(vis, torch.int32, "vis", C * (N * (N + 1) // 2) * P * P * 2) if C > 0 else 0
+    _check(load().hai_correlate(ctx, vp, C, T, N, P, op, accumulate, _stream(stream)), "hai_correlate")
+
+
+def hai_xfft_image(ctx, layout: Layout, vis, C: int, img, accumulate: int = 0, stream=None):
+    import torch
+    ne, P, n = layout.n_elem, layout.n_pol, layout.grid_n
+    vp = _dev_ptr(vis, torch.int32, "vis", C * (ne * (ne + 1) // 2) * P * P * 2) if C > 0 else 0
+    ip = _dev_ptr(img, torch.float32, "img", C * layout.n_planes * n * n) if C > 0 else 0
+    _check(load().hai_xfft_image(ctx, layout.handle, vp, C, ip, accumulate, _stream(stream)), "hai_xfft_image")
