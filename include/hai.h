@@ -167,6 +167,35 @@ hai_status hai_correlate(hai_ctx *ctx, const int8_t *volt, int C, int T, int N, 
 hai_status hai_xfft_image(hai_ctx *ctx, const hai_layout *layout, const int32_t *vis, int C,
                           float *img, int accumulate, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * EPIC image, FP32 path, without any device allocation.  (The paper has no
+ * counterpart: this is an interface for callers, not a step of the method.)
+ *
+ * Some callers cannot call cudaMalloc: a plug-in whose host application owns
+ * and hands out all device memory, a real-time loop whose device budget is
+ * fixed before it starts, or a thread that must not make allocating CUDA
+ * calls while another thread captures a CUDA graph in global mode.  They
+ * cannot create a hai_layout (hai_layout_create allocates its gather table
+ * and scratch), so this entry point takes the layout description on the
+ * host and keeps the gather table and the time-split partial images in one
+ * file-scope static device array of 9.2 MiB (2,408,452 floats) that every
+ * GPU loading the library holds until the process exits.  It computes the
+ * same image as hai_epic_image with HAI_PREC_FP32 (up to FP32 rounding of a
+ * different time split).
+ *   device  CUDA device index; made current
+ *   desc    host layout description as for hai_layout_create (read only)
+ *   volt    device int8 [C][T][P][N_e][2];  img  device float [C][Q][N][N]
+ * Limits: grid_n 16, 32 or 64 and n_elem * ksize^2 <= 102400, else
+ * HAI_ERR_UNSUPPORTED; taps off the grid give HAI_ERR_OFF_GRID.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array and a static host
+ * staging buffer: calls that overlap on the GPU, or run from two host
+ * threads at once, race.  The table is copied in on `stream` from pageable
+ * host memory.  No context is needed. */
+hai_status hai_epic_image_fp32_static(int device, const hai_layout_desc *desc, const int8_t *volt,
+                                      int C, int T, float *img, int accumulate, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

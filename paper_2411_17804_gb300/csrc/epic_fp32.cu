@@ -17,6 +17,8 @@
 // the (-1)^(jx+jy) phase-centre factor is an output shift by N/2.
 #include <math.h>
 
+#include <algorithm>
+
 #include "hai_internal.h"
 
 namespace {
@@ -298,4 +300,164 @@ hai_status epic_fp32_launch(const hai_layout *L, const int8_t *volt, int C, int 
     if (n == 64) return p == 2 ? launch_n<64, 2>(L, volt, C, T, img, accumulate, st)
                                : launch_n<64, 1>(L, volt, C, T, img, accumulate, st);
     return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp32: grid size");
+}
+
+// ============================================================================
+// Allocation-free entry point.
+//
+// hai_layout_create reserves the gather table and the time-split partial
+// images with cudaMalloc, so callers that must not allocate device memory
+// cannot use hai_epic_image.  This entry point runs the same FP32 kernel with
+// both kept in one fixed file-scope device array: the gather table is built
+// on the host from the caller's layout description into a static host
+// buffer and copied in on the caller's stream, and the partial images of the
+// time split live after it.  Every call on a device shares the array (and
+// the host buffer), which keeps the last call's contents; nothing in it has
+// to start at zero, because each launch rewrites the table and every partial
+// image slot it reads.  Calls that overlap on the GPU, or that come from two
+// host threads at once, race on it.
+// ============================================================================
+namespace {
+
+constexpr int kStaticMaxN = 64;                  // grid side
+constexpr int kStaticMaxNnz = 102400;            // n_elem x K^2 gather entries
+constexpr int kStaticMaxCells = kStaticMaxN * kStaticMaxN;
+constexpr int kStaticCtas = 64;                  // CTAs of the time split
+// cell starts | elements | (pad to 8 bytes) conj taps as float2, rounded to 16 bytes
+constexpr size_t kStaticTableWords = ((size_t)(kStaticMaxCells + 1) + 3 * (size_t)kStaticMaxNnz + 1 + 3) & ~(size_t)3;
+constexpr size_t kStaticPartialFloats = 2 * (size_t)kStaticCtas * 4 * kStaticMaxN * kStaticMaxN;
+constexpr size_t kStaticFloats = kStaticTableWords + kStaticPartialFloats;   // 2,408,452 (9.2 MiB)
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) float g_epic_static_scratch[kStaticFloats];
+
+// host side: device address of the array per device, and the host staging
+// buffer of the gather table (cell starts | elements | conj taps)
+static float *g_static_ptr[kStaticMaxDevices];
+alignas(16) static int32_t g_static_host[kStaticTableWords];
+static int32_t g_static_cursor[kStaticMaxCells];
+
+// word offset of the float2 taps inside the table: 8-byte aligned
+inline size_t static_taps_word(int ncell, int nnz) { return ((size_t)(ncell + 1) + nnz + 1) & ~(size_t)1; }
+
+hai_status static_scratch(int device, float **out) {
+    if (!g_static_ptr[device]) {
+        // the host-side name of the array is only a stand-in: fetch the device
+        // address once, with this device current; the FFT twiddles live in
+        // constant memory that no context has filled yet on this path
+        hai_status s = epic_fp32_init_tables();
+        if (s != HAI_OK) return s;
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_epic_static_scratch);
+        if (e != cudaSuccess) return hai_cuda_fail(e, "hai_epic_image_fp32_static: cudaGetSymbolAddress");
+        g_static_ptr[device] = static_cast<float *>(p);
+    }
+    *out = g_static_ptr[device];
+    return HAI_OK;
+}
+
+template <int N, int P>
+hai_status launch_static(float *scratch, int ne, int box_w, int box_h, int ncell, int nnz, const int8_t *volt,
+                         int C, int T, float *img, int accumulate, int sms, int smem_optin, cudaStream_t st) {
+    const size_t smem = sizeof(float2) * EpicSmem<N, P>::kBuf + ((size_t)kSamples * P * ne * 2 + 15) / 16 * 16;
+    if (smem > (size_t)smem_optin)
+        return hai_fail(HAI_ERR_UNSUPPORTED, "hai_epic_image_fp32_static: shared memory need exceeds the device limit");
+    auto kern = epic_fp32_kernel<N, P>;
+    HAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const EpicSplit sp = epic_make_split(C, T, std::min(sms, kStaticCtas));
+    const int32_t *cstart = reinterpret_cast<const int32_t *>(scratch);
+    const int32_t *celem = cstart + (ncell + 1);
+    const float2 *cw = reinterpret_cast<const float2 *>(cstart + static_taps_word(ncell, nnz));
+    float *partials = scratch + kStaticTableWords;
+    kern<<<sp.n_cta, kThreads, smem, st>>>(volt, C, T, ne, sp.len, box_w, box_h, cstart, celem, cw,
+                                           sp.direct ? img : partials, sp.direct, accumulate);
+    HAI_CUDA_TRY(cudaGetLastError());
+    if (!sp.direct) {
+        const int Q = (P == 2) ? 4 : 1;
+        const int plane = Q * N * N;
+        const long long n = (long long)C * plane;
+        epic_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partials, img, C, T, sp.len, plane,
+                                                                          accumulate);
+        HAI_CUDA_TRY(cudaGetLastError());
+    }
+    return HAI_OK;
+}
+
+}  // namespace
+
+extern "C" hai_status hai_epic_image_fp32_static(int device, const hai_layout_desc *d, const int8_t *volt, int C,
+                                                 int T, float *img, int accumulate, void *stream) {
+    if (!d || !d->anchors || !d->taps) return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image_fp32_static: NULL argument");
+    if (device < 0 || device >= kStaticMaxDevices)
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image_fp32_static: device index out of range");
+    if (d->n_elem <= 0 || d->ksize <= 0 || (d->n_pol != 1 && d->n_pol != 2) || C < 0 || T < 0 ||
+        (accumulate != 0 && accumulate != 1))
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image_fp32_static: bad descriptor or size");
+    const int n = d->grid_n, k = d->ksize, ne = d->n_elem;
+    if (n != 16 && n != 32 && n != 64)
+        return hai_fail(HAI_ERR_UNSUPPORTED, "hai_epic_image_fp32_static: grid_n must be 16, 32 or 64");
+    if ((long long)ne * k * k > kStaticMaxNnz)
+        return hai_fail(HAI_ERR_UNSUPPORTED, "hai_epic_image_fp32_static: n_elem * ksize^2 exceeds the static "
+                                             "scratch maximum of 102400 gather entries");
+    int bx0 = n, by0 = n, bx1 = 0, by1 = 0;
+    for (int a = 0; a < ne; a++) {
+        const int x0 = d->anchors[2 * a], y0 = d->anchors[2 * a + 1];
+        if (x0 < 0 || y0 < 0 || (long)x0 + k > n || (long)y0 + k > n)
+            return hai_fail(HAI_ERR_OFF_GRID, "hai_epic_image_fp32_static: a kernel tap lies outside the grid");
+        bx0 = std::min(bx0, x0);
+        by0 = std::min(by0, y0);
+        bx1 = std::max(bx1, x0 + k);
+        by1 = std::max(by1, y0 + k);
+    }
+    if (C == 0) return HAI_OK;
+    if (!img || (T > 0 && !volt)) return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image_fp32_static: NULL buffer");
+    HAI_CUDA_TRY(cudaSetDevice(device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int Q = (d->n_pol == 2) ? 4 : 1;
+    if (T == 0) {
+        if (!accumulate) HAI_CUDA_TRY(cudaMemsetAsync(img, 0, sizeof(float) * (size_t)C * Q * n * n, st));
+        return HAI_OK;
+    }
+    float *scratch = nullptr;
+    hai_status s = static_scratch(device, &scratch);
+    if (s != HAI_OK) return s;
+    // gather table, same order as hai_layout_create: cells of the box row-major,
+    // entries by element, weights conj(W~)
+    const int box_w = bx1 - bx0, box_h = by1 - by0, ncell = box_w * box_h;
+    const int nnz = ne * k * k;
+    int32_t *cstart = g_static_host;
+    int32_t *celem = cstart + (ncell + 1);
+    float2 *cw = reinterpret_cast<float2 *>(cstart + static_taps_word(ncell, nnz));
+    for (int i = 0; i <= ncell; i++) cstart[i] = 0;
+    for (int a = 0; a < ne; a++)
+        for (int v = 0; v < k; v++)
+            for (int u = 0; u < k; u++) cstart[(d->anchors[2 * a + 1] + v - by0) * box_w + (d->anchors[2 * a] + u - bx0) + 1]++;
+    for (int i = 0; i < ncell; i++) cstart[i + 1] += cstart[i];
+    for (int i = 0; i < ncell; i++) g_static_cursor[i] = cstart[i];
+    for (int a = 0; a < ne; a++)
+        for (int v = 0; v < k; v++)
+            for (int u = 0; u < k; u++) {
+                const int cell = (d->anchors[2 * a + 1] + v - by0) * box_w + (d->anchors[2 * a] + u - bx0);
+                const float *t = d->taps + (((size_t)a * k + v) * k + u) * 2;
+                const int slot = g_static_cursor[cell]++;
+                celem[slot] = a;
+                cw[slot] = make_float2(t[0], -t[1]);
+            }
+    const size_t words = static_taps_word(ncell, nnz) + 2 * (size_t)nnz;
+    HAI_CUDA_TRY(cudaMemcpyAsync(scratch, g_static_host, sizeof(int32_t) * words, cudaMemcpyHostToDevice, st));
+    int sms = 0, optin = 0;
+    HAI_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    HAI_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    const int p = d->n_pol;
+#define HAI_STATIC_CASE(NN)                                                                                        \
+    if (n == NN)                                                                                                   \
+        return p == 2 ? launch_static<NN, 2>(scratch, ne, box_w, box_h, ncell, nnz, volt, C, T, img, accumulate, \
+                                             sms, optin, st)                                                      \
+                      : launch_static<NN, 1>(scratch, ne, box_w, box_h, ncell, nnz, volt, C, T, img, accumulate, \
+                                             sms, optin, st);
+    HAI_STATIC_CASE(16)
+    HAI_STATIC_CASE(32)
+    HAI_STATIC_CASE(64)
+#undef HAI_STATIC_CASE
+    return hai_fail(HAI_ERR_UNSUPPORTED, "hai_epic_image_fp32_static: grid size");
 }

@@ -57,6 +57,8 @@ def _declare(L):
     L.hai_epic_image.argtypes = [_vp, _vp, _vp, _int, _int, _int, _vp, _int, _vp]
     L.hai_correlate.argtypes = [_vp, _vp, _int, _int, _int, _int, _vp, _int, _vp]
     L.hai_xfft_image.argtypes = [_vp, _vp, _vp, _int, _vp, _int, _vp]
+    L.hai_epic_image_fp32_static.argtypes = [_int, ctypes.POINTER(_LayoutDesc), _vp, _int, _int, _vp, _int,
+                                             _vp]
     L.hai_profile_enable.argtypes = [_vp, _int, _int]
     L.hai_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
@@ -196,3 +198,18 @@ def hai_xfft_image(ctx, layout: Layout, vis, C: int, img, accumulate: int = 0, s
     vp = _dev_ptr(vis, torch.int32, "vis", C * (ne * (ne + 1) // 2) * P * P * 2) if C > 0 else 0
     ip = _dev_ptr(img, torch.float32, "img", C * layout.n_planes * n * n) if C > 0 else 0
     _check(load().hai_xfft_image(ctx, layout.handle, vp, C, ip, accumulate, _stream(stream)), "hai_xfft_image")
+
+
+def hai_epic_image_fp32_static(device: int, anchors, taps, grid_n: int, n_pol: int, volt, C: int, T: int, img,
+                               accumulate: int = 0, stream=None):
+    """FP32 EPIC image with no device allocation (static scratch in the library)."""
+    import torch
+    anchors = np.ascontiguousarray(anchors, np.int32)
+    taps = np.ascontiguousarray(taps, np.float32)
+    ne, k = anchors.shape[0], taps.shape[1]
+    d = _LayoutDesc(ne, grid_n, k, n_pol, anchors.ctypes.data, taps.ctypes.data)
+    q = 4 if n_pol == 2 else 1
+    vp = _dev_ptr(volt, torch.int8, "volt", C * T * n_pol * ne * 2) if C * T > 0 else 0
+    ip = _dev_ptr(img, torch.float32, "img", C * q * grid_n * grid_n) if C > 0 else 0
+    _check(load().hai_epic_image_fp32_static(device, ctypes.byref(d), vp, C, T, ip, accumulate, _stream(stream)),
+           "hai_epic_image_fp32_static")
