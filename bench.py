@@ -36,6 +36,7 @@ def parse():
     ap.add_argument("--prec", choices=["fp16", "fp32"], default="fp16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-components", action="store_true")
     ap.add_argument("--channels", type=int, default=0,
                     help="image only this many channels (small cases for profiling)")
     return ap.parse_args()
@@ -142,6 +143,39 @@ def tc_mma_flops_per_unit(cfg, box=32):
     complex products, 8 real FLOP per complex MAC)."""
     n = cfg.grid_n
     return 8.0 * (box * n * box + n * n * box) / (n * n)
+
+
+def corr_mma_flops(C, T, N, P):
+    """Executed tensor-core FLOP of one correlator launch: tiles x 32-sample
+    stages x 4 MMAs of 128 x 128 x 16 (rows: P x 128/P elements, columns:
+    2 x P x 64/P elements)."""
+    em, en = 128 // P, 64 // P
+    nbi, nbj = -(-N // em), -(-N // en)
+    tiles = sum(min(nbj, min(N - 1, (i + 1) * em - 1) // en + 1) for i in range(nbi))
+    stages = -(-T // 32)
+    return C * tiles * stages * 4 * 2.0 * 128 * 128 * 16
+
+
+def corr_useful_ops(C, T, N, P):
+    """Integer operations the correlation itself needs: 8 per complex MAC
+    (P^2 pol pairs, N(N+1)/2 baselines, T samples)."""
+    return 8.0 * C * T * P * P * N * (N + 1) / 2
+
+
+def time_call(fn, steps, warm, flush):
+    import torch
+    st = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn(st)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.add_(1.0)
+        ev[i][0].record(st)
+        fn(st)
+        ev[i][1].record(st)
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
 
 
 def fp32_alu_peak_tflops(sm_count, sm_mhz):
@@ -333,6 +367,26 @@ def main():
     if fp32 is not None:
         line["plain_fp32"] = fp32
         line["tc_over_fp32"] = value / fp32["value"]
+    # comparison paths on the same cadence: correlator (exact int8) and XFFT
+    if not args.no_components:
+        N = cfg.n_elem
+        vis = torch.empty((C, N * (N + 1) // 2, P, P, 2), dtype=torch.int32, device="cuda")
+        hai.hai_profile_read(ctx)
+        cms = time_call(lambda st: hai.hai_correlate(ctx, volt, C, T, N, P, vis, 0, st), 10, 3, flush)
+        xms = time_call(lambda st: hai.hai_xfft_image(ctx, lay, vis, C, img, 0, st), 10, 3, flush)
+        dom_c = hai.hai_profile_read(ctx)
+        mma = corr_mma_flops(C, T, N, P)
+        pk = float(peaks.get("bf16_tflops", 1900.0))
+        line["components"] = {
+            "correlator": {"ms": cms, "visibilities_per_s": C * N * (N + 1) / 2 * P * P / (cms * 1e-3),
+                           "useful_tops": corr_useful_ops(C, T, N, P) / (cms * 1e-3) / 1e12,
+                           "roofline": {"bound": "tensor", "achieved": mma / (cms * 1e-3) / 1e12, "peak": pk,
+                                        "unit": "TFLOP/s", "frac": mma / (cms * 1e-3) / 1e12 / pk,
+                                        "peak_source": "of measured bf16_tflops (fp16 nominal ratio 1)"}},
+            "xfft": {"ms": xms, "units_per_s": units / (xms * 1e-3),
+                     "note": "per cadence after the correlator; XFFT cadence = correlator + xfft"},
+            "xfft_total_units_per_s": units / ((cms + xms) * 1e-3)}
+        del vis
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         hai.hai_epic_image(ctx, lay, volt, C, T, prec, img, 0, st)
         torch.cuda.synchronize()
