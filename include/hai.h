@@ -168,6 +168,25 @@ hai_status hai_xfft_image(hai_ctx *ctx, const hai_layout *layout, const int32_t 
                           float *img, int accumulate, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Voltage beamformer (Eq. intra-station BF) with diagonal polarisation
+ * weights: for every station s, channel c, sample t, beam k and pol p,
+ *   B^p_k = sum_a conj(w^p_{s,k,a}) E^p_{s,a}(c, t).
+ *   volt   device int8 [S][C][T][P][N][2], 16-byte aligned
+ *   w      device int8 [S][K][P][N][2]
+ *   beams  requant_shift < 0: device int32 [S][C][T][K][P][2], exact;
+ *          requant_shift >= 0: device int8, same layout, each component
+ *          divided by 2^shift rounding half away from zero and clamped to
+ *          [-127, 127]
+ *   n_saturated  device int64 counter (or NULL), incremented by the number of
+ *          clamped components
+ * Exact for N <= 512 (products summed in FP32 stay integers below 2^24).
+ * HAI_ERR_UNSUPPORTED unless N is a multiple of 8 and <= 512 and K a multiple
+ * of 8 and <= 64, or if one station's weights do not fit in shared memory. */
+hai_status hai_beamform(hai_ctx *ctx, const int8_t *volt, const int8_t *w, int S, int C, int T, int K,
+                        int N, int P, int requant_shift, void *beams, long long *n_saturated,
+                        void *stream);
+
+/* ---------------------------------------------------------------------------
  * EPIC image, FP32 path, without any device allocation.  (The paper has no
  * counterpart: this is an interface for callers, not a step of the method.)
  *

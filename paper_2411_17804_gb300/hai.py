@@ -57,6 +57,7 @@ def _declare(L):
     L.hai_epic_image.argtypes = [_vp, _vp, _vp, _int, _int, _int, _vp, _int, _vp]
     L.hai_correlate.argtypes = [_vp, _vp, _int, _int, _int, _int, _vp, _int, _vp]
     L.hai_xfft_image.argtypes = [_vp, _vp, _vp, _int, _vp, _int, _vp]
+    L.hai_beamform.argtypes = [_vp, _vp, _vp, _int, _int, _int, _int, _int, _int, _int, _vp, _vp, _vp]
     L.hai_epic_image_fp32_static.argtypes = [_int, ctypes.POINTER(_LayoutDesc), _vp, _int, _int, _vp, _int,
                                              _vp]
     L.hai_profile_enable.argtypes = [_vp, _int, _int]
@@ -213,3 +214,15 @@ def hai_epic_image_fp32_static(device: int, anchors, taps, grid_n: int, n_pol: i
     ip = _dev_ptr(img, torch.float32, "img", C * q * grid_n * grid_n) if C > 0 else 0
     _check(load().hai_epic_image_fp32_static(device, ctypes.byref(d), vp, C, T, ip, accumulate, _stream(stream)),
            "hai_epic_image_fp32_static")
+
+
+def hai_beamform(ctx, volt, w, S: int, C: int, T: int, K: int, N: int, P: int, requant_shift: int, beams,
+                 n_saturated=None, stream=None):
+    import torch
+    vp = _dev_ptr(volt, torch.int8, "volt", S * C * T * P * N * 2)
+    wp = _dev_ptr(w, torch.int8, "w", S * K * P * N * 2)
+    bdt = torch.int32 if requant_shift < 0 else torch.int8
+    bp = _dev_ptr(beams, bdt, "beams", S * C * T * K * P * 2)
+    sp = _dev_ptr(n_saturated, torch.int64, "n_saturated", 1) if n_saturated is not None else 0
+    _check(load().hai_beamform(ctx, vp, wp, S, C, T, K, N, P, requant_shift, bp, sp, _stream(stream)),
+           "hai_beamform")
