@@ -267,6 +267,36 @@ def time_epic(hai, ctx, lay, volt, img, C, T, prec, steps, warm, flush, ws):
     return float(np.sum(step_ms)), dom_ms / max(dom_n, 1), launches
 
 
+def bf_component(hai, ctx, flush, peaks):
+    """int8 station beamformer on the hierarchical workload's shape (256
+    stations x 256 elements, 32 channels, 2 pols, 1000 samples, 16 beams),
+    random int8 voltages and weights (the kernel's time does not depend on
+    the values), int32 beams and requantised int8 beams.  HBM-bound: the
+    algorithmic bytes are the voltages read plus the beams written."""
+    import torch
+    S, C, T, K, N, P = 256, 32, 1000, 16, 256, 2
+    g = torch.Generator(device="cuda").manual_seed(11)
+    volt = torch.randint(-128, 128, (S, C, T, P, N, 2), dtype=torch.int8, device="cuda", generator=g)
+    w = torch.randint(-127, 128, (S, K, P, N, 2), dtype=torch.int8, device="cuda", generator=g)
+    sat = torch.zeros(1, dtype=torch.int64, device="cuda")
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out = {"shape": {"stations": S, "channels": C, "samples": T, "beams": K, "elements": N, "pols": P}}
+    for name, shift, dt, osz in (("int32", -1, torch.int32, 4), ("int8_requant", 10, torch.int8, 1)):
+        beams = torch.empty((S, C, T, K, P, 2), dtype=dt, device="cuda")
+        ms = time_call(lambda st: hai.hai_beamform(ctx, volt, w, S, C, T, K, N, P, shift, beams,
+                                                   sat if shift >= 0 else None, st), 5, 3, flush)
+        byts = volt.numel() + w.numel() + beams.numel() * osz
+        gbs = byts / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "beam_samples_per_s": S * C * T * K * P / (ms * 1e-3),
+                     "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                  "frac": gbs / hbm, "traffic": None, "algorithmic_bytes": byts,
+                                  "peak_source": "of measured hbm_gbs" if "hbm_gbs" in peaks
+                                  else "of fallback 6.8 TB/s"}}
+        del beams
+    del volt, w
+    return out
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args.gpus)
@@ -387,6 +417,7 @@ def main():
                      "note": "per cadence after the correlator; XFFT cadence = correlator + xfft"},
             "xfft_total_units_per_s": units / ((cms + xms) * 1e-3)}
         del vis
+        line["components"]["beamformer"] = bf_component(hai, ctx, flush, peaks)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         hai.hai_epic_image(ctx, lay, volt, C, T, prec, img, 0, st)
         torch.cuda.synchronize()

@@ -1,132 +1,154 @@
-// EPIC direct imager on tcgen05 tensor cores (Eq. intra-station EPIC, then the
-// squaring and temporal sum of Eq. intra-station squaring), FP16 operands with
-// FP32 accumulation in tensor memory.
+// EPIC direct imager on tcgen05 tensor cores for grid sides N = 32 and 64
+// (Eq. intra-station EPIC, then the squaring and temporal sum of Eq.
+// intra-station squaring), FP16 operands with FP32 accumulation in tensor
+// memory.
 //
 // The 2D DFT of each gridded field is two dense complex products with a
 // constant DFT matrix, written as real GEMMs (complex -> (re, im) pairs):
 //   stage 1 (along x):  H[y][l_x] = sum_x G[y][x] W'[x][l_x]
 //   stage 2 (along y):  F[l_y][l_x] = sum_y W'[y][l_y] H[y][l_x]
 // with W'[j][l] = (-1)^j exp(+2 pi i l j / N).  Only the kernel's bounding
-// box (<= 32 x 32 cells) is transformed, from the box origin: the shift by the
-// box corner multiplies F by a phase common to both polarisations, which
+// box (<= N/2 x N/2 cells) is transformed, from the box origin: the shift by
+// the box corner multiplies F by a phase common to both polarisations, which
 // cancels in every F_a conj(F_b); the (-1)^j factor puts the phase centre at
 // pixel (N/2, N/2).
 //
+// A step takes 128 / (N/2) fields (samples x 2 pols) so that stage 1 is one
+// M = 128 product: rows (field, y), columns (re/im, l_x), contraction (x,
+// re/im).  Stage 2 runs per "tile" of 128 rows (sample, l_x, pol) with the
+// transposed stage-1 result as the MN-major operand A and the same DFT matrix
+// as B; a tile holds one sample for N = 64 and two for N = 32.
+//
 // CTA = 16 warps, one CTA per SM, persistent over a contiguous range of the
-// flattened (channel, sample) index, two samples (four fields: 2 samples x
-// 2 pols) per step:
+// flattened (station, channel, sample) index:
 //   warps 0-6  "front": re-pack the step's voltages (landed by TMA bulk
-//              copies) as fp16 per element, gather-grid the four fields over
-//              tiles of the layout's non-empty cells into A1 (fp16, K-major)
-//              with FP32 sums; warps 0-3 then move
-//              stage-1 results from TMEM into the stage-2 operand A2 (fp16,
-//              MN-major), transposing on the way;
+//              copies) as fp16 per element, gather-grid the step's fields
+//              over tiles of the station's non-empty cells into A1 (fp16,
+//              K-major) with FP32 sums; warps 0-3 then move stage-1 results
+//              from TMEM into the stage-2 operand A2 (fp16, MN-major),
+//              transposing on the way;
 //   warp 7     one thread streams the voltages (TMA) and issues every MMA;
 //   warps 8-15 epilogue: read stage-2 results from TMEM, add |F_X|^2,
-//              |F_Y|^2 and F_X conj(F_Y) into register accumulators.
-// Every hand-off between the roles is an mbarrier phase, so no role blocks
-// on another's barrier.  TMEM (512 columns): stage-1 results double-buffered
-// (2 x 128 columns) and stage-2 results in two per-sample slots (2 x 128), so
-// the MMAs of one sample overlap the epilogue of the previous one.
+//              |F_Y|^2 and F_X conj(F_Y) into register accumulators, and
+//              write them out when a (station, channel) block ends.
+// Every hand-off between the roles is an mbarrier phase.  TMEM: stage-1
+// results double-buffered, stage-2 results in two tile slots, so the MMAs of
+// one tile overlap the epilogue of the previous one.
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
 #include <vector>
 
+#include "epic_tc.cuh"
 #include "hai_internal.h"
 #include "tc.cuh"
 
 namespace {
 
-constexpr int kN = 64;                  // grid side
-constexpr int kBox = 32;                // padded box side
 constexpr int kThreads = 512;
 constexpr int kFront = 224;             // warps 0-6
 constexpr int kMmaWarp = 7;
 constexpr int kEpi = 256;               // warps 8-15
 constexpr int kStages = 4;              // voltage steps in flight
 constexpr uint32_t kKs = 128;           // K-major operands: K-group stride
-constexpr uint32_t kMNs = 1024;         // K-major operands: MN-group stride (8 K groups)
-constexpr uint32_t kOpBytes = 16384;    // 128 rows x 64 K x 2 bytes
-constexpr uint32_t kImgBytes = 4096;    // one field's 32 rows inside A1
 constexpr uint32_t kA2Ks = 2064;        // MN-major A2: K-group stride (16 groups + 16 B pad)
 constexpr uint32_t kA2MNs = 128;        // MN-major A2: MN-group stride
-constexpr uint32_t kA2Bytes = 8 * kA2Ks;
-constexpr uint32_t kOffA1 = kOpBytes;   // after B
-constexpr uint32_t kOffA2 = kOffA1 + 2 * kOpBytes;
-constexpr uint32_t kOffE = kOffA2 + 4 * kA2Bytes;
-constexpr uint32_t kIdesc1 = tc::idesc_f16(128, 128, 0, 0);
-constexpr uint32_t kIdesc2 = tc::idesc_f16(128, 128, 1, 0);
 
-// Device table written by epic_tc_build_table (byte layout).  The non-empty
-// cells of the kernel's box are dealt into tiles of 32 (one per warp lane),
-// sorted by entry count so a tile's lanes run the same number of slots; a
-// tile's entries are stored slot-major, entry (slot k, lane l) at
-// tile_base + 32 k + l, with zero-weight padding.
-//   [0, 16384)         DFT operand B (K-major)
-//   cell offsets       uint32 [ntile * 32]  A1 byte offset of the lane's cell (field 0),
-//                                           0xffffffff for an unused lane
-//   tile bases         int32 [ntile + 1]    first entry of each tile (slots = diff / 32)
-//   (pad to 16)
-//   entry weights      float2 [nent]        a + ib = conj(W~)
-//   entry elements     uint16 [nent]
-struct TableLayout {
-    uint32_t off_cell, off_base, off_w, off_e, bytes;
+template <int N>
+struct Geo {
+    static constexpr int kBox = N / 2;                 // box side
+    static constexpr int kFields = 128 / kBox;         // fields per step: 4 or 8
+    static constexpr int kSps = kFields / 2;           // samples per step: 2 or 4
+    static constexpr int kTileSamples = 128 / (2 * N); // samples per stage-2 tile: 1 or 2
+    static constexpr int kTiles = kSps / kTileSamples; // tiles per step
+    static constexpr int kK = 2 * kBox;                // contraction of both stages: 64 or 32
+    static constexpr int kNcol = 2 * N;                // MMA N of both stages: 128 or 64
+    static constexpr int kU = kFields / 4;             // uint4 of fp16 voltages per element
+    static constexpr int kLy = N / 2;                  // output rows per epilogue thread
+    static constexpr uint32_t kMNs = (kK / 8) * kKs;   // K-major MN-group stride
+    static constexpr uint32_t kBBytes = (kNcol / 8) * kMNs;
+    static constexpr uint32_t kA1Bytes = 16 * kMNs;    // 128 rows
+    static constexpr uint32_t kImgBytes = (kBox / 8) * kMNs;   // one field's rows
+    static constexpr uint32_t kA2Bytes = (kK / 8) * kA2Ks;
+    static constexpr uint32_t kOffA1 = kBBytes;
+    static constexpr uint32_t kOffA2 = kOffA1 + 2 * kA1Bytes;
+    static constexpr uint32_t kOffE = kOffA2 + 2 * kTiles * kA2Bytes;
+    static constexpr uint32_t kTmemCols = (4 * kNcol <= 256) ? 256 : 512;
+    static constexpr uint32_t kIdesc1 = tc::idesc_f16(128, kNcol, 0, 0);
+    static constexpr uint32_t kIdesc2 = tc::idesc_f16(128, kNcol, 1, 0);
+    static_assert(kTiles == 2, "two stage-2 tiles per step");
 };
-__host__ __device__ inline TableLayout table_layout(int ntile, int nent) {
-    TableLayout t;
-    t.off_cell = kOpBytes;
-    t.off_base = t.off_cell + 4u * 32u * ntile;
-    t.off_w = (t.off_base + 4u * (ntile + 1) + 15u) & ~15u;
-    t.off_e = t.off_w + 8u * nent;
-    t.bytes = (t.off_e + 2u * nent + 15u) & ~15u;
-    return t;
-}
 
-struct EpicTcParams {
+struct Params {
     const int8_t *volt;
-    int C, T, ne;
-    long long len;
-    int ntile, nent;
-    const uint8_t *table;
-    float *out;
-    int direct, accumulate, use_tma;
+    float *img;
+    const TcStation *stations;
+    const uint8_t *dft;          // DFT operand B (K-major)
+    const long long *cta_begin;
+    long long len, total;
+    int C, T;
+    int ne_max;
+    uint32_t vstage;
+    int direct, accumulate, use_tma, guard;
+    float *partials;
     unsigned *status;
 };
 
-__device__ __forceinline__ void bar_front() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
+// One step of the flattened index: samples [t, t + nv) of block blk.
+struct Step {
+    long long blk;
+    int t, nv;
+};
 
-__global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const EpicTcParams p) {
+// Walks a CTA's range step by step; steps never straddle blocks.
+struct Cursor {
+    long long f, end;
+    int T, sps;
+    __device__ Step next() {
+        Step s;
+        s.blk = f / T;
+        s.t = (int)(f - s.blk * T);
+        const long long lim = min((s.blk + 1) * (long long)T, end);
+        s.nv = (int)min((long long)sps, lim - f);
+        f += s.nv;
+        return s;
+    }
+};
+
+__device__ __forceinline__ void bar_front() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
+__device__ __forceinline__ void bar_epi() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
+
+// Start of a step's voltages, rounded down to 16 bytes when the layout has
+// guard bytes (delta = bytes skipped).
+__device__ __forceinline__ const int8_t *step_src(const Params &p, const TcStation &st, const Step &s,
+                                                  uint32_t &delta) {
+    const long long c = s.blk % p.C;
+    const int8_t *src = p.volt + st.volt_off + ((c * p.T + s.t) * 4ll * st.ne);
+    delta = p.guard ? (uint32_t)((uintptr_t)src & 15u) : 0u;
+    return src - delta;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
+    using G = Geo<N>;
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t mb_v[kStages];
     __shared__ __align__(8) uint64_t mb_a1[2], mb_d1[2], mb_a2[2], mb_full[2], mb_empty[2];
     __shared__ uint32_t tmem_slot;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ne = p.ne;
-    const int sample_bytes = 4 * ne;                       // 2 pols x ne x (re, im)
-    const uint32_t vstage = (2u * sample_bytes + 15u) & ~15u;
-    const TableLayout tl = table_layout(p.ntile, p.nent);
     uint8_t *sB = smem;
-    uint8_t *sA1 = smem + kOffA1;
-    uint8_t *sA2 = smem + kOffA2;
-    uint4 *sE = reinterpret_cast<uint4 *>(smem + kOffE);    // [2 buffers][ne] 4 fields as half2
-    const uint32_t off_v = kOffE + 2u * 16u * ne;
+    uint8_t *sA1 = smem + G::kOffA1;
+    uint8_t *sA2 = smem + G::kOffA2;
+    uint4 *sE = reinterpret_cast<uint4 *>(smem + G::kOffE);   // [2][ne_max][kU]
+    const uint32_t off_v = G::kOffE + 2u * 16u * G::kU * p.ne_max;
     int8_t *sV = reinterpret_cast<int8_t *>(smem + off_v);
-    uint8_t *sT = smem + off_v + kStages * vstage;          // copy of the table after B
-    const uint32_t *s_cell = reinterpret_cast<const uint32_t *>(sT + tl.off_cell - kOpBytes);
-    const int32_t *s_base = reinterpret_cast<const int32_t *>(sT + tl.off_base - kOpBytes);
-    const float2 *s_w = reinterpret_cast<const float2 *>(sT + tl.off_w - kOpBytes);
-    const uint16_t *s_e = reinterpret_cast<const uint16_t *>(sT + tl.off_e - kOpBytes);
+    uint8_t *sT = smem + off_v + kStages * p.vstage;         // the current station's gather table
 
-    // ---- set-up: constant tables, zeroed A1, barriers, TMEM
-    for (int i = tid; i < (int)(kOpBytes / 16); i += kThreads)
-        reinterpret_cast<int4 *>(sB)[i] = __ldg(reinterpret_cast<const int4 *>(p.table) + i);
-    for (int i = tid; i < (int)((tl.bytes - kOpBytes) / 16); i += kThreads)
-        reinterpret_cast<int4 *>(sT)[i] = __ldg(reinterpret_cast<const int4 *>(p.table + kOpBytes) + i);
-    for (int i = tid; i < (int)(2 * kOpBytes / 16); i += kThreads)
-        reinterpret_cast<int4 *>(sA1)[i] = make_int4(0, 0, 0, 0);
+    // ---- set-up: DFT operand, barriers, TMEM
+    for (int i = tid; i < (int)(G::kBBytes / 16); i += kThreads)
+        reinterpret_cast<int4 *>(sB)[i] = __ldg(reinterpret_cast<const int4 *>(p.dft) + i);
     if (tid == 0) {
         for (int s = 0; s < kStages; s++) tc::mbar_init(&mb_v[s], 1);
         for (int b = 0; b < 2; b++) {
@@ -138,298 +160,499 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const EpicTcParams
         }
         tc::mbar_fence_init();
     }
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, G::kTmemCols);
     tc::fence_proxy_async();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tmem_slot;
 
-    const long long total = (long long)p.C * p.T;
-    const long long s0 = (long long)blockIdx.x * p.len;
-    const long long s1 = min(total, s0 + p.len);
-    const int nsamp = (int)max(0ll, s1 - s0);
-    const int npairs = (nsamp + 1) / 2;
-    auto pair_valid = [&](int i) { return min(2, nsamp - 2 * i); };
+    const long long s0 = p.cta_begin ? p.cta_begin[blockIdx.x] : (long long)blockIdx.x * p.len;
+    const long long s1 = p.cta_begin ? p.cta_begin[blockIdx.x + 1] : min(s0 + p.len, p.total);
+    // number of steps of the range
+    int nsteps = 0;
+    {
+        Cursor c{s0, s1, p.T, G::kSps};
+        while (c.f < c.end) {
+            const long long blk = c.f / p.T;
+            const long long lim = min((blk + 1) * (long long)p.T, s1);
+            nsteps += (int)((lim - c.f + G::kSps - 1) / G::kSps);
+            c.f = lim;
+        }
+    }
 
     if (warp < kMmaWarp) {
         // ================================================================ front
-        // voltages of step i -> sE[i & 1]: per element the four fields as
-        // half2 (int8 values are exact in fp16); ends with a front barrier
-        auto stage_volt = [&](int i) {
-            const int8_t *V = sV + (i % kStages) * vstage;
-            const int nv = pair_valid(i);
-            if (p.use_tma) {
-                tc::mbar_wait(&mb_v[i % kStages], (uint32_t)((i / kStages) & 1), p.status);
-            } else {
-                const int bytes = nv * sample_bytes;
-                const int8_t *src = p.volt + (size_t)(s0 + 2 * i) * sample_bytes;
-                int8_t *dst = sV + (i % kStages) * vstage;
-                for (int b = tid; b < bytes; b += kFront) dst[b] = src[b];
-                bar_front();
+        int cur_station = -1, ne = 0;
+        int a1_st0 = -1, a1_st1 = -1;          // station whose cells buffer 0 / 1 holds
+        int ntile = 0;
+        const uint32_t *s_cell = nullptr;
+        const int32_t *s_base = nullptr;
+        const float2 *s_w = nullptr;
+        const uint16_t *s_e = nullptr;
+
+        // new station: its gather table into shared memory; A1 buffer b zeroed
+        // when it last held another station's cells
+        auto prepare = [&](const Step &s, int i) {
+            const int stn = (int)(s.blk / p.C);
+            const int b = i & 1;
+            if (stn == cur_station && (b ? a1_st1 : a1_st0) == stn) return;
+            bar_front();                           // every front warp is done with step i-1
+            if (stn != cur_station) {
+                const TcStation st = p.stations[stn];
+                for (int k = tid; k < (int)(st.table_bytes / 16); k += kFront)
+                    reinterpret_cast<int4 *>(sT)[k] = __ldg(reinterpret_cast<const int4 *>(st.table) + k);
+                const GatherLayout gl = gather_layout(st.ntile, st.nent);
+                s_cell = reinterpret_cast<const uint32_t *>(sT + gl.off_cell);
+                s_base = reinterpret_cast<const int32_t *>(sT + gl.off_base);
+                s_w = reinterpret_cast<const float2 *>(sT + gl.off_w);
+                s_e = reinterpret_cast<const uint16_t *>(sT + gl.off_e);
+                ntile = st.ntile;
+                ne = st.ne;
+                cur_station = stn;
             }
-            // two consecutive elements x four fields per thread
-            uint4 *E = sE + (i & 1) * ne;
-            const char2 *v2 = reinterpret_cast<const char2 *>(V);
-            for (int a0 = 2 * tid; a0 < ne; a0 += 2 * kFront) {
-                uint32_t h0[4], h1[4];
-#pragma unroll
-                for (int f = 0; f < 4; f++) {
-                    char2 x = make_char2(0, 0), y = make_char2(0, 0);   // missing sample: 0
-                    if (f < 2 * nv) {
-                        x = v2[f * ne + a0];
-                        if (a0 + 1 < ne) y = v2[f * ne + a0 + 1];
-                    }
-                    h0[f] = tc::pack_half2((float)x.x, (float)x.y);
-                    h1[f] = tc::pack_half2((float)y.x, (float)y.y);
-                }
-                E[a0] = make_uint4(h0[0], h0[1], h0[2], h0[3]);
-                if (a0 + 1 < ne) E[a0 + 1] = make_uint4(h1[0], h1[1], h1[2], h1[3]);
+            if ((b ? a1_st1 : a1_st0) != stn) {
+                for (int k = tid; k < (int)(G::kA1Bytes / 16); k += kFront)
+                    reinterpret_cast<int4 *>(sA1 + b * G::kA1Bytes)[k] = make_int4(0, 0, 0, 0);
+                (b ? a1_st1 : a1_st0) = stn;
             }
             bar_front();
         };
-        // gridded values of the four fields: G_f[cell] = sum conj(W~) E_f,
+        // voltages of step i -> sE[i & 1]: per element the step's fields as
+        // half2 (int8 values are exact in fp16); ends with a front barrier
+        auto stage_volt = [&](const Step &s, int i) {
+            const int8_t *V;
+            if (p.use_tma) {
+                uint32_t delta;
+                step_src(p, p.stations[cur_station], s, delta);
+                tc::mbar_wait(&mb_v[i % kStages], (uint32_t)((i / kStages) & 1), p.status);
+                V = sV + (i % kStages) * p.vstage + delta;
+            } else {
+                uint32_t delta;
+                const int8_t *src = step_src(p, p.stations[cur_station], s, delta);
+                const int bytes = s.nv * 4 * ne;
+                int8_t *dst = sV + (i % kStages) * p.vstage;
+                for (int b = tid; b < bytes; b += kFront) dst[b] = src[b];
+                bar_front();
+                V = dst;
+            }
+            uint4 *E = sE + (size_t)(i & 1) * p.ne_max * G::kU;
+            const char2 *v2 = reinterpret_cast<const char2 *>(V);
+            for (int a = tid; a < ne; a += kFront) {
+                uint32_t h[G::kFields];
+#pragma unroll
+                for (int f = 0; f < G::kFields; f++) {
+                    char2 x = make_char2(0, 0);    // missing sample: 0
+                    if (f < 2 * s.nv) x = v2[f * ne + a];
+                    h[f] = tc::pack_half2((float)x.x, (float)x.y);
+                }
+#pragma unroll
+                for (int u = 0; u < G::kU; u++)
+                    E[a * G::kU + u] = make_uint4(h[4 * u], h[4 * u + 1], h[4 * u + 2], h[4 * u + 3]);
+            }
+            bar_front();
+        };
+        // gridded values of the step's fields: G_f[cell] = sum conj(W~) E_f,
         // one cell per lane, one tile of 32 cells per warp at a time
-        auto grid_pair = [&](int i) {
-            uint8_t *A = sA1 + (i & 1) * kOpBytes;
-            const uint4 *E = sE + (i & 1) * ne;
-            for (int t = warp; t < p.ntile; t += kMmaWarp) {
-                float2 g0 = make_float2(0.f, 0.f), g1 = g0, g2 = g0, g3 = g0;
+        auto grid_step = [&](int i) {
+            uint8_t *A = sA1 + (i & 1) * G::kA1Bytes;
+            const uint4 *E = sE + (size_t)(i & 1) * p.ne_max * G::kU;
+            for (int t = warp; t < ntile; t += kMmaWarp) {
+                float2 g[G::kFields];
+#pragma unroll
+                for (int f = 0; f < G::kFields; f++) g[f] = make_float2(0.f, 0.f);
                 const int qe = s_base[t + 1];
                 int q = s_base[t] + lane;
                 // software pipeline: slot k+1's weight and voltages load while slot k computes
                 float2 w_n = s_w[q];
-                uint4 e_n = E[s_e[q]];
+                uint4 e_n[G::kU];
+#pragma unroll
+                for (int u = 0; u < G::kU; u++) e_n[u] = E[s_e[q] * G::kU + u];
                 for (; q < qe; q += 32) {
                     const float2 w = w_n;
-                    const uint4 e = e_n;
+                    uint4 e[G::kU];
+#pragma unroll
+                    for (int u = 0; u < G::kU; u++) e[u] = e_n[u];
                     if (q + 32 < qe) {
                         w_n = s_w[q + 32];
-                        e_n = E[s_e[q + 32]];
+                        const int en = s_e[q + 32];
+#pragma unroll
+                        for (int u = 0; u < G::kU; u++) e_n[u] = E[en * G::kU + u];
                     }
-                    const float2 e0 = __half22float2(*reinterpret_cast<const __half2 *>(&e.x));
-                    const float2 e1 = __half22float2(*reinterpret_cast<const __half2 *>(&e.y));
-                    const float2 e2 = __half22float2(*reinterpret_cast<const __half2 *>(&e.z));
-                    const float2 e3 = __half22float2(*reinterpret_cast<const __half2 *>(&e.w));
-                    g0.x = fmaf(w.x, e0.x, fmaf(-w.y, e0.y, g0.x));
-                    g0.y = fmaf(w.x, e0.y, fmaf(w.y, e0.x, g0.y));
-                    g1.x = fmaf(w.x, e1.x, fmaf(-w.y, e1.y, g1.x));
-                    g1.y = fmaf(w.x, e1.y, fmaf(w.y, e1.x, g1.y));
-                    g2.x = fmaf(w.x, e2.x, fmaf(-w.y, e2.y, g2.x));
-                    g2.y = fmaf(w.x, e2.y, fmaf(w.y, e2.x, g2.y));
-                    g3.x = fmaf(w.x, e3.x, fmaf(-w.y, e3.y, g3.x));
-                    g3.y = fmaf(w.x, e3.y, fmaf(w.y, e3.x, g3.y));
+#pragma unroll
+                    for (int u = 0; u < G::kU; u++) {
+                        const uint32_t ev[4] = {e[u].x, e[u].y, e[u].z, e[u].w};
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            const float2 x = __half22float2(*reinterpret_cast<const __half2 *>(&ev[k]));
+                            float2 &acc = g[4 * u + k];
+                            acc.x = fmaf(w.x, x.x, fmaf(-w.y, x.y, acc.x));
+                            acc.y = fmaf(w.x, x.y, fmaf(w.y, x.x, acc.y));
+                        }
+                    }
                 }
                 const uint32_t off = s_cell[t * 32 + lane];
                 if (off != 0xffffffffu) {
                     uint8_t *c = A + off;
-                    *reinterpret_cast<uint32_t *>(c) = tc::pack_half2(g0.x, g0.y);
-                    *reinterpret_cast<uint32_t *>(c + kImgBytes) = tc::pack_half2(g1.x, g1.y);
-                    *reinterpret_cast<uint32_t *>(c + 2 * kImgBytes) = tc::pack_half2(g2.x, g2.y);
-                    *reinterpret_cast<uint32_t *>(c + 3 * kImgBytes) = tc::pack_half2(g3.x, g3.y);
+#pragma unroll
+                    for (int f = 0; f < G::kFields; f++)
+                        *reinterpret_cast<uint32_t *>(c + f * G::kImgBytes) = tc::pack_half2(g[f].x, g[f].y);
                 }
             }
         };
-        auto convert = [&](int i) {               // warps 0-3: field f = warp, row y = lane
-            const int f = warp, g = f >> 1, pol = f & 1, y = lane;
-            if (g >= pair_valid(i)) return;
-            uint8_t *A2 = sA2 + ((i & 1) * 2 + g) * kA2Bytes;
-            const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(i & 1) * 128u;
+        // warps 0-3: D1 row m = (field, y) -> A2 tile of its sample, column
+        // (y, re/im), rows (sample in tile, l_x, pol)
+        auto convert = [&](const Step &s, int i) {
+            const int m = warp * 32 + lane;
+            const int f = m / G::kBox, y = m % G::kBox;
+            const int smp = f >> 1, pol = f & 1;
+            const int tile = smp / G::kTileSamples, s2 = smp % G::kTileSamples;
+            if (tile * G::kTileSamples >= s.nv) return;   // tile not issued
+            uint8_t *A2 = sA2 + ((i & 1) * G::kTiles + tile) * G::kA2Bytes;
+            const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(i & 1) * G::kNcol;
 #pragma unroll
-            for (int ch = 0; ch < 4; ch++) {       // 32 columns: component c, frequencies kx0..kx0+31
+            for (int ch = 0; ch < G::kNcol / 32; ch++) {   // 32 columns: component c, l_x = kx0 .. kx0+31
                 uint32_t r[32];
                 tc::tmem_ld32(base + ch * 32, r);
                 tc::tmem_wait_ld();
-                const int c = ch >> 1, kx0 = (ch & 1) * 32;
+                const int c = (ch * 32) / N, kx0 = (ch * 32) % N;
                 const int kappa = 2 * y + c;
 #pragma unroll
                 for (int h = 0; h < 4; h++) {      // 8 frequencies -> one 16-byte row of A2
                     const int kx = kx0 + 8 * h;
-                    const int m = (kx >> 4) * 32 + pol * 16 + (kx & 15);
+                    const int m2 = s2 * 2 * N + (kx >> 4) * 32 + pol * 16 + (kx & 15);
                     uint4 v;
                     v.x = tc::pack_half2(__uint_as_float(r[8 * h + 0]), __uint_as_float(r[8 * h + 1]));
                     v.y = tc::pack_half2(__uint_as_float(r[8 * h + 2]), __uint_as_float(r[8 * h + 3]));
                     v.z = tc::pack_half2(__uint_as_float(r[8 * h + 4]), __uint_as_float(r[8 * h + 5]));
                     v.w = tc::pack_half2(__uint_as_float(r[8 * h + 6]), __uint_as_float(r[8 * h + 7]));
-                    *reinterpret_cast<uint4 *>(A2 + tc::off_mnmajor(m, kappa, kA2Ks, kA2MNs)) = v;
+                    *reinterpret_cast<uint4 *>(A2 + tc::off_mnmajor(m2, kappa, kA2Ks, kA2MNs)) = v;
                 }
             }
         };
         // A1 buffer (i+1)&1 was last read by MMA1(i-1), whose completion the
-        // converters saw before the stage barrier; A2 buffer i&1 was last read
-        // by MMA2(i-2), issued before MMA1(i), whose completion convert waits.
-        for (int i = -1; i < npairs; i++) {
-            if (i + 1 < npairs) {
-                stage_volt(i + 1);
-                grid_pair(i + 1);
+        // converters saw before the next front barrier; A2 buffer i&1 was last
+        // read by MMA2(i-2), issued before MMA1(i), whose completion convert waits.
+        Cursor cur{s0, s1, p.T, G::kSps};
+        Step prev{0, 0, 0}, nxt{0, 0, 0};
+        for (int i = -1; i < nsteps; i++) {
+            if (i + 1 < nsteps) {
+                nxt = cur.next();
+                prepare(nxt, i + 1);
+                stage_volt(nxt, i + 1);
+                grid_step(i + 1);
                 tc::fence_proxy_async();
                 tc::mbar_arrive(&mb_a1[(i + 1) & 1]);
             }
             if (i >= 0 && warp < 4) {
                 tc::mbar_wait(&mb_d1[i & 1], (uint32_t)((i >> 1) & 1), p.status);
                 tc::fence_after();
-                convert(i);
+                convert(prev, i);
                 tc::fence_proxy_async();
                 tc::fence_before();
                 tc::mbar_arrive(&mb_a2[i & 1]);
             }
+            prev = nxt;
         }
     } else if (warp == kMmaWarp) {
         // ================================================================ MMA + TMA
         if (lane == 0) {
             const uint32_t b = tc::smem_u32(sB);
-            auto issue_load = [&](int i) {
-                if (i >= npairs || !p.use_tma) return;
-                const uint32_t bytes = (uint32_t)pair_valid(i) * sample_bytes;
-                const int st = i % kStages;
-                tc::mbar_arrive_expect_tx(&mb_v[st], bytes);
-                tc::bulk_g2s(sV + st * vstage, p.volt + (size_t)(s0 + 2 * i) * sample_bytes, bytes, &mb_v[st]);
+            Cursor ld{s0, s1, p.T, G::kSps};
+            int n_loaded = 0;
+            auto issue_load = [&]() {
+                if (n_loaded >= nsteps || !p.use_tma) return;
+                const Step s = ld.next();
+                const TcStation &st = p.stations[s.blk / p.C];
+                uint32_t delta;
+                const int8_t *src = step_src(p, st, s, delta);
+                const uint32_t bytes = (delta + (uint32_t)s.nv * 4u * st.ne + 15u) & ~15u;
+                const int sg = n_loaded % kStages;
+                tc::mbar_arrive_expect_tx(&mb_v[sg], bytes);
+                tc::bulk_g2s(sV + sg * p.vstage, src, bytes, &mb_v[sg]);
+                n_loaded++;
             };
-            for (int q = 0; q < kStages; q++) issue_load(q);
-            for (int k = -1; k < npairs; k++) {
-                if (k + 1 < npairs) {              // stage 1 of step k+1
+            for (int q = 0; q < kStages; q++) issue_load();
+            Cursor cur{s0, s1, p.T, G::kSps};
+            Step prev{0, 0, 0}, nxt{0, 0, 0};
+            int jt = 0;                            // stage-2 tiles issued
+            for (int k = -1; k < nsteps; k++) {
+                if (k + 1 < nsteps) {              // stage 1 of step k+1
                     const int i = k + 1;
+                    nxt = cur.next();
                     tc::mbar_wait(&mb_a1[i & 1], (uint32_t)((i >> 1) & 1), p.status);
-                    issue_load(i + kStages);       // its voltage stage has been widened
+                    issue_load();                  // its voltage stage has been widened
                     tc::fence_after();
-                    const uint32_t a = tc::smem_u32(sA1 + (i & 1) * kOpBytes);
-                    const uint32_t d = tmem + (uint32_t)(i & 1) * 128u;
+                    const uint32_t a = tc::smem_u32(sA1 + (i & 1) * G::kA1Bytes);
+                    const uint32_t d = tmem + (uint32_t)(i & 1) * G::kNcol;
 #pragma unroll
-                    for (int s = 0; s < 4; s++)
-                        tc::mma_f16(d, tc::desc(a + s * 2 * kKs, kKs, kMNs), tc::desc(b + s * 2 * kKs, kKs, kMNs),
-                                    kIdesc1, s > 0);
+                    for (int s = 0; s < G::kK / 16; s++)
+                        tc::mma_f16(d, tc::desc(a + s * 2 * kKs, kKs, G::kMNs), tc::desc(b + s * 2 * kKs, kKs, G::kMNs),
+                                    G::kIdesc1, s > 0);
                     tc::mma_commit(&mb_d1[i & 1]);
                 }
-                if (k >= 0) {                      // stage 2 of step k, one slot per sample
+                if (k >= 0) {                      // stage 2 of step k, one slot per tile
                     tc::mbar_wait(&mb_a2[k & 1], (uint32_t)((k >> 1) & 1), p.status);
-                    const int nv = pair_valid(k);
-                    for (int g = 0; g < nv; g++) {
-                        const int j = 2 * k + g;
-                        if (j >= 2) tc::mbar_wait(&mb_empty[g], (uint32_t)(((j >> 1) - 1) & 1), p.status);
+                    const int ntl = (prev.nv + G::kTileSamples - 1) / G::kTileSamples;
+                    for (int g = 0; g < ntl; g++, jt++) {
+                        const int slot = jt & 1;
+                        if (jt >= 2) tc::mbar_wait(&mb_empty[slot], (uint32_t)(((jt >> 1) - 1) & 1), p.status);
                         tc::fence_after();
-                        const uint32_t a = tc::smem_u32(sA2 + ((k & 1) * 2 + g) * kA2Bytes);
-                        const uint32_t d = tmem + 256u + (uint32_t)g * 128u;
+                        const uint32_t a = tc::smem_u32(sA2 + ((k & 1) * G::kTiles + g) * G::kA2Bytes);
+                        const uint32_t d = tmem + 2u * G::kNcol + (uint32_t)slot * G::kNcol;
 #pragma unroll
-                        for (int s = 0; s < 4; s++)
+                        for (int s = 0; s < G::kK / 16; s++)
                             tc::mma_f16(d, tc::desc(a + s * 2 * kA2Ks, kA2Ks, kA2MNs),
-                                        tc::desc(b + s * 2 * kKs, kKs, kMNs), kIdesc2, s > 0);
-                        tc::mma_commit(&mb_full[g]);
+                                        tc::desc(b + s * 2 * kKs, kKs, G::kMNs), G::kIdesc2, s > 0);
+                        tc::mma_commit(&mb_full[slot]);
                     }
                 }
+                prev = nxt;
             }
         }
     } else {
         // ============================================================= epilogue
         const int q = warp & 3, h = (warp - 8) >> 2;
-        const int pol = lane >> 4, kx = 16 * q + (lane & 15);
+        const int m = 32 * q + lane;
+        const int s2 = m / (2 * N), mm = m % (2 * N);
+        const int pol = (mm >> 4) & 1, kx = (mm >> 5) * 16 + (mm & 15);
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        float acc_a[32], acc_x[32];
+        constexpr int kLy = G::kLy;
+        constexpr int kNN = N * N;
+        float acc_a[kLy], acc_x[kLy];
 #pragma unroll
-        for (int t = 0; t < 32; t++) acc_a[t] = acc_x[t] = 0.f;
+        for (int t = 0; t < kLy; t++) acc_a[t] = acc_x[t] = 0.f;
         int seg = 0;
-        int cur_c = nsamp > 0 ? (int)(s0 / p.T) : 0;
-        auto flush = [&](int c, int sgm) {
-            float *dst = p.direct ? p.out + (size_t)c * 4 * kN * kN
-                                  : p.out + ((size_t)blockIdx.x * 2 + sgm) * 4 * kN * kN;
+        long long cur_blk = -1;
+        // the two sample slots of an N = 32 tile hold partial sums of the same
+        // pixels: slot 0 writes, slot 1 adds after an epilogue barrier
+        auto flush = [&](long long blk, int sgm) {
+            const int stn = (int)(blk / p.C), c = (int)(blk % p.C);
+            float *dst = p.direct ? p.img + p.stations[stn].img_off + (size_t)c * 4 * kNN
+                                  : p.partials + ((size_t)blockIdx.x * 2 + sgm) * 4 * kNN;
 #pragma unroll
-            for (int t = 0; t < 32; t++) {
-                const int idx = pol * kN * kN + (32 * h + t) * kN + kx;
-                float v = acc_a[t];
-                if (p.direct && p.accumulate) v += dst[idx];
-                dst[idx] = v;
-                acc_a[t] = 0.f;
-            }
-            // cross products: the X thread holds X conj(Y) at even rows, the Y
-            // thread Y conj(X) = conj(X conj(Y)) at odd rows
-            const float sgn = pol ? -1.f : 1.f;
+            for (int phase = 0; phase < G::kTileSamples; phase++) {
+                if (phase > 0) bar_epi();
+                if (s2 != phase) continue;
+                const bool add = phase > 0 || (p.direct && p.accumulate);
 #pragma unroll
-            for (int t = 0; t < 16; t++) {
-                const int ly = 32 * h + 16 * (t >> 3) + 2 * (t & 7) + pol;
-                const int idx = 2 * kN * kN + ly * kN + kx;
-                float vr = acc_x[2 * t], vi = sgn * acc_x[2 * t + 1];
-                if (p.direct && p.accumulate) {
-                    vr += dst[idx];
-                    vi += dst[idx + kN * kN];
+                for (int t = 0; t < kLy; t++) {
+                    const int idx = pol * kNN + (kLy * h + t) * N + kx;
+                    float v = acc_a[t];
+                    if (add) v += dst[idx];
+                    dst[idx] = v;
+                    acc_a[t] = 0.f;
                 }
-                dst[idx] = vr;
-                dst[idx + kN * kN] = vi;
-                acc_x[2 * t] = acc_x[2 * t + 1] = 0.f;
+                // cross products: the X thread holds X conj(Y) at even rows, the Y
+                // thread Y conj(X) = conj(X conj(Y)) at odd rows
+                const float sgn = pol ? -1.f : 1.f;
+#pragma unroll
+                for (int t = 0; t < kLy / 2; t++) {
+                    const int ly = kLy * h + 16 * (t >> 3) + 2 * (t & 7) + pol;
+                    const int idx = 2 * kNN + ly * N + kx;
+                    float vr = acc_x[2 * t], vi = sgn * acc_x[2 * t + 1];
+                    if (add) {
+                        vr += dst[idx];
+                        vi += dst[idx + kNN];
+                    }
+                    dst[idx] = vr;
+                    dst[idx + kNN] = vi;
+                    acc_x[2 * t] = acc_x[2 * t + 1] = 0.f;
+                }
             }
         };
-        for (int j = 0; j < nsamp; j++) {
-            const int g = j & 1;
-            tc::mbar_wait(&mb_full[g], (uint32_t)((j >> 1) & 1), p.status);
-            tc::fence_after();
-            const int c = (int)((s0 + j) / p.T);
-            if (c != cur_c) {
-                flush(cur_c, seg);
-                seg++;
-                cur_c = c;
-            }
-#pragma unroll
-            for (int cc = 0; cc < 2; cc++) {
-                const uint32_t col = 256u + (uint32_t)g * 128u + (uint32_t)(32 * h + 16 * cc);
-                uint32_t rr[16], ri[16];
-                tc::tmem_ld16(tmem + lane_base + col, rr);
-                tc::tmem_ld16(tmem + lane_base + col + 64, ri);
-                tc::tmem_wait_ld();
-#pragma unroll
-                for (int t = 0; t < 16; t++) {
-                    const float fr = __uint_as_float(rr[t]), fi = __uint_as_float(ri[t]);
-                    acc_a[16 * cc + t] = fmaf(fr, fr, fmaf(fi, fi, acc_a[16 * cc + t]));
+        Cursor cur{s0, s1, p.T, G::kSps};
+        int jt = 0;
+        for (int i = 0; i < nsteps; i++) {
+            const Step s = cur.next();
+            if (s.blk != cur_blk) {
+                if (cur_blk >= 0) {
+                    flush(cur_blk, seg);
+                    seg++;
                 }
-#pragma unroll
-                for (int k = 0; k < 8; k++) {
-                    // own value at row 2k + pol, partner's value at the same row
-                    const float e_r = __uint_as_float(rr[2 * k]), e_i = __uint_as_float(ri[2 * k]);
-                    const float o_r = __uint_as_float(rr[2 * k + 1]), o_i = __uint_as_float(ri[2 * k + 1]);
-                    const float mr = pol ? o_r : e_r, mi = pol ? o_i : e_i;
-                    const float sr = __shfl_xor_sync(0xffffffffu, pol ? e_r : o_r, 16);
-                    const float si = __shfl_xor_sync(0xffffffffu, pol ? e_i : o_i, 16);
-                    const int a = 2 * (8 * cc + k);
-                    acc_x[a] = fmaf(mr, sr, fmaf(mi, si, acc_x[a]));            // Re own conj(other)
-                    acc_x[a + 1] = fmaf(mi, sr, fmaf(-mr, si, acc_x[a + 1]));   // Im own conj(other)
-                }
+                cur_blk = s.blk;
             }
-            tc::fence_before();
-            tc::mbar_arrive(&mb_empty[g]);
+            const int ntl = (s.nv + G::kTileSamples - 1) / G::kTileSamples;
+            for (int g = 0; g < ntl; g++, jt++) {
+                const int slot = jt & 1;
+                tc::mbar_wait(&mb_full[slot], (uint32_t)((jt >> 1) & 1), p.status);
+                tc::fence_after();
+#pragma unroll
+                for (int cc = 0; cc < kLy / 16; cc++) {
+                    const uint32_t col = 2u * G::kNcol + (uint32_t)slot * G::kNcol + (uint32_t)(kLy * h + 16 * cc);
+                    uint32_t rr[16], ri[16];
+                    tc::tmem_ld16(tmem + lane_base + col, rr);
+                    tc::tmem_ld16(tmem + lane_base + col + N, ri);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int t = 0; t < 16; t++) {
+                        const float fr = __uint_as_float(rr[t]), fi = __uint_as_float(ri[t]);
+                        acc_a[16 * cc + t] = fmaf(fr, fr, fmaf(fi, fi, acc_a[16 * cc + t]));
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        // own value at row 2k + pol, partner's value at the same row
+                        const float e_r = __uint_as_float(rr[2 * k]), e_i = __uint_as_float(ri[2 * k]);
+                        const float o_r = __uint_as_float(rr[2 * k + 1]), o_i = __uint_as_float(ri[2 * k + 1]);
+                        const float mr = pol ? o_r : e_r, mi = pol ? o_i : e_i;
+                        const float sr = __shfl_xor_sync(0xffffffffu, pol ? e_r : o_r, 16);
+                        const float si = __shfl_xor_sync(0xffffffffu, pol ? e_i : o_i, 16);
+                        const int a = 2 * (8 * cc + k);
+                        acc_x[a] = fmaf(mr, sr, fmaf(mi, si, acc_x[a]));            // Re own conj(other)
+                        acc_x[a + 1] = fmaf(mi, sr, fmaf(-mr, si, acc_x[a + 1]));   // Im own conj(other)
+                    }
+                }
+                tc::fence_before();
+                tc::mbar_arrive(&mb_empty[slot]);
+            }
         }
-        if (nsamp > 0) flush(cur_c, seg);
+        if (cur_blk >= 0) flush(cur_blk, seg);
     }
 
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if (warp == 0) tc::tmem_dealloc(tmem, G::kTmemCols);
 }
 
-size_t smem_bytes(int ne, int ntile, int nent) {
-    const uint32_t vstage = (8u * ne + 15u) & ~15u;
-    return kOffE + 32ull * ne + (size_t)kStages * vstage + (table_layout(ntile, nent).bytes - kOpBytes);
+template <int N>
+size_t smem_bytes(int ne_max, uint32_t table_max) {
+    using G = Geo<N>;
+    const uint32_t vstage = ((uint32_t)G::kSps * 4u * ne_max + 16u + 15u) & ~15u;
+    return G::kOffE + 32ull * G::kU * ne_max + (size_t)kStages * vstage + table_max;
+}
+
+template <int N>
+hai_status run_n(hai_ctx *ctx, const TcLaunch &l, cudaStream_t st) {
+    using G = Geo<N>;
+    const size_t smem = smem_bytes<N>(l.ne_max, l.table_max);
+    if (smem > (size_t)ctx->smem_optin)
+        return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16: shared memory need exceeds the device limit");
+    const void *dft = epic_tc_dft(ctx, N);
+    if (!dft) return hai_fail(HAI_ERR_INVALID_ARG, "epic fp16: DFT operand not prepared");
+    HAI_CUDA_TRY(cudaFuncSetAttribute(epic_tc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    Params p;
+    p.volt = l.volt;
+    p.img = l.img;
+    p.stations = l.stations;
+    p.dft = static_cast<const uint8_t *>(dft);
+    p.cta_begin = l.cta_begin;
+    p.len = l.len;
+    p.total = (long long)l.n_station * l.C * l.T;
+    p.C = l.C;
+    p.T = l.T;
+    p.ne_max = l.ne_max;
+    p.vstage = ((uint32_t)G::kSps * 4u * l.ne_max + 16u + 15u) & ~15u;
+    p.direct = l.direct;
+    p.accumulate = l.accumulate;
+    p.guard = l.guard;
+    // without guard bytes every step must start on 16 bytes: 4 ne % 16 == 0
+    // for every station and an aligned base
+    p.use_tma = l.guard || (((uintptr_t)l.volt & 15) == 0 && (4 * l.ne_max) % 16 == 0 && l.n_station == 1);
+    p.partials = l.partials;
+    p.status = ctx->d_status;
+    const int pidx = prof_begin(ctx, st);
+    epic_tc_kernel<N><<<l.n_cta, kThreads, smem, st>>>(p);
+    prof_end(ctx, pidx, st);
+    prof_count(ctx, 1);
+    HAI_CUDA_TRY(cudaGetLastError());
+    return HAI_OK;
 }
 
 }  // namespace
 
-bool epic_tc_supported(const hai_layout *L) {
-    return L->grid_n == kN && L->n_pol == 2 && L->box_w <= kBox && L->box_h <= kBox && L->n_elem <= 65535;
+void epic_tc_a1_strides(int N, uint32_t &k_stride, uint32_t &mn_stride) {
+    k_stride = kKs;
+    mn_stride = (N == 32) ? Geo<32>::kMNs : (N == 64) ? Geo<64>::kMNs : 16 * kKs;   // N = 128: K = 128
 }
 
-// Tables of the tensor-core path: the DFT operand of both stages,
-// B[n][kappa] with n = (out re/im, l) and kappa = (j, in re/im), in the
-// K-major layout (W'[j][l] = (-1)^j exp(+2 pi i l j / 64)); and the gather
-// tiles of the non-empty cells (see TableLayout).
-void epic_tc_build_table(const hai_layout *L, const std::vector<int32_t> &cstart,
-                         const std::vector<int32_t> &elem, const std::vector<float2> &w,
-                         std::vector<uint8_t> &out, int &ntile, int &nent) {
-    std::vector<int> cells;
-    for (int y = 0; y < L->box_h; y++)
-        for (int x = 0; x < L->box_w; x++)
-            if (cstart[y * L->box_w + x + 1] > cstart[y * L->box_w + x]) cells.push_back(y * L->box_w + x);
-    auto count = [&](int c) { return cstart[c + 1] - cstart[c]; };
-    auto a1off = [&](int cell) {
-        const int y = cell / L->box_w, x = cell % L->box_w;
-        return tc::off_kmajor(y, 2 * x, kKs, kMNs);
+int epic_tc_group(int N) { return N == 128 ? 4 : 1; }
+
+size_t epic_tc_smem(hai_ctx *, int N, int ne_max, uint32_t table_max) {
+    if (N == 32) return smem_bytes<32>(ne_max, table_max);
+    if (N == 64) return smem_bytes<64>(ne_max, table_max);
+    if (N == 128) return epic_tc128_smem(ne_max, table_max);
+    return (size_t)-1;
+}
+
+hai_status epic_tc_run(hai_ctx *ctx, int N, const TcLaunch &l, cudaStream_t st) {
+    if (l.n_cta <= 0) return HAI_OK;
+    if (N == 32) return run_n<32>(ctx, l, st);
+    if (N == 64) return run_n<64>(ctx, l, st);
+    if (N == 128) return epic_tc128_run(ctx, l, st);
+    return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16: grid size");
+}
+
+double epic_tc_dft_entry(int N, int c_out, int l, int j, int c_in) {
+    const double ang = 2.0 * 3.14159265358979323846 * (double)(((long long)l * j) % N) / N;
+    const double sgn = (j & 1) ? -1.0 : 1.0;
+    const double wr = sgn * cos(ang), wi = sgn * sin(ang);
+    // y_re = sum x_re wr - x_im wi ; y_im = sum x_re wi + x_im wr
+    if (c_out == 0) return c_in == 0 ? wr : -wi;
+    return c_in == 0 ? wi : wr;
+}
+
+// DFT operands, one blob per grid side, owned by the context.  N = 32, 64:
+// B[n = (c_out, l)][kappa = (j, c_in)], K-major, j < N/2.  N = 128: the four
+// column-quarter operands B1[r][n = (c_out, l mod 32)][kappa = (x, c_in)]
+// (l = 32 r + l mod 32), then the stage-2 operand A2[l_y][kappa = (y, c_in)]
+// (see epic_tc128.cu), all K-major with K = 128.
+hai_status epic_tc_dft_prepare(hai_ctx *ctx, int N) {
+    const int slot = (N == 32) ? 0 : (N == 64) ? 1 : (N == 128) ? 2 : -1;
+    if (slot < 0) return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16: grid size");
+    if (ctx->d_dft[slot]) return HAI_OK;
+    std::vector<uint8_t> out;
+    auto put = [&](size_t base, uint32_t off, double v) {
+        const __half hv = __double2half(v);
+        memcpy(&out[base + off], &hv, 2);
     };
+    if (N <= 64) {
+        const int box = N / 2, K = 2 * box;
+        const uint32_t mns = (uint32_t)(K / 8) * kKs;
+        out.assign((size_t)(2 * N / 8) * mns, 0);
+        for (int n = 0; n < 2 * N; n++)
+            for (int kappa = 0; kappa < K; kappa++)
+                put(0, tc::off_kmajor(n, kappa, kKs, mns), epic_tc_dft_entry(N, n / N, n % N, kappa >> 1, kappa & 1));
+    } else {
+        const uint32_t mns = 16 * kKs;              // K = 128
+        const size_t qbytes = 8 * (size_t)mns;     // 64 rows
+        out.assign(4 * qbytes + 16 * (size_t)mns, 0);
+        for (int r = 0; r < 4; r++)
+            for (int n = 0; n < 64; n++)
+                for (int kappa = 0; kappa < 128; kappa++)
+                    put(r * qbytes, tc::off_kmajor(n, kappa, kKs, mns),
+                        epic_tc_dft_entry(N, n >> 5, 32 * r + (n & 31), kappa >> 1, kappa & 1));
+        // A2[l_y][(y, c_in)]: row l_y of W'^T as the left factor of stage 2;
+        // (y, 0) -> Re W'[y][l_y], (y, 1) -> Im W'[y][l_y]
+        for (int ly = 0; ly < 128; ly++)
+            for (int kappa = 0; kappa < 128; kappa++) {
+                const double re = epic_tc_dft_entry(N, 0, ly, kappa >> 1, 0);   // wr
+                const double im = epic_tc_dft_entry(N, 1, ly, kappa >> 1, 0);   // wi
+                put(4 * qbytes, tc::off_kmajor(ly, kappa, kKs, mns), (kappa & 1) ? im : re);
+            }
+    }
+    void *d = nullptr;
+    HAI_CUDA_TRY(cudaSetDevice(ctx->device));
+    HAI_CUDA_TRY(cudaMalloc(&d, out.size()));
+    HAI_CUDA_TRY(cudaMemcpy(d, out.data(), out.size(), cudaMemcpyHostToDevice));
+    ctx->d_dft[slot] = d;
+    return HAI_OK;
+}
+
+const void *epic_tc_dft(hai_ctx *ctx, int N) {
+    const int slot = (N == 32) ? 0 : (N == 64) ? 1 : (N == 128) ? 2 : -1;
+    return slot < 0 ? nullptr : ctx->d_dft[slot];
+}
+
+void epic_tc_build_gather(int box_w, int box_h, const std::vector<int32_t> &cstart,
+                          const std::vector<int32_t> &elem, const std::vector<float2> &w, uint32_t k_stride,
+                          uint32_t mn_stride, std::vector<uint8_t> &out, int &ntile, int &nent) {
+    std::vector<int> cells;
+    for (int y = 0; y < box_h; y++)
+        for (int x = 0; x < box_w; x++)
+            if (cstart[y * box_w + x + 1] > cstart[y * box_w + x]) cells.push_back(y * box_w + x);
+    auto count = [&](int c) { return cstart[c + 1] - cstart[c]; };
+    auto a1off = [&](int cell) { return tc::off_kmajor(cell / box_w, 2 * (cell % box_w), k_stride, mn_stride); };
     std::stable_sort(cells.begin(), cells.end(), [&](int a, int b) {
         if (count(a) != count(b)) return count(a) > count(b);
         return a1off(a) < a1off(b);
@@ -442,22 +665,12 @@ void epic_tc_build_table(const hai_layout *L, const std::vector<int32_t> &cstart
         base[t + 1] = base[t] + 32 * slots;
     }
     nent = base[ntile];
-    const TableLayout tl = table_layout(ntile, nent);
-    out.assign(tl.bytes, 0);
-    for (int n = 0; n < 128; n++)
-        for (int kappa = 0; kappa < 2 * kBox; kappa++) {
-            const int j = kappa >> 1, c = kappa & 1, l = n & 63, im_out = n >> 6;
-            const double ang = 2.0 * 3.14159265358979323846 * (double)((l * j) % kN) / kN;
-            const double sgn = (j & 1) ? -1.0 : 1.0;
-            const double wr = sgn * cos(ang), wi = sgn * sin(ang);
-            const double v = im_out ? (c == 0 ? wi : wr) : (c == 0 ? wr : -wi);
-            const __half hv = __double2half(v);
-            memcpy(&out[tc::off_kmajor(n, kappa, kKs, kMNs)], &hv, 2);
-        }
-    uint32_t *o_cell = reinterpret_cast<uint32_t *>(&out[tl.off_cell]);
-    int32_t *o_base = reinterpret_cast<int32_t *>(&out[tl.off_base]);
-    float2 *o_w = reinterpret_cast<float2 *>(&out[tl.off_w]);
-    uint16_t *o_e = reinterpret_cast<uint16_t *>(&out[tl.off_e]);
+    const GatherLayout gl = gather_layout(ntile, nent);
+    out.assign(gl.bytes, 0);
+    uint32_t *o_cell = reinterpret_cast<uint32_t *>(&out[gl.off_cell]);
+    int32_t *o_base = reinterpret_cast<int32_t *>(&out[gl.off_base]);
+    float2 *o_w = reinterpret_cast<float2 *>(&out[gl.off_w]);
+    uint16_t *o_e = reinterpret_cast<uint16_t *>(&out[gl.off_e]);
     for (int t = 0; t <= ntile; t++) o_base[t] = base[t];
     for (int t = 0; t < ntile; t++)
         for (int l = 0; l < 32; l++) {
@@ -476,37 +689,56 @@ void epic_tc_build_table(const hai_layout *L, const std::vector<int32_t> &cstart
         }
 }
 
+void epic_tc_station_table(int grid_n, int box_w, int box_h, const std::vector<int32_t> &cstart,
+                           const std::vector<int32_t> &elem, const std::vector<float2> &w,
+                           std::vector<uint8_t> &out, int &ntile, int &nent, uint32_t &shared_bytes) {
+    if (grid_n == 128) {
+        epic_tc128_build_blob(box_w, box_h, cstart, elem, w, out, shared_bytes);
+        ntile = nent = 0;
+        return;
+    }
+    uint32_t ks, mns;
+    epic_tc_a1_strides(grid_n, ks, mns);
+    epic_tc_build_gather(box_w, box_h, cstart, elem, w, ks, mns, out, ntile, nent);
+    shared_bytes = (uint32_t)out.size();
+}
+
+// ---------------------------------------------------------------- one layout
+bool epic_tc_supported(const hai_layout *L) {
+    const int n = L->grid_n;
+    return (n == 32 || n == 64 || n == 128) && L->n_pol == 2 && L->box_w <= n / 2 && L->box_h <= n / 2 &&
+           L->n_elem <= 65535;
+}
+
 hai_status epic_tc_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
                           cudaStream_t st) {
-    if (!epic_tc_supported(L) || !L->d_tc_tables)
+    if (!epic_tc_supported(L) || !L->d_tc_station)
         return hai_fail(HAI_ERR_UNSUPPORTED,
-                        "epic fp16: this build's tensor-core path needs N = 64, 2 pols and a kernel box <= 32 x 32");
-    const size_t smem = smem_bytes(L->n_elem, L->tc_ntile, L->tc_nent);
-    if (smem > (size_t)L->ctx->smem_optin)
-        return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16: shared memory need exceeds the device limit");
-    HAI_CUDA_TRY(cudaFuncSetAttribute(epic_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const EpicSplit sp = epic_make_split(C, T, L->ctx->num_sms);
+                        "epic fp16: the tensor-core path needs N = 32, 64 or 128, 2 pols and a kernel box "
+                        "<= N/2 x N/2");
+    hai_ctx *ctx = L->ctx;
+    const int N = L->grid_n, grp = epic_tc_group(N);
+    const EpicSplit sp = epic_make_split(C, T, ctx->num_sms / grp);
     if (!sp.direct && (size_t)sp.n_cta * 2 > L->partial_slots)
         return hai_fail(HAI_ERR_INVALID_ARG, "epic fp16: partial buffer too small");
-    EpicTcParams p;
-    p.volt = volt;
-    p.C = C;
-    p.T = T;
-    p.ne = L->n_elem;
-    p.len = sp.len;
-    p.ntile = L->tc_ntile;
-    p.nent = L->tc_nent;
-    p.table = static_cast<const uint8_t *>(L->d_tc_tables);
-    p.out = sp.direct ? img : L->d_partials;
-    p.direct = sp.direct;
-    p.accumulate = accumulate;
-    p.use_tma = ((4 * L->n_elem) % 16 == 0) && ((((uintptr_t)volt) & 15) == 0);
-    p.status = L->ctx->d_status;
-    const int pidx = prof_begin(L->ctx, st);
-    epic_tc_kernel<<<sp.n_cta, kThreads, smem, st>>>(p);
-    prof_end(L->ctx, pidx, st);
-    prof_count(L->ctx, 1);
-    HAI_CUDA_TRY(cudaGetLastError());
+    TcLaunch l;
+    l.volt = volt;
+    l.img = img;
+    l.stations = static_cast<const TcStation *>(L->d_tc_station);
+    l.n_station = 1;
+    l.ne_max = L->n_elem;
+    l.table_max = (uint32_t)L->tc_tables_bytes;
+    l.cta_begin = nullptr;
+    l.len = sp.len;
+    l.n_cta = sp.n_cta;
+    l.C = C;
+    l.T = T;
+    l.direct = sp.direct;
+    l.accumulate = accumulate;
+    l.guard = 0;
+    l.partials = L->d_partials;
+    const hai_status s = epic_tc_run(ctx, N, l, st);
+    if (s != HAI_OK) return s;
     if (!sp.direct) return epic_reduce_launch(L, sp, C, T, img, accumulate, st);
     return HAI_OK;
 }

@@ -1,0 +1,105 @@
+// Pieces shared by the tensor-core EPIC kernels (epic_tc.cu for N = 32 and
+// 64, epic_tc128.cu for N = 128) and the batched plan (plan.cu).
+//
+// A launch images one or more stations ("a class": same grid side) over one
+// cadence of C channels x T samples.  The flattened sample index runs over
+// blocks (station, channel) of T samples each, block = station * C + channel,
+// and every CTA (or CTA group) takes a contiguous range of it.
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "hai_internal.h"
+
+// One station of a launch, in device memory.
+struct TcStation {
+    const uint8_t *table;   // gather table (GatherLayout) in global memory
+    long long volt_off;     // byte offset of the station's voltages [C][T][2][ne][2] int8
+    long long img_off;      // float offset of the station's images [C][4][N][N]
+    int ne;                 // elements
+    int ntile, nent;        // gather tiles and entries
+    uint32_t table_bytes;   // multiple of 16
+};
+
+// Gather table of the gridding step.  The non-empty cells of the kernel's
+// bounding box are dealt into tiles of 32 (one per warp lane), sorted by
+// entry count so a tile's lanes run the same number of slots; a tile's
+// entries are stored slot-major, entry (slot k, lane l) at tile_base + 32 k
+// + l, with zero-weight padding.
+//   cell offsets   uint32 [ntile * 32]  byte offset of the lane's cell in the
+//                                       stage-1 operand (field 0), or
+//                                       0xffffffff for an unused lane
+//   tile bases     int32 [ntile + 1]    first entry of each tile
+//   (pad to 16)
+//   weights        float2 [nent]        a + ib = conj(W~)
+//   elements       uint16 [nent]
+struct GatherLayout {
+    uint32_t off_cell, off_base, off_w, off_e, bytes;
+};
+__host__ __device__ inline GatherLayout gather_layout(int ntile, int nent) {
+    GatherLayout t;
+    t.off_cell = 0;
+    t.off_base = 4u * 32u * ntile;
+    t.off_w = (t.off_base + 4u * (ntile + 1) + 15u) & ~15u;
+    t.off_e = t.off_w + 8u * nent;
+    t.bytes = (t.off_e + 2u * nent + 15u) & ~15u;
+    return t;
+}
+
+// Builds the gather table of one station from its CSR cell lists (cells of
+// the box row-major, cstart[box_w * box_h + 1]).  Cell (x, y) of the box
+// lands at byte tc::off_kmajor(y, 2 x, k_stride, mn_stride) of the stage-1
+// operand.
+void epic_tc_build_gather(int box_w, int box_h, const std::vector<int32_t> &cstart,
+                          const std::vector<int32_t> &elem, const std::vector<float2> &w, uint32_t k_stride,
+                          uint32_t mn_stride, std::vector<uint8_t> &out, int &ntile, int &nent);
+
+// fp16 W'[j][l] = (-1)^j exp(+2 pi i l j / N) as a real matrix entry: row
+// (c_out, l), column (j, c_in) of the complex product y = W'^T x written for
+// (re, im) pairs.
+double epic_tc_dft_entry(int N, int c_out, int l, int j, int c_in);
+
+// DFT operands of the tensor-core kernels for grid side N (built once per
+// context, device memory owned by the context).
+const void *epic_tc_dft(hai_ctx *ctx, int N);
+hai_status epic_tc_dft_prepare(hai_ctx *ctx, int N);
+
+// Launchers over a list of stations of one grid side.  cta_begin (device,
+// n_cta + 1 flat sample indices) gives each CTA's range; when it is null the
+// ranges are b * len.  direct = 1: every block lies inside one CTA's range
+// and is written straight into the station's image (with accumulate);
+// direct = 0: blocks go to two partial slots per CTA for epic_reduce.
+// guard = 1: every station's voltage block has 16 spare bytes before and
+// after it, so voltage copies may round their start down and their end up
+// to 16 bytes.
+struct TcLaunch {
+    const int8_t *volt;
+    float *img;
+    const TcStation *stations;
+    int n_station;
+    int ne_max;
+    uint32_t table_max;
+    const long long *cta_begin;
+    long long len;
+    int n_cta;
+    int C, T;
+    int direct, accumulate, guard;
+    float *partials;
+};
+hai_status epic_tc_run(hai_ctx *ctx, int N, const TcLaunch &l, cudaStream_t st);
+size_t epic_tc_smem(hai_ctx *ctx, int N, int ne_max, uint32_t table_max);
+// Stage-1 operand strides of the gather table for grid side N.
+void epic_tc_a1_strides(int N, uint32_t &k_stride, uint32_t &mn_stride);
+// CTAs that image one channel together (1, or 4 for N = 128).
+int epic_tc_group(int N);
+hai_status epic_tc128_run(hai_ctx *ctx, const TcLaunch &l, cudaStream_t st);
+size_t epic_tc128_smem(int ne_max, uint32_t table_max);
+// Per-rank gather blob of one station for the N = 128 kernel;
+// max_rank_bytes = the largest rank table (what a CTA keeps in shared memory).
+void epic_tc128_build_blob(int box_w, int box_h, const std::vector<int32_t> &cstart,
+                           const std::vector<int32_t> &elem, const std::vector<float2> &w,
+                           std::vector<uint8_t> &out, uint32_t &max_rank_bytes);
+// Clusters of the N = 128 kernel resident at once (0 if it cannot run).
+int epic_tc128_max_groups(hai_ctx *ctx, int ne_max, uint32_t table_max);

@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include "epic_tc.cuh"
 #include "hai_internal.h"
 
 // ------------------------------------------------------------------ errors
@@ -101,6 +102,7 @@ extern "C" void hai_destroy(hai_ctx *ctx) {
     cudaSetDevice(ctx->device);
     prof_release(ctx);
     cudaFree(ctx->d_status);
+    for (void *d : ctx->d_dft) cudaFree(d);
     delete ctx;
 }
 
@@ -170,7 +172,7 @@ extern "C" hai_status hai_sync(hai_ctx *ctx, void *stream) {
 }
 
 // ------------------------------------------------------------------ layout
-static bool grid_supported(int n) { return n == 16 || n == 32 || n == 64; }
+static bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128; }
 
 static void layout_free(hai_layout *L) {
     if (!L) return;
@@ -181,6 +183,7 @@ static void layout_free(hai_layout *L) {
     cudaFree(L->d_entry_w);
     cudaFree(L->d_partials);
     cudaFree(L->d_tc_tables);
+    cudaFree(L->d_tc_station);
     delete L;
 }
 
@@ -262,15 +265,23 @@ extern "C" hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *d, 
         e = cudaMemcpy(L->d_entry_w, w.data(), sizeof(float2) * L->nnz, cudaMemcpyHostToDevice);
     // partial images of the time split (two channel segments per CTA)
     const int Q = (L->n_pol == 2) ? 4 : 1;
-    L->partial_slots = epic_partial_slots(epic_fp32_target_ctas(ctx, n));
+    L->partial_slots = epic_partial_slots(std::max(epic_fp32_target_ctas(ctx, n), ctx->num_sms));
     if (e == cudaSuccess)
         e = cudaMalloc(&L->d_partials, sizeof(float) * L->partial_slots * Q * (size_t)n * n);
-    if (e == cudaSuccess && epic_tc_supported(L)) {   // DFT operand of the tensor-core path
+    if (e == cudaSuccess && epic_tc_supported(L)) {   // tensor-core path: gather table, station record
         std::vector<uint8_t> tab;
-        epic_tc_build_table(L, count, elem, w, tab, L->tc_ntile, L->tc_nent);
-        L->tc_tables_bytes = tab.size();
+        TcStation rec = {};
+        uint32_t shared_bytes = 0;
+        epic_tc_station_table(n, L->box_w, L->box_h, count, elem, w, tab, rec.ntile, rec.nent, shared_bytes);
+        L->tc_tables_bytes = shared_bytes;
         e = cudaMalloc(&L->d_tc_tables, tab.size());
         if (e == cudaSuccess) e = cudaMemcpy(L->d_tc_tables, tab.data(), tab.size(), cudaMemcpyHostToDevice);
+        rec.table = static_cast<const uint8_t *>(L->d_tc_tables);
+        rec.ne = ne;
+        rec.table_bytes = shared_bytes;
+        if (e == cudaSuccess) e = cudaMalloc(&L->d_tc_station, sizeof(TcStation));
+        if (e == cudaSuccess) e = cudaMemcpy(L->d_tc_station, &rec, sizeof(TcStation), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && epic_tc_dft_prepare(ctx, n) != HAI_OK) e = cudaErrorMemoryAllocation;
     }
     if (e != cudaSuccess) {
         layout_free(L);

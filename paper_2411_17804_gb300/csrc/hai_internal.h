@@ -22,6 +22,7 @@ struct hai_ctx {
     std::vector<cudaEvent_t> prof_ev;   // pairs: [2i] before, [2i+1] after
     size_t prof_used = 0;               // pairs recorded
     long long prof_launches = 0;        // all kernels launched
+    void *d_dft[3] = {nullptr, nullptr, nullptr};   // tensor-core DFT operands, N = 32, 64, 128
 };
 
 // Profiling helpers: prof_begin returns the pair index or -1.
@@ -46,10 +47,11 @@ struct hai_layout {
     float2 *d_entry_w = nullptr;        // [nnz] conj(tap)
     float *d_partials = nullptr;        // EPIC time-split partial images
     size_t partial_slots = 0;           // capacity in images of [Q][N][N]
-    // tensor-core path tables (fp16 DFT operands); built at create time
+    // tensor-core path: gather table (or, for N = 128, the per-rank blob),
+    // its size in shared memory, and the one-station record the kernels read
     void *d_tc_tables = nullptr;
     size_t tc_tables_bytes = 0;
-    int tc_ntile = 0, tc_nent = 0;      // gather tiles of the tensor-core path
+    void *d_tc_station = nullptr;
 };
 
 // ---------------------------------------------------------------- errors
@@ -83,8 +85,10 @@ int epic_fp32_target_ctas(const hai_ctx *ctx, int grid_n);
 hai_status epic_tc_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img,
                           int accumulate, cudaStream_t st);
 bool epic_tc_supported(const hai_layout *L);
-void epic_tc_build_table(const hai_layout *L, const std::vector<int32_t> &cstart,
-                         const std::vector<int32_t> &elem, const std::vector<float2> &w,
-                         std::vector<uint8_t> &out, int &ntile, int &nent);
+// Gather table of a layout for the tensor-core kernel of its grid side;
+// shared_bytes = what the kernel keeps in shared memory.
+void epic_tc_station_table(int grid_n, int box_w, int box_h, const std::vector<int32_t> &cstart,
+                           const std::vector<int32_t> &elem, const std::vector<float2> &w,
+                           std::vector<uint8_t> &out, int &ntile, int &nent, uint32_t &shared_bytes);
 hai_status epic_reduce_launch(const hai_layout *L, const EpicSplit &sp, int C, int T, float *img,
                               int accumulate, cudaStream_t st);

@@ -83,6 +83,13 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
+// 32 lanes x 8 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
 // 32 lanes x 16 consecutive 32-bit columns: thread i of the warp receives
 // lane (quadrant base + i), columns taddr.col .. +15.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -169,6 +176,74 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(m))
         : "memory");
+}
+
+// ---------------------------------------------------------------- clusters
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Every thread of every CTA of the cluster arrives and waits.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release;\n barrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// Shared-memory address of the same variable in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t peer_addr(uint32_t local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+
+// Local shared -> shared of another CTA of the cluster, `bytes` (multiple of
+// 16, 16-byte aligned), completing on that CTA's mbarrier (cluster address).
+__device__ __forceinline__ void bulk_s2peer(uint32_t dst_cluster, const void *src, uint32_t bytes,
+                                            uint32_t mbar_cluster) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst_cluster),
+        "r"(smem_u32(src)), "r"(bytes), "r"(mbar_cluster)
+        : "memory");
+}
+
+// Arrive on the mbarrier at the same offset in every CTA of `mask` once all
+// MMAs issued so far by this thread complete.
+__device__ __forceinline__ void mma_commit_multicast(uint64_t *mbar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(mbar)),
+        "h"(mask)
+        : "memory");
+}
+
+// try_wait with cluster-scope acquire, for phases completed by other CTAs.
+__device__ __forceinline__ uint32_t mbar_try_wait_cluster(uint64_t *m, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(m)), "r"(parity), "r"(20000u)
+        : "memory");
+    return done;
+}
+
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *m, uint32_t parity, unsigned *status) {
+    if (mbar_try_wait_cluster(m, parity)) return true;
+    if (*reinterpret_cast<volatile unsigned *>(status) & HAI_DEV_TIMEOUT) return false;
+    const long long t0 = clock64();
+    unsigned ns = 32;
+    for (;;) {
+        __nanosleep(ns);
+        if (mbar_try_wait_cluster(m, parity)) return true;
+        if (ns < 512) ns <<= 1;
+        if (clock64() - t0 > (1ll << 32)) {
+            atomicOr(status, (unsigned)HAI_DEV_TIMEOUT);
+            return false;
+        }
+    }
 }
 
 __device__ __forceinline__ uint32_t pack_half2(float a, float b) {

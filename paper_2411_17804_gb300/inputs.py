@@ -298,12 +298,28 @@ def uneven_station_sizes(cfg: UnevenConfig) -> np.ndarray:
                   ).astype(np.int64)
 
 
+def uneven_diameter(n_elem: int, cfg: UnevenConfig) -> float:
+    """Station diameter: the 256-element station's, scaled with sqrt(N_e) so
+    the element density stays that of the SKA-low station."""
+    return cfg.ref_diameter_m * math.sqrt(n_elem / 256.0)
+
+
 def uneven_grid_side(n_elem: int, cfg: UnevenConfig) -> int:
-    """Padded grid side of a station: next power of two >= 2 x (diameter in
-    cells) + K, clamped to [32, 256]; the diameter scales with sqrt(N_e)."""
-    d = cfg.ref_diameter_m * math.sqrt(n_elem / 256.0)
-    need = 2.0 * d / (cfg.lam_m * cfg.cell_lambda) + cfg.ksize
+    """Padded grid side of a station: the next power of two >= 2 x (diameter
+    in cells + K), i.e. padding factor 2 on the kernel's full support, clamped
+    to [32, 256]."""
+    need = 2.0 * (uneven_diameter(n_elem, cfg) / (cfg.lam_m * cfg.cell_lambda) + cfg.ksize)
     n = 32
     while n < need and n < 256:
         n *= 2
     return n
+
+
+def uneven_station(cfg: UnevenConfig, index: int, n_elem: int | None = None) -> StationConfig:
+    """StationConfig of station `index` of the uneven array (its own seed)."""
+    ne = int(uneven_station_sizes(cfg)[index]) if n_elem is None else int(n_elem)
+    return StationConfig(
+        name=f"{cfg.name}_s{index}", n_elem=ne, diameter_m=uneven_diameter(ne, cfg),
+        min_spacing_m=1.5, lam_m=cfg.lam_m, n_chan=cfg.n_chan, n_pol=cfg.n_pol,
+        n_time=cfg.n_time, grid_n=uneven_grid_side(ne, cfg), cell_lambda=cfg.cell_lambda,
+        ksize=cfg.ksize, n_src=20, seed=cfg.seed * 7919 + index)

@@ -199,6 +199,42 @@ def test_tc_accumulate_and_deterministic(hai, ctx):
     hai.hai_layout_destroy(lay)
 
 
+@pytest.mark.parametrize("n_elem,C,T", [
+    (40, 3, 37),      # N = 32: time split over CTAs, ragged 4-sample steps
+    (40, 160, 5),     # N = 32: one CTA per channel
+    (60, 1, 1),       # N = 32: a single sample
+    (300, 2, 9),      # N = 64 station of the uneven array
+    (700, 2, 13),     # N = 128: time split over 4-CTA clusters
+    (1000, 40, 3),    # N = 128: one cluster per channel, largest station
+    (500, 1, 2),      # N = 128: fewer samples than clusters
+])
+def test_tc_uneven_station_grid_sides(hai, ctx, n_elem, C, T):
+    """Stations of the uneven array at their own grid side (32, 64, 128):
+    voltages of the seeded sky, then complex taps with uniform voltages; both
+    also accumulated a second time onto the first result."""
+    sc = I.uneven_station(I.UnevenConfig(), 0, n_elem)
+    pos, anchors, taps = station(sc)
+    n = sc.grid_n
+    rng = np.random.default_rng(n_elem)
+    ctaps = taps.copy()
+    ctaps[..., 1] = 0.3 * rng.standard_normal(taps.shape[:-1]).astype(np.float32)
+    cases = [(taps, I.station_voltages(sc, pos, n_chan=C, n_time=T)),
+             (ctaps, I.random_voltages((C, T, 2, len(pos), 2), seed=n_elem + C + T))]
+    for tp, volt in cases:
+        lay = hai.hai_layout_create(ctx, anchors, tp, n, 2)
+        img = torch.full((C, 4, n, n), float("nan"), device="cuda")
+        v = volt.cuda()
+        hai.hai_epic_image(ctx, lay, v, C, T, hai.HAI_PREC_FP16, img, 0)
+        hai.hai_sync(ctx)
+        want = O.epic_image(n, anchors, tp, volt.numpy())
+        got = img.cpu().numpy()
+        assert rel_err_planes(got, want).max() < REDUCED_TOL, (n, rel_err_planes(got, want).max())
+        hai.hai_epic_image(ctx, lay, v, C, T, hai.HAI_PREC_FP16, img, 1)
+        hai.hai_sync(ctx)
+        assert rel_err_planes(img.cpu().numpy(), 2 * want).max() < REDUCED_TOL
+        hai.hai_layout_destroy(lay)
+
+
 def test_tc_unsupported_layout_is_reported(hai, ctx):
     cfg = I.SINGLE_STATION_64
     pos, anchors, taps = station(cfg)
