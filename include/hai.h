@@ -130,12 +130,63 @@ hai_status hai_layout_box(const hai_layout *layout, int *box);
  *   volt  device int8 [C][T][P][N_e][2]
  *   img   device float [C][Q][N][N], Q = 1 (P = 1) or 4 (P = 2); overwritten
  *         (accumulate = 0) or added to (accumulate = 1)
- *   prec  HAI_PREC_FP32 (CUDA-core FFT) or HAI_PREC_FP16 (tensor cores)
+ *   prec  HAI_PREC_FP32 (CUDA-core FFT; N = 16, 32 or 64) or HAI_PREC_FP16
+ *         (tensor cores; N = 32, 64 or 128, P = 2 and a kernel box of at most
+ *         N/2 x N/2 cells, else HAI_ERR_UNSUPPORTED)
  * C >= 0, T >= 0 (C = 0 or T = 0: nothing to image; with accumulate = 0 the
  * image is zeroed). */
 hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *layout, const int8_t *volt,
                           int C, int T, hai_precision prec, float *img, int accumulate,
                           void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched EPIC over an array of stations of uneven size (the heterogeneous
+ * stations the paper's hierarchical arrays allow, Section 2): the EPIC image
+ * of every station (as hai_epic_image with HAI_PREC_FP16) for one cadence of
+ * C channels x T samples, run as ONE CUDA-graph launch per cadence.  The
+ * plan groups the stations by grid side, gives every group a share of the
+ * SMs (a persistent tensor-core kernel per group, all groups concurrent) and
+ * cuts each group's (station, channel) blocks into per-CTA ranges of equal
+ * modelled cost; hai_plan_autotune refits the shares from measured times.
+ *
+ * hai_plan_create: `stations` = S layouts (host array of pointers) of this
+ * context, each with P = 2, grid side 32, 64 or 128 and a kernel box of at
+ * most N/2 x N/2 (else HAI_ERR_UNSUPPORTED); prec must be HAI_PREC_FP16.
+ * The plan copies what it needs: the layouts may be destroyed afterwards.
+ * Device memory for tables and schedules is reserved here, none at run time.
+ */
+typedef struct hai_plan hai_plan;
+hai_status hai_plan_create(hai_ctx *ctx, const hai_layout *const *stations, int S, int C, int T,
+                           hai_precision prec, hai_plan **out);
+void hai_plan_destroy(hai_plan *plan);
+
+/* Buffer layout of the plan (host outputs; pass NULL for any not wanted):
+ *   volt_off[S]  byte offset of station s's voltages [C][T][2][N_e,s][2]
+ *                int8 inside the one voltage buffer; every block starts on
+ *                16 bytes and has at least 16 unused bytes before and after
+ *                it (the kernels read 16-byte aligned spans that may cover
+ *                them; their content is ignored)
+ *   img_off[S]   float offset of station s's images [C][4][N_s][N_s]
+ *   volt_bytes   size of the voltage buffer;  img_floats  size of the image buffer */
+hai_status hai_plan_layout(const hai_plan *plan, int64_t *volt_off, int64_t *img_off, int64_t *volt_bytes,
+                           int64_t *img_floats);
+
+/* Image one cadence: volt (device, volt_bytes, 16-byte aligned) -> img
+ * (device, img_floats, 16-byte aligned, overwritten).  The first call with a
+ * given (volt, img) pair captures the graph (allocating host-side graph
+ * objects); later calls with the same pair only launch it on `stream`. */
+hai_status hai_plan_run(hai_plan *plan, const int8_t *volt, float *img, void *stream);
+
+/* Autotuner: `rounds` times, run every grid group alone on its current SM
+ * share (twice, timing the second run with events on `stream`), then
+ * re-divide the SMs so that the groups' measured SM-time is balanced.  Runs
+ * the kernels on (volt, img), overwriting img.  Synchronises the stream. */
+hai_status hai_plan_autotune(hai_plan *plan, const int8_t *volt, float *img, int rounds, void *stream);
+
+/* Schedule of the plan (host outputs, arrays of length *n_class <= 3):
+ * grid side, CTAs and last measured time alone (ms, 0 before autotuning) of
+ * every grid group. */
+hai_status hai_plan_schedule(const hai_plan *plan, int *n_class, int *grid_n, int *ctas, double *measured_ms);
 
 /* ---------------------------------------------------------------------------
  * Correlator (Eq. intra-station visibilities): for every element pair a >= b

@@ -95,39 +95,8 @@ struct Params {
     unsigned *status;
 };
 
-// One step of the flattened index: samples [t, t + nv) of block blk.
-struct Step {
-    long long blk;
-    int t, nv;
-};
-
-// Walks a CTA's range step by step; steps never straddle blocks.
-struct Cursor {
-    long long f, end;
-    int T, sps;
-    __device__ Step next() {
-        Step s;
-        s.blk = f / T;
-        s.t = (int)(f - s.blk * T);
-        const long long lim = min((s.blk + 1) * (long long)T, end);
-        s.nv = (int)min((long long)sps, lim - f);
-        f += s.nv;
-        return s;
-    }
-};
-
 __device__ __forceinline__ void bar_front() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
 __device__ __forceinline__ void bar_epi() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
-
-// Start of a step's voltages, rounded down to 16 bytes when the layout has
-// guard bytes (delta = bytes skipped).
-__device__ __forceinline__ const int8_t *step_src(const Params &p, const TcStation &st, const Step &s,
-                                                  uint32_t &delta) {
-    const long long c = s.blk % p.C;
-    const int8_t *src = p.volt + st.volt_off + ((c * p.T + s.t) * 4ll * st.ne);
-    delta = p.guard ? (uint32_t)((uintptr_t)src & 15u) : 0u;
-    return src - delta;
-}
 
 template <int N>
 __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
@@ -169,17 +138,7 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
 
     const long long s0 = p.cta_begin ? p.cta_begin[blockIdx.x] : (long long)blockIdx.x * p.len;
     const long long s1 = p.cta_begin ? p.cta_begin[blockIdx.x + 1] : min(s0 + p.len, p.total);
-    // number of steps of the range
-    int nsteps = 0;
-    {
-        Cursor c{s0, s1, p.T, G::kSps};
-        while (c.f < c.end) {
-            const long long blk = c.f / p.T;
-            const long long lim = min((blk + 1) * (long long)p.T, s1);
-            nsteps += (int)((lim - c.f + G::kSps - 1) / G::kSps);
-            c.f = lim;
-        }
-    }
+    const int nsteps = tc_count_steps(s0, s1, p.T, G::kSps);
 
     if (warp < kMmaWarp) {
         // ================================================================ front
@@ -193,8 +152,8 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
 
         // new station: its gather table into shared memory; A1 buffer b zeroed
         // when it last held another station's cells
-        auto prepare = [&](const Step &s, int i) {
-            const int stn = (int)(s.blk / p.C);
+        auto prepare = [&](const TcStep &s, int i) {
+            const int stn = s.stn;
             const int b = i & 1;
             if (stn == cur_station && (b ? a1_st1 : a1_st0) == stn) return;
             bar_front();                           // every front warp is done with step i-1
@@ -220,16 +179,14 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
         };
         // voltages of step i -> sE[i & 1]: per element the step's fields as
         // half2 (int8 values are exact in fp16); ends with a front barrier
-        auto stage_volt = [&](const Step &s, int i) {
+        auto stage_volt = [&](const TcStep &s, int i) {
             const int8_t *V;
+            uint32_t delta;
+            const int8_t *src = tc_aligned_src(s.src, p.guard, delta);
             if (p.use_tma) {
-                uint32_t delta;
-                step_src(p, p.stations[cur_station], s, delta);
                 tc::mbar_wait(&mb_v[i % kStages], (uint32_t)((i / kStages) & 1), p.status);
                 V = sV + (i % kStages) * p.vstage + delta;
             } else {
-                uint32_t delta;
-                const int8_t *src = step_src(p, p.stations[cur_station], s, delta);
                 const int bytes = s.nv * 4 * ne;
                 int8_t *dst = sV + (i % kStages) * p.vstage;
                 for (int b = tid; b < bytes; b += kFront) dst[b] = src[b];
@@ -302,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
         };
         // warps 0-3: D1 row m = (field, y) -> A2 tile of its sample, column
         // (y, re/im), rows (sample in tile, l_x, pol)
-        auto convert = [&](const Step &s, int i) {
+        auto convert = [&](const TcStep &s, int i) {
             const int m = warp * 32 + lane;
             const int f = m / G::kBox, y = m % G::kBox;
             const int smp = f >> 1, pol = f & 1;
@@ -333,11 +290,12 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
         // A1 buffer (i+1)&1 was last read by MMA1(i-1), whose completion the
         // converters saw before the next front barrier; A2 buffer i&1 was last
         // read by MMA2(i-2), issued before MMA1(i), whose completion convert waits.
-        Cursor cur{s0, s1, p.T, G::kSps};
-        Step prev{0, 0, 0}, nxt{0, 0, 0};
+        TcWalker wk;
+        wk.init(p.volt, p.stations, p.C, p.T, s0, s1);
+        TcStep prev{}, nxt{};
         for (int i = -1; i < nsteps; i++) {
             if (i + 1 < nsteps) {
-                nxt = cur.next();
+                nxt = wk.next(G::kSps);
                 prepare(nxt, i + 1);
                 stage_volt(nxt, i + 1);
                 grid_step(i + 1);
@@ -358,28 +316,29 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
         // ================================================================ MMA + TMA
         if (lane == 0) {
             const uint32_t b = tc::smem_u32(sB);
-            Cursor ld{s0, s1, p.T, G::kSps};
+            TcWalker ld;
+            ld.init(p.volt, p.stations, p.C, p.T, s0, s1);
             int n_loaded = 0;
             auto issue_load = [&]() {
                 if (n_loaded >= nsteps || !p.use_tma) return;
-                const Step s = ld.next();
-                const TcStation &st = p.stations[s.blk / p.C];
+                const TcStep s = ld.next(G::kSps);
                 uint32_t delta;
-                const int8_t *src = step_src(p, st, s, delta);
-                const uint32_t bytes = (delta + (uint32_t)s.nv * 4u * st.ne + 15u) & ~15u;
+                const int8_t *src = tc_aligned_src(s.src, p.guard, delta);
+                const uint32_t bytes = (delta + (uint32_t)s.nv * 4u * s.ne + 15u) & ~15u;
                 const int sg = n_loaded % kStages;
                 tc::mbar_arrive_expect_tx(&mb_v[sg], bytes);
                 tc::bulk_g2s(sV + sg * p.vstage, src, bytes, &mb_v[sg]);
                 n_loaded++;
             };
             for (int q = 0; q < kStages; q++) issue_load();
-            Cursor cur{s0, s1, p.T, G::kSps};
-            Step prev{0, 0, 0}, nxt{0, 0, 0};
+            TcWalker wk;
+            wk.init(p.volt, p.stations, p.C, p.T, s0, s1);
+            TcStep prev{}, nxt{};
             int jt = 0;                            // stage-2 tiles issued
             for (int k = -1; k < nsteps; k++) {
                 if (k + 1 < nsteps) {              // stage 1 of step k+1
                     const int i = k + 1;
-                    nxt = cur.next();
+                    nxt = wk.next(G::kSps);
                     tc::mbar_wait(&mb_a1[i & 1], (uint32_t)((i >> 1) & 1), p.status);
                     issue_load();                  // its voltage stage has been widened
                     tc::fence_after();
@@ -426,8 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
         long long cur_blk = -1;
         // the two sample slots of an N = 32 tile hold partial sums of the same
         // pixels: slot 0 writes, slot 1 adds after an epilogue barrier
-        auto flush = [&](long long blk, int sgm) {
-            const int stn = (int)(blk / p.C), c = (int)(blk % p.C);
+        auto flush = [&](int stn, int c, int sgm) {
             float *dst = p.direct ? p.img + p.stations[stn].img_off + (size_t)c * 4 * kNN
                                   : p.partials + ((size_t)blockIdx.x * 2 + sgm) * 4 * kNN;
 #pragma unroll
@@ -461,16 +419,20 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
                 }
             }
         };
-        Cursor cur{s0, s1, p.T, G::kSps};
-        int jt = 0;
+        TcWalker wk;
+        wk.init(p.volt, p.stations, p.C, p.T, s0, s1);
+        int jt = 0, cur_stn = 0, cur_chan = 0;
         for (int i = 0; i < nsteps; i++) {
-            const Step s = cur.next();
-            if (s.blk != cur_blk) {
+            const TcStep s = wk.next(G::kSps);
+            const long long blk = s.blk(p.C);
+            if (blk != cur_blk) {
                 if (cur_blk >= 0) {
-                    flush(cur_blk, seg);
+                    flush(cur_stn, cur_chan, seg);
                     seg++;
                 }
-                cur_blk = s.blk;
+                cur_blk = blk;
+                cur_stn = s.stn;
+                cur_chan = s.chan;
             }
             const int ntl = (s.nv + G::kTileSamples - 1) / G::kTileSamples;
             for (int g = 0; g < ntl; g++, jt++) {
@@ -506,7 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
                 tc::mbar_arrive(&mb_empty[slot]);
             }
         }
-        if (cur_blk >= 0) flush(cur_blk, seg);
+        if (cur_blk >= 0) flush(cur_stn, cur_chan, seg);
     }
 
     tc::fence_before();
@@ -526,11 +488,15 @@ template <int N>
 hai_status run_n(hai_ctx *ctx, const TcLaunch &l, cudaStream_t st) {
     using G = Geo<N>;
     const size_t smem = smem_bytes<N>(l.ne_max, l.table_max);
-    if (smem > (size_t)ctx->smem_optin)
+    if (smem + kStaticSmem > (size_t)ctx->smem_optin)
         return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16: shared memory need exceeds the device limit");
     const void *dft = epic_tc_dft(ctx, N);
     if (!dft) return hai_fail(HAI_ERR_INVALID_ARG, "epic fp16: DFT operand not prepared");
-    HAI_CUDA_TRY(cudaFuncSetAttribute(epic_tc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the limit is the device's, so launches of any size (and captured graphs) stay valid
+    if (!l.no_attr) {
+        const hai_status s = epic_tc_set_attr(ctx, N);
+        if (s != HAI_OK) return s;
+    }
     Params p;
     p.volt = l.volt;
     p.img = l.img;
@@ -573,6 +539,24 @@ size_t epic_tc_smem(hai_ctx *, int N, int ne_max, uint32_t table_max) {
     if (N == 64) return smem_bytes<64>(ne_max, table_max);
     if (N == 128) return epic_tc128_smem(ne_max, table_max);
     return (size_t)-1;
+}
+
+// Dynamic shared memory a kernel may use: the device's opt-in limit less the
+// kernel's static shared memory.
+template <typename K>
+hai_status raise_limit(hai_ctx *ctx, K kern) {
+    cudaFuncAttributes a;
+    HAI_CUDA_TRY(cudaFuncGetAttributes(&a, kern));
+    HAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      ctx->smem_optin - (int)a.sharedSizeBytes));
+    return HAI_OK;
+}
+
+hai_status epic_tc_set_attr(hai_ctx *ctx, int N) {
+    if (N == 32) return raise_limit(ctx, epic_tc_kernel<32>);
+    if (N == 64) return raise_limit(ctx, epic_tc_kernel<64>);
+    if (N == 128) return epic_tc128_set_attr(ctx);
+    return HAI_OK;
 }
 
 hai_status epic_tc_run(hai_ctx *ctx, int N, const TcLaunch &l, cudaStream_t st) {
@@ -691,9 +675,10 @@ void epic_tc_build_gather(int box_w, int box_h, const std::vector<int32_t> &csta
 
 void epic_tc_station_table(int grid_n, int box_w, int box_h, const std::vector<int32_t> &cstart,
                            const std::vector<int32_t> &elem, const std::vector<float2> &w,
-                           std::vector<uint8_t> &out, int &ntile, int &nent, uint32_t &shared_bytes) {
+                           std::vector<uint8_t> &out, int &ntile, int &nent, uint32_t &shared_bytes,
+                           long long &entries) {
     if (grid_n == 128) {
-        epic_tc128_build_blob(box_w, box_h, cstart, elem, w, out, shared_bytes);
+        epic_tc128_build_blob(box_w, box_h, cstart, elem, w, out, shared_bytes, entries);
         ntile = nent = 0;
         return;
     }
@@ -701,6 +686,7 @@ void epic_tc_station_table(int grid_n, int box_w, int box_h, const std::vector<i
     epic_tc_a1_strides(grid_n, ks, mns);
     epic_tc_build_gather(box_w, box_h, cstart, elem, w, ks, mns, out, ntile, nent);
     shared_bytes = (uint32_t)out.size();
+    entries = nent;
 }
 
 // ---------------------------------------------------------------- one layout
@@ -718,7 +704,7 @@ hai_status epic_tc_launch(const hai_layout *L, const int8_t *volt, int C, int T,
                         "<= N/2 x N/2");
     hai_ctx *ctx = L->ctx;
     const int N = L->grid_n, grp = epic_tc_group(N);
-    const EpicSplit sp = epic_make_split(C, T, ctx->num_sms / grp);
+    const EpicSplit sp = epic_make_split(C, T, N == 128 ? L->tc_groups : ctx->num_sms / grp);
     if (!sp.direct && (size_t)sp.n_cta * 2 > L->partial_slots)
         return hai_fail(HAI_ERR_INVALID_ARG, "epic fp16: partial buffer too small");
     TcLaunch l;
@@ -737,6 +723,7 @@ hai_status epic_tc_launch(const hai_layout *L, const int8_t *volt, int C, int T,
     l.accumulate = accumulate;
     l.guard = 0;
     l.partials = L->d_partials;
+    l.no_attr = 0;
     const hai_status s = epic_tc_run(ctx, N, l, st);
     if (s != HAI_OK) return s;
     if (!sp.direct) return epic_reduce_launch(L, sp, C, T, img, accumulate, st);

@@ -13,6 +13,10 @@
 
 #include "hai_internal.h"
 
+// Static shared memory of the tensor-core EPIC kernels (mbarriers, TMEM
+// address), which the device's per-block opt-in limit also has to hold.
+constexpr size_t kStaticSmem = 1024;
+
 // One station of a launch, in device memory.
 struct TcStation {
     const uint8_t *table;   // gather table (GatherLayout) in global memory
@@ -22,6 +26,84 @@ struct TcStation {
     int ntile, nent;        // gather tiles and entries
     uint32_t table_bytes;   // multiple of 16
 };
+
+// One step of a CTA's range: samples [t, t + nv) of channel chan of station
+// stn (a step never straddles a block); src = its first voltage byte.
+struct TcStep {
+    int stn, chan, t, nv, ne;
+    const int8_t *src;
+    __device__ long long blk(int C) const { return (long long)stn * C + chan; }
+};
+
+// Walks a CTA's range [f, end) of the flattened index step by step, keeping
+// the current station's element count and voltage offset in registers: one
+// division at the start, none per step, a station-record load only when the
+// station changes.
+struct TcWalker {
+    const int8_t *volt;
+    const TcStation *stations;
+    int C, T;
+    long long f, end;
+    int stn, chan, t, ne;
+    long long volt_off;
+    __device__ void init(const int8_t *v, const TcStation *st, int C_, int T_, long long s0, long long s1) {
+        volt = v;
+        stations = st;
+        C = C_;
+        T = T_;
+        f = s0;
+        end = s1;
+        const long long blk = s0 / T;
+        t = (int)(s0 - blk * T);
+        stn = (int)(blk / C);
+        chan = (int)(blk - (long long)stn * C);
+        ne = 0;
+        volt_off = 0;
+        if (f < end) load();
+    }
+    __device__ void load() {
+        ne = stations[stn].ne;
+        volt_off = stations[stn].volt_off;
+    }
+    __device__ TcStep next(int sps) {
+        TcStep s;
+        s.stn = stn;
+        s.chan = chan;
+        s.t = t;
+        s.nv = (int)min((long long)min(sps, T - t), end - f);
+        s.ne = ne;
+        s.src = volt + volt_off + ((long long)chan * T + t) * 4ll * ne;
+        f += s.nv;
+        t += s.nv;
+        if (t == T) {
+            t = 0;
+            if (++chan == C) {
+                chan = 0;
+                ++stn;
+                if (f < end) load();
+            }
+        }
+        return s;
+    }
+};
+
+// Start of a step's voltages rounded down to 16 bytes when the layout has
+// guard bytes (delta = bytes skipped).
+__device__ __forceinline__ const int8_t *tc_aligned_src(const int8_t *src, int guard, uint32_t &delta) {
+    delta = guard ? (uint32_t)((uintptr_t)src & 15u) : 0u;
+    return src - delta;
+}
+
+// Steps of size `sps` in the range [s0, s1): whole blocks of T samples.
+__device__ __forceinline__ int tc_count_steps(long long s0, long long s1, int T, int sps) {
+    int n = 0;
+    for (long long f = s0; f < s1;) {
+        const long long lim = min((f / T + 1) * (long long)T, s1);
+        n += (int)((lim - f + sps - 1) / sps);
+        f = lim;
+    }
+    return n;
+}
 
 // Gather table of the gridding step.  The non-empty cells of the kernel's
 // bounding box are dealt into tiles of 32 (one per warp lane), sorted by
@@ -87,7 +169,10 @@ struct TcLaunch {
     int C, T;
     int direct, accumulate, guard;
     float *partials;
+    int no_attr;            // 1: the kernel's shared-memory attribute is already set
 };
+// Raises the kernel's dynamic shared-memory limit to the device's.
+hai_status epic_tc_set_attr(hai_ctx *ctx, int N);
 hai_status epic_tc_run(hai_ctx *ctx, int N, const TcLaunch &l, cudaStream_t st);
 size_t epic_tc_smem(hai_ctx *ctx, int N, int ne_max, uint32_t table_max);
 // Stage-1 operand strides of the gather table for grid side N.
@@ -95,11 +180,12 @@ void epic_tc_a1_strides(int N, uint32_t &k_stride, uint32_t &mn_stride);
 // CTAs that image one channel together (1, or 4 for N = 128).
 int epic_tc_group(int N);
 hai_status epic_tc128_run(hai_ctx *ctx, const TcLaunch &l, cudaStream_t st);
+hai_status epic_tc128_set_attr(hai_ctx *ctx);
 size_t epic_tc128_smem(int ne_max, uint32_t table_max);
 // Per-rank gather blob of one station for the N = 128 kernel;
 // max_rank_bytes = the largest rank table (what a CTA keeps in shared memory).
 void epic_tc128_build_blob(int box_w, int box_h, const std::vector<int32_t> &cstart,
                            const std::vector<int32_t> &elem, const std::vector<float2> &w,
-                           std::vector<uint8_t> &out, uint32_t &max_rank_bytes);
+                           std::vector<uint8_t> &out, uint32_t &max_rank_bytes, long long &max_rank_entries);
 // Clusters of the N = 128 kernel resident at once (0 if it cannot run).
 int epic_tc128_max_groups(hai_ctx *ctx, int ne_max, uint32_t table_max);

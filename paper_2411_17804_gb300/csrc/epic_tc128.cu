@@ -16,11 +16,12 @@
 // Nothing is computed twice except the stage-1 input: every CTA needs the
 // whole gridded field G.  The box (<= 64 rows) is cut into eight 8-row
 // groups, dealt to the four CTAs to balance their gather entries; each CTA
-// grids its groups into its own copy of G and sends them to the three others
-// with shared-to-shared bulk copies that complete on the receiver's
-// mbarrier.  The receiver's MMA warp reports the end of its stage-1 MMAs to
-// every CTA of the cluster (multicast commit), which frees that G buffer for
-// the next-but-one step.
+// grids its groups and every lane stores its cell straight into all four
+// CTAs' copies of G (distributed shared memory), after which one thread per
+// CTA arrives, with cluster-scope release, on every CTA's barrier of that
+// buffer.  Each CTA's MMA warp reports the end of its stage-1 MMAs to every
+// CTA of the cluster (multicast commit), which frees that G buffer for the
+// next-but-one step.  Only a group's owner ever writes its rows, in any copy.
 //
 // Roles as in the N = 32/64 kernel: warps 0-6 front (voltages, gridding,
 // warps 0-3 also move stage-1 results from TMEM into operand B2), warp 7 TMA
@@ -90,27 +91,7 @@ struct Params {
     unsigned *status;
 };
 
-struct Step {
-    long long blk;
-    int t;
-};
-
 __device__ __forceinline__ void bar_front() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
-
-__device__ __forceinline__ const int8_t *step_src(const Params &p, const TcStation &st, const Step &s,
-                                                  uint32_t &delta) {
-    const long long c = s.blk % p.C;
-    const int8_t *src = p.volt + st.volt_off + ((c * p.T + s.t) * 4ll * st.ne);
-    delta = p.guard ? (uint32_t)((uintptr_t)src & 15u) : 0u;
-    return src - delta;
-}
-
-__device__ __forceinline__ Step step_at(long long f, int T) {
-    Step s;
-    s.blk = f / T;
-    s.t = (int)(f - s.blk * T);
-    return s;
-}
 
 __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) epic_tc128_kernel(const Params p) {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -138,7 +119,7 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
     if (tid == 0) {
         for (int s = 0; s < kStages; s++) tc::mbar_init(&mb_v[s], 1);
         for (int b = 0; b < 2; b++) {
-            tc::mbar_init(&mb_a1[b], 1);
+            tc::mbar_init(&mb_a1[b], kRanks);
             tc::mbar_init(&mb_a1free[b], kRanks);
             tc::mbar_init(&mb_d1[b], 1);
             tc::mbar_init(&mb_full[b], 1);
@@ -162,9 +143,13 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
 
     if (warp < kMmaWarp) {
         // ================================================================ front
+        uint32_t peer_a1[kRanks];              // cluster addresses of every CTA's G buffers
+#pragma unroll
+        for (int r = 0; r < kRanks; r++) peer_a1[r] = tc::peer_addr(tc::smem_u32(sA1), (uint32_t)r);
         int cur_station = -1, ne = 0, ntile = 0;
         int a1_st0 = -1, a1_st1 = -1;          // station whose cells buffer 0 / 1 holds
-        uint32_t own_mask = 0, incoming = 0;
+        uint32_t own_mask = 0;
+        bool dead = false;                     // a wait of this thread gave up: signal nothing more
         const uint32_t *s_cell = nullptr;
         const int32_t *s_base = nullptr;
         const float2 *s_w = nullptr;
@@ -189,23 +174,26 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
                 own_mask = 0;
                 for (int g = 0; g < 8; g++)
                     if (hd->owner[g] == rank) own_mask |= 1u << g;
-                incoming = (uint32_t)(8 - __popc(own_mask)) * 2u * kGroupBytes;
                 cur_station = stn;
             }
-            if ((b ? a1_st1 : a1_st0) != stn) {     // own row groups of buffer b
-                uint8_t *A = sA1 + b * kA1Bytes;
-                for (int k = tid; k < (int)(16 * kGroupBytes / 16); k += kFront) {
-                    const int grp = (k * 16) / kGroupBytes;     // 0..15: pol * 8 + group
-                    if (own_mask & (1u << (grp & 7))) reinterpret_cast<int4 *>(A)[k] = make_int4(0, 0, 0, 0);
-                }
+            if ((b ? a1_st1 : a1_st0) != stn) {     // own row groups of buffer b, in every copy
+                const uint32_t off_b = (uint32_t)b * kA1Bytes;
+#pragma unroll
+                for (int r = 0; r < kRanks; r++)
+                    for (int k = tid; k < (int)(16 * kGroupBytes / 16); k += kFront) {
+                        const uint32_t byte = (uint32_t)k * 16u;
+                        const int grp = byte / kGroupBytes;      // 0..15: pol * 8 + group
+                        if (own_mask & (1u << (grp & 7)))
+                            tc::st_cluster_v4(peer_a1[r] + off_b + byte, make_uint4(0, 0, 0, 0));
+                    }
                 (b ? a1_st1 : a1_st0) = stn;
             }
             bar_front();
         };
-        auto stage_volt = [&](const Step &s, int i) {
+        auto stage_volt = [&](const TcStep &s, int i) {
             const int8_t *V;
             uint32_t delta;
-            const int8_t *src = step_src(p, p.stations[cur_station], s, delta);
+            const int8_t *src = tc_aligned_src(s.src, p.guard, delta);
             if (p.use_tma) {
                 tc::mbar_wait(&mb_v[i % kStages], (uint32_t)((i / kStages) & 1), p.status);
                 V = sV + (i % kStages) * p.vstage + delta;
@@ -224,7 +212,6 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
             bar_front();
         };
         auto grid_step = [&](int i) {
-            uint8_t *A = sA1 + (i & 1) * kA1Bytes;
             const uint2 *E = sE + (size_t)(i & 1) * ((p.ne_max + 1) & ~1);
             for (int t = warp; t < ntile; t += kMmaWarp) {
                 float2 g0 = make_float2(0.f, 0.f), g1 = g0;
@@ -248,30 +235,22 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
                 }
                 const uint32_t off = s_cell[t * 32 + lane];
                 if (off != 0xffffffffu) {
-                    *reinterpret_cast<uint32_t *>(A + off) = tc::pack_half2(g0.x, g0.y);
-                    *reinterpret_cast<uint32_t *>(A + off + kPolBytes) = tc::pack_half2(g1.x, g1.y);
+                    const uint32_t v0 = tc::pack_half2(g0.x, g0.y), v1 = tc::pack_half2(g1.x, g1.y);
+                    const uint32_t o = (uint32_t)(i & 1) * kA1Bytes + off;
+#pragma unroll
+                    for (int r = 0; r < kRanks; r++) {
+                        tc::st_cluster(peer_a1[r] + o, v0);
+                        tc::st_cluster(peer_a1[r] + o + kPolBytes, v1);
+                    }
                 }
             }
         };
-        // own row groups of G -> the three other CTAs; then this CTA's own
-        // arrival, expecting the bytes the others send
-        auto send = [&](int i) {
-            const int b = i & 1;
-            uint8_t *A = sA1 + b * kA1Bytes;
-            const bool dead = (*reinterpret_cast<volatile unsigned *>(p.status) & HAI_DEV_TIMEOUT) != 0;
-            if (!dead)
-                for (uint32_t peer = 0; peer < kRanks; peer++) {
-                    if (peer == rank) continue;
-                    const uint32_t mb = tc::peer_addr(tc::smem_u32(&mb_a1[b]), peer);
-                    for (int g = 0; g < 8; g++) {
-                        if (!(own_mask & (1u << g))) continue;
-                        for (int pol = 0; pol < 2; pol++) {
-                            const uint32_t off = (uint32_t)pol * kPolBytes + (uint32_t)g * kGroupBytes;
-                            tc::bulk_s2peer(tc::peer_addr(tc::smem_u32(A + off), peer), A + off, kGroupBytes, mb);
-                        }
-                    }
-                }
-            tc::mbar_arrive_expect_tx(&mb_a1[b], incoming);
+        // this CTA's rows of G are in every copy: arrive on every CTA's barrier
+        auto signal = [&](int i) {
+            if (dead) return;
+            const uint32_t mb = tc::smem_u32(&mb_a1[i & 1]);
+#pragma unroll
+            for (int r = 0; r < kRanks; r++) tc::mbar_arrive_cluster(tc::peer_addr(mb, (uint32_t)r));
         };
         // warps 0-3: D1 row (pol, y) -> column (y, re/im) of B2 for the
         // rows (pol, out re/im, l_x): out re <- (H_r, -H_i), out im <- (H_i, H_r)
@@ -309,18 +288,21 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
                 }
             }
         };
+        TcWalker wk;
+        wk.init(p.volt, p.stations, p.C, p.T, s0, s1);
         for (int i = -1; i < nsteps; i++) {
             if (i + 1 < nsteps) {
                 const int j = i + 1, b = j & 1;
-                const Step s = step_at(s0 + j, p.T);
+                const TcStep s = wk.next(1);
                 // G buffer b was last read by the stage-1 MMAs of step j - 2 in every CTA
-                if (j >= 2) tc::mbar_wait_cluster(&mb_a1free[b], (uint32_t)(((j >> 1) - 1) & 1), p.status);
-                prepare((int)(s.blk / p.C), b);
+                if (j >= 2 && !tc::mbar_wait_cluster(&mb_a1free[b], (uint32_t)(((j >> 1) - 1) & 1), p.status))
+                    dead = true;
+                prepare(s.stn, b);
                 stage_volt(s, j);
                 grid_step(j);
-                tc::fence_proxy_async();
+                tc::fence_proxy_async_cluster();
                 bar_front();
-                if (tid == 0) send(j);
+                if (tid == 0) signal(j);
             }
             if (i >= 0 && warp < 4) {
                 tc::mbar_wait(&mb_d1[i & 1], (uint32_t)((i >> 1) & 1), p.status);
@@ -337,13 +319,14 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
         if (lane == 0) {
             const uint32_t b1 = tc::smem_u32(sB1), a2 = tc::smem_u32(sA2), b2 = tc::smem_u32(sB2);
             int n_loaded = 0;
+            TcWalker ld;
+            ld.init(p.volt, p.stations, p.C, p.T, s0, s1);
             auto issue_load = [&]() {
                 if (n_loaded >= nsteps || !p.use_tma) return;
-                const Step s = step_at(s0 + n_loaded, p.T);
-                const TcStation &st = p.stations[s.blk / p.C];
+                const TcStep s = ld.next(1);
                 uint32_t delta;
-                const int8_t *src = step_src(p, st, s, delta);
-                const uint32_t bytes = (delta + 4u * st.ne + 15u) & ~15u;
+                const int8_t *src = tc_aligned_src(s.src, p.guard, delta);
+                const uint32_t bytes = (delta + 4u * s.ne + 15u) & ~15u;
                 const int sg = n_loaded % kStages;
                 tc::mbar_arrive_expect_tx(&mb_v[sg], bytes);
                 tc::bulk_g2s(sV + sg * p.vstage, src, bytes, &mb_v[sg]);
@@ -392,8 +375,7 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
         for (int t = 0; t < 16; t++) xx[t] = yy[t] = xr[t] = xi[t] = 0.f;
         int seg = 0;
         long long cur_blk = -1;
-        auto flush = [&](long long blk, int sgm) {
-            const int stn = (int)(blk / p.C), c = (int)(blk % p.C);
+        auto flush = [&](int stn, int c, int sgm) {
             float *dst = p.direct ? p.img + p.stations[stn].img_off + (size_t)c * 4 * kNN
                                   : p.partials + ((size_t)group * 2 + sgm) * 4 * kNN;
             auto put = [&](int pl, float (&a)[16]) {
@@ -418,34 +400,40 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
 #pragma unroll
             for (int t = 0; t < 16; t++) xx[t] = yy[t] = xr[t] = xi[t] = 0.f;
         };
+        TcWalker wk;
+        wk.init(p.volt, p.stations, p.C, p.T, s0, s1);
+        int cur_stn = 0, cur_chan = 0;
         for (int k = 0; k < nsteps; k++) {
-            const Step s = step_at(s0 + k, p.T);
-            if (s.blk != cur_blk) {
+            const TcStep s = wk.next(1);
+            const long long blk = s.blk(p.C);
+            if (blk != cur_blk) {
                 if (cur_blk >= 0) {
-                    flush(cur_blk, seg);
+                    flush(cur_stn, cur_chan, seg);
                     seg++;
                 }
-                cur_blk = s.blk;
+                cur_blk = blk;
+                cur_stn = s.stn;
+                cur_chan = s.chan;
             }
             const int slot = k & 1;
             tc::mbar_wait(&mb_full[slot], (uint32_t)((k >> 1) & 1), p.status);
             tc::fence_after();
             const uint32_t col = kD2Col + (uint32_t)slot * 128u + 16u * h;
 #pragma unroll
-            for (int half = 0; half < 2; half++) {
-                uint32_t ar[8], ai[8], br[8], bi[8];
-                tc::tmem_ld8(tmem + lane_base + col + 8 * half, ar);         // X re
-                tc::tmem_ld8(tmem + lane_base + col + 8 * half + 32, ai);    // X im
-                tc::tmem_ld8(tmem + lane_base + col + 8 * half + 64, br);    // Y re
-                tc::tmem_ld8(tmem + lane_base + col + 8 * half + 96, bi);    // Y im
+            for (int qt = 0; qt < 4; qt++) {                // 4 columns l_x at a time
+                uint32_t ar[4], ai[4], br[4], bi[4];
+                tc::tmem_ld4(tmem + lane_base + col + 4 * qt, ar);         // X re
+                tc::tmem_ld4(tmem + lane_base + col + 4 * qt + 32, ai);    // X im
+                tc::tmem_ld4(tmem + lane_base + col + 4 * qt + 64, br);    // Y re
+                tc::tmem_ld4(tmem + lane_base + col + 4 * qt + 96, bi);    // Y im
                 tc::tmem_wait_ld();
-                if (half == 1) {
+                if (qt == 3) {
                     tc::fence_before();
                     tc::mbar_arrive(&mb_empty[slot]);
                 }
 #pragma unroll
-                for (int e = 0; e < 8; e++) {
-                    const int t = 8 * half + e;
+                for (int e = 0; e < 4; e++) {
+                    const int t = 4 * qt + e;
                     const float a_r = __uint_as_float(ar[e]), a_i = __uint_as_float(ai[e]);
                     const float b_r = __uint_as_float(br[e]), b_i = __uint_as_float(bi[e]);
                     xx[t] = fmaf(a_r, a_r, fmaf(a_i, a_i, xx[t]));
@@ -455,7 +443,7 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
                 }
             }
         }
-        if (cur_blk >= 0) flush(cur_blk, seg);
+        if (cur_blk >= 0) flush(cur_stn, cur_chan, seg);
     }
 
     tc::fence_before();
@@ -478,7 +466,7 @@ size_t epic_tc128_smem(int ne_max, uint32_t table_max) {
 // rank), then one gather table per rank with the cells of its groups.
 void epic_tc128_build_blob(int box_w, int box_h, const std::vector<int32_t> &cstart,
                            const std::vector<int32_t> &elem, const std::vector<float2> &w,
-                           std::vector<uint8_t> &out, uint32_t &max_rank_bytes) {
+                           std::vector<uint8_t> &out, uint32_t &max_rank_bytes, long long &max_rank_entries) {
     long long cnt[8] = {0};
     for (int y = 0; y < box_h; y++)
         for (int x = 0; x < box_w; x++) cnt[y / 8] += cstart[y * box_w + x + 1] - cstart[y * box_w + x];
@@ -501,6 +489,7 @@ void epic_tc128_build_blob(int box_w, int box_h, const std::vector<int32_t> &cst
     memcpy(hd.owner, owner, 8);
     std::vector<std::vector<uint8_t>> tabs(kRanks);
     max_rank_bytes = 0;
+    max_rank_entries = 0;
     for (int r = 0; r < kRanks; r++) {
         // CSR restricted to the rank's rows (other cells empty)
         std::vector<int32_t> cs(cstart.size(), 0);
@@ -519,6 +508,7 @@ void epic_tc128_build_blob(int box_w, int box_h, const std::vector<int32_t> &cst
         epic_tc_build_gather(box_w, box_h, cs, el, ww, kKs, kMNs, tabs[r], hd.ntile[r], hd.nent[r]);
         hd.bytes[r] = (uint32_t)tabs[r].size();
         max_rank_bytes = std::max(max_rank_bytes, hd.bytes[r]);
+        max_rank_entries = std::max<long long>(max_rank_entries, hd.nent[r]);
     }
     uint32_t off = sizeof(Blob128);
     for (int r = 0; r < kRanks; r++) {
@@ -532,11 +522,14 @@ void epic_tc128_build_blob(int box_w, int box_h, const std::vector<int32_t> &cst
 
 hai_status epic_tc128_run(hai_ctx *ctx, const TcLaunch &l, cudaStream_t st) {
     const size_t smem = epic_tc128_smem(l.ne_max, l.table_max);
-    if (smem > (size_t)ctx->smem_optin)
+    if (smem + kStaticSmem > (size_t)ctx->smem_optin)
         return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16 (N = 128): shared memory need exceeds the device limit");
     const void *dft = epic_tc_dft(ctx, 128);
     if (!dft) return hai_fail(HAI_ERR_INVALID_ARG, "epic fp16 (N = 128): DFT operand not prepared");
-    HAI_CUDA_TRY(cudaFuncSetAttribute(epic_tc128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (!l.no_attr) {
+        const hai_status s = epic_tc128_set_attr(ctx);
+        if (s != HAI_OK) return s;
+    }
     Params p;
     p.volt = l.volt;
     p.img = l.img;
@@ -563,13 +556,19 @@ hai_status epic_tc128_run(hai_ctx *ctx, const TcLaunch &l, cudaStream_t st) {
     return HAI_OK;
 }
 
+hai_status epic_tc128_set_attr(hai_ctx *ctx) {
+    cudaFuncAttributes a;
+    HAI_CUDA_TRY(cudaFuncGetAttributes(&a, epic_tc128_kernel));
+    HAI_CUDA_TRY(cudaFuncSetAttribute(epic_tc128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      ctx->smem_optin - (int)a.sharedSizeBytes));
+    return HAI_OK;
+}
+
 // Clusters of four of this kernel that can be resident at once.
 int epic_tc128_max_groups(hai_ctx *ctx, int ne_max, uint32_t table_max) {
     const size_t smem = epic_tc128_smem(ne_max, table_max);
-    if (smem > (size_t)ctx->smem_optin) return 0;
-    if (cudaFuncSetAttribute(epic_tc128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return 0;
+    if (smem + kStaticSmem > (size_t)ctx->smem_optin) return 0;
+    if (epic_tc128_set_attr(ctx) != HAI_OK) return 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kRanks * 64, 1, 1);
     cfg.blockDim = dim3(kThreads, 1, 1);

@@ -128,7 +128,7 @@ extern "C" hai_status hai_profile_enable(hai_ctx *ctx, int enable, int max_recor
 }
 
 int prof_begin(hai_ctx *ctx, cudaStream_t st) {
-    if (!ctx->prof_on || 2 * (ctx->prof_used + 1) > ctx->prof_ev.size()) return -1;
+    if (!ctx->prof_on || ctx->capturing || 2 * (ctx->prof_used + 1) > ctx->prof_ev.size()) return -1;
     int idx = (int)ctx->prof_used++;
     cudaEventRecord(ctx->prof_ev[2 * idx], st);
     return idx;
@@ -272,8 +272,10 @@ extern "C" hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *d, 
         std::vector<uint8_t> tab;
         TcStation rec = {};
         uint32_t shared_bytes = 0;
-        epic_tc_station_table(n, L->box_w, L->box_h, count, elem, w, tab, rec.ntile, rec.nent, shared_bytes);
+        epic_tc_station_table(n, L->box_w, L->box_h, count, elem, w, tab, rec.ntile, rec.nent, shared_bytes,
+                              L->tc_entries);
         L->tc_tables_bytes = shared_bytes;
+        L->tc_blob_bytes = tab.size();
         e = cudaMalloc(&L->d_tc_tables, tab.size());
         if (e == cudaSuccess) e = cudaMemcpy(L->d_tc_tables, tab.data(), tab.size(), cudaMemcpyHostToDevice);
         rec.table = static_cast<const uint8_t *>(L->d_tc_tables);
@@ -282,6 +284,9 @@ extern "C" hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *d, 
         if (e == cudaSuccess) e = cudaMalloc(&L->d_tc_station, sizeof(TcStation));
         if (e == cudaSuccess) e = cudaMemcpy(L->d_tc_station, &rec, sizeof(TcStation), cudaMemcpyHostToDevice);
         if (e == cudaSuccess && epic_tc_dft_prepare(ctx, n) != HAI_OK) e = cudaErrorMemoryAllocation;
+        L->tc_groups = n == 128 ? std::min(ctx->num_sms / 4, epic_tc128_max_groups(ctx, ne, shared_bytes))
+                                : ctx->num_sms;
+        if (L->tc_groups <= 0) L->tc_groups = 1;
     }
     if (e != cudaSuccess) {
         layout_free(L);
@@ -307,6 +312,9 @@ extern "C" hai_status hai_layout_box(const hai_layout *L, int *box) {
 // ------------------------------------------------------------------ EPIC
 EpicSplit epic_make_split(int C, int T, int target_ctas) {
     EpicSplit sp;
+    // one CTA per channel once the channels fill the CTAs; below that a time
+    // split whose ranges (len <= T) touch at most two channels each, which
+    // is what the two partial slots per CTA hold
     if (C >= target_ctas) {
         sp.direct = 1;
         sp.n_cta = C;

@@ -23,6 +23,7 @@ struct hai_ctx {
     size_t prof_used = 0;               // pairs recorded
     long long prof_launches = 0;        // all kernels launched
     void *d_dft[3] = {nullptr, nullptr, nullptr};   // tensor-core DFT operands, N = 32, 64, 128
+    int capturing = 0;                  // a plan is capturing a graph: no profiling events
 };
 
 // Profiling helpers: prof_begin returns the pair index or -1.
@@ -50,7 +51,10 @@ struct hai_layout {
     // tensor-core path: gather table (or, for N = 128, the per-rank blob),
     // its size in shared memory, and the one-station record the kernels read
     void *d_tc_tables = nullptr;
-    size_t tc_tables_bytes = 0;
+    size_t tc_tables_bytes = 0;         // kept in shared memory by one CTA
+    size_t tc_blob_bytes = 0;           // whole device table
+    long long tc_entries = 0;           // gather entries one CTA runs per sample step
+    int tc_groups = 0;                  // CTAs (N = 128: 4-CTA clusters) resident at once
     void *d_tc_station = nullptr;
 };
 
@@ -89,6 +93,7 @@ bool epic_tc_supported(const hai_layout *L);
 // shared_bytes = what the kernel keeps in shared memory.
 void epic_tc_station_table(int grid_n, int box_w, int box_h, const std::vector<int32_t> &cstart,
                            const std::vector<int32_t> &elem, const std::vector<float2> &w,
-                           std::vector<uint8_t> &out, int &ntile, int &nent, uint32_t &shared_bytes);
+                           std::vector<uint8_t> &out, int &ntile, int &nent, uint32_t &shared_bytes,
+                           long long &entries);
 hai_status epic_reduce_launch(const hai_layout *L, const EpicSplit &sp, int C, int T, float *img,
                               int accumulate, cudaStream_t st);

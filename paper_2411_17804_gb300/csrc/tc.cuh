@@ -83,6 +83,13 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
+// 32 lanes x 4 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
+
 // 32 lanes x 8 consecutive 32-bit columns.
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -144,25 +151,29 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *m, uint32_t parity) 
     return done;
 }
 
-// Bounded wait for the phase with the given parity to complete.  Polls with
-// an exponential nanosleep back-off (32 ns .. 512 ns) so waiting warps leave
-// the issue slots to working ones.  Gives up after ~2^32 SM cycles (about two
-// seconds), flags HAI_DEV_TIMEOUT in the device status word and returns
-// false; the caller carries on so that every thread still reaches every
-// barrier and the kernel ends.
+// Bounded wait for the phase with the given parity to complete.  Polls
+// try_wait (which may suspend the thread in hardware until the phase flips)
+// and reads the device status word only once every 2^14 cycles of waiting,
+// so a wait that ends within a few microseconds never leaves the SM.  Gives
+// up after ~2^32 SM cycles (about two seconds), or at the next check once
+// another wait of the launch has given up, flagging HAI_DEV_TIMEOUT in the
+// status word and returning false; the caller carries on so that every
+// thread still reaches every barrier and the kernel ends.
 __device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity, unsigned *status) {
     if (mbar_try_wait(m, parity)) return true;
-    // once any wait of the launch has given up, later waits give up at once
-    if (*reinterpret_cast<volatile unsigned *>(status) & HAI_DEV_TIMEOUT) return false;
     const long long t0 = clock64();
-    unsigned ns = 32;
+    long long next_check = 1ll << 14;
     for (;;) {
-        __nanosleep(ns);
         if (mbar_try_wait(m, parity)) return true;
-        if (ns < 512) ns <<= 1;
-        if (clock64() - t0 > (1ll << 32)) {
-            atomicOr(status, (unsigned)HAI_DEV_TIMEOUT);
-            return false;
+        const long long dt = clock64() - t0;
+        if (dt > next_check) {
+            if (*reinterpret_cast<volatile unsigned *>(status) & HAI_DEV_TIMEOUT) return false;
+            if (dt > (1ll << 32)) {
+                atomicOr(status, (unsigned)HAI_DEV_TIMEOUT);
+                return false;
+            }
+            next_check = dt + (1ll << 14);
+            __nanosleep(128);
         }
     }
 }
@@ -197,6 +208,28 @@ __device__ __forceinline__ uint32_t peer_addr(uint32_t local, uint32_t rank) {
     return r;
 }
 
+// 32-bit and 128-bit stores to shared memory of any CTA of the cluster
+// (cluster address from peer_addr).
+__device__ __forceinline__ void st_cluster(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint4 v) {
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+
+// Make this thread's generic-proxy writes to cluster shared memory visible
+// to the async proxy (the tensor cores of the CTAs that own it).
+__device__ __forceinline__ void fence_proxy_async_cluster() {
+    asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+}
+
+// Arrive (release at cluster scope) on an mbarrier of any CTA of the cluster.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t mbar_cluster) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(mbar_cluster) : "memory");
+}
+
 // Local shared -> shared of another CTA of the cluster, `bytes` (multiple of
 // 16, 16-byte aligned), completing on that CTA's mbarrier (cluster address).
 __device__ __forceinline__ void bulk_s2peer(uint32_t dst_cluster, const void *src, uint32_t bytes,
@@ -218,30 +251,35 @@ __device__ __forceinline__ void mma_commit_multicast(uint64_t *mbar, uint16_t ma
         : "memory");
 }
 
-// try_wait with cluster-scope acquire, for phases completed by other CTAs.
+// try_wait with cluster-scope acquire, for phases completed by other CTAs;
+// no suspend-time hint, so the poll returns after the hardware's own short
+// wait rather than sleeping through a remote completion.
 __device__ __forceinline__ uint32_t mbar_try_wait_cluster(uint64_t *m, uint32_t parity) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(smem_u32(m)), "r"(parity), "r"(20000u)
+        : "r"(smem_u32(m)), "r"(parity)
         : "memory");
     return done;
 }
 
 __device__ __forceinline__ bool mbar_wait_cluster(uint64_t *m, uint32_t parity, unsigned *status) {
     if (mbar_try_wait_cluster(m, parity)) return true;
-    if (*reinterpret_cast<volatile unsigned *>(status) & HAI_DEV_TIMEOUT) return false;
     const long long t0 = clock64();
-    unsigned ns = 32;
+    long long next_check = 1ll << 14;
     for (;;) {
-        __nanosleep(ns);
         if (mbar_try_wait_cluster(m, parity)) return true;
-        if (ns < 512) ns <<= 1;
-        if (clock64() - t0 > (1ll << 32)) {
-            atomicOr(status, (unsigned)HAI_DEV_TIMEOUT);
-            return false;
+        const long long dt = clock64() - t0;
+        if (dt > next_check) {
+            if (*reinterpret_cast<volatile unsigned *>(status) & HAI_DEV_TIMEOUT) return false;
+            if (dt > (1ll << 32)) {
+                atomicOr(status, (unsigned)HAI_DEV_TIMEOUT);
+                return false;
+            }
+            next_check = dt + (1ll << 14);
+            __nanosleep(128);
         }
     }
 }

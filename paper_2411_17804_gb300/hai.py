@@ -60,6 +60,13 @@ def _declare(L):
     L.hai_beamform.argtypes = [_vp, _vp, _vp, _int, _int, _int, _int, _int, _int, _int, _vp, _vp, _vp]
     L.hai_epic_image_fp32_static.argtypes = [_int, ctypes.POINTER(_LayoutDesc), _vp, _int, _int, _vp, _int,
                                              _vp]
+    L.hai_plan_create.argtypes = [_vp, ctypes.POINTER(_vp), _int, _int, _int, _int, ctypes.POINTER(_vp)]
+    L.hai_plan_destroy.argtypes = [_vp]
+    L.hai_plan_destroy.restype = None
+    L.hai_plan_layout.argtypes = [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    L.hai_plan_run.argtypes = [_vp, _vp, _vp, _vp]
+    L.hai_plan_autotune.argtypes = [_vp, _vp, _vp, _int, _vp]
+    L.hai_plan_schedule.argtypes = [_vp, ctypes.POINTER(_int), _vp, _vp, _vp]
     L.hai_profile_enable.argtypes = [_vp, _int, _int]
     L.hai_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
@@ -226,3 +233,63 @@ def hai_beamform(ctx, volt, w, S: int, C: int, T: int, K: int, N: int, P: int, r
     sp = _dev_ptr(n_saturated, torch.int64, "n_saturated", 1) if n_saturated is not None else 0
     _check(load().hai_beamform(ctx, vp, wp, S, C, T, K, N, P, requant_shift, bp, sp, _stream(stream)),
            "hai_beamform")
+
+
+# ------------------------------------------------------------------ batched plan
+class Plan:
+    """Handle of a hai_plan with its buffer layout (host copies)."""
+
+    def __init__(self, handle, S: int):
+        self.handle = handle
+        self.S = S
+        self.volt_off = np.zeros(S, np.int64)
+        self.img_off = np.zeros(S, np.int64)
+        vb, nf = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().hai_plan_layout(handle, self.volt_off.ctypes.data, self.img_off.ctypes.data,
+                                      ctypes.byref(vb), ctypes.byref(nf)), "hai_plan_layout")
+        self.volt_bytes = vb.value
+        self.img_floats = nf.value
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+
+def hai_plan_create(ctx, layouts, C: int, T: int, prec: int = HAI_PREC_FP16) -> Plan:
+    arr = (_vp * len(layouts))(*[ly.handle for ly in layouts])
+    h = _vp()
+    _check(load().hai_plan_create(ctx, arr, len(layouts), C, T, prec, ctypes.byref(h)), "hai_plan_create")
+    return Plan(h, len(layouts))
+
+
+def hai_plan_destroy(plan: Plan):
+    load().hai_plan_destroy(plan.handle)
+
+
+def hai_plan_layout(plan: Plan):
+    """(volt_off[S] bytes, img_off[S] floats, volt_bytes, img_floats)."""
+    return plan.volt_off, plan.img_off, plan.volt_bytes, plan.img_floats
+
+
+def hai_plan_run(plan: Plan, volt, img, stream=None):
+    import torch
+    vp = _dev_ptr(volt, torch.int8, "volt", plan.volt_bytes)
+    ip = _dev_ptr(img, torch.float32, "img", plan.img_floats)
+    _check(load().hai_plan_run(plan.handle, vp, ip, _stream(stream)), "hai_plan_run")
+
+
+def hai_plan_autotune(plan: Plan, volt, img, rounds: int = 2, stream=None):
+    import torch
+    vp = _dev_ptr(volt, torch.int8, "volt", plan.volt_bytes)
+    ip = _dev_ptr(img, torch.float32, "img", plan.img_floats)
+    _check(load().hai_plan_autotune(plan.handle, vp, ip, rounds, _stream(stream)), "hai_plan_autotune")
+
+
+def hai_plan_schedule(plan: Plan):
+    """[(grid side, CTAs, measured ms alone)] per grid group."""
+    n = _int()
+    g = (_int * 3)()
+    c = (_int * 3)()
+    m = (ctypes.c_double * 3)()
+    _check(load().hai_plan_schedule(plan.handle, ctypes.byref(n), g, c, m), "hai_plan_schedule")
+    return [(g[k], c[k], m[k]) for k in range(n.value)]
