@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
         int a1_st0 = -1, a1_st1 = -1;          // station whose cells buffer 0 / 1 holds
         int ntile = 0;
         const uint32_t *s_cell = nullptr;
-        const int32_t *s_base = nullptr;
+        const int32_t *s_base = nullptr, *s_warp = nullptr;
         const float2 *s_w = nullptr;
         const uint16_t *s_e = nullptr;
 
@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
                 const GatherLayout gl = gather_layout(st.ntile, st.nent);
                 s_cell = reinterpret_cast<const uint32_t *>(sT + gl.off_cell);
                 s_base = reinterpret_cast<const int32_t *>(sT + gl.off_base);
+                s_warp = reinterpret_cast<const int32_t *>(sT + gl.off_warp);
                 s_w = reinterpret_cast<const float2 *>(sT + gl.off_w);
                 s_e = reinterpret_cast<const uint16_t *>(sT + gl.off_e);
                 ntile = st.ntile;
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
         auto grid_step = [&](int i) {
             uint8_t *A = sA1 + (i & 1) * G::kA1Bytes;
             const uint4 *E = sE + (size_t)(i & 1) * p.ne_max * G::kU;
-            for (int t = warp; t < ntile; t += kMmaWarp) {
+            for (int t = s_warp[warp]; t < s_warp[warp + 1]; t++) {
                 float2 g[G::kFields];
 #pragma unroll
                 for (int f = 0; f < G::kFields; f++) g[f] = make_float2(0.f, 0.f);
@@ -630,7 +631,7 @@ const void *epic_tc_dft(hai_ctx *ctx, int N) {
 
 void epic_tc_build_gather(int box_w, int box_h, const std::vector<int32_t> &cstart,
                           const std::vector<int32_t> &elem, const std::vector<float2> &w, uint32_t k_stride,
-                          uint32_t mn_stride, std::vector<uint8_t> &out, int &ntile, int &nent) {
+                          uint32_t mn_stride, std::vector<uint8_t> &out, int &ntile, int &nent, int n_warps) {
     std::vector<int> cells;
     for (int y = 0; y < box_h; y++)
         for (int x = 0; x < box_w; x++)
@@ -642,29 +643,47 @@ void epic_tc_build_gather(int box_w, int box_h, const std::vector<int32_t> &csta
         return a1off(a) < a1off(b);
     });
     ntile = ((int)cells.size() + 31) / 32;
-    std::vector<int> base(ntile + 1, 0);
-    for (int t = 0; t < ntile; t++) {
-        int slots = 0;
-        for (int l = 0; l < 32 && t * 32 + l < (int)cells.size(); l++) slots = std::max(slots, count(cells[t * 32 + l]));
-        base[t + 1] = base[t] + 32 * slots;
+    // tiles in cell order, then dealt to the gridding warps longest-first
+    std::vector<int> slots(ntile, 0);
+    for (int t = 0; t < ntile; t++)
+        for (int l = 0; l < 32 && t * 32 + l < (int)cells.size(); l++) slots[t] = std::max(slots[t], count(cells[t * 32 + l]));
+    std::vector<int> by_cost(ntile);
+    for (int t = 0; t < ntile; t++) by_cost[t] = t;
+    std::stable_sort(by_cost.begin(), by_cost.end(), [&](int a, int b) { return slots[a] > slots[b]; });
+    std::vector<std::vector<int>> mine(kGatherWarps);
+    std::vector<int> load(n_warps, 0);
+    for (int t : by_cost) {
+        const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        mine[w].push_back(t);
+        load[w] += slots[t] + 1;
     }
+    std::vector<int> order;                  // new position -> original tile
+    std::vector<int> wrange(kGatherWarps + 1, 0);
+    for (int w = 0; w < kGatherWarps; w++) {
+        order.insert(order.end(), mine[w].begin(), mine[w].end());
+        wrange[w + 1] = (int)order.size();
+    }
+    std::vector<int> base(ntile + 1, 0);
+    for (int t = 0; t < ntile; t++) base[t + 1] = base[t] + 32 * slots[order[t]];
     nent = base[ntile];
     const GatherLayout gl = gather_layout(ntile, nent);
     out.assign(gl.bytes, 0);
     uint32_t *o_cell = reinterpret_cast<uint32_t *>(&out[gl.off_cell]);
     int32_t *o_base = reinterpret_cast<int32_t *>(&out[gl.off_base]);
+    int32_t *o_warp = reinterpret_cast<int32_t *>(&out[gl.off_warp]);
     float2 *o_w = reinterpret_cast<float2 *>(&out[gl.off_w]);
     uint16_t *o_e = reinterpret_cast<uint16_t *>(&out[gl.off_e]);
     for (int t = 0; t <= ntile; t++) o_base[t] = base[t];
+    for (int w = 0; w <= kGatherWarps; w++) o_warp[w] = wrange[w];
     for (int t = 0; t < ntile; t++)
         for (int l = 0; l < 32; l++) {
-            const int ci = t * 32 + l;
+            const int ci = order[t] * 32 + l;      // cell of lane l of the tile now at position t
             if (ci >= (int)cells.size()) {
-                o_cell[ci] = 0xffffffffu;
+                o_cell[t * 32 + l] = 0xffffffffu;
                 continue;
             }
             const int cell = cells[ci];
-            o_cell[ci] = a1off(cell);
+            o_cell[t * 32 + l] = a1off(cell);
             for (int k = 0; k < count(cell); k++) {
                 const int q = base[t] + 32 * k + l;
                 o_w[q] = w[cstart[cell] + k];                 // conj(W~) = a + ib

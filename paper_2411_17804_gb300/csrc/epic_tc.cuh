@@ -114,17 +114,22 @@ __device__ __forceinline__ int tc_count_steps(long long s0, long long s1, int T,
 //                                       stage-1 operand (field 0), or
 //                                       0xffffffff for an unused lane
 //   tile bases     int32 [ntile + 1]    first entry of each tile
+//   warp ranges    int32 [kGatherWarps + 1]  warp w grids tiles [r[w], r[w+1]);
+//                                       tiles are dealt to the warps by
+//                                       longest-first (slots + 1 per tile)
 //   (pad to 16)
 //   weights        float2 [nent]        a + ib = conj(W~)
 //   elements       uint16 [nent]
+constexpr int kGatherWarps = 7;
 struct GatherLayout {
-    uint32_t off_cell, off_base, off_w, off_e, bytes;
+    uint32_t off_cell, off_base, off_warp, off_w, off_e, bytes;
 };
 __host__ __device__ inline GatherLayout gather_layout(int ntile, int nent) {
     GatherLayout t;
     t.off_cell = 0;
     t.off_base = 4u * 32u * ntile;
-    t.off_w = (t.off_base + 4u * (ntile + 1) + 15u) & ~15u;
+    t.off_warp = t.off_base + 4u * (ntile + 1);
+    t.off_w = (t.off_warp + 4u * (kGatherWarps + 1) + 15u) & ~15u;
     t.off_e = t.off_w + 8u * nent;
     t.bytes = (t.off_e + 2u * nent + 15u) & ~15u;
     return t;
@@ -134,9 +139,11 @@ __host__ __device__ inline GatherLayout gather_layout(int ntile, int nent) {
 // the box row-major, cstart[box_w * box_h + 1]).  Cell (x, y) of the box
 // lands at byte tc::off_kmajor(y, 2 x, k_stride, mn_stride) of the stage-1
 // operand.
+// n_warps (<= kGatherWarps) of the front warps get tiles; the others none.
 void epic_tc_build_gather(int box_w, int box_h, const std::vector<int32_t> &cstart,
                           const std::vector<int32_t> &elem, const std::vector<float2> &w, uint32_t k_stride,
-                          uint32_t mn_stride, std::vector<uint8_t> &out, int &ntile, int &nent);
+                          uint32_t mn_stride, std::vector<uint8_t> &out, int &ntile, int &nent,
+                          int n_warps = kGatherWarps);
 
 // fp16 W'[j][l] = (-1)^j exp(+2 pi i l j / N) as a real matrix entry: row
 // (c_out, l), column (j, c_in) of the complex product y = W'^T x written for

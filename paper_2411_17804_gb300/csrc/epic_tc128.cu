@@ -16,12 +16,12 @@
 // Nothing is computed twice except the stage-1 input: every CTA needs the
 // whole gridded field G.  The box (<= 64 rows) is cut into eight 8-row
 // groups, dealt to the four CTAs to balance their gather entries; each CTA
-// grids its groups and every lane stores its cell straight into all four
-// CTAs' copies of G (distributed shared memory), after which one thread per
-// CTA arrives, with cluster-scope release, on every CTA's barrier of that
-// buffer.  Each CTA's MMA warp reports the end of its stage-1 MMAs to every
-// CTA of the cluster (multicast commit), which frees that G buffer for the
-// next-but-one step.  Only a group's owner ever writes its rows, in any copy.
+// grids its groups into its own copy of G, then the lanes of one warp send
+// them to the three other CTAs at once with shared-to-shared bulk copies
+// that complete on the receiver's mbarrier.  Each CTA's MMA warp reports the
+// end of its stage-1 MMAs to every CTA of the cluster (multicast commit),
+// which frees that G buffer for the next-but-one step.  Only a group's owner
+// ever writes its rows, in any copy.
 //
 // Roles as in the N = 32/64 kernel: warps 0-6 front (voltages, gridding,
 // warps 0-3 also move stage-1 results from TMEM into operand B2), warp 7 TMA
@@ -47,6 +47,7 @@ constexpr int kMmaWarp = 7;
 constexpr int kEpi = 256;
 constexpr int kStages = 4;
 constexpr int kRanks = 4;
+constexpr int kSendWarp = 6;                 // front warp that ships G rows to the peers
 constexpr uint32_t kKs = 128;                // K-major: K-group stride
 constexpr uint32_t kMNs = 16 * kKs;          // K-major, K = 128: MN-group stride (2048)
 constexpr uint32_t kGroupBytes = kMNs;       // 8 rows of a K-major operand
@@ -72,7 +73,8 @@ struct Blob128 {
     uint32_t off[kRanks], bytes[kRanks];
     int32_t ntile[kRanks], nent[kRanks];
     uint8_t owner[8];
-    uint8_t pad[56];
+    int32_t box_w, box_h;       // kernel box of the station (cells)
+    uint8_t pad[48];
 };
 static_assert(sizeof(Blob128) == 128, "blob header");
 
@@ -119,7 +121,7 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
     if (tid == 0) {
         for (int s = 0; s < kStages; s++) tc::mbar_init(&mb_v[s], 1);
         for (int b = 0; b < 2; b++) {
-            tc::mbar_init(&mb_a1[b], kRanks);
+            tc::mbar_init(&mb_a1[b], 1);
             tc::mbar_init(&mb_a1free[b], kRanks);
             tc::mbar_init(&mb_d1[b], 1);
             tc::mbar_init(&mb_full[b], 1);
@@ -143,15 +145,13 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
 
     if (warp < kMmaWarp) {
         // ================================================================ front
-        uint32_t peer_a1[kRanks];              // cluster addresses of every CTA's G buffers
-#pragma unroll
-        for (int r = 0; r < kRanks; r++) peer_a1[r] = tc::peer_addr(tc::smem_u32(sA1), (uint32_t)r);
         int cur_station = -1, ne = 0, ntile = 0;
         int a1_st0 = -1, a1_st1 = -1;          // station whose cells buffer 0 / 1 holds
-        uint32_t own_mask = 0;
-        bool dead = false;                     // a wait of this thread gave up: signal nothing more
+        uint32_t own_mask = 0, incoming = 0;
+        uint32_t box_mask = 0, copy_bytes = 0;    // groups inside the box; bytes of a group's box columns
+        bool dead = false;                     // a wait of this thread gave up: send nothing more
         const uint32_t *s_cell = nullptr;
-        const int32_t *s_base = nullptr;
+        const int32_t *s_base = nullptr, *s_warp = nullptr;
         const float2 *s_w = nullptr;
         const uint16_t *s_e = nullptr;
 
@@ -167,6 +167,7 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
                 const GatherLayout gl = gather_layout(hd->ntile[rank], hd->nent[rank]);
                 s_cell = reinterpret_cast<const uint32_t *>(sT + gl.off_cell);
                 s_base = reinterpret_cast<const int32_t *>(sT + gl.off_base);
+                s_warp = reinterpret_cast<const int32_t *>(sT + gl.off_warp);
                 s_w = reinterpret_cast<const float2 *>(sT + gl.off_w);
                 s_e = reinterpret_cast<const uint16_t *>(sT + gl.off_e);
                 ntile = hd->ntile[rank];
@@ -174,18 +175,25 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
                 own_mask = 0;
                 for (int g = 0; g < 8; g++)
                     if (hd->owner[g] == rank) own_mask |= 1u << g;
+                box_mask = 0;
+                for (int g = 0; g < 8; g++)
+                    if (8 * g < hd->box_h) box_mask |= 1u << g;
+                // K-groups (8 values: 4 cells of (re, im)) that hold box columns
+                copy_bytes = (uint32_t)((2 * hd->box_w + 7) / 8) * kKs;
+                incoming = (uint32_t)__popc(box_mask & ~own_mask) * 2u * copy_bytes;
                 cur_station = stn;
             }
-            if ((b ? a1_st1 : a1_st0) != stn) {     // own row groups of buffer b, in every copy
-                const uint32_t off_b = (uint32_t)b * kA1Bytes;
-#pragma unroll
-                for (int r = 0; r < kRanks; r++)
-                    for (int k = tid; k < (int)(16 * kGroupBytes / 16); k += kFront) {
-                        const uint32_t byte = (uint32_t)k * 16u;
-                        const int grp = byte / kGroupBytes;      // 0..15: pol * 8 + group
-                        if (own_mask & (1u << (grp & 7)))
-                            tc::st_cluster_v4(peer_a1[r] + off_b + byte, make_uint4(0, 0, 0, 0));
-                    }
+            if ((b ? a1_st1 : a1_st0) != stn) {
+                // zero what no other CTA writes into this copy: own groups, groups
+                // outside the box, and the columns past the box of every group
+                uint8_t *A = sA1 + b * kA1Bytes;
+                for (int k = tid; k < (int)(16 * kGroupBytes / 16); k += kFront) {
+                    const uint32_t byte = (uint32_t)k * 16u;
+                    const int g = (byte / kGroupBytes) & 7;
+                    const uint32_t in_group = byte % kGroupBytes;
+                    if ((own_mask & (1u << g)) || !(box_mask & (1u << g)) || in_group >= copy_bytes)
+                        reinterpret_cast<int4 *>(A)[k] = make_int4(0, 0, 0, 0);
+                }
                 (b ? a1_st1 : a1_st0) = stn;
             }
             bar_front();
@@ -212,8 +220,9 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
             bar_front();
         };
         auto grid_step = [&](int i) {
+            uint8_t *A = sA1 + (i & 1) * kA1Bytes;
             const uint2 *E = sE + (size_t)(i & 1) * ((p.ne_max + 1) & ~1);
-            for (int t = warp; t < ntile; t += kMmaWarp) {
+            for (int t = s_warp[warp]; t < s_warp[warp + 1]; t++) {
                 float2 g0 = make_float2(0.f, 0.f), g1 = g0;
                 const int qe = s_base[t + 1];
                 int q = s_base[t] + lane;
@@ -235,22 +244,35 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
                 }
                 const uint32_t off = s_cell[t * 32 + lane];
                 if (off != 0xffffffffu) {
-                    const uint32_t v0 = tc::pack_half2(g0.x, g0.y), v1 = tc::pack_half2(g1.x, g1.y);
-                    const uint32_t o = (uint32_t)(i & 1) * kA1Bytes + off;
-#pragma unroll
-                    for (int r = 0; r < kRanks; r++) {
-                        tc::st_cluster(peer_a1[r] + o, v0);
-                        tc::st_cluster(peer_a1[r] + o + kPolBytes, v1);
-                    }
+                    *reinterpret_cast<uint32_t *>(A + off) = tc::pack_half2(g0.x, g0.y);
+                    *reinterpret_cast<uint32_t *>(A + off + kPolBytes) = tc::pack_half2(g1.x, g1.y);
                 }
             }
         };
-        // this CTA's rows of G are in every copy: arrive on every CTA's barrier
-        auto signal = [&](int i) {
-            if (dead) return;
-            const uint32_t mb = tc::smem_u32(&mb_a1[i & 1]);
-#pragma unroll
-            for (int r = 0; r < kRanks; r++) tc::mbar_arrive_cluster(tc::peer_addr(mb, (uint32_t)r));
+        // warp 6: the box columns of the own in-box row groups of G -> the
+        // three other CTAs, one bulk copy per lane (peer, group, pol); then
+        // this CTA's own arrival, expecting the bytes the others send
+        auto send = [&](int i) {
+            const int b = i & 1;
+            uint8_t *A = sA1 + b * kA1Bytes;
+            const uint32_t mine = own_mask & box_mask;
+            const int n_own = __popc(mine);
+            if (!dead)
+                for (int c = lane; c < (kRanks - 1) * n_own * 2; c += 32) {
+                    const int pol = c & 1, k = (c >> 1) % n_own, pi = (c >> 1) / n_own;
+                    const uint32_t peer = (uint32_t)pi + (pi >= (int)rank ? 1u : 0u);
+                    int g = -1;
+                    for (int x = 0, seen = 0; x < 8; x++)
+                        if (mine & (1u << x)) {
+                            if (seen == k) g = x;
+                            seen++;
+                        }
+                    const uint32_t off = (uint32_t)pol * kPolBytes + (uint32_t)g * kGroupBytes;
+                    tc::bulk_s2peer(tc::peer_addr(tc::smem_u32(A + off), peer), A + off, copy_bytes,
+                                    tc::peer_addr(tc::smem_u32(&mb_a1[b]), peer));
+                }
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive_expect_tx(&mb_a1[b], incoming);
         };
         // warps 0-3: D1 row (pol, y) -> column (y, re/im) of B2 for the
         // rows (pol, out re/im, l_x): out re <- (H_r, -H_i), out im <- (H_i, H_r)
@@ -300,9 +322,9 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
                 prepare(s.stn, b);
                 stage_volt(s, j);
                 grid_step(j);
-                tc::fence_proxy_async_cluster();
+                tc::fence_proxy_async();
                 bar_front();
-                if (tid == 0) signal(j);
+                if (warp == kSendWarp) send(j);
             }
             if (i >= 0 && warp < 4) {
                 tc::mbar_wait(&mb_d1[i & 1], (uint32_t)((i >> 1) & 1), p.status);
@@ -334,6 +356,19 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
             };
             for (int q = 0; q < kStages; q++) issue_load();
             for (int k = -1; k < nsteps; k++) {
+                if (k >= 0) {                      // stage 2 of step k
+                    tc::mbar_wait(&mb_a2, (uint32_t)(k & 1), p.status);
+                    const int slot = k & 1;
+                    if (k >= 2) tc::mbar_wait(&mb_empty[slot], (uint32_t)(((k >> 1) - 1) & 1), p.status);
+                    tc::fence_after();
+                    const uint32_t d = tmem + kD2Col + (uint32_t)slot * 128u;
+#pragma unroll
+                    for (int s = 0; s < 8; s++)
+                        tc::mma_f16(d, tc::desc(a2 + s * 2 * kKs, kKs, kMNs), tc::desc(b2 + s * 2 * kB2Ks, kB2Ks, kB2MNs),
+                                    kIdesc2, s > 0);
+                    tc::mma_commit(&mb_full[slot]);
+                    tc::mma_commit(&mb_b2free);
+                }
                 if (k + 1 < nsteps) {              // stage 1 of step k+1
                     const int i = k + 1;
                     tc::mbar_wait_cluster(&mb_a1[i & 1], (uint32_t)((i >> 1) & 1), p.status);
@@ -348,19 +383,6 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
                     tc::mma_commit(&mb_d1[i & 1]);
                     // every CTA waits for this only before step i + 2
                     if (i + 2 < nsteps) tc::mma_commit_multicast(&mb_a1free[i & 1], (uint16_t)((1u << kRanks) - 1));
-                }
-                if (k >= 0) {                      // stage 2 of step k
-                    tc::mbar_wait(&mb_a2, (uint32_t)(k & 1), p.status);
-                    const int slot = k & 1;
-                    if (k >= 2) tc::mbar_wait(&mb_empty[slot], (uint32_t)(((k >> 1) - 1) & 1), p.status);
-                    tc::fence_after();
-                    const uint32_t d = tmem + kD2Col + (uint32_t)slot * 128u;
-#pragma unroll
-                    for (int s = 0; s < 8; s++)
-                        tc::mma_f16(d, tc::desc(a2 + s * 2 * kKs, kKs, kMNs), tc::desc(b2 + s * 2 * kB2Ks, kB2Ks, kB2MNs),
-                                    kIdesc2, s > 0);
-                    tc::mma_commit(&mb_full[slot]);
-                    tc::mma_commit(&mb_b2free);
                 }
             }
         }
@@ -487,6 +509,8 @@ void epic_tc128_build_blob(int box_w, int box_h, const std::vector<int32_t> &cst
     Blob128 hd;
     memset(&hd, 0, sizeof(hd));
     memcpy(hd.owner, owner, 8);
+    hd.box_w = box_w;
+    hd.box_h = box_h;
     std::vector<std::vector<uint8_t>> tabs(kRanks);
     max_rank_bytes = 0;
     max_rank_entries = 0;
@@ -505,7 +529,8 @@ void epic_tc128_build_blob(int box_w, int box_h, const std::vector<int32_t> &cst
                     }
                 cs[c + 1] = (int32_t)el.size();
             }
-        epic_tc_build_gather(box_w, box_h, cs, el, ww, kKs, kMNs, tabs[r], hd.ntile[r], hd.nent[r]);
+        // warp 6 sends the rows to the other CTAs instead of gridding
+        epic_tc_build_gather(box_w, box_h, cs, el, ww, kKs, kMNs, tabs[r], hd.ntile[r], hd.nent[r], kGatherWarps - 1);
         hd.bytes[r] = (uint32_t)tabs[r].size();
         max_rank_bytes = std::max(max_rank_bytes, hd.bytes[r]);
         max_rank_entries = std::max<long long>(max_rank_entries, hd.nent[r]);
