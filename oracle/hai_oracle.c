@@ -28,6 +28,10 @@
  *     (autos included) gridded with the autocorrelation of the element
  *     kernels, K_ab[d] = sum_j g_a[j + d] conj(g_b[j]), g_a = placed conj taps,
  *     on the circular N grid, then the same (-1)^d and DFT as EPIC.
+ *   - inter-station XFFT (Eq. inter-station XFFT): station visibilities
+ *     phased towards the beam direction with exp(+2 pi i s_k.dr / lambda) in
+ *     FP64, gridded with a 2x2 bilinear kernel at uv = dr / cell; pairs whose
+ *     footprint leaves the grid are dropped and counted.
  */
 #include <math.h>
 #include <stdint.h>
@@ -381,6 +385,105 @@ int orc_xfft_image(int n, int ne, int k, const int32_t *anchors, const float *ta
                     }
                 }
         free(kab);
+        free(gr);
+        free(gi);
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Inter-station XFFT (Eq. inter-station XFFT) of station visibilities phased  */
+/* towards beam directions s_k: every ordered station pair (m, n), autos        */
+/* included, contributes V~_mn = V_mn exp(+2 pi i s_k.(r_m - r_n) / lambda)     */
+/* (phase in FP64) through the 2x2 bilinear kernel at uv = (r_m - r_n) / cell   */
+/* (in cells): weights (1-fu)(1-fv), fu(1-fv), (1-fu)fv, fu fv on the cells     */
+/* (u0, v0) .. (u0+1, v0+1), u0 = floor(u), fu = u - u0.  A pair whose 2x2      */
+/* footprint, or its mirror's, leaves [-n/2, n/2 - 1]^2 is dropped (counted     */
+/* once per unordered pair in *n_offgrid).  Cell (u, v) sits at (u mod n,       */
+/* v mod n) of the row-major grid; then (-1)^(u+v) and the DFT (+) as EPIC.     */
+/* pos [S][2] m; dir [K][2]; vis int64 [K][C][S(S+1)/2][P][P][2];               */
+/* img [K][C][P][P][n][n][2] complex for every polarisation pair.               */
+/* ------------------------------------------------------------------------- */
+static void bilinear(double u, long *u0, double *fu) {
+    double f = floor(u);
+    *u0 = (long)f;
+    *fu = u - f;
+}
+
+static int footprint_on_grid(int n, long u0, long v0) {
+    return u0 >= -n / 2 && u0 + 1 <= n / 2 - 1 && v0 >= -n / 2 && v0 + 1 <= n / 2 - 1;
+}
+
+int orc_station_xfft(int n, int S, const double *pos, double lambda, double cell, int K, const double *dir,
+                     const int64_t *vis, int C, int P, double *img, int64_t *n_offgrid) {
+    if (!is_pow2(n) || n < 4 || S <= 0 || K <= 0 || C < 0 || P < 1 || P > 2 || !(lambda > 0) || !(cell > 0))
+        return ORC_ERR_ARG;
+    const long nn = (long)n * n, nbl = (long)S * (S + 1) / 2;
+    /* pairs dropped: the test is geometric, the same for every image */
+    int64_t dropped = 0;
+    for (int m = 0; m < S; m++)
+        for (int q = 0; q < m; q++) {
+            long a0, b0, c0, d0;
+            double fa, fb, fc, fd;
+            bilinear((pos[2 * m] - pos[2 * q]) / cell, &a0, &fa);
+            bilinear((pos[2 * m + 1] - pos[2 * q + 1]) / cell, &b0, &fb);
+            bilinear((pos[2 * q] - pos[2 * m]) / cell, &c0, &fc);
+            bilinear((pos[2 * q + 1] - pos[2 * m + 1]) / cell, &d0, &fd);
+            if (!footprint_on_grid(n, a0, b0) || !footprint_on_grid(n, c0, d0)) dropped++;
+        }
+    if (n_offgrid) *n_offgrid = dropped;
+    memset(img, 0, sizeof(double) * (size_t)K * C * P * P * nn * 2);
+#pragma omp parallel
+    {
+        double *gr = (double *)malloc(sizeof(double) * nn);
+        double *gi = (double *)malloc(sizeof(double) * nn);
+#pragma omp for collapse(4) schedule(dynamic, 1)
+        for (int kk = 0; kk < K; kk++)
+            for (int c = 0; c < C; c++)
+                for (int al = 0; al < P; al++)
+                    for (int be = 0; be < P; be++) {
+                        memset(gr, 0, sizeof(double) * nn);
+                        memset(gi, 0, sizeof(double) * nn);
+                        for (int m = 0; m < S; m++)
+                            for (int q = 0; q < S; q++) {
+                                const double dx = pos[2 * m] - pos[2 * q], dy = pos[2 * m + 1] - pos[2 * q + 1];
+                                long u0, v0, mu0, mv0;
+                                double fu, fv, mfu, mfv;
+                                bilinear(dx / cell, &u0, &fu);
+                                bilinear(dy / cell, &v0, &fv);
+                                bilinear(-dx / cell, &mu0, &mfu);
+                                bilinear(-dy / cell, &mv0, &mfv);
+                                if (!footprint_on_grid(n, u0, v0) || !footprint_on_grid(n, mu0, mv0)) continue;
+                                double vr, vi;
+                                if (m >= q) {      /* stored: V^{al be}_{mq} */
+                                    const int64_t *v = vis + (((((size_t)kk * C + c) * nbl + (long)m * (m + 1) / 2 + q) * P + al) * P + be) * 2;
+                                    vr = (double)v[0];
+                                    vi = (double)v[1];
+                                } else {           /* V^{al be}_{mq} = conj(V^{be al}_{qm}) */
+                                    const int64_t *v = vis + (((((size_t)kk * C + c) * nbl + (long)q * (q + 1) / 2 + m) * P + be) * P + al) * 2;
+                                    vr = (double)v[0];
+                                    vi = -(double)v[1];
+                                }
+                                /* steering towards s_k, FP64 phase */
+                                const double ph = ORC_TWO_PI * (dir[2 * kk] * dx + dir[2 * kk + 1] * dy) / lambda;
+                                const double cr = cos(ph), ci = sin(ph);
+                                const double sr = vr * cr - vi * ci, si = vr * ci + vi * cr;
+                                const double w[4] = {(1 - fu) * (1 - fv), fu * (1 - fv), (1 - fu) * fv, fu * fv};
+                                for (int t = 0; t < 4; t++) {
+                                    const long uu = u0 + (t & 1), vv = v0 + (t >> 1);
+                                    const long cx = ((uu % n) + n) % n, cy = ((vv % n) + n) % n;
+                                    gr[cy * n + cx] += w[t] * sr;
+                                    gi[cy * n + cx] += w[t] * si;
+                                }
+                            }
+                        checkerboard(n, gr, gi);
+                        orc_fft2d(n, gr, gi);
+                        double *o = img + (((((size_t)kk * C + c) * P + al) * P + be) * nn) * 2;
+                        for (long l = 0; l < nn; l++) {
+                            o[2 * l] = gr[l];
+                            o[2 * l + 1] = gi[l];
+                        }
+                    }
         free(gr);
         free(gi);
     }

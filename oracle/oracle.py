@@ -63,6 +63,9 @@ def lib():
             L.orc_vis_kernel.restype = None
             L.orc_xfft_image.argtypes = [c_int, c_int, c_int, _i32p, _f32p, _i64p, c_int, c_int,
                                          _f64p]
+            L.orc_station_xfft.argtypes = [c_int, c_int, _f64p, ctypes.c_double, ctypes.c_double, c_int,
+                                           _f64p, _i64p, c_int, c_int, _f64p,
+                                           ctypes.POINTER(ctypes.c_int64)]
             L.orc_dft2d_brute.argtypes = [c_int, _f64p, _f64p, _f64p, _f64p]
             L.orc_dft2d_brute.restype = None
             _lib = L
@@ -201,6 +204,24 @@ def xfft_image(n: int, anchors, taps, vis: np.ndarray) -> np.ndarray:
     img = np.empty((C, P, P, n, n, 2))
     _check(lib().orc_xfft_image(n, ne, k, anchors, taps, vis, C, P, img), "xfft_image")
     return img[..., 0] + 1j * img[..., 1]
+
+
+def station_xfft(n: int, pos_m, lam_m: float, cell_m: float, dirs, vis: np.ndarray):
+    """Dirty images of Eq. (inter-station XFFT): station visibilities int64
+    [K][C][S(S+1)/2][P][P][2] phased towards dirs [K][2] (direction cosines)
+    in FP64, gridded bilinearly at (r_m - r_n) / cell on an n x n grid.
+    Returns (complex [K][C][P][P][n][n], pairs dropped off the grid)."""
+    pos = np.ascontiguousarray(pos_m, np.float64)
+    dirs = np.ascontiguousarray(dirs, np.float64)
+    vis = np.ascontiguousarray(vis, np.int64)
+    K, C, nbl, P, _, _ = vis.shape
+    S = pos.shape[0]
+    assert nbl == S * (S + 1) // 2 and dirs.shape == (K, 2)
+    img = np.empty((K, C, P, P, n, n, 2))
+    dropped = ctypes.c_int64()
+    _check(lib().orc_station_xfft(n, S, pos, lam_m, cell_m, K, dirs, vis, C, P, img, ctypes.byref(dropped)),
+           "station_xfft")
+    return img[..., 0] + 1j * img[..., 1], dropped.value
 
 
 def xfft_as_epic_planes(ximg: np.ndarray) -> np.ndarray:

@@ -312,3 +312,108 @@ def test_epic_equals_xfft_with_wrapped_lags():
     epic = O.epic_image(n, anchors, taps, volt)
     ximg = O.xfft_image(n, anchors, taps, O.correlate(volt))
     assert rel(O.xfft_as_epic_planes(ximg), epic) < 1e-11
+
+
+# ---------------------------------------------------------------- inter-station XFFT
+def _vis_const(K, C, S, P, value):
+    vis = np.zeros((K, C, S * (S + 1) // 2, P, P, 2), np.int64)
+    vis[..., 0] = value
+    return vis
+
+
+def test_station_xfft_source_at_phase_centre_closed_form():
+    """Visibilities of a source at the phase centre (V = A for every pair):
+    all S^2 ordered pairs add at pixel (N/2, N/2), whatever the layout, and
+    XX is real and peaks there."""
+    rng = np.random.default_rng(4)
+    S, n, A = 7, 32, 3
+    pos = rng.uniform(-20.0, 20.0, (S, 2))
+    img, dropped = O.station_xfft(n, pos, 3.0, 4.0, np.zeros((1, 2)), _vis_const(1, 1, S, 1, A))
+    xx = img[0, 0, 0, 0]
+    assert dropped == 0
+    assert xx[n // 2, n // 2].real == pytest.approx(A * S * S, rel=1e-12)
+    assert np.abs(xx.imag).max() < 1e-10 * A * S * S
+    assert xx.real.max() == pytest.approx(A * S * S, rel=1e-12)
+
+
+@pytest.mark.parametrize("shift", [(3, 0), (-2, 5)])
+def test_station_xfft_steering_moves_the_source_by_closed_form(shift):
+    """Stations on whole cells, V = A (a source at zenith): steering towards
+    s_k puts the source at s_src - s_k, i.e. pixel (N/2, N/2) - N cell s_k /
+    lambda, with the full peak A S^2 (fixes the sign of the steering phase)."""
+    S, n, A, lam, cell = 6, 32, 2, 3.0, 5.0
+    rng = np.random.default_rng(9)
+    pos = rng.integers(-4, 5, (S, 2)).astype(np.float64) * cell
+    px, py = shift
+    d = np.array([[px * lam / (n * cell), py * lam / (n * cell)]])
+    img, _ = O.station_xfft(n, pos, lam, cell, d, _vis_const(1, 1, S, 1, A))
+    xx = img[0, 0, 0, 0].real
+    assert xx[n // 2 - py, n // 2 - px] == pytest.approx(A * S * S, rel=1e-12)
+    assert np.unravel_index(np.argmax(xx), xx.shape) == (n // 2 - py, n // 2 - px)
+
+
+def test_station_xfft_bilinear_half_cell_closed_form():
+    """Two stations half a cell apart in x: the grid holds 3A at u = 0 and
+    A/2 at u = +-1, so every image row is A (3 + cos(2 pi (l - N/2) / N))."""
+    n, A = 16, 4
+    pos = np.array([[0.0, 0.0], [0.5, 0.0]])
+    img, dropped = O.station_xfft(n, pos, 1.0, 1.0, np.zeros((1, 2)), _vis_const(1, 1, 2, 1, A))
+    xx = img[0, 0, 0, 0]
+    l = np.arange(n)
+    want = A * (3 + np.cos(2 * np.pi * (l - n // 2) / n))
+    assert dropped == 0
+    for row in range(n):
+        assert np.allclose(xx[row].real, want, atol=1e-12)
+    assert np.abs(xx.imag).max() < 1e-12
+
+
+def test_station_xfft_offgrid_pairs_brute_force():
+    """A pair is dropped when its 2x2 footprint or its mirror's leaves
+    [-N/2, N/2 - 1]^2; count by brute force and check the dropped pairs no
+    longer contribute (image = image of the kept stations only)."""
+    rng = np.random.default_rng(12)
+    n, cell = 16, 1.0
+    core = rng.uniform(-3.0, 3.0, (5, 2))
+    tail = np.array([[40.0, 1.0], [-2.0, 30.0]])
+    pos = np.vstack([core, tail])
+    S = len(pos)
+    want = 0
+    for m in range(S):
+        for q in range(m):
+            ok = True
+            for sgn in (1, -1):
+                u0 = np.floor(sgn * (pos[m, 0] - pos[q, 0]) / cell)
+                v0 = np.floor(sgn * (pos[m, 1] - pos[q, 1]) / cell)
+                ok &= (-n // 2 <= u0) and (u0 + 1 <= n // 2 - 1) and (-n // 2 <= v0) and (v0 + 1 <= n // 2 - 1)
+            want += not ok
+    img, dropped = O.station_xfft(n, pos, 2.0, cell, np.zeros((1, 2)), _vis_const(1, 1, S, 1, 1))
+    assert dropped == want
+    # every pair with a tail station is off the grid: of the tail only its two
+    # autos (value 1 at uv = 0, a constant 1 in the image each) remain
+    core_img, _ = O.station_xfft(n, core, 2.0, cell, np.zeros((1, 2)), _vis_const(1, 1, len(core), 1, 1))
+    assert dropped == 2 * len(core) + 1
+    assert np.allclose(img[0, 0, 0, 0].real, core_img[0, 0, 0, 0].real + 2.0, atol=1e-10)
+
+
+def test_station_xfft_equals_intra_xfft_with_unit_taps():
+    """Stations on whole cells, no steering: the bilinear kernel reduces to a
+    single tap, so the inter-station XFFT equals the intra-station XFFT of
+    the same visibilities with 1x1 unit taps at the same cells, for every
+    polarisation pair (two independently written oracle routines)."""
+    rng = np.random.default_rng(5)
+    n, S, P, C, cell = 16, 6, 2, 2, 2.0
+    cells = np.stack([rng.permutation(6)[:S], rng.permutation(6)[:S]], axis=1) + 4
+    pos = cells.astype(np.float64) * cell
+    vis = rng.integers(-500, 500, (C, S * (S + 1) // 2, P, P, 2)).astype(np.int64)
+    # autos of the auto-pol products are real
+    for m in range(S):
+        bl = m * (m + 1) // 2 + m
+        vis[:, bl, 0, 0, 1] = 0
+        vis[:, bl, 1, 1, 1] = 0
+        vis[:, bl, 1, 0] = vis[:, bl, 0, 1] * np.array([1, -1])
+    st, dropped = O.station_xfft(n, pos, 3.0, cell, np.zeros((1, 2)), vis[None])
+    taps = np.zeros((S, 1, 1, 2), np.float32)
+    taps[..., 0] = 1.0
+    intra = O.xfft_image(n, cells.astype(np.int32), taps, vis)
+    assert dropped == 0
+    assert np.abs(st[0] - intra).max() < 1e-9 * np.abs(intra).max()
