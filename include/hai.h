@@ -238,6 +238,58 @@ hai_status hai_beamform(hai_ctx *ctx, const int8_t *volt, const int8_t *w, int S
                         void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Inter-station stage of a hierarchical array (Section 6).
+ *
+ * hai_beams_to_corr: station beams -> correlator input, so that hai_correlate
+ * with the K*C (beam, channel) pairs as channels and the S stations as
+ * elements gives the inter-station visibilities of Eq. inter-station
+ * visibilities, V^{pq}_{mn}(s_k) = sum_t E^p_m(s_k) conj(E^q_n(s_k)).
+ *   beams  device int8 [S][C][T][K][P][2] (hai_beamform's requantised output)
+ *   out    device int8 [K][C][T][P][S][2]
+ * HAI_ERR_UNSUPPORTED if 2 K P (S + 1) bytes exceed 48 KB. */
+hai_status hai_beams_to_corr(hai_ctx *ctx, const int8_t *beams, int S, int C, int T, int K, int P, int8_t *out,
+                             void *stream);
+
+/* Station array for the inter-station XFFT (copied in; FP64 geometry). */
+typedef struct {
+    int n_station;       /* S */
+    const double *pos_m; /* host [S][2] station centres, metres */
+    double lambda_m;     /* wavelength */
+    double cell_m;       /* uv cell of the array grid, metres */
+    int grid_n;          /* N: power of two, 16..256 */
+    int n_pol;           /* must be 2 */
+    int n_dir;           /* K beam directions */
+    const double *dir;   /* host [K][2] direction cosines s_k, or NULL (all zenith) */
+} hai_vis_layout_desc;
+typedef struct hai_vis_layout hai_vis_layout;
+
+/* Build the gridding records (FP64 on the host: the 2x2 bilinear footprint of
+ * every station pair at uv = (r_m - r_n) / cell and of its mirror) and the
+ * steering phasors exp(+2 pi i s_k.(r_m - r_n) / lambda), computed in FP64 on
+ * the GPU and stored in FP32.  Pairs whose footprint, or its mirror's, leaves
+ * [-N/2, N/2 - 1]^2 are dropped (hai_vis_layout_offgrid counts them).
+ * HAI_ERR_UNSUPPORTED if the uv window of the kept pairs does not fit in
+ * shared memory or n_pol != 2. */
+hai_status hai_vis_layout_create(hai_ctx *ctx, const hai_vis_layout_desc *desc, hai_vis_layout **out);
+void hai_vis_layout_destroy(hai_vis_layout *layout);
+/* Station pairs (unordered, autos never) dropped off the grid, per image. */
+hai_status hai_vis_layout_offgrid(const hai_vis_layout *layout, long long *n_offgrid);
+
+/* Dirty images of Eq. inter-station XFFT: for every beam k and channel c,
+ * all ordered station pairs (autos included) of the visibilities, phased
+ * towards s_k, gridded bilinearly, (-1)^(u+v) and a 2D DFT (exponent +).
+ *   vis  device int32 [K][C][S(S+1)/2][2][2][2] (hai_correlate's output for
+ *        the K*C channels of hai_beams_to_corr).  As from a correlator, the
+ *        autos must have real XX and YY and YX = conj(XY): the XX and YY
+ *        images are real and are computed together as one complex FFT.
+ *   img  device float [K][C][4][N][N]: XX, YY, Re XY, Im XY (overwritten; the
+ *        planes also serve as the gridding scratch)
+ * Phase centre at pixel (N/2, N/2); pixel l looks along s_k + (l - N/2) *
+ * lambda / (N cell). */
+hai_status hai_xfft_station_image(hai_ctx *ctx, const hai_vis_layout *layout, const int32_t *vis, int C, float *img,
+                                  void *stream);
+
+/* ---------------------------------------------------------------------------
  * EPIC image, FP32 path, without any device allocation.  (The paper has no
  * counterpart: this is an interface for callers, not a step of the method.)
  *

@@ -35,6 +35,12 @@ class _LayoutDesc(ctypes.Structure):
                 ("n_pol", ctypes.c_int), ("anchors", ctypes.c_void_p), ("taps", ctypes.c_void_p)]
 
 
+class _VisLayoutDesc(ctypes.Structure):
+    _fields_ = [("n_station", ctypes.c_int), ("pos_m", ctypes.c_void_p), ("lambda_m", ctypes.c_double),
+                ("cell_m", ctypes.c_double), ("grid_n", ctypes.c_int), ("n_pol", ctypes.c_int),
+                ("n_dir", ctypes.c_int), ("dir", ctypes.c_void_p)]
+
+
 _lib = None
 _lock = threading.Lock()
 _vp = ctypes.c_void_p
@@ -67,6 +73,12 @@ def _declare(L):
     L.hai_plan_run.argtypes = [_vp, _vp, _vp, _vp]
     L.hai_plan_autotune.argtypes = [_vp, _vp, _vp, _int, _vp]
     L.hai_plan_schedule.argtypes = [_vp, ctypes.POINTER(_int), _vp, _vp, _vp]
+    L.hai_beams_to_corr.argtypes = [_vp, _vp, _int, _int, _int, _int, _int, _vp, _vp]
+    L.hai_vis_layout_create.argtypes = [_vp, ctypes.POINTER(_VisLayoutDesc), ctypes.POINTER(_vp)]
+    L.hai_vis_layout_destroy.argtypes = [_vp]
+    L.hai_vis_layout_destroy.restype = None
+    L.hai_vis_layout_offgrid.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.hai_xfft_station_image.argtypes = [_vp, _vp, _vp, _int, _vp, _vp]
     L.hai_profile_enable.argtypes = [_vp, _int, _int]
     L.hai_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
@@ -293,3 +305,54 @@ def hai_plan_schedule(plan: Plan):
     m = (ctypes.c_double * 3)()
     _check(load().hai_plan_schedule(plan.handle, ctypes.byref(n), g, c, m), "hai_plan_schedule")
     return [(g[k], c[k], m[k]) for k in range(n.value)]
+
+
+# ------------------------------------------------------------------ inter-station stage
+def hai_beams_to_corr(ctx, beams, S: int, C: int, T: int, K: int, P: int, out, stream=None):
+    import torch
+    bp = _dev_ptr(beams, torch.int8, "beams", S * C * T * K * P * 2)
+    op = _dev_ptr(out, torch.int8, "out", S * C * T * K * P * 2)
+    _check(load().hai_beams_to_corr(ctx, bp, S, C, T, K, P, op, _stream(stream)), "hai_beams_to_corr")
+
+
+class VisLayout:
+    """Handle of a hai_vis_layout with its sizes."""
+
+    def __init__(self, handle, S, N, K):
+        self.handle, self.S, self.N, self.K = handle, S, N, K
+
+    @property
+    def n_baselines(self):
+        return self.S * (self.S + 1) // 2
+
+
+def hai_vis_layout_create(ctx, pos_m, lambda_m: float, cell_m: float, grid_n: int, dirs=None,
+                          n_pol: int = 2) -> VisLayout:
+    pos = np.ascontiguousarray(pos_m, np.float64)
+    S = pos.shape[0]
+    if pos.shape != (S, 2):
+        raise ValueError("pos_m must be [S][2]")
+    d = None if dirs is None else np.ascontiguousarray(dirs, np.float64)
+    K = 1 if d is None else d.shape[0]
+    desc = _VisLayoutDesc(S, pos.ctypes.data, lambda_m, cell_m, grid_n, n_pol, K,
+                          None if d is None else d.ctypes.data)
+    h = _vp()
+    _check(load().hai_vis_layout_create(ctx, ctypes.byref(desc), ctypes.byref(h)), "hai_vis_layout_create")
+    return VisLayout(h, S, grid_n, K)
+
+
+def hai_vis_layout_destroy(layout: VisLayout):
+    load().hai_vis_layout_destroy(layout.handle)
+
+
+def hai_vis_layout_offgrid(layout: VisLayout) -> int:
+    n = ctypes.c_longlong()
+    _check(load().hai_vis_layout_offgrid(layout.handle, ctypes.byref(n)), "hai_vis_layout_offgrid")
+    return n.value
+
+
+def hai_xfft_station_image(ctx, layout: VisLayout, vis, C: int, img, stream=None):
+    import torch
+    vp = _dev_ptr(vis, torch.int32, "vis", layout.K * C * layout.n_baselines * 8)
+    ip = _dev_ptr(img, torch.float32, "img", layout.K * C * 4 * layout.N * layout.N)
+    _check(load().hai_xfft_station_image(ctx, layout.handle, vp, C, ip, _stream(stream)), "hai_xfft_station_image")

@@ -86,6 +86,8 @@ class HierarchyConfig:
     n_pol: int = 2
     n_time: int = 1000
     grid_n: int = 256         # station-level (inter-station) grid
+    cell_m: float = 19.0      # its uv cell: half a station diameter (padding 2)
+    requant_shift: int = 11   # beams / 2^11: noise-dominated beam rms ~ 18 counts
     seed: int = SEED0 + 3
 
 
@@ -290,6 +292,35 @@ def station_centres(cfg: HierarchyConfig) -> np.ndarray:
     ang = rng.uniform(0, 2 * np.pi, cfg.n_tail)
     tail = np.stack([rad * np.cos(ang), rad * np.sin(ang)], axis=1)
     return np.vstack([core, tail])
+
+
+def hierarchy_voltages(cfg: HierarchyConfig, centres_m: np.ndarray, elem_m: np.ndarray,
+                       dirs: np.ndarray, flux: np.ndarray, n_station: int, n_chan: int,
+                       n_time: int, device="cpu", scale: float = 16.0):
+    """int8 voltages [S][C][T][P][N_e][2] of the first n_station stations: one
+    sky per (channel, sample, pol) seen by every element at r_m + r_a with
+    phase exp(-2 pi i s.(r_m + r_a) / lambda), plus independent unit complex
+    noise per (station, element); quantised as `voltages`."""
+    import torch
+
+    P, ne, lam = cfg.n_pol, len(elem_m), cfg.station.lam_m
+    out = torch.empty((n_station, n_chan, n_time, P, ne, 2), dtype=torch.int8, device=device)
+    sd = torch.tensor(np.sqrt(flux / P / 2.0), dtype=torch.float32, device=device)
+    gen = torch.Generator(device=device)
+    rows = n_time * P
+    for c in range(n_chan):
+        gen.manual_seed(int(cfg.seed) * 1000003 + c)
+        a = torch.randn((rows, len(flux), 2), generator=gen, device=device) * sd[None, :, None]
+        amp = torch.complex(a[..., 0], a[..., 1])
+        for m in range(n_station):
+            ph = -2.0 * np.pi * (dirs @ (elem_m + centres_m[m]).T) / lam
+            steer = torch.tensor(np.exp(1j * ph), dtype=torch.complex64, device=device)
+            sig = amp @ steer
+            gen.manual_seed(int(cfg.seed) * 1000003 + 7919 * (m + 1) + c)
+            nz = torch.randn((rows, ne, 2), generator=gen, device=device) * math.sqrt(0.5)
+            x = torch.stack([sig.real, sig.imag], dim=-1) + nz
+            out[m, c] = torch.clamp(torch.round(x * scale), -127, 127).to(torch.int8).view(n_time, P, ne, 2)
+    return out
 
 
 def uneven_station_sizes(cfg: UnevenConfig) -> np.ndarray:
