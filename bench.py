@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--no-components", action="store_true")
     ap.add_argument("--channels", type=int, default=0,
                     help="image only this many channels (small cases for profiling)")
+    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "bf"], default=None,
+                    help="run one small case of a kernel twice, untimed, and exit (for ncu captures)")
     return ap.parse_args()
 
 
@@ -297,6 +299,18 @@ def bf_component(hai, ctx, flush, peaks):
     return out
 
 
+# DRAM bytes (read + write) of one epic_tc_kernel<64> launch over 16 channels of
+# the SKA-low station, from an ncu capture of `bench.py --case tc64` with the
+# kernel as it is now; traffic grows in proportion to the channels imaged.
+TC64_TRAFFIC_16CH = 33.656576e6
+
+
+def traffic_tc64(cfg, C):
+    if cfg.name != "ska_low_station256_grid64" or cfg.n_time != 2048:
+        return None
+    return TC64_TRAFFIC_16CH * C / 16
+
+
 def plan_mma_flops(n, ne=None):
     """Executed tensor-core FLOP per (channel, sample) of a station of grid
     side n: N = 32: 3 products 128 x 64 x 32 per 4 samples; N = 64: 3 products
@@ -372,8 +386,108 @@ def plan_component(hai, ctx, flush, peaks, steps):
     return out
 
 
+def hierarchy_component(hai, ctx, flush, peaks):
+    """The hierarchical workload's cadence: 256 stations x 256 elements, 32
+    channels, 2 pols, 1000 samples; int8 beamforming to 16 beams per station
+    with requantisation, beams to correlator layout, the station correlator
+    (32,896 pairs per beam and channel) and the FP64-steered XFFT on a 256^2
+    station grid.  Uniform random int8 voltages (times do not depend on the
+    values); units = station-image pixels x beams x channels x pols x samples."""
+    import torch
+    from paper_2411_17804_gb300 import inputs as I
+    H = I.HierarchyConfig()
+    S, C, T, K, P, ne, n = H.n_station, H.n_chan, H.n_time, H.n_beam, H.n_pol, H.station.n_elem, H.grid_n
+    g = torch.Generator(device="cuda").manual_seed(13)
+    volt = torch.randint(-128, 128, (S, C, T, P, ne, 2), dtype=torch.int8, device="cuda", generator=g)
+    elem = I.station_layout(H.station)
+    centres = I.station_centres(H)
+    dirs = I.beam_directions(K, H.station.lam_m, H.station.diameter_m)
+    w = torch.from_numpy(np.repeat(I.bf_weights(elem, H.station.lam_m, dirs, P)[None], S, axis=0)).cuda()
+    lay = hai.hai_vis_layout_create(ctx, centres, H.station.lam_m, H.cell_m, n, dirs)
+    beams = torch.empty((S, C, T, K, P, 2), dtype=torch.int8, device="cuda")
+    cin = torch.empty((K, C, T, P, S, 2), dtype=torch.int8, device="cuda")
+    vis = torch.empty((K * C, S * (S + 1) // 2, P, P, 2), dtype=torch.int32, device="cuda")
+    img = torch.empty((K * C, 4, n, n), device="cuda")
+    sat = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stages = {
+        "beamform_requant": lambda st: hai.hai_beamform(ctx, volt, w, S, C, T, K, ne, P, H.requant_shift, beams, sat, st),
+        "beams_to_corr": lambda st: hai.hai_beams_to_corr(ctx, beams, S, C, T, K, P, cin, st),
+        "station_correlator": lambda st: hai.hai_correlate(ctx, cin.view(K * C, T, P, S, 2), K * C, T, S, P, vis, 0, st),
+        "station_xfft": lambda st: hai.hai_xfft_station_image(ctx, lay, vis, C, img, st)}
+    ms = {k: time_call(f, 5, 2, flush) for k, f in stages.items()}
+    total = time_call(lambda st: [f(st) for f in stages.values()], 5, 2, flush)
+    units = n * n * K * C * P * T
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    pk = float(peaks.get("bf16_tflops", 1900.0))
+    bf_bytes = volt.numel() + w.numel() + beams.numel()
+    tr_bytes = 2 * beams.numel()
+    mma = corr_mma_flops(K * C, T, S, P)
+    out = {"workload": H.name, "stations": S, "elements": ne, "channels": C, "samples": T, "beams": K,
+           "station_grid": n, "pairs_off_grid": hai.hai_vis_layout_offgrid(lay),
+           "stage_ms": ms, "ms": total, "units_per_s": units / (total * 1e-3), "unit": UNIT,
+           "roofline": {
+               "beamform_requant": {"bound": "hbm", "achieved": bf_bytes / (ms["beamform_requant"] * 1e-3) / 1e9,
+                                    "peak": hbm, "unit": "GB/s"},
+               "beams_to_corr": {"bound": "hbm", "achieved": tr_bytes / (ms["beams_to_corr"] * 1e-3) / 1e9,
+                                 "peak": hbm, "unit": "GB/s"},
+               "station_correlator": {"bound": "tensor", "achieved": mma / (ms["station_correlator"] * 1e-3) / 1e12,
+                                      "peak": pk, "unit": "TFLOP/s"}}}
+    for r in out["roofline"].values():
+        r["frac"] = r["achieved"] / r["peak"]
+    hai.hai_vis_layout_destroy(lay)
+    del volt, w, beams, cin, vis, img
+    return out
+
+
+def run_case(name):
+    """Small cases sized for full ncu captures (inputs above L2, a few GB at most)."""
+    import torch
+    from paper_2411_17804_gb300 import hai, inputs as I
+    ctx = hai.hai_create(0)
+    if name == "bf":                      # 16 stations of the hierarchical shape: 525 MB of voltages
+        S, C, T, K, N, P = 16, 32, 1000, 16, 256, 2
+        g = torch.Generator(device="cuda").manual_seed(1)
+        v = torch.randint(-128, 128, (S, C, T, P, N, 2), dtype=torch.int8, device="cuda", generator=g)
+        w = torch.randint(-127, 128, (S, K, P, N, 2), dtype=torch.int8, device="cuda", generator=g)
+        out = torch.empty((S, C, T, K, P, 2), dtype=torch.int8, device="cuda")
+        for _ in range(2):
+            hai.hai_beamform(ctx, v, w, S, C, T, K, N, P, 11, out)
+    elif name in ("tc64", "corr"):        # 16 channels of the SKA-low station: 33.6 MB of voltages
+        cfg = I.SKA_LOW_STATION_256
+        pos = I.station_layout(cfg)
+        an, tp = I.station_kernel(cfg, pos)
+        C = 16
+        v = I.station_voltages(cfg, pos, device="cuda", n_chan=C)
+        if name == "tc64":
+            lay = hai.hai_layout_create(ctx, an, tp, 64, 2)
+            img = torch.empty((C, 4, 64, 64), device="cuda")
+            for _ in range(2):
+                hai.hai_epic_image(ctx, lay, v, C, cfg.n_time, hai.HAI_PREC_FP16, img, 0)
+        else:
+            N = cfg.n_elem
+            vis = torch.empty((C, N * (N + 1) // 2, 2, 2, 2), dtype=torch.int32, device="cuda")
+            for _ in range(2):
+                hai.hai_correlate(ctx, v, C, cfg.n_time, N, 2, vis, 0)
+    elif name == "tc128":                 # a 700-element station of the uneven array, N = 128
+        sc = I.uneven_station(I.UnevenConfig(), 0, 700)
+        pos = I.station_layout(sc)
+        an, tp = I.station_kernel(sc, pos)
+        lay = hai.hai_layout_create(ctx, an, tp, 128, 2)
+        C, T = 36, 256
+        v = I.random_voltages((C, T, 2, len(pos), 2), seed=5, device="cuda")
+        img = torch.empty((C, 4, 128, 128), device="cuda")
+        for _ in range(2):
+            hai.hai_epic_image(ctx, lay, v, C, T, hai.HAI_PREC_FP16, img, 0)
+    torch.cuda.synchronize()
+    hai.hai_destroy(ctx)
+    print(json.dumps({"case": name, "ok": True}))
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args.case)
+        return
     ws, rank, local = dist_init(args.gpus)
     if args.impl == "reference":
         run_reference(args, ws, rank)
@@ -442,7 +556,7 @@ def main():
         ach = mma_unit * units / (dom_ms * 1e-3) / 1e12
         pk = float(peaks.get("bf16_tflops", 1900.0))
         roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                "traffic": None, "kernel": "epic_tc_kernel",
+                "traffic": traffic_tc64(cfg, C), "kernel": "epic_tc_kernel",
                 "peak_source": "of measured: MEASURED_PEAKS bf16_tflops (burst) x fp16/bf16 nominal ratio 1"
                                if "bf16_tflops" in peaks else "of fallback 1.9 PFLOP/s",
                 "flop_per_unit": mma_unit, "kernel_ms": dom_ms,
@@ -494,6 +608,7 @@ def main():
         del vis
         line["components"]["beamformer"] = bf_component(hai, ctx, flush, peaks)
         line["components"]["batched_uneven"] = plan_component(hai, ctx, flush, peaks, 10)
+        line["components"]["hierarchical"] = hierarchy_component(hai, ctx, flush, peaks)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         hai.hai_epic_image(ctx, lay, volt, C, T, prec, img, 0, st)
         torch.cuda.synchronize()

@@ -224,8 +224,9 @@ hai_status hai_xfft_image(hai_ctx *ctx, const hai_layout *layout, const int32_t 
  *   B^p_k = sum_a conj(w^p_{s,k,a}) E^p_{s,a}(c, t).
  *   volt   device int8 [S][C][T][P][N][2], 16-byte aligned
  *   w      device int8 [S][K][P][N][2]
- *   beams  requant_shift < 0: device int32 [S][C][T][K][P][2], exact;
- *          requant_shift >= 0: device int8, same layout, each component
+ *   beams  16-byte aligned; requant_shift < 0: device int32
+ *          [S][C][T][K][P][2], exact; requant_shift >= 0: device int8, same
+ *          layout, each component
  *          divided by 2^shift rounding half away from zero and clamped to
  *          [-127, 127]
  *   n_saturated  device int64 counter (or NULL), incremented by the number of

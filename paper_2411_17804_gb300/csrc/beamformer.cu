@@ -13,12 +13,14 @@
 //
 // CTA = 12 warps, persistent over a contiguous range of (s, c, tile) units:
 //   warps 0-6  producers: cp.async 16-byte copies of the voltage rows of a
-//              64-element chunk (zero-filled past T) into an int8 ring, then
-//              fp16 widening into the K-major A stage; the station's weights
-//              are widened into B when the station changes;
+//              64-element chunk (zero-filled past T) into a 5-deep int8 ring
+//              (4 chunks, 64 KB, in flight per SM to cover HBM latency), then
+//              fp16 widening into a 2-deep K-major A ring; the station's
+//              weights are widened into B when the station changes;
 //   warp 7     one thread issues the MMAs (8 per chunk);
-//   warps 8-11 epilogue: TMEM -> int32, optional requantisation, writes of
-//              [t][k][p][re, im] rows (contiguous per sample).
+//   warps 8-11 epilogue: TMEM -> int32, optional requantisation; each thread
+//              assembles its sample's [k][p][re, im] row from both pols and
+//              writes it with 16-byte stores (rows are contiguous per unit).
 #include "hai_internal.h"
 #include "tc.cuh"
 
@@ -30,7 +32,9 @@ constexpr int kMmaWarp = 7;
 constexpr int kEpi = 128;              // warps 8-11
 constexpr int kTile = 128;             // samples per unit (MMA M)
 constexpr int kChunkE = 64;            // elements per K chunk (128 real K)
-constexpr int kStages = 3;
+constexpr int kI8Stages = 5;           // int8 landing ring: 4 chunks in flight
+constexpr int kAhead = kI8Stages - 1;
+constexpr int kAStages = 2;            // fp16 operand ring
 constexpr uint32_t kI8Bytes = kTile * kChunkE * 2;   // int8 chunk: 128 rows x 128 B
 constexpr uint32_t kAKs = 128;         // A: K-group stride
 constexpr uint32_t kAMNs = 2048;       // A: row-group stride (16 K groups)
@@ -89,21 +93,21 @@ __device__ __forceinline__ int requant(int x, int shift, int &sat) {
 
 __global__ void __launch_bounds__(kThreads, 1) bf_kernel(const BfParams p) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t mb_full[kStages], mb_empty[kStages], mb_dfull[2], mb_dempty[2];
+    __shared__ __align__(8) uint64_t mb_full[kAStages], mb_empty[kAStages], mb_dfull[2], mb_dempty[2];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nchunk = (p.ne + kChunkE - 1) / kChunkE;        // per polarisation
     const int ne_pad = nchunk * kChunkE;                      // B covers whole chunks, zero-padded
     const uint32_t bmns = (uint32_t)ne_pad * 32u;             // B: row-group stride (2 ne_pad / 8 groups)
     const uint32_t bbytes = (uint32_t)(2 * p.K / 8) * bmns;   // B of one polarisation
-    uint8_t *sI8 = smem;                                      // [kStages][kI8Bytes]
-    uint8_t *sA = smem + kStages * kI8Bytes;                  // [kStages][kABytes]
-    uint8_t *sB = sA + kStages * kABytes;                     // [P][bbytes]
+    uint8_t *sI8 = smem;                                      // [kI8Stages][kI8Bytes]
+    uint8_t *sA = smem + kI8Stages * kI8Bytes;                // [kAStages][kABytes]
+    uint8_t *sB = sA + kAStages * kABytes;                    // [P][bbytes]
     const int ncols = 2 * p.K;                                // MMA N per polarisation
     const uint32_t dcols = (uint32_t)(p.P * ncols);           // TMEM columns per unit
 
     if (tid == 0) {
-        for (int s = 0; s < kStages; s++) {
+        for (int s = 0; s < kAStages; s++) {
             tc::mbar_init(&mb_full[s], kProd);
             tc::mbar_init(&mb_empty[s], 1);
         }
@@ -146,7 +150,7 @@ __global__ void __launch_bounds__(kThreads, 1) bf_kernel(const BfParams p) {
                 const int s = (int)(u / ((long long)p.C * p.tiles));
                 const int c = (int)((u / p.tiles) % p.C);
                 const int t0 = (int)(u % p.tiles) * kTile;
-                uint8_t *dst = sI8 + (q % kStages) * kI8Bytes;
+                uint8_t *dst = sI8 + (q % kI8Stages) * kI8Bytes;
                 for (int it = tid; it < kTile * 8; it += kProd) {      // 128 rows x 8 x 16 B
                     const int t = it >> 3, g = it & 7;
                     const int a0 = kc * kChunkE + g * 8;
@@ -159,23 +163,22 @@ __global__ void __launch_bounds__(kThreads, 1) bf_kernel(const BfParams p) {
             }
             cp_async_commit();
         };
-        issue(0);
-        issue(1);
+        for (int q = 0; q < kAhead; q++) issue(q);
         for (long long q = 0; q < nq; q++, gq++) {
             long long u;
             int pol, kc;
             chunk_src(q, u, pol, kc);
             const int s = (int)(u / ((long long)p.C * p.tiles));
-            issue(q + 2);
-            cp_async_wait<2>();
-            const int slot = (int)(gq % kStages);
-            if (gq >= kStages) tc::mbar_wait(&mb_empty[slot], (uint32_t)(((gq / kStages) - 1) & 1), p.status);
+            issue(q + kAhead);             // its ring slot was drained at the end of iteration q - 1
+            cp_async_wait<kAhead>();
+            const int slot = (int)(gq % kAStages);
+            if (gq >= kAStages) tc::mbar_wait(&mb_empty[slot], (uint32_t)(((gq / kAStages) - 1) & 1), p.status);
             if (s != cur_s) {
                 // new station: every MMA issued so far has completed (the empty
                 // barrier of the previous chunk), so B can be rewritten
                 if (gq >= 1) {
                     const long long pq = gq - 1;
-                    tc::mbar_wait(&mb_empty[pq % kStages], (uint32_t)((pq / kStages) & 1), p.status);
+                    tc::mbar_wait(&mb_empty[pq % kAStages], (uint32_t)((pq / kAStages) & 1), p.status);
                 }
                 for (int it = tid; it < (int)(p.P * bbytes / 16); it += kProd)
                     reinterpret_cast<uint4 *>(sB)[it] = make_uint4(0, 0, 0, 0);
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1) bf_kernel(const BfParams p) {
                 cur_s = s;
             }
             bar_prod();                                        // int8 stage landed for all threads
-            const uint8_t *src = sI8 + (q % kStages) * kI8Bytes;
+            const uint8_t *src = sI8 + (q % kI8Stages) * kI8Bytes;
             uint8_t *A = sA + slot * kABytes;
             for (int it = tid; it < kTile * 8; it += kProd) {  // (row t, 16-byte group g)
                 const int t = (it & 7) | ((it >> 6) << 3), g = (it >> 3) & 7;
@@ -220,8 +223,8 @@ __global__ void __launch_bounds__(kThreads, 1) bf_kernel(const BfParams p) {
                     const uint32_t d = tmem + (uint32_t)b * dcols + (uint32_t)pol * ncols;
                     const uint32_t bb = tc::smem_u32(sB + pol * bbytes);
                     for (int kc = 0; kc < nchunk; kc++, gq++) {
-                        const int slot = (int)(gq % kStages);
-                        tc::mbar_wait(&mb_full[slot], (uint32_t)((gq / kStages) & 1), p.status);
+                        const int slot = (int)(gq % kAStages);
+                        tc::mbar_wait(&mb_full[slot], (uint32_t)((gq / kAStages) & 1), p.status);
                         tc::fence_after();
                         const uint32_t a = tc::smem_u32(sA + slot * kABytes);
 #pragma unroll
@@ -250,29 +253,62 @@ __global__ void __launch_bounds__(kThreads, 1) bf_kernel(const BfParams p) {
             const int c = (int)((u / p.tiles) % p.C);
             const int t = (int)(u % p.tiles) * kTile + t_local;
             const size_t row = (((size_t)s * p.C + c) * p.T + t) * p.K * p.P * 2;   // [s][c][t][k][p][2]
-            for (int pol = 0; pol < p.P; pol++)
-                for (int c0 = 0; c0 < ncols; c0 += 16) {
-                    uint32_t r[16];
-                    tc::tmem_ld16(tmem + lane_base + (uint32_t)b * dcols + (uint32_t)(pol * ncols + c0), r);
-                    tc::tmem_wait_ld();
-                    if (t < p.T) {
+            // 8 beams at a time: both pols' (re, im) of beams k0..k0+7, in output order
+            for (int c0 = 0; c0 < ncols; c0 += 16) {
+                int v[2][16];
 #pragma unroll
-                        for (int j = 0; j < 16; j += 2) {
-                            const int kk = (c0 + j) >> 1;
-                            const int vr = __float2int_rn(__uint_as_float(r[j]));
-                            const int vi = __float2int_rn(__uint_as_float(r[j + 1]));
-                            const size_t o = row + ((size_t)kk * p.P + pol) * 2;
-                            if (p.shift < 0) {
-                                *reinterpret_cast<int2 *>(reinterpret_cast<int32_t *>(p.beams) + o) = make_int2(vr, vi);
-                            } else {
-                                char2 qv;
-                                qv.x = (signed char)requant(vr, p.shift, sat);
-                                qv.y = (signed char)requant(vi, p.shift, sat);
-                                *reinterpret_cast<char2 *>(reinterpret_cast<int8_t *>(p.beams) + o) = qv;
-                            }
-                        }
+                for (int pol = 0; pol < 2; pol++) {
+                    if (pol < p.P) {
+                        uint32_t r[16];
+                        tc::tmem_ld16(tmem + lane_base + (uint32_t)b * dcols + (uint32_t)(pol * ncols + c0), r);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 16; j++) v[pol][j] = __float2int_rn(__uint_as_float(r[j]));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; j++) v[pol][j] = 0;
                     }
                 }
+                if (t >= p.T) continue;
+                const int k0 = c0 >> 1;
+                if (p.shift < 0) {
+                    int32_t *o = reinterpret_cast<int32_t *>(p.beams) + row + (size_t)k0 * p.P * 2;
+                    if (p.P == 2) {
+#pragma unroll
+                        for (int j = 0; j < 8; j++)             // beam k0 + j: X (re, im), Y (re, im)
+                            reinterpret_cast<int4 *>(o)[j] = make_int4(v[0][2 * j], v[0][2 * j + 1], v[1][2 * j],
+                                                                       v[1][2 * j + 1]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; j++)
+                            reinterpret_cast<int4 *>(o)[j] = make_int4(v[0][4 * j], v[0][4 * j + 1], v[0][4 * j + 2],
+                                                                       v[0][4 * j + 3]);
+                    }
+                } else {
+                    uint32_t wds[8];                             // P = 2: 8 words; P = 1: 4
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {                // beam k0 + j
+                        const uint32_t b0 = (uint8_t)requant(v[0][2 * j], p.shift, sat);
+                        const uint32_t b1 = (uint8_t)requant(v[0][2 * j + 1], p.shift, sat);
+                        if (p.P == 2) {
+                            const uint32_t b2 = (uint8_t)requant(v[1][2 * j], p.shift, sat);
+                            const uint32_t b3 = (uint8_t)requant(v[1][2 * j + 1], p.shift, sat);
+                            wds[j] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+                        } else {
+                            const uint32_t h = b0 | (b1 << 8);
+                            if (j & 1) wds[j >> 1] |= h << 16;
+                            else wds[j >> 1] = h;
+                        }
+                    }
+                    int8_t *o = reinterpret_cast<int8_t *>(p.beams) + row + (size_t)k0 * p.P * 2;
+                    if (p.P == 2) {                              // 32 bytes
+                        reinterpret_cast<uint4 *>(o)[0] = make_uint4(wds[0], wds[1], wds[2], wds[3]);
+                        reinterpret_cast<uint4 *>(o)[1] = make_uint4(wds[4], wds[5], wds[6], wds[7]);
+                    } else {                                     // P = 1: 16 bytes
+                        reinterpret_cast<uint4 *>(o)[0] = make_uint4(wds[0], wds[1], wds[2], wds[3]);
+                    }
+                }
+            }
             tc::fence_before();
             tc::mbar_arrive(&mb_dempty[b]);
         }
@@ -302,7 +338,8 @@ extern "C" hai_status hai_beamform(hai_ctx *ctx, const int8_t *volt, const int8_
                         "K a multiple of 8 and <= 64");
     if ((long long)S * C * T == 0) return HAI_OK;
     if (!volt || !w || !beams) return hai_fail(HAI_ERR_INVALID_ARG, "hai_beamform: NULL buffer");
-    if ((((uintptr_t)volt) & 15) != 0) return hai_fail(HAI_ERR_INVALID_ARG, "hai_beamform: volt must be 16-byte aligned");
+    if ((((uintptr_t)volt) & 15) != 0 || (((uintptr_t)beams) & 15) != 0)
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_beamform: volt and beams must be 16-byte aligned");
     if (hai_fault_injected("launch")) return hai_fail(HAI_ERR_CUDA, "hai_beamform: injected launch failure");
     HAI_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
@@ -324,7 +361,7 @@ extern "C" hai_status hai_beamform(hai_ctx *ctx, const int8_t *volt, const int8_
     p.nsat = reinterpret_cast<unsigned long long *>(n_saturated);
     p.status = ctx->d_status;
     const size_t bbytes = (size_t)(2 * K / 8) * ((N + kChunkE - 1) / kChunkE * kChunkE) * 32;
-    const size_t smem = kStages * (kI8Bytes + kABytes) + (size_t)P * bbytes;
+    const size_t smem = kI8Stages * kI8Bytes + kAStages * kABytes + (size_t)P * bbytes;
     if (smem > (size_t)ctx->smem_optin)
         return hai_fail(HAI_ERR_UNSUPPORTED, "hai_beamform: weights of one station exceed shared memory");
     HAI_CUDA_TRY(cudaFuncSetAttribute(bf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

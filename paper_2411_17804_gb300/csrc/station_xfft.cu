@@ -209,21 +209,50 @@ __global__ void __launch_bounds__(kThreads) fft_cols_kernel(float *__restrict__ 
     }
 }
 
-// beams [S][C][T][K][P][2] -> [K][C][T][P][S][2]; one CTA per (c, t).
+// beams [S][C][T][K][P][2] -> [K][C][T][P][S][2]; one CTA per (c, t).  VEC:
+// S and K P multiples of 8, 16-byte aligned buffers: every station's K P
+// values and every output row move as 16-byte vectors through a shared slab
+// [K P][Spad] (rows padded to keep 16-byte alignment).
+template <bool VEC>
 __global__ void __launch_bounds__(256) beams_to_corr_kernel(const char2 *__restrict__ in, int S, int C, int T, int KP,
                                                             int P, char2 *__restrict__ out) {
-    extern __shared__ char2 slab[];    // [K P][S + 1]
+    extern __shared__ __align__(16) char2 slab[];
+    const int Spad = VEC ? ((S + 7) & ~7) + 8 : S + 1;
     const long long ct = blockIdx.x;   // c * T + t
     const int c = (int)(ct / T), t = (int)(ct - (long long)c * T);
-    for (int i = threadIdx.x; i < S * KP; i += blockDim.x) {
-        const int s = i / KP, j = i - s * KP;
-        slab[j * (S + 1) + s] = in[((size_t)s * C * T + ct) * KP + j];
+    if (VEC) {
+        const int vpr = KP / 8;        // vectors per station segment
+        for (int i = threadIdx.x; i < S * vpr; i += blockDim.x) {
+            const int st = i / vpr, j0 = (i - st * vpr) * 8;
+            const uint4 v = reinterpret_cast<const uint4 *>(in + ((size_t)st * C * T + ct) * KP)[i - st * vpr];
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                const uint32_t h = (w[e >> 1] >> (16 * (e & 1))) & 0xffffu;
+                slab[(j0 + e) * Spad + st] = *reinterpret_cast<const char2 *>(&h);
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < S * KP; i += blockDim.x) {
+            const int st = i / KP, j = i - st * KP;
+            slab[j * Spad + st] = in[((size_t)st * C * T + ct) * KP + j];
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < S * KP; i += blockDim.x) {
-        const int j = i / S, s = i - j * S;      // j = (k, p)
-        const int k = j / P, p = j - k * P;
-        out[((((size_t)k * C + c) * T + t) * P + p) * S + s] = slab[j * (S + 1) + s];
+    if (VEC) {
+        const int vpr = S / 8;
+        for (int i = threadIdx.x; i < KP * vpr; i += blockDim.x) {
+            const int j = i / vpr, s0 = (i - j * vpr) * 8;   // j = (k, p)
+            const int k = j / P, p = j - k * P;
+            char2 *o = out + ((((size_t)k * C + c) * T + t) * P + p) * S + s0;
+            *reinterpret_cast<uint4 *>(o) = *reinterpret_cast<const uint4 *>(slab + j * Spad + s0);
+        }
+    } else {
+        for (int i = threadIdx.x; i < S * KP; i += blockDim.x) {
+            const int j = i / S, st = i - j * S;     // j = (k, p)
+            const int k = j / P, p = j - k * P;
+            out[((((size_t)k * C + c) * T + t) * P + p) * S + st] = slab[j * Spad + st];
+        }
     }
 }
 
@@ -438,13 +467,19 @@ extern "C" hai_status hai_beams_to_corr(hai_ctx *ctx, const int8_t *beams, int S
         return hai_fail(HAI_ERR_INVALID_ARG, "hai_beams_to_corr: bad sizes");
     if ((long long)C * T == 0) return HAI_OK;
     if (!beams || !out) return hai_fail(HAI_ERR_INVALID_ARG, "hai_beams_to_corr: NULL buffer");
-    const size_t smem = sizeof(char2) * (size_t)K * P * (S + 1);
+    const bool vec = S % 8 == 0 && (K * P) % 8 == 0 && (((uintptr_t)beams | (uintptr_t)out) & 15) == 0;
+    const size_t smem = sizeof(char2) * (size_t)K * P * (vec ? ((S + 7) & ~7) + 8 : S + 1);
     if (smem > 48 * 1024) return hai_fail(HAI_ERR_UNSUPPORTED, "hai_beams_to_corr: S x K x P too large for one tile");
     if ((long long)C * T > 0x7fffffffll) return hai_fail(HAI_ERR_UNSUPPORTED, "hai_beams_to_corr: too many samples");
     HAI_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
-    beams_to_corr_kernel<<<(unsigned)((long long)C * T), 256, smem, st>>>(reinterpret_cast<const char2 *>(beams), S, C,
-                                                                          T, K * P, P, reinterpret_cast<char2 *>(out));
+    const unsigned grid = (unsigned)((long long)C * T);
+    const char2 *in = reinterpret_cast<const char2 *>(beams);
+    char2 *o = reinterpret_cast<char2 *>(out);
+    if (vec)
+        beams_to_corr_kernel<true><<<grid, 256, smem, st>>>(in, S, C, T, K * P, P, o);
+    else
+        beams_to_corr_kernel<false><<<grid, 256, smem, st>>>(in, S, C, T, K * P, P, o);
     prof_count(ctx, 1);
     HAI_CUDA_TRY(cudaGetLastError());
     return HAI_OK;

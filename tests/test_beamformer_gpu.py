@@ -42,8 +42,8 @@ def test_beamformer_bit_exact(hai, ctx, S, C, T, K, N, P):
     assert np.array_equal(got.astype(np.int64), want)
 
 
-def test_beamformer_requantised(hai, ctx):
-    S, C, T, K, N, P = 2, 2, 130, 16, 256, 2
+@pytest.mark.parametrize("S,C,T,K,N,P", [(2, 2, 130, 16, 256, 2), (1, 2, 70, 8, 64, 1), (2, 1, 260, 24, 96, 2)])
+def test_beamformer_requantised(hai, ctx, S, C, T, K, N, P):
     volt = I.random_voltages((S, C, T, P, N, 2), seed=1)
     w = I.random_voltages((S, K, P, N, 2), seed=2, lo=-127)
     want = O.beamform(volt.numpy(), w.numpy())
