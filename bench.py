@@ -386,6 +386,34 @@ def plan_component(hai, ctx, flush, peaks, steps):
     return out
 
 
+def dense_component(hai, ctx, flush, peaks, sms):
+    """The dense all-sky lattice: 128 x 128 elements at 0.5 lambda, 512^2
+    grid, 16 channels, 2 pols, 100 samples of the seeded sky, through the
+    FP32 large-grid path (row FFTs to an L2 scratch, column FFTs with the
+    squaring).  ALU roofline on the FFT-equivalent work."""
+    import torch
+    from paper_2411_17804_gb300 import inputs as I
+    cfg = I.DENSE_ALLSKY_16384
+    pos = I.station_layout(cfg)
+    anchors, taps = I.station_kernel(cfg, pos)
+    volt = I.station_voltages(cfg, pos, device="cuda")
+    n, C, T, P = cfg.grid_n, cfg.n_chan, cfg.n_time, cfg.n_pol
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, P)
+    img = torch.empty((C, 4, n, n), device="cuda")
+    ms = time_call(lambda st: hai.hai_epic_image(ctx, lay, volt, C, T, hai.HAI_PREC_FP32, img, 0, st), 5, 2, flush)
+    units = cfg.units_per_cadence
+    flop = epic_flops_per_unit(cfg) * units
+    peak = fp32_alu_peak_tflops(sms, float(peaks.get("sm_max_mhz", 2070.0)))
+    ach = flop / (ms * 1e-3) / 1e12
+    hai.hai_layout_destroy(lay)
+    del volt, img
+    return {"workload": cfg.name, "elements": cfg.n_elem, "grid": n, "channels": C, "samples": T, "pols": P,
+            "precision": "fp32", "ms": ms, "units_per_s": units / (ms * 1e-3), "unit": UNIT,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "flop_per_unit": epic_flops_per_unit(cfg),
+                         "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x max SM clock"}}
+
+
 def hierarchy_component(hai, ctx, flush, peaks):
     """The hierarchical workload's cadence: 256 stations x 256 elements, 32
     channels, 2 pols, 1000 samples; int8 beamforming to 16 beams per station
@@ -609,6 +637,7 @@ def main():
         line["components"]["beamformer"] = bf_component(hai, ctx, flush, peaks)
         line["components"]["batched_uneven"] = plan_component(hai, ctx, flush, peaks, 10)
         line["components"]["hierarchical"] = hierarchy_component(hai, ctx, flush, peaks)
+        line["components"]["dense_allsky"] = dense_component(hai, ctx, flush, peaks, sms)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         hai.hai_epic_image(ctx, lay, volt, C, T, prec, img, 0, st)
         torch.cuda.synchronize()

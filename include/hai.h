@@ -104,7 +104,7 @@ hai_status hai_profile_read(hai_ctx *ctx, double *dominant_ms, long long *domina
  * ------------------------------------------------------------------------- */
 typedef struct {
     int n_elem;              /* N_e > 0                                       */
-    int grid_n;              /* N: power of two, 16..64 in this build         */
+    int grid_n;              /* N: power of two, 16..512                       */
     int ksize;               /* K >= 1                                        */
     int n_pol;               /* P: 1 or 2                                     */
     const int32_t *anchors;  /* host [n_elem][2] (x0, y0), copied             */
@@ -130,7 +130,7 @@ hai_status hai_layout_box(const hai_layout *layout, int *box);
  *   volt  device int8 [C][T][P][N_e][2]
  *   img   device float [C][Q][N][N], Q = 1 (P = 1) or 4 (P = 2); overwritten
  *         (accumulate = 0) or added to (accumulate = 1)
- *   prec  HAI_PREC_FP32 (CUDA-core FFT; N = 16, 32 or 64) or HAI_PREC_FP16
+ *   prec  HAI_PREC_FP32 (CUDA-core FFT; N = 16 .. 512) or HAI_PREC_FP16
  *         (tensor cores; N = 32, 64 or 128, P = 2 and a kernel box of at most
  *         N/2 x N/2 cells, else HAI_ERR_UNSUPPORTED)
  * C >= 0, T >= 0 (C = 0 or T = 0: nothing to image; with accumulate = 0 the

@@ -299,6 +299,7 @@ hai_status epic_fp32_launch(const hai_layout *L, const int8_t *volt, int C, int 
                                : launch_n<32, 1>(L, volt, C, T, img, accumulate, st);
     if (n == 64) return p == 2 ? launch_n<64, 2>(L, volt, C, T, img, accumulate, st)
                                : launch_n<64, 1>(L, volt, C, T, img, accumulate, st);
+    if (epic_large_supported(n)) return epic_large_launch(L, volt, C, T, img, accumulate, st);
     return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp32: grid size");
 }
 

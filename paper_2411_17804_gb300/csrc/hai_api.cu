@@ -172,7 +172,7 @@ extern "C" hai_status hai_sync(hai_ctx *ctx, void *stream) {
 }
 
 // ------------------------------------------------------------------ layout
-static bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128; }
+static bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
 
 static void layout_free(hai_layout *L) {
     if (!L) return;
@@ -184,6 +184,7 @@ static void layout_free(hai_layout *L) {
     cudaFree(L->d_partials);
     cudaFree(L->d_tc_tables);
     cudaFree(L->d_tc_station);
+    cudaFree(L->d_large_scratch);
     delete L;
 }
 
@@ -265,9 +266,16 @@ extern "C" hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *d, 
         e = cudaMemcpy(L->d_entry_w, w.data(), sizeof(float2) * L->nnz, cudaMemcpyHostToDevice);
     // partial images of the time split (two channel segments per CTA)
     const int Q = (L->n_pol == 2) ? 4 : 1;
-    L->partial_slots = epic_partial_slots(std::max(epic_fp32_target_ctas(ctx, n), ctx->num_sms));
-    if (e == cudaSuccess)
-        e = cudaMalloc(&L->d_partials, sizeof(float) * L->partial_slots * Q * (size_t)n * n);
+    // time-split partial images (grids up to 128); row scratch of the large-grid FP32 path
+    if (n <= 128) {
+        L->partial_slots = epic_partial_slots(std::max(epic_fp32_target_ctas(ctx, n), ctx->num_sms));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&L->d_partials, sizeof(float) * L->partial_slots * Q * (size_t)n * n);
+    }
+    if (n >= 128 && e == cudaSuccess) {
+        L->large_scratch_bytes = epic_large_scratch_bytes(n, L->box_h);
+        e = cudaMalloc(&L->d_large_scratch, L->large_scratch_bytes);
+    }
     if (e == cudaSuccess && epic_tc_supported(L)) {   // tensor-core path: gather table, station record
         std::vector<uint8_t> tab;
         TcStation rec = {};

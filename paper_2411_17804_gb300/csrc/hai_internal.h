@@ -55,6 +55,9 @@ struct hai_layout {
     size_t tc_blob_bytes = 0;           // whole device table
     long long tc_entries = 0;           // gather entries one CTA runs per sample step
     int tc_groups = 0;                  // CTAs (N = 128: 4-CTA clusters) resident at once
+    // FP32 path of large grids (N >= 128): L2-resident row-transform scratch
+    void *d_large_scratch = nullptr;
+    size_t large_scratch_bytes = 0;
     void *d_tc_station = nullptr;
 };
 
@@ -97,3 +100,9 @@ void epic_tc_station_table(int grid_n, int box_w, int box_h, const std::vector<i
                            long long &entries);
 hai_status epic_reduce_launch(const hai_layout *L, const EpicSplit &sp, int C, int T, float *img,
                               int accumulate, cudaStream_t st);
+// FP32 EPIC for N = 128, 256, 512 (row FFTs to a scratch, then column FFTs,
+// squaring and accumulation).
+bool epic_large_supported(int grid_n);
+size_t epic_large_scratch_bytes(int grid_n, int box_h);
+hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
+                             cudaStream_t st);

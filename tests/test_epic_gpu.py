@@ -245,3 +245,71 @@ def test_tc_unsupported_layout_is_reported(hai, ctx):
         hai.hai_epic_image(ctx, lay, volt, 1, 4, hai.HAI_PREC_FP16, img, 0)
     assert e.value.status == 4
     hai.hai_layout_destroy(lay)
+
+
+# ------------------------------------------------------------------ FP32, large grids (N = 128 .. 512)
+def _dense(n_side=128):
+    cfg = I.DENSE_ALLSKY_16384
+    pos = I.station_layout(cfg)
+    anchors, taps = I.station_kernel(cfg, pos)
+    return cfg, pos, anchors, taps
+
+
+@pytest.mark.parametrize("case,C,T,P", [
+    ("n128", 2, 5, 2),        # a 700-element station of the uneven array
+    ("n256", 3, 7, 2),        # the SKA station on a 256^2 grid
+    ("n512", 2, 3, 2),        # the dense lattice, 128 x 128 box
+    ("n512", 1, 2, 1),        # one polarisation
+    ("n512", 9, 9, 2),        # two sample batches and two channel blocks of the row scratch
+])
+def test_large_grid_fp32_matches_oracle(hai, ctx, case, C, T, P):
+    if case == "n128":
+        sc = I.uneven_station(I.UnevenConfig(), 0, 700)
+        pos, anchors, taps = station(sc)
+        n = 128
+        volt = I.random_voltages((C, T, P, len(pos), 2), seed=C + T)
+    elif case == "n256":
+        pos, anchors, taps = station(I.SKA_LOW_STATION_256)
+        n = 256
+        volt = I.random_voltages((C, T, P, len(pos), 2), seed=C * T)
+    else:
+        cfg, pos, anchors, taps = _dense()
+        n = 512
+        volt = I.random_voltages((C, T, P, len(pos), 2), seed=C + 2 * T)
+    got = run_epic(hai, ctx, anchors, taps, n, volt, hai.HAI_PREC_FP32)
+    want = O.epic_image(n, anchors, taps, volt.numpy())
+    assert rel_err_planes(got, want).max() < FP32_TOL
+    # accumulate onto the first result
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, P)
+    img = torch.from_numpy(got).cuda()
+    hai.hai_epic_image(ctx, lay, volt.cuda(), C, T, hai.HAI_PREC_FP32, img, 1)
+    hai.hai_sync(ctx)
+    assert rel_err_planes(img.cpu().numpy(), 2 * want).max() < FP32_TOL
+    hai.hai_layout_destroy(lay)
+
+
+def test_dense_allsky_full_cadence_sampled_channel(hai, ctx):
+    """The dense all-sky lattice at full size (16,384 elements, 512^2 grid,
+    16 channels, 2 pols, 100 samples of the seeded sky) in one call; the
+    oracle recomputes channel 0."""
+    cfg, pos, anchors, taps = _dense()
+    volt = I.station_voltages(cfg, pos, device="cuda")
+    n, C, T = cfg.grid_n, cfg.n_chan, cfg.n_time
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, 2)
+    img = torch.empty((C, 4, n, n), device="cuda")
+    hai.hai_epic_image(ctx, lay, volt, C, T, hai.HAI_PREC_FP32, img, 0)
+    hai.hai_sync(ctx)
+    hai.hai_layout_destroy(lay)
+    want = O.epic_image(n, anchors, taps, volt[:1].cpu().numpy())
+    assert rel_err_planes(img[:1].cpu().numpy(), want).max() < FP32_TOL
+
+
+def test_large_grid_fp16_is_reported_unsupported(hai, ctx):
+    cfg, pos, anchors, taps = _dense()
+    lay = hai.hai_layout_create(ctx, anchors, taps, 512, 2)
+    volt = torch.zeros((1, 2, 2, len(pos), 2), dtype=torch.int8, device="cuda")
+    img = torch.zeros((1, 4, 512, 512), device="cuda")
+    with pytest.raises(hai.HaiError) as e:
+        hai.hai_epic_image(ctx, lay, volt, 1, 2, hai.HAI_PREC_FP16, img, 0)
+    assert e.value.status == 4
+    hai.hai_layout_destroy(lay)
