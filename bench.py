@@ -192,10 +192,25 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(cfg, anchors, taps, volt_host, gpu_img=None):
+def image_error(got, want):
+    """Per-(channel, plane) relative Frobenius error of GPU images against the
+    oracle's (cross-pol planes measured against the auto planes' scale)."""
+    n_chan = want.shape[0]
+    got = got[:n_chan].astype(np.float64)
+    d = np.linalg.norm((got - want).reshape(n_chan, want.shape[1], -1), axis=-1)
+    r = np.linalg.norm(want.reshape(n_chan, want.shape[1], -1), axis=-1)
+    r = np.maximum(r, 1e-3 * r[:, :2].max(axis=1, keepdims=True))
+    e = d / r
+    return {"metric": "||I_gpu - I_oracle||_F / ||I_oracle||_F per (channel, plane)",
+            "channels": n_chan, "max": float(e.max()), "median": float(np.median(e)),
+            "per_plane_max": [float(x) for x in e.max(axis=0)]}
+
+
+def cpu_baseline(cfg, anchors, taps, volt_host, gpu_imgs=None):
     """FP64 oracle on the host cores over a bounded sample of the workload
     (the first n_chan channels of the cadence).  The oracle's images of that
-    sample also give the per-image error of the GPU images of those channels."""
+    sample also give the per-image error of the GPU images of those channels
+    (one entry per precision in gpu_imgs)."""
     from oracle import oracle as O
     volt = volt_host
     n_chan = volt.shape[0]
@@ -206,17 +221,8 @@ def cpu_baseline(cfg, anchors, taps, volt_host, gpu_img=None):
     out = {"value": units / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
            "sample": f"{n_chan} of {cfg.n_chan} channels x {cfg.n_time} samples of the cadence "
                      f"({dt:.1f} s)"}
-    err = None
-    if gpu_img is not None:
-        got = gpu_img[:n_chan].astype(np.float64)
-        d = np.linalg.norm((got - want).reshape(n_chan, want.shape[1], -1), axis=-1)
-        r = np.linalg.norm(want.reshape(n_chan, want.shape[1], -1), axis=-1)
-        r = np.maximum(r, 1e-3 * r[:, :2].max(axis=1, keepdims=True))
-        e = d / r
-        err = {"metric": "||I_gpu - I_oracle||_F / ||I_oracle||_F per (channel, plane)",
-               "channels": n_chan, "max": float(e.max()), "median": float(np.median(e)),
-               "per_plane_max": [float(x) for x in e.max(axis=0)]}
-    return out, err
+    errs = {k: image_error(v, want) for k, v in (gpu_imgs or {}).items()}
+    return out, errs
 
 
 def run_reference(args, ws, rank):
@@ -614,6 +620,13 @@ def main():
     if fp32 is not None:
         line["plain_fp32"] = fp32
         line["tc_over_fp32"] = value / fp32["value"]
+    if prec == hai.HAI_PREC_FP16 and not args.no_fp32_compare:
+        ns = max(3, args.steps // 4)
+        tsp, _, _ = time_epic(hai, ctx, lay, volt, img, C, T, hai.HAI_PREC_FP16_SPLIT, ns, 2, flush, ws)
+        line["fp16_split"] = {"value": ws * units / (tsp / ns * 1e-3), "unit": UNIT,
+                              "note": "hi/lo split products: FP32-level image error (see image_error_by_precision)"}
+        if fp32 is not None:
+            line["fp16_split"]["over_fp32"] = line["fp16_split"]["value"] / fp32["value"]
     # comparison paths on the same cadence: correlator (exact int8) and XFFT
     if not args.no_components:
         N = cfg.n_elem
@@ -639,11 +652,16 @@ def main():
         line["components"]["hierarchical"] = hierarchy_component(hai, ctx, flush, peaks)
         line["components"]["dense_allsky"] = dense_component(hai, ctx, flush, peaks, sms)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        hai.hai_epic_image(ctx, lay, volt, C, T, prec, img, 0, st)
-        torch.cuda.synchronize()
-        cb, err = cpu_baseline(cfg, anchors, taps, volt[:min(16, C)].cpu().numpy(), gpu_img=img.cpu().numpy())
+        nc = min(16, C)
+        imgs = {}
+        for name, pr in (("main", prec), ("fp16_split", hai.HAI_PREC_FP16_SPLIT), ("fp32", hai.HAI_PREC_FP32)):
+            hai.hai_epic_image(ctx, lay, volt[:nc].contiguous(), nc, T, pr, img[:nc], 0, st)
+            torch.cuda.synchronize()
+            imgs[name] = img[:nc].cpu().numpy()
+        cb, errs = cpu_baseline(cfg, anchors, taps, volt[:nc].cpu().numpy(), gpu_imgs=imgs)
         line["cpu_baseline"] = cb
-        line["image_error_vs_oracle"] = err
+        line["image_error_vs_oracle"] = errs["main"]
+        line["image_error_by_precision"] = {k: {"max": v["max"], "median": v["median"]} for k, v in errs.items()}
     hai.hai_layout_destroy(lay)
     hai.hai_destroy(ctx)
     if rank == 0:

@@ -55,8 +55,11 @@ typedef enum {
 } hai_status;
 
 typedef enum {
-    HAI_PREC_FP32 = 0,   /* FP32 FFT on CUDA cores                              */
-    HAI_PREC_FP16 = 1    /* FP16 DFT-as-GEMM on tcgen05 tensor cores, FP32 acc.  */
+    HAI_PREC_FP32 = 0,      /* FP32 FFT on CUDA cores                              */
+    HAI_PREC_FP16 = 1,      /* FP16 DFT-as-GEMM on tcgen05 tensor cores, FP32 acc.  */
+    HAI_PREC_FP16_SPLIT = 2 /* as FP16 with every operand split into hi + lo fp16
+                               parts and the products hi*hi + hi*lo + lo*hi:
+                               ~FP32 accuracy at 3x the tensor work (N = 32, 64) */
 } hai_precision;
 
 typedef struct hai_ctx hai_ctx;
@@ -130,9 +133,10 @@ hai_status hai_layout_box(const hai_layout *layout, int *box);
  *   volt  device int8 [C][T][P][N_e][2]
  *   img   device float [C][Q][N][N], Q = 1 (P = 1) or 4 (P = 2); overwritten
  *         (accumulate = 0) or added to (accumulate = 1)
- *   prec  HAI_PREC_FP32 (CUDA-core FFT; N = 16 .. 512) or HAI_PREC_FP16
+ *   prec  HAI_PREC_FP32 (CUDA-core FFT; N = 16 .. 512), HAI_PREC_FP16
  *         (tensor cores; N = 32, 64 or 128, P = 2 and a kernel box of at most
- *         N/2 x N/2 cells, else HAI_ERR_UNSUPPORTED)
+ *         N/2 x N/2 cells, else HAI_ERR_UNSUPPORTED) or HAI_PREC_FP16_SPLIT
+ *         (tensor cores, hi/lo split; N = 32 or 64)
  * C >= 0, T >= 0 (C = 0 or T = 0: nothing to image; with accumulate = 0 the
  * image is zeroed). */
 hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *layout, const int8_t *volt,

@@ -55,8 +55,10 @@ constexpr uint32_t kKs = 128;           // K-major operands: K-group stride
 constexpr uint32_t kA2Ks = 2064;        // MN-major A2: K-group stride (16 groups + 16 B pad)
 constexpr uint32_t kA2MNs = 128;        // MN-major A2: MN-group stride
 
-template <int N>
+template <int N, bool SP>
 struct Geo {
+    static constexpr int kSet = SP ? 2 : 1;            // operand copies: hi (and lo)
+    static constexpr int kA2Steps = SP ? 1 : 2;        // stage-2 operand buffering (steps)
     static constexpr int kBox = N / 2;                 // box side
     static constexpr int kFields = 128 / kBox;         // fields per step: 4 or 8
     static constexpr int kSps = kFields / 2;           // samples per step: 2 or 4
@@ -71,9 +73,9 @@ struct Geo {
     static constexpr uint32_t kA1Bytes = 16 * kMNs;    // 128 rows
     static constexpr uint32_t kImgBytes = (kBox / 8) * kMNs;   // one field's rows
     static constexpr uint32_t kA2Bytes = (kK / 8) * kA2Ks;
-    static constexpr uint32_t kOffA1 = kBBytes;
-    static constexpr uint32_t kOffA2 = kOffA1 + 2 * kA1Bytes;
-    static constexpr uint32_t kOffE = kOffA2 + 2 * kTiles * kA2Bytes;
+    static constexpr uint32_t kOffA1 = kSet * kBBytes;                  // B hi [, B lo]
+    static constexpr uint32_t kOffA2 = kOffA1 + 2 * kSet * kA1Bytes;    // A1 [2 buffers][hi, lo]
+    static constexpr uint32_t kOffE = kOffA2 + kA2Steps * kTiles * kSet * kA2Bytes;
     static constexpr uint32_t kTmemCols = (4 * kNcol <= 256) ? 256 : 512;
     static constexpr uint32_t kIdesc1 = tc::idesc_f16(128, kNcol, 0, 0);
     static constexpr uint32_t kIdesc2 = tc::idesc_f16(128, kNcol, 1, 0);
@@ -98,12 +100,12 @@ struct Params {
 __device__ __forceinline__ void bar_front() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
 __device__ __forceinline__ void bar_epi() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
 
-template <int N>
+template <int N, bool SP>
 __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
-    using G = Geo<N>;
+    using G = Geo<N, SP>;
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t mb_v[kStages];
-    __shared__ __align__(8) uint64_t mb_a1[2], mb_d1[2], mb_a2[2], mb_full[2], mb_empty[2];
+    __shared__ __align__(8) uint64_t mb_a1[2], mb_d1[2], mb_a2[2], mb_full[2], mb_empty[2], mb_a2free;
     __shared__ uint32_t tmem_slot;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
     uint8_t *sT = smem + off_v + kStages * p.vstage;         // the current station's gather table
 
     // ---- set-up: DFT operand, barriers, TMEM
-    for (int i = tid; i < (int)(G::kBBytes / 16); i += kThreads)
+    for (int i = tid; i < (int)(G::kSet * G::kBBytes / 16); i += kThreads)
         reinterpret_cast<int4 *>(sB)[i] = __ldg(reinterpret_cast<const int4 *>(p.dft) + i);
     if (tid == 0) {
         for (int s = 0; s < kStages; s++) tc::mbar_init(&mb_v[s], 1);
@@ -127,6 +129,7 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
             tc::mbar_init(&mb_full[b], 1);
             tc::mbar_init(&mb_empty[b], kEpi);
         }
+        tc::mbar_init(&mb_a2free, 1);
         tc::mbar_fence_init();
     }
     if (warp == 0) tc::tmem_alloc(&tmem_slot, G::kTmemCols);
@@ -172,8 +175,8 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
                 cur_station = stn;
             }
             if ((b ? a1_st1 : a1_st0) != stn) {
-                for (int k = tid; k < (int)(G::kA1Bytes / 16); k += kFront)
-                    reinterpret_cast<int4 *>(sA1 + b * G::kA1Bytes)[k] = make_int4(0, 0, 0, 0);
+                for (int k = tid; k < (int)(G::kSet * G::kA1Bytes / 16); k += kFront)
+                    reinterpret_cast<int4 *>(sA1 + b * G::kSet * G::kA1Bytes)[k] = make_int4(0, 0, 0, 0);
                 (b ? a1_st1 : a1_st0) = stn;
             }
             bar_front();
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
         // gridded values of the step's fields: G_f[cell] = sum conj(W~) E_f,
         // one cell per lane, one tile of 32 cells per warp at a time
         auto grid_step = [&](int i) {
-            uint8_t *A = sA1 + (i & 1) * G::kA1Bytes;
+            uint8_t *A = sA1 + (i & 1) * G::kSet * G::kA1Bytes;
             const uint4 *E = sE + (size_t)(i & 1) * p.ne_max * G::kU;
             for (int t = s_warp[warp]; t < s_warp[warp + 1]; t++) {
                 float2 g[G::kFields];
@@ -253,8 +256,15 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
                 if (off != 0xffffffffu) {
                     uint8_t *c = A + off;
 #pragma unroll
-                    for (int f = 0; f < G::kFields; f++)
-                        *reinterpret_cast<uint32_t *>(c + f * G::kImgBytes) = tc::pack_half2(g[f].x, g[f].y);
+                    for (int f = 0; f < G::kFields; f++) {
+                        const uint32_t hi = tc::pack_half2(g[f].x, g[f].y);
+                        *reinterpret_cast<uint32_t *>(c + f * G::kImgBytes) = hi;
+                        if (SP) {              // the rounding remainder as the lo copy
+                            const float2 back = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
+                            *reinterpret_cast<uint32_t *>(c + G::kA1Bytes + f * G::kImgBytes) =
+                                tc::pack_half2(g[f].x - back.x, g[f].y - back.y);
+                        }
+                    }
                 }
             }
         };
@@ -266,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
             const int smp = f >> 1, pol = f & 1;
             const int tile = smp / G::kTileSamples, s2 = smp % G::kTileSamples;
             if (tile * G::kTileSamples >= s.nv) return;   // tile not issued
-            uint8_t *A2 = sA2 + ((i & 1) * G::kTiles + tile) * G::kA2Bytes;
+            uint8_t *A2 = sA2 + (((i % G::kA2Steps) * G::kTiles + tile) * G::kSet) * G::kA2Bytes;
             const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(i & 1) * G::kNcol;
 #pragma unroll
             for (int ch = 0; ch < G::kNcol / 32; ch++) {   // 32 columns: component c, l_x = kx0 .. kx0+31
@@ -279,12 +289,19 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
                 for (int h = 0; h < 4; h++) {      // 8 frequencies -> one 16-byte row of A2
                     const int kx = kx0 + 8 * h;
                     const int m2 = s2 * 2 * N + (kx >> 4) * 32 + pol * 16 + (kx & 15);
-                    uint4 v;
-                    v.x = tc::pack_half2(__uint_as_float(r[8 * h + 0]), __uint_as_float(r[8 * h + 1]));
-                    v.y = tc::pack_half2(__uint_as_float(r[8 * h + 2]), __uint_as_float(r[8 * h + 3]));
-                    v.z = tc::pack_half2(__uint_as_float(r[8 * h + 4]), __uint_as_float(r[8 * h + 5]));
-                    v.w = tc::pack_half2(__uint_as_float(r[8 * h + 6]), __uint_as_float(r[8 * h + 7]));
-                    *reinterpret_cast<uint4 *>(A2 + tc::off_mnmajor(m2, kappa, kA2Ks, kA2MNs)) = v;
+                    uint32_t hv[4], lv[4];
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const float x0 = __uint_as_float(r[8 * h + 2 * e]), x1 = __uint_as_float(r[8 * h + 2 * e + 1]);
+                        hv[e] = tc::pack_half2(x0, x1);
+                        if (SP) {
+                            const float2 back = __half22float2(*reinterpret_cast<const __half2 *>(&hv[e]));
+                            lv[e] = tc::pack_half2(x0 - back.x, x1 - back.y);
+                        }
+                    }
+                    const uint32_t off = tc::off_mnmajor(m2, kappa, kA2Ks, kA2MNs);
+                    *reinterpret_cast<uint4 *>(A2 + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                    if (SP) *reinterpret_cast<uint4 *>(A2 + G::kA2Bytes + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                 }
             }
         };
@@ -305,6 +322,8 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
             }
             if (i >= 0 && warp < 4) {
                 tc::mbar_wait(&mb_d1[i & 1], (uint32_t)((i >> 1) & 1), p.status);
+                // one stage-2 operand buffer (split): the MMAs of step i-1 read it
+                if (SP && i >= 1) tc::mbar_wait(&mb_a2free, (uint32_t)((i - 1) & 1), p.status);
                 tc::fence_after();
                 convert(prev, i);
                 tc::fence_proxy_async();
@@ -343,12 +362,17 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
                     tc::mbar_wait(&mb_a1[i & 1], (uint32_t)((i >> 1) & 1), p.status);
                     issue_load();                  // its voltage stage has been widened
                     tc::fence_after();
-                    const uint32_t a = tc::smem_u32(sA1 + (i & 1) * G::kA1Bytes);
+                    const uint32_t a = tc::smem_u32(sA1 + (i & 1) * G::kSet * G::kA1Bytes);
                     const uint32_t d = tmem + (uint32_t)(i & 1) * G::kNcol;
+                    // products hi*hi [+ hi*lo + lo*hi]: (A offset, B offset) per product
 #pragma unroll
-                    for (int s = 0; s < G::kK / 16; s++)
-                        tc::mma_f16(d, tc::desc(a + s * 2 * kKs, kKs, G::kMNs), tc::desc(b + s * 2 * kKs, kKs, G::kMNs),
-                                    G::kIdesc1, s > 0);
+                    for (int pr = 0; pr < (SP ? 3 : 1); pr++) {
+                        const uint32_t ao = pr == 2 ? G::kA1Bytes : 0u, bo = pr == 1 ? G::kBBytes : 0u;
+#pragma unroll
+                        for (int s = 0; s < G::kK / 16; s++)
+                            tc::mma_f16(d, tc::desc(a + ao + s * 2 * kKs, kKs, G::kMNs),
+                                        tc::desc(b + bo + s * 2 * kKs, kKs, G::kMNs), G::kIdesc1, (pr > 0 || s > 0));
+                    }
                     tc::mma_commit(&mb_d1[i & 1]);
                 }
                 if (k >= 0) {                      // stage 2 of step k, one slot per tile
@@ -358,14 +382,20 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
                         const int slot = jt & 1;
                         if (jt >= 2) tc::mbar_wait(&mb_empty[slot], (uint32_t)(((jt >> 1) - 1) & 1), p.status);
                         tc::fence_after();
-                        const uint32_t a = tc::smem_u32(sA2 + ((k & 1) * G::kTiles + g) * G::kA2Bytes);
+                        const uint32_t a =
+                            tc::smem_u32(sA2 + (((k % G::kA2Steps) * G::kTiles + g) * G::kSet) * G::kA2Bytes);
                         const uint32_t d = tmem + 2u * G::kNcol + (uint32_t)slot * G::kNcol;
 #pragma unroll
-                        for (int s = 0; s < G::kK / 16; s++)
-                            tc::mma_f16(d, tc::desc(a + s * 2 * kA2Ks, kA2Ks, kA2MNs),
-                                        tc::desc(b + s * 2 * kKs, kKs, G::kMNs), G::kIdesc2, s > 0);
+                        for (int pr = 0; pr < (SP ? 3 : 1); pr++) {
+                            const uint32_t ao = pr == 2 ? G::kA2Bytes : 0u, bo = pr == 1 ? G::kBBytes : 0u;
+#pragma unroll
+                            for (int s = 0; s < G::kK / 16; s++)
+                                tc::mma_f16(d, tc::desc(a + ao + s * 2 * kA2Ks, kA2Ks, kA2MNs),
+                                            tc::desc(b + bo + s * 2 * kKs, kKs, G::kMNs), G::kIdesc2, (pr > 0 || s > 0));
+                        }
                         tc::mma_commit(&mb_full[slot]);
                     }
+                    if (SP) tc::mma_commit(&mb_a2free);   // the single stage-2 operand may be rewritten
                 }
                 prev = nxt;
             }
@@ -478,17 +508,28 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
     if (warp == 0) tc::tmem_dealloc(tmem, G::kTmemCols);
 }
 
-template <int N>
+template <int N, bool SP>
 size_t smem_bytes(int ne_max, uint32_t table_max) {
-    using G = Geo<N>;
+    using G = Geo<N, SP>;
     const uint32_t vstage = ((uint32_t)G::kSps * 4u * ne_max + 16u + 15u) & ~15u;
     return G::kOffE + 32ull * G::kU * ne_max + (size_t)kStages * vstage + table_max;
 }
 
-template <int N>
+// Dynamic shared memory a kernel may use: the device's opt-in limit less the
+// kernel's static shared memory.
+template <typename K>
+hai_status raise_limit(hai_ctx *ctx, K kern) {
+    cudaFuncAttributes a;
+    HAI_CUDA_TRY(cudaFuncGetAttributes(&a, kern));
+    HAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      ctx->smem_optin - (int)a.sharedSizeBytes));
+    return HAI_OK;
+}
+
+template <int N, bool SP>
 hai_status run_n(hai_ctx *ctx, const TcLaunch &l, cudaStream_t st) {
-    using G = Geo<N>;
-    const size_t smem = smem_bytes<N>(l.ne_max, l.table_max);
+    using G = Geo<N, SP>;
+    const size_t smem = smem_bytes<N, SP>(l.ne_max, l.table_max);
     if (smem + kStaticSmem > (size_t)ctx->smem_optin)
         return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16: shared memory need exceeds the device limit");
     const void *dft = epic_tc_dft(ctx, N);
@@ -496,6 +537,10 @@ hai_status run_n(hai_ctx *ctx, const TcLaunch &l, cudaStream_t st) {
     // the limit is the device's, so launches of any size (and captured graphs) stay valid
     if (!l.no_attr) {
         const hai_status s = epic_tc_set_attr(ctx, N);
+        if (s != HAI_OK) return s;
+    }
+    if (SP) {
+        const hai_status s = raise_limit(ctx, epic_tc_kernel<N, true>);
         if (s != HAI_OK) return s;
     }
     Params p;
@@ -519,7 +564,7 @@ hai_status run_n(hai_ctx *ctx, const TcLaunch &l, cudaStream_t st) {
     p.partials = l.partials;
     p.status = ctx->d_status;
     const int pidx = prof_begin(ctx, st);
-    epic_tc_kernel<N><<<l.n_cta, kThreads, smem, st>>>(p);
+    epic_tc_kernel<N, SP><<<l.n_cta, kThreads, smem, st>>>(p);
     prof_end(ctx, pidx, st);
     prof_count(ctx, 1);
     HAI_CUDA_TRY(cudaGetLastError());
@@ -530,40 +575,34 @@ hai_status run_n(hai_ctx *ctx, const TcLaunch &l, cudaStream_t st) {
 
 void epic_tc_a1_strides(int N, uint32_t &k_stride, uint32_t &mn_stride) {
     k_stride = kKs;
-    mn_stride = (N == 32) ? Geo<32>::kMNs : (N == 64) ? Geo<64>::kMNs : 16 * kKs;   // N = 128: K = 128
+    mn_stride = (N == 32) ? Geo<32, false>::kMNs : (N == 64) ? Geo<64, false>::kMNs : 16 * kKs;   // N = 128: K = 128
 }
 
 int epic_tc_group(int N) { return N == 128 ? 4 : 1; }
 
 size_t epic_tc_smem(hai_ctx *, int N, int ne_max, uint32_t table_max) {
-    if (N == 32) return smem_bytes<32>(ne_max, table_max);
-    if (N == 64) return smem_bytes<64>(ne_max, table_max);
+    if (N == 32) return smem_bytes<32, false>(ne_max, table_max);
+    if (N == 64) return smem_bytes<64, false>(ne_max, table_max);
     if (N == 128) return epic_tc128_smem(ne_max, table_max);
     return (size_t)-1;
 }
 
-// Dynamic shared memory a kernel may use: the device's opt-in limit less the
-// kernel's static shared memory.
-template <typename K>
-hai_status raise_limit(hai_ctx *ctx, K kern) {
-    cudaFuncAttributes a;
-    HAI_CUDA_TRY(cudaFuncGetAttributes(&a, kern));
-    HAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      ctx->smem_optin - (int)a.sharedSizeBytes));
-    return HAI_OK;
-}
-
 hai_status epic_tc_set_attr(hai_ctx *ctx, int N) {
-    if (N == 32) return raise_limit(ctx, epic_tc_kernel<32>);
-    if (N == 64) return raise_limit(ctx, epic_tc_kernel<64>);
+    if (N == 32) return raise_limit(ctx, epic_tc_kernel<32, false>);
+    if (N == 64) return raise_limit(ctx, epic_tc_kernel<64, false>);
     if (N == 128) return epic_tc128_set_attr(ctx);
     return HAI_OK;
 }
 
 hai_status epic_tc_run(hai_ctx *ctx, int N, const TcLaunch &l, cudaStream_t st) {
     if (l.n_cta <= 0) return HAI_OK;
-    if (N == 32) return run_n<32>(ctx, l, st);
-    if (N == 64) return run_n<64>(ctx, l, st);
+    if (l.split) {
+        if (N == 32) return run_n<32, true>(ctx, l, st);
+        if (N == 64) return run_n<64, true>(ctx, l, st);
+        return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16 split: this build has the hi/lo variant for N = 32 and 64");
+    }
+    if (N == 32) return run_n<32, false>(ctx, l, st);
+    if (N == 64) return run_n<64, false>(ctx, l, st);
     if (N == 128) return epic_tc128_run(ctx, l, st);
     return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16: grid size");
 }
@@ -592,12 +631,18 @@ hai_status epic_tc_dft_prepare(hai_ctx *ctx, int N) {
         memcpy(&out[base + off], &hv, 2);
     };
     if (N <= 64) {
+        // hi = fp16(W'), then lo = fp16(W' - hi) for the split variant
         const int box = N / 2, K = 2 * box;
         const uint32_t mns = (uint32_t)(K / 8) * kKs;
-        out.assign((size_t)(2 * N / 8) * mns, 0);
+        const size_t half_bytes = (size_t)(2 * N / 8) * mns;
+        out.assign(2 * half_bytes, 0);
         for (int n = 0; n < 2 * N; n++)
-            for (int kappa = 0; kappa < K; kappa++)
-                put(0, tc::off_kmajor(n, kappa, kKs, mns), epic_tc_dft_entry(N, n / N, n % N, kappa >> 1, kappa & 1));
+            for (int kappa = 0; kappa < K; kappa++) {
+                const double v = epic_tc_dft_entry(N, n / N, n % N, kappa >> 1, kappa & 1);
+                const double hi = (double)__half2float(__double2half(v));
+                put(0, tc::off_kmajor(n, kappa, kKs, mns), v);
+                put(half_bytes, tc::off_kmajor(n, kappa, kKs, mns), v - hi);
+            }
     } else {
         const uint32_t mns = 16 * kKs;              // K = 128
         const size_t qbytes = 8 * (size_t)mns;     // 64 rows
@@ -716,7 +761,7 @@ bool epic_tc_supported(const hai_layout *L) {
 }
 
 hai_status epic_tc_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
-                          cudaStream_t st) {
+                          cudaStream_t st, int split) {
     if (!epic_tc_supported(L) || !L->d_tc_station)
         return hai_fail(HAI_ERR_UNSUPPORTED,
                         "epic fp16: the tensor-core path needs N = 32, 64 or 128, 2 pols and a kernel box "
@@ -743,6 +788,7 @@ hai_status epic_tc_launch(const hai_layout *L, const int8_t *volt, int C, int T,
     l.guard = 0;
     l.partials = L->d_partials;
     l.no_attr = 0;
+    l.split = split;
     const hai_status s = epic_tc_run(ctx, N, l, st);
     if (s != HAI_OK) return s;
     if (!sp.direct) return epic_reduce_launch(L, sp, C, T, img, accumulate, st);

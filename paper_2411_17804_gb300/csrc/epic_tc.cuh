@@ -177,6 +177,7 @@ struct TcLaunch {
     int direct, accumulate, guard;
     float *partials;
     int no_attr;            // 1: the kernel's shared-memory attribute is already set
+    int split;              // 1: hi/lo split products (N = 32, 64)
 };
 // Raises the kernel's dynamic shared-memory limit to the device's.
 hai_status epic_tc_set_attr(hai_ctx *ctx, int N);

@@ -345,7 +345,7 @@ extern "C" hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *L, const in
     if (C < 0 || T < 0) return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: negative C or T");
     if (accumulate != 0 && accumulate != 1)
         return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: accumulate must be 0 or 1");
-    if (prec != HAI_PREC_FP32 && prec != HAI_PREC_FP16)
+    if (prec != HAI_PREC_FP32 && prec != HAI_PREC_FP16 && prec != HAI_PREC_FP16_SPLIT)
         return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: unknown precision");
     if (C == 0) return HAI_OK;
     if (!img || (T > 0 && !volt)) return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: NULL buffer");
@@ -359,5 +359,5 @@ extern "C" hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *L, const in
         return HAI_OK;
     }
     if (prec == HAI_PREC_FP32) return epic_fp32_launch(L, volt, C, T, img, accumulate, st);
-    return epic_tc_launch(L, volt, C, T, img, accumulate, st);
+    return epic_tc_launch(L, volt, C, T, img, accumulate, st, prec == HAI_PREC_FP16_SPLIT ? 1 : 0);
 }

@@ -90,7 +90,7 @@ hai_status epic_fp32_launch(const hai_layout *L, const int8_t *volt, int C, int 
                             int accumulate, cudaStream_t st);
 int epic_fp32_target_ctas(const hai_ctx *ctx, int grid_n);
 hai_status epic_tc_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img,
-                          int accumulate, cudaStream_t st);
+                          int accumulate, cudaStream_t st, int split);
 bool epic_tc_supported(const hai_layout *L);
 // Gather table of a layout for the tensor-core kernel of its grid side;
 // shared_bytes = what the kernel keeps in shared memory.

@@ -179,6 +179,7 @@ TcLaunch class_launch(const hai_plan *p, const PlanClass &c, const int8_t *volt,
     l.guard = 1;
     l.partials = nullptr;
     l.no_attr = 1;
+    l.split = 0;
     return l;
 }
 

@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "HAI_OK", 1: "HAI_ERR_INVALID_ARG", 2: "HAI_ERR_OFF_GRID",
                 6: "HAI_ERR_TIMEOUT", 7: "HAI_ERR_NO_MEMORY"}
 HAI_PREC_FP32 = 0
 HAI_PREC_FP16 = 1
+HAI_PREC_FP16_SPLIT = 2
 
 
 class HaiError(RuntimeError):

@@ -313,3 +313,40 @@ def test_large_grid_fp16_is_reported_unsupported(hai, ctx):
         hai.hai_epic_image(ctx, lay, volt, 1, 2, hai.HAI_PREC_FP16, img, 0)
     assert e.value.status == 4
     hai.hai_layout_destroy(lay)
+
+
+# ------------------------------------------------------------------ FP16 split hi/lo
+@pytest.mark.parametrize("n_elem,C,T,cplx", [(256, 3, 40, False), (256, 2, 301, True), (50, 5, 9, False),
+                                              (300, 1, 1, True)])
+def test_tc_split_recovers_fp32_accuracy(hai, ctx, n_elem, C, T, cplx):
+    """Every operand as hi + lo fp16 and the products hi*hi + hi*lo + lo*hi:
+    the images meet the FP32 bound and are far closer to the oracle than the
+    plain FP16 path's."""
+    if n_elem == 256:
+        sc = I.SKA_LOW_STATION_256
+    else:
+        sc = I.uneven_station(I.UnevenConfig(), 0, n_elem)
+    pos, anchors, taps = station(sc)
+    if cplx:
+        taps = taps.copy()
+        taps[..., 1] = 0.3 * np.random.default_rng(n_elem).standard_normal(taps.shape[:-1]).astype(np.float32)
+    volt = I.station_voltages(sc, pos, n_chan=C, n_time=T) if not cplx else \
+        I.random_voltages((C, T, 2, len(pos), 2), seed=C + T)
+    want = O.epic_image(sc.grid_n, anchors, taps, volt.numpy())
+    split = run_epic(hai, ctx, anchors, taps, sc.grid_n, volt, hai.HAI_PREC_FP16_SPLIT)
+    plain = run_epic(hai, ctx, anchors, taps, sc.grid_n, volt, hai.HAI_PREC_FP16)
+    e_split, e_plain = rel_err_planes(split, want).max(), rel_err_planes(plain, want).max()
+    assert e_split < FP32_TOL, e_split
+    assert e_split < e_plain / 20, (e_split, e_plain)
+
+
+def test_tc_split_unsupported_at_128(hai, ctx):
+    sc = I.uneven_station(I.UnevenConfig(), 0, 700)
+    pos, anchors, taps = station(sc)
+    lay = hai.hai_layout_create(ctx, anchors, taps, 128, 2)
+    volt = torch.zeros((1, 2, 2, len(pos), 2), dtype=torch.int8, device="cuda")
+    img = torch.zeros((1, 4, 128, 128), device="cuda")
+    with pytest.raises(hai.HaiError) as e:
+        hai.hai_epic_image(ctx, lay, volt, 1, 2, hai.HAI_PREC_FP16_SPLIT, img, 0)
+    assert e.value.status == 4
+    hai.hai_layout_destroy(lay)
