@@ -11,16 +11,22 @@
 // Only the lower triangle a >= b is stored; the pair (b, a) contributes
 // conj(V^{beta alpha}_{ab} K_ab[d]) at lag -d (Hermitian mirror).
 //
-// One CTA per channel holds the grids of the needed polarisation products
-// (XX, YY, XY) in shared memory as FP32, adds every baseline's 2 (2K-1)^2
-// terms with shared-memory atomics, then runs the 2D FFTs in place.
+// A cluster of kRanks CTAs per channel: every CTA holds the grids of the
+// needed polarisation products (XX, YY, XY) in shared memory as FP32 and adds
+// its share of the baselines' 2 (2K-1)^2 terms with shared-memory atomics;
+// the other CTAs then add their grids into rank 0's through distributed
+// shared memory, and rank 0 runs the 2D FFTs in place.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "hai_internal.h"
 
+namespace cg = cooperative_groups;
+
 namespace {
 
 constexpr int kThreads = 512;
+constexpr int kRanks = 4;              // CTAs per channel (one cluster)
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -56,18 +62,20 @@ __device__ void fft_line(float2 *x, int s) {
 }
 
 template <int N>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1)
 xfft_kernel(const int32_t *__restrict__ vis, int ne, int P, int K, const int32_t *__restrict__ anchors,
             const float2 *__restrict__ taps, float *__restrict__ img, int accumulate) {
     extern __shared__ __align__(16) float2 grid[];          // [np][N][N]
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
     const int np = (P == 2) ? 3 : 1;                         // XX, YY, XY
-    const int c = blockIdx.x;
+    const int c = blockIdx.x / kRanks;
     const long long nbl = (long long)ne * (ne + 1) / 2;
     for (int i = threadIdx.x; i < np * N * N; i += kThreads) grid[i] = make_float2(0.f, 0.f);
     __syncthreads();
 
     const int W = 2 * K - 1;
-    for (long long bl = threadIdx.x; bl < nbl; bl += kThreads) {
+    for (long long bl = (long long)rank * kThreads + threadIdx.x; bl < nbl; bl += (long long)kRanks * kThreads) {
         // baseline index -> (a, b), a >= b
         int a = (int)((sqrt(8.0 * (double)bl + 1.0) - 1.0) * 0.5);
         while ((long long)(a + 1) * (a + 2) / 2 <= bl) a++;
@@ -109,7 +117,15 @@ xfft_kernel(const int32_t *__restrict__ vis, int ne, int P, int K, const int32_t
                 (void)W;
             }
     }
-    __syncthreads();
+    // the other ranks' grids into rank 0's
+    cluster.sync();
+    if (rank != 0) {
+        float *dst = reinterpret_cast<float *>(cluster.map_shared_rank(grid, 0));
+        const float *src = reinterpret_cast<const float *>(grid);
+        for (int i = threadIdx.x; i < 2 * np * N * N; i += kThreads) atomicAdd(&dst[i], src[i]);
+    }
+    cluster.sync();
+    if (rank != 0) return;
     // (-1)^(dx+dy), then rows and columns
     for (int i = threadIdx.x; i < np * N * N; i += kThreads) {
         const int dx = i % N, dy = (i / N) % N;
@@ -151,8 +167,8 @@ hai_status launch(const hai_layout *L, const int32_t *vis, int C, float *img, in
         return hai_fail(HAI_ERR_UNSUPPORTED, "hai_xfft_image: grid does not fit in shared memory");
     HAI_CUDA_TRY(cudaFuncSetAttribute(xfft_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int pidx = prof_begin(L->ctx, st);
-    xfft_kernel<N><<<C, kThreads, smem, st>>>(vis, L->n_elem, L->n_pol, L->ksize, L->d_anchors, L->d_taps, img,
-                                              accumulate);
+    xfft_kernel<N><<<C * kRanks, kThreads, smem, st>>>(vis, L->n_elem, L->n_pol, L->ksize, L->d_anchors, L->d_taps,
+                                                       img, accumulate);
     prof_end(L->ctx, pidx, st);
     prof_count(L->ctx, 1);
     HAI_CUDA_TRY(cudaGetLastError());
