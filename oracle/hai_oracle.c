@@ -28,6 +28,10 @@
  *     (autos included) gridded with the autocorrelation of the element
  *     kernels, K_ab[d] = sum_j g_a[j + d] conj(g_b[j]), g_a = placed conj taps,
  *     on the circular N grid, then the same (-1)^d and DFT as EPIC.
+ *   - FFT correlator (Section 4.1.2, Section 5.2.2): the inverse DFT of the
+ *     accumulated EPIC image planes, normalised by 1/N^2 and multiplied by
+ *     (-1)^d, read as gridded visibilities at the lags d (zero lag at cell
+ *     (0, 0)).
  *   - inter-station XFFT (Eq. inter-station XFFT): station visibilities
  *     phased towards the beam direction with exp(+2 pi i s_k.dr / lambda) in
  *     FP64, gridded with a 2x2 bilinear kernel at uv = dr / cell; pairs whose
@@ -332,24 +336,26 @@ void orc_vis_kernel(int k, const int32_t *anchors, const float *taps, int a, int
         }
 }
 
-int orc_xfft_image(int n, int ne, int k, const int32_t *anchors, const float *taps,
-                   const int64_t *vis, int C, int P, double *img) {
+/* Gridded visibilities of Eq. intra-station XFFT (the bracket): for every
+ * (channel, alpha, beta) the grid sum over all ordered pairs (a, b), autos
+ * included, of V^{alpha beta}_{ab} K_ab[d] at the lags d on the circular n
+ * grid (cell (d_x mod n, d_y mod n) of a row-major [n][n] grid).
+ * grid [C][P][P][n][n][2]. */
+int orc_xfft_grid(int n, int ne, int k, const int32_t *anchors, const float *taps,
+                  const int64_t *vis, int C, int P, double *grid) {
     if (!is_pow2(n) || n < 4 || ne <= 0 || k <= 0 || C < 0 || P < 1 || P > 2) return ORC_ERR_ARG;
     if (orc_check_layout(n, ne, k, anchors)) return ORC_ERR_OFF_GRID;
     const long nn = (long)n * n, nbl = (long)ne * (ne + 1) / 2;
     const int w2 = 2 * k - 1;
-    memset(img, 0, sizeof(double) * (size_t)C * P * P * nn * 2);
+    memset(grid, 0, sizeof(double) * (size_t)C * P * P * nn * 2);
 #pragma omp parallel
     {
         double *kab = (double *)malloc(sizeof(double) * 2 * w2 * w2);
-        double *gr = (double *)malloc(sizeof(double) * nn);
-        double *gi = (double *)malloc(sizeof(double) * nn);
 #pragma omp for collapse(3) schedule(dynamic, 1)
         for (int c = 0; c < C; c++)
             for (int al = 0; al < P; al++)
                 for (int be = 0; be < P; be++) {
-                    memset(gr, 0, sizeof(double) * nn);
-                    memset(gi, 0, sizeof(double) * nn);
+                    double *g = grid + ((((size_t)c * P + al) * P + be) * nn) * 2;
                     /* every ordered pair (a, b), autos included */
                     for (int a = 0; a < ne; a++)
                         for (int b = 0; b < ne; b++) {
@@ -372,19 +378,93 @@ int orc_xfft_image(int n, int ne, int k, const int32_t *anchors, const float *ta
                                     /* lag wrapped onto the circular n grid */
                                     int cx = ((dx0 + ex) % n + n) % n, cy = ((dy0 + ey) % n + n) % n;
                                     long cell = (long)cy * n + cx;
-                                    gr[cell] += vr * kk[0] - vi * kk[1];
-                                    gi[cell] += vr * kk[1] + vi * kk[0];
+                                    g[2 * cell] += vr * kk[0] - vi * kk[1];
+                                    g[2 * cell + 1] += vr * kk[1] + vi * kk[0];
                                 }
                         }
-                    checkerboard(n, gr, gi);
-                    orc_fft2d(n, gr, gi);
-                    double *o = img + ((((size_t)c * P + al) * P + be) * nn) * 2;
-                    for (long l = 0; l < nn; l++) {
-                        o[2 * l] = gr[l];
-                        o[2 * l + 1] = gi[l];
-                    }
                 }
         free(kab);
+    }
+    return ORC_OK;
+}
+
+/* Dirty image of Eq. intra-station XFFT: the gridded visibilities, then the
+ * same (-1)^d and DFT (+) as EPIC.  img [C][P][P][n][n][2]. */
+int orc_xfft_image(int n, int ne, int k, const int32_t *anchors, const float *taps,
+                   const int64_t *vis, int C, int P, double *img) {
+    int rc = orc_xfft_grid(n, ne, k, anchors, taps, vis, C, P, img);
+    if (rc != ORC_OK) return rc;
+    const long nn = (long)n * n;
+#pragma omp parallel
+    {
+        double *gr = (double *)malloc(sizeof(double) * nn);
+        double *gi = (double *)malloc(sizeof(double) * nn);
+#pragma omp for schedule(dynamic, 1)
+        for (long pl = 0; pl < (long)C * P * P; pl++) {
+            double *o = img + (size_t)pl * nn * 2;
+            for (long l = 0; l < nn; l++) {
+                gr[l] = o[2 * l];
+                gi[l] = o[2 * l + 1];
+            }
+            checkerboard(n, gr, gi);
+            orc_fft2d(n, gr, gi);
+            for (long l = 0; l < nn; l++) {
+                o[2 * l] = gr[l];
+                o[2 * l + 1] = gi[l];
+            }
+        }
+        free(gr);
+        free(gi);
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* FFT correlator (Section 4.1.2 and Section 5.2.2: visibilities obtained from */
+/* accumulated EPIC images by an inverse FFT).  The accumulated image          */
+/* I_{alpha beta}[l] = sum_t F_alpha[l] conj(F_beta[l]) is the DFT (+) of the  */
+/* circular autocorrelation of the checkerboarded grids (-1)^j G[j], so        */
+/* R[d] = (-1)^(dx+dy) (1/n^2) sum_l I[l] exp(-2 pi i l.d / n)                 */
+/* returns the gridded visibilities sum_j G_alpha[j+d] conj(G_beta[j]) at lag  */
+/* d.  planes [C][Q][n][n] as the EPIC image stores them (Q = 1: XX; Q = 4:    */
+/* XX, YY, Re XY, Im XY); I_YX is conj(I_XY) pixel by pixel.                   */
+/* grid [C][P][P][n][n][2].                                                    */
+/* ------------------------------------------------------------------------- */
+int orc_fft_correlate(int n, int C, int P, const double *planes, double *grid) {
+    if (!is_pow2(n) || n < 4 || C < 0 || P < 1 || P > 2) return ORC_ERR_ARG;
+    const long nn = (long)n * n;
+    const int Q = (P == 2) ? 4 : 1;
+#pragma omp parallel
+    {
+        double *gr = (double *)malloc(sizeof(double) * nn);
+        double *gi = (double *)malloc(sizeof(double) * nn);
+#pragma omp for collapse(3) schedule(dynamic, 1)
+        for (int c = 0; c < C; c++)
+            for (int al = 0; al < P; al++)
+                for (int be = 0; be < P; be++) {
+                    const double *pl = planes + (size_t)c * Q * nn;
+                    for (long o = 0; o < nn; o++) {
+                        double ir, ii;
+                        if (al == be) {            /* XX or YY: real */
+                            ir = pl[(size_t)al * nn + o];
+                            ii = 0.0;
+                        } else {                   /* XY, or YX = conj(XY) */
+                            ir = pl[2 * nn + o];
+                            ii = (al == 0) ? pl[3 * nn + o] : -pl[3 * nn + o];
+                        }
+                        /* inverse DFT as conj(DFT+(conj(x))) / n^2 */
+                        gr[o] = ir;
+                        gi[o] = -ii;
+                    }
+                    orc_fft2d(n, gr, gi);
+                    for (long d = 0; d < nn; d++) gi[d] = -gi[d];
+                    checkerboard(n, gr, gi);
+                    double *g = grid + ((((size_t)c * P + al) * P + be) * nn) * 2;
+                    for (long d = 0; d < nn; d++) {
+                        g[2 * d] = gr[d] / (double)nn;
+                        g[2 * d + 1] = gi[d] / (double)nn;
+                    }
+                }
         free(gr);
         free(gi);
     }

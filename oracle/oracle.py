@@ -63,6 +63,9 @@ def lib():
             L.orc_vis_kernel.restype = None
             L.orc_xfft_image.argtypes = [c_int, c_int, c_int, _i32p, _f32p, _i64p, c_int, c_int,
                                          _f64p]
+            L.orc_xfft_grid.argtypes = [c_int, c_int, c_int, _i32p, _f32p, _i64p, c_int, c_int,
+                                        _f64p]
+            L.orc_fft_correlate.argtypes = [c_int, c_int, c_int, _f64p, _f64p]
             L.orc_station_xfft.argtypes = [c_int, c_int, _f64p, ctypes.c_double, ctypes.c_double, c_int,
                                            _f64p, _i64p, c_int, c_int, _f64p,
                                            ctypes.POINTER(ctypes.c_int64)]
@@ -204,6 +207,34 @@ def xfft_image(n: int, anchors, taps, vis: np.ndarray) -> np.ndarray:
     img = np.empty((C, P, P, n, n, 2))
     _check(lib().orc_xfft_image(n, ne, k, anchors, taps, vis, C, P, img), "xfft_image")
     return img[..., 0] + 1j * img[..., 1]
+
+
+def xfft_grid(n: int, anchors, taps, vis: np.ndarray) -> np.ndarray:
+    """Gridded visibilities of Eq. (intra-station XFFT), the bracket before
+    the transform: sum over all ordered pairs of V^{alpha beta}_{ab} K_ab[d]
+    on the circular n grid (lag d at cell (d_x mod n, d_y mod n)).  Returns
+    complex [C][P][P][n][n]."""
+    anchors, taps, ne, k = _layout(anchors, taps)
+    vis = np.ascontiguousarray(vis, np.int64)
+    C, nbl, P, _, _ = vis.shape
+    assert nbl == ne * (ne + 1) // 2
+    g = np.empty((C, P, P, n, n, 2))
+    _check(lib().orc_xfft_grid(n, ne, k, anchors, taps, vis, C, P, g), "xfft_grid")
+    return g[..., 0] + 1j * g[..., 1]
+
+
+def fft_correlate(planes: np.ndarray) -> np.ndarray:
+    """FFT correlator (Section 4.1.2, Section 5.2.2): inverse DFT, normalised
+    by 1/n^2 and multiplied by (-1)^(dx+dy), of accumulated EPIC image planes
+    [C][Q][n][n] (Q = 1: XX; Q = 4: XX, YY, Re XY, Im XY).  Returns the
+    gridded visibilities, complex [C][P][P][n][n] with the zero lag at cell
+    (0, 0)."""
+    planes = np.ascontiguousarray(planes, np.float64)
+    C, Q, n, _ = planes.shape
+    P = 2 if Q == 4 else 1
+    g = np.empty((C, P, P, n, n, 2))
+    _check(lib().orc_fft_correlate(n, C, P, planes, g), "fft_correlate")
+    return g[..., 0] + 1j * g[..., 1]
 
 
 def station_xfft(n: int, pos_m, lam_m: float, cell_m: float, dirs, vis: np.ndarray):

@@ -417,3 +417,72 @@ def test_station_xfft_equals_intra_xfft_with_unit_taps():
     intra = O.xfft_image(n, cells.astype(np.int32), taps, vis)
     assert dropped == 0
     assert np.abs(st[0] - intra).max() < 1e-9 * np.abs(intra).max()
+
+
+# ---------------------------------------------------------------- FFT correlator
+@pytest.mark.parametrize("P,cplx_taps", [(1, False), (2, False), (2, True)])
+def test_fft_correlator_recovers_the_gridded_visibilities(P, cplx_taps):
+    """The inverse DFT of the accumulated EPIC image is the full correlation
+    set gridded with the illumination autocorrelation kernel (the bracket of
+    Eq. intra-station XFFT), computed here by the other route: the int64
+    correlator and the explicit lag sums."""
+    n = 16
+    pos, anchors, taps = _small_station()
+    if cplx_taps:
+        taps = taps.copy()
+        taps[..., 1] = 0.3 * np.random.default_rng(9).standard_normal(taps.shape[:-1])
+    volt = I.random_voltages((2, 5, P, len(anchors), 2), seed=31).numpy()
+    got = O.fft_correlate(O.epic_image(n, anchors, taps, volt))
+    want = O.xfft_grid(n, anchors, taps, O.correlate(volt))
+    assert rel(got, want) < 1e-11
+    # Hermitian: R_ab[-d] = conj(R_ba[d])
+    flip = np.roll(np.flip(want, axis=(-2, -1)), 1, axis=(-2, -1))
+    assert rel(np.conj(flip), np.swapaxes(want, 1, 2)) < 1e-12
+
+
+def test_fft_correlator_on_a_lattice_sums_redundant_baselines():
+    """Elements on distinct cells with 1 x 1 unit taps: every lag holds the
+    plain sum of the visibilities of the pairs separated by it (the FFT
+    correlator of redundant arrays), brute-forced pair by pair."""
+    n = 16
+    cells, taps = _on_cell_station(n)
+    ne = len(cells)
+    P = 2
+    volt = I.random_voltages((1, 4, P, ne, 2), seed=4).numpy()
+    e = volt[..., 0].astype(np.int64) + 1j * volt[..., 1].astype(np.int64)   # [C][T][P][ne]
+    want = np.zeros((1, P, P, n, n), complex)
+    for a in range(ne):
+        for b in range(ne):
+            d = (cells[a] - cells[b]) % n
+            for al in range(P):
+                for be in range(P):
+                    want[0, al, be, d[1], d[0]] += np.sum(e[0, :, al, a] * np.conj(e[0, :, be, b]))
+    got = O.fft_correlate(O.epic_image(n, cells, taps, volt))
+    assert rel(got, want) < 1e-12
+    assert rel(O.xfft_grid(n, cells, taps, O.correlate(volt)), want) == 0.0
+
+
+def test_fft_correlate_closed_forms():
+    """Normalisation and sign of the inverse transform: a constant XX plane
+    is a zero-lag delta of that value; an XY plane exp(+2 pi i o.d0 / n) is a
+    delta (-1)^(d0x+d0y) at lag d0 for XY and at -d0 for YX (the
+    checkerboard that puts the phase centre at pixel n/2)."""
+    n = 8
+    planes = np.zeros((1, 4, n, n))
+    planes[0, 0] = 3.0
+    oy, ox = np.mgrid[0:n, 0:n]
+    d0 = (3, 1)
+    ph = 2 * np.pi * (ox * d0[0] + oy * d0[1]) / n
+    planes[0, 2], planes[0, 3] = np.cos(ph), np.sin(ph)
+    g = O.fft_correlate(planes)
+    want_xx = np.zeros((n, n), complex)
+    want_xx[0, 0] = 3.0
+    assert np.abs(g[0, 0, 0] - want_xx).max() < 1e-14
+    assert np.abs(g[0, 1, 1]).max() < 1e-14
+    want_xy = np.zeros((n, n), complex)
+    sgn = (-1.0) ** (d0[0] + d0[1])
+    want_xy[d0[1], d0[0]] = sgn
+    assert np.abs(g[0, 0, 1] - want_xy).max() < 1e-14
+    want_yx = np.zeros((n, n), complex)
+    want_yx[(-d0[1]) % n, (-d0[0]) % n] = sgn
+    assert np.abs(g[0, 1, 0] - want_yx).max() < 1e-14
