@@ -434,12 +434,23 @@ def dense_component(hai, ctx, flush, peaks, sms):
     peak = fp32_alu_peak_tflops(sms, float(peaks.get("sm_max_mhz", 2070.0)))
     ach = flop / (ms * 1e-3) / 1e12
     hai.hai_layout_destroy(lay)
-    del volt, img
+    # FFT correlator on the accumulated images: redundant-baseline sums of
+    # the lattice at every lag (the inverse FFT once per cadence)
+    grid = torch.empty((C, P, P, n, n, 2), device="cuda")
+    fc_ms = time_call(lambda st: hai.hai_fft_correlate(ctx, img, C, n, P, grid, st), 10, 3, flush)
+    fc_bytes = img.numel() * 4 + grid.numel() * 4          # image read once, grid written once
+    fc_gbs = fc_bytes / (fc_ms * 1e-3) / 1e9
+    del volt, img, grid
     return {"workload": cfg.name, "elements": cfg.n_elem, "grid": n, "channels": C, "samples": T, "pols": P,
             "precision": "fp32", "ms": ms, "units_per_s": units / (ms * 1e-3), "unit": UNIT,
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                          "flop_per_unit": epic_flops_per_unit(cfg),
-                         "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x max SM clock"}}
+                         "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x max SM clock"},
+            "fft_correlator": {
+                "what": "inverse FFT of the accumulated images -> visibilities summed per lag, all 4 pol pairs",
+                "ms": fc_ms, "lags_per_s": C * P * P * n * n / (fc_ms * 1e-3),
+                "roofline": {"bound": "hbm", "achieved": fc_gbs, "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s",
+                             "frac": fc_gbs / float(peaks.get("hbm_gbs", 6800.0)), "algorithmic_bytes": fc_bytes}}}
 
 
 def hierarchy_component(hai, ctx, flush, peaks):

@@ -223,6 +223,25 @@ hai_status hai_xfft_image(hai_ctx *ctx, const hai_layout *layout, const int32_t 
                           float *img, int accumulate, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * FFT correlator (Section 4.1.2 and Section 5.2.2: visibilities from the
+ * accumulated EPIC images by an inverse FFT).  For every channel and
+ * polarisation pair (alpha, beta)
+ *   R_ab[d] = (-1)^(dx+dy) / N^2  sum_l I_ab[l] exp(-2 pi i l.d / N),
+ * which for an image written by hai_epic_image is the gridded visibility set
+ * sum_t sum_j G_alpha[j + d] conj(G_beta[j]) = sum over ordered element pairs
+ * of V^{alpha beta}_{ab} K_ab[d] (the bracket of Eq. intra-station XFFT); on
+ * a lattice with one unit tap per element each lag is the sum of the
+ * visibilities of the baselines separated by it.
+ *   img   device float [C][Q][N][N] as hai_epic_image writes it (Q = 1: XX;
+ *         Q = 4: XX, YY, Re XY, Im XY), 4-byte aligned; read only
+ *   grid  device float complex [C][P][P][N][N][2], 8-byte aligned; lag d at
+ *         cell (dx mod N, dy mod N) of the row-major plane (zero lag at
+ *         (0, 0)); overwritten.  YX is conj(XY) mirrored.
+ * N a power of two in [16, 512] (else HAI_ERR_UNSUPPORTED).  FP32 radix-2
+ * transforms; no scratch memory. */
+hai_status hai_fft_correlate(hai_ctx *ctx, const float *img, int C, int N, int P, float *grid, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Voltage beamformer (Eq. intra-station BF) with diagonal polarisation
  * weights: for every station s, channel c, sample t, beam k and pol p,
  *   B^p_k = sum_a conj(w^p_{s,k,a}) E^p_{s,a}(c, t).

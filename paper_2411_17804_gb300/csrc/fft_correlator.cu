@@ -1,0 +1,146 @@
+// FFT correlator (Section 4.1.2 and Section 5.2.2: visibilities obtained from
+// the accumulated EPIC images by an inverse FFT).
+//
+// The accumulated image I_ab[l] = sum_t F_a[l] conj(F_b[l]) is the DFT (+) of
+// the circular autocorrelation of the checkerboarded grids (-1)^j G[j], so
+//   R_ab[d] = (-1)^(dx+dy) / N^2  sum_l I_ab[l] exp(-2 pi i l.d / N)
+// is the grid sum_t sum_j G_a[j + d] conj(G_b[j]) at lag d, the same grid the
+// correlator + XFFT path fills with V_ab K_ab[d] (zero lag at cell (0, 0)).
+// On a lattice with one unit tap per element every lag holds the plain sum of
+// the visibilities of the baselines separated by it.
+//
+// Two passes over the output buffer, which holds the rows in between:
+//   rows:    one warp per (channel, product, row): the row of the real XX /
+//            YY plane or of the complex XY plane, radix-2 FFT (exponent -)
+//            in shared memory, complex row written to the output plane;
+//   columns: one CTA per (channel, product, 16 columns), one warp per
+//            column: FFT along y, times (-1)^(dx+dy) / N^2, written back; the
+//            XY CTA also writes YX[-d] = conj(XY[d]) (I_YX = conj(I_XY)).
+#include <algorithm>
+
+#include "hai_internal.h"
+
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kCols = 16;                 // columns per column CTA = warps per CTA
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// Twiddles exp(-2 pi i k / N), k < N / 2.
+__device__ __forceinline__ void fill_twiddles(float2 *tw, int N) {
+    for (int k = threadIdx.x; k < N / 2; k += blockDim.x) {
+        float s, c;
+        sincospif(2.0f * (float)k / (float)N, &s, &c);
+        tw[k] = make_float2(c, -s);
+    }
+}
+
+// In-place radix-2 FFT (exponent -) of N points held in bit-reversed order,
+// by one warp, with the twiddle table of length N / 2.
+__device__ __forceinline__ void warp_ifft(float2 *x, int n, int log2n, const float2 *tw, int lane) {
+    for (int s = 0; s < log2n; s++) {
+        const int half = 1 << s;
+        const int tstep = n >> (s + 1);
+        for (int b = lane; b < n / 2; b += 32) {
+            const int pos = b & (half - 1);
+            const int i0 = ((b - pos) << 1) + pos, i1 = i0 + half;
+            const float2 a = x[i0];
+            const float2 t = cmul(x[i1], tw[pos * tstep]);
+            x[i0] = make_float2(a.x + t.x, a.y + t.y);
+            x[i1] = make_float2(a.x - t.x, a.y - t.y);
+        }
+        __syncwarp();
+    }
+}
+
+// Output plane (polarisation pair index alpha * P + beta) of source product
+// pr (0 = XX, 1 = YY, 2 = XY).
+__device__ __forceinline__ int out_plane(int pr, int P) { return P == 1 ? 0 : (pr == 0 ? 0 : (pr == 1 ? 3 : 1)); }
+
+__global__ void __launch_bounds__(kThreads) fc_rows_kernel(const float *__restrict__ img, int N, int log2n, int P,
+                                                           float2 *__restrict__ out) {
+    extern __shared__ float2 sm[];
+    float2 *tw = sm;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 *line = sm + N / 2 + (size_t)warp * N;
+    fill_twiddles(tw, N);
+    __syncthreads();
+    const int np = (P == 2) ? 3 : 1, Q = (P == 2) ? 4 : 1;
+    const int c = blockIdx.x / np, pr = blockIdx.x % np;
+    const int y = blockIdx.y * (kThreads / 32) + warp;
+    if (y >= N) return;
+    const size_t NN = (size_t)N * N;
+    const float *re = img + ((size_t)c * Q + (pr == 2 ? 2 : pr)) * NN + (size_t)y * N;
+    const float *im = (pr == 2) ? re + NN : nullptr;
+    for (int x = lane; x < N; x += 32)
+        line[__brev(x) >> (32 - log2n)] = make_float2(__ldg(re + x), im ? __ldg(im + x) : 0.f);
+    __syncwarp();
+    warp_ifft(line, N, log2n, tw, lane);
+    float2 *dst = out + ((size_t)c * P * P + out_plane(pr, P)) * NN + (size_t)y * N;
+    for (int x = lane; x < N; x += 32) dst[x] = line[x];
+}
+
+__global__ void __launch_bounds__(kThreads) fc_cols_kernel(int N, int log2n, int P, float2 *__restrict__ out) {
+    extern __shared__ float2 sm[];
+    float2 *tw = sm;
+    float2 *F = sm + N / 2;                         // [kCols][N]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    fill_twiddles(tw, N);
+    const int np = (P == 2) ? 3 : 1;
+    const int c = blockIdx.x / np, pr = blockIdx.x % np;
+    const int x0 = blockIdx.y * kCols;
+    const size_t NN = (size_t)N * N;
+    float2 *plane = out + ((size_t)c * P * P + out_plane(pr, P)) * NN;
+    for (int i = threadIdx.x; i < N * kCols; i += kThreads) {
+        const int j = i % kCols, y = i / kCols;
+        F[(size_t)j * N + (__brev(y) >> (32 - log2n))] = plane[(size_t)y * N + x0 + j];
+    }
+    __syncthreads();
+    warp_ifft(F + (size_t)warp * N, N, log2n, tw, lane);
+    __syncthreads();
+    const float inv = 1.0f / (float)NN;
+    float2 *mirror = (pr == 2) ? out + ((size_t)c * P * P + 2) * NN : nullptr;   // YX
+    for (int i = threadIdx.x; i < N * kCols; i += kThreads) {
+        const int j = i % kCols, dy = i / kCols, dx = x0 + j;
+        const float s = ((dx + dy) & 1) ? -inv : inv;
+        const float2 v = F[(size_t)j * N + dy];
+        const float2 r = make_float2(v.x * s, v.y * s);
+        plane[(size_t)dy * N + dx] = r;
+        if (mirror) mirror[(size_t)((N - dy) & (N - 1)) * N + ((N - dx) & (N - 1))] = make_float2(r.x, -r.y);
+    }
+}
+
+}  // namespace
+
+extern "C" hai_status hai_fft_correlate(hai_ctx *ctx, const float *img, int C, int N, int P, float *grid,
+                                        void *stream) {
+    if (!ctx) return hai_fail(HAI_ERR_INVALID_ARG, "hai_fft_correlate: NULL ctx");
+    if (C < 0 || (P != 1 && P != 2)) return hai_fail(HAI_ERR_INVALID_ARG, "hai_fft_correlate: bad C or P");
+    int log2n = 0;
+    while ((1 << log2n) < N && log2n < 30) log2n++;
+    if (N < 16 || N > 512 || (1 << log2n) != N)
+        return hai_fail(HAI_ERR_UNSUPPORTED, "hai_fft_correlate: N must be a power of two in [16, 512]");
+    if (C == 0) return HAI_OK;
+    if (!img || !grid) return hai_fail(HAI_ERR_INVALID_ARG, "hai_fft_correlate: NULL buffer");
+    if ((reinterpret_cast<uintptr_t>(img) & 3) || (reinterpret_cast<uintptr_t>(grid) & 7))
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_fft_correlate: img must be 4-byte and grid 8-byte aligned");
+    if (hai_fault_injected("launch")) return hai_fail(HAI_ERR_CUDA, "hai_fft_correlate: injected launch failure");
+    HAI_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int np = (P == 2) ? 3 : 1;
+    const size_t smem = sizeof(float2) * ((size_t)N / 2 + (size_t)kCols * N);   // both passes
+    HAI_CUDA_TRY(cudaFuncSetAttribute(fc_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HAI_CUDA_TRY(cudaFuncSetAttribute(fc_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    float2 *out = reinterpret_cast<float2 *>(grid);
+    const int pidx = prof_begin(ctx, st);
+    fc_rows_kernel<<<dim3(C * np, (N + kThreads / 32 - 1) / (kThreads / 32)), kThreads, smem, st>>>(img, N, log2n,
+                                                                                                     P, out);
+    fc_cols_kernel<<<dim3(C * np, N / kCols), kThreads, smem, st>>>(N, log2n, P, out);
+    prof_end(ctx, pidx, st);
+    prof_count(ctx, 2);
+    HAI_CUDA_TRY(cudaGetLastError());
+    return HAI_OK;
+}

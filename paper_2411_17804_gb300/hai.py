@@ -64,6 +64,7 @@ def _declare(L):
     L.hai_epic_image.argtypes = [_vp, _vp, _vp, _int, _int, _int, _vp, _int, _vp]
     L.hai_correlate.argtypes = [_vp, _vp, _int, _int, _int, _int, _vp, _int, _vp]
     L.hai_xfft_image.argtypes = [_vp, _vp, _vp, _int, _vp, _int, _vp]
+    L.hai_fft_correlate.argtypes = [_vp, _vp, _int, _int, _int, _vp, _vp]
     L.hai_beamform.argtypes = [_vp, _vp, _vp, _int, _int, _int, _int, _int, _int, _int, _vp, _vp, _vp]
     L.hai_epic_image_fp32_static.argtypes = [_int, ctypes.POINTER(_LayoutDesc), _vp, _int, _int, _vp, _int,
                                              _vp]
@@ -219,6 +220,19 @@ def hai_xfft_image(ctx, layout: Layout, vis, C: int, img, accumulate: int = 0, s
     vp = _dev_ptr(vis, torch.int32, "vis", C * (ne * (ne + 1) // 2) * P * P * 2) if C > 0 else 0
     ip = _dev_ptr(img, torch.float32, "img", C * layout.n_planes * n * n) if C > 0 else 0
     _check(load().hai_xfft_image(ctx, layout.handle, vp, C, ip, accumulate, _stream(stream)), "hai_xfft_image")
+
+
+def hai_fft_correlate(ctx, img, C: int, N: int, P: int, grid, stream=None):
+    """Gridded visibilities from accumulated EPIC images (inverse FFT);
+    grid: float32 [C][P][P][N][N][2] (or complex64 of [C][P][P][N][N])."""
+    import torch
+    q = 4 if P == 2 else 1
+    ip = _dev_ptr(img, torch.float32, "img", C * q * N * N) if C > 0 else 0
+    if C > 0 and isinstance(grid, torch.Tensor) and grid.dtype == torch.complex64:
+        gp = _dev_ptr(torch.view_as_real(grid), torch.float32, "grid", C * P * P * N * N * 2)
+    else:
+        gp = _dev_ptr(grid, torch.float32, "grid", C * P * P * N * N * 2) if C > 0 else 0
+    _check(load().hai_fft_correlate(ctx, ip, C, N, P, gp, _stream(stream)), "hai_fft_correlate")
 
 
 def hai_epic_image_fp32_static(device: int, anchors, taps, grid_n: int, n_pol: int, volt, C: int, T: int, img,

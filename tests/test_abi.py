@@ -50,6 +50,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.hai_epic_image(None, None, None, 1, 1, 0, None, 0, None) == 1
     assert "NULL" in hai.hai_last_error()
     assert lib.hai_sync(None, None) == 1
+    assert lib.hai_fft_correlate(None, None, 1, 64, 2, None, None) == 1
 
 
 def test_fault_injection_on_host(lib, monkeypatch):
