@@ -274,6 +274,24 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def paper_cost(array, level, channels, samples, step_ms, measured="EPIC"):
+    """The paper's own FLOP-cost estimate of one cadence (Table 2 formulas on
+    the Table 1 row of `array`, per station or station beam), for every
+    architecture of the stage, with the count of the `measured` architecture
+    over the time measured for it here."""
+    from paper_2411_17804_gb300 import cost as K
+    n, ratio = K.level_args(K.ARRAYS[array], level)
+    flop = {x: K.flop_per_cadence(x, n, ratio, channels, samples) for x in K.ARCHS}
+    t_acc = samples * K.DELTA_T
+    return {"source": f"Table 2 formulas, Table 1 {array} ({level}-station: n = {n}, ratio = {ratio:.4g}), "
+                      f"n_p 2, delta t 25 us",
+            "t_acc_s": t_acc, "channels_x_beams": channels, "flop_per_cadence": flop,
+            "cheapest": min(flop, key=flop.get),
+            "measured_arch": measured,
+            "paper_flop_per_s_at_measured_time": flop[measured] / (step_ms * 1e-3),
+            "voxels_per_channel": ratio * ratio}
+
+
 def time_epic(hai, ctx, lay, volt, img, C, T, prec, steps, warm, flush, ws):
     import torch
     st = torch.cuda.current_stream()
@@ -501,6 +519,9 @@ def hierarchy_component(hai, ctx, flush, peaks):
                                       "peak": pk, "unit": "TFLOP/s"}}}
     for r in out["roofline"].values():
         r["frac"] = r["achieved"] / r["peak"]
+    # inter-station stage of the paper's SKA-low-core (256 stations), per beam
+    out["paper_cost_inter_station"] = paper_cost("SKA-low-core", "inter", C * K, T,
+                                                 ms["station_correlator"] + ms["station_xfft"], "XFFT")
     hai.hai_vis_layout_destroy(lay)
     del volt, w, beams, cin, vis, img
     return out
@@ -651,6 +672,10 @@ def main():
             "e2e": {"value": ws * units / (e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": int(volt.numel()), "d2h_bytes_per_step": int(img.numel() * 4)},
             "gpu_launches": int(launches), "clocks": clk, "roofline": roof}
+    line["paper_cost"] = paper_cost("SKA-low", "intra", C * ws, T, ms_step)
+    line["paper_cost"]["note"] = ("context, not a target: the paper counts (D_s/D_e)^2 independent pixels per "
+                                  f"channel; the image here holds N^2 = {n * n} pixels (padding 2, "
+                                  f"{cfg.ksize}x{cfg.ksize} kernel, power-of-two grid)")
     if fp32 is not None:
         line["plain_fp32"] = fp32
         line["tc_over_fp32"] = value / fp32["value"]
