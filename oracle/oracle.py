@@ -255,6 +255,41 @@ def station_xfft(n: int, pos_m, lam_m: float, cell_m: float, dirs, vis: np.ndarr
     return img[..., 0] + 1j * img[..., 1], dropped.value
 
 
+def station_epic_layout(n: int, pos_m, lam_m: float, cell_m: float, direction):
+    """Gridding kernel of Eq. (inter-station EPIC) with N_ks = 1 cell: station
+    m sits at its nearest cell j_m = floor(r_m / cell + n/2 + 1/2) with the
+    weight conj(W~_m) = exp(+2 pi i s_k . r_m / lambda) (FP64), which brings
+    the beam direction s_k to the phase-centre pixel.  A station whose cell
+    lies outside [0, n)^2 is dropped: zero weight, parked on the centre cell.
+    Returns (anchors int32 [S][2], taps float32 [S][1][1][2] holding W~_m as
+    the EPIC gridding expects, stations dropped)."""
+    pos = np.asarray(pos_m, np.float64)
+    d = np.asarray(direction, np.float64)
+    cells = np.floor(pos / cell_m + n / 2.0 + 0.5).astype(np.int64)
+    on = np.all((cells >= 0) & (cells < n), axis=1)
+    anchors = np.where(on[:, None], cells, n // 2).astype(np.int32)
+    turns = (pos @ d) / lam_m
+    taps = np.zeros((len(pos), 1, 1, 2), np.float32)
+    taps[:, 0, 0, 0] = np.where(on, np.cos(2 * np.pi * turns), 0.0)
+    taps[:, 0, 0, 1] = np.where(on, -np.sin(2 * np.pi * turns), 0.0)
+    return anchors, taps, int(np.count_nonzero(~on))
+
+
+def station_epic(n: int, pos_m, lam_m: float, cell_m: float, dirs, beams: np.ndarray):
+    """Images of Eq. (inter-station EPIC) then the squaring and temporal sum
+    of Eq. (inter-station squaring): for every beam direction s_k the station
+    beams E_m(s_k) int8 [K][C][T][P][S][2] gridded with station_epic_layout,
+    transformed and squared as intra-station EPIC.  Returns (float64
+    [K][C][Q][n][n], stations dropped)."""
+    beams = np.asarray(beams)
+    K = beams.shape[0]
+    out, dropped = [], 0
+    for k in range(K):
+        anchors, taps, dropped = station_epic_layout(n, pos_m, lam_m, cell_m, dirs[k])
+        out.append(epic_image(n, anchors, taps, np.ascontiguousarray(beams[k])))
+    return np.stack(out), dropped
+
+
 def xfft_as_epic_planes(ximg: np.ndarray) -> np.ndarray:
     """Pick the stored planes (XX, YY, Re XY, Im XY) out of a full complex
     polarisation-pair image [C][P][P][n][n]."""

@@ -486,3 +486,78 @@ def test_fft_correlate_closed_forms():
     want_yx = np.zeros((n, n), complex)
     want_yx[(-d0[1]) % n, (-d0[0]) % n] = sgn
     assert np.abs(g[0, 1, 0] - want_yx).max() < 1e-14
+
+
+# ---------------------------------------------------------------- inter-station EPIC
+def _stations_on_cells(n, S, cell, seed, far=0):
+    """S stations on distinct whole cells of the central (n/2 - 1)^2 box of
+    the grid (every pair's 2 x 2 bilinear footprint stays on the grid), plus
+    `far` stations on cells well outside it."""
+    rng = np.random.default_rng(seed)
+    w = n // 2 - 1
+    idx = rng.choice(w * w, S, replace=False)
+    cells = np.stack([idx % w, idx // w], axis=1) - n // 4
+    pos = cells.astype(np.float64) * cell
+    if far:
+        pos = np.concatenate([pos, rng.integers(3 * n, 5 * n, (far, 2)) * cell])
+    return pos
+
+
+def _quarter_turn_beams(pos, lam, cell, src, A, T):
+    """Station beams of a point source at direction `src` whose phases
+    exp(-2 pi i src.r_m / lambda) are whole quarter turns (exact in int8)."""
+    turns = (pos @ np.asarray(src, np.float64)) / lam
+    q = np.rint(4 * turns).astype(np.int64)
+    assert np.allclose(4 * turns, q)
+    rot = (-1j) ** (q % 4)                                   # exp(-2 pi i q / 4)
+    S, P = len(pos), len(A)
+    b = np.zeros((1, 1, T, P, S, 2), np.int8)
+    for p in range(P):
+        v = A[p] * rot
+        b[0, 0, :, p, :, 0] = np.rint(v.real).astype(np.int8)
+        b[0, 0, :, p, :, 1] = np.rint(v.imag).astype(np.int8)
+    return b
+
+
+@pytest.mark.parametrize("offset", [(0, 0), (4, 0), (-4, 4)])
+def test_station_epic_steered_point_source_closed_form(offset):
+    """Beams of a source at s_k + (l - n/2) lambda / (n cell) from stations on
+    cells: after the FP64 steering weights every on-grid station adds
+    coherently at pixel l, with power T |S_on A|^2 (XX, YY) and
+    T S_on^2 A_X conj(A_Y) (XY); far stations are dropped and counted."""
+    n, lam, cell, T = 16, 2.0, 2.0, 3
+    pos = _stations_on_cells(n, 10, cell, seed=3, far=3)
+    s_k = np.array([0.25, 0.5])                      # quarter turns per cell (cell = lambda)
+    src = s_k + np.array(offset) * lam / (n * cell)
+    A = np.array([3 - 2j, -1 + 4j])
+    beams = _quarter_turn_beams(pos, lam, cell, src, A, T)
+    img, dropped = O.station_epic(n, pos, lam, cell, s_k[None], beams)
+    assert dropped == 3
+    S_on = 10
+    ly, lx = n // 2 + offset[1], n // 2 + offset[0]
+    xx = img[0, 0, 0]
+    assert np.unravel_index(np.argmax(xx), xx.shape) == (ly, lx)
+    assert xx[ly, lx] == pytest.approx(T * abs(S_on * A[0]) ** 2, rel=1e-6)
+    assert img[0, 0, 1, ly, lx] == pytest.approx(T * abs(S_on * A[1]) ** 2, rel=1e-6)
+    xy = T * S_on ** 2 * A[0] * np.conj(A[1])
+    assert img[0, 0, 2, ly, lx] == pytest.approx(xy.real, rel=1e-6)
+    assert img[0, 0, 3, ly, lx] == pytest.approx(xy.imag, rel=1e-6)
+
+
+def test_station_epic_equals_station_xfft_for_stations_on_cells():
+    """The array-level invariant: for stations on whole cells the bilinear
+    kernel of the inter-station XFFT is the autocorrelation of the 1-cell
+    EPIC kernel, so the two independently written routines give the same
+    image, steering included (EPIC weights in FP32, XFFT phases in FP64)."""
+    n, lam, cell, T, S = 16, 3.0, 5.0, 4, 9
+    pos = _stations_on_cells(n, S, cell, seed=11)
+    dirs = np.array([[0.0, 0.0], [0.137, -0.291]])
+    rng = np.random.default_rng(12)
+    beams = rng.integers(-60, 60, (2, 2, T, 2, S, 2)).astype(np.int8)
+    epic, dropped = O.station_epic(n, pos, lam, cell, dirs, beams)
+    assert dropped == 0
+    vis = np.stack([O.correlate(beams[k]) for k in range(2)])
+    ximg, off = O.station_xfft(n, pos, lam, cell, dirs, vis)
+    assert off == 0
+    for k in range(2):
+        assert rel(O.xfft_as_epic_planes(ximg[k]), epic[k]) < 1e-6
