@@ -501,6 +501,19 @@ def hierarchy_component(hai, ctx, flush, peaks):
         "station_xfft": lambda st: hai.hai_xfft_station_image(ctx, lay, vis, C, img, st)}
     ms = {k: time_call(f, 5, 2, flush) for k, f in stages.items()}
     total = time_call(lambda st: [f(st) for f in stages.values()], 5, 2, flush)
+    # the coherent inter-station alternative on the same beams: EPIC over the
+    # stations (FP64-steered 1-cell weights, 128^2 array grid = padding 2 on
+    # the 1 km core), tensor cores, one launch per beam direction
+    ne_grid = 128
+    elays = [hai.hai_station_epic_layout_create(ctx, centres, H.station.lam_m, H.cell_m, ne_grid, dirs, k, P)
+             for k in range(K)]
+    eimg = torch.empty((K, C, 4, ne_grid, ne_grid), device="cuda")
+
+    def station_epic(st):
+        for k in range(K):
+            hai.hai_epic_image(ctx, elays[k][0], cin[k], C, T, hai.HAI_PREC_FP16, eimg[k], 0, st)
+
+    ems = time_call(station_epic, 5, 2, flush)
     units = n * n * K * C * P * T
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     pk = float(peaks.get("bf16_tflops", 1900.0))
@@ -519,9 +532,20 @@ def hierarchy_component(hai, ctx, flush, peaks):
                                       "peak": pk, "unit": "TFLOP/s"}}}
     for r in out["roofline"].values():
         r["frac"] = r["achieved"] / r["peak"]
+    emma = plan_mma_flops(ne_grid) * K * C * T
+    out["station_epic"] = {
+        "what": "inter-station EPIC on the same requantised beams (alternative to correlator + XFFT)",
+        "grid": ne_grid, "stations_dropped": elays[0][1], "ms": ems,
+        "units_per_s": ne_grid * ne_grid * K * C * P * T / (ems * 1e-3),
+        "roofline": {"bound": "tensor", "achieved": emma / (ems * 1e-3) / 1e12, "peak": pk, "unit": "TFLOP/s",
+                     "frac": emma / (ems * 1e-3) / 1e12 / pk}}
     # inter-station stage of the paper's SKA-low-core (256 stations), per beam
     out["paper_cost_inter_station"] = paper_cost("SKA-low-core", "inter", C * K, T,
                                                  ms["station_correlator"] + ms["station_xfft"], "XFFT")
+    out["paper_cost_inter_station"]["measured_epic_ms"] = ems
+    for lay_k, _ in elays:
+        hai.hai_layout_destroy(lay_k)
+    del eimg
     hai.hai_vis_layout_destroy(lay)
     del volt, w, beams, cin, vis, img
     return out

@@ -314,6 +314,28 @@ hai_status hai_xfft_station_image(hai_ctx *ctx, const hai_vis_layout *layout, co
                                   void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Inter-station EPIC (Eq. inter-station EPIC, then the squaring and temporal
+ * sum of Eq. inter-station squaring) runs on hai_epic_image with a layout in
+ * which the stations are the elements: for beam direction s_k = dir[k],
+ * station m sits on its nearest cell of the array grid,
+ *   j_m = floor(r_m / cell + N/2 + 1/2)  (per axis),
+ * with one tap (N_ks = 1 cell) W~_m such that conj(W~_m) = exp(+2 pi i
+ * s_k . r_m / lambda): the phase is taken in FP64 on the host, reduced to a
+ * fraction of a turn, and stored in FP32.  The padding factor 2 per
+ * dimension (Section 5.2.2) gives the array the central half of the grid: a
+ * station whose cell falls outside [N/4, 3N/4)^2 is dropped (weight 0,
+ * counted in *n_dropped when non-NULL); the kept stations' box then fits
+ * N/2, so the tensor-core kernels take N = 32, 64, 128.  The
+ * voltages are the station beams of direction k in the layout [C][T][P][S][2],
+ * i.e. block k of hai_beams_to_corr's output.  Phase centre at pixel
+ * (N/2, N/2); pixel l looks along s_k + (l - N/2) lambda / (N cell).
+ *   desc  as for hai_vis_layout_create (grid_n: any size hai_layout_create
+ *         takes; n_pol 1 or 2); k in [0, max(1, n_dir))
+ * Release with hai_layout_destroy. */
+hai_status hai_station_epic_layout_create(hai_ctx *ctx, const hai_vis_layout_desc *desc, int k, hai_layout **out,
+                                          long long *n_dropped);
+
+/* ---------------------------------------------------------------------------
  * EPIC image, FP32 path, without any device allocation.  (The paper has no
  * counterpart: this is an interface for callers, not a step of the method.)
  *

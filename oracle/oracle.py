@@ -259,14 +259,16 @@ def station_epic_layout(n: int, pos_m, lam_m: float, cell_m: float, direction):
     """Gridding kernel of Eq. (inter-station EPIC) with N_ks = 1 cell: station
     m sits at its nearest cell j_m = floor(r_m / cell + n/2 + 1/2) with the
     weight conj(W~_m) = exp(+2 pi i s_k . r_m / lambda) (FP64), which brings
-    the beam direction s_k to the phase-centre pixel.  A station whose cell
-    lies outside [0, n)^2 is dropped: zero weight, parked on the centre cell.
+    the beam direction s_k to the phase-centre pixel.  The padding factor
+    gamma_A = 2 per dimension (Section 5.2.2) leaves the array the central
+    half of the grid: a station whose cell lies outside [n/4, 3n/4)^2 is
+    dropped (zero weight, parked on the centre cell).
     Returns (anchors int32 [S][2], taps float32 [S][1][1][2] holding W~_m as
     the EPIC gridding expects, stations dropped)."""
     pos = np.asarray(pos_m, np.float64)
     d = np.asarray(direction, np.float64)
     cells = np.floor(pos / cell_m + n / 2.0 + 0.5).astype(np.int64)
-    on = np.all((cells >= 0) & (cells < n), axis=1)
+    on = np.all((cells >= n // 4) & (cells < n - n // 4), axis=1)
     anchors = np.where(on[:, None], cells, n // 2).astype(np.int32)
     turns = (pos @ d) / lam_m
     taps = np.zeros((len(pos), 1, 1, 2), np.float32)

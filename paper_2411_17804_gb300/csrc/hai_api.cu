@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -303,6 +304,55 @@ extern "C" hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *d, 
     }
     *out = L;
     return HAI_OK;
+}
+
+// Inter-station EPIC (Eq. inter-station EPIC, N_ks = 1 cell): station m at
+// its nearest cell floor(r_m / cell + N/2 + 1/2), weight conj(W~_m) =
+// exp(+2 pi i s_k . r_m / lambda) from an FP64 phase reduced to a fraction of
+// a turn.  With the padding factor 2 per dimension (Section 5.2.2) the array
+// keeps to the central half of the grid: stations outside [N/4, 3N/4)^2 are
+// parked on the centre cell with weight 0 (the box then fits N/2, which the
+// tensor-core kernels need, and no lag of the squared image wraps).
+extern "C" hai_status hai_station_epic_layout_create(hai_ctx *ctx, const hai_vis_layout_desc *d, int k,
+                                                     hai_layout **out, long long *n_dropped) {
+    if (!ctx || !d || !out) return hai_fail(HAI_ERR_INVALID_ARG, "hai_station_epic_layout_create: NULL argument");
+    *out = nullptr;
+    const int S = d->n_station, n = d->grid_n;
+    if (S <= 0 || !d->pos_m || !(d->lambda_m > 0.0) || !(d->cell_m > 0.0) || n <= 0 ||
+        (d->n_pol != 1 && d->n_pol != 2) || k < 0 || k >= std::max(1, d->n_dir))
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_station_epic_layout_create: bad descriptor or direction index");
+    const double sx = d->dir ? d->dir[2 * k] : 0.0, sy = d->dir ? d->dir[2 * k + 1] : 0.0;
+    if (!std::isfinite(sx) || !std::isfinite(sy))
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_station_epic_layout_create: direction not finite");
+    std::vector<int32_t> anchors(2 * (size_t)S);
+    std::vector<float> taps(2 * (size_t)S, 0.0f);
+    long long dropped = 0;
+    for (int m = 0; m < S; m++) {
+        const double x = d->pos_m[2 * m], y = d->pos_m[2 * m + 1];
+        const double gx = std::floor(x / d->cell_m + n / 2.0 + 0.5), gy = std::floor(y / d->cell_m + n / 2.0 + 0.5);
+        const double lo = n / 4, hi = n - n / 4;
+        if (!(gx >= lo && gx < hi && gy >= lo && gy < hi)) {
+            anchors[2 * m] = anchors[2 * m + 1] = n / 2;
+            dropped++;
+            continue;
+        }
+        anchors[2 * m] = (int32_t)gx;
+        anchors[2 * m + 1] = (int32_t)gy;
+        const double turns = (sx * x + sy * y) / d->lambda_m;
+        const double ang = 6.283185307179586476925286766559 * (turns - std::nearbyint(turns));
+        taps[2 * m] = (float)std::cos(ang);              // W~_m = exp(-i ang)
+        taps[2 * m + 1] = (float)-std::sin(ang);
+    }
+    hai_layout_desc ld;
+    ld.n_elem = S;
+    ld.grid_n = n;
+    ld.ksize = 1;
+    ld.n_pol = d->n_pol;
+    ld.anchors = anchors.data();
+    ld.taps = taps.data();
+    const hai_status rc = hai_layout_create(ctx, &ld, out);
+    if (rc == HAI_OK && n_dropped) *n_dropped = dropped;
+    return rc;
 }
 
 extern "C" void hai_layout_destroy(hai_layout *L) {

@@ -80,6 +80,8 @@ def _declare(L):
     L.hai_vis_layout_destroy.argtypes = [_vp]
     L.hai_vis_layout_destroy.restype = None
     L.hai_vis_layout_offgrid.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.hai_station_epic_layout_create.argtypes = [_vp, ctypes.POINTER(_VisLayoutDesc), _int, ctypes.POINTER(_vp),
+                                                 ctypes.POINTER(ctypes.c_longlong)]
     L.hai_xfft_station_image.argtypes = [_vp, _vp, _vp, _int, _vp, _vp]
     L.hai_profile_enable.argtypes = [_vp, _int, _int]
     L.hai_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
@@ -354,6 +356,25 @@ def hai_vis_layout_create(ctx, pos_m, lambda_m: float, cell_m: float, grid_n: in
     h = _vp()
     _check(load().hai_vis_layout_create(ctx, ctypes.byref(desc), ctypes.byref(h)), "hai_vis_layout_create")
     return VisLayout(h, S, grid_n, K)
+
+
+def hai_station_epic_layout_create(ctx, pos_m, lambda_m: float, cell_m: float, grid_n: int, dirs=None, k: int = 0,
+                                   n_pol: int = 2):
+    """Layout of the inter-station EPIC for beam direction k (stations as the
+    elements, FP64 steering weights).  Returns (Layout, stations dropped)."""
+    pos = np.ascontiguousarray(pos_m, np.float64)
+    S = pos.shape[0]
+    if pos.shape != (S, 2):
+        raise ValueError("pos_m must be [S][2]")
+    d = None if dirs is None else np.ascontiguousarray(dirs, np.float64)
+    K = 1 if d is None else d.shape[0]
+    desc = _VisLayoutDesc(S, pos.ctypes.data, lambda_m, cell_m, grid_n, n_pol, K,
+                          None if d is None else d.ctypes.data)
+    h = _vp()
+    dropped = ctypes.c_longlong()
+    _check(load().hai_station_epic_layout_create(ctx, ctypes.byref(desc), k, ctypes.byref(h), ctypes.byref(dropped)),
+           "hai_station_epic_layout_create")
+    return Layout(h, S, grid_n, 1, n_pol), dropped.value
 
 
 def hai_vis_layout_destroy(layout: VisLayout):
