@@ -10,7 +10,11 @@
  *     (Section 5.2, Eq. intra-station EPIC + Eq. intra-station squaring);
  *   - the comparison paths: the int8 correlator (Eq. intra-station
  *     visibilities), the correlator + FFT imager (Eq. intra-station XFFT) and
- *     the pre-correlation voltage beamformer (Eq. intra-station BF).
+ *     the pre-correlation voltage beamformer (Eq. intra-station BF);
+ *   - the inter-station stage of a hierarchical array: station beams to the
+ *     correlator layout, the FP64-steered XFFT (Eq. inter-station XFFT) and
+ *     the coherent EPIC over stations (Eq. inter-station EPIC);
+ *   - the FFT correlator: visibilities from accumulated EPIC images.
  *
  * Conventions shared by every entry point
  *   - Every function returns hai_status; HAI_OK is 0.  On failure nothing is
