@@ -223,23 +223,8 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
 #pragma unroll
                 for (int f = 0; f < G::kFields; f++) g[f] = make_float2(0.f, 0.f);
                 const int qe = s_base[t + 1];
-                int q = s_base[t] + lane;
-                // software pipeline: slot k+1's weight and voltages load while slot k computes
-                float2 w_n = s_w[q];
-                uint4 e_n[G::kU];
-#pragma unroll
-                for (int u = 0; u < G::kU; u++) e_n[u] = E[s_e[q] * G::kU + u];
-                for (; q < qe; q += 32) {
-                    const float2 w = w_n;
-                    uint4 e[G::kU];
-#pragma unroll
-                    for (int u = 0; u < G::kU; u++) e[u] = e_n[u];
-                    if (q + 32 < qe) {
-                        w_n = s_w[q + 32];
-                        const int en = s_e[q + 32];
-#pragma unroll
-                        for (int u = 0; u < G::kU; u++) e_n[u] = E[en * G::kU + u];
-                    }
+                // add one slot's conj(W~) E into the fields' sums
+                auto mac = [&](const float2 w, const uint4 *e) {
 #pragma unroll
                     for (int u = 0; u < G::kU; u++) {
                         const uint32_t ev[4] = {e[u].x, e[u].y, e[u].z, e[u].w};
@@ -251,6 +236,34 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
                             acc.y = fmaf(w.x, x.y, fmaf(w.y, x.x, acc.y));
                         }
                     }
+                };
+                // the lane's slots are q, q + 32, ...: four at a time with all
+                // their shared-memory loads issued before the first use (the
+                // loop is bound by load latency, not by issue)
+                int q = s_base[t] + lane;
+                for (; q + 96 < qe; q += 128) {
+                    float2 w[4];
+                    int en[4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        w[j] = s_w[q + 32 * j];
+                        en[j] = s_e[q + 32 * j];
+                    }
+                    uint4 e[4][G::kU];
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+#pragma unroll
+                        for (int u = 0; u < G::kU; u++) e[j][u] = E[en[j] * G::kU + u];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) mac(w[j], e[j]);
+                }
+                for (; q < qe; q += 32) {
+                    const float2 w = s_w[q];
+                    uint4 e[G::kU];
+                    const int en = s_e[q];
+#pragma unroll
+                    for (int u = 0; u < G::kU; u++) e[u] = E[en * G::kU + u];
+                    mac(w, e);
                 }
                 const uint32_t off = s_cell[t * 32 + lane];
                 if (off != 0xffffffffu) {
@@ -409,9 +422,11 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         constexpr int kLy = G::kLy;
         constexpr int kNN = N * N;
-        float acc_a[kLy], acc_x[kLy];
+        // packed pairs: acc_a[t / 2] holds rows t, t + 1 of the own polarisation's
+        // power; acc_x[t] the (re, im) cross product of one row
+        float2 acc_a[kLy / 2], acc_x[kLy / 2];
 #pragma unroll
-        for (int t = 0; t < kLy; t++) acc_a[t] = acc_x[t] = 0.f;
+        for (int t = 0; t < kLy / 2; t++) acc_a[t] = acc_x[t] = make_float2(0.f, 0.f);
         int seg = 0;
         long long cur_blk = -1;
         // the two sample slots of an N = 32 tile hold partial sums of the same
@@ -427,11 +442,12 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
 #pragma unroll
                 for (int t = 0; t < kLy; t++) {
                     const int idx = pol * kNN + (kLy * h + t) * N + kx;
-                    float v = acc_a[t];
+                    float v = (t & 1) ? acc_a[t >> 1].y : acc_a[t >> 1].x;
                     if (add) v += dst[idx];
                     dst[idx] = v;
-                    acc_a[t] = 0.f;
                 }
+#pragma unroll
+                for (int t = 0; t < kLy / 2; t++) acc_a[t] = make_float2(0.f, 0.f);
                 // cross products: the X thread holds X conj(Y) at even rows, the Y
                 // thread Y conj(X) = conj(X conj(Y)) at odd rows
                 const float sgn = pol ? -1.f : 1.f;
@@ -439,14 +455,14 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
                 for (int t = 0; t < kLy / 2; t++) {
                     const int ly = kLy * h + 16 * (t >> 3) + 2 * (t & 7) + pol;
                     const int idx = 2 * kNN + ly * N + kx;
-                    float vr = acc_x[2 * t], vi = sgn * acc_x[2 * t + 1];
+                    float vr = acc_x[t].x, vi = sgn * acc_x[t].y;
                     if (add) {
                         vr += dst[idx];
                         vi += dst[idx + kNN];
                     }
                     dst[idx] = vr;
                     dst[idx + kNN] = vi;
-                    acc_x[2 * t] = acc_x[2 * t + 1] = 0.f;
+                    acc_x[t] = make_float2(0.f, 0.f);
                 }
             }
         };
@@ -478,9 +494,11 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
                     tc::tmem_ld16(tmem + lane_base + col + N, ri);
                     tc::tmem_wait_ld();
 #pragma unroll
-                    for (int t = 0; t < 16; t++) {
-                        const float fr = __uint_as_float(rr[t]), fi = __uint_as_float(ri[t]);
-                        acc_a[16 * cc + t] = fmaf(fr, fr, fmaf(fi, fi, acc_a[16 * cc + t]));
+                    for (int t = 0; t < 16; t += 2) {
+                        const float2 fr = make_float2(__uint_as_float(rr[t]), __uint_as_float(rr[t + 1]));
+                        const float2 fi = make_float2(__uint_as_float(ri[t]), __uint_as_float(ri[t + 1]));
+                        float2 &a = acc_a[(16 * cc + t) >> 1];
+                        a = __ffma2_rn(fr, fr, __ffma2_rn(fi, fi, a));     // fmaf(fr, fr, fmaf(fi, fi, a))
                     }
 #pragma unroll
                     for (int k = 0; k < 8; k++) {
@@ -490,9 +508,11 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
                         const float mr = pol ? o_r : e_r, mi = pol ? o_i : e_i;
                         const float sr = __shfl_xor_sync(0xffffffffu, pol ? e_r : o_r, 16);
                         const float si = __shfl_xor_sync(0xffffffffu, pol ? e_i : o_i, 16);
-                        const int a = 2 * (8 * cc + k);
-                        acc_x[a] = fmaf(mr, sr, fmaf(mi, si, acc_x[a]));            // Re own conj(other)
-                        acc_x[a + 1] = fmaf(mi, sr, fmaf(-mr, si, acc_x[a + 1]));   // Im own conj(other)
+                        // (Re, Im) own conj(other): fmaf(mr, sr, fmaf(mi, si, re)),
+                        // fmaf(mi, sr, fmaf(-mr, si, im)) as packed pairs
+                        float2 &a = acc_x[8 * cc + k];
+                        a = __ffma2_rn(make_float2(mr, mi), make_float2(sr, sr),
+                                       __ffma2_rn(make_float2(mi, -mr), make_float2(si, si), a));
                     }
                 }
                 tc::fence_before();

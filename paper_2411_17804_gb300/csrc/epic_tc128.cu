@@ -225,23 +225,33 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
             for (int t = s_warp[warp]; t < s_warp[warp + 1]; t++) {
                 float2 g0 = make_float2(0.f, 0.f), g1 = g0;
                 const int qe = s_base[t + 1];
-                int q = s_base[t] + lane;
-                float2 w_n = s_w[q];
-                uint2 e_n = E[s_e[q]];
-                for (; q < qe; q += 32) {
-                    const float2 w = w_n;
-                    const uint2 e = e_n;
-                    if (q + 32 < qe) {
-                        w_n = s_w[q + 32];
-                        e_n = E[s_e[q + 32]];
-                    }
+                // (re, im) += conj(W~) e per pol as packed FMAs, the roundings of
+                // fmaf(w.x, x.x, fmaf(-w.y, x.y, re)) and fmaf(w.x, x.y, fmaf(w.y, x.x, im))
+                auto mac = [&](const float2 w, const uint2 e) {
                     const float2 x = __half22float2(*reinterpret_cast<const __half2 *>(&e.x));
                     const float2 y = __half22float2(*reinterpret_cast<const __half2 *>(&e.y));
-                    g0.x = fmaf(w.x, x.x, fmaf(-w.y, x.y, g0.x));
-                    g0.y = fmaf(w.x, x.y, fmaf(w.y, x.x, g0.y));
-                    g1.x = fmaf(w.x, y.x, fmaf(-w.y, y.y, g1.x));
-                    g1.y = fmaf(w.x, y.y, fmaf(w.y, y.x, g1.y));
+                    const float2 wr = make_float2(w.x, w.x), wi = make_float2(-w.y, w.y);
+                    g0 = __ffma2_rn(wr, x, __ffma2_rn(wi, make_float2(x.y, x.x), g0));
+                    g1 = __ffma2_rn(wr, y, __ffma2_rn(wi, make_float2(y.y, y.x), g1));
+                };
+                // the lane's slots q, q + 32, ...: four at a time with every
+                // shared-memory load issued before the first use
+                int q = s_base[t] + lane;
+                for (; q + 96 < qe; q += 128) {
+                    float2 w[4];
+                    int en[4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        w[j] = s_w[q + 32 * j];
+                        en[j] = s_e[q + 32 * j];
+                    }
+                    uint2 e[4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) e[j] = E[en[j]];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) mac(w[j], e[j]);
                 }
+                for (; q < qe; q += 32) mac(s_w[q], E[s_e[q]]);
                 const uint32_t off = s_cell[t * 32 + lane];
                 if (off != 0xffffffffu) {
                     *reinterpret_cast<uint32_t *>(A + off) = tc::pack_half2(g0.x, g0.y);
@@ -392,19 +402,22 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
         const int ly = 32 * q + lane;
         const int lx0 = 32 * (int)rank + 16 * h;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        float xx[16], yy[16], xr[16], xi[16];
+        // packed accumulators: pw[t] = (|X|^2, |Y|^2), cx[t] = (Re, Im) X conj(Y)
+        float2 pw[16], cx[16];
 #pragma unroll
-        for (int t = 0; t < 16; t++) xx[t] = yy[t] = xr[t] = xi[t] = 0.f;
+        for (int t = 0; t < 16; t++) pw[t] = cx[t] = make_float2(0.f, 0.f);
         int seg = 0;
         long long cur_blk = -1;
         auto flush = [&](int stn, int c, int sgm) {
             float *dst = p.direct ? p.img + p.stations[stn].img_off + (size_t)c * 4 * kNN
                                   : p.partials + ((size_t)group * 2 + sgm) * 4 * kNN;
-            auto put = [&](int pl, float (&a)[16]) {
+            // plane pl: component c (0 = .x, 1 = .y) of the pairs in a
+            auto put = [&](int pl, const float2 (&a)[16], int c) {
                 float4 *d4 = reinterpret_cast<float4 *>(dst + (size_t)pl * kNN + (size_t)ly * kN + lx0);
 #pragma unroll
                 for (int v = 0; v < 4; v++) {
-                    float4 o = make_float4(a[4 * v], a[4 * v + 1], a[4 * v + 2], a[4 * v + 3]);
+                    float4 o = c ? make_float4(a[4 * v].y, a[4 * v + 1].y, a[4 * v + 2].y, a[4 * v + 3].y)
+                                 : make_float4(a[4 * v].x, a[4 * v + 1].x, a[4 * v + 2].x, a[4 * v + 3].x);
                     if (p.direct && p.accumulate) {
                         const float4 old = d4[v];
                         o.x += old.x;
@@ -415,12 +428,12 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
                     d4[v] = o;
                 }
             };
-            put(0, xx);
-            put(1, yy);
-            put(2, xr);
-            put(3, xi);
+            put(0, pw, 0);
+            put(1, pw, 1);
+            put(2, cx, 0);
+            put(3, cx, 1);
 #pragma unroll
-            for (int t = 0; t < 16; t++) xx[t] = yy[t] = xr[t] = xi[t] = 0.f;
+            for (int t = 0; t < 16; t++) pw[t] = cx[t] = make_float2(0.f, 0.f);
         };
         TcWalker wk;
         wk.init(p.volt, p.stations, p.C, p.T, s0, s1);
@@ -458,10 +471,13 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
                     const int t = 4 * qt + e;
                     const float a_r = __uint_as_float(ar[e]), a_i = __uint_as_float(ai[e]);
                     const float b_r = __uint_as_float(br[e]), b_i = __uint_as_float(bi[e]);
-                    xx[t] = fmaf(a_r, a_r, fmaf(a_i, a_i, xx[t]));
-                    yy[t] = fmaf(b_r, b_r, fmaf(b_i, b_i, yy[t]));
-                    xr[t] = fmaf(a_r, b_r, fmaf(a_i, b_i, xr[t]));      // Re X conj(Y)
-                    xi[t] = fmaf(a_i, b_r, fmaf(-a_r, b_i, xi[t]));     // Im X conj(Y)
+                    // |X|^2 = fmaf(a_r, a_r, fmaf(a_i, a_i, .)), |Y|^2 likewise;
+                    // Re X conj(Y) = fmaf(a_r, b_r, fmaf(a_i, b_i, .)),
+                    // Im X conj(Y) = fmaf(a_i, b_r, fmaf(-a_r, b_i, .)): packed pairs
+                    const float2 re = make_float2(a_r, b_r), im = make_float2(a_i, b_i);
+                    pw[t] = __ffma2_rn(re, re, __ffma2_rn(im, im, pw[t]));
+                    cx[t] = __ffma2_rn(make_float2(a_r, a_i), make_float2(b_r, b_r),
+                                       __ffma2_rn(make_float2(a_i, -a_r), make_float2(b_i, b_i), cx[t]));
                 }
             }
         }
