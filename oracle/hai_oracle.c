@@ -32,6 +32,9 @@
  *     accumulated EPIC image planes, normalised by 1/N^2 and multiplied by
  *     (-1)^d, read as gridded visibilities at the lags d (zero lag at cell
  *     (0, 0)).
+ *   - inter-station XBF (Eq. inter-station XBF): the direct DFT of the
+ *     station visibilities at every pixel, FP64 phase, all pairs or only the
+ *     pairs the inter-station XFFT grid drops.
  *   - inter-station XFFT (Eq. inter-station XFFT): station visibilities
  *     phased towards the beam direction with exp(+2 pi i s_k.dr / lambda) in
  *     FP64, gridded with a 2x2 bilinear kernel at uv = dr / cell; pairs whose
@@ -571,6 +574,69 @@ int orc_station_xfft(int n, int S, const double *pos, double lambda, double cell
 }
 
 /* Brute-force 2D DFT (O(n^4)), exponent +2 pi i l.j / n, for tiny grids. */
+/* ------------------------------------------------------------------------- */
+/* Inter-station XBF (Eq. inter-station XBF) with diagonal, unit polarisation  */
+/* weights: for every beam k, channel c and polarisation pair (al, be) the     */
+/* direct sum over ordered station pairs (m, q), autos once,                   */
+/*   I[ly][lx] = sum V^{al be}_{mq} exp(+2 pi i sigma . (r_m - r_q) / lambda), */
+/*   sigma = s_k + ((lx - n/2), (ly - n/2)) lambda / (n cell),                 */
+/* phase in FP64.  pair_set 0: every pair; 1: only the pairs the              */
+/* inter-station XFFT drops (2x2 footprint or its mirror's off the n grid;    */
+/* autos are never dropped).  Layouts as orc_station_xfft; img                 */
+/* [K][C][P][P][n][n][2].                                                      */
+/* ------------------------------------------------------------------------- */
+static int pair_dropped(int n, const double *pos, double cell, int m, int q) {
+    long a0, b0, c0, d0;
+    double fa, fb, fc, fd;
+    bilinear((pos[2 * m] - pos[2 * q]) / cell, &a0, &fa);
+    bilinear((pos[2 * m + 1] - pos[2 * q + 1]) / cell, &b0, &fb);
+    bilinear((pos[2 * q] - pos[2 * m]) / cell, &c0, &fc);
+    bilinear((pos[2 * q + 1] - pos[2 * m + 1]) / cell, &d0, &fd);
+    return !footprint_on_grid(n, a0, b0) || !footprint_on_grid(n, c0, d0);
+}
+
+int orc_station_xbf(int n, int S, const double *pos, double lambda, double cell, int K, const double *dir,
+                    const int64_t *vis, int C, int P, int pair_set, double *img) {
+    if (!is_pow2(n) || n < 4 || S <= 0 || K <= 0 || C < 0 || P < 1 || P > 2 || !(lambda > 0) || !(cell > 0) ||
+        (pair_set != 0 && pair_set != 1))
+        return ORC_ERR_ARG;
+    const long nn = (long)n * n, nbl = (long)S * (S + 1) / 2;
+    memset(img, 0, sizeof(double) * (size_t)K * C * P * P * nn * 2);
+#pragma omp parallel for collapse(4) schedule(dynamic, 1)
+    for (int kk = 0; kk < K; kk++)
+        for (int c = 0; c < C; c++)
+            for (int al = 0; al < P; al++)
+                for (int be = 0; be < P; be++) {
+                    double *o = img + (((((size_t)kk * C + c) * P + al) * P + be) * nn) * 2;
+                    for (int m = 0; m < S; m++)
+                        for (int q = 0; q < S; q++) {
+                            if (m != q && pair_set == 1 && !pair_dropped(n, pos, cell, m, q)) continue;
+                            if (m == q && pair_set == 1) continue;
+                            double vr, vi;
+                            if (m >= q) {      /* stored: V^{al be}_{mq} */
+                                const int64_t *v = vis + (((((size_t)kk * C + c) * nbl + (long)m * (m + 1) / 2 + q) * P + al) * P + be) * 2;
+                                vr = (double)v[0];
+                                vi = (double)v[1];
+                            } else {           /* V^{al be}_{mq} = conj(V^{be al}_{qm}) */
+                                const int64_t *v = vis + (((((size_t)kk * C + c) * nbl + (long)q * (q + 1) / 2 + m) * P + be) * P + al) * 2;
+                                vr = (double)v[0];
+                                vi = -(double)v[1];
+                            }
+                            const double dx = pos[2 * m] - pos[2 * q], dy = pos[2 * m + 1] - pos[2 * q + 1];
+                            for (int ly = 0; ly < n; ly++)
+                                for (int lx = 0; lx < n; lx++) {
+                                    const double sx = dir[2 * kk] + (lx - n / 2) * lambda / (n * cell);
+                                    const double sy = dir[2 * kk + 1] + (ly - n / 2) * lambda / (n * cell);
+                                    const double ph = ORC_TWO_PI * (sx * dx + sy * dy) / lambda;
+                                    const double cr = cos(ph), ci = sin(ph);
+                                    o[2 * (ly * n + lx)] += vr * cr - vi * ci;
+                                    o[2 * (ly * n + lx) + 1] += vr * ci + vi * cr;
+                                }
+                        }
+                }
+    return ORC_OK;
+}
+
 void orc_dft2d_brute(int n, const double *re, const double *im, double *ore, double *oim) {
     for (int ly = 0; ly < n; ly++)
         for (int lx = 0; lx < n; lx++) {

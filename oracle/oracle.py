@@ -69,6 +69,8 @@ def lib():
             L.orc_station_xfft.argtypes = [c_int, c_int, _f64p, ctypes.c_double, ctypes.c_double, c_int,
                                            _f64p, _i64p, c_int, c_int, _f64p,
                                            ctypes.POINTER(ctypes.c_int64)]
+            L.orc_station_xbf.argtypes = [c_int, c_int, _f64p, ctypes.c_double, ctypes.c_double, c_int,
+                                          _f64p, _i64p, c_int, c_int, c_int, _f64p]
             L.orc_dft2d_brute.argtypes = [c_int, _f64p, _f64p, _f64p, _f64p]
             L.orc_dft2d_brute.restype = None
             _lib = L
@@ -290,6 +292,24 @@ def station_epic(n: int, pos_m, lam_m: float, cell_m: float, dirs, beams: np.nda
         anchors, taps, dropped = station_epic_layout(n, pos_m, lam_m, cell_m, dirs[k])
         out.append(epic_image(n, anchors, taps, np.ascontiguousarray(beams[k])))
     return np.stack(out), dropped
+
+
+def station_xbf(n: int, pos_m, lam_m: float, cell_m: float, dirs, vis: np.ndarray, offgrid_only=False):
+    """Images of Eq. (inter-station XBF): the direct FP64 DFT of station
+    visibilities int64 [K][C][S(S+1)/2][P][P][2] over every ordered station
+    pair (autos once) at the pixels sigma = s_k + (l - n/2) lambda / (n cell),
+    or (offgrid_only) over the pairs the inter-station XFFT grid drops.
+    Returns complex [K][C][P][P][n][n]."""
+    pos = np.ascontiguousarray(pos_m, np.float64)
+    dirs = np.ascontiguousarray(dirs, np.float64)
+    vis = np.ascontiguousarray(vis, np.int64)
+    K, C, nbl, P, _, _ = vis.shape
+    S = pos.shape[0]
+    assert nbl == S * (S + 1) // 2 and dirs.shape == (K, 2)
+    img = np.empty((K, C, P, P, n, n, 2))
+    _check(lib().orc_station_xbf(n, S, pos, lam_m, cell_m, K, dirs, vis, C, P, 1 if offgrid_only else 0, img),
+           "station_xbf")
+    return img[..., 0] + 1j * img[..., 1]
 
 
 def xfft_as_epic_planes(ximg: np.ndarray) -> np.ndarray:

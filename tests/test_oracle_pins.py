@@ -561,3 +561,67 @@ def test_station_epic_equals_station_xfft_for_stations_on_cells():
     assert off == 0
     for k in range(2):
         assert rel(O.xfft_as_epic_planes(ximg[k]), epic[k]) < 1e-6
+
+
+# ---------------------------------------------------------------- inter-station XBF
+def _hermitian_vis(rng, K, C, S, P, lo=-500, hi=500):
+    """Random int64 station visibilities whose autos are what a correlator
+    gives: XX, YY real and YX = conj(XY)."""
+    vis = rng.integers(lo, hi, (K, C, S * (S + 1) // 2, P, P, 2)).astype(np.int64)
+    for m in range(S):
+        bl = m * (m + 1) // 2 + m
+        for p in range(P):
+            vis[..., bl, p, p, 1] = 0
+        if P == 2:
+            vis[..., bl, 1, 0, 0] = vis[..., bl, 0, 1, 0]
+            vis[..., bl, 1, 0, 1] = -vis[..., bl, 0, 1, 1]
+    return vis
+
+
+def test_station_xbf_array_factor_closed_form():
+    """Unit visibilities for every pair: the image is |sum_m exp(2 pi i
+    sigma . r_m / lambda)|^2, the squared array factor, at every pixel."""
+    n, lam, cell, S = 16, 3.0, 7.3, 11
+    rng = np.random.default_rng(21)
+    pos = rng.uniform(-40.0, 40.0, (S, 2))
+    vis = np.zeros((1, 1, S * (S + 1) // 2, 1, 1, 2), np.int64)
+    vis[..., 0] = 1
+    s_k = np.array([0.021, -0.034])
+    img = O.station_xbf(n, pos, lam, cell, s_k[None], vis)[0, 0, 0, 0]
+    ly, lx = np.mgrid[0:n, 0:n]
+    sx = s_k[0] + (lx - n // 2) * lam / (n * cell)
+    sy = s_k[1] + (ly - n // 2) * lam / (n * cell)
+    af = np.zeros((n, n), complex)
+    for m in range(S):
+        af += np.exp(2j * np.pi * (sx * pos[m, 0] + sy * pos[m, 1]) / lam)
+    assert np.abs(img - np.abs(af) ** 2).max() < 1e-10 * S * S
+
+
+def test_station_xbf_equals_station_xfft_on_whole_cells():
+    """Stations on whole cells with every pair on the grid: gridding is exact
+    and the FFT evaluates the same sum, so XBF (direct DFT) = XFFT, steering
+    included, for every polarisation pair."""
+    n, lam, cell, S = 16, 3.0, 5.0, 8
+    pos = _stations_on_cells(n, S, cell, seed=31)
+    dirs = np.array([[0.0, 0.0], [0.11, -0.07]])
+    vis = _hermitian_vis(np.random.default_rng(32), 2, 2, S, 2)
+    xfft, off = O.station_xfft(n, pos, lam, cell, dirs, vis)
+    assert off == 0
+    xbf = O.station_xbf(n, pos, lam, cell, dirs, vis)
+    assert rel(xbf, xfft) < 1e-10
+
+
+def test_station_xbf_images_exactly_the_pairs_the_grid_drops():
+    """A core and a far tail, all on whole cells: the XFFT image of the kept
+    pairs plus the XBF image of the dropped pairs is the XBF image of all
+    pairs."""
+    n, lam, cell, S = 16, 3.0, 5.0, 9
+    pos = _stations_on_cells(n, S - 3, cell, seed=41, far=3)
+    dirs = np.array([[0.05, 0.02]])
+    vis = _hermitian_vis(np.random.default_rng(42), 1, 2, S, 2)
+    xfft, off = O.station_xfft(n, pos, lam, cell, dirs, vis)
+    assert off >= 3 * (S - 3)
+    part = O.station_xbf(n, pos, lam, cell, dirs, vis, offgrid_only=True)
+    full = O.station_xbf(n, pos, lam, cell, dirs, vis)
+    assert rel(xfft + part, full) < 1e-10
+    assert np.abs(part).max() > 0.1 * np.abs(full).max()
