@@ -340,6 +340,45 @@ hai_status hai_station_epic_layout_create(hai_ctx *ctx, const hai_vis_layout_des
                                           long long *n_dropped);
 
 /* ---------------------------------------------------------------------------
+ * Inter-station correlator beamforming (Eq. inter-station XBF) with diagonal,
+ * unit polarisation weights: for beam k, channel c and polarisation pair
+ * (a, b), at the same pixels as hai_xfft_station_image (pixel l looks along
+ * s_k + (l - N/2) lambda / (N cell)),
+ *   I[l] = sum over ordered station pairs (m, n) of the set, autos once, of
+ *          V^{ab}_{mn} exp(+2 pi i sigma_l . (r_m - r_n) / lambda),
+ * evaluated directly (no gridding).  Pair sets:
+ *   HAI_XBF_ALL_PAIRS      every pair and every auto;
+ *   HAI_XBF_OFFGRID_PAIRS  only the pairs the inter-station XFFT drops (its
+ *                          2x2 footprint or its mirror's off the N grid), so
+ *                          that hai_xfft_station_image followed by this call
+ *                          with accumulate = 1 images every pair.
+ * The layout holds the geometry phases exp(+2 pi i (l - N/2).(r_m - r_n) /
+ * (N cell)) of every pair and pixel (FP64 phase on the GPU, fp16 storage:
+ * 4 N^2 bytes per pair, 1.45 GB for 5,515 pairs at N = 256) and a coefficient
+ * buffer for up to n_dir * max_channels images; hai_xbf_layout_info reports
+ * the pair count and these bytes.  HAI_ERR_NO_MEMORY if they do not fit.
+ * desc as for hai_vis_layout_create (n_pol 2; grid_n a power of two in
+ * 16..512). */
+enum { HAI_XBF_ALL_PAIRS = 0, HAI_XBF_OFFGRID_PAIRS = 1 };
+typedef struct hai_xbf_layout hai_xbf_layout;
+hai_status hai_xbf_layout_create(hai_ctx *ctx, const hai_vis_layout_desc *desc, int pair_set, int max_channels,
+                                 hai_xbf_layout **out);
+void hai_xbf_layout_destroy(hai_xbf_layout *layout);
+hai_status hai_xbf_layout_info(const hai_xbf_layout *layout, long long *n_pairs, long long *device_bytes);
+
+/* Images of the layout's pair set.
+ *   vis  device int32 [K][C][S(S+1)/2][2][2][2] (hai_correlate's output for
+ *        the K*C channels of hai_beams_to_corr); C <= max_channels
+ *   img  device float [K][C][4][N][N]: XX, YY, Re XY, Im XY, 16-byte aligned;
+ *        overwritten (accumulate = 0) or added to (accumulate = 1)
+ * One tcgen05 GEMM, img[rows][pixels] = A x Phi^T, fp16 operands and FP32
+ * accumulation: the per-image coefficients A (from V and the FP64 steering
+ * phasor exp(+2 pi i s_k . (r_m - r_n) / lambda)) are scaled by a power of two
+ * per image to keep them in fp16 range, which the epilogue undoes. */
+hai_status hai_xbf_station_image(hai_ctx *ctx, const hai_xbf_layout *layout, const int32_t *vis, int C, float *img,
+                                 int accumulate, void *stream);
+
+/* ---------------------------------------------------------------------------
  * EPIC image, FP32 path, without any device allocation.  (The paper has no
  * counterpart: this is an interface for callers, not a step of the method.)
  *

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <string>
@@ -106,3 +107,16 @@ bool epic_large_supported(int grid_n);
 size_t epic_large_scratch_bytes(int grid_n, int box_h);
 hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
                              cudaStream_t st);
+
+// ---------------------------------------------------------------- station pairs
+// The inter-station XFFT keeps a pair when the 2x2 bilinear footprint of its
+// uv = (r_m - r_n) / cell and of its mirror -uv both lie in [-N/2, N/2 - 1]^2
+// (du, dv in cells, FP64); the XBF images the pairs it drops.
+inline bool station_pair_kept(int N, double du, double dv) {
+    auto on_grid = [&](double u, double v) {
+        const double a = floor(u), b = floor(v);
+        return a >= -N / 2 && a + 1 <= N / 2 - 1 && b >= -N / 2 && b + 1 <= N / 2 - 1;
+    };
+    return on_grid(du, dv) && on_grid(-du, -dv);
+}
+

@@ -296,7 +296,6 @@ extern "C" hai_status hai_vis_layout_create(hai_ctx *ctx, const hai_vis_layout_d
     std::vector<char> ok(nbl);
     long umin = N, vmin = N, umax = -N, vmax = -N;
     long long dropped = 0;
-    auto on_grid = [&](long u0, long v0) { return u0 >= -N / 2 && u0 + 1 <= N / 2 - 1 && v0 >= -N / 2 && v0 + 1 <= N / 2 - 1; };
     for (int m = 0, bl = 0; m < S; m++)
         for (int n = 0; n <= m; n++, bl++) {
             const double du = (d->pos_m[2 * m] - d->pos_m[2 * n]) / d->cell_m;
@@ -310,7 +309,7 @@ extern "C" hai_status hai_vis_layout_create(hai_ctx *ctx, const hai_vis_layout_d
             fv[bl] = (float)(dv - b);
             mfu[bl] = (float)(-du - ma);
             mfv[bl] = (float)(-dv - mb);
-            ok[bl] = on_grid(cu[bl], cv[bl]) && on_grid(mcu[bl], mcv[bl]);
+            ok[bl] = station_pair_kept(N, du, dv);
             if (!ok[bl]) {
                 dropped++;
                 continue;

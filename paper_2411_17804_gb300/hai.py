@@ -82,6 +82,11 @@ def _declare(L):
     L.hai_vis_layout_offgrid.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
     L.hai_station_epic_layout_create.argtypes = [_vp, ctypes.POINTER(_VisLayoutDesc), _int, ctypes.POINTER(_vp),
                                                  ctypes.POINTER(ctypes.c_longlong)]
+    L.hai_xbf_layout_create.argtypes = [_vp, ctypes.POINTER(_VisLayoutDesc), _int, _int, ctypes.POINTER(_vp)]
+    L.hai_xbf_layout_destroy.argtypes = [_vp]
+    L.hai_xbf_layout_destroy.restype = None
+    L.hai_xbf_layout_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    L.hai_xbf_station_image.argtypes = [_vp, _vp, _vp, _int, _vp, _int, _vp]
     L.hai_xfft_station_image.argtypes = [_vp, _vp, _vp, _int, _vp, _vp]
     L.hai_profile_enable.argtypes = [_vp, _int, _int]
     L.hai_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
@@ -375,6 +380,52 @@ def hai_station_epic_layout_create(ctx, pos_m, lambda_m: float, cell_m: float, g
     _check(load().hai_station_epic_layout_create(ctx, ctypes.byref(desc), k, ctypes.byref(h), ctypes.byref(dropped)),
            "hai_station_epic_layout_create")
     return Layout(h, S, grid_n, 1, n_pol), dropped.value
+
+
+HAI_XBF_ALL_PAIRS = 0
+HAI_XBF_OFFGRID_PAIRS = 1
+
+
+class XbfLayout:
+    """Handle of a hai_xbf_layout with its sizes."""
+
+    def __init__(self, handle, S, N, K, max_channels):
+        self.handle, self.S, self.N, self.K, self.max_channels = handle, S, N, K, max_channels
+
+
+def hai_xbf_layout_create(ctx, pos_m, lambda_m: float, cell_m: float, grid_n: int, dirs=None,
+                          pair_set: int = HAI_XBF_ALL_PAIRS, max_channels: int = 1) -> XbfLayout:
+    pos = np.ascontiguousarray(pos_m, np.float64)
+    S = pos.shape[0]
+    if pos.shape != (S, 2):
+        raise ValueError("pos_m must be [S][2]")
+    d = None if dirs is None else np.ascontiguousarray(dirs, np.float64)
+    K = 1 if d is None else d.shape[0]
+    desc = _VisLayoutDesc(S, pos.ctypes.data, lambda_m, cell_m, grid_n, 2, K, None if d is None else d.ctypes.data)
+    h = _vp()
+    _check(load().hai_xbf_layout_create(ctx, ctypes.byref(desc), pair_set, max_channels, ctypes.byref(h)),
+           "hai_xbf_layout_create")
+    return XbfLayout(h, S, grid_n, K, max_channels)
+
+
+def hai_xbf_layout_destroy(layout: XbfLayout):
+    load().hai_xbf_layout_destroy(layout.handle)
+
+
+def hai_xbf_layout_info(layout: XbfLayout):
+    """(pairs in the set, device bytes of the phase and coefficient buffers)."""
+    n, b = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load().hai_xbf_layout_info(layout.handle, ctypes.byref(n), ctypes.byref(b)), "hai_xbf_layout_info")
+    return n.value, b.value
+
+
+def hai_xbf_station_image(ctx, layout: XbfLayout, vis, C: int, img, accumulate: int = 0, stream=None):
+    import torch
+    S, N, K = layout.S, layout.N, layout.K
+    vp = _dev_ptr(vis, torch.int32, "vis", K * C * (S * (S + 1) // 2) * 8) if C > 0 else 0
+    ip = _dev_ptr(img, torch.float32, "img", K * C * 4 * N * N) if C > 0 else 0
+    _check(load().hai_xbf_station_image(ctx, layout.handle, vp, C, ip, accumulate, _stream(stream)),
+           "hai_xbf_station_image")
 
 
 def hai_vis_layout_destroy(layout: VisLayout):
