@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--no-components", action="store_true")
     ap.add_argument("--channels", type=int, default=0,
                     help="image only this many channels (small cases for profiling)")
-    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "bf"], default=None,
+    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "bf", "xbf", "fc"], default=None,
                     help="run one small case of a kernel twice, untimed, and exit (for ncu captures)")
     return ap.parse_args()
 
@@ -532,7 +532,22 @@ def hierarchy_component(hai, ctx, flush, peaks):
                                       "peak": pk, "unit": "TFLOP/s"}}}
     for r in out["roofline"].values():
         r["frac"] = r["achieved"] / r["peak"]
+    # XBF of the pairs the station grid drops (the 65 km tail), added onto the
+    # XFFT image: one tensor-core GEMM against the layout's geometry phases
+    xl = hai.hai_xbf_layout_create(ctx, centres, H.station.lam_m, H.cell_m, n, dirs, hai.HAI_XBF_OFFGRID_PAIRS, C)
+    xpairs, xbytes = hai.hai_xbf_layout_info(xl)
+    xms = time_call(lambda st: hai.hai_xbf_station_image(ctx, xl, vis, C, img, 1, st), 5, 2, flush)
+    rows = K * C * 4
+    kd = -(-2 * xpairs // 64) * 64
+    xflop = 2.0 * (-(-rows // 128) * 128) * kd * n * n
+    out_xbf = {"what": "XBF of the pairs the station grid drops, accumulated onto the XFFT image",
+               "pairs": xpairs, "phase_bytes": xbytes, "ms": xms,
+               "roofline": {"bound": "tensor", "achieved": xflop / (xms * 1e-3) / 1e12, "peak": pk,
+                            "unit": "TFLOP/s", "frac": xflop / (xms * 1e-3) / 1e12 / pk,
+                            "flop": xflop}}
+    hai.hai_xbf_layout_destroy(xl)
     emma = plan_mma_flops(ne_grid) * K * C * T
+    out["station_xbf_offgrid"] = out_xbf
     out["station_epic"] = {
         "what": "inter-station EPIC on the same requantised beams (alternative to correlator + XFFT)",
         "grid": ne_grid, "stations_dropped": elays[0][1], "ms": ems,
@@ -543,6 +558,7 @@ def hierarchy_component(hai, ctx, flush, peaks):
     out["paper_cost_inter_station"] = paper_cost("SKA-low-core", "inter", C * K, T,
                                                  ms["station_correlator"] + ms["station_xfft"], "XFFT")
     out["paper_cost_inter_station"]["measured_epic_ms"] = ems
+    out["paper_cost_inter_station"]["measured_xbf_offgrid_ms"] = xms
     for lay_k, _ in elays:
         hai.hai_layout_destroy(lay_k)
     del eimg
@@ -590,6 +606,25 @@ def run_case(name):
         img = torch.empty((C, 4, 128, 128), device="cuda")
         for _ in range(2):
             hai.hai_epic_image(ctx, lay, v, C, T, hai.HAI_PREC_FP16, img, 0)
+    elif name == "xbf":                   # the hierarchical array's dropped pairs, 4 beams x 8 channels
+        H = I.HierarchyConfig()
+        centres = I.station_centres(H)
+        S, n, K, C = len(centres), H.grid_n, 4, 8
+        dirs = I.beam_directions(H.n_beam, H.station.lam_m, H.station.diameter_m)[:K]
+        g = torch.Generator(device="cuda").manual_seed(3)
+        vis = torch.randint(-2**20, 2**20, (K * C, S * (S + 1) // 2, 2, 2, 2), dtype=torch.int32, device="cuda",
+                            generator=g)
+        xl = hai.hai_xbf_layout_create(ctx, centres, H.station.lam_m, H.cell_m, n, dirs, hai.HAI_XBF_OFFGRID_PAIRS, C)
+        img = torch.empty((K * C, 4, n, n), device="cuda")
+        for _ in range(2):
+            hai.hai_xbf_station_image(ctx, xl, vis, C, img, 0)
+        torch.cuda.synchronize()
+        hai.hai_xbf_layout_destroy(xl)
+    elif name == "fc":                    # FFT correlator on 16 channels of 512^2 images (67 MB in)
+        img = torch.randn((16, 4, 512, 512), device="cuda")
+        grid = torch.empty((16, 2, 2, 512, 512, 2), device="cuda")
+        for _ in range(2):
+            hai.hai_fft_correlate(ctx, img, 16, 512, 2, grid)
     torch.cuda.synchronize()
     hai.hai_destroy(ctx)
     print(json.dumps({"case": name, "ok": True}))
