@@ -348,7 +348,7 @@ def bf_component(hai, ctx, flush, peaks):
 # DRAM bytes (read + write) of one epic_tc_kernel<64> launch over 16 channels of
 # the SKA-low station, from an ncu capture of `bench.py --case tc64` with the
 # kernel as it is now; traffic grows in proportion to the channels imaged.
-TC64_TRAFFIC_16CH = 33.656576e6
+TC64_TRAFFIC_16CH = 33.657344e6
 
 
 def traffic_tc64(cfg, C):
