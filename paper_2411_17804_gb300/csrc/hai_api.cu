@@ -186,6 +186,7 @@ static void layout_free(hai_layout *L) {
     cudaFree(L->d_tc_tables);
     cudaFree(L->d_tc_station);
     cudaFree(L->d_large_scratch);
+    cudaFree(L->d_big);
     delete L;
 }
 
@@ -296,6 +297,13 @@ extern "C" hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *d, 
         L->tc_groups = n == 128 ? std::min(ctx->num_sms / 4, epic_tc128_max_groups(ctx, ne, shared_bytes))
                                 : ctx->num_sms;
         if (L->tc_groups <= 0) L->tc_groups = 1;
+    }
+    if (e == cudaSuccess && epic_big_supported(L)) {
+        const hai_status bs = epic_big_prepare(L);
+        if (bs != HAI_OK) {
+            layout_free(L);
+            return bs;
+        }
     }
     if (e != cudaSuccess) {
         layout_free(L);
@@ -409,5 +417,6 @@ extern "C" hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *L, const in
         return HAI_OK;
     }
     if (prec == HAI_PREC_FP32) return epic_fp32_launch(L, volt, C, T, img, accumulate, st);
+    if (prec == HAI_PREC_FP16 && L->grid_n >= 256) return epic_big_launch(L, volt, C, T, img, accumulate, st);
     return epic_tc_launch(L, volt, C, T, img, accumulate, st, prec == HAI_PREC_FP16_SPLIT ? 1 : 0);
 }

@@ -60,6 +60,11 @@ struct hai_layout {
     void *d_large_scratch = nullptr;
     size_t large_scratch_bytes = 0;
     void *d_tc_station = nullptr;
+    // tensor-core path of large grids (N = 256, 512): DFT operands and the
+    // stage scratch of one batch of (channel, sample) pairs
+    void *d_big = nullptr;
+    void *big_b1 = nullptr, *big_b2 = nullptr, *big_a1 = nullptr, *big_a2 = nullptr;
+    long long big_batch = 0;
 };
 
 // ---------------------------------------------------------------- errors
@@ -107,6 +112,12 @@ bool epic_large_supported(int grid_n);
 size_t epic_large_scratch_bytes(int grid_n, int box_h);
 hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
                              cudaStream_t st);
+// FP16 tensor-core EPIC for N = 256, 512 (box <= N/2, box height <= 128):
+// gridding, stage-1 GEMM and stage-2 GEMM + squaring through an HBM scratch.
+bool epic_big_supported(const hai_layout *L);
+hai_status epic_big_prepare(hai_layout *L);
+hai_status epic_big_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
+                           cudaStream_t st);
 
 // ---------------------------------------------------------------- station pairs
 // The inter-station XFFT keeps a pair when the 2x2 bilinear footprint of its

@@ -304,10 +304,63 @@ def test_dense_allsky_full_cadence_sampled_channel(hai, ctx):
     assert rel_err_planes(img[:1].cpu().numpy(), want).max() < FP32_TOL
 
 
-def test_large_grid_fp16_is_reported_unsupported(hai, ctx):
+@pytest.mark.parametrize("case,C,T", [
+    ("n512", 2, 3),           # the dense lattice: 128 x 128 box, 1 x 1 unit taps
+    ("n512", 3, 5),
+    ("n256", 2, 7),           # the SKA station (3 x 3 Gaussian taps) on a 256^2 grid
+    ("n256_cplx", 1, 4),      # random complex taps, random anchors over a 100 x 120 box
+])
+def test_large_grid_tensor_cores_match_oracle(hai, ctx, case, C, T):
+    """FP16 tensor-core path of the large grids (gridding, stage-1 GEMM into
+    an HBM operand, stage-2 GEMM with the squaring) against the oracle."""
+    if case == "n512":
+        cfg, pos, anchors, taps = _dense()
+        n = 512
+    elif case == "n256":
+        pos, anchors, taps = station(I.SKA_LOW_STATION_256)
+        n = 256
+    else:
+        rng = np.random.default_rng(3)
+        n, ne, k = 256, 150, 3
+        anchors = np.stack([rng.integers(40, 138, ne), rng.integers(30, 148, ne)], axis=1).astype(np.int32)
+        taps = rng.standard_normal((ne, k, k, 2)).astype(np.float32)
+        pos = anchors
+    volt = I.random_voltages((C, T, 2, len(anchors), 2), seed=C * 7 + T)
+    got = run_epic(hai, ctx, anchors, taps, n, volt, hai.HAI_PREC_FP16)
+    want = O.epic_image(n, anchors, taps, volt.numpy())
+    assert rel_err_planes(got, want).max() < REDUCED_TOL
+    # accumulate onto the first result
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, 2)
+    img = torch.from_numpy(got).cuda()
+    hai.hai_epic_image(ctx, lay, volt.cuda(), C, T, hai.HAI_PREC_FP16, img, 1)
+    hai.hai_sync(ctx)
+    assert rel_err_planes(img.cpu().numpy(), 2 * want).max() < REDUCED_TOL
+    hai.hai_layout_destroy(lay)
+
+
+def test_large_grid_tensor_cores_full_dense_cadence_sampled_channel(hai, ctx):
+    """The dense all-sky lattice's full cadence (16 channels x 100 samples,
+    two scratch batches) in one call; the oracle recomputes two channels,
+    one of them split across the batches."""
     cfg, pos, anchors, taps = _dense()
+    volt = I.station_voltages(cfg, pos, device="cuda")
+    n, C, T = cfg.grid_n, cfg.n_chan, cfg.n_time
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, 2)
+    img = torch.empty((C, 4, n, n), device="cuda")
+    hai.hai_epic_image(ctx, lay, volt, C, T, hai.HAI_PREC_FP16, img, 0)
+    hai.hai_sync(ctx)
+    for c in (0, 8):
+        want = O.epic_image(n, anchors, taps, volt[c:c + 1].cpu().numpy())
+        assert rel_err_planes(img[c:c + 1].cpu().numpy(), want).max() < REDUCED_TOL, c
+    hai.hai_layout_destroy(lay)
+
+
+def test_large_grid_fp16_tall_box_is_reported_unsupported(hai, ctx):
+    """Boxes taller than 128 cells at N = 512 keep to the FP32 path."""
+    anchors = np.array([[10, 10], [40, 200]], np.int32)
+    taps = np.ones((2, 1, 1, 2), np.float32)
     lay = hai.hai_layout_create(ctx, anchors, taps, 512, 2)
-    volt = torch.zeros((1, 2, 2, len(pos), 2), dtype=torch.int8, device="cuda")
+    volt = torch.zeros((1, 2, 2, 2, 2), dtype=torch.int8, device="cuda")
     img = torch.zeros((1, 4, 512, 512), device="cuda")
     with pytest.raises(hai.HaiError) as e:
         hai.hai_epic_image(ctx, lay, volt, 1, 2, hai.HAI_PREC_FP16, img, 0)
