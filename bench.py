@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--no-components", action="store_true")
     ap.add_argument("--channels", type=int, default=0,
                     help="image only this many channels (small cases for profiling)")
-    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "bf", "xbf", "fc"], default=None,
+    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "bf", "xbf", "fc", "big"], default=None,
                     help="run one small case of a kernel twice, untimed, and exit (for ncu captures)")
     return ap.parse_args()
 
@@ -451,6 +451,17 @@ def dense_component(hai, ctx, flush, peaks, sms):
     flop = epic_flops_per_unit(cfg) * units
     peak = fp32_alu_peak_tflops(sms, float(peaks.get("sm_max_mhz", 2070.0)))
     ach = flop / (ms * 1e-3) / 1e12
+    # the tensor-core path of the same cadence (fp16 operands, FP32 accumulation)
+    tc_ms = time_call(lambda st: hai.hai_epic_image(ctx, lay, volt, C, T, hai.HAI_PREC_FP16, img, 0, st), 5, 2, flush)
+    bxp, byp = 128, 128                                  # the lattice's box, padded to the tiles
+    s1 = 2.0 * 128 * 256 * (2 * bxp) * (C * T * P) * (byp // 128) * (n // 128)
+    s2 = 2.0 * 128 * 128 * (2 * byp) * C * T * (n // 64) ** 2
+    pkt = float(peaks.get("bf16_tflops", 1900.0))
+    tc_ach = (s1 + s2) / (tc_ms * 1e-3) / 1e12
+    tensor = {"precision": "fp16", "ms": tc_ms, "units_per_s": units / (tc_ms * 1e-3), "over_fp32": ms / tc_ms,
+              "roofline": {"bound": "tensor", "achieved": tc_ach, "peak": pkt, "unit": "TFLOP/s",
+                           "frac": tc_ach / pkt, "executed_flop": s1 + s2,
+                           "peak_source": "of measured bf16_tflops (fp16 nominal ratio 1)"}}
     hai.hai_layout_destroy(lay)
     # FFT correlator on the accumulated images: redundant-baseline sums of
     # the lattice at every lag (the inverse FFT once per cadence)
@@ -464,6 +475,7 @@ def dense_component(hai, ctx, flush, peaks, sms):
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                          "flop_per_unit": epic_flops_per_unit(cfg),
                          "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x max SM clock"},
+            "tensor_cores": tensor,
             "fft_correlator": {
                 "what": "inverse FFT of the accumulated images -> visibilities summed per lag, all 4 pol pairs",
                 "ms": fc_ms, "lags_per_s": C * P * P * n * n / (fc_ms * 1e-3),
@@ -620,6 +632,15 @@ def run_case(name):
             hai.hai_xbf_station_image(ctx, xl, vis, C, img, 0)
         torch.cuda.synchronize()
         hai.hai_xbf_layout_destroy(xl)
+    elif name == "big":                   # the dense lattice on tensor cores, 4 channels x 20 samples
+        cfg = I.DENSE_ALLSKY_16384
+        pos = I.station_layout(cfg)
+        an, tp = I.station_kernel(cfg, pos)
+        lay = hai.hai_layout_create(ctx, an, tp, 512, 2)
+        v = I.random_voltages((4, 20, 2, len(pos), 2), seed=5, device="cuda")
+        img = torch.empty((4, 4, 512, 512), device="cuda")
+        for _ in range(2):
+            hai.hai_epic_image(ctx, lay, v, 4, 20, hai.HAI_PREC_FP16, img, 0)
     elif name == "fc":                    # FFT correlator on 16 channels of 512^2 images (67 MB in)
         img = torch.randn((16, 4, 512, 512), device="cuda")
         grid = torch.empty((16, 2, 2, 512, 512, 2), device="cuda")
