@@ -98,7 +98,7 @@ struct S1Params {
     unsigned *status;
 };
 
-__global__ void __launch_bounds__(256, 1) big_s1_kernel(const S1Params p) {
+__global__ void __launch_bounds__(384, 1) big_s1_kernel(const S1Params p) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t full[kS1Stages], empty[kS1Stages], dfull[2], dempty[2];
     __shared__ uint32_t tslot;
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256, 1) big_s1_kernel(const S1Params p) {
         }
         for (int b = 0; b < 2; b++) {
             tc::mbar_init(&dfull[b], 1);
-            tc::mbar_init(&dempty[b], 128);
+            tc::mbar_init(&dempty[b], 256);
         }
         tc::mbar_fence_init();
     }
@@ -163,9 +163,10 @@ __global__ void __launch_bounds__(256, 1) big_s1_kernel(const S1Params p) {
             }
         }
     } else if (warp >= 4) {
-        // epilogue: thread = row y of the tile; its 128 (re, im) values -> the
-        // stage-2 operand rows (l_x, pol), K index 2 y + re/im
-        const int q = warp & 3, row = q * 32 + lane;
+        // epilogue, warps 4-11: thread = row y of the tile and one half (h) of
+        // its 128 (re, im) values -> the stage-2 operand rows (l_x, pol), K
+        // index 2 y + re/im
+        const int q = warp & 3, row = q * 32 + lane, h = (warp - 4) >> 2;
         long long gt = 0;
         for (long long tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, gt++) {
             const int b = (int)(gt & 1);
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(256, 1) big_s1_kernel(const S1Params p) {
             tc::mbar_wait(&dfull[b], (uint32_t)((gt >> 1) & 1), p.status);
             tc::fence_after();
 #pragma unroll 1
-            for (int ch = 0; ch < 8; ch++) {                   // 16 l_x values per chunk
+            for (int ch = 4 * h; ch < 4 * h + 4; ch++) {       // 16 l_x values per chunk
                 uint32_t rr[16], ri[16];
                 tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * 256u + (uint32_t)(16 * ch), rr);
                 tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * 256u + 128u + (uint32_t)(16 * ch), ri);
@@ -499,7 +500,7 @@ hai_status epic_big_launch(const hai_layout *L, const int8_t *volt, int C, int T
         p1.nfield = nfield;
         p1.ntiles = nfield * g.yb * g.lb1;
         p1.status = ctx->d_status;
-        big_s1_kernel<<<(unsigned)std::min<long long>(p1.ntiles, ctx->num_sms), 256, s1_smem, st>>>(p1);
+        big_s1_kernel<<<(unsigned)std::min<long long>(p1.ntiles, ctx->num_sms), 384, s1_smem, st>>>(p1);
         S2Params p2;
         p2.a2 = static_cast<const uint8_t *>(L->big_a2);
         p2.b2 = static_cast<const uint8_t *>(L->big_b2);
