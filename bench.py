@@ -546,7 +546,8 @@ def hierarchy_component(hai, ctx, flush, peaks):
         r["frac"] = r["achieved"] / r["peak"]
     # XBF of the pairs the station grid drops (the 65 km tail), added onto the
     # XFFT image: one tensor-core GEMM against the layout's geometry phases
-    xl = hai.hai_xbf_layout_create(ctx, centres, H.station.lam_m, H.cell_m, n, dirs, hai.HAI_XBF_OFFGRID_PAIRS, C)
+    xl = hai.hai_xbf_layout_create(ctx, centres, H.station.lam_m, H.cell_m, n, dirs, hai.HAI_XBF_OFFGRID_PAIRS, C,
+                                   hai.HAI_PREC_FP16)
     xpairs, xbytes = hai.hai_xbf_layout_info(xl)
     xms = time_call(lambda st: hai.hai_xbf_station_image(ctx, xl, vis, C, img, 1, st), 5, 2, flush)
     rows = K * C * 4
@@ -558,6 +559,14 @@ def hierarchy_component(hai, ctx, flush, peaks):
                             "unit": "TFLOP/s", "frac": xflop / (xms * 1e-3) / 1e12 / pk,
                             "flop": xflop}}
     hai.hai_xbf_layout_destroy(xl)
+    # the same with hi/lo split operands (FP32-level accuracy, three times the work)
+    xs = hai.hai_xbf_layout_create(ctx, centres, H.station.lam_m, H.cell_m, n, dirs, hai.HAI_XBF_OFFGRID_PAIRS, C,
+                                   hai.HAI_PREC_FP16_SPLIT)
+    xsms = time_call(lambda st: hai.hai_xbf_station_image(ctx, xs, vis, C, img, 1, st), 5, 2, flush)
+    hai.hai_xbf_layout_destroy(xs)
+    out_xbf["split"] = {"ms": xsms, "roofline": {"bound": "tensor", "achieved": 3 * xflop / (xsms * 1e-3) / 1e12,
+                                                 "peak": pk, "unit": "TFLOP/s",
+                                                 "frac": 3 * xflop / (xsms * 1e-3) / 1e12 / pk}}
     emma = plan_mma_flops(ne_grid) * K * C * T
     out["station_xbf_offgrid"] = out_xbf
     out["station_epic"] = {
@@ -626,7 +635,8 @@ def run_case(name):
         g = torch.Generator(device="cuda").manual_seed(3)
         vis = torch.randint(-2**20, 2**20, (K * C, S * (S + 1) // 2, 2, 2, 2), dtype=torch.int32, device="cuda",
                             generator=g)
-        xl = hai.hai_xbf_layout_create(ctx, centres, H.station.lam_m, H.cell_m, n, dirs, hai.HAI_XBF_OFFGRID_PAIRS, C)
+        xl = hai.hai_xbf_layout_create(ctx, centres, H.station.lam_m, H.cell_m, n, dirs, hai.HAI_XBF_OFFGRID_PAIRS, C,
+                                   hai.HAI_PREC_FP16)
         img = torch.empty((K * C, 4, n, n), device="cuda")
         for _ in range(2):
             hai.hai_xbf_station_image(ctx, xl, vis, C, img, 0)

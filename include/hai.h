@@ -138,9 +138,10 @@ hai_status hai_layout_box(const hai_layout *layout, int *box);
  *   img   device float [C][Q][N][N], Q = 1 (P = 1) or 4 (P = 2); overwritten
  *         (accumulate = 0) or added to (accumulate = 1)
  *   prec  HAI_PREC_FP32 (CUDA-core FFT; N = 16 .. 512), HAI_PREC_FP16
- *         (tensor cores; N = 32, 64 or 128, P = 2 and a kernel box of at most
- *         N/2 x N/2 cells, else HAI_ERR_UNSUPPORTED) or HAI_PREC_FP16_SPLIT
- *         (tensor cores, hi/lo split; N = 32 or 64)
+ *         (tensor cores; N = 32, 64, 128, 256 or 512, P = 2 and a kernel box of
+ *         at most N/2 x N/2 cells, for N >= 256 at most 128 cells high, else
+ *         HAI_ERR_UNSUPPORTED) or HAI_PREC_FP16_SPLIT (tensor cores, hi/lo
+ *         split; N = 32 or 64)
  * C >= 0, T >= 0 (C = 0 or T = 0: nothing to image; with accumulate = 0 the
  * image is zeroed). */
 hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *layout, const int8_t *volt,
@@ -358,11 +359,13 @@ hai_status hai_station_epic_layout_create(hai_ctx *ctx, const hai_vis_layout_des
  * buffer for up to n_dir * max_channels images; hai_xbf_layout_info reports
  * the pair count and these bytes.  HAI_ERR_NO_MEMORY if they do not fit.
  * desc as for hai_vis_layout_create (n_pol 2; grid_n a power of two in
- * 16..512). */
+ * 16..512).  prec: HAI_PREC_FP16 (fp16 operands) or HAI_PREC_FP16_SPLIT (every
+ * operand as fp16 hi + lo parts, products hi*hi + hi*lo + lo*hi: FP32-level
+ * accuracy, three times the work and phase memory). */
 enum { HAI_XBF_ALL_PAIRS = 0, HAI_XBF_OFFGRID_PAIRS = 1 };
 typedef struct hai_xbf_layout hai_xbf_layout;
 hai_status hai_xbf_layout_create(hai_ctx *ctx, const hai_vis_layout_desc *desc, int pair_set, int max_channels,
-                                 hai_xbf_layout **out);
+                                 hai_precision prec, hai_xbf_layout **out);
 void hai_xbf_layout_destroy(hai_xbf_layout *layout);
 hai_status hai_xbf_layout_info(const hai_xbf_layout *layout, long long *n_pairs, long long *device_bytes);
 

@@ -20,6 +20,11 @@
 // rebuilt per call from the int32 visibilities with a power-of-two scale per
 // image that keeps the fp16 values in range (undone in the epilogue).
 //
+// HAI_PREC_FP16_SPLIT: every value is split into an fp16 hi part and the fp16
+// rounding remainder lo, and the K dimension is laid out three times,
+// A' = [A_hi | A_hi | A_lo] against Phi' = [Phi_hi | Phi_lo | Phi_hi], so the
+// same GEMM sums hi*hi + hi*lo + lo*hi (FP32-level accuracy, 3x the work).
+//
 // GEMM: one CTA per 128 x 256 output tile; a 4-stage pipeline of 48 KB bulk
 // copies (A 128 x 64 and Phi 256 x 64, fp16); warp 0 streams, warp 1 issues
 // tcgen05.mma (M = 128, N = 256, K = 16) into a 256-column TMEM accumulator,
@@ -48,7 +53,8 @@ constexpr size_t kSmem = (size_t)kStages * (kABytes + kBBytes);
 __host__ __device__ __forceinline__ uint32_t tile_off(int row, int k) { return tc::off_kmajor(row, k, kLBO, kSBO); }
 
 // Phi[pixel][(b, re/im)], 16 bytes (4 pairs) per thread
-__global__ void xbf_phi_kernel(const double2 *__restrict__ duv, int B, int N, int log2n, int n_kblk,
+// split: K segments [Phi_hi | Phi_lo | Phi_hi] against [A_hi | A_hi | A_lo]
+__global__ void xbf_phi_kernel(const double2 *__restrict__ duv, int B, int N, int log2n, int n_kblk, int split,
                                uint8_t *__restrict__ phi) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int groups = n_kblk * (kTK / 8);
@@ -56,7 +62,7 @@ __global__ void xbf_phi_kernel(const double2 *__restrict__ duv, int B, int N, in
     const int g = (int)(i % groups);
     const int p = (int)(i / groups);
     const double ox = (double)((p & (N - 1)) - N / 2), oy = (double)((p >> log2n) - N / 2);
-    uint32_t h[4];
+    uint32_t h[4], l[4];
 #pragma unroll
     for (int j = 0; j < 4; j++) {
         const int b = 4 * g + j;
@@ -68,10 +74,17 @@ __global__ void xbf_phi_kernel(const double2 *__restrict__ duv, int B, int N, in
             sincospif(2.0f * f, &s, &c);
         }
         h[j] = tc::pack_half2(c, s);
+        const float2 back = __half22float2(*reinterpret_cast<const __half2 *>(&h[j]));
+        l[j] = tc::pack_half2(c - back.x, s - back.y);
     }
     const int nb = p / kTN, r = p % kTN, kb = g / (kTK / 8), kk = (g % (kTK / 8)) * 8;
-    *reinterpret_cast<uint4 *>(phi + ((size_t)nb * n_kblk + kb) * kBBytes + tile_off(r, kk)) =
-        make_uint4(h[0], h[1], h[2], h[3]);
+    const int ktot = split ? 3 * n_kblk : n_kblk;
+    uint8_t *base = phi + (size_t)nb * ktot * kBBytes + tile_off(r, kk);
+    *reinterpret_cast<uint4 *>(base + (size_t)kb * kBBytes) = make_uint4(h[0], h[1], h[2], h[3]);
+    if (split) {
+        *reinterpret_cast<uint4 *>(base + (size_t)(n_kblk + kb) * kBBytes) = make_uint4(l[0], l[1], l[2], l[3]);
+        *reinterpret_cast<uint4 *>(base + (size_t)(2 * n_kblk + kb) * kBBytes) = make_uint4(h[0], h[1], h[2], h[3]);
+    }
 }
 
 // steering phasor e = exp(+2 pi i s_k . dr / lambda) per (beam, pair), FP64 phase
@@ -128,7 +141,8 @@ __device__ __forceinline__ void pair_coefs(const int2 *__restrict__ v, int2 mn, 
 __global__ void __launch_bounds__(256) xbf_coef_kernel(const int32_t *__restrict__ vis, long long nbl,
                                                        const int2 *__restrict__ pairs,
                                                        const float2 *__restrict__ steer, int B, int C, int n_kblk,
-                                                       uint8_t *__restrict__ A, float *__restrict__ scale) {
+                                                       int split, uint8_t *__restrict__ A,
+                                                       float *__restrict__ scale) {
     __shared__ float red[8];
     const int img = blockIdx.x, k = img / C;
     const int2 *v = reinterpret_cast<const int2 *>(vis) + (size_t)img * nbl * 4;
@@ -156,11 +170,20 @@ __global__ void __launch_bounds__(256) xbf_coef_kernel(const int32_t *__restrict
         float o[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (b < B) pair_coefs(v, pairs[b], steer[(size_t)k * B + b], o);
         const int kb = b / (kTK / 2), kk = 2 * (b % (kTK / 2));
+        const int ktot = split ? 3 * n_kblk : n_kblk;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             const int r = row0 + j;
-            uint8_t *dst = A + ((size_t)(r / kTM) * n_kblk + kb) * kABytes + tile_off(r % kTM, kk);
-            *reinterpret_cast<uint32_t *>(dst) = tc::pack_half2(o[2 * j] * sc, o[2 * j + 1] * sc);
+            uint8_t *dst = A + ((size_t)(r / kTM) * ktot + kb) * kABytes + tile_off(r % kTM, kk);
+            const float x0 = o[2 * j] * sc, x1 = o[2 * j + 1] * sc;
+            const uint32_t hi = tc::pack_half2(x0, x1);
+            *reinterpret_cast<uint32_t *>(dst) = hi;
+            if (split) {                        // segments [A_hi | A_hi | A_lo]
+                const float2 back = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
+                *reinterpret_cast<uint32_t *>(dst + (size_t)n_kblk * kABytes) = hi;
+                *reinterpret_cast<uint32_t *>(dst + (size_t)2 * n_kblk * kABytes) =
+                    tc::pack_half2(x0 - back.x, x1 - back.y);
+            }
         }
     }
 }
@@ -259,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1) xbf_gemm_kernel(const GemmParams 
 
 struct hai_xbf_layout {
     hai_ctx *ctx = nullptr;
-    int S = 0, N = 0, K = 0, pair_set = 0, max_images = 0, n_kblk = 0, n_mblk = 0;
+    int S = 0, N = 0, K = 0, pair_set = 0, max_images = 0, n_kblk = 0, n_mblk = 0, split = 0;
     long long B = 0, nbl = 0;
     int2 *d_pairs = nullptr;
     float2 *d_steer = nullptr;
@@ -281,7 +304,7 @@ static void xbf_free(hai_xbf_layout *L) {
 }
 
 extern "C" hai_status hai_xbf_layout_create(hai_ctx *ctx, const hai_vis_layout_desc *d, int pair_set,
-                                            int max_channels, hai_xbf_layout **out) {
+                                            int max_channels, hai_precision prec, hai_xbf_layout **out) {
     if (!ctx || !d || !out) return hai_fail(HAI_ERR_INVALID_ARG, "hai_xbf_layout_create: NULL argument");
     *out = nullptr;
     const int S = d->n_station, N = d->grid_n, K = d->n_dir;
@@ -291,6 +314,8 @@ extern "C" hai_status hai_xbf_layout_create(hai_ctx *ctx, const hai_vis_layout_d
                         "hai_xbf_layout_create: bad descriptor (grid_n a power of two in 16..512), pair set or "
                         "channel count");
     if (d->n_pol != 2) return hai_fail(HAI_ERR_UNSUPPORTED, "hai_xbf_layout_create: station images need 2 pols");
+    if (prec != HAI_PREC_FP16 && prec != HAI_PREC_FP16_SPLIT)
+        return hai_fail(HAI_ERR_UNSUPPORTED, "hai_xbf_layout_create: precision must be FP16 or FP16_SPLIT");
     if ((long long)K * max_channels * 4 > (1ll << 30))
         return hai_fail(HAI_ERR_UNSUPPORTED, "hai_xbf_layout_create: too many images");
     if (hai_fault_injected("alloc")) return hai_fail(HAI_ERR_NO_MEMORY, "hai_xbf_layout_create: injected allocation failure");
@@ -316,9 +341,11 @@ extern "C" hai_status hai_xbf_layout_create(hai_ctx *ctx, const hai_vis_layout_d
     L->B = (long long)pairs.size();
     L->n_kblk = (int)((2 * L->B + kTK - 1) / kTK);
     L->n_mblk = (L->max_images * 4 + kTM - 1) / kTM;
+    L->split = prec == HAI_PREC_FP16_SPLIT ? 1 : 0;
+    const int nseg = L->split ? 3 : 1;
     const size_t npix = (size_t)N * N;
-    L->phi_bytes = (size_t)L->n_kblk * kBBytes * (npix / kTN);
-    L->coef_bytes = (size_t)L->n_kblk * kABytes * L->n_mblk;
+    L->phi_bytes = (size_t)nseg * L->n_kblk * kBBytes * (npix / kTN);
+    L->coef_bytes = (size_t)nseg * L->n_kblk * kABytes * L->n_mblk;
     cudaError_t e = cudaSetDevice(ctx->device);
     double2 *d_duv = nullptr, *d_dr = nullptr;
     double *d_dir = nullptr;
@@ -349,7 +376,8 @@ extern "C" hai_status hai_xbf_layout_create(hai_ctx *ctx, const hai_vis_layout_d
         int log2n = 0;
         while ((1 << log2n) < N) log2n++;
         const long long nthr = (long long)npix * L->n_kblk * (kTK / 8);
-        xbf_phi_kernel<<<(unsigned)((nthr + 255) / 256), 256>>>(d_duv, (int)L->B, N, log2n, L->n_kblk, L->d_phi);
+        xbf_phi_kernel<<<(unsigned)((nthr + 255) / 256), 256>>>(d_duv, (int)L->B, N, log2n, L->n_kblk, L->split,
+                                                              L->d_phi);
         const long long ns = (long long)K * L->B;
         xbf_steer_kernel<<<(unsigned)((ns + 255) / 256), 256>>>(d_dr, d_dir, K, (int)L->B, 1.0 / d->lambda_m,
                                                               L->d_steer);
@@ -393,14 +421,14 @@ extern "C" hai_status hai_xbf_station_image(hai_ctx *ctx, const hai_xbf_layout *
         return HAI_OK;
     }
     HAI_CUDA_TRY(cudaFuncSetAttribute(xbf_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
-    xbf_coef_kernel<<<n_img, 256, 0, st>>>(vis, L->nbl, L->d_pairs, L->d_steer, (int)L->B, C, L->n_kblk, L->d_coef,
-                                           L->d_scale);
+    xbf_coef_kernel<<<n_img, 256, 0, st>>>(vis, L->nbl, L->d_pairs, L->d_steer, (int)L->B, C, L->n_kblk, L->split,
+                                           L->d_coef, L->d_scale);
     GemmParams gp;
     gp.A = L->d_coef;
     gp.phi = L->d_phi;
     gp.scale = L->d_scale;
     gp.img = img;
-    gp.n_kblk = L->n_kblk;
+    gp.n_kblk = (L->split ? 3 : 1) * L->n_kblk;
     gp.M = M;
     gp.npix = (int)npix;
     gp.accumulate = accumulate;

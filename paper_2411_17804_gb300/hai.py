@@ -82,7 +82,7 @@ def _declare(L):
     L.hai_vis_layout_offgrid.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
     L.hai_station_epic_layout_create.argtypes = [_vp, ctypes.POINTER(_VisLayoutDesc), _int, ctypes.POINTER(_vp),
                                                  ctypes.POINTER(ctypes.c_longlong)]
-    L.hai_xbf_layout_create.argtypes = [_vp, ctypes.POINTER(_VisLayoutDesc), _int, _int, ctypes.POINTER(_vp)]
+    L.hai_xbf_layout_create.argtypes = [_vp, ctypes.POINTER(_VisLayoutDesc), _int, _int, _int, ctypes.POINTER(_vp)]
     L.hai_xbf_layout_destroy.argtypes = [_vp]
     L.hai_xbf_layout_destroy.restype = None
     L.hai_xbf_layout_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
@@ -394,7 +394,8 @@ class XbfLayout:
 
 
 def hai_xbf_layout_create(ctx, pos_m, lambda_m: float, cell_m: float, grid_n: int, dirs=None,
-                          pair_set: int = HAI_XBF_ALL_PAIRS, max_channels: int = 1) -> XbfLayout:
+                          pair_set: int = HAI_XBF_ALL_PAIRS, max_channels: int = 1,
+                          prec: int = HAI_PREC_FP16) -> XbfLayout:
     pos = np.ascontiguousarray(pos_m, np.float64)
     S = pos.shape[0]
     if pos.shape != (S, 2):
@@ -403,7 +404,7 @@ def hai_xbf_layout_create(ctx, pos_m, lambda_m: float, cell_m: float, grid_n: in
     K = 1 if d is None else d.shape[0]
     desc = _VisLayoutDesc(S, pos.ctypes.data, lambda_m, cell_m, grid_n, 2, K, None if d is None else d.ctypes.data)
     h = _vp()
-    _check(load().hai_xbf_layout_create(ctx, ctypes.byref(desc), pair_set, max_channels, ctypes.byref(h)),
+    _check(load().hai_xbf_layout_create(ctx, ctypes.byref(desc), pair_set, max_channels, prec, ctypes.byref(h)),
            "hai_xbf_layout_create")
     return XbfLayout(h, S, grid_n, K, max_channels)
 

@@ -52,7 +52,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.hai_sync(None, None) == 1
     assert lib.hai_fft_correlate(None, None, 1, 64, 2, None, None) == 1
     assert lib.hai_station_epic_layout_create(None, None, 0, None, None) == 1
-    assert lib.hai_xbf_layout_create(None, None, 0, 1, None) == 1
+    assert lib.hai_xbf_layout_create(None, None, 0, 1, 1, None) == 1
     assert lib.hai_xbf_station_image(None, None, None, 1, None, 0, None) == 1
 
 

@@ -39,9 +39,10 @@ def hermitian_vis(rng, K, C, S, lo=-2**20, hi=2**20):
     return vis
 
 
-def run_xbf(hai, ctx, pos, lam, cell, n, dirs, vis, pair_set, img=None, accumulate=0):
+def run_xbf(hai, ctx, pos, lam, cell, n, dirs, vis, pair_set, img=None, accumulate=0, prec=None):
     K, C = vis.shape[:2]
-    lay = hai.hai_xbf_layout_create(ctx, pos, lam, cell, n, dirs, pair_set, C)
+    prec = hai.HAI_PREC_FP16 if prec is None else prec
+    lay = hai.hai_xbf_layout_create(ctx, pos, lam, cell, n, dirs, pair_set, C, prec)
     if img is None:
         img = torch.full((K * C, 4, n, n), float("nan"), device="cuda")
     hai.hai_xbf_station_image(ctx, lay, torch.from_numpy(vis).cuda(), C, img, accumulate)
@@ -103,6 +104,27 @@ def test_hierarchical_array_full_grid(hai, ctx):
     assert rel_err_planes(got, planes(want)).max() < REDUCED_TOL
 
 
+@pytest.mark.parametrize("S,K,C,n,offgrid", [(12, 2, 2, 32, False), (40, 1, 2, 64, False), (24, 2, 1, 32, True)])
+def test_split_products_reach_fp32_accuracy(hai, ctx, S, K, C, n, offgrid):
+    """HAI_PREC_FP16_SPLIT (hi*hi + hi*lo + lo*hi through the same GEMM):
+    FP32-level image error, far below the plain fp16 one."""
+    rng = np.random.default_rng(S + n)
+    cell, lam = 19.0, 3.0
+    pos = rng.uniform(-n * cell / 3, n * cell / 3, (S, 2))
+    if offgrid:
+        pos[-4:] = rng.uniform(2 * n * cell, 6 * n * cell, (4, 2))
+    dirs = rng.uniform(-0.1, 0.1, (K, 2))
+    vis = hermitian_vis(rng, K, C, S)
+    ps = hai.HAI_XBF_OFFGRID_PAIRS if offgrid else hai.HAI_XBF_ALL_PAIRS
+    want = planes(O.station_xbf(n, pos, lam, cell, dirs, vis.astype(np.int64), offgrid_only=offgrid))
+    split, (_, nbytes) = run_xbf(hai, ctx, pos, lam, cell, n, dirs, vis, ps, prec=hai.HAI_PREC_FP16_SPLIT)
+    plain, (_, nbytes1) = run_xbf(hai, ctx, pos, lam, cell, n, dirs, vis, ps)
+    e_split, e_plain = rel_err_planes(split, want).max(), rel_err_planes(plain, want).max()
+    assert e_split < FP32_TOL, e_split
+    assert e_split < e_plain / 20, (e_split, e_plain)
+    assert nbytes > 2.5 * nbytes1
+
+
 def test_no_pairs_and_bad_arguments(hai, ctx):
     pos = np.array([[0.0, 0.0], [10.0, 5.0], [-7.0, 3.0]])
     vis = hermitian_vis(np.random.default_rng(1), 1, 1, 3)
@@ -112,6 +134,9 @@ def test_no_pairs_and_bad_arguments(hai, ctx):
     with pytest.raises(hai.HaiError) as e:
         hai.hai_xbf_layout_create(ctx, pos, 3.0, 19.0, 48, None, 0, 1)
     assert e.value.status == 1
+    with pytest.raises(hai.HaiError) as e:
+        hai.hai_xbf_layout_create(ctx, pos, 3.0, 19.0, 32, None, 0, 1, hai.HAI_PREC_FP32)
+    assert e.value.status == 4
     lay = hai.hai_xbf_layout_create(ctx, pos, 3.0, 19.0, 32, None, 0, 1)
     img = torch.zeros((2, 4, 32, 32), device="cuda")
     with pytest.raises(hai.HaiError) as e:       # more channels than the layout holds
