@@ -8,19 +8,29 @@
 //   Re V = sum_k X_a[k] X_b[k],   Im V = sum_k X_a[k] X'_b[k],
 // where X'_b = (-Im, Re) per sample, so one MMA with B = [X_b ; X'_b]
 // (N = 128) yields both parts.  int8 values are exact in FP16, products are
-// below 2^14, and the FP32 accumulator holds every partial sum exactly while
-// it stays below 2^24, i.e. for up to 512 samples; every 512 samples the
-// epilogue moves the accumulator into int32 registers (exact) and the MMA
-// restarts.  |V| <= 2^15 T, so int32 holds any T <= 65535.
+// at most 2^14 in magnitude, and an FP32 sum of 1024 of them (512 samples)
+// stays an exact integer (|sum| <= 2^24): the tensor cores accumulate one
+// 512-sample block in TMEM, the epilogue rounds it to int32 (exact) and adds
+// it to integer sums kept in a third TMEM region, and after the last block
+// writes (or adds) the tile's visibilities once.  |V| <= 2^15 T, so int32 holds any
+// T <= 65535.
 //
-// CTA = 16 warps, persistent over (channel, row block I, column block J)
-// tiles that touch the lower triangle a >= b:
-//   warps 0-6  producers: 16-byte int8 loads (prefetched one stage ahead),
-//              int8 -> fp16 by a bit trick, MN-major operand stages in smem;
-//   warp 7     one thread issues the MMAs (4 per 32-sample stage);
-//   warps 8-15 epilogue: TMEM -> int32 accumulators, then the lower-triangle
-//              visibilities are written.
-// Tile: rows M = 128 = P x (128/P) elements, columns 2 x P x (64/P) elements.
+// Two kernels per batch of channels and samples (sized to the context's
+// workspace):
+//   pack:  int8 -> fp16 operand images, K-major in the tensor cores' tile
+//          order: one 16 KB image (128 rows x 64 K = 32 samples) per
+//          (channel, k block, column block J) holding [X ; X'] of the 64 / P
+//          elements of column block J, both pols, rows (x', pol, element),
+//          transposed through shared memory;
+//   gemm:  persistent, one work item per (lower-triangle tile, channel).
+//          The A operand of row block I (128 / P elements, rows (half, pol,
+//          element)) is the X halves of images 2I and 2I+1, so it needs no
+//          images of its own: per k block three bulk copies (8 + 8 + 16 KB)
+//          fill one stage of a 6-stage ring, one thread issues the MMAs
+//          (M = 128, N = 128, K = 16, four per k block) into one of two TMEM
+//          accumulators (one per 512-sample block, alternating, so the
+//          epilogue of a block overlaps the MMAs of the next), and four
+//          epilogue warps drain them.
 #include <string.h>
 
 #include <algorithm>
@@ -30,36 +40,32 @@
 
 namespace {
 
-constexpr int kThreads = 512;
-constexpr int kProd = 224;              // warps 0-6
-constexpr int kMmaWarp = 7;
-constexpr int kEpi = 256;               // warps 8-15
-constexpr int kStageT = 32;             // samples per stage (K = 64)
 constexpr int kChunkT = 512;            // samples per exact FP32 block
-constexpr int kStages = 4;
-constexpr uint32_t kKs = 2064;          // MN-major: K-group stride (16 MN groups + 16 B)
-constexpr uint32_t kMNs = 128;          // MN-major: MN-group stride
-constexpr uint32_t kOpBytes = 8 * kKs;  // one operand stage (128 rows x 64 K)
-constexpr uint32_t kIdesc = tc::idesc_f16(128, 128, 1, 1);
+constexpr int kKbT = 32;                // samples per k block (K = 64)
+constexpr int kKbPerChunk = kChunkT / kKbT;
+constexpr int kStages = 6;
+constexpr uint32_t kLBO = 128;          // K-major: K-group stride
+constexpr uint32_t kSBO = 1024;         // K-major: MN-group stride
+constexpr uint32_t kImg = 16384;        // 128 rows x 64 K fp16
+constexpr uint32_t kHalf = kImg / 2;    // rows 0..63 of an image
+constexpr uint32_t kStage = 2 * kImg;   // A + B
+constexpr uint32_t kIdesc = tc::idesc_f16(128, 128, 0, 0);
+constexpr int kThreads = 256;           // warp 0 loads, warp 1 MMA, warps 4-7 epilogue
+constexpr uint32_t kTmemCols = 512;     // two 128-column FP32 accumulators + int32 sums
 
-struct CorrParams {
-    const int8_t *volt;
-    int C, T, ne, P;
-    int em, en;                  // elements per row block / column block
+struct CorrGeo {
+    int T, ne, P;
+    int em, E;                   // elements per row block; per column block (= per 64-row half)
     int nbi, nbj;                // row / column blocks per channel
+    int nimg;                    // images per (channel, k block): max(nbj, 2 nbi)
     int tiles_per_chan;
-    long long ntiles;
-    int32_t *vis;
-    int accumulate;
-    int vec;                     // 16-byte loads are aligned
-    unsigned *status;
 };
 
 // (I, J) of the k-th lower-triangle tile of a channel, row-block major.
-__device__ __forceinline__ void decode_tile(const CorrParams &p, int k, int &I, int &J) {
-    for (I = 0; I < p.nbi; I++) {
-        const int amax = min(p.ne - 1, (I + 1) * p.em - 1);
-        const int nj = min(p.nbj, amax / p.en + 1);
+__device__ __forceinline__ void decode_tile(const CorrGeo &g, int k, int &I, int &J) {
+    for (I = 0; I < g.nbi; I++) {
+        const int amax = min(g.ne - 1, (I + 1) * g.em - 1);
+        const int nj = min(g.nbj, amax / g.E + 1);
         if (k < nj) {
             J = k;
             return;
@@ -69,238 +75,210 @@ __device__ __forceinline__ void decode_tile(const CorrParams &p, int k, int &I, 
     I = J = 0;
 }
 
-// int8 (re, im) x 8 in 16 bytes -> fp16 re[8] and im[8] packed in uint4s.
-// half(1024 + u) has bits 0x6400 + u for 0 <= u < 1024, and u = x + 128 is
-// the int8 with its sign bit flipped; subtracting 1152 leaves x exactly.
-__device__ __forceinline__ void int8x16_to_half(const int4 raw, uint4 &re, uint4 &im) {
-    const uint32_t w[4] = {(uint32_t)raw.x ^ 0x80808080u, (uint32_t)raw.y ^ 0x80808080u,
-                           (uint32_t)raw.z ^ 0x80808080u, (uint32_t)raw.w ^ 0x80808080u};
-    const __half2 bias = __floats2half2_rn(1152.f, 1152.f);
-    uint32_t r[4], m[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        // word k holds (re, im) of elements 2k and 2k+1: bytes re0 im0 re1 im1
-        const uint32_t pr = __byte_perm(w[k], 0x64646464u, 0x4240);   // re0, 0x64, re1, 0x64
-        const uint32_t pi = __byte_perm(w[k], 0x64646464u, 0x4341);   // im0, 0x64, im1, 0x64
-        __half2 hr = __hsub2(*reinterpret_cast<const __half2 *>(&pr), bias);
-        __half2 hi = __hsub2(*reinterpret_cast<const __half2 *>(&pi), bias);
-        r[k] = *reinterpret_cast<uint32_t *>(&hr);
-        m[k] = *reinterpret_cast<uint32_t *>(&hi);
-    }
-    re = make_uint4(r[0], r[1], r[2], r[3]);
-    im = make_uint4(m[0], m[1], m[2], m[3]);
+// image J of (channel cb, k block kb) of a batch holding nkb k blocks per channel
+__host__ __device__ __forceinline__ size_t img_index(const CorrGeo &g, int nkb, int cb, int kb, int J) {
+    return ((size_t)cb * nkb + kb) * g.nimg + J;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) corr_kernel(const CorrParams p) {
-    extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t mb_full[kStages], mb_empty[kStages];
-    __shared__ __align__(8) uint64_t mb_dfull[2], mb_dempty[2];
-    __shared__ uint32_t tmem_slot;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    uint8_t *sA = smem;                               // [kStages][kOpBytes]
-    uint8_t *sB = smem + kStages * kOpBytes;
+// One CTA per (channel, k block, group of kPackJ column blocks): the 32
+// samples x P pols x kPackJ * 64 / P elements of the group are read once,
+// coalesced, into shared memory ([sample][pol][element], 32 KB), and written
+// out as kPackJ images, one thread per 16-byte K group (4 samples) of one
+// image row, lanes over rows so that stores fill whole 128-byte row groups.
+constexpr int kPackJ = 8;
+constexpr int kPackCols = kPackJ * 64;       // P x elements of a group
 
+__global__ void __launch_bounds__(256) corr_pack_kernel(const int8_t *__restrict__ volt, CorrGeo g, int c0, int kb0,
+                                                        int nkb, int vec16, uint8_t *__restrict__ ws) {
+    __shared__ __align__(16) char2 tile[kKbT][kPackCols];
+    const int njg = (g.nimg + kPackJ - 1) / kPackJ;
+    const int kb = blockIdx.x / njg, jg = blockIdx.x % njg, cb = blockIdx.y;
+    const int ge = kPackJ * g.E;                 // elements of the group
+    const int a0 = jg * ge;
+    const int8_t *vc = volt + (size_t)(c0 + cb) * g.T * g.P * g.ne * 2;
+    const int tb = (kb0 + kb) * kKbT;
+    // load: rows (t, pol) of ge elements; 16-byte vectors where the rows allow
+    if (vec16 && a0 + ge <= g.ne) {
+        const int nv = ge / 8;                   // 8 elements per 16 bytes
+        for (int i = threadIdx.x; i < kKbT * g.P * nv; i += blockDim.x) {
+            const int v = i % nv, tp = i / nv, t = tp / g.P, pol = tp % g.P;
+            uint4 x = make_uint4(0, 0, 0, 0);
+            if (tb + t < g.T)
+                x = *reinterpret_cast<const uint4 *>(vc + (((size_t)(tb + t) * g.P + pol) * g.ne + a0 + 8 * v) * 2);
+            *reinterpret_cast<uint4 *>(&tile[t][pol * ge + 8 * v]) = x;
+        }
+    } else {
+        for (int i = threadIdx.x; i < kKbT * g.P * ge; i += blockDim.x) {
+            const int e = i % ge, tp = i / ge, t = tp / g.P, pol = tp % g.P;
+            char2 x = make_char2(0, 0);
+            if (tb + t < g.T && a0 + e < g.ne)
+                x = reinterpret_cast<const char2 *>(vc)[((size_t)(tb + t) * g.P + pol) * g.ne + a0 + e];
+            tile[t][pol * ge + e] = x;
+        }
+    }
+    __syncthreads();
+    const int nj = min(kPackJ, g.nimg - jg * kPackJ);
+    for (int i = threadIdx.x; i < nj * 1024; i += blockDim.x) {
+        const int r = i & 127, kg = (i >> 7) & 7, jl = i >> 10;
+        const int rr = r & 63, pol = rr / g.E;
+        const int col = pol * ge + jl * g.E + rr % g.E;
+        uint32_t h2[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const char2 v = tile[4 * kg + j][col];
+            h2[j] = r >= 64 ? tc::pack_half2(-(float)v.y, (float)v.x) : tc::pack_half2((float)v.x, (float)v.y);
+        }
+        uint8_t *dst = ws + img_index(g, nkb, cb, kb, jg * kPackJ + jl) * kImg + tc::off_kmajor(r, 8 * kg, kLBO, kSBO);
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(h2[0], h2[1], h2[2], h2[3]);
+    }
+}
+
+struct GemmParams {
+    const uint8_t *ws;
+    CorrGeo g;
+    int c0, ncb;                 // channels of this batch
+    int nkb;                     // k blocks of this batch (per channel)
+    int add;                     // add to vis (else overwrite)
+    int32_t *vis;
+    unsigned *status;
+};
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, 1) corr_gemm_kernel(const GemmParams p) {
+    constexpr int E = 64 / P;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accf[2], acce[2];
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const CorrGeo g = p.g;
+    const int nitems = g.tiles_per_chan * p.ncb;
+    const int nchunk = (p.nkb + kKbPerChunk - 1) / kKbPerChunk;
     if (tid == 0) {
         for (int s = 0; s < kStages; s++) {
-            tc::mbar_init(&mb_full[s], kProd);
-            tc::mbar_init(&mb_empty[s], 1);
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; b++) {
-            tc::mbar_init(&mb_dfull[b], 1);
-            tc::mbar_init(&mb_dempty[b], kEpi);
+            tc::mbar_init(&accf[b], 1);
+            tc::mbar_init(&acce[b], 128);
         }
         tc::mbar_fence_init();
     }
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, 256);
+    if (warp == 0) tc::tmem_alloc(&tslot, kTmemCols);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    const uint32_t tmem = tmem_slot;
-
-    const int nstage = (p.T + kStageT - 1) / kStageT;          // stages per tile
-    const int per_chunk = kChunkT / kStageT;                   // stages per exact block
-    const int nchunk = (nstage + per_chunk - 1) / per_chunk;   // blocks per tile
-    const int sample_bytes = p.P * p.ne * 2;
-
-    if (warp < kMmaWarp) {
-        // ============================================================ producers
-        // work items of a stage: A (rows): P x 32 samples x em/8 groups,
-        // B (columns): P x 32 samples x en/8 groups
-        const int ga = p.em / 8, gb = p.en / 8;
-        const int na = p.P * kStageT * ga, nb = p.P * kStageT * gb;
-        const int nitem = na + nb;
-        constexpr int kMaxItems = 4;                           // per thread per stage
-        long long gs = 0;                                      // global stage counter
-        for (long long tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
-            const int c = (int)(tile / p.tiles_per_chan);
-            int I, J;
-            decode_tile(p, (int)(tile % p.tiles_per_chan), I, J);
-            const int8_t *vc = p.volt + (size_t)c * p.T * sample_bytes;
-            // item -> (pol, sample, 8-element group); each warp's 32 items are
-            // 8 consecutive samples x 4 consecutive groups, so global loads
-            // fill 32-byte sectors and the 16-byte smem stores of a phase land
-            // in distinct bank groups
-            auto item_src = [&](int it, int st, int &pol, int &t, int &a0, bool &is_b) {
-                is_b = it >= na;
-                const int r = is_b ? it - na : it;
-                const int gq = (is_b ? gb : ga) / 4;
-                const int li = r & 31, blk = r >> 5;
-                const int gqi = blk % gq, tb = (blk / gq) % (kStageT / 8);
-                pol = blk / (gq * (kStageT / 8));
-                t = st * kStageT + tb * 8 + (li & 7);
-                a0 = (is_b ? J * p.en : I * p.em) + (gqi * 4 + (li >> 3)) * 8;
-            };
-            auto load = [&](int it, int st) -> int4 {
-                int pol, t, a0;
-                bool is_b;
-                item_src(it, st, pol, t, a0, is_b);
-                if (t >= p.T) return make_int4(0, 0, 0, 0);
-                const int8_t *src = vc + (size_t)t * sample_bytes + (size_t)pol * p.ne * 2 + (size_t)a0 * 2;
-                if (p.vec && a0 + 8 <= p.ne) return __ldg(reinterpret_cast<const int4 *>(src));
-                uint32_t wv[4];                               // ragged edge: byte loads
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    wv[k] = 0;
-#pragma unroll
-                    for (int j = 0; j < 4; j++)
-                        if (a0 + (4 * k + j) / 2 < p.ne) wv[k] |= (uint32_t)(uint8_t)src[4 * k + j] << (8 * j);
-                }
-                return make_int4((int)wv[0], (int)wv[1], (int)wv[2], (int)wv[3]);
-            };
-            int4 cur[kMaxItems], nxt[kMaxItems];
-#pragma unroll
-            for (int k = 0; k < kMaxItems; k++) {
-                const int it = tid + k * kProd;
-                cur[k] = it < nitem ? load(it, 0) : make_int4(0, 0, 0, 0);
-            }
-            for (int st = 0; st < nstage; st++, gs++) {
-#pragma unroll
-                for (int k = 0; k < kMaxItems; k++) {          // prefetch the next stage
-                    const int it = tid + k * kProd;
-                    nxt[k] = (it < nitem && st + 1 < nstage) ? load(it, st + 1) : make_int4(0, 0, 0, 0);
-                }
-                const int slot = (int)(gs % kStages);
-                if (gs >= kStages) tc::mbar_wait(&mb_empty[slot], (uint32_t)(((gs / kStages) - 1) & 1), p.status);
-                uint8_t *A = sA + slot * kOpBytes, *B = sB + slot * kOpBytes;
-#pragma unroll
-                for (int k = 0; k < kMaxItems; k++) {
-                    const int it = tid + k * kProd;
-                    if (it >= nitem) continue;
-                    int pol, t, a0;
-                    bool is_b;
-                    item_src(it, st, pol, t, a0, is_b);
-                    uint4 re, im;
-                    int8x16_to_half(cur[k], re, im);
-                    const int tl = t - st * kStageT;
-                    const int kre = 2 * tl, kim = 2 * tl + 1;
-                    if (!is_b) {
-                        const int m = pol * p.em + (a0 - I * p.em);
-                        *reinterpret_cast<uint4 *>(A + tc::off_mnmajor(m, kre, kKs, kMNs)) = re;
-                        *reinterpret_cast<uint4 *>(A + tc::off_mnmajor(m, kim, kKs, kMNs)) = im;
-                    } else {
-                        const int n = pol * p.en + (a0 - J * p.en);
-                        const uint4 nim = make_uint4(im.x ^ 0x80008000u, im.y ^ 0x80008000u,
-                                                     im.z ^ 0x80008000u, im.w ^ 0x80008000u);
-                        *reinterpret_cast<uint4 *>(B + tc::off_mnmajor(n, kre, kKs, kMNs)) = re;
-                        *reinterpret_cast<uint4 *>(B + tc::off_mnmajor(n, kim, kKs, kMNs)) = im;
-                        *reinterpret_cast<uint4 *>(B + tc::off_mnmajor(n + 64, kre, kKs, kMNs)) = nim;
-                        *reinterpret_cast<uint4 *>(B + tc::off_mnmajor(n + 64, kim, kKs, kMNs)) = re;
-                    }
-                }
-                tc::fence_proxy_async();
-                tc::mbar_arrive(&mb_full[slot]);
-#pragma unroll
-                for (int k = 0; k < kMaxItems; k++) cur[k] = nxt[k];
-            }
-        }
-    } else if (warp == kMmaWarp) {
-        // ============================================================ MMA
+    const uint32_t tmem = tslot;
+    if (warp == 0) {
         if (lane == 0) {
-            long long gs = 0, gc = 0;                          // stage and block counters
-            for (long long tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
-                for (int ch = 0; ch < nchunk; ch++, gc++) {
-                    const int b = (int)(gc & 1);
-                    if (gc >= 2) tc::mbar_wait(&mb_dempty[b], (uint32_t)(((gc >> 1) - 1) & 1), p.status);
-                    tc::fence_after();
-                    const uint32_t d = tmem + (uint32_t)b * 128u;
-                    const int s_end = min(nstage, (ch + 1) * per_chunk);
-                    for (int st = ch * per_chunk; st < s_end; st++, gs++) {
-                        const int slot = (int)(gs % kStages);
-                        tc::mbar_wait(&mb_full[slot], (uint32_t)((gs / kStages) & 1), p.status);
-                        tc::fence_after();
-                        const uint32_t a = tc::smem_u32(sA + slot * kOpBytes), bb = tc::smem_u32(sB + slot * kOpBytes);
-#pragma unroll
-                        for (int s = 0; s < 4; s++)
-                            tc::mma_f16(d, tc::desc(a + s * 2 * kKs, kKs, kMNs), tc::desc(bb + s * 2 * kKs, kKs, kMNs),
-                                        kIdesc, (st > ch * per_chunk || s > 0) ? 1u : 0u);
-                        tc::mma_commit(&mb_empty[slot]);
-                    }
-                    tc::mma_commit(&mb_dfull[b]);
+            long long it = 0;                      // k blocks loaded by this CTA
+            for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+                int I, J;
+                decode_tile(g, w % g.tiles_per_chan, I, J);
+                const int cb = w / g.tiles_per_chan;
+                for (int kb = 0; kb < p.nkb; kb++, it++) {
+                    const int s = (int)(it % kStages);
+                    if (it >= kStages) tc::mbar_wait(&empty[s], (uint32_t)(((it / kStages) - 1) & 1), p.status);
+                    uint8_t *st = smem + (size_t)s * kStage;
+                    tc::mbar_arrive_expect_tx(&full[s], kStage);
+                    tc::bulk_g2s(st, p.ws + img_index(g, p.nkb, cb, kb, 2 * I) * kImg, kHalf, &full[s]);
+                    tc::bulk_g2s(st + kHalf, p.ws + img_index(g, p.nkb, cb, kb, 2 * I + 1) * kImg, kHalf, &full[s]);
+                    tc::bulk_g2s(st + kImg, p.ws + img_index(g, p.nkb, cb, kb, J) * kImg, kImg, &full[s]);
                 }
             }
         }
-    } else {
-        // ============================================================ epilogue
-        const int q = warp & 3, h = (warp - 8) >> 2;
-        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        const int m = q * 32 + lane;                           // tile row of this thread
-        const int pol = m / p.em;
-        long long gc = 0;
-        const long long nbl = (long long)p.ne * (p.ne + 1) / 2;
-        for (long long tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
-            const int c = (int)(tile / p.tiles_per_chan);
+    } else if (warp == 1) {
+        if (lane == 0) {
+            long long it = 0, grp = 0;             // k blocks consumed; accumulator groups
+            for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+                for (int ch = 0; ch < nchunk; ch++, grp++) {
+                    const int b = (int)(grp & 1);
+                    if (grp >= 2) tc::mbar_wait(&acce[b], (uint32_t)(((grp >> 1) - 1) & 1), p.status);
+                    tc::fence_after();
+                    const uint32_t d = tmem + (uint32_t)(b * 128);
+                    const int kb1 = min(p.nkb, (ch + 1) * kKbPerChunk);
+                    for (int kb = ch * kKbPerChunk; kb < kb1; kb++, it++) {
+                        const int s = (int)(it % kStages);
+                        tc::mbar_wait(&full[s], (uint32_t)((it / kStages) & 1), p.status);
+                        tc::fence_after();
+                        const uint32_t sa = tc::smem_u32(smem + (size_t)s * kStage), sb = sa + kImg;
+#pragma unroll
+                        for (int j = 0; j < 4; j++)
+                            tc::mma_f16(d, tc::desc(sa + j * 2 * kLBO, kLBO, kSBO),
+                                        tc::desc(sb + j * 2 * kLBO, kLBO, kSBO), kIdesc,
+                                        (kb > ch * kKbPerChunk || j > 0) ? 1u : 0u);
+                        tc::mma_commit(&empty[s]);
+                    }
+                    tc::mma_commit(&accf[b]);
+                }
+            }
+        }
+    } else if (warp >= 4) {
+        const int q = warp & 3, m = q * 32 + lane;
+        const int h = m >> 6, rr = m & 63;
+        const int pol = rr / E;
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+        const uint32_t tsum = lane_base + 256u;   // int32 sums of the work item: re 0..63, im 64..127
+        const long long nbl = (long long)g.ne * (g.ne + 1) / 2;
+        long long grp = 0;
+        for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
             int I, J;
-            decode_tile(p, (int)(tile % p.tiles_per_chan), I, J);
-            int acc_r[32], acc_i[32];
-#pragma unroll
-            for (int k = 0; k < 32; k++) acc_r[k] = acc_i[k] = 0;
-            for (int ch = 0; ch < nchunk; ch++, gc++) {
-                const int b = (int)(gc & 1);
-                tc::mbar_wait(&mb_dfull[b], (uint32_t)((gc >> 1) & 1), p.status);
+            decode_tile(g, w % g.tiles_per_chan, I, J);
+            const int c = p.c0 + w / g.tiles_per_chan;
+            const int a = I * (2 * E) + h * E + rr % E;
+            int2 *row = a < g.ne ? reinterpret_cast<int2 *>(p.vis) +
+                                       (((size_t)c * nbl + (long long)a * (a + 1) / 2) * P + pol) * P
+                                 : nullptr;
+            for (int ch = 0; ch < nchunk; ch++, grp++) {
+                const int b = (int)(grp & 1);
+                const bool first = ch == 0, last = ch == nchunk - 1;
+                tc::mbar_wait(&accf[b], (uint32_t)((grp >> 1) & 1), p.status);
                 tc::fence_after();
-#pragma unroll
-                for (int half = 0; half < 2; half++) {
-                    uint32_t rr[16], ri[16];
-                    const uint32_t col = (uint32_t)b * 128u + (uint32_t)(32 * h + 16 * half);
-                    tc::tmem_ld16(tmem + lane_base + col, rr);
-                    tc::tmem_ld16(tmem + lane_base + col + 64, ri);
+                const uint32_t tacc = lane_base + (uint32_t)(b * 128);
+#pragma unroll 1
+                for (int n0 = 0; n0 < 64; n0 += 16) {
+                    uint32_t vr[16], vi[16], sr[16], si[16];
+                    tc::tmem_ld16(tacc + (uint32_t)n0, vr);
+                    tc::tmem_ld16(tacc + 64u + (uint32_t)n0, vi);
+                    if (!first) {
+                        tc::tmem_ld16(tsum + (uint32_t)n0, sr);
+                        tc::tmem_ld16(tsum + 64u + (uint32_t)n0, si);
+                    }
                     tc::tmem_wait_ld();
 #pragma unroll
                     for (int k = 0; k < 16; k++) {
-                        acc_r[16 * half + k] += __float2int_rn(__uint_as_float(rr[k]));
-                        acc_i[16 * half + k] += __float2int_rn(__uint_as_float(ri[k]));
+                        sr[k] = (first ? 0u : sr[k]) + (uint32_t)__float2int_rn(__uint_as_float(vr[k]));
+                        si[k] = (first ? 0u : si[k]) + (uint32_t)__float2int_rn(__uint_as_float(vi[k]));
                     }
-                }
-                tc::fence_before();
-                tc::mbar_arrive(&mb_dempty[b]);
-            }
-            // lower-triangle outputs of this thread's row (element a, pol)
-            const int a = I * p.em + (m - pol * p.em);
-            if (a < p.ne) {
+                    if (!last) {
+                        tc::tmem_st16(tsum + (uint32_t)n0, sr);
+                        tc::tmem_st16(tsum + 64u + (uint32_t)n0, si);
+                    } else if (row) {
 #pragma unroll
-                for (int k = 0; k < 32; k++) {
-                    const int n = 32 * h + k;                  // column 0..63
-                    const int qq = n / p.en;
-                    const int bidx = J * p.en + (n - qq * p.en);
-                    if (bidx > a || bidx >= p.ne) continue;
-                    const long long bl = (long long)a * (a + 1) / 2 + bidx;
-                    int2 *o = reinterpret_cast<int2 *>(p.vis) + (((size_t)c * nbl + bl) * p.P + pol) * p.P + qq;
-                    int2 v = make_int2(acc_r[k], acc_i[k]);
-                    if (p.accumulate) {
-                        const int2 old = *o;
-                        v.x += old.x;
-                        v.y += old.y;
+                        for (int k = 0; k < 16; k++) {
+                            const int n = n0 + k, qq = n / E, bb = J * E + n % E;
+                            if (bb > a || bb >= g.ne) continue;
+                            int2 *o = row + (size_t)bb * (P * P) + qq;
+                            int2 v = make_int2((int)sr[k], (int)si[k]);
+                            if (p.add) {
+                                const int2 old = *o;
+                                v.x += old.x;
+                                v.y += old.y;
+                            }
+                            *o = v;
+                        }
                     }
-                    *o = v;
                 }
+                if (!last) tc::tmem_wait_st();
+                tc::fence_before();
+                tc::mbar_arrive(&acce[b]);
             }
         }
     }
-
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
 }  // namespace
@@ -311,7 +289,18 @@ extern "C" hai_status hai_correlate(hai_ctx *ctx, const int8_t *volt, int C, int
     if (C < 0 || T < 0 || N <= 0 || (P != 1 && P != 2) || (accumulate != 0 && accumulate != 1))
         return hai_fail(HAI_ERR_INVALID_ARG, "hai_correlate: bad size, polarisation count or flag");
     if (T > 65535) return hai_fail(HAI_ERR_OVERFLOW_RISK, "hai_correlate: T > 65535 may overflow int32");
-    if (N > 65535) return hai_fail(HAI_ERR_UNSUPPORTED, "hai_correlate: N > 65535");
+    CorrGeo g;
+    g.T = T;
+    g.ne = N;
+    g.P = P;
+    g.em = 128 / P;
+    g.E = 64 / P;
+    g.nbi = (N + g.em - 1) / g.em;
+    g.nbj = (N + g.E - 1) / g.E;
+    g.nimg = std::max(g.nbj, 2 * g.nbi);
+    const size_t chunk_bytes = (size_t)kKbPerChunk * g.nimg * kImg;   // one channel, one 512-sample block
+    if (chunk_bytes > ctx->corr_ws_bytes)
+        return hai_fail(HAI_ERR_UNSUPPORTED, "hai_correlate: N too large for the operand workspace");
     if (C == 0) return HAI_OK;
     if (!vis || (T > 0 && !volt)) return hai_fail(HAI_ERR_INVALID_ARG, "hai_correlate: NULL buffer");
     if (hai_fault_injected("launch")) return hai_fail(HAI_ERR_CUDA, "hai_correlate: injected launch failure");
@@ -322,35 +311,48 @@ extern "C" hai_status hai_correlate(hai_ctx *ctx, const int8_t *volt, int C, int
         if (!accumulate) HAI_CUDA_TRY(cudaMemsetAsync(vis, 0, sizeof(int32_t) * 2 * P * P * nbl * C, st));
         return HAI_OK;
     }
-    CorrParams p;
-    p.volt = volt;
-    p.C = C;
-    p.T = T;
-    p.ne = N;
-    p.P = P;
-    p.em = 128 / P;
-    p.en = 64 / P;
-    p.nbi = (N + p.em - 1) / p.em;
-    p.nbj = (N + p.en - 1) / p.en;
+    if (((uintptr_t)vis) & 7) return hai_fail(HAI_ERR_INVALID_ARG, "hai_correlate: vis must be 8-byte aligned");
     int tpc = 0;
-    for (int I = 0; I < p.nbi; I++) {
-        const int amax = std::min(N - 1, (I + 1) * p.em - 1);
-        tpc += std::min(p.nbj, amax / p.en + 1);
+    for (int I = 0; I < g.nbi; I++) {
+        const int amax = std::min(N - 1, (I + 1) * g.em - 1);
+        tpc += std::min(g.nbj, amax / g.E + 1);
     }
-    p.tiles_per_chan = tpc;
-    p.ntiles = (long long)tpc * C;
-    p.vis = vis;
-    p.accumulate = accumulate;
-    p.vec = ((N % 8) == 0) && ((((uintptr_t)volt) & 15) == 0);
-    p.status = ctx->d_status;
-    const size_t smem = 2 * (size_t)kStages * kOpBytes;
-    if (smem > (size_t)ctx->smem_optin) return hai_fail(HAI_ERR_UNSUPPORTED, "hai_correlate: shared memory");
-    HAI_CUDA_TRY(cudaFuncSetAttribute(corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = (int)std::min<long long>(p.ntiles, ctx->num_sms);
+    g.tiles_per_chan = tpc;
+    // batches: as many 512-sample blocks per channel as fit, then as many channels
+    const int nchunk_all = (T + kChunkT - 1) / kChunkT;
+    const int chunks_per_batch = (int)std::min<size_t>(nchunk_all, ctx->corr_ws_bytes / chunk_bytes);
+    const size_t chan_bytes = chunk_bytes * chunks_per_batch;
+    const int chans_per_batch = (int)std::min<size_t>(
+        {(size_t)C, (size_t)65535, ctx->corr_ws_bytes / chan_bytes, (size_t)(INT32_MAX / tpc)});
+    const size_t smem = (size_t)kStages * kStage;
+    auto gemm = P == 2 ? corr_gemm_kernel<2> : corr_gemm_kernel<1>;
+    HAI_CUDA_TRY(cudaFuncSetAttribute(gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    uint8_t *ws = static_cast<uint8_t *>(ctx->d_corr_ws);
+    // rows of the voltage array start on 16-byte boundaries when 2 N is a multiple of 16
+    const int vec16 = (N % 8 == 0 && ((uintptr_t)volt & 15) == 0) ? 1 : 0;
     const int pidx = prof_begin(ctx, st);
-    corr_kernel<<<grid, kThreads, smem, st>>>(p);
+    for (int ch0 = 0; ch0 < nchunk_all; ch0 += chunks_per_batch) {
+        const int kb0 = ch0 * kKbPerChunk;
+        const int t1 = std::min(T, (ch0 + chunks_per_batch) * kChunkT);
+        const int nkb = (t1 - kb0 * kKbT + kKbT - 1) / kKbT;
+        for (int c0 = 0; c0 < C; c0 += chans_per_batch) {
+            const int ncb = std::min(chans_per_batch, C - c0);
+            const int njg = (g.nimg + kPackJ - 1) / kPackJ;
+            corr_pack_kernel<<<dim3(nkb * njg, ncb), 256, 0, st>>>(volt, g, c0, kb0, nkb, vec16, ws);
+            GemmParams gp;
+            gp.ws = ws;
+            gp.g = g;
+            gp.c0 = c0;
+            gp.ncb = ncb;
+            gp.nkb = nkb;
+            gp.add = (ch0 > 0 || accumulate) ? 1 : 0;
+            gp.vis = vis;
+            gp.status = ctx->d_status;
+            gemm<<<std::min(tpc * ncb, ctx->num_sms), kThreads, smem, st>>>(gp);
+            prof_count(ctx, 2);
+        }
+    }
     prof_end(ctx, pidx, st);
-    prof_count(ctx, 1);
     HAI_CUDA_TRY(cudaGetLastError());
     return HAI_OK;
 }

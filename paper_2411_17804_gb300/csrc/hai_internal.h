@@ -25,7 +25,12 @@ struct hai_ctx {
     long long prof_launches = 0;        // all kernels launched
     void *d_dft[3] = {nullptr, nullptr, nullptr};   // tensor-core DFT operands, N = 32, 64, 128
     int capturing = 0;                  // a plan is capturing a graph: no profiling events
+    void *d_corr_ws = nullptr;          // correlator: fp16 operand images of a batch of channels
+    size_t corr_ws_bytes = 0;
 };
+
+// Correlator workspace reserved with the context.
+constexpr size_t kCorrWorkspaceBytes = (size_t)256 << 20;
 
 // Profiling helpers: prof_begin returns the pair index or -1.
 int prof_begin(hai_ctx *ctx, cudaStream_t st);

@@ -33,12 +33,26 @@ def run_corr(hai, ctx, volt, accumulate=0, vis=None):
     (1, 600, 96, 2),     # crosses the 512-sample exact block
     (2, 1030, 130, 1),   # three blocks, ragged everything
     (1, 64, 256, 2),     # SKA-low station size
+    (1, 96, 700, 2),     # several pack groups, the last one partial
 ])
 def test_correlator_bit_exact(hai, ctx, C, T, N, P):
     volt = I.random_voltages((C, T, P, N, 2), seed=C * 1000 + T + N)
     got = run_corr(hai, ctx, volt)
     want = O.correlate(volt.numpy())
     assert np.array_equal(got, want)
+
+
+def test_correlator_unaligned_voltages(hai, ctx):
+    """A voltage pointer 2 bytes past a 16-byte boundary (N a multiple of 8):
+    the pack takes its element-wise loads instead of 16-byte vectors."""
+    C, T, N, P = 2, 77, 64, 2
+    volt = I.random_voltages((C, T, P, N, 2), seed=9)
+    flat = torch.zeros(volt.numel() + 16, dtype=torch.int8, device="cuda")
+    flat[2:2 + volt.numel()] = volt.flatten().cuda()
+    vis = torch.zeros((C, N * (N + 1) // 2, P, P, 2), dtype=torch.int32, device="cuda")
+    hai.hai_correlate(ctx, flat[2:2 + volt.numel()], C, T, N, P, vis, 0)
+    hai.hai_sync(ctx)
+    assert np.array_equal(vis.cpu().numpy().astype(np.int64), O.correlate(volt.numpy()))
 
 
 def test_correlator_adversarial_extremes(hai, ctx):
