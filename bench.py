@@ -170,14 +170,15 @@ def tc_mma_flops_per_unit(cfg, box=32):
 
 
 def corr_mma_flops(C, T, N, P):
-    """Executed tensor-core FLOP of one correlator launch: tiles x 32-sample
-    stages x 4 MMAs of 128 x 128 x 16 (rows: P x 128/P elements, columns:
-    2 x P x 64/P elements)."""
-    em, en = 128 // P, 64 // P
-    nbi, nbj = -(-N // em), -(-N // en)
-    tiles = sum(min(nbj, min(N - 1, (i + 1) * em - 1) // en + 1) for i in range(nbi))
+    """Executed tensor-core FLOP of one correlator launch: tiles (row block of
+    128 / P elements x two column blocks of 64 / P elements, a >= b somewhere
+    in it) x 32-sample k blocks x 4 MMAs of 128 x 256 x 16."""
+    em, E = 128 // P, 64 // P
+    nbi, nbj = -(-N // em), -(-N // E)
+    npairs = max((nbj + 1) // 2, nbi)
+    tiles = sum(min(npairs, min(N - 1, (i + 1) * em - 1) // (2 * E) + 1) for i in range(nbi))
     stages = -(-T // 32)
-    return C * tiles * stages * 4 * 2.0 * 128 * 128 * 16
+    return C * tiles * stages * 4 * 2.0 * 128 * 256 * 16
 
 
 def corr_useful_ops(C, T, N, P):

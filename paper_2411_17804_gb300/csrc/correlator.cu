@@ -3,17 +3,16 @@
 // results.
 //
 // Per channel the voltages form a real matrix X[m][k] with rows m = (pol,
-// element) and columns k = (sample, re/im).  For a tile of rows (elements
-// a) and columns (elements b):
+// element) and columns k = (sample, re/im).  For rows (elements a) and
+// columns (elements b):
 //   Re V = sum_k X_a[k] X_b[k],   Im V = sum_k X_a[k] X'_b[k],
-// where X'_b = (-Im, Re) per sample, so one MMA with B = [X_b ; X'_b]
-// (N = 128) yields both parts.  int8 values are exact in FP16, products are
-// at most 2^14 in magnitude, and an FP32 sum of 1024 of them (512 samples)
-// stays an exact integer (|sum| <= 2^24): the tensor cores accumulate one
-// 512-sample block in TMEM, the epilogue rounds it to int32 (exact) and adds
-// it to integer sums kept in a third TMEM region, and after the last block
-// writes (or adds) the tile's visibilities once.  |V| <= 2^15 T, so int32 holds any
-// T <= 65535.
+// where X'_b = (-Im, Re) per sample, so B = [X_b ; X'_b] gives both parts in
+// one product.  int8 values are exact in FP16, products are at most 2^14 in
+// magnitude, and an FP32 sum of 1024 of them (512 samples) stays an exact
+// integer (|sum| <= 2^24): the tensor cores accumulate one 512-sample block
+// in TMEM, the epilogue rounds it to int32 (exact) and adds it to integer
+// sums held in registers, and after the last block writes (or adds) the
+// tile's visibilities once.  |V| <= 2^15 T, so int32 holds any T <= 65535.
 //
 // Two kernels per batch of channels and samples (sized to the context's
 // workspace):
@@ -22,15 +21,19 @@
 //          (channel, k block, column block J) holding [X ; X'] of the 64 / P
 //          elements of column block J, both pols, rows (x', pol, element),
 //          transposed through shared memory;
-//   gemm:  persistent, one work item per (lower-triangle tile, channel).
-//          The A operand of row block I (128 / P elements, rows (half, pol,
-//          element)) is the X halves of images 2I and 2I+1, so it needs no
-//          images of its own: per k block three bulk copies (8 + 8 + 16 KB)
-//          fill one stage of a 6-stage ring, one thread issues the MMAs
-//          (M = 128, N = 128, K = 16, four per k block) into one of two TMEM
-//          accumulators (one per 512-sample block, alternating, so the
-//          epilogue of a block overlaps the MMAs of the next), and four
-//          epilogue warps drain them.
+//   gemm:  persistent, one work item per (row block I, pair of column blocks
+//          2JP, 2JP+1, channel) with a >= b somewhere in it.  The A operand
+//          of row block I (128 / P elements, rows (half, pol, element)) is the
+//          X halves of images 2I and 2I+1, so it needs no images of its own;
+//          B is images 2JP and 2JP+1, adjacent in the workspace.  Per k block
+//          three bulk copies (8 + 8 + 32 KB) fill one stage of a 4-stage ring
+//          and one thread issues four MMAs of M = 128, N = 256, K = 16 (one
+//          commit per k block: a commit-and-wait round trip costs about as
+//          much as four MMAs of N = 256, so narrower MMAs would leave the
+//          tensor pipe idle) into one of two 256-column TMEM accumulators,
+//          alternating per 512-sample block so that the epilogue of a block
+//          overlaps the MMAs of the next.  Eight epilogue warps (two per TMEM
+//          lane quadrant, one per column block of the pair) drain them.
 #include <string.h>
 
 #include <algorithm>
@@ -43,36 +46,39 @@ namespace {
 constexpr int kChunkT = 512;            // samples per exact FP32 block
 constexpr int kKbT = 32;                // samples per k block (K = 64)
 constexpr int kKbPerChunk = kChunkT / kKbT;
-constexpr int kStages = 6;
+constexpr int kStages = 4;
 constexpr uint32_t kLBO = 128;          // K-major: K-group stride
 constexpr uint32_t kSBO = 1024;         // K-major: MN-group stride
 constexpr uint32_t kImg = 16384;        // 128 rows x 64 K fp16
 constexpr uint32_t kHalf = kImg / 2;    // rows 0..63 of an image
-constexpr uint32_t kStage = 2 * kImg;   // A + B
-constexpr uint32_t kIdesc = tc::idesc_f16(128, 128, 0, 0);
-constexpr int kThreads = 256;           // warp 0 loads, warp 1 MMA, warps 4-7 epilogue
-constexpr uint32_t kTmemCols = 512;     // two 128-column FP32 accumulators + int32 sums
+constexpr uint32_t kStage = 3 * kImg;   // A (16 KB) + B (32 KB)
+constexpr uint32_t kIdesc = tc::idesc_f16(128, 256, 0, 0);
+constexpr int kThreads = 320;           // warp 0 loads, warp 1 MMA, warps 2-9 epilogue
+constexpr int kEpiThreads = 256;
+constexpr uint32_t kTmemCols = 512;     // two 256-column FP32 accumulators
 
 struct CorrGeo {
     int T, ne, P;
     int em, E;                   // elements per row block; per column block (= per 64-row half)
     int nbi, nbj;                // row / column blocks per channel
-    int nimg;                    // images per (channel, k block): max(nbj, 2 nbi)
+    int nimg;                    // images per (channel, k block): max(nbj rounded up to even, 2 nbi)
     int tiles_per_chan;
 };
 
-// (I, J) of the k-th lower-triangle tile of a channel, row-block major.
-__device__ __forceinline__ void decode_tile(const CorrGeo &g, int k, int &I, int &J) {
+// (I, JP) of the k-th tile of a channel (row block I, column blocks 2JP and
+// 2JP+1) with some a >= b, row-block major.
+__device__ __forceinline__ void decode_tile(const CorrGeo &g, int k, int &I, int &JP) {
+    const int njp_all = g.nimg / 2;
     for (I = 0; I < g.nbi; I++) {
         const int amax = min(g.ne - 1, (I + 1) * g.em - 1);
-        const int nj = min(g.nbj, amax / g.E + 1);
-        if (k < nj) {
-            J = k;
+        const int njp = min(njp_all, amax / (2 * g.E) + 1);
+        if (k < njp) {
+            JP = k;
             return;
         }
-        k -= nj;
+        k -= njp;
     }
-    I = J = 0;
+    I = JP = 0;
 }
 
 // image J of (channel cb, k block kb) of a batch holding nkb k blocks per channel
@@ -160,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_gemm_kernel(const GemmParams
         }
         for (int b = 0; b < 2; b++) {
             tc::mbar_init(&accf[b], 1);
-            tc::mbar_init(&acce[b], 128);
+            tc::mbar_init(&acce[b], kEpiThreads);
         }
         tc::mbar_fence_init();
     }
@@ -169,109 +175,133 @@ __global__ void __launch_bounds__(kThreads, 1) corr_gemm_kernel(const GemmParams
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tslot;
+    // The loader and MMA loops run on one thread each and sit on the critical
+    // path: stage and parity are toggled, not divided, pointers and
+    // descriptors advance by additions.
     if (warp == 0) {
         if (lane == 0) {
-            long long it = 0;                      // k blocks loaded by this CTA
+            int s = 0;
+            uint32_t ph = 1;                       // first pass over the ring waits on nothing
+            bool wrapped = false;
+            const size_t kb_stride = (size_t)g.nimg * kImg;
             for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
-                int I, J;
-                decode_tile(g, w % g.tiles_per_chan, I, J);
-                const int cb = w / g.tiles_per_chan;
-                for (int kb = 0; kb < p.nkb; kb++, it++) {
-                    const int s = (int)(it % kStages);
-                    if (it >= kStages) tc::mbar_wait(&empty[s], (uint32_t)(((it / kStages) - 1) & 1), p.status);
+                int I, JP;
+                decode_tile(g, w % g.tiles_per_chan, I, JP);
+                const uint8_t *base = p.ws + img_index(g, p.nkb, w / g.tiles_per_chan, 0, 0) * kImg;
+                const uint8_t *pa0 = base + (size_t)(2 * I) * kImg, *pa1 = pa0 + kImg;
+                const uint8_t *pb = base + (size_t)(2 * JP) * kImg;
+                for (int kb = 0; kb < p.nkb; kb++) {
+                    if (wrapped) tc::mbar_wait(&empty[s], ph, p.status);
                     uint8_t *st = smem + (size_t)s * kStage;
                     tc::mbar_arrive_expect_tx(&full[s], kStage);
-                    tc::bulk_g2s(st, p.ws + img_index(g, p.nkb, cb, kb, 2 * I) * kImg, kHalf, &full[s]);
-                    tc::bulk_g2s(st + kHalf, p.ws + img_index(g, p.nkb, cb, kb, 2 * I + 1) * kImg, kHalf, &full[s]);
-                    tc::bulk_g2s(st + kImg, p.ws + img_index(g, p.nkb, cb, kb, J) * kImg, kImg, &full[s]);
+                    tc::bulk_g2s(st, pa0, kHalf, &full[s]);
+                    tc::bulk_g2s(st + kHalf, pa1, kHalf, &full[s]);
+                    tc::bulk_g2s(st + kImg, pb, 2 * kImg, &full[s]);
+                    pa0 += kb_stride;
+                    pa1 += kb_stride;
+                    pb += kb_stride;
+                    if (++s == kStages) {
+                        s = 0;
+                        ph ^= 1u;
+                        wrapped = true;
+                    }
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            long long it = 0, grp = 0;             // k blocks consumed; accumulator groups
+            int s = 0;
+            uint32_t ph = 0;                       // full[] parity
+            uint32_t acc_ph = 3u, acc_used = 0u;   // per buffer (bit b): acce[] parity, buffer used before
+            int b = 0;
+            // descriptors of stage 0; a stage is kStage bytes = kStage >> 4 in the address field
+            const uint64_t da0 = tc::desc(tc::smem_u32(smem), kLBO, kSBO);
+            const uint64_t db0 = tc::desc(tc::smem_u32(smem) + kImg, kLBO, kSBO);
+            constexpr uint64_t kStageD = kStage >> 4, kStepD = (2 * kLBO) >> 4;
             for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
-                for (int ch = 0; ch < nchunk; ch++, grp++) {
-                    const int b = (int)(grp & 1);
-                    if (grp >= 2) tc::mbar_wait(&acce[b], (uint32_t)(((grp >> 1) - 1) & 1), p.status);
+                for (int ch = 0; ch < nchunk; ch++) {
+                    if ((acc_used >> b) & 1u) tc::mbar_wait(&acce[b], (acc_ph >> b) & 1u, p.status);
+                    acc_ph ^= 1u << b;
+                    acc_used |= 1u << b;
                     tc::fence_after();
-                    const uint32_t d = tmem + (uint32_t)(b * 128);
-                    const int kb1 = min(p.nkb, (ch + 1) * kKbPerChunk);
-                    for (int kb = ch * kKbPerChunk; kb < kb1; kb++, it++) {
-                        const int s = (int)(it % kStages);
-                        tc::mbar_wait(&full[s], (uint32_t)((it / kStages) & 1), p.status);
+                    const uint32_t d = tmem + (uint32_t)(b * 256);
+                    const int nk = min(kKbPerChunk, p.nkb - ch * kKbPerChunk);
+                    for (int kb = 0; kb < nk; kb++) {
+                        tc::mbar_wait(&full[s], ph, p.status);
                         tc::fence_after();
-                        const uint32_t sa = tc::smem_u32(smem + (size_t)s * kStage), sb = sa + kImg;
-#pragma unroll
-                        for (int j = 0; j < 4; j++)
-                            tc::mma_f16(d, tc::desc(sa + j * 2 * kLBO, kLBO, kSBO),
-                                        tc::desc(sb + j * 2 * kLBO, kLBO, kSBO), kIdesc,
-                                        (kb > ch * kKbPerChunk || j > 0) ? 1u : 0u);
+                        const uint64_t da = da0 + (uint64_t)s * kStageD, db = db0 + (uint64_t)s * kStageD;
+                        tc::mma_f16(d, da, db, kIdesc, kb > 0 ? 1u : 0u);
+                        tc::mma_f16(d, da + kStepD, db + kStepD, kIdesc, 1u);
+                        tc::mma_f16(d, da + 2 * kStepD, db + 2 * kStepD, kIdesc, 1u);
+                        tc::mma_f16(d, da + 3 * kStepD, db + 3 * kStepD, kIdesc, 1u);
                         tc::mma_commit(&empty[s]);
+                        if (++s == kStages) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
                     }
                     tc::mma_commit(&accf[b]);
+                    b ^= 1;
                 }
             }
         }
-    } else if (warp >= 4) {
-        const int q = warp & 3, m = q * 32 + lane;
+    } else {
+        // epilogue, warps 2-9: TMEM lane quadrant q = warp % 4 (row m), column
+        // block hs of the pair; 64 (b, q) outputs, their int32 sums in registers
+        const int q = warp & 3, hs = (warp - 2) >> 2, m = q * 32 + lane;
         const int h = m >> 6, rr = m & 63;
         const int pol = rr / E;
-        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-        const uint32_t tsum = lane_base + 256u;   // int32 sums of the work item: re 0..63, im 64..127
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hs * 128);
         const long long nbl = (long long)g.ne * (g.ne + 1) / 2;
         long long grp = 0;
         for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
-            int I, J;
-            decode_tile(g, w % g.tiles_per_chan, I, J);
+            int I, JP;
+            decode_tile(g, w % g.tiles_per_chan, I, JP);
+            const int J = 2 * JP + hs;
             const int c = p.c0 + w / g.tiles_per_chan;
             const int a = I * (2 * E) + h * E + rr % E;
-            int2 *row = a < g.ne ? reinterpret_cast<int2 *>(p.vis) +
-                                       (((size_t)c * nbl + (long long)a * (a + 1) / 2) * P + pol) * P
-                                 : nullptr;
+            int sre[64], sim[64];
+#pragma unroll
+            for (int k = 0; k < 64; k++) sre[k] = sim[k] = 0;
             for (int ch = 0; ch < nchunk; ch++, grp++) {
                 const int b = (int)(grp & 1);
-                const bool first = ch == 0, last = ch == nchunk - 1;
                 tc::mbar_wait(&accf[b], (uint32_t)((grp >> 1) & 1), p.status);
                 tc::fence_after();
-                const uint32_t tacc = lane_base + (uint32_t)(b * 128);
-#pragma unroll 1
+                const uint32_t tacc = lane_base + (uint32_t)(b * 256);
+#pragma unroll
                 for (int n0 = 0; n0 < 64; n0 += 16) {
-                    uint32_t vr[16], vi[16], sr[16], si[16];
+                    uint32_t vr[16], vi[16];
                     tc::tmem_ld16(tacc + (uint32_t)n0, vr);
                     tc::tmem_ld16(tacc + 64u + (uint32_t)n0, vi);
-                    if (!first) {
-                        tc::tmem_ld16(tsum + (uint32_t)n0, sr);
-                        tc::tmem_ld16(tsum + 64u + (uint32_t)n0, si);
-                    }
                     tc::tmem_wait_ld();
 #pragma unroll
                     for (int k = 0; k < 16; k++) {
-                        sr[k] = (first ? 0u : sr[k]) + (uint32_t)__float2int_rn(__uint_as_float(vr[k]));
-                        si[k] = (first ? 0u : si[k]) + (uint32_t)__float2int_rn(__uint_as_float(vi[k]));
-                    }
-                    if (!last) {
-                        tc::tmem_st16(tsum + (uint32_t)n0, sr);
-                        tc::tmem_st16(tsum + 64u + (uint32_t)n0, si);
-                    } else if (row) {
-#pragma unroll
-                        for (int k = 0; k < 16; k++) {
-                            const int n = n0 + k, qq = n / E, bb = J * E + n % E;
-                            if (bb > a || bb >= g.ne) continue;
-                            int2 *o = row + (size_t)bb * (P * P) + qq;
-                            int2 v = make_int2((int)sr[k], (int)si[k]);
-                            if (p.add) {
-                                const int2 old = *o;
-                                v.x += old.x;
-                                v.y += old.y;
-                            }
-                            *o = v;
-                        }
+                        sre[n0 + k] += __float2int_rn(__uint_as_float(vr[k]));
+                        sim[n0 + k] += __float2int_rn(__uint_as_float(vi[k]));
                     }
                 }
-                if (!last) tc::tmem_wait_st();
                 tc::fence_before();
                 tc::mbar_arrive(&acce[b]);
+            }
+            if (a < g.ne) {
+                int2 *row = reinterpret_cast<int2 *>(p.vis) + (((size_t)c * nbl + (long long)a * (a + 1) / 2) * P + pol) * P;
+#pragma unroll
+                for (int n0 = 0; n0 < 64; n0 += 16) {
+#pragma unroll
+                    for (int k = 0; k < 16; k++) {
+                        const int n = n0 + k, qq = n / E, bb = J * E + n % E;
+                        if (bb > a || bb >= g.ne) continue;
+                        int2 *o = row + (size_t)bb * (P * P) + qq;
+                        int2 v = make_int2(sre[n], sim[n]);
+                        if (p.add) {
+                            const int2 old = *o;
+                            v.x += old.x;
+                            v.y += old.y;
+                        }
+                        *o = v;
+                    }
+                    asm volatile("" ::: "memory");   // keep the read-modify-writes in groups of 16
+                }
             }
         }
     }
@@ -289,6 +319,7 @@ extern "C" hai_status hai_correlate(hai_ctx *ctx, const int8_t *volt, int C, int
     if (C < 0 || T < 0 || N <= 0 || (P != 1 && P != 2) || (accumulate != 0 && accumulate != 1))
         return hai_fail(HAI_ERR_INVALID_ARG, "hai_correlate: bad size, polarisation count or flag");
     if (T > 65535) return hai_fail(HAI_ERR_OVERFLOW_RISK, "hai_correlate: T > 65535 may overflow int32");
+    if (N > 65535) return hai_fail(HAI_ERR_UNSUPPORTED, "hai_correlate: N > 65535");
     CorrGeo g;
     g.T = T;
     g.ne = N;
@@ -297,7 +328,7 @@ extern "C" hai_status hai_correlate(hai_ctx *ctx, const int8_t *volt, int C, int
     g.E = 64 / P;
     g.nbi = (N + g.em - 1) / g.em;
     g.nbj = (N + g.E - 1) / g.E;
-    g.nimg = std::max(g.nbj, 2 * g.nbi);
+    g.nimg = std::max((g.nbj + 1) & ~1, 2 * g.nbi);
     const size_t chunk_bytes = (size_t)kKbPerChunk * g.nimg * kImg;   // one channel, one 512-sample block
     if (chunk_bytes > ctx->corr_ws_bytes)
         return hai_fail(HAI_ERR_UNSUPPORTED, "hai_correlate: N too large for the operand workspace");
@@ -315,7 +346,7 @@ extern "C" hai_status hai_correlate(hai_ctx *ctx, const int8_t *volt, int C, int
     int tpc = 0;
     for (int I = 0; I < g.nbi; I++) {
         const int amax = std::min(N - 1, (I + 1) * g.em - 1);
-        tpc += std::min(g.nbj, amax / g.E + 1);
+        tpc += std::min(g.nimg / 2, amax / (2 * g.E) + 1);
     }
     g.tiles_per_chan = tpc;
     // batches: as many 512-sample blocks per channel as fit, then as many channels

@@ -30,7 +30,7 @@ struct hai_ctx {
 };
 
 // Correlator workspace reserved with the context.
-constexpr size_t kCorrWorkspaceBytes = (size_t)256 << 20;
+constexpr size_t kCorrWorkspaceBytes = (size_t)512 << 20;
 
 // Profiling helpers: prof_begin returns the pair index or -1.
 int prof_begin(hai_ctx *ctx, cudaStream_t st);
