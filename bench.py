@@ -602,11 +602,11 @@ def run_case(name):
         out = torch.empty((S, C, T, K, P, 2), dtype=torch.int8, device="cuda")
         for _ in range(2):
             hai.hai_beamform(ctx, v, w, S, C, T, K, N, P, 11, out)
-    elif name in ("tc64", "corr"):        # 16 channels of the SKA-low station: 33.6 MB of voltages
+    elif name in ("tc64", "corr"):        # the SKA-low station: 16 channels (33.6 MB) for tc64, 64 for corr
         cfg = I.SKA_LOW_STATION_256
         pos = I.station_layout(cfg)
         an, tp = I.station_kernel(cfg, pos)
-        C = 16
+        C = 16 if name == "tc64" else cfg.n_chan
         v = I.station_voltages(cfg, pos, device="cuda", n_chan=C)
         if name == "tc64":
             lay = hai.hai_layout_create(ctx, an, tp, 64, 2)
