@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--no-components", action="store_true")
     ap.add_argument("--channels", type=int, default=0,
                     help="image only this many channels (small cases for profiling)")
-    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "bf", "xbf", "fc", "big"], default=None,
+    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "bf", "xbf", "fc", "big", "big16"], default=None,
                     help="run one small case of a kernel twice, untimed, and exit (for ncu captures)")
     return ap.parse_args()
 
@@ -643,15 +643,16 @@ def run_case(name):
             hai.hai_xbf_station_image(ctx, xl, vis, C, img, 0)
         torch.cuda.synchronize()
         hai.hai_xbf_layout_destroy(xl)
-    elif name == "big":                   # the dense lattice on tensor cores, 4 channels x 20 samples
-        cfg = I.DENSE_ALLSKY_16384
+    elif name in ("big", "big16"):        # the dense lattice on tensor cores: 4 ch x 20 samples, or the
+        cfg = I.DENSE_ALLSKY_16384        # benchmark's cadence (16 ch x 100 samples)
         pos = I.station_layout(cfg)
         an, tp = I.station_kernel(cfg, pos)
         lay = hai.hai_layout_create(ctx, an, tp, 512, 2)
-        v = I.random_voltages((4, 20, 2, len(pos), 2), seed=5, device="cuda")
-        img = torch.empty((4, 4, 512, 512), device="cuda")
+        C, T = (4, 20) if name == "big" else (16, 100)
+        v = I.random_voltages((C, T, 2, len(pos), 2), seed=5, device="cuda")
+        img = torch.empty((C, 4, 512, 512), device="cuda")
         for _ in range(2):
-            hai.hai_epic_image(ctx, lay, v, 4, 20, hai.HAI_PREC_FP16, img, 0)
+            hai.hai_epic_image(ctx, lay, v, C, T, hai.HAI_PREC_FP16, img, 0)
     elif name == "fc":                    # FFT correlator on 16 channels of 512^2 images (67 MB in)
         img = torch.randn((16, 4, 512, 512), device="cuda")
         grid = torch.empty((16, 2, 2, 512, 512, 2), device="cuda")

@@ -10,8 +10,9 @@
 // one SM, so the stages run as three kernels per batch of (channel, sample)
 // pairs, through HBM:
 //   grid:   every field (channel, sample, pol) gathered into its box (FP32
-//           sums of conj(W~) E, stored fp16), K-major in the tensor cores'
-//           tile order: A1[field][y block][k block] = 128 rows y x 64 (x, re/im);
+//           sums of conj(W~) E, stored fp16; one thread per cell and 8
+//           fields), K-major in the tensor cores' tile order:
+//           A1[field][y block][k block] = 128 rows y x 64 (x, re/im);
 //   stage1: H[y][l_x] = sum_x G[y][x] W'[x][l_x]: persistent CTAs over
 //           (field, y block, 128-wide l_x block) tiles, bulk copies of A1 and
 //           the constant DFT operand, tcgen05.mma M = 128, N = 256 (re, im of
@@ -57,35 +58,52 @@ struct BigGeo {
 };
 
 // ------------------------------------------------------------------ grid
-// one thread per (field, cell of the padded box row-major); fields of the
-// batch are (c, t, p) with c T + t in [b0, b1)
-__global__ void __launch_bounds__(256) big_grid_kernel(const int8_t *__restrict__ volt, int T, int ne,
+// one thread per (cell of the padded box, row-major; group of kGridFields
+// fields): the cell's entries are read once for the group and the fields'
+// voltage loads are independent, so they are in flight together.  Fields of
+// the batch are f = (c T + t - b0) P + pol.
+constexpr int kGridFields = 8;
+
+__global__ void __launch_bounds__(256) big_grid_kernel(const int8_t *__restrict__ volt, int ne,
                                                        const int32_t *__restrict__ cell_start,
                                                        const int32_t *__restrict__ entry_elem,
                                                        const float2 *__restrict__ entry_w, BigGeo g, long long b0,
                                                        long long nfield, uint8_t *__restrict__ a1) {
     const int bxp = g.kb1 * 32, byp = g.yb * 128;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nfield * bxp * byp) return;
-    const int x = (int)(i % bxp), y = (int)((i / bxp) % byp);
-    const long long f = i / ((long long)bxp * byp);            // field in the batch
-    const int pol = (int)(f % g.P);
-    const long long ct = b0 + f / g.P;                         // c T + t
-    float2 acc = make_float2(0.f, 0.f);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= bxp * byp) return;
+    const int x = i % bxp, y = i / bxp;
+    const long long f0 = (long long)blockIdx.y * kGridFields;
+    const int nf = (int)(nfield - f0 < kGridFields ? nfield - f0 : kGridFields);
+    int k0 = 0, k1 = 0;
     if (x < g.bx && y < g.by) {
-        const char2 *E = reinterpret_cast<const char2 *>(volt) + (size_t)(ct * g.P + pol) * ne;
-        const int cell = y * g.bx + x;
-        for (int k = cell_start[cell]; k < cell_start[cell + 1]; k++) {
-            const char2 e = E[entry_elem[k]];
-            const float2 w = entry_w[k];                       // conj(W~)
-            acc.x = fmaf(w.x, (float)e.x, fmaf(-w.y, (float)e.y, acc.x));
-            acc.y = fmaf(w.x, (float)e.y, fmaf(w.y, (float)e.x, acc.y));
+        k0 = cell_start[y * g.bx + x];
+        k1 = cell_start[y * g.bx + x + 1];
+    }
+    // voltages of field f: volt + ((b0 P + f) ne) char2
+    const char2 *E = reinterpret_cast<const char2 *>(volt) + (size_t)(b0 * g.P + f0) * ne;
+    float2 acc[kGridFields];
+#pragma unroll
+    for (int j = 0; j < kGridFields; j++) acc[j] = make_float2(0.f, 0.f);
+    for (int k = k0; k < k1; k++) {
+        const int e = entry_elem[k];
+        const float2 w = entry_w[k];                           // conj(W~)
+        char2 v[kGridFields];
+#pragma unroll
+        for (int j = 0; j < kGridFields; j++) v[j] = j < nf ? E[(size_t)j * ne + e] : make_char2(0, 0);
+#pragma unroll
+        for (int j = 0; j < kGridFields; j++) {
+            acc[j].x = fmaf(w.x, (float)v[j].x, fmaf(-w.y, (float)v[j].y, acc[j].x));
+            acc[j].y = fmaf(w.x, (float)v[j].y, fmaf(w.y, (float)v[j].x, acc[j].y));
         }
     }
     const int k = 2 * x;
-    uint8_t *dst = a1 + (((size_t)f * g.yb + y / 128) * g.kb1 + k / 64) * kTile16 +
+    const size_t field_bytes = (size_t)g.yb * g.kb1 * kTile16;
+    uint8_t *dst = a1 + (size_t)f0 * field_bytes + ((size_t)(y / 128) * g.kb1 + k / 64) * kTile16 +
                    tc::off_kmajor(y % 128, k % 64, kKBytes, kKMN);
-    *reinterpret_cast<uint32_t *>(dst) = tc::pack_half2(acc.x, acc.y);
+#pragma unroll
+    for (int j = 0; j < kGridFields; j++)
+        if (j < nf) *reinterpret_cast<uint32_t *>(dst + (size_t)j * field_bytes) = tc::pack_half2(acc[j].x, acc[j].y);
 }
 
 // ------------------------------------------------------------------ stage 1
@@ -226,11 +244,15 @@ struct S2Params {
 };
 
 constexpr int kS2Threads = 384;             // warp 0 loads, warp 1 MMA, warps 4-11 epilogue
+constexpr int kS2Kb = 4;                    // k blocks of stage 2 (boxes <= 128 rows: 2 x 128 / 64)
 constexpr int kS2Epi = 256;
 
 __global__ void __launch_bounds__(kS2Threads, 1) big_s2_kernel(const S2Params p) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t bfull, afull[2], aempty[2], dfull[2], dempty[2];
+    // sdone[b]: every MMA of the sample in A buffer / accumulator b has completed
+    // (one commit per sample: the loader may refill A buffer b, the epilogue
+    // may read accumulator b)
+    __shared__ __align__(8) uint64_t bfull, afull[2], sdone[2], dempty[2];
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const BigGeo g = p.g;
@@ -241,8 +263,7 @@ __global__ void __launch_bounds__(kS2Threads, 1) big_s2_kernel(const S2Params p)
         tc::mbar_init(&bfull, 1);
         for (int b = 0; b < 2; b++) {
             tc::mbar_init(&afull[b], 1);
-            tc::mbar_init(&aempty[b], 1);
-            tc::mbar_init(&dfull[b], 1);
+            tc::mbar_init(&sdone[b], 1);
             tc::mbar_init(&dempty[b], kS2Epi);
         }
         tc::mbar_fence_init();
@@ -268,7 +289,7 @@ __global__ void __launch_bounds__(kS2Threads, 1) big_s2_kernel(const S2Params p)
                 const int c = p.c_first + it / per_chan, r = it % per_chan, lxb = r / g.lb2, lyb = r % g.lb2;
                 if (lyb != cur_lyb) {
                     // the previous item's MMAs have all completed once its last A stage is released
-                    if (gs > 0) tc::mbar_wait(&aempty[(gs - 1) & 1], (uint32_t)(((gs - 1) >> 1) & 1), p.status);
+                    if (gs > 0) tc::mbar_wait(&sdone[(gs - 1) & 1], (uint32_t)(((gs - 1) >> 1) & 1), p.status);
                     tc::mbar_arrive_expect_tx(&bfull, abytes);
                     tc::bulk_g2s(sB, p.b2 + (size_t)lyb * abytes, abytes, &bfull);
                     cur_lyb = lyb;
@@ -278,7 +299,7 @@ __global__ void __launch_bounds__(kS2Threads, 1) big_s2_kernel(const S2Params p)
                 trange(c, t0, t1);
                 for (int t = t0; t < t1; t++, gs++) {
                     const int s = (int)(gs & 1);
-                    if (gs >= 2) tc::mbar_wait(&aempty[s], (uint32_t)(((gs >> 1) - 1) & 1), p.status);
+                    if (gs >= 2) tc::mbar_wait(&sdone[s], (uint32_t)(((gs >> 1) - 1) & 1), p.status);
                     const long long ct = (long long)c * p.T + t - p.b0;
                     tc::mbar_arrive_expect_tx(&afull[s], abytes);
                     tc::bulk_g2s(sA(s), p.a2 + ((size_t)ct * g.lb2 + lxb) * abytes, abytes, &afull[s]);
@@ -286,10 +307,15 @@ __global__ void __launch_bounds__(kS2Threads, 1) big_s2_kernel(const S2Params p)
             }
         }
     } else if (warp == 1) {
+        // one thread issues 16 MMAs per sample (4 k blocks x 4), one commit;
+        // descriptors advance by additions to their 14-bit address field
         if (lane == 0) {
             long long gs = 0;
             int cur_lyb = -1;
             uint32_t bph = 0;
+            const uint64_t db0 = tc::desc(tc::smem_u32(sB), kKBytes, kKMN);
+            const uint64_t da0 = tc::desc(tc::smem_u32(sA(0)), kMKs, kMMN);
+            const uint64_t kBufD = abytes >> 4, kKbD = kTile16 >> 4, kStepA = (2 * kMKs) >> 4, kStepB = (2 * kKBytes) >> 4;
             for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
                 const int c = p.c_first + it / per_chan, r = it % per_chan, lyb = r % g.lb2;
                 if (lyb != cur_lyb) {
@@ -301,18 +327,19 @@ __global__ void __launch_bounds__(kS2Threads, 1) big_s2_kernel(const S2Params p)
                 trange(c, t0, t1);
                 for (int t = t0; t < t1; t++, gs++) {
                     const int s = (int)(gs & 1);
-                    if (gs >= 2) tc::mbar_wait(&dempty[s], (uint32_t)(((gs >> 1) - 1) & 1), p.status);
-                    tc::mbar_wait(&afull[s], (uint32_t)((gs >> 1) & 1), p.status);
+                    const uint32_t ph = (uint32_t)((gs >> 1) & 1);
+                    if (gs >= 2) tc::mbar_wait(&dempty[s], ph ^ 1u, p.status);
+                    tc::mbar_wait(&afull[s], ph, p.status);
                     tc::fence_after();
-                    const uint32_t a = tc::smem_u32(sA(s)), bq = tc::smem_u32(sB), d = tmem + (uint32_t)s * 128u;
-                    for (int kb = 0; kb < g.kb2; kb++)
+                    const uint64_t da = da0 + (uint64_t)s * kBufD;
+                    const uint32_t d = tmem + (uint32_t)s * 128u;
+#pragma unroll
+                    for (int kb = 0; kb < kS2Kb; kb++)
 #pragma unroll
                         for (int j = 0; j < 4; j++)
-                            tc::mma_f16(d, tc::desc(a + kb * kTile16 + j * 2 * kMKs, kMKs, kMMN),
-                                        tc::desc(bq + kb * kTile16 + j * 2 * kKBytes, kKBytes, kKMN), kIdesc2,
+                            tc::mma_f16(d, da + kb * kKbD + j * kStepA, db0 + kb * kKbD + j * kStepB, kIdesc2,
                                         (kb > 0 || j > 0) ? 1u : 0u);
-                    tc::mma_commit(&aempty[s]);
-                    tc::mma_commit(&dfull[s]);
+                    tc::mma_commit(&sdone[s]);
                 }
             }
         }
@@ -335,7 +362,7 @@ __global__ void __launch_bounds__(kS2Threads, 1) big_s2_kernel(const S2Params p)
             trange(c, t0, t1);
             for (int t = t0; t < t1; t++, gs++) {
                 const int s = (int)(gs & 1);
-                tc::mbar_wait(&dfull[s], (uint32_t)((gs >> 1) & 1), p.status);
+                tc::mbar_wait(&sdone[s], (uint32_t)((gs >> 1) & 1), p.status);
                 tc::fence_after();
 #pragma unroll
                 for (int cc = 0; cc < 2; cc++) {
@@ -476,6 +503,7 @@ hai_status epic_big_launch(const hai_layout *L, const int8_t *volt, int C, int T
                                              "a box <= N/2");
     hai_ctx *ctx = L->ctx;
     const BigGeo g = big_geo(L);
+    if (g.kb2 != kS2Kb) return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16 (large grid): box taller than 128 cells");
     const size_t s1_smem = (size_t)kS1Stages * (kTile16 + kTile32);
     const size_t s2_smem = (size_t)3 * g.kb2 * kTile16;
     if (s1_smem > (size_t)ctx->smem_optin - 2048 || s2_smem > (size_t)ctx->smem_optin - 2048)
@@ -487,10 +515,10 @@ hai_status epic_big_launch(const hai_layout *L, const int8_t *volt, int C, int T
     for (long long b0 = 0; b0 < total; b0 += L->big_batch) {
         const long long b1 = std::min(total, b0 + L->big_batch);
         const long long nfield = (b1 - b0) * g.P;
-        const long long ncell = nfield * (long long)(g.kb1 * 32) * (g.yb * 128);
-        big_grid_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(
-            volt, T, L->n_elem, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g, b0, nfield,
-            static_cast<uint8_t *>(L->big_a1));
+        const int ncell = (g.kb1 * 32) * (g.yb * 128);
+        big_grid_kernel<<<dim3((ncell + 255) / 256, (unsigned)((nfield + kGridFields - 1) / kGridFields)), 256, 0,
+                          st>>>(volt, L->n_elem, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g, b0, nfield,
+                                static_cast<uint8_t *>(L->big_a1));
         S1Params p1;
         p1.a1 = static_cast<const uint8_t *>(L->big_a1);
         p1.b1 = static_cast<const uint8_t *>(L->big_b1);
