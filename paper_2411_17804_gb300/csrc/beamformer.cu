@@ -133,42 +133,58 @@ __global__ void __launch_bounds__(kThreads, 1) bf_kernel(const BfParams p) {
         // ============================================================ producers
         long long gq = 0;                                      // chunk counter (stages)
         int cur_s = -1;
-        // chunk q of the CTA -> (unit, pol, element chunk)
-        auto chunk_src = [&](long long q, long long &u, int &pol, int &kc) {
-            const long long per_unit = (long long)p.P * nchunk;
-            u = u0 + q / per_unit;
-            const int r = (int)(q % per_unit);
-            pol = r / nchunk;
-            kc = r % nchunk;
+        // chunks of the CTA in order: (unit = (station, channel, tile), pol,
+        // element chunk), walked by counters (no 64-bit divisions per chunk);
+        // one walker for the copies issued kAhead chunks early, one for the
+        // chunk being widened
+        struct Walk {
+            int s, c, tile, pol, kc;
+        };
+        auto walk_init = [&](Walk &w) {
+            w.s = (int)(u0 / ((long long)p.C * p.tiles));
+            w.c = (int)((u0 / p.tiles) % p.C);
+            w.tile = (int)(u0 % p.tiles);
+            w.pol = 0;
+            w.kc = 0;
+        };
+        auto walk_next = [&](Walk &w) {
+            if (++w.kc < nchunk) return;
+            w.kc = 0;
+            if (++w.pol < p.P) return;
+            w.pol = 0;
+            if (++w.tile < p.tiles) return;
+            w.tile = 0;
+            if (++w.c < p.C) return;
+            w.c = 0;
+            ++w.s;
         };
         const long long nq = (u1 - u0) * p.P * nchunk;
+        const uint32_t t_stride = (uint32_t)(p.P * row_bytes);  // bytes between samples of one pol
+        Walk wi, wc;
+        walk_init(wi);
+        walk_init(wc);
         auto issue = [&](long long q) {                        // cp.async of chunk q into its int8 stage
             if (q < nq) {
-                long long u;
-                int pol, kc;
-                chunk_src(q, u, pol, kc);
-                const int s = (int)(u / ((long long)p.C * p.tiles));
-                const int c = (int)((u / p.tiles) % p.C);
-                const int t0 = (int)(u % p.tiles) * kTile;
+                const int t0 = wi.tile * kTile;
+                const int8_t *base = p.volt + ((((size_t)wi.s * p.C + wi.c) * p.T + t0) * p.P + wi.pol) * row_bytes +
+                                     (size_t)wi.kc * kChunkE * 2;
                 uint8_t *dst = sI8 + (q % kI8Stages) * kI8Bytes;
+                const int t_valid = p.T - t0, a_left = p.ne - wi.kc * kChunkE;
                 for (int it = tid; it < kTile * 8; it += kProd) {      // 128 rows x 8 x 16 B
                     const int t = it >> 3, g = it & 7;
-                    const int a0 = kc * kChunkE + g * 8;
-                    const bool ok = (t0 + t < p.T) && (a0 < p.ne);
-                    const int8_t *src = p.volt + ((((size_t)s * p.C + c) * p.T + (ok ? t0 + t : 0)) * p.P + pol) *
-                                                     row_bytes + (size_t)(ok ? a0 : 0) * 2;
+                    const bool ok = (t < t_valid) && (g * 8 < a_left);
+                    const int8_t *src = ok ? base + (uint32_t)t * t_stride + g * 16 : p.volt;
                     // 16-byte group g of row t stored at g ^ (t & 7): conflict-free reads below
                     cp_async16(dst + t * 128 + ((g ^ (t & 7)) * 16), src, ok ? 16u : 0u);
                 }
+                walk_next(wi);
             }
             cp_async_commit();
         };
         for (int q = 0; q < kAhead; q++) issue(q);
         for (long long q = 0; q < nq; q++, gq++) {
-            long long u;
-            int pol, kc;
-            chunk_src(q, u, pol, kc);
-            const int s = (int)(u / ((long long)p.C * p.tiles));
+            const int s = wc.s;
+            walk_next(wc);
             issue(q + kAhead);             // its ring slot was drained at the end of iteration q - 1
             cp_async_wait<kAhead>();
             const int slot = (int)(gq % kAStages);
