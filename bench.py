@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--no-components", action="store_true")
     ap.add_argument("--channels", type=int, default=0,
                     help="image only this many channels (small cases for profiling)")
-    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "bf", "xbf", "fc", "big", "big16"], default=None,
+    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "bf", "xbf", "sxfft", "fc", "big", "big16"], default=None,
                     help="run one small case of a kernel twice, untimed, and exit (for ncu captures)")
     return ap.parse_args()
 
@@ -643,6 +643,20 @@ def run_case(name):
             hai.hai_xbf_station_image(ctx, xl, vis, C, img, 0)
         torch.cuda.synchronize()
         hai.hai_xbf_layout_destroy(xl)
+    elif name == "sxfft":                 # station XFFT of the hierarchical cadence: 16 beams x 32 channels
+        H = I.HierarchyConfig()
+        centres = I.station_centres(H)
+        S, n, K, C = len(centres), H.grid_n, H.n_beam, 32
+        dirs = I.beam_directions(H.n_beam, H.station.lam_m, H.station.diameter_m)
+        g = torch.Generator(device="cuda").manual_seed(4)
+        vis = torch.randint(-2**20, 2**20, (K * C, S * (S + 1) // 2, 2, 2, 2), dtype=torch.int32, device="cuda",
+                            generator=g)
+        vl = hai.hai_vis_layout_create(ctx, centres, H.station.lam_m, H.cell_m, n, dirs)
+        img = torch.empty((K * C, 4, n, n), device="cuda")
+        for _ in range(2):
+            hai.hai_xfft_station_image(ctx, vl, vis, C, img)
+        torch.cuda.synchronize()
+        hai.hai_vis_layout_destroy(vl)
     elif name in ("big", "big16"):        # the dense lattice on tensor cores: 4 ch x 20 samples, or the
         cfg = I.DENSE_ALLSKY_16384        # benchmark's cadence (16 ch x 100 samples)
         pos = I.station_layout(cfg)

@@ -25,7 +25,8 @@
 // tiles (<= 112 x 112 cells) of the window of uv cells that on-grid pairs
 // touch, one CTA per (image, grid, tile) with the pairs binned to each tile on
 // the host, and writes its cells with the (-1)^(u+v) checkerboard that puts
-// the phase centre at pixel (N/2, N/2).
+// the phase centre at pixel (N/2, N/2).  The FFTs read their twiddles from
+// a shared-memory table.
 #include <math.h>
 #include <string.h>
 
@@ -145,17 +146,27 @@ __global__ void __launch_bounds__(kThreads) station_grid_kernel(
     }
 }
 
+// Twiddles exp(+2 pi i k / n), k < n / 2, into shared memory: sincospif of
+// 2k / n, the same argument (exact in FP32 for power-of-two n) as pos / half
+// of the butterfly that uses entry k.
+__device__ __forceinline__ void load_twiddles(float2 *tw, int n) {
+    for (int k = threadIdx.x; k < n / 2; k += blockDim.x) {
+        float s, c;
+        sincospif((float)(2 * k) / (float)n, &s, &c);
+        tw[k] = make_float2(c, s);
+    }
+}
+
 // In-place radix-2 FFT (exponent +) of n points held in bit-reversed order at
-// x[0], x[stride], ... by one warp.
-__device__ void warp_fft(float2 *x, int stride, int n, int lane) {
-    for (int half = 1; half < n; half <<= 1) {
+// x[0], x[stride], ... by one warp; tw as load_twiddles wrote it.
+__device__ void warp_fft(float2 *x, int stride, int n, int log2n, const float2 *tw, int lane) {
+    for (int lh = 0; lh < log2n; lh++) {
+        const int half = 1 << lh, tshift = log2n - 1 - lh;       // twiddle of pos: tw[pos * n / (2 half)]
         for (int b = lane; b < n / 2; b += 32) {
             const int pos = b & (half - 1);
             const int i0 = ((b - pos) << 1) + pos, i1 = i0 + half;
-            float s, c;
-            sincospif((float)pos / (float)half, &s, &c);
             const float2 a = x[i0 * stride];
-            const float2 t = cmulf(x[i1 * stride], make_float2(c, s));
+            const float2 t = cmulf(x[i1 * stride], tw[pos << tshift]);
             x[i0 * stride] = make_float2(a.x + t.x, a.y + t.y);
             x[i1 * stride] = make_float2(a.x - t.x, a.y - t.y);
         }
@@ -165,7 +176,10 @@ __device__ void warp_fft(float2 *x, int stride, int n, int lane) {
 
 // Row pass: one warp per row of a plane pair (re plane, im plane).
 __global__ void __launch_bounds__(kThreads) fft_rows_kernel(float *__restrict__ img, int N, int log2n) {
-    extern __shared__ float2 rows[];   // [16][N]
+    extern __shared__ float2 rows[];   // [16][N], then the N / 2 twiddles
+    float2 *tw = rows + (size_t)(kThreads / 32) * N;
+    load_twiddles(tw, N);
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int pair = blockIdx.x;       // image * 2 + h
     const int y = blockIdx.y * (kThreads / 32) + warp;
@@ -173,9 +187,25 @@ __global__ void __launch_bounds__(kThreads) fft_rows_kernel(float *__restrict__ 
     float *pre = img + ((size_t)(pair >> 1) * 4 + 2 * (pair & 1)) * N * N + (size_t)y * N;
     float *pim = pre + (size_t)N * N;
     float2 *x = rows + (size_t)warp * N;
-    for (int j = lane; j < N; j += 32) x[__brev(j) >> (32 - log2n)] = make_float2(pre[j], pim[j]);
+    // lane takes the N / 32 consecutive points j = E lane + k: their
+    // bit-reversed slots for one k are a permutation of 32 adjacent entries,
+    // so the stores are free of bank conflicts (j = lane + 32 k would put the
+    // lanes 64 bytes apart)
+    const int E = N / 32;
+    if (E >= 4) {
+        for (int k = 0; k < E; k += 4) {
+            const int j = E * lane + k;
+            const float4 r = *reinterpret_cast<const float4 *>(pre + j), m = *reinterpret_cast<const float4 *>(pim + j);
+            x[__brev(j) >> (32 - log2n)] = make_float2(r.x, m.x);
+            x[__brev(j + 1) >> (32 - log2n)] = make_float2(r.y, m.y);
+            x[__brev(j + 2) >> (32 - log2n)] = make_float2(r.z, m.z);
+            x[__brev(j + 3) >> (32 - log2n)] = make_float2(r.w, m.w);
+        }
+    } else {
+        for (int j = lane; j < N; j += 32) x[__brev(j) >> (32 - log2n)] = make_float2(pre[j], pim[j]);
+    }
     __syncwarp();
-    warp_fft(x, 1, N, lane);
+    warp_fft(x, 1, N, log2n, tw, lane);
     for (int j = lane; j < N; j += 32) {
         pre[j] = x[j].x;
         pim[j] = x[j].y;
@@ -185,7 +215,9 @@ __global__ void __launch_bounds__(kThreads) fft_rows_kernel(float *__restrict__ 
 // Column pass: a CTA loads 32 columns of a plane pair and each warp
 // transforms two of them.
 __global__ void __launch_bounds__(kThreads) fft_cols_kernel(float *__restrict__ img, int N, int log2n) {
-    extern __shared__ float2 tile[];   // [N][33]
+    extern __shared__ float2 tile[];   // [N][33], then the N / 2 twiddles
+    float2 *tw = tile + (size_t)N * 33;
+    load_twiddles(tw, N);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int pair = blockIdx.x;
     const int x0 = blockIdx.y * 32;
@@ -198,7 +230,7 @@ __global__ void __launch_bounds__(kThreads) fft_cols_kernel(float *__restrict__ 
                                                                                pim[(size_t)y * N + x0 + c]);
     }
     __syncthreads();
-    for (int c = warp; c < ncol; c += kThreads / 32) warp_fft(tile + c, 33, N, lane);
+    for (int c = warp; c < ncol; c += kThreads / 32) warp_fft(tile + c, 33, N, log2n, tw, lane);
     __syncthreads();
     for (int i = threadIdx.x; i < N * 32; i += kThreads) {
         const int y = i / 32, c = i % 32;
@@ -449,9 +481,9 @@ extern "C" hai_status hai_xfft_station_image(hai_ctx *ctx, const hai_vis_layout 
     HAI_CUDA_TRY(cudaGetLastError());
     const int rows_per_cta = kThreads / 32;
     fft_rows_kernel<<<dim3(images * 2, (N + rows_per_cta - 1) / rows_per_cta), kThreads,
-                      sizeof(float2) * rows_per_cta * N, st>>>(img, N, log2n);
+                      sizeof(float2) * (rows_per_cta * N + N / 2), st>>>(img, N, log2n);
     HAI_CUDA_TRY(cudaGetLastError());
-    const size_t tile = sizeof(float2) * (size_t)N * 33;
+    const size_t tile = sizeof(float2) * ((size_t)N * 33 + N / 2);
     HAI_CUDA_TRY(cudaFuncSetAttribute(fft_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile));
     fft_cols_kernel<<<dim3(images * 2, (N + 31) / 32), kThreads, tile, st>>>(img, N, log2n);
     prof_count(ctx, 3);
