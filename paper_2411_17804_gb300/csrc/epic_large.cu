@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(512) large_cols_kernel(const float2 *__restric
                                                          Batch bt, float *__restrict__ img, int add) {
     extern __shared__ float2 sm[];
     float2 *tw = sm;                                   // [N / 2]
-    float2 *F = sm + N / 2;                            // [P][kCols][N]
+    float2 *F = sm + N / 2;                            // [P][kCols][N + 1]: the pad spreads the columns over the banks
+    const int Fs = N + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const int cc = blockIdx.x, l0 = blockIdx.y * kCols;
     const int ly = threadIdx.x;
@@ -124,22 +125,22 @@ __global__ void __launch_bounds__(512) large_cols_kernel(const float2 *__restric
     for (int tt = 0; tt < bt.tb; tt++) {
         __syncthreads();
         // columns l0 .. l0+15 of the box rows, bit-reversed along y, zeros elsewhere
-        for (int i = threadIdx.x; i < P * kCols * N; i += blockDim.x) F[i] = make_float2(0.f, 0.f);
+        for (int i = threadIdx.x; i < P * kCols * Fs; i += blockDim.x) F[i] = make_float2(0.f, 0.f);
         __syncthreads();
         for (int i = threadIdx.x; i < P * box_h * kCols; i += blockDim.x) {
             const int j = i % kCols, y = (i / kCols) % box_h, pol = i / (kCols * box_h);
             const size_t f = ((size_t)cc * bt.tb + tt) * P + pol;
-            F[((size_t)pol * kCols + j) * N + (__brev(y) >> (32 - log2n))] = H[(f * box_h + y) * N + l0 + j];
+            F[((size_t)pol * kCols + j) * Fs + (__brev(y) >> (32 - log2n))] = H[(f * box_h + y) * N + l0 + j];
         }
         __syncthreads();
-        for (int line = warp; line < P * kCols; line += nwarp) warp_fft(F + (size_t)line * N, N, log2n, tw, lane);
+        for (int line = warp; line < P * kCols; line += nwarp) warp_fft(F + (size_t)line * Fs, N, log2n, tw, lane);
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < kCols; j++) {
-            const float2 a = F[(size_t)j * N + ly];
+            const float2 a = F[(size_t)j * Fs + ly];
             acc[0][j] = fmaf(a.x, a.x, fmaf(a.y, a.y, acc[0][j]));
             if (P == 2) {
-                const float2 b = F[((size_t)kCols + j) * N + ly];
+                const float2 b = F[((size_t)kCols + j) * Fs + ly];
                 acc[1][j] = fmaf(b.x, b.x, fmaf(b.y, b.y, acc[1][j]));
                 acc[2][j] = fmaf(a.x, b.x, fmaf(a.y, b.y, acc[2][j]));      // Re X conj(Y)
                 acc[3][j] = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc[3][j]));     // Im X conj(Y)
@@ -186,7 +187,7 @@ hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int
     // batch: up to 8 samples of as many channels as the scratch holds
     const int tb_max = (int)std::max<long long>(1, std::min<long long>(8, fields_cap / P));
     const size_t row_smem = sizeof(float2) * ((size_t)N / 2 + (size_t)(kRowThreads / 32) * N);
-    const size_t col_smem = sizeof(float2) * ((size_t)N / 2 + (size_t)P * kCols * N);
+    const size_t col_smem = sizeof(float2) * ((size_t)N / 2 + (size_t)P * kCols * (N + 1));
     HAI_CUDA_TRY(cudaFuncSetAttribute(large_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem));
     if (P == 2)
         HAI_CUDA_TRY(cudaFuncSetAttribute(large_cols_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem));

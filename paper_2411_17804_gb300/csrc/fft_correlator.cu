@@ -75,8 +75,19 @@ __global__ void __launch_bounds__(kThreads) fc_rows_kernel(const float *__restri
     const size_t NN = (size_t)N * N;
     const float *re = img + ((size_t)c * Q + (pr == 2 ? 2 : pr)) * NN + (size_t)y * N;
     const float *im = (pr == 2) ? re + NN : nullptr;
-    for (int x = lane; x < N; x += 32)
-        line[__brev(x) >> (32 - log2n)] = make_float2(__ldg(re + x), im ? __ldg(im + x) : 0.f);
+    // lane takes N / 32 consecutive points: their bit-reversed slots for one
+    // step are a permutation of 32 adjacent entries (no bank conflicts; points
+    // x = lane + 32 k would put the lanes N / 32 entries apart)
+    if (N >= 32) {
+        const int E = N / 32;
+        for (int k = 0; k < E; k++) {
+            const int x = E * lane + k;
+            line[__brev(x) >> (32 - log2n)] = make_float2(__ldg(re + x), im ? __ldg(im + x) : 0.f);
+        }
+    } else {
+        for (int x = lane; x < N; x += 32)
+            line[__brev(x) >> (32 - log2n)] = make_float2(__ldg(re + x), im ? __ldg(im + x) : 0.f);
+    }
     __syncwarp();
     warp_ifft(line, N, log2n, tw, lane);
     float2 *dst = out + ((size_t)c * P * P + out_plane(pr, P)) * NN + (size_t)y * N;
@@ -86,7 +97,8 @@ __global__ void __launch_bounds__(kThreads) fc_rows_kernel(const float *__restri
 __global__ void __launch_bounds__(kThreads) fc_cols_kernel(int N, int log2n, int P, float2 *__restrict__ out) {
     extern __shared__ float2 sm[];
     float2 *tw = sm;
-    float2 *F = sm + N / 2;                         // [kCols][N]
+    float2 *F = sm + N / 2;                         // [kCols][N + 1]: the pad spreads the columns over the banks
+    const int Fs = N + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     fill_twiddles(tw, N);
     const int np = (P == 2) ? 3 : 1;
@@ -96,17 +108,17 @@ __global__ void __launch_bounds__(kThreads) fc_cols_kernel(int N, int log2n, int
     float2 *plane = out + ((size_t)c * P * P + out_plane(pr, P)) * NN;
     for (int i = threadIdx.x; i < N * kCols; i += kThreads) {
         const int j = i % kCols, y = i / kCols;
-        F[(size_t)j * N + (__brev(y) >> (32 - log2n))] = plane[(size_t)y * N + x0 + j];
+        F[(size_t)j * Fs + (__brev(y) >> (32 - log2n))] = plane[(size_t)y * N + x0 + j];
     }
     __syncthreads();
-    warp_ifft(F + (size_t)warp * N, N, log2n, tw, lane);
+    warp_ifft(F + (size_t)warp * Fs, N, log2n, tw, lane);
     __syncthreads();
     const float inv = 1.0f / (float)NN;
     float2 *mirror = (pr == 2) ? out + ((size_t)c * P * P + 2) * NN : nullptr;   // YX
     for (int i = threadIdx.x; i < N * kCols; i += kThreads) {
         const int j = i % kCols, dy = i / kCols, dx = x0 + j;
         const float s = ((dx + dy) & 1) ? -inv : inv;
-        const float2 v = F[(size_t)j * N + dy];
+        const float2 v = F[(size_t)j * Fs + dy];
         const float2 r = make_float2(v.x * s, v.y * s);
         plane[(size_t)dy * N + dx] = r;
         if (mirror) mirror[(size_t)((N - dy) & (N - 1)) * N + ((N - dx) & (N - 1))] = make_float2(r.x, -r.y);
@@ -131,7 +143,7 @@ extern "C" hai_status hai_fft_correlate(hai_ctx *ctx, const float *img, int C, i
     HAI_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     const int np = (P == 2) ? 3 : 1;
-    const size_t smem = sizeof(float2) * ((size_t)N / 2 + (size_t)kCols * N);   // both passes
+    const size_t smem = sizeof(float2) * ((size_t)N / 2 + (size_t)kCols * (N + 1));   // both passes
     HAI_CUDA_TRY(cudaFuncSetAttribute(fc_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     HAI_CUDA_TRY(cudaFuncSetAttribute(fc_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     float2 *out = reinterpret_cast<float2 *>(grid);
