@@ -148,6 +148,23 @@ hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *layout, const int8_t *
                           int C, int T, hai_precision prec, float *img, int accumulate,
                           void *stream);
 
+/* hai_epic_image on HOST buffers, the channels streamed through the GPU in
+ * chunks so that the copies overlap the imaging: chunk k is imaged on
+ * `stream` while the context's copy stream moves chunk k+1's voltages in and
+ * chunk k-1's images out (two device staging buffers of each, owned by the
+ * context, grown on first use).
+ *   volt   host int8 [C][T][P][N_e][2]; img host float [C][Q][N][N]
+ *          (overwritten, or added to with accumulate = 1: then the host
+ *          image is copied in as well).  Page-locked (pinned) host memory is
+ *          needed for the copies to overlap; pageable memory works but the
+ *          copies then serialise.
+ *   chunk  channels per chunk, 1..C (0: C/4 rounded up)
+ * Same precisions, limits and errors as hai_epic_image.  Asynchronous like
+ * it: synchronise `stream` before reading img.  Calls on one context must not
+ * run concurrently on different streams (they share the staging buffers). */
+hai_status hai_epic_image_host(hai_ctx *ctx, const hai_layout *layout, const int8_t *volt, int C, int T,
+                               hai_precision prec, float *img, int accumulate, int chunk, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Batched EPIC over an array of stations of uneven size (the heterogeneous
  * stations the paper's hierarchical arrays allow, Section 2): the EPIC image

@@ -109,6 +109,8 @@ extern "C" void hai_destroy(hai_ctx *ctx) {
     cudaFree(ctx->d_status);
     cudaFree(ctx->d_corr_ws);
     for (void *d : ctx->d_dft) cudaFree(d);
+    cudaFree(ctx->d_stage);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     delete ctx;
 }
 

@@ -27,6 +27,11 @@ struct hai_ctx {
     int capturing = 0;                  // a plan is capturing a graph: no profiling events
     void *d_corr_ws = nullptr;          // correlator: fp16 operand images of a batch of channels
     size_t corr_ws_bytes = 0;
+    // hai_epic_image_host: copy stream and device staging (two voltage and two
+    // image chunks), created / grown on first use
+    cudaStream_t copy_stream = nullptr;
+    void *d_stage = nullptr;
+    size_t stage_bytes = 0;
 };
 
 // Correlator workspace reserved with the context.

@@ -62,6 +62,7 @@ def _declare(L):
     L.hai_layout_destroy.restype = None
     L.hai_layout_box.argtypes = [_vp, ctypes.POINTER(_int)]
     L.hai_epic_image.argtypes = [_vp, _vp, _vp, _int, _int, _int, _vp, _int, _vp]
+    L.hai_epic_image_host.argtypes = [_vp, _vp, _vp, _int, _int, _int, _vp, _int, _int, _vp]
     L.hai_correlate.argtypes = [_vp, _vp, _int, _int, _int, _int, _vp, _int, _vp]
     L.hai_xfft_image.argtypes = [_vp, _vp, _vp, _int, _vp, _int, _vp]
     L.hai_fft_correlate.argtypes = [_vp, _vp, _int, _int, _int, _vp, _vp]
@@ -117,6 +118,19 @@ def _stream(stream):
         import torch
         return torch.cuda.current_stream().cuda_stream
     return getattr(stream, "cuda_stream", stream)
+
+
+def _host_ptr(t, dtype, name, numel=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+        raise ValueError(f"{name} must be a host (CPU) tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return t.data_ptr()
 
 
 def _dev_ptr(t, dtype, name, numel=None):
@@ -212,6 +226,17 @@ def hai_epic_image(ctx, layout: Layout, volt, C: int, T: int, prec: int, img, ac
     ip = _dev_ptr(img, torch.float32, "img", C * layout.n_planes * n * n) if C > 0 else 0
     _check(load().hai_epic_image(ctx, layout.handle, vp, C, T, prec, ip, accumulate, _stream(stream)),
            "hai_epic_image")
+
+
+def hai_epic_image_host(ctx, layout: Layout, volt, C: int, T: int, prec: int, img, accumulate: int = 0,
+                        chunk: int = 0, stream=None):
+    """hai_epic_image on host tensors (pin them for the copies to overlap)."""
+    import torch
+    P, ne, n = layout.n_pol, layout.n_elem, layout.grid_n
+    vp = _host_ptr(volt, torch.int8, "volt", C * T * P * ne * 2) if C * T > 0 else 0
+    ip = _host_ptr(img, torch.float32, "img", C * layout.n_planes * n * n) if C > 0 else 0
+    _check(load().hai_epic_image_host(ctx, layout.handle, vp, C, T, prec, ip, accumulate, chunk, _stream(stream)),
+           "hai_epic_image_host")
 
 
 def hai_correlate(ctx, volt, C: int, T: int, N: int, P: int, vis, accumulate: int = 0, stream=None):

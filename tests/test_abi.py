@@ -54,6 +54,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.hai_station_epic_layout_create(None, None, 0, None, None) == 1
     assert lib.hai_xbf_layout_create(None, None, 0, 1, 1, None) == 1
     assert lib.hai_xbf_station_image(None, None, None, 1, None, 0, None) == 1
+    assert lib.hai_epic_image_host(None, None, None, 1, 1, 0, None, 0, 0, None) == 1
 
 
 def test_fault_injection_on_host(lib, monkeypatch):
