@@ -158,7 +158,8 @@ hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *layout, const int8_t *
  *          image is copied in as well).  Page-locked (pinned) host memory is
  *          needed for the copies to overlap; pageable memory works but the
  *          copies then serialise.
- *   chunk  channels per chunk, 1..C (0: C/4 rounded up)
+ *   chunk  channels per chunk, 1..C (0: C/4 rounded up); the first two
+ *          chunks take a quarter and a half of it, to start imaging early
  * Same precisions, limits and errors as hai_epic_image.  Asynchronous like
  * it: synchronise `stream` before reading img.  Calls on one context must not
  * run concurrently on different streams (they share the staging buffers). */

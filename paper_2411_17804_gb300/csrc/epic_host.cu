@@ -4,7 +4,8 @@
 //
 // The channels of a cadence are independent, so chunk k is imaged by
 // hai_epic_image on the caller's stream while the context's copy stream moves
-// chunk k + 1's voltages in and chunk k - 1's images out.  Two voltage and
+// chunk k + 1's voltages in and chunk k - 1's images out (the first two chunks
+// are shorter, so the imaging starts early).  Two voltage and
 // two image staging buffers alternate between chunks; events order each
 // buffer's reuse:
 //   copy stream:    H2D(0) | H2D(1) D2H(0) | H2D(2) D2H(1) | ...
@@ -14,6 +15,7 @@
 // asynchronous as hai_epic_image and the caller synchronises its stream
 // before reading img.
 #include <algorithm>
+#include <vector>
 
 #include "hai_internal.h"
 
@@ -73,9 +75,15 @@ extern "C" hai_status hai_epic_image_host(hai_ctx *ctx, const hai_layout *L, con
     // the copies follow whatever the caller queued before this call
     HAI_CUDA_TRY(cudaEventRecord(ev.start, cs));
     HAI_CUDA_TRY(cudaStreamWaitEvent(xs, ev.start, 0));
-    const int nchunk = (C + chunk - 1) / chunk;
+    // chunk boundaries: the first two chunks are a quarter and a half of
+    // `chunk`, so the imaging starts after a short first copy (the pipeline fill)
+    std::vector<int> c0s{0};
+    for (int step : {std::max(1, chunk / 4), std::max(1, chunk / 2)})
+        if (c0s.back() < C) c0s.push_back(std::min(C, c0s.back() + step));
+    while (c0s.back() < C) c0s.push_back(std::min(C, c0s.back() + chunk));
+    const int nchunk = (int)c0s.size() - 1;
     auto h2d = [&](int k) -> cudaError_t {
-        const int b = k & 1, c0 = k * chunk, cc = std::min(chunk, C - c0);
+        const int b = k & 1, c0 = c0s[k], cc = c0s[k + 1] - c0s[k];
         cudaError_t e = cudaSuccess;
         if (k >= 2) e = cudaStreamWaitEvent(xs, ev.done[b], 0);   // image(k - 2) has read vin[b]
         if (e == cudaSuccess && T > 0)
@@ -88,7 +96,7 @@ extern "C" hai_status hai_epic_image_host(hai_ctx *ctx, const hai_layout *L, con
     };
     HAI_CUDA_TRY(h2d(0));
     for (int k = 0; k < nchunk; k++) {
-        const int b = k & 1, c0 = k * chunk, cc = std::min(chunk, C - c0);
+        const int b = k & 1, c0 = c0s[k], cc = c0s[k + 1] - c0s[k];
         if (k + 1 < nchunk) HAI_CUDA_TRY(h2d(k + 1));
         // D2H(k - 2) of idev[b] precedes H2D(k) on the copy stream, so in[b] also
         // means idev[b] is free
