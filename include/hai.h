@@ -227,8 +227,9 @@ hai_status hai_plan_schedule(const hai_plan *plan, int *n_class, int *grid_n, in
  * below 2^24) and the blocks in int32.  V^{qp}_{ba} = conj(V^{pq}_{ab}) gives
  * the upper triangle.  HAI_ERR_OVERFLOW_RISK if T > 65535 (|V| could exceed
  * 2^31 - 1); HAI_ERR_UNSUPPORTED if N > 65535.  vis must be 8-byte aligned.
- * The fp16 operands are staged in the context's 512 MB workspace, so calls
- * on one context must not run concurrently on different streams. */
+ * The fp16 operands are staged in the context's 512 MB workspace (allocated
+ * by the first call), so calls on one context must not run concurrently on
+ * different streams. */
 hai_status hai_correlate(hai_ctx *ctx, const int8_t *volt, int C, int T, int N, int P,
                          int32_t *vis, int accumulate, void *stream);
 

@@ -330,7 +330,7 @@ extern "C" hai_status hai_correlate(hai_ctx *ctx, const int8_t *volt, int C, int
     g.nbj = (N + g.E - 1) / g.E;
     g.nimg = std::max((g.nbj + 1) & ~1, 2 * g.nbi);
     const size_t chunk_bytes = (size_t)kKbPerChunk * g.nimg * kImg;   // one channel, one 512-sample block
-    if (chunk_bytes > ctx->corr_ws_bytes)
+    if (chunk_bytes > kCorrWorkspaceBytes)
         return hai_fail(HAI_ERR_UNSUPPORTED, "hai_correlate: N too large for the operand workspace");
     if (C == 0) return HAI_OK;
     if (!vis || (T > 0 && !volt)) return hai_fail(HAI_ERR_INVALID_ARG, "hai_correlate: NULL buffer");
@@ -343,6 +343,10 @@ extern "C" hai_status hai_correlate(hai_ctx *ctx, const int8_t *volt, int C, int
         return HAI_OK;
     }
     if (((uintptr_t)vis) & 7) return hai_fail(HAI_ERR_INVALID_ARG, "hai_correlate: vis must be 8-byte aligned");
+    if (!ctx->d_corr_ws) {
+        HAI_CUDA_TRY(cudaMalloc(&ctx->d_corr_ws, kCorrWorkspaceBytes));
+        ctx->corr_ws_bytes = kCorrWorkspaceBytes;
+    }
     int tpc = 0;
     for (int I = 0; I < g.nbi; I++) {
         const int amax = std::min(N - 1, (I + 1) * g.em - 1);

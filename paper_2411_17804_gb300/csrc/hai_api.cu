@@ -77,18 +77,14 @@ extern "C" hai_status hai_create(int device, hai_ctx **out) {
         e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_corr_ws, kCorrWorkspaceBytes);
     if (e != cudaSuccess) {
         if (c->d_status) cudaFree(c->d_status);
-        if (c->d_corr_ws) cudaFree(c->d_corr_ws);
         delete c;
         return hai_cuda_fail(e, "hai_create");
     }
-    c->corr_ws_bytes = kCorrWorkspaceBytes;
     hai_status s = epic_fp32_init_tables();
     if (s != HAI_OK) {
         cudaFree(c->d_status);
-        cudaFree(c->d_corr_ws);
         delete c;
         return s;
     }

@@ -25,8 +25,8 @@ struct hai_ctx {
     long long prof_launches = 0;        // all kernels launched
     void *d_dft[3] = {nullptr, nullptr, nullptr};   // tensor-core DFT operands, N = 32, 64, 128
     int capturing = 0;                  // a plan is capturing a graph: no profiling events
-    void *d_corr_ws = nullptr;          // correlator: fp16 operand images of a batch of channels
-    size_t corr_ws_bytes = 0;
+    void *d_corr_ws = nullptr;          // correlator: fp16 operand images of a batch of channels,
+    size_t corr_ws_bytes = 0;           // allocated on the first hai_correlate call
     // hai_epic_image_host: copy stream and device staging (two voltage and two
     // image chunks), created / grown on first use
     cudaStream_t copy_stream = nullptr;
@@ -34,7 +34,7 @@ struct hai_ctx {
     size_t stage_bytes = 0;
 };
 
-// Correlator workspace reserved with the context.
+// Correlator workspace (allocated on first use).
 constexpr size_t kCorrWorkspaceBytes = (size_t)512 << 20;
 
 // Profiling helpers: prof_begin returns the pair index or -1.
