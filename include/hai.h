@@ -244,7 +244,12 @@ hai_status hai_correlate(hai_ctx *ctx, const int8_t *volt, int C, int T, int N, 
  *   vis   device int32 [C][N_e(N_e+1)/2][P][P][2] as written by hai_correlate
  *   img   device float [C][Q][N][N]; overwritten or added to (accumulate)
  * The pair (b, a) is the Hermitian mirror of the stored (a, b).  FP32 grid and
- * FFT; grid sums use atomics, so the last bits may vary between runs. */
+ * FFT; each grid cell sums its contributions in a fixed order, so results are
+ * deterministic.  The first call for a layout builds on the host, and copies
+ * to the device (synchronously), the per-cell list of K_ab contributions
+ * (layout-only data, freed with the layout); the channels are staged through
+ * the context's operand workspace, so calls on one context must not run
+ * concurrently on different streams.  N = 16, 32 or 64. */
 hai_status hai_xfft_image(hai_ctx *ctx, const hai_layout *layout, const int32_t *vis, int C,
                           float *img, int accumulate, void *stream);
 

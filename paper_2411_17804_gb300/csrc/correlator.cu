@@ -343,10 +343,8 @@ extern "C" hai_status hai_correlate(hai_ctx *ctx, const int8_t *volt, int C, int
         return HAI_OK;
     }
     if (((uintptr_t)vis) & 7) return hai_fail(HAI_ERR_INVALID_ARG, "hai_correlate: vis must be 8-byte aligned");
-    if (!ctx->d_corr_ws) {
-        HAI_CUDA_TRY(cudaMalloc(&ctx->d_corr_ws, kCorrWorkspaceBytes));
-        ctx->corr_ws_bytes = kCorrWorkspaceBytes;
-    }
+    const hai_status wst = hai_workspace(ctx);
+    if (wst != HAI_OK) return wst;
     int tpc = 0;
     for (int I = 0; I < g.nbi; I++) {
         const int amax = std::min(N - 1, (I + 1) * g.em - 1);

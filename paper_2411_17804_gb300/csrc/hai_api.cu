@@ -92,6 +92,13 @@ extern "C" hai_status hai_create(int device, hai_ctx **out) {
     return HAI_OK;
 }
 
+hai_status hai_workspace(hai_ctx *ctx) {
+    if (ctx->d_corr_ws) return HAI_OK;
+    HAI_CUDA_TRY(cudaMalloc(&ctx->d_corr_ws, kCorrWorkspaceBytes));
+    ctx->corr_ws_bytes = kCorrWorkspaceBytes;
+    return HAI_OK;
+}
+
 static void prof_release(hai_ctx *ctx) {
     for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
     ctx->prof_ev.clear();
@@ -190,6 +197,9 @@ static void layout_free(hai_layout *L) {
     cudaFree(L->d_tc_station);
     cudaFree(L->d_large_scratch);
     cudaFree(L->d_big);
+    cudaFree(L->d_xcell);
+    cudaFree(L->d_xent);
+    cudaFree(L->d_xk);
     delete L;
 }
 

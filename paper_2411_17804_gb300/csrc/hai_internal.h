@@ -5,6 +5,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -34,8 +35,10 @@ struct hai_ctx {
     size_t stage_bytes = 0;
 };
 
-// Correlator workspace (allocated on first use).
+// Operand workspace of the correlator and the XFFT (allocated on first use by
+// hai_workspace; calls that use it on one context run on one stream).
 constexpr size_t kCorrWorkspaceBytes = (size_t)512 << 20;
+hai_status hai_workspace(hai_ctx *ctx);
 
 // Profiling helpers: prof_begin returns the pair index or -1.
 int prof_begin(hai_ctx *ctx, cudaStream_t st);
@@ -75,6 +78,11 @@ struct hai_layout {
     void *d_big = nullptr;
     void *big_b1 = nullptr, *big_b2 = nullptr, *big_a1 = nullptr, *big_a2 = nullptr;
     long long big_batch = 0;
+    // XFFT: per grid cell the (pair, K_ab value, mirror) entries landing there,
+    // built on the first hai_xfft_image call (layout-only data)
+    mutable int32_t *d_xcell = nullptr, *d_xent = nullptr;
+    mutable float2 *d_xk = nullptr;
+    mutable std::mutex xfft_mu;
 };
 
 // ---------------------------------------------------------------- errors

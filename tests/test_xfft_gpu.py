@@ -73,3 +73,22 @@ def test_xfft_accumulate(hai, ctx):
     img = torch.tensor(first, device="cuda")
     again, _ = xfft_gpu(hai, ctx, anchors, taps, n, volt, accumulate=1, img=img)
     assert rel_err_planes(again, 2 * first).max() < FP32_TOL
+
+
+def test_xfft_is_deterministic(hai, ctx):
+    """Each grid cell sums its contributions in a fixed order: repeated calls
+    agree to the bit (the layout's gridding list is built by the first)."""
+    cfg = I.SKA_LOW_STATION_256
+    pos, anchors, taps = station(cfg)
+    volt = I.station_voltages(cfg, pos, n_chan=3, n_time=64)
+    n = cfg.grid_n
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, 2)
+    vis = torch.empty((3, cfg.n_elem * (cfg.n_elem + 1) // 2, 2, 2, 2), dtype=torch.int32, device="cuda")
+    hai.hai_correlate(ctx, volt.cuda(), 3, 64, cfg.n_elem, 2, vis, 0)
+    a = torch.empty((3, 4, n, n), device="cuda")
+    b = torch.full((3, 4, n, n), float("nan"), device="cuda")
+    hai.hai_xfft_image(ctx, lay, vis, 3, a)
+    hai.hai_xfft_image(ctx, lay, vis, 3, b)
+    hai.hai_sync(ctx)
+    assert torch.equal(a, b)
+    hai.hai_layout_destroy(lay)
