@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--no-components", action="store_true")
     ap.add_argument("--channels", type=int, default=0,
                     help="image only this many channels (small cases for profiling)")
-    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "bf", "xbf", "sxfft", "fc", "big", "big16"], default=None,
+    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "xfft", "bf", "xbf", "sxfft", "fc", "big", "big16"], default=None,
                     help="run one small case of a kernel twice, untimed, and exit (for ncu captures)")
     return ap.parse_args()
 
@@ -624,6 +624,20 @@ def run_case(name):
             vis = torch.empty((C, N * (N + 1) // 2, 2, 2, 2), dtype=torch.int32, device="cuda")
             for _ in range(2):
                 hai.hai_correlate(ctx, v, C, cfg.n_time, N, 2, vis, 0)
+    elif name == "xfft":                  # correlator + XFFT of the 64-channel SKA-low cadence
+        cfg = I.SKA_LOW_STATION_256
+        pos = I.station_layout(cfg)
+        an, tp = I.station_kernel(cfg, pos)
+        C, N = cfg.n_chan, cfg.n_elem
+        v = I.station_voltages(cfg, pos, device="cuda", n_chan=C)
+        lay = hai.hai_layout_create(ctx, an, tp, cfg.grid_n, 2)
+        vis = torch.empty((C, N * (N + 1) // 2, 2, 2, 2), dtype=torch.int32, device="cuda")
+        img = torch.empty((C, 4, cfg.grid_n, cfg.grid_n), device="cuda")
+        for _ in range(2):
+            hai.hai_correlate(ctx, v, C, cfg.n_time, N, 2, vis, 0)
+            hai.hai_xfft_image(ctx, lay, vis, C, img, 0)
+        torch.cuda.synchronize()
+        hai.hai_layout_destroy(lay)
     elif name == "tc128":                 # a 700-element station of the uneven array, N = 128
         sc = I.uneven_station(I.UnevenConfig(), 0, 700)
         pos = I.station_layout(sc)
