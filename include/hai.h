@@ -247,7 +247,8 @@ hai_status hai_correlate(hai_ctx *ctx, const int8_t *volt, int C, int T, int N, 
  * FFT; each grid cell sums its contributions in a fixed order, so results are
  * deterministic.  The first call for a layout builds on the host, and copies
  * to the device (synchronously), the per-cell list of K_ab contributions
- * (layout-only data, freed with the layout); the channels are staged through
+ * (layout-only data, freed with the layout; HAI_ERR_UNSUPPORTED beyond 2e8
+ * entries, i.e. N_e(N_e+1)(2K-1)^2 > 2e8); the channels are staged through
  * the context's operand workspace, so calls on one context must not run
  * concurrently on different streams.  N = 16, 32 or 64. */
 hai_status hai_xfft_image(hai_ctx *ctx, const hai_layout *layout, const int32_t *vis, int C,

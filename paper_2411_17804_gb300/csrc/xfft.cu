@@ -173,6 +173,10 @@ static hai_status ensure_table(const hai_layout *L) {
     std::lock_guard<std::mutex> lock(L->xfft_mu);
     if (L->d_xcell) return HAI_OK;
     const int N = L->grid_n, K = L->ksize, ne = L->n_elem;
+    // at most 2 (2K-1)^2 entries per stored pair, 12 bytes each on the device
+    const double max_ent = (double)ne * (ne + 1) / 2 * 2.0 * (2 * K - 1) * (2 * K - 1);
+    if (max_ent > 2.0e8)
+        return hai_fail(HAI_ERR_UNSUPPORTED, "hai_xfft_image: the layout's gridding list would exceed 2e8 entries");
     const float2 *taps = reinterpret_cast<const float2 *>(L->h_taps.data());   // [ne][K][K], as given
     const int32_t *anc = L->h_anchors.data();
     struct Ent {
