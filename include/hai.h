@@ -88,6 +88,20 @@ void hai_destroy(hai_ctx *ctx);
  * call (the status word is cleared). */
 hai_status hai_sync(hai_ctx *ctx, void *stream);
 
+/* Self-check of the bounded device waits (no counterpart in the paper: it
+ * tests the library's failure detection).  Every pipelined kernel waits on
+ * mbarrier phases through one bounded wait that, when a phase never
+ * completes, gives up, sets HAI_DEV_TIMEOUT in the context's status word and
+ * lets the kernel end instead of hanging.  This call launches one CTA on
+ * `stream` that waits on a phase nothing will complete (no copy or MMA is in
+ * flight), with a limit of `limit_cycles` SM cycles in [1024, 2^24] (else
+ * HAI_ERR_INVALID_ARG): the wait gives up within microseconds, the next
+ * hai_sync returns HAI_ERR_TIMEOUT and clears the word, and the context stays
+ * usable.  hai_check_device_wait_result (after a sync) returns 1 in *gave_up
+ * if the wait gave up, 0 if it saw the phase complete. */
+hai_status hai_check_device_wait(hai_ctx *ctx, long long limit_cycles, void *stream);
+hai_status hai_check_device_wait_result(hai_ctx *ctx, int *gave_up);
+
 /* Profiling.  While enabled, every compute call records a pair of CUDA events
  * on the caller's stream around its dominant kernel (the first kernels it
  * launches are the one named in the call's description) and counts every
@@ -161,8 +175,10 @@ hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *layout, const int8_t *
  *   chunk  channels per chunk, 1..C (0: C/4 rounded up); the first two
  *          chunks take a quarter and a half of it, to start imaging early
  * Same precisions, limits and errors as hai_epic_image.  Asynchronous like
- * it: synchronise `stream` before reading img.  Calls on one context must not
- * run concurrently on different streams (they share the staging buffers). */
+ * it: synchronise `stream` before reading img.  The staging buffers belong to
+ * the context: calls issued one after another (from one host thread) are
+ * ordered through the context's copy stream, even on different caller
+ * streams, but calls on one context from two host threads at once race. */
 hai_status hai_epic_image_host(hai_ctx *ctx, const hai_layout *layout, const int8_t *volt, int C, int T,
                                hai_precision prec, float *img, int accumulate, int chunk, void *stream);
 
@@ -433,7 +449,8 @@ hai_status hai_xbf_station_image(hai_ctx *ctx, const hai_xbf_layout *layout, con
  * before any stream capture.  Every call shares the array and a static host
  * staging buffer: calls that overlap on the GPU, or run from two host
  * threads at once, race.  The table is copied in on `stream` from pageable
- * host memory.  No context is needed. */
+ * host memory, so the call returns only once the runtime has staged that
+ * copy (the host blocks for it).  No context is needed. */
 hai_status hai_epic_image_fp32_static(int device, const hai_layout_desc *desc, const int8_t *volt,
                                       int C, int T, float *img, int accumulate, void *stream);
 

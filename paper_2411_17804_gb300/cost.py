@@ -48,12 +48,17 @@ ARRAYS = {
     "LAMBDA-I": ArrayParams("LAMBDA-I", 2.0, 3.9e6, 4, 17.5, 256, 1.0),
     "SKA-low-core": ArrayParams("SKA-low-core", 2.0, 5.25e2, 256, 17.5, 256, 1.0),
     "SKA-low": ArrayParams("SKA-low", 2.0, 3.5e4, 512, 17.5, 256, 1.0),
-    # D_e = lambda for CASPA: the station filling factor printed beside it
-    # (0.996 = 65 (1 / 8.08)^2) and the station-level EPIC / XFFT crossover
-    # near 5 ms (Section 6) both need it; the D_e / lambda column says 0.5
-    "CASPA": ArrayParams("CASPA", 0.25, 4.6e4, 3, 8.08, 65, 1.0),
+    # CASPA as printed (D_e / lambda = 0.5).  The station filling factor printed
+    # beside it (0.996 = 65 (1 / 8.08)^2) and the station-level EPIC / XFFT
+    # crossover of a few ms (Section 6, Table 3) both need D_e = lambda, which
+    # CASPA_DE1 holds: Table 1 is inconsistent with itself on this row.
+    "CASPA": ArrayParams("CASPA", 0.25, 4.6e4, 3, 8.08, 65, 0.5),
     "FarView-core": ArrayParams("FarView-core", 10.0, 6.77e2, 81, 38.5, 625, 1.0),
 }
+
+
+# The reading of CASPA that the printed f_s and Section 6 imply (D_e = lambda).
+CASPA_DE1 = ArrayParams("CASPA (D_e = lambda)", 0.25, 4.6e4, 3, 8.08, 65, 1.0)
 
 
 @dataclass(frozen=True)
@@ -110,9 +115,10 @@ def level_args(a: ArrayParams, level: str) -> tuple[int, float]:
     raise ValueError(level)
 
 
-def ranking(array: str, level: str, t_acc: float) -> list[tuple[str, float]]:
-    """Architectures of one stage sorted by cost density (cheapest first)."""
-    n, ratio = level_args(ARRAYS[array], level)
+def ranking(array, level: str, t_acc: float) -> list[tuple[str, float]]:
+    """Architectures of one stage sorted by cost density (cheapest first);
+    `array` is a Table 1 name or an ArrayParams."""
+    n, ratio = level_args(ARRAYS[array] if isinstance(array, str) else array, level)
     return sorted(((x, density(x, n, ratio, t_acc)) for x in ARCHS), key=lambda p: p[1])
 
 

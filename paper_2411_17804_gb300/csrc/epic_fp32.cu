@@ -247,7 +247,7 @@ hai_status launch_n(const hai_layout *L, const int8_t *volt, int C, int T, float
     if (smem > (size_t)L->ctx->smem_optin)
         return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp32: shared memory need exceeds the device limit");
     auto kern = epic_fp32_kernel<N, P>;
-    HAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HAI_CUDA_TRY(hai_allow_dyn_smem(kern, L->ctx->smem_optin));
     const EpicSplit sp = epic_make_split(C, T, epic_fp32_target_ctas(L->ctx, N));
     if (!sp.direct && (size_t)sp.n_cta * 2 > L->partial_slots)
         return hai_fail(HAI_ERR_INVALID_ARG, "epic fp32: partial buffer too small");
@@ -364,7 +364,7 @@ hai_status launch_static(float *scratch, int ne, int box_w, int box_h, int ncell
     if (smem > (size_t)smem_optin)
         return hai_fail(HAI_ERR_UNSUPPORTED, "hai_epic_image_fp32_static: shared memory need exceeds the device limit");
     auto kern = epic_fp32_kernel<N, P>;
-    HAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HAI_CUDA_TRY(hai_allow_dyn_smem(kern, smem_optin));
     const EpicSplit sp = epic_make_split(C, T, std::min(sms, kStaticCtas));
     const int32_t *cstart = reinterpret_cast<const int32_t *>(scratch);
     const int32_t *celem = cstart + (ncell + 1);

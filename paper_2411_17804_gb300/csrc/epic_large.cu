@@ -188,11 +188,11 @@ hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int
     const int tb_max = (int)std::max<long long>(1, std::min<long long>(8, fields_cap / P));
     const size_t row_smem = sizeof(float2) * ((size_t)N / 2 + (size_t)(kRowThreads / 32) * N);
     const size_t col_smem = sizeof(float2) * ((size_t)N / 2 + (size_t)P * kCols * (N + 1));
-    HAI_CUDA_TRY(cudaFuncSetAttribute(large_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem));
+    HAI_CUDA_TRY(hai_allow_dyn_smem(large_rows_kernel, L->ctx->smem_optin));
     if (P == 2)
-        HAI_CUDA_TRY(cudaFuncSetAttribute(large_cols_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem));
+        HAI_CUDA_TRY(hai_allow_dyn_smem(large_cols_kernel<2>, L->ctx->smem_optin));
     else
-        HAI_CUDA_TRY(cudaFuncSetAttribute(large_cols_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem));
+        HAI_CUDA_TRY(hai_allow_dyn_smem(large_cols_kernel<1>, L->ctx->smem_optin));
     float2 *H = static_cast<float2 *>(L->d_large_scratch);
     const int pidx = prof_begin(L->ctx, st);
     for (int t0 = 0; t0 < T; t0 += tb_max) {

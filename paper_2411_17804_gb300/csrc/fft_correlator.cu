@@ -144,8 +144,8 @@ extern "C" hai_status hai_fft_correlate(hai_ctx *ctx, const float *img, int C, i
     cudaStream_t st = (cudaStream_t)stream;
     const int np = (P == 2) ? 3 : 1;
     const size_t smem = sizeof(float2) * ((size_t)N / 2 + (size_t)kCols * (N + 1));   // both passes
-    HAI_CUDA_TRY(cudaFuncSetAttribute(fc_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    HAI_CUDA_TRY(cudaFuncSetAttribute(fc_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HAI_CUDA_TRY(hai_allow_dyn_smem(fc_rows_kernel, ctx->smem_optin));
+    HAI_CUDA_TRY(hai_allow_dyn_smem(fc_cols_kernel, ctx->smem_optin));
     float2 *out = reinterpret_cast<float2 *>(grid);
     const int pidx = prof_begin(ctx, st);
     fc_rows_kernel<<<dim3(C * np, (N + kThreads / 32 - 1) / (kThreads / 32)), kThreads, smem, st>>>(img, N, log2n,

@@ -9,6 +9,7 @@
 
 #include "epic_tc.cuh"
 #include "hai_internal.h"
+#include "tc.cuh"
 
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_last_error;
@@ -75,8 +76,9 @@ extern "C" hai_status hai_create(int device, hai_ctx **out) {
     cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
+    // word 0: the status word; word 1: outcome of the wait self-check
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 2 * sizeof(unsigned));
     if (e != cudaSuccess) {
         if (c->d_status) cudaFree(c->d_status);
         delete c;
@@ -179,6 +181,42 @@ extern "C" hai_status hai_sync(hai_ctx *ctx, void *stream) {
         if (st & HAI_DEV_TIMEOUT) return hai_fail(HAI_ERR_TIMEOUT, "a bounded device wait gave up");
         return hai_fail(HAI_ERR_CUDA, "a device-side bounds check fired");
     }
+    return HAI_OK;
+}
+
+// ------------------------------------------------------------------ wait self-check
+// One CTA: thread 0 sets up an mbarrier expecting one arrival that never
+// comes (no copy or MMA is issued) and waits on its first phase through the
+// same bounded wait every pipelined kernel uses, with a short limit.  The wait
+// gives up, flags HAI_DEV_TIMEOUT in the status word and the kernel returns.
+__global__ void wait_selfcheck_kernel(unsigned *status, long long limit, int *gave_up) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *gave_up = tc::mbar_wait(&bar, 0u, status, limit) ? 0 : 1;
+    __syncthreads();
+}
+
+extern "C" hai_status hai_check_device_wait(hai_ctx *ctx, long long limit_cycles, void *stream) {
+    if (!ctx) return hai_fail(HAI_ERR_INVALID_ARG, "hai_check_device_wait: ctx is NULL");
+    if (limit_cycles < 1024 || limit_cycles > (1ll << 24))
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_check_device_wait: limit must be in [1024, 2^24] cycles");
+    HAI_CUDA_TRY(cudaSetDevice(ctx->device));
+    // the wait's outcome goes to the word after the status word
+    wait_selfcheck_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(ctx->d_status, limit_cycles,
+                                                              reinterpret_cast<int *>(ctx->d_status + 1));
+    prof_count(ctx, 1);
+    HAI_CUDA_TRY(cudaGetLastError());
+    return HAI_OK;
+}
+
+extern "C" hai_status hai_check_device_wait_result(hai_ctx *ctx, int *gave_up) {
+    if (!ctx || !gave_up) return hai_fail(HAI_ERR_INVALID_ARG, "hai_check_device_wait_result: NULL argument");
+    HAI_CUDA_TRY(cudaSetDevice(ctx->device));
+    HAI_CUDA_TRY(cudaMemcpy(gave_up, ctx->d_status + 1, sizeof(int), cudaMemcpyDeviceToHost));
     return HAI_OK;
 }
 

@@ -91,6 +91,19 @@ hai_status hai_fail(hai_status s, const std::string &msg);
 hai_status hai_cuda_fail(cudaError_t e, const char *what);
 bool hai_fault_injected(const char *site);   // host-side fault injection
 
+// Let `kern` use the device's whole opt-in dynamic shared memory (less its
+// static shared memory).  The value is the same for every call, so callers on
+// other host threads launching with other sizes never lower each other's
+// limit between their set and their launch; each launch's own size still
+// decides its occupancy.
+template <typename K>
+inline cudaError_t hai_allow_dyn_smem(K kern, int smem_optin) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kern);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin - (int)a.sharedSizeBytes);
+}
+
 #define HAI_CUDA_TRY(call)                                         \
     do {                                                           \
         cudaError_t _e = (call);                                   \

@@ -469,7 +469,7 @@ extern "C" hai_status hai_xfft_station_image(hai_ctx *ctx, const hai_vis_layout 
     int log2n = 0;
     while ((1 << log2n) < N) log2n++;
     const size_t win_bytes = (size_t)2 * L->tw * L->th * sizeof(float);
-    HAI_CUDA_TRY(cudaFuncSetAttribute(station_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_bytes));
+    HAI_CUDA_TRY(hai_allow_dyn_smem(station_grid_kernel, ctx->smem_optin));
     if ((long long)images * 2 > 0x7fffffffll) return hai_fail(HAI_ERR_UNSUPPORTED, "hai_xfft_station_image: too many images");
     // cells outside the window stay zero; the tiles write the rest
     HAI_CUDA_TRY(cudaMemsetAsync(img, 0, sizeof(float) * (size_t)images * 4 * N * N, st));
@@ -484,7 +484,7 @@ extern "C" hai_status hai_xfft_station_image(hai_ctx *ctx, const hai_vis_layout 
                       sizeof(float2) * (rows_per_cta * N + N / 2), st>>>(img, N, log2n);
     HAI_CUDA_TRY(cudaGetLastError());
     const size_t tile = sizeof(float2) * ((size_t)N * 33 + N / 2);
-    HAI_CUDA_TRY(cudaFuncSetAttribute(fft_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile));
+    HAI_CUDA_TRY(hai_allow_dyn_smem(fft_cols_kernel, ctx->smem_optin));
     fft_cols_kernel<<<dim3(images * 2, (N + 31) / 32), kThreads, tile, st>>>(img, N, log2n);
     prof_count(ctx, 3);
     HAI_CUDA_TRY(cudaGetLastError());

@@ -167,11 +167,15 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *m, uint32_t parity) 
 // try_wait (which may suspend the thread in hardware until the phase flips)
 // and reads the device status word only once every 2^14 cycles of waiting,
 // so a wait that ends within a few microseconds never leaves the SM.  Gives
-// up after ~2^32 SM cycles (about two seconds), or at the next check once
-// another wait of the launch has given up, flagging HAI_DEV_TIMEOUT in the
-// status word and returning false; the caller carries on so that every
-// thread still reaches every barrier and the kernel ends.
-__device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity, unsigned *status) {
+// up after `limit` SM cycles (default 2^32, about two seconds; checked at the
+// same 2^14-cycle points), or at the next check once another wait of the
+// launch has given up, flagging HAI_DEV_TIMEOUT in the status word and
+// returning false; the caller carries on so that every thread still reaches
+// every barrier and the kernel ends.
+constexpr long long kWaitLimitCycles = 1ll << 32;
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity, unsigned *status,
+                                          long long limit = kWaitLimitCycles) {
     if (mbar_try_wait(m, parity)) return true;
     const long long t0 = clock64();
     long long next_check = 1ll << 14;
@@ -180,7 +184,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity, unsigned
         const long long dt = clock64() - t0;
         if (dt > next_check) {
             if (*reinterpret_cast<volatile unsigned *>(status) & HAI_DEV_TIMEOUT) return false;
-            if (dt > (1ll << 32)) {
+            if (dt > limit) {
                 atomicOr(status, (unsigned)HAI_DEV_TIMEOUT);
                 return false;
             }

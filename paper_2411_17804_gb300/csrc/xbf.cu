@@ -368,11 +368,15 @@ extern "C" hai_status hai_xbf_layout_create(hai_ctx *ctx, const hai_vis_layout_d
         if ((e = cudaMalloc(&d_dir, sizeof(double) * 2 * K)) != cudaSuccess) return fail(e);
         std::vector<double> dir(2 * (size_t)K, 0.0);
         if (d->dir) std::copy(d->dir, d->dir + 2 * (size_t)K, dir.begin());
-        cudaMemcpy(L->d_pairs, pairs.data(), sizeof(int2) * L->B, cudaMemcpyHostToDevice);
-        cudaMemcpy(d_duv, duv.data(), sizeof(double2) * L->B, cudaMemcpyHostToDevice);
-        cudaMemcpy(d_dr, dr.data(), sizeof(double2) * L->B, cudaMemcpyHostToDevice);
-        cudaMemcpy(d_dir, dir.data(), sizeof(double) * 2 * K, cudaMemcpyHostToDevice);
-        cudaMemset(L->d_coef, 0, L->coef_bytes);
+        if ((e = cudaMemcpy(L->d_pairs, pairs.data(), sizeof(int2) * L->B, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(e);
+        if ((e = cudaMemcpy(d_duv, duv.data(), sizeof(double2) * L->B, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(e);
+        if ((e = cudaMemcpy(d_dr, dr.data(), sizeof(double2) * L->B, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(e);
+        if ((e = cudaMemcpy(d_dir, dir.data(), sizeof(double) * 2 * K, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(e);
+        if ((e = cudaMemset(L->d_coef, 0, L->coef_bytes)) != cudaSuccess) return fail(e);
         int log2n = 0;
         while ((1 << log2n) < N) log2n++;
         const long long nthr = (long long)npix * L->n_kblk * (kTK / 8);

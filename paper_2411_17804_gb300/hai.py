@@ -90,6 +90,8 @@ def _declare(L):
     L.hai_xbf_station_image.argtypes = [_vp, _vp, _vp, _int, _vp, _int, _vp]
     L.hai_xfft_station_image.argtypes = [_vp, _vp, _vp, _int, _vp, _vp]
     L.hai_profile_enable.argtypes = [_vp, _int, _int]
+    L.hai_check_device_wait.argtypes = [_vp, ctypes.c_longlong, _vp]
+    L.hai_check_device_wait_result.argtypes = [_vp, ctypes.POINTER(_int)]
     L.hai_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
 
@@ -171,6 +173,16 @@ def hai_destroy(ctx):
 
 def hai_sync(ctx, stream=None):
     _check(load().hai_sync(ctx, _stream(stream)), "hai_sync")
+
+
+def hai_check_device_wait(ctx, limit_cycles: int, stream=None):
+    _check(load().hai_check_device_wait(ctx, int(limit_cycles), _stream(stream)), "hai_check_device_wait")
+
+
+def hai_check_device_wait_result(ctx) -> int:
+    g = _int()
+    _check(load().hai_check_device_wait_result(ctx, ctypes.byref(g)), "hai_check_device_wait_result")
+    return g.value
 
 
 def hai_profile_enable(ctx, enable: bool = True, max_records: int = 4096):

@@ -4,19 +4,55 @@ import numpy as np
 
 from paper_2411_17804_gb300 import inputs as I
 
-FP32_TOL = 1e-5     # relative Frobenius error per image plane, FP32 path
-REDUCED_TOL = 2e-3  # relative error per image plane, FP16 tensor-core path
+FP32_TOL = 1e-5     # per image plane, FP32 path
+REDUCED_TOL = 2e-3  # per image plane, fp16 / bf16 tensor-core paths
+
+
+def _plane_scales(want):
+    """Per-(channel, plane) Frobenius norm and peak of the expected image, with
+    the cross-polarisation planes (which may be near zero) measured against the
+    auto planes' scale: floor at 1e-3 x the larger auto plane."""
+    C, Q = want.shape[:2]
+    w = want.reshape(C, Q, -1)
+    den = np.linalg.norm(w, axis=-1)
+    peak = np.abs(w).max(axis=-1)
+    na = min(2, Q)
+    den = np.maximum(den, 1e-3 * den[:, :na].max(axis=1, keepdims=True))
+    peak = np.maximum(peak, 1e-3 * peak[:, :na].max(axis=1, keepdims=True))
+    return den, peak
+
+
+def frob_err_planes(got, want):
+    """Relative Frobenius error per (channel, plane): [C][Q] (the reported
+    image-error metric)."""
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    C, Q = want.shape[:2]
+    num = np.linalg.norm((got - want).reshape(C, Q, -1), axis=-1)
+    den, _ = _plane_scales(want)
+    return num / den
+
+
+def pixel_err_planes(got, want):
+    """Element-by-element error per (channel, plane): max over pixels of
+    |I_gpu - I_ref| / max |I_ref|: [C][Q]."""
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    C, Q = want.shape[:2]
+    num = np.abs(got - want).reshape(C, Q, -1).max(axis=-1)
+    _, peak = _plane_scales(want)
+    return num / peak
 
 
 def rel_err_planes(got, want):
-    """Relative Frobenius error per (channel, plane): [C][Q] array."""
+    """Per (channel, plane) the larger of the relative Frobenius error and the
+    per-pixel error |I_gpu - I_ref| / max |I_ref|, so that a test asserting
+    `rel_err_planes(...) < tol` holds every pixel to the tolerance as well as
+    the plane's norm.  NaN anywhere fails."""
     got = np.asarray(got, np.float64)
-    want = np.asarray(want, np.float64)
-    num = np.linalg.norm((got - want).reshape(got.shape[0], got.shape[1], -1), axis=-1)
-    den = np.linalg.norm(want.reshape(want.shape[0], want.shape[1], -1), axis=-1)
-    # cross-pol planes may be tiny; measure them against the auto planes' scale
-    auto = np.max(den[:, : min(2, want.shape[1])], axis=1, keepdims=True)
-    return num / np.maximum(den, 1e-3 * auto)
+    if not np.all(np.isfinite(got)):
+        return np.full(np.asarray(want).shape[:2], np.inf)
+    return np.maximum(frob_err_planes(got, want), pixel_err_planes(got, want))
 
 
 def station(cfg, seed=None):

@@ -26,7 +26,14 @@ def rows(name):
 def test_filling_factors_as_printed():
     for name, fa, fs in rows("table1_filling_factors.txt"):
         a = K.ARRAYS[name]
-        assert float(f"{a.f_s:.3g}") == pytest.approx(float(fs), rel=1e-9), name
+        if name == "CASPA":
+            # recorded inconsistency of Table 1: with the printed D_e / lambda =
+            # 0.5 the formula gives a quarter of the printed f_s; the printed
+            # value is the formula with D_e = lambda
+            assert a.f_s == pytest.approx(float(fs) / 4, rel=0.01)
+            assert float(f"{K.CASPA_DE1.f_s:.3g}") == pytest.approx(float(fs), rel=1e-9)
+        else:
+            assert float(f"{a.f_s:.3g}") == pytest.approx(float(fs), rel=1e-9), name
         if name == "LAMBDA-I":
             # the printed f_A is twice N_s (D_s / D_A)^2 with the printed N_s = 4
             assert a.f_A == pytest.approx(float(fa) / 2, rel=0.01)
@@ -94,7 +101,26 @@ def test_intra_station_choice_matches_table3_in_every_cell():
         if stage != "intra":
             continue
         for col, want in zip(COLS.values(), cells):
+            if name == "CASPA":
+                # the printed row follows D_e = lambda (see the filling factor)
+                assert K.ranking(K.CASPA_DE1, "intra", col)[0][0] == want, (name, col)
+                continue
             assert K.ranking(name, "intra", col)[0][0] == want, (name, col)
+
+
+def test_caspa_as_printed_is_a_recorded_inconsistency():
+    """With the printed D_e / lambda = 0.5 the Table 2 formulas move CASPA's
+    station-level EPIC / XFFT crossover to about 0.1 ms, so Table 3's EPIC at
+    1 ms does not follow from them; with D_e = lambda it does."""
+    rank = K.ranking("CASPA", "intra", 1e-3)
+    assert rank[0][0] == "XFFT"
+    assert K.ranking(K.CASPA_DE1, "intra", 1e-3)[0][0] == "EPIC"
+    for arr, lo, hi in ((K.ARRAYS["CASPA"], 3e-5, 3e-4), (K.CASPA_DE1, 1e-3, 10e-3)):
+        n, ratio = K.level_args(arr, "intra")
+        ts = np.geomspace(1e-5, 1.0, 800)
+        diff = [K.density("EPIC", n, ratio, t) - K.density("XFFT", n, ratio, t) for t in ts]
+        cross = ts[np.argmax(np.array(diff) > 0)]
+        assert lo < cross < hi, (arr.name, cross)
 
 
 def test_inter_station_choice_is_among_table3_entries():
@@ -118,8 +144,9 @@ def test_section6_statements():
         for t in K.CADENCES:
             d = dict(K.ranking(name, "intra", t))
             assert d["EPIC"] < d["BF"]
-    # CASPA stations: EPIC below and XFFT above a crossover of a few ms
-    n, ratio = K.level_args(K.ARRAYS["CASPA"], "intra")
+    # CASPA stations: EPIC below and XFFT above a crossover of a few ms (with
+    # D_e = lambda; the printed D_e puts it near 0.1 ms, tested above)
+    n, ratio = K.level_args(K.CASPA_DE1, "intra")
     ts = np.geomspace(1e-4, 1.0, 400)
     diff = [K.density("EPIC", n, ratio, t) - K.density("XFFT", n, ratio, t) for t in ts]
     cross = ts[np.argmax(np.array(diff) > 0)]

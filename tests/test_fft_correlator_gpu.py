@@ -19,12 +19,19 @@ def ctx(hai):
 
 
 def grid_err(got, want):
-    """Frobenius error per (channel, alpha, beta) grid relative to the largest
-    auto-polarisation grid of the channel: [C][P][P]."""
+    """Error per (channel, alpha, beta) grid relative to the largest
+    auto-polarisation grid of the channel, [C][P][P]: the larger of the
+    Frobenius error (against that grid's norm) and the largest per-lag error
+    (against that grid's largest |value|), so every lag is held to the
+    tolerance."""
     C, P = want.shape[:2]
+    if not np.all(np.isfinite(got)):
+        return np.full((C, P, P), np.inf)
     num = np.linalg.norm((got - want).reshape(C, P, P, -1), axis=-1)
     auto = np.max([np.linalg.norm(want[:, p, p].reshape(C, -1), axis=-1) for p in range(P)], axis=0)
-    return num / auto[:, None, None]
+    pix = np.abs(got - want).reshape(C, P, P, -1).max(axis=-1)
+    peak = np.max([np.abs(want[:, p, p]).reshape(C, -1).max(axis=-1) for p in range(P)], axis=0)
+    return np.maximum(num / auto[:, None, None], pix / peak[:, None, None])
 
 
 def fft_correlate(hai, ctx, img, N, P):

@@ -1,17 +1,19 @@
-"""The allocation-free EPIC entry point against the regular one.
+"""The allocation-free EPIC entry point against the regular one and the oracle.
 
 hai_epic_image_fp32_static is for callers that cannot call cudaMalloc (it
 keeps its gather table and partial images in a static device array inside
 the library).  Through the C ABI it must give the image of hai_epic_image's
 FP32 path on the same inputs, on consecutive calls that reuse the shared
-array.  This file is collected last so that a run stopping at the first
-failure has run every other test first."""
+array, and the FP64 oracle's image within the FP32 tolerance.  This file is
+collected last so that a run stopping at the first failure has run every
+other test first."""
 import ctypes
 
 import numpy as np
 import pytest
 import torch
 
+from oracle import oracle as O
 from paper_2411_17804_gb300 import inputs as I
 from tests.helpers import FP32_TOL, rel_err_planes, station
 
@@ -56,6 +58,9 @@ def test_static_entry_matches_regular_entry_on_consecutive_calls(hai):
     got2 = static_image(hai, anchors, taps, cfg.grid_n, v2).cpu().numpy()
     assert rel_err_planes(got1, reference_image(hai, anchors, taps, cfg.grid_n, v1)).max() < FP32_TOL
     assert rel_err_planes(got2, reference_image(hai, anchors, taps, cfg.grid_n, v2)).max() < FP32_TOL
+    # and the oracle's images directly
+    assert rel_err_planes(got1, O.epic_image(cfg.grid_n, anchors, taps, v1.cpu().numpy())).max() < FP32_TOL
+    assert rel_err_planes(got2, O.epic_image(cfg.grid_n, anchors, taps, v2.cpu().numpy())).max() < FP32_TOL
 
 
 def test_static_entry_other_layouts_and_accumulate(hai):
@@ -67,6 +72,34 @@ def test_static_entry_other_layouts_and_accumulate(hai):
     assert rel_err_planes(img.cpu().numpy(), want).max() < FP32_TOL
     img = static_image(hai, anchors, taps, cfg.grid_n, volt, accumulate=1, img=img)
     assert rel_err_planes(img.cpu().numpy(), 2 * want).max() < FP32_TOL
+    assert rel_err_planes(img.cpu().numpy(), 2 * O.epic_image(cfg.grid_n, anchors, taps, volt.cpu().numpy())).max() \
+        < FP32_TOL
+
+
+def test_static_entry_direct_path_many_channels(hai):
+    """64 channels: one CTA per channel writes the image in place (no partial
+    images, no reduction), with and without accumulate."""
+    cfg = I.SKA_LOW_STATION_256
+    pos, anchors, taps = station(cfg)
+    volt = I.station_voltages(cfg, pos, n_chan=64, n_time=6, device="cuda")
+    want = O.epic_image(cfg.grid_n, anchors, taps, volt.cpu().numpy())
+    img = static_image(hai, anchors, taps, cfg.grid_n, volt)
+    assert rel_err_planes(img.cpu().numpy(), want).max() < FP32_TOL
+    assert rel_err_planes(img.cpu().numpy(), reference_image(hai, anchors, taps, cfg.grid_n, volt)).max() < FP32_TOL
+    img = static_image(hai, anchors, taps, cfg.grid_n, volt, accumulate=1, img=img)
+    assert rel_err_planes(img.cpu().numpy(), 2 * want).max() < FP32_TOL
+
+
+def test_static_entry_refuses_taps_off_the_grid(hai):
+    cfg = I.SINGLE_STATION_64
+    _, anchors, taps = station(cfg)
+    anchors = anchors.copy()
+    anchors[7] = (cfg.grid_n - 1, 3)                  # a 3x3 window starting on the last column
+    volt = torch.zeros((1, 2, 1, len(anchors), 2), dtype=torch.int8, device="cuda")
+    img = torch.zeros((1, 1, cfg.grid_n, cfg.grid_n), device="cuda")
+    with pytest.raises(hai.HaiError) as e:
+        hai.hai_epic_image_fp32_static(0, anchors, taps, cfg.grid_n, 1, volt, 1, 2, img)
+    assert e.value.status == 2
 
 
 def test_static_entry_rejects_sizes_beyond_its_maximum(hai):
