@@ -6,6 +6,14 @@ from paper_2411_17804_gb300 import inputs as I
 
 FP32_TOL = 1e-5     # per image plane, FP32 path
 REDUCED_TOL = 2e-3  # per image plane, fp16 / bf16 tensor-core paths
+# Split hi/lo tensor-core products are a reduced-precision path (fp16 / bf16
+# operands), bound by REDUCED_TOL; the tests hold them to the FP32 level
+# instead: Frobenius error < FP32_TOL and every pixel within SPLIT_PIXEL_TOL of
+# the plane's peak.  Per pixel the FP32 accumulation of K products (in TMEM,
+# K up to ~5,000 for the XBF) leaves about sqrt(K) 2^-24 of the sum of |terms|
+# (~4e-6), and the dropped lo*lo term 2^-22 per product, on pixels where the
+# terms cancel, so the per-pixel bound is twice the FP32 one.
+SPLIT_PIXEL_TOL = 2e-5
 
 
 def _plane_scales(want):

