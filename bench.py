@@ -1,9 +1,10 @@
 """Benchmark of the EPIC hot path on GB300 (one JSON line on rank 0).
 
-A step is one cadence of the EPIC imager of the SKA-low-shaped station
-(256 elements, 2 polarisations, 64 channels, 2048 samples, 64 x 64 grid):
-gridding, the per-sample 2D DFT, squaring and accumulation, through the C ABI
-(hai_epic_image).  value = imaged pixel x channel x pol x sample per second.
+A step is one cadence of the EPIC imager of the dense all-sky lattice
+(16,384 elements, 512 x 512 grid, 16 channels, 2 polarisations, 10^4 samples):
+gridding, the per-sample 2D DFT on tensor cores, squaring and accumulation,
+through the C ABI (hai_epic_image).  value = imaged pixel x channel x pol x
+sample per second.
 `--impl reference` times the FP64 CPU oracle on a bounded sample instead.
 Multi-GPU: every rank images its own cadence (channels are independent), no
 collective on the data path; value is the sum over ranks / the max time.
@@ -28,18 +29,23 @@ METRIC = "imaged pix·chan·pol·samples/s"
 UNIT = "pix·chan·pol·samples/s"
 
 
+PRECS = {"fp32": 0, "fp16": 1, "fp16_split": 2, "bf16": 3, "bf16_split": 4}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["fp16", "fp32"], default="fp16")
+    ap.add_argument("--prec", choices=list(PRECS), default="fp16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-components", action="store_true")
     ap.add_argument("--channels", type=int, default=0,
                     help="image only this many channels (small cases for profiling)")
+    ap.add_argument("--samples", type=int, default=0,
+                    help="samples per cadence of the headline workload (default 10^4)")
     ap.add_argument("--case", choices=["tc64", "tc128", "corr", "xfft", "bf", "xbf", "sxfft", "fc", "big", "big16"], default=None,
                     help="run one small case of a kernel twice, untimed, and exit (for ncu captures)")
     return ap.parse_args()
@@ -95,12 +101,33 @@ def job_value(ws, units_per_rank, max_ms):
     return ws * units_per_rank / (max_ms * 1e-3)
 
 
-def workload():
+HEADLINE_T = 10000
+
+
+def workload(samples=0):
+    """The dense all-sky lattice (128 x 128 elements at 0.5 lambda, 512^2 grid,
+    1 x 1 unit taps, 16 channels, 2 pols) over the longest cadence of its
+    range, 10^4 samples: the largest workload that fits one GPU (10.5 GB of
+    voltages, 8.4e10 imaged units per cadence)."""
+    import dataclasses
     from paper_2411_17804_gb300 import inputs as I
-    cfg = I.SKA_LOW_STATION_256
+    cfg = dataclasses.replace(I.DENSE_ALLSKY_16384, n_time=samples or HEADLINE_T)
+    cfg = dataclasses.replace(cfg, name=f"dense_allsky16384_grid512_T{cfg.n_time}")
     pos = I.station_layout(cfg)
     anchors, taps = I.station_kernel(cfg, pos)
     return cfg, pos, anchors, taps
+
+
+def pruned_dft_flop(n, R, Cnz):
+    """Algorithmic tensor-core FLOP of one field's two-stage DFT of the
+    kernel's bounding box (R rows, Cnz columns): 8 (R N Cnz + N^2 R) real FLOP
+    (8 per complex multiply-add)."""
+    return 8.0 * (R * n * Cnz + n * n * R)
+
+
+def stage2_flop(n, R):
+    """The second stage's share: 8 N^2 R per field."""
+    return 8.0 * n * n * R
 
 
 class Clocks:
@@ -168,14 +195,6 @@ def epic_flops_per_unit(cfg):
     return 5 * math.log2(n * n) + 8.0 * cfg.n_elem * cfg.ksize ** 2 / (n * n) + 8.0
 
 
-def tc_mma_flops_per_unit(cfg, box=32):
-    """Executed tensor-core FLOP per imaged unit of the two-stage DFT-as-GEMM:
-    per field 8 (R N C + N^2 R) with the padded box R = C = 32 (real-ified
-    complex products, 8 real FLOP per complex MAC)."""
-    n = cfg.grid_n
-    return 8.0 * (box * n * box + n * n * box) / (n * n)
-
-
 def corr_mma_flops(C, T, N, P):
     """Executed tensor-core FLOP of one correlator launch: tiles (row block of
     128 / P elements x two column blocks of 64 / P elements, a >= b somewhere
@@ -223,67 +242,83 @@ def measured_peaks():
 
 
 def image_error(got, want):
-    """Per-(channel, plane) relative Frobenius error of GPU images against the
-    oracle's (cross-pol planes measured against the auto planes' scale)."""
+    """Per-(channel, plane) error of GPU images against the oracle's: the
+    relative Frobenius error and the largest per-pixel error over the plane's
+    peak (cross-pol planes measured against the auto planes' scale)."""
     n_chan = want.shape[0]
     got = got[:n_chan].astype(np.float64)
-    d = np.linalg.norm((got - want).reshape(n_chan, want.shape[1], -1), axis=-1)
-    r = np.linalg.norm(want.reshape(n_chan, want.shape[1], -1), axis=-1)
+    w = want.reshape(n_chan, want.shape[1], -1)
+    g = got.reshape(w.shape)
+    d = np.linalg.norm(g - w, axis=-1)
+    r = np.linalg.norm(w, axis=-1)
     r = np.maximum(r, 1e-3 * r[:, :2].max(axis=1, keepdims=True))
+    pk = np.abs(w).max(axis=-1)
+    pk = np.maximum(pk, 1e-3 * pk[:, :2].max(axis=1, keepdims=True))
     e = d / r
-    return {"metric": "||I_gpu - I_oracle||_F / ||I_oracle||_F per (channel, plane)",
+    px = np.abs(g - w).max(axis=-1) / pk
+    return {"metric": "||I_gpu - I_oracle||_F / ||I_oracle||_F per (channel, plane); pixel: max|dI| / max|I_oracle|",
             "channels": n_chan, "max": float(e.max()), "median": float(np.median(e)),
-            "per_plane_max": [float(x) for x in e.max(axis=0)]}
+            "pixel_max": float(px.max()), "per_plane_max": [float(x) for x in e.max(axis=0)]}
 
 
-def cpu_baseline(cfg, anchors, taps, volt_host, n_err, gpu_imgs=None, min_s=10.0):
-    """FP64 oracle on the host cores over the whole cadence (every channel),
-    repeated until at least min_s seconds of CPU work have run (a bounded
-    sample: about 10-20 s).  Its images of the first n_err channels also give
-    the per-image error of the GPU images of those channels (one entry per
-    precision in gpu_imgs)."""
+def cpu_baseline(cfg, anchors, taps, volt_host, gpu_imgs=None, min_s=10.0):
+    """FP64 oracle on the host cores over a bounded sample of the cadence (the
+    channels in volt_host, every sample), repeated until at least min_s seconds
+    of CPU work have run.  Its images also give the per-image error of the GPU
+    images of those channels (one entry per precision in gpu_imgs)."""
     from oracle import oracle as O
-    n_chan = volt_host.shape[0]
+    n_chan, T = volt_host.shape[0], volt_host.shape[1]
     reps, want = 0, None
     t0 = time.perf_counter()
     while True:
         out_img = O.epic_image(cfg.grid_n, anchors, taps, volt_host)
         if want is None:
-            want = out_img[:n_err]
+            want = out_img
         reps += 1
         dt = time.perf_counter() - t0
         if dt >= min_s:
             break
-    units = cfg.grid_n ** 2 * n_chan * cfg.n_pol * cfg.n_time * reps
+    units = cfg.grid_n ** 2 * n_chan * cfg.n_pol * T * reps
     out = {"value": units / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-           "sample": f"the whole cadence ({n_chan} channels x {cfg.n_time} samples) x {reps} ({dt:.1f} s)"}
+           "sample": f"{n_chan} of {cfg.n_chan} channels x all {T} samples of the cadence, x {reps} ({dt:.1f} s)"}
     errs = {k: image_error(v, want) for k, v in (gpu_imgs or {}).items()}
     return out, errs
 
 
+def headline_config(cfg, prec_name, ws):
+    return {"workload": cfg.name, "elements": cfg.n_elem, "channels": cfg.n_chan, "pols": cfg.n_pol,
+            "samples": cfg.n_time, "grid": cfg.grid_n, "kernel_taps": cfg.ksize ** 2, "precision": prec_name,
+            "l2": "inputs larger than L2 (10.5 GB of voltages per step), and a 256 MB write between steps",
+            "parallelism": f"channel bands x{ws} (rank r images channels [r C, (r+1) C), no collective)"}
+
+
 def run_reference(args, ws, rank):
+    """The oracle itself (this workload's reference arm): every step images a
+    bounded sample of the headline workload, 1 channel x 100 samples, on the
+    host cores."""
     if rank != 0:
         return
-    cfg, pos, anchors, taps = workload()
+    cfg, pos, anchors, taps = workload(args.samples)
     steps, warm = args.steps, args.warmup
-    sample_chan = 2
+    sample_chan, sample_t = 1, min(100, cfg.n_time)
     from oracle import oracle as O
     from paper_2411_17804_gb300 import inputs as I
-    volt = I.station_voltages(cfg, pos, n_chan=sample_chan).numpy()
+    volt = I.station_voltages(cfg, pos, n_chan=sample_chan, n_time=sample_t).numpy()
     for _ in range(warm):
-        O.epic_image(cfg.grid_n, anchors, taps, volt[:, :64])
+        O.epic_image(cfg.grid_n, anchors, taps, volt[:, :4])
     t0 = time.perf_counter()
     for _ in range(steps):
         O.epic_image(cfg.grid_n, anchors, taps, volt)
     dt = (time.perf_counter() - t0) / steps
-    units = cfg.grid_n ** 2 * sample_chan * cfg.n_pol * cfg.n_time
+    units = cfg.grid_n ** 2 * sample_chan * cfg.n_pol * sample_t
     v = units / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": steps, "warmup": warm, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg.name, "sample": f"{sample_chan} channels x {cfg.n_time} samples per step"},
+            "config": headline_config(cfg, args.prec, ws),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-                             "sample": f"{sample_chan} of {cfg.n_chan} channels per step"},
+                             "sample": f"{sample_chan} of {cfg.n_chan} channels x {sample_t} of {cfg.n_time} "
+                                       "samples per step"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -326,7 +361,9 @@ def time_epic(hai, ctx, lay, volt, img, C, T, prec, steps, warm, flush, ws):
     hai.hai_sync(ctx, st)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     dom_ms, dom_n, launches = hai.hai_profile_read(ctx)
-    return float(np.sum(step_ms)), dom_ms / max(dom_n, 1), launches
+    # total step time, summed dominant-kernel time and library kernel launches
+    # over the timed steps
+    return float(np.sum(step_ms)), dom_ms, launches
 
 
 def bf_component(hai, ctx, flush, peaks):
@@ -357,18 +394,6 @@ def bf_component(hai, ctx, flush, peaks):
         del beams
     del volt, w
     return out
-
-
-# DRAM bytes (read + write) of one epic_tc_kernel<64> launch over 16 channels of
-# the SKA-low station, from an ncu capture of `bench.py --case tc64` with the
-# kernel as it is now; traffic grows in proportion to the channels imaged.
-TC64_TRAFFIC_16CH = 33.657344e6
-
-
-def traffic_tc64(cfg, C):
-    if cfg.name != "ska_low_station256_grid64" or cfg.n_time != 2048:
-        return None
-    return TC64_TRAFFIC_16CH * C / 16
 
 
 def plan_mma_flops(n, ne=None):
@@ -446,55 +471,92 @@ def plan_component(hai, ctx, flush, peaks, steps):
     return out
 
 
-def dense_component(hai, ctx, flush, peaks, sms):
-    """The dense all-sky lattice: 128 x 128 elements at 0.5 lambda, 512^2
-    grid, 16 channels, 2 pols, 100 samples of the seeded sky, through the
-    FP32 large-grid path (row FFTs to an L2 scratch, column FFTs with the
-    squaring).  ALU roofline on the FFT-equivalent work."""
+def fft_correlator_component(hai, ctx, img, C, n, P, flush, peaks):
+    """FFT correlator on the headline's accumulated images: the redundant-
+    baseline visibility sums of the lattice at every lag (the inverse FFT,
+    once per cadence).  HBM roofline: image read once, grid written once."""
     import torch
-    from paper_2411_17804_gb300 import inputs as I
-    cfg = I.DENSE_ALLSKY_16384
-    pos = I.station_layout(cfg)
-    anchors, taps = I.station_kernel(cfg, pos)
-    volt = I.station_voltages(cfg, pos, device="cuda")
-    n, C, T, P = cfg.grid_n, cfg.n_chan, cfg.n_time, cfg.n_pol
-    lay = hai.hai_layout_create(ctx, anchors, taps, n, P)
-    img = torch.empty((C, 4, n, n), device="cuda")
-    ms = time_call(lambda st: hai.hai_epic_image(ctx, lay, volt, C, T, hai.HAI_PREC_FP32, img, 0, st), 5, 2, flush)
-    units = cfg.units_per_cadence
-    flop = epic_flops_per_unit(cfg) * units
-    peak = fp32_alu_peak_tflops(sms, float(peaks.get("sm_max_mhz", 2070.0)))
-    ach = flop / (ms * 1e-3) / 1e12
-    # the tensor-core path of the same cadence (fp16 operands, FP32 accumulation)
-    tc_ms = time_call(lambda st: hai.hai_epic_image(ctx, lay, volt, C, T, hai.HAI_PREC_FP16, img, 0, st), 5, 2, flush)
-    bxp, byp = 128, 128                                  # the lattice's box, padded to the tiles
-    s1 = 2.0 * 128 * 256 * (2 * bxp) * (C * T * P) * (byp // 128) * (n // 128)
-    s2 = 2.0 * 128 * 128 * (2 * byp) * C * T * (n // 64) ** 2
-    pkt = float(peaks.get("bf16_tflops", 1900.0))
-    tc_ach = (s1 + s2) / (tc_ms * 1e-3) / 1e12
-    tensor = {"precision": "fp16", "ms": tc_ms, "units_per_s": units / (tc_ms * 1e-3), "over_fp32": ms / tc_ms,
-              "roofline": {"bound": "tensor", "achieved": tc_ach, "peak": pkt, "unit": "TFLOP/s",
-                           "frac": tc_ach / pkt, "executed_flop": s1 + s2,
-                           "peak_source": "of measured bf16_tflops (fp16 nominal ratio 1)"}}
-    hai.hai_layout_destroy(lay)
-    # FFT correlator on the accumulated images: redundant-baseline sums of
-    # the lattice at every lag (the inverse FFT once per cadence)
     grid = torch.empty((C, P, P, n, n, 2), device="cuda")
     fc_ms = time_call(lambda st: hai.hai_fft_correlate(ctx, img, C, n, P, grid, st), 10, 3, flush)
-    fc_bytes = img.numel() * 4 + grid.numel() * 4          # image read once, grid written once
+    fc_bytes = img.numel() * 4 + grid.numel() * 4
     fc_gbs = fc_bytes / (fc_ms * 1e-3) / 1e9
-    del volt, img, grid
-    return {"workload": cfg.name, "elements": cfg.n_elem, "grid": n, "channels": C, "samples": T, "pols": P,
-            "precision": "fp32", "ms": ms, "units_per_s": units / (ms * 1e-3), "unit": UNIT,
-            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                         "flop_per_unit": epic_flops_per_unit(cfg),
-                         "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x max SM clock"},
-            "tensor_cores": tensor,
-            "fft_correlator": {
-                "what": "inverse FFT of the accumulated images -> visibilities summed per lag, all 4 pol pairs",
-                "ms": fc_ms, "lags_per_s": C * P * P * n * n / (fc_ms * 1e-3),
-                "roofline": {"bound": "hbm", "achieved": fc_gbs, "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s",
-                             "frac": fc_gbs / float(peaks.get("hbm_gbs", 6800.0)), "algorithmic_bytes": fc_bytes}}}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    del grid
+    return {"what": "inverse FFT of the accumulated images -> visibilities summed per lag, all 4 pol pairs",
+            "ms": fc_ms, "lags_per_s": C * P * P * n * n / (fc_ms * 1e-3),
+            "roofline": {"bound": "hbm", "achieved": fc_gbs, "peak": hbm, "unit": "GB/s", "frac": fc_gbs / hbm,
+                         "algorithmic_bytes": fc_bytes}}
+
+
+def ska_component(hai, ctx, flush, peaks, sms, steps):
+    """The SKA-low-shaped station (256 elements in a 38 m disk, 3 x 3 Gaussian
+    taps, 64^2 grid, 64 channels x 2 pols x 2048 samples): EPIC on tensor
+    cores (fp16, and the hi/lo split), on CUDA cores (FP32), end to end through
+    host buffers, and the correlator + XFFT comparison path on the same
+    cadence.  The tensor-core roofline counts the pruned DFT of the layout's
+    own kernel box (8 (R N C + N^2 R) per field)."""
+    import torch
+    from paper_2411_17804_gb300 import inputs as I
+    cfg = I.SKA_LOW_STATION_256
+    pos = I.station_layout(cfg)
+    anchors, taps = I.station_kernel(cfg, pos)
+    C, T, P, n = cfg.n_chan, cfg.n_time, cfg.n_pol, cfg.grid_n
+    volt = I.station_voltages(cfg, pos, device="cuda")
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, P)
+    img = torch.empty((C, 4, n, n), device="cuda")
+    units = cfg.units_per_cadence
+    x0, y0, x1, y1 = hai.hai_layout_box(lay)
+    R, Cnz = y1 - y0, x1 - x0
+    pk = float(peaks.get("bf16_tflops", 1900.0))
+    hai.hai_profile_read(ctx)
+    out = {"workload": cfg.name, "elements": cfg.n_elem, "channels": C, "pols": P, "samples": T, "grid": n,
+           "kernel_box": [Cnz, R]}
+    for name, prec in (("fp16", hai.HAI_PREC_FP16), ("fp16_split", hai.HAI_PREC_FP16_SPLIT),
+                       ("fp32", hai.HAI_PREC_FP32)):
+        ns = steps if name == "fp16" else max(3, steps // 4)
+        tot, dom, _ = time_epic(hai, ctx, lay, volt, img, C, T, prec, ns, 2, flush, 1)
+        ms, dom = tot / ns, dom / ns
+        e = {"ms": ms, "units_per_s": units / (ms * 1e-3), "kernel_ms": dom}
+        if prec != hai.HAI_PREC_FP32:
+            fl = pruned_dft_flop(n, R, Cnz) * C * T * P * (3 if name.endswith("split") else 1)
+            ach = fl / (dom * 1e-3) / 1e12
+            e["roofline"] = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                             "kernel": "epic_tc_kernel", "flop_per_field": pruned_dft_flop(n, R, Cnz),
+                             "basis": f"pruned DFT of the {Cnz} x {R} kernel box, 8 (R N C + N^2 R) per field"}
+        out[name] = e
+    out["tc_over_fp32"] = out["fp32"]["ms"] / out["fp16"]["ms"]
+    # end to end through the C ABI with host buffers (pinned)
+    vh = volt.cpu().pin_memory()
+    ih = torch.empty(img.shape, dtype=torch.float32).pin_memory()
+    st = torch.cuda.current_stream()
+    for _ in range(2):
+        hai.hai_epic_image_host(ctx, lay, vh, C, T, hai.HAI_PREC_FP16, ih, 0, 0, st)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(5):
+        hai.hai_epic_image_host(ctx, lay, vh, C, T, hai.HAI_PREC_FP16, ih, 0, 0, st)
+    torch.cuda.synchronize()
+    e_ms = (time.perf_counter() - e0) * 1e3 / 5
+    out["e2e"] = {"value": units / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(volt.numel()),
+                  "d2h_bytes_per_step": int(img.numel() * 4), "api": "hai_epic_image_host"}
+    # the comparison path on the same cadence: correlator (exact int8) + XFFT
+    N = cfg.n_elem
+    vis = torch.empty((C, N * (N + 1) // 2, P, P, 2), dtype=torch.int32, device="cuda")
+    cms = time_call(lambda st: hai.hai_correlate(ctx, volt, C, T, N, P, vis, 0, st), 10, 3, flush)
+    xms = time_call(lambda st: hai.hai_xfft_image(ctx, lay, vis, C, img, 0, st), 10, 3, flush)
+    mma = corr_mma_flops(C, T, N, P)
+    out["correlator"] = {"ms": cms, "visibilities_per_s": C * N * (N + 1) / 2 * P * P / (cms * 1e-3),
+                         "useful_tops": corr_useful_ops(C, T, N, P) / (cms * 1e-3) / 1e12,
+                         "roofline": {"bound": "tensor", "achieved": mma / (cms * 1e-3) / 1e12, "peak": pk,
+                                      "unit": "TFLOP/s", "frac": mma / (cms * 1e-3) / 1e12 / pk,
+                                      "peak_source": "of measured bf16_tflops (fp16 nominal ratio 1)"}}
+    out["xfft"] = {"ms": xms, "units_per_s": units / (xms * 1e-3),
+                   "note": "per cadence after the correlator; XFFT cadence = correlator + xfft"}
+    out["xfft_total_units_per_s"] = units / ((cms + xms) * 1e-3)
+    out["paper_cost"] = paper_cost("SKA-low", "intra", C, T, out["fp16"]["ms"])
+    hai.hai_layout_destroy(lay)
+    del vis, volt, img, vh, ih
+    return out
 
 
 def hierarchy_component(hai, ctx, flush, peaks):
@@ -714,23 +776,24 @@ def main():
         run_reference(args, ws, rank)
         return
     import torch
-    from paper_2411_17804_gb300 import hai
+    from paper_2411_17804_gb300 import hai, inputs as I
     torch.cuda.set_device(local)
-    cfg, pos, anchors, taps = workload()
+    cfg, pos, anchors, taps = workload(args.samples)
     if args.channels:
         import dataclasses
         cfg = dataclasses.replace(cfg, n_chan=args.channels)
     C, T, P, n = cfg.n_chan, cfg.n_time, cfg.n_pol, cfg.grid_n
-    prec = hai.HAI_PREC_FP16 if args.prec == "fp16" else hai.HAI_PREC_FP32
+    prec = PRECS[args.prec]
     chan0, _ = rank_channels(rank, C)
-    volt = __import__("paper_2411_17804_gb300.inputs", fromlist=["x"]).station_voltages(
-        cfg, pos, device="cuda", chan0=chan0)
+    volt = I.station_voltages(cfg, pos, device="cuda", chan0=chan0)
     ctx = hai.hai_create(local)
     lay = hai.hai_layout_create(ctx, anchors, taps, n, P)
     img = torch.empty((C, lay.n_planes, n, n), device="cuda")
     flush = torch.zeros(64 * 1024 * 1024, device="cuda")       # 256 MB > L2
-    hai.hai_profile_enable(ctx, True, 4096)
+    hai.hai_profile_enable(ctx, True, 1 << 16)
     units = cfg.units_per_cadence
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
 
     clocks = Clocks(local)
     clocks.start()
@@ -740,6 +803,7 @@ def main():
     total_ms = max_over_ranks(total_ms, ws)
     ms_step = total_ms / args.steps
     value = job_value(ws, units, ms_step)
+    dom_per_step = dom_ms / args.steps                         # stage-2 (or FP32) kernel time per step
 
     # end to end through the C ABI with host buffers (pinned): hai_epic_image_host
     # copies every voltage in and every image out inside the call, chunks of
@@ -747,111 +811,93 @@ def main():
     vh = volt.cpu().pin_memory()
     ih = torch.empty(img.shape, dtype=torch.float32).pin_memory()
     st = torch.cuda.current_stream()
-    for _ in range(2):
-        hai.hai_epic_image_host(ctx, lay, vh, C, T, prec, ih, 0, 0, st)
+    hai.hai_epic_image_host(ctx, lay, vh, C, T, prec, ih, 0, 0, st)
     torch.cuda.synchronize()
     barrier(ws)
     e0 = time.perf_counter()
-    e_steps = max(3, args.steps // 2)
+    e_steps = 3
     for _ in range(e_steps):
         hai.hai_epic_image_host(ctx, lay, vh, C, T, prec, ih, 0, 0, st)
     torch.cuda.synchronize()
     e_ms = max_over_ranks((time.perf_counter() - e0) * 1e3 / e_steps, ws)
     hai.hai_profile_read(ctx)
 
-    # plain FP32 form for comparison (metric: tensor cores vs plain FP32)
-    fp32 = None
-    if prec != hai.HAI_PREC_FP32 and not args.no_fp32_compare:
-        t32, d32, _ = time_epic(hai, ctx, lay, volt, img, C, T, hai.HAI_PREC_FP32, max(3, args.steps // 4),
-                                2, flush, ws)
-        fp32 = {"value": ws * units / (t32 / max(3, args.steps // 4) * 1e-3), "unit": UNIT}
-
-    peaks = measured_peaks()
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    flop_unit = epic_flops_per_unit(cfg)
-    achieved = flop_unit * units / (dom_ms * 1e-3) / 1e12
-    if prec == hai.HAI_PREC_FP16:
-        mma_unit = tc_mma_flops_per_unit(cfg)
-        ach = mma_unit * units / (dom_ms * 1e-3) / 1e12
-        pk = float(peaks.get("bf16_tflops", 1900.0))
-        roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                "traffic": traffic_tc64(cfg, C), "kernel": "epic_tc_kernel",
+    x0, y0, x1, y1 = hai.hai_layout_box(lay)
+    R, Cnz = y1 - y0, x1 - x0
+    fields = C * T * P
+    pkt = float(peaks.get("bf16_tflops", 1900.0))
+    split = 3 if args.prec.endswith("split") else 1
+    if prec != hai.HAI_PREC_FP32:
+        s2 = stage2_flop(n, R) * fields * split
+        ach = s2 / (dom_per_step * 1e-3) / 1e12
+        whole = pruned_dft_flop(n, R, Cnz) * fields * split / (ms_step * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": pkt, "unit": "TFLOP/s", "frac": ach / pkt,
+                "traffic": None, "kernel": "big_s2_kernel",
                 "peak_source": "of measured: MEASURED_PEAKS bf16_tflops (burst) x fp16/bf16 nominal ratio 1"
                                if "bf16_tflops" in peaks else "of fallback 1.9 PFLOP/s",
-                "flop_per_unit": mma_unit, "kernel_ms": dom_ms,
-                "fft_equiv_tflops": achieved}
-    elif prec == hai.HAI_PREC_FP32:
+                "flop_per_field": stage2_flop(n, R) * split,
+                "basis": f"stage 2 of the pruned DFT of the {Cnz} x {R} kernel box: 8 N^2 R per field "
+                         f"(x{split} products), {fields} fields per step",
+                "kernel_ms_per_step": dom_per_step,
+                "whole_path": {"achieved": whole, "frac": whole / pkt,
+                               "basis": "8 (R N C + N^2 R) per field over the step time (all kernels)"}}
+    else:
         peak_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         peak = fp32_alu_peak_tflops(sms, peak_mhz)
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "epic_fp32_kernel", "peak_source":
-                f"derived: {sms} SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
-                "flop_per_unit": flop_unit, "kernel_ms": dom_ms}
-    else:
-        roof = None
+        achieved = epic_flops_per_unit(cfg) * units / (dom_per_step * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "large_cols_kernel",
+                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz",
+                "flop_per_unit": epic_flops_per_unit(cfg)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == hai.HAI_PREC_FP32 else "f16",
-            "data": "synthetic",
-            "config": {"workload": cfg.name, "elements": cfg.n_elem, "channels": C, "pols": P,
-                       "samples": T, "grid": n, "kernel_taps": cfg.ksize ** 2,
-                       "precision": args.prec, "l2": "flushed between steps (256 MB write)",
-                       "parallelism": f"channel bands x{ws} (rank r images channels [r C, (r+1) C), no collective)"},
+            "vs_baseline": None, "dtype": "f32" if prec == hai.HAI_PREC_FP32 else args.prec[:4],
+            "data": "synthetic", "config": headline_config(cfg, args.prec, ws),
             "e2e": {"value": ws * units / (e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": int(volt.numel()), "d2h_bytes_per_step": int(img.numel() * 4),
                     "api": "hai_epic_image_host (host buffers, chunks of C/4 channels)"},
             "gpu_launches": int(launches), "clocks": clk, "roofline": roof}
-    line["paper_cost"] = paper_cost("SKA-low", "intra", C * ws, T, ms_step)
-    line["paper_cost"]["note"] = ("context, not a target: the paper counts (D_s/D_e)^2 independent pixels per "
-                                  f"channel; the image here holds N^2 = {n * n} pixels (padding 2, "
-                                  f"{cfg.ksize}x{cfg.ksize} kernel, power-of-two grid)")
-    if fp32 is not None:
-        line["plain_fp32"] = fp32
-        line["tc_over_fp32"] = value / fp32["value"]
-    if prec == hai.HAI_PREC_FP16 and not args.no_fp32_compare:
-        ns = max(3, args.steps // 4)
-        tsp, _, _ = time_epic(hai, ctx, lay, volt, img, C, T, hai.HAI_PREC_FP16_SPLIT, ns, 2, flush, ws)
-        line["fp16_split"] = {"value": ws * units / (tsp / ns * 1e-3), "unit": UNIT,
-                              "note": "hi/lo split products: FP32-level image error (see image_error_by_precision)"}
-        if fp32 is not None:
-            line["fp16_split"]["over_fp32"] = line["fp16_split"]["value"] / fp32["value"]
-    # comparison paths on the same cadence: correlator (exact int8) and XFFT
+    # every operand form on the same cadence: the metric's comparison with
+    # plain FP32 on CUDA cores, and the bf16 / split forms
+    if not args.no_fp32_compare:
+        forms = {}
+        for name, pr in PRECS.items():
+            if pr == prec:
+                continue
+            ns = 2 if pr == hai.HAI_PREC_FP32 else 3
+            tf, df, _ = time_epic(hai, ctx, lay, volt, img, C, T, pr, ns, 1, flush, ws)
+            forms[name] = {"value": ws * units / (tf / ns * 1e-3), "unit": UNIT, "ms_per_step": tf / ns}
+        forms[args.prec] = {"value": value, "unit": UNIT, "ms_per_step": ms_step}
+        line["by_precision"] = forms
+        if "fp32" in forms and prec != hai.HAI_PREC_FP32:
+            line["plain_fp32"] = forms["fp32"]
+            line["tc_over_fp32"] = value / forms["fp32"]["value"]
+    line["paper_cost"] = {"note": "the dense lattice is not a Table 1 array; see components.ska_station.paper_cost"}
     if not args.no_components:
-        N = cfg.n_elem
-        vis = torch.empty((C, N * (N + 1) // 2, P, P, 2), dtype=torch.int32, device="cuda")
-        hai.hai_profile_read(ctx)
-        cms = time_call(lambda st: hai.hai_correlate(ctx, volt, C, T, N, P, vis, 0, st), 10, 3, flush)
-        xms = time_call(lambda st: hai.hai_xfft_image(ctx, lay, vis, C, img, 0, st), 10, 3, flush)
-        dom_c = hai.hai_profile_read(ctx)
-        mma = corr_mma_flops(C, T, N, P)
-        pk = float(peaks.get("bf16_tflops", 1900.0))
-        line["components"] = {
-            "correlator": {"ms": cms, "visibilities_per_s": C * N * (N + 1) / 2 * P * P / (cms * 1e-3),
-                           "useful_tops": corr_useful_ops(C, T, N, P) / (cms * 1e-3) / 1e12,
-                           "roofline": {"bound": "tensor", "achieved": mma / (cms * 1e-3) / 1e12, "peak": pk,
-                                        "unit": "TFLOP/s", "frac": mma / (cms * 1e-3) / 1e12 / pk,
-                                        "peak_source": "of measured bf16_tflops (fp16 nominal ratio 1)"}},
-            "xfft": {"ms": xms, "units_per_s": units / (xms * 1e-3),
-                     "note": "per cadence after the correlator; XFFT cadence = correlator + xfft"},
-            "xfft_total_units_per_s": units / ((cms + xms) * 1e-3)}
-        del vis
+        hai.hai_epic_image(ctx, lay, volt, C, T, prec, img, 0, st)
+        line["components"] = {"fft_correlator": fft_correlator_component(hai, ctx, img, C, n, P, flush, peaks)}
+        del volt, vh, ih
+        torch.cuda.empty_cache()
+        line["components"]["ska_station"] = ska_component(hai, ctx, flush, peaks, sms, 20)
         line["components"]["beamformer"] = bf_component(hai, ctx, flush, peaks)
         line["components"]["batched_uneven"] = plan_component(hai, ctx, flush, peaks, 10)
         line["components"]["hierarchical"] = hierarchy_component(hai, ctx, flush, peaks)
-        line["components"]["dense_allsky"] = dense_component(hai, ctx, flush, peaks, sms)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        nc = min(16, C)
+        # one channel of the cadence: every precision's GPU image of it against
+        # the oracle's, which is also the timed CPU baseline
+        v1 = I.station_voltages(cfg, pos, device="cuda", n_chan=1, chan0=chan0)
+        i1 = torch.empty((1, 4, n, n), device="cuda")
         imgs = {}
-        for name, pr in (("main", prec), ("fp16_split", hai.HAI_PREC_FP16_SPLIT), ("fp32", hai.HAI_PREC_FP32)):
-            hai.hai_epic_image(ctx, lay, volt[:nc].contiguous(), nc, T, pr, img[:nc], 0, st)
+        for name, pr in PRECS.items():
+            hai.hai_epic_image(ctx, lay, v1, 1, T, pr, i1, 0, st)
             torch.cuda.synchronize()
-            imgs[name] = img[:nc].cpu().numpy()
-        cb, errs = cpu_baseline(cfg, anchors, taps, volt.cpu().numpy(), nc, gpu_imgs=imgs)
+            imgs[name] = i1.cpu().numpy()
+        cb, errs = cpu_baseline(cfg, anchors, taps, v1.cpu().numpy(), gpu_imgs=imgs)
         line["cpu_baseline"] = cb
-        line["image_error_vs_oracle"] = errs["main"]
-        line["image_error_by_precision"] = {k: {"max": v["max"], "median": v["median"]} for k, v in errs.items()}
+        line["image_error_vs_oracle"] = errs[args.prec]
+        line["image_error_by_precision"] = {k: {"max": v["max"], "median": v["median"], "pixel_max": v["pixel_max"]}
+                                            for k, v in errs.items()}
     hai.hai_layout_destroy(lay)
     hai.hai_destroy(ctx)
     if rank == 0:

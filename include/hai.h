@@ -59,11 +59,14 @@ typedef enum {
 } hai_status;
 
 typedef enum {
-    HAI_PREC_FP32 = 0,      /* FP32 FFT on CUDA cores                              */
-    HAI_PREC_FP16 = 1,      /* FP16 DFT-as-GEMM on tcgen05 tensor cores, FP32 acc.  */
-    HAI_PREC_FP16_SPLIT = 2 /* as FP16 with every operand split into hi + lo fp16
-                               parts and the products hi*hi + hi*lo + lo*hi:
-                               ~FP32 accuracy at 3x the tensor work (N = 32, 64) */
+    HAI_PREC_FP32 = 0,       /* FP32 FFT on CUDA cores                              */
+    HAI_PREC_FP16 = 1,       /* FP16 DFT-as-GEMM on tcgen05 tensor cores, FP32 acc.  */
+    HAI_PREC_FP16_SPLIT = 2, /* as FP16 with every operand split into hi + lo fp16
+                                parts and the products hi*hi + hi*lo + lo*hi:
+                                ~FP32 accuracy at 3x the tensor work              */
+    HAI_PREC_BF16 = 3,       /* BF16 DFT-as-GEMM (8-bit mantissa: ~8x the FP16
+                                error), FP32 accumulation                         */
+    HAI_PREC_BF16_SPLIT = 4  /* as BF16 with hi + lo bf16 parts (three products)  */
 } hai_precision;
 
 typedef struct hai_ctx hai_ctx;

@@ -1,32 +1,44 @@
 // EPIC on tcgen05 tensor cores for large grids (N = 256, 512): Eq.
 // intra-station EPIC, then the squaring and temporal sum of Eq. intra-station
-// squaring, FP16 operands and FP32 accumulation.
+// squaring, with 16-bit operands (FP16 or BF16, optionally split into hi + lo
+// parts whose products hi*hi + hi*lo + lo*hi reach ~FP32 accuracy) and FP32
+// accumulation.
 //
 // The 2D DFT of the kernel's bounding box (<= N/2 x N/2 cells, at the
 // transform's origin; the shift by the box corner is a phase common to both
 // polarisations and cancels in every product) is two dense complex products
 // with W'[j][l] = (-1)^j exp(+2 pi i l j / N) (the (-1)^j puts the phase
 // centre at pixel N/2), written as real GEMMs.  A grid of 512^2 does not fit
-// one SM, so the stages run as three kernels per batch of (channel, sample)
-// pairs, through HBM:
+// one SM, so the stages run as kernels per batch through an HBM scratch.  A
+// batch is a block of samples [t0, t1) of every channel, so that a long
+// cadence of few channels still gives stage 2 work for every SM:
 //   grid:   every field (channel, sample, pol) gathered into its box (FP32
-//           sums of conj(W~) E, stored fp16; one thread per cell and 8
-//           fields), K-major in the tensor cores' tile order:
-//           A1[field][y block][k block] = 128 rows y x 64 (x, re/im);
+//           sums of conj(W~) E, stored as 16-bit (hi, lo) values; one thread per
+//           cell and 8 fields), K-major in the tensor cores' tile order:
+//           A1[field][k block] = 128 rows y x 64 (x, re/im);
 //   stage1: H[y][l_x] = sum_x G[y][x] W'[x][l_x]: persistent CTAs over
-//           (field, y block, 128-wide l_x block) tiles, bulk copies of A1 and
-//           the constant DFT operand, tcgen05.mma M = 128, N = 256 (re, im of
-//           128 l_x), accumulator double-buffered in TMEM; the epilogue stores
-//           H as fp16, transposed, into the stage-2 operand layout:
+//           contiguous ranges of (l_x block, field) tiles, the l_x block's DFT
+//           operand resident in shared memory, A1 streamed by bulk copies,
+//           tcgen05.mma M = 128 (y), N = 2 W1 (re, im of W1 l_x), accumulator
+//           double-buffered in TMEM; the epilogue stores H (16-bit),
+//           transposed, into the stage-2 operand:
 //           A2[channel, sample][64-wide l_x block][k block] = MN-major tiles
 //           of 128 rows (l_x, pol) x 64 (y, re/im);
-//   stage2: F[l_y][l_x] = sum_y W'[y][l_y] H[y][l_x] for a 64 x 64 pixel
-//           tile of one channel: persistent CTAs over (channel, l_x block,
-//           l_y block), the tile's DFT operand resident in shared memory, the
-//           A2 tiles of each sample streamed by bulk copies, M = 128 (l_x,
-//           pol), N = 128 (re, im of 64 l_y); the epilogue adds |F_X|^2,
-//           |F_Y|^2 and F_X conj(F_Y) of the pixel tile into registers over
-//           the samples and writes the tile once per item.
+//   stage2: F[l_y][l_x] = sum_y W'[y][l_y] H[y][l_x] for a 64 x W2 pixel
+//           tile of one channel: an item is (l_y block, channel, l_x block);
+//           persistent CTAs take contiguous ranges of (item, sample) units, so
+//           every CTA gets the same number of samples; the l_y block's DFT
+//           operand stays resident while the CTA's items share it, A2 is
+//           streamed per k block, M = 128 (l_x, pol), N = 2 W2 (re, im of W2
+//           l_y); sixteen epilogue warps add |F_X|^2, |F_Y|^2 and F_X conj(F_Y)
+//           into registers over the samples.  The CTA holding an item's first
+//           sample writes (or adds to) the image tile; a CTA whose range begins
+//           inside an item writes its partial tile to its own slot, and
+//   fixup:  adds the slots of every split item to the image in CTA order
+//           (deterministic: the same order on every run).
+// W1 = W2 = 128 (MMA N = 256) for plain operands, 64 (N = 128) for split ones
+// (the hi and lo DFT operands then fit shared memory together).
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -42,34 +54,48 @@ constexpr uint32_t kKBytes = 128;        // K-major: K-group stride
 constexpr uint32_t kKMN = 1024;          // K-major: MN-group stride (64-deep k block)
 constexpr uint32_t kMKs = 2048;          // MN-major (128 rows): K-group stride
 constexpr uint32_t kMMN = 128;           // MN-major: MN-group stride
-constexpr uint32_t kTile16 = 16384;      // 128 rows x 64 K fp16
-constexpr uint32_t kTile32 = 32768;      // 256 rows x 64 K fp16
-constexpr int kS1Stages = 4;
-constexpr uint32_t kIdesc1 = tc::idesc_f16(128, 256, 0, 0);
-constexpr uint32_t kIdesc2 = tc::idesc_f16(128, 128, 1, 0);
+constexpr uint32_t kTile16 = 16384;      // 128 rows x 64 K x 2 bytes
+constexpr int kKb2 = 4;                  // k blocks of stage 2 (box rows padded to 128: 2 x 128 / 64)
+constexpr int kMaxKb1 = 4;               // k blocks of stage 1 (box <= 128 columns)
 
 struct BigGeo {
     int N, P, bx, by;            // grid, pols, box (cells)
     int kb1;                     // k blocks of stage 1: 2 bx_pad / 64
-    int yb;                      // y blocks of 128 rows: by_pad / 128
-    int kb2;                     // k blocks of stage 2: 2 by_pad / 64
-    int lb1;                     // 128-wide l_x blocks: N / 128
-    int lb2;                     // 64-wide l blocks: N / 64
+    int lb2;                     // 64-wide l_x blocks: N / 64
+};
+
+// Per-variant constants of the two GEMM kernels.
+template <bool SP>
+struct Var {
+    static constexpr int W = SP ? 64 : 128;             // l values per tile (both stages)
+    static constexpr int NM = 2 * W;                     // MMA N (re, im)
+    static constexpr int Parts = SP ? 2 : 1;             // operand parts (hi, lo)
+    static constexpr uint32_t BTile = (uint32_t)NM * 128u;   // one k block of a DFT operand part
+    static constexpr int S1Stages = SP ? 3 : 4;
+    static constexpr int S2Stages = SP ? 3 : 6;
+    static constexpr uint32_t AStage = kTile16 * Parts;      // one k block of A (all parts)
+    static constexpr uint32_t S1Smem = (uint32_t)kMaxKb1 * BTile * Parts + S1Stages * AStage;
+    static constexpr uint32_t S2Smem = (uint32_t)kKb2 * BTile * Parts + S2Stages * AStage;
+    static constexpr uint32_t TmemCols = 2 * NM;         // double-buffered accumulator
+    static constexpr int Ly = W / 4;                     // l_y per stage-2 epilogue thread
+    static constexpr int SlotFloats = 4 * W * 64;        // one partial pixel tile
 };
 
 // ------------------------------------------------------------------ grid
 // one thread per (cell of the padded box, row-major; group of kGridFields
 // fields): the cell's entries are read once for the group and the fields'
-// voltage loads are independent, so they are in flight together.  Fields of
-// the batch are f = (c T + t - b0) P + pol.
+// voltage loads are independent, so they are in flight together.  Field f of
+// the batch is (c, t0 + s, pol) with f = (c tb + s) P + pol.
 constexpr int kGridFields = 8;
 
-__global__ void __launch_bounds__(256) big_grid_kernel(const int8_t *__restrict__ volt, int ne,
+template <bool BF, bool SP>
+__global__ void __launch_bounds__(256) big_grid_kernel(const int8_t *__restrict__ volt, int ne, int T,
                                                        const int32_t *__restrict__ cell_start,
                                                        const int32_t *__restrict__ entry_elem,
-                                                       const float2 *__restrict__ entry_w, BigGeo g, long long b0,
-                                                       long long nfield, uint8_t *__restrict__ a1) {
-    const int bxp = g.kb1 * 32, byp = g.yb * 128;
+                                                       const float2 *__restrict__ entry_w, BigGeo g, int t0,
+                                                       int tb, long long nfield, uint8_t *__restrict__ a1,
+                                                       uint8_t *__restrict__ a1lo) {
+    const int bxp = g.kb1 * 32, byp = 128;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= bxp * byp) return;
     const int x = i % bxp, y = i / bxp;
@@ -80,8 +106,15 @@ __global__ void __launch_bounds__(256) big_grid_kernel(const int8_t *__restrict_
         k0 = cell_start[y * g.bx + x];
         k1 = cell_start[y * g.bx + x + 1];
     }
-    // voltages of field f: volt + ((b0 P + f) ne) char2
-    const char2 *E = reinterpret_cast<const char2 *>(volt) + (size_t)(b0 * g.P + f0) * ne;
+    const char2 *E[kGridFields];
+#pragma unroll
+    for (int j = 0; j < kGridFields; j++) {
+        const long long f = f0 + (j < nf ? j : 0);
+        const long long ct = f / g.P;
+        const int pol = (int)(f % g.P);
+        const long long c = ct / tb, t = t0 + ct % tb;
+        E[j] = reinterpret_cast<const char2 *>(volt) + ((c * T + t) * g.P + pol) * (long long)ne;
+    }
     float2 acc[kGridFields];
 #pragma unroll
     for (int j = 0; j < kGridFields; j++) acc[j] = make_float2(0.f, 0.f);
@@ -90,7 +123,7 @@ __global__ void __launch_bounds__(256) big_grid_kernel(const int8_t *__restrict_
         const float2 w = entry_w[k];                           // conj(W~)
         char2 v[kGridFields];
 #pragma unroll
-        for (int j = 0; j < kGridFields; j++) v[j] = j < nf ? E[(size_t)j * ne + e] : make_char2(0, 0);
+        for (int j = 0; j < kGridFields; j++) v[j] = j < nf ? E[j][e] : make_char2(0, 0);
 #pragma unroll
         for (int j = 0; j < kGridFields; j++) {
             acc[j].x = fmaf(w.x, (float)v[j].x, fmaf(-w.y, (float)v[j].y, acc[j].x));
@@ -98,32 +131,47 @@ __global__ void __launch_bounds__(256) big_grid_kernel(const int8_t *__restrict_
         }
     }
     const int k = 2 * x;
-    const size_t field_bytes = (size_t)g.yb * g.kb1 * kTile16;
-    uint8_t *dst = a1 + (size_t)f0 * field_bytes + ((size_t)(y / 128) * g.kb1 + k / 64) * kTile16 +
-                   tc::off_kmajor(y % 128, k % 64, kKBytes, kKMN);
+    const size_t field_bytes = (size_t)g.kb1 * kTile16;
+    const size_t off = (size_t)f0 * field_bytes + (size_t)(k / 64) * kTile16 + tc::off_kmajor(y, k % 64, kKBytes, kKMN);
 #pragma unroll
     for (int j = 0; j < kGridFields; j++)
-        if (j < nf) *reinterpret_cast<uint32_t *>(dst + (size_t)j * field_bytes) = tc::pack_half2(acc[j].x, acc[j].y);
+        if (j < nf) {
+            if constexpr (SP) {
+                uint32_t hi, lo;
+                tc::pack2_split<BF>(acc[j].x, acc[j].y, hi, lo);
+                *reinterpret_cast<uint32_t *>(a1 + off + (size_t)j * field_bytes) = hi;
+                *reinterpret_cast<uint32_t *>(a1lo + off + (size_t)j * field_bytes) = lo;
+            } else {
+                *reinterpret_cast<uint32_t *>(a1 + off + (size_t)j * field_bytes) = tc::pack2<BF>(acc[j].x, acc[j].y);
+            }
+        }
 }
 
 // ------------------------------------------------------------------ stage 1
 struct S1Params {
-    const uint8_t *a1, *b1;
-    uint8_t *a2;
+    const uint8_t *a1, *a1lo;    // A1 (hi, lo)
+    const uint8_t *b1, *b1lo;    // DFT operand (hi, lo): [l_x block][k block] tiles
+    uint8_t *a2, *a2lo;          // stage-2 operand (hi, lo)
     BigGeo g;
-    long long b0, nfield;        // batch start (c T + t) and fields in the batch
-    long long ntiles;
+    long long nfield;            // fields in the batch
+    long long ntiles;            // (l_x block, field) tiles
     unsigned *status;
 };
 
+template <bool BF, bool SP>
 __global__ void __launch_bounds__(384, 1) big_s1_kernel(const S1Params p) {
+    using V = Var<SP>;
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t full[kS1Stages], empty[kS1Stages], dfull[2], dempty[2];
+    __shared__ __align__(8) uint64_t full[V::S1Stages], empty[V::S1Stages], dfull[2], dempty[2], bfull;
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const BigGeo g = p.g;
+    constexpr uint32_t kIdesc = tc::idesc_f16_as(BF, 128, V::NM, 0, 0);
+    const uint32_t bpart = (uint32_t)g.kb1 * V::BTile;                 // one DFT operand part of a block
+    uint8_t *sB = smem;                                                 // [part][kb1][BTile]
+    uint8_t *sA0 = smem + (size_t)kMaxKb1 * V::BTile * V::Parts;       // ring [stage][part][16 KB]
     if (tid == 0) {
-        for (int s = 0; s < kS1Stages; s++) {
+        for (int s = 0; s < V::S1Stages; s++) {
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
@@ -131,50 +179,84 @@ __global__ void __launch_bounds__(384, 1) big_s1_kernel(const S1Params p) {
             tc::mbar_init(&dfull[b], 1);
             tc::mbar_init(&dempty[b], 256);
         }
+        tc::mbar_init(&bfull, 1);
         tc::mbar_fence_init();
     }
-    if (warp == 0) tc::tmem_alloc(&tslot, 512);
+    if (warp == 0) tc::tmem_alloc(&tslot, V::TmemCols);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tslot;
-    auto sA = [&](int s) { return smem + (size_t)s * (kTile16 + kTile32); };
-    auto sB = [&](int s) { return smem + (size_t)s * (kTile16 + kTile32) + kTile16; };
-    const int per_field = g.yb * g.lb1;
+    const int lbs = g.N / V::W;
+    const long long nf = p.nfield;
+    // contiguous tile range of this CTA; tiles are (l_x block, field), field fastest
+    const long long r0 = p.ntiles * blockIdx.x / gridDim.x, r1 = p.ntiles * (blockIdx.x + 1) / gridDim.x;
     if (warp == 0) {
         if (lane == 0) {
             long long gs = 0;
-            for (long long tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
-                const long long f = tile / per_field;
-                const int r = (int)(tile % per_field), ybk = r / g.lb1, lb = r % g.lb1;
-                const uint8_t *ab = p.a1 + ((size_t)f * g.yb + ybk) * g.kb1 * kTile16;
-                const uint8_t *bb = p.b1 + (size_t)lb * g.kb1 * kTile32;
+            int cur_lb = -1;
+            for (long long tile = r0; tile < r1; tile++) {
+                const int lb = (int)(tile / nf);
+                const long long f = tile % nf;
+                if (lb != cur_lb) {
+                    // every MMA reading the old operand has completed once the
+                    // previous tile's accumulator is full
+                    const long long gt = tile - r0;
+                    if (gt > 0) tc::mbar_wait(&dfull[(gt - 1) & 1], (uint32_t)(((gt - 1) >> 1) & 1), p.status);
+                    tc::mbar_arrive_expect_tx(&bfull, bpart * V::Parts);
+                    for (int part = 0; part < V::Parts; part++) {
+                        const uint8_t *src = (part ? p.b1lo : p.b1) + (size_t)lb * bpart;
+                        tc::bulk_g2s(sB + (size_t)part * kMaxKb1 * V::BTile, src, bpart, &bfull);
+                    }
+                    cur_lb = lb;
+                }
                 for (int kb = 0; kb < g.kb1; kb++, gs++) {
-                    const int s = (int)(gs % kS1Stages);
-                    if (gs >= kS1Stages) tc::mbar_wait(&empty[s], (uint32_t)(((gs / kS1Stages) - 1) & 1), p.status);
-                    tc::mbar_arrive_expect_tx(&full[s], kTile16 + kTile32);
-                    tc::bulk_g2s(sA(s), ab + (size_t)kb * kTile16, kTile16, &full[s]);
-                    tc::bulk_g2s(sB(s), bb + (size_t)kb * kTile32, kTile32, &full[s]);
+                    const int s = (int)(gs % V::S1Stages);
+                    if (gs >= V::S1Stages)
+                        tc::mbar_wait(&empty[s], (uint32_t)(((gs / V::S1Stages) - 1) & 1), p.status);
+                    tc::mbar_arrive_expect_tx(&full[s], V::AStage);
+                    const size_t off = ((size_t)f * g.kb1 + kb) * kTile16;
+                    tc::bulk_g2s(sA0 + (size_t)s * V::AStage, p.a1 + off, kTile16, &full[s]);
+                    if constexpr (SP) tc::bulk_g2s(sA0 + (size_t)s * V::AStage + kTile16, p.a1lo + off, kTile16, &full[s]);
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            long long gs = 0, gt = 0;
-            for (long long tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, gt++) {
+            long long gs = 0;
+            int cur_lb = -1;
+            uint32_t bph = 0;
+            for (long long tile = r0; tile < r1; tile++) {
+                const long long gt = tile - r0;
+                const int lb = (int)(tile / nf);
+                if (lb != cur_lb) {
+                    tc::mbar_wait(&bfull, bph & 1, p.status);
+                    bph++;
+                    cur_lb = lb;
+                }
                 const int b = (int)(gt & 1);
                 if (gt >= 2) tc::mbar_wait(&dempty[b], (uint32_t)(((gt >> 1) - 1) & 1), p.status);
                 tc::fence_after();
-                const uint32_t d = tmem + (uint32_t)b * 256u;
+                const uint32_t d = tmem + (uint32_t)b * V::NM;
                 for (int kb = 0; kb < g.kb1; kb++, gs++) {
-                    const int s = (int)(gs % kS1Stages);
-                    tc::mbar_wait(&full[s], (uint32_t)((gs / kS1Stages) & 1), p.status);
+                    const int s = (int)(gs % V::S1Stages);
+                    tc::mbar_wait(&full[s], (uint32_t)((gs / V::S1Stages) & 1), p.status);
                     tc::fence_after();
-                    const uint32_t a = tc::smem_u32(sA(s)), bq = tc::smem_u32(sB(s));
+                    const uint32_t a = tc::smem_u32(sA0 + (size_t)s * V::AStage);
+                    const uint32_t bq = tc::smem_u32(sB + (size_t)kb * V::BTile);
 #pragma unroll
-                    for (int j = 0; j < 4; j++)
-                        tc::mma_f16(d, tc::desc(a + j * 2 * kKBytes, kKBytes, kKMN),
-                                    tc::desc(bq + j * 2 * kKBytes, kKBytes, kKMN), kIdesc1, (kb > 0 || j > 0) ? 1u : 0u);
+                    for (int j = 0; j < 4; j++) {
+                        const uint32_t acc0 = (kb > 0 || j > 0) ? 1u : 0u;
+                        const uint64_t da = tc::desc(a + j * 2 * kKBytes, kKBytes, kKMN);
+                        const uint64_t db = tc::desc(bq + j * 2 * kKBytes, kKBytes, kKMN);
+                        tc::mma_f16(d, da, db, kIdesc, acc0);
+                        if constexpr (SP) {
+                            const uint64_t dal = tc::desc(a + kTile16 + j * 2 * kKBytes, kKBytes, kKMN);
+                            const uint64_t dbl = tc::desc(bq + kMaxKb1 * V::BTile + j * 2 * kKBytes, kKBytes, kKMN);
+                            tc::mma_f16(d, da, dbl, kIdesc, 1u);
+                            tc::mma_f16(d, dal, db, kIdesc, 1u);
+                        }
+                    }
                     tc::mma_commit(&empty[s]);
                 }
                 tc::mma_commit(&dfull[b]);
@@ -182,44 +264,55 @@ __global__ void __launch_bounds__(384, 1) big_s1_kernel(const S1Params p) {
         }
     } else if (warp >= 4) {
         // epilogue, warps 4-11: thread = row y of the tile and one half (h) of
-        // its 128 (re, im) values -> the stage-2 operand rows (l_x, pol), K
-        // index 2 y + re/im
-        const int q = warp & 3, row = q * 32 + lane, h = (warp - 4) >> 2;
+        // its W1 l_x -> the stage-2 operand rows (l_x, pol), K index 2 y + re/im
+        const int q = warp & 3, y = q * 32 + lane, h = (warp - 4) >> 2;
+        const int kb2 = (2 * y) / 64, kk = (2 * y) % 64;   // K of the real part; imag at kk + 1
+        constexpr int kChunks = V::W / 32;                   // 16 l_x per chunk, per half
         long long gt = 0;
-        for (long long tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, gt++) {
+        for (long long tile = r0; tile < r1; tile++, gt++) {
             const int b = (int)(gt & 1);
-            const long long f = tile / per_field;
-            const int r = (int)(tile % per_field), ybk = r / g.lb1, lb = r % g.lb1;
+            const int lb = (int)(tile / nf);
+            const long long f = tile % nf;
             const int pol = (int)(f % g.P);
-            const long long ct = f / g.P;                       // (c, t) in the batch
-            const int y = ybk * 128 + row;
-            const int kr = 2 * y, kb2 = kr / 64, kk = kr % 64;  // K of the real part; imag at kk + 1
+            const long long ct = f / g.P;                       // (c, s) of the batch
             tc::mbar_wait(&dfull[b], (uint32_t)((gt >> 1) & 1), p.status);
             tc::fence_after();
 #pragma unroll 1
-            for (int ch = 4 * h; ch < 4 * h + 4; ch++) {       // 16 l_x values per chunk
+            for (int ch = kChunks * h; ch < kChunks * h + kChunks; ch++) {
                 uint32_t rr[16], ri[16];
-                tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * 256u + (uint32_t)(16 * ch), rr);
-                tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * 256u + 128u + (uint32_t)(16 * ch), ri);
+                const uint32_t t0 = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * V::NM + (uint32_t)(16 * ch);
+                tc::tmem_ld16(t0, rr);
+                tc::tmem_ld16(t0 + V::W, ri);
                 tc::tmem_wait_ld();
-                const int lx = lb * 128 + 16 * ch;             // first l_x of the chunk
+                const int lx = lb * V::W + 16 * ch;             // first l_x of the chunk
                 const int lxb = lx / 64, lx64 = lx % 64;
-                uint8_t *tile2 = p.a2 + (((size_t)ct * g.lb2 + lxb) * g.kb2 + kb2) * kTile16;
+                const size_t toff = (((size_t)ct * g.lb2 + lxb) * kKb2 + kb2) * kTile16;
                 // rows (l_x, pol): m = (l_x >> 4) 32 + pol 16 + (l_x & 15)
                 const int m0 = (lx64 >> 4) * 32 + pol * 16;
 #pragma unroll
                 for (int half = 0; half < 2; half++) {          // 8 l_x -> one 16-byte run per K value
-                    uint32_t hr[4], hi[4];
+                    uint32_t hr[4], hi[4], lr[4], li[4];
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
-                        hr[e] = tc::pack_half2(__uint_as_float(rr[8 * half + 2 * e]), __uint_as_float(rr[8 * half + 2 * e + 1]));
-                        hi[e] = tc::pack_half2(__uint_as_float(ri[8 * half + 2 * e]), __uint_as_float(ri[8 * half + 2 * e + 1]));
+                        const float a0 = __uint_as_float(rr[8 * half + 2 * e]), a1v = __uint_as_float(rr[8 * half + 2 * e + 1]);
+                        const float b0 = __uint_as_float(ri[8 * half + 2 * e]), b1v = __uint_as_float(ri[8 * half + 2 * e + 1]);
+                        if constexpr (SP) {
+                            tc::pack2_split<BF>(a0, a1v, hr[e], lr[e]);
+                            tc::pack2_split<BF>(b0, b1v, hi[e], li[e]);
+                        } else {
+                            hr[e] = tc::pack2<BF>(a0, a1v);
+                            hi[e] = tc::pack2<BF>(b0, b1v);
+                        }
                     }
                     const int m = m0 + 8 * half;
-                    *reinterpret_cast<uint4 *>(tile2 + tc::off_mnmajor(m, kk, kMKs, kMMN)) =
-                        make_uint4(hr[0], hr[1], hr[2], hr[3]);
-                    *reinterpret_cast<uint4 *>(tile2 + tc::off_mnmajor(m, kk + 1, kMKs, kMMN)) =
-                        make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    const size_t o_r = toff + tc::off_mnmajor(m, kk, kMKs, kMMN);
+                    const size_t o_i = toff + tc::off_mnmajor(m, kk + 1, kMKs, kMMN);
+                    *reinterpret_cast<uint4 *>(p.a2 + o_r) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+                    *reinterpret_cast<uint4 *>(p.a2 + o_i) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    if constexpr (SP) {
+                        *reinterpret_cast<uint4 *>(p.a2lo + o_r) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+                        *reinterpret_cast<uint4 *>(p.a2lo + o_i) = make_uint4(li[0], li[1], li[2], li[3]);
+                    }
                 }
             }
             tc::fence_before();
@@ -229,200 +322,269 @@ __global__ void __launch_bounds__(384, 1) big_s1_kernel(const S1Params p) {
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if (warp == 0) tc::tmem_dealloc(tmem, V::TmemCols);
 }
 
 // ------------------------------------------------------------------ stage 2
 struct S2Params {
-    const uint8_t *a2, *b2;
+    const uint8_t *a2, *a2lo;    // stage-2 operand (hi, lo) of the batch
+    const uint8_t *b2, *b2lo;    // DFT operand (hi, lo): [l_y block][k block] tiles
     float *img;
+    float *slots;                // one partial pixel tile per CTA
     BigGeo g;
-    long long b0, b1;            // batch range of c T + t
-    int T, c_first, n_items;     // items: (channel - c_first, l_x block, l_y block)
-    int accumulate;
+    int C, tb;                   // channels, samples of the batch
+    long long units;             // items x tb
+    int add;                     // 1: the head part adds to the image (accumulate or a later batch)
     unsigned *status;
 };
 
-constexpr int kS2Threads = 384;             // warp 0 loads, warp 1 MMA, warps 4-11 epilogue
-constexpr int kS2Kb = 4;                    // k blocks of stage 2 (boxes <= 128 rows: 2 x 128 / 64)
-constexpr int kS2Epi = 256;
+// Unit range of CTA k of G over U units: [U k / G, U (k + 1) / G).
+__host__ __device__ __forceinline__ long long unit_start(long long U, int G, int k) { return U * k / G; }
 
-__global__ void __launch_bounds__(kS2Threads, 1) big_s2_kernel(const S2Params p) {
+template <bool BF, bool SP>
+__global__ void __launch_bounds__(576, 1) big_s2_kernel(const S2Params p) {
+    using V = Var<SP>;
     extern __shared__ __align__(1024) uint8_t smem[];
-    // sdone[b]: every MMA of the sample in A buffer / accumulator b has completed
-    // (one commit per sample: the loader may refill A buffer b, the epilogue
-    // may read accumulator b)
-    __shared__ __align__(8) uint64_t bfull, afull[2], sdone[2], dempty[2];
+    __shared__ __align__(8) uint64_t bfull, afull[V::S2Stages], aempty[V::S2Stages], dfull[2], dempty[2];
     __shared__ uint32_t tslot;
+    constexpr int kEpi = 512;                               // 16 epilogue warps
+    constexpr uint32_t kIdesc = tc::idesc_f16_as(BF, 128, V::NM, 1, 0);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const BigGeo g = p.g;
-    const uint32_t abytes = (uint32_t)g.kb2 * kTile16;     // one sample's A2 for a 64-wide l_x block
-    uint8_t *sB = smem;                                      // [kb2][16 KB]
-    auto sA = [&](int s) { return smem + abytes + (size_t)s * abytes; };
+    uint8_t *sB = smem;                                                  // [part][kb2][BTile]
+    uint8_t *sA0 = smem + (size_t)kKb2 * V::BTile * V::Parts;           // ring [stage][part][16 KB]
     if (tid == 0) {
         tc::mbar_init(&bfull, 1);
+        for (int s = 0; s < V::S2Stages; s++) {
+            tc::mbar_init(&afull[s], 1);
+            tc::mbar_init(&aempty[s], 1);
+        }
         for (int b = 0; b < 2; b++) {
-            tc::mbar_init(&afull[b], 1);
-            tc::mbar_init(&sdone[b], 1);
-            tc::mbar_init(&dempty[b], kS2Epi);
+            tc::mbar_init(&dfull[b], 1);
+            tc::mbar_init(&dempty[b], kEpi);
         }
         tc::mbar_fence_init();
     }
-    if (warp == 0) tc::tmem_alloc(&tslot, 256);
+    if (warp == 0) tc::tmem_alloc(&tslot, V::TmemCols);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tslot;
-    const int per_chan = g.lb2 * g.lb2;
-    // samples of channel c in the batch
-    auto trange = [&](int c, int &t0, int &t1) {
-        const long long lo = (long long)c * p.T, hi = lo + p.T;
-        t0 = (int)(max(p.b0, lo) - lo);
-        t1 = (int)(min(p.b1, hi) - lo);
-    };
+    const int per_lyb = p.C * g.lb2;                       // items per l_y block
+    const int tb = p.tb;
+    const long long u0 = unit_start(p.units, gridDim.x, blockIdx.x);
+    const long long u1 = unit_start(p.units, gridDim.x, blockIdx.x + 1);
+    const uint32_t bbytes = (uint32_t)kKb2 * V::BTile;     // one DFT operand part of an l_y block
     if (warp == 0) {
         if (lane == 0) {
-            long long gs = 0;
+            long long gs = 0, gk = 0;                      // samples and k blocks loaded
             int cur_lyb = -1;
-            uint32_t bphase = 0;
-            for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
-                const int c = p.c_first + it / per_chan, r = it % per_chan, lxb = r / g.lb2, lyb = r % g.lb2;
+            for (long long u = u0; u < u1;) {
+                const long long it = u / tb;
+                const int s0 = (int)(u % tb), s1 = (int)std::min<long long>(tb, s0 + (u1 - u));
+                const int lyb = (int)(it / per_lyb), rem = (int)(it % per_lyb), c = rem / g.lb2, lxb = rem % g.lb2;
                 if (lyb != cur_lyb) {
-                    // the previous item's MMAs have all completed once its last A stage is released
-                    if (gs > 0) tc::mbar_wait(&sdone[(gs - 1) & 1], (uint32_t)(((gs - 1) >> 1) & 1), p.status);
-                    tc::mbar_arrive_expect_tx(&bfull, abytes);
-                    tc::bulk_g2s(sB, p.b2 + (size_t)lyb * abytes, abytes, &bfull);
+                    // every MMA reading the old operand has completed once the
+                    // last sample's accumulator is full
+                    if (gs > 0) tc::mbar_wait(&dfull[(gs - 1) & 1], (uint32_t)(((gs - 1) >> 1) & 1), p.status);
+                    tc::mbar_arrive_expect_tx(&bfull, bbytes * V::Parts);
+                    for (int part = 0; part < V::Parts; part++)
+                        tc::bulk_g2s(sB + (size_t)part * bbytes, (part ? p.b2lo : p.b2) + (size_t)lyb * bbytes, bbytes,
+                                     &bfull);
                     cur_lyb = lyb;
-                    bphase++;
                 }
-                int t0, t1;
-                trange(c, t0, t1);
-                for (int t = t0; t < t1; t++, gs++) {
-                    const int s = (int)(gs & 1);
-                    if (gs >= 2) tc::mbar_wait(&sdone[s], (uint32_t)(((gs >> 1) - 1) & 1), p.status);
-                    const long long ct = (long long)c * p.T + t - p.b0;
-                    tc::mbar_arrive_expect_tx(&afull[s], abytes);
-                    tc::bulk_g2s(sA(s), p.a2 + ((size_t)ct * g.lb2 + lxb) * abytes, abytes, &afull[s]);
+                for (int s = s0; s < s1; s++, gs++) {
+                    const size_t base = (((size_t)c * tb + s) * g.lb2 + lxb) * kKb2 * kTile16;
+                    for (int kb = 0; kb < kKb2; kb++, gk++) {
+                        const int st = (int)(gk % V::S2Stages);
+                        if (gk >= V::S2Stages)
+                            tc::mbar_wait(&aempty[st], (uint32_t)(((gk / V::S2Stages) - 1) & 1), p.status);
+                        tc::mbar_arrive_expect_tx(&afull[st], V::AStage);
+                        tc::bulk_g2s(sA0 + (size_t)st * V::AStage, p.a2 + base + (size_t)kb * kTile16, kTile16, &afull[st]);
+                        if constexpr (SP)
+                            tc::bulk_g2s(sA0 + (size_t)st * V::AStage + kTile16, p.a2lo + base + (size_t)kb * kTile16,
+                                         kTile16, &afull[st]);
+                    }
                 }
+                u += s1 - s0;
             }
         }
     } else if (warp == 1) {
-        // one thread issues 16 MMAs per sample (4 k blocks x 4), one commit;
-        // descriptors advance by additions to their 14-bit address field
+        // one thread issues the MMAs: per k block 4 K-steps (x 3 products when
+        // split), one commit per k block (frees the A stage) and one per sample
+        // (fills the accumulator)
         if (lane == 0) {
-            long long gs = 0;
+            long long gs = 0, gk = 0;
             int cur_lyb = -1;
             uint32_t bph = 0;
-            const uint64_t db0 = tc::desc(tc::smem_u32(sB), kKBytes, kKMN);
-            const uint64_t da0 = tc::desc(tc::smem_u32(sA(0)), kMKs, kMMN);
-            const uint64_t kBufD = abytes >> 4, kKbD = kTile16 >> 4, kStepA = (2 * kMKs) >> 4, kStepB = (2 * kKBytes) >> 4;
-            for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
-                const int c = p.c_first + it / per_chan, r = it % per_chan, lyb = r % g.lb2;
+            const uint32_t sb0 = tc::smem_u32(sB), sa0 = tc::smem_u32(sA0);
+            for (long long u = u0; u < u1;) {
+                const long long it = u / tb;
+                const int s0 = (int)(u % tb), s1 = (int)std::min<long long>(tb, s0 + (u1 - u));
+                const int lyb = (int)(it / per_lyb);
                 if (lyb != cur_lyb) {
                     tc::mbar_wait(&bfull, bph & 1, p.status);
                     bph++;
                     cur_lyb = lyb;
                 }
-                int t0, t1;
-                trange(c, t0, t1);
-                for (int t = t0; t < t1; t++, gs++) {
-                    const int s = (int)(gs & 1);
-                    const uint32_t ph = (uint32_t)((gs >> 1) & 1);
-                    if (gs >= 2) tc::mbar_wait(&dempty[s], ph ^ 1u, p.status);
-                    tc::mbar_wait(&afull[s], ph, p.status);
+                for (int s = s0; s < s1; s++, gs++) {
+                    const int b = (int)(gs & 1);
+                    if (gs >= 2) tc::mbar_wait(&dempty[b], (uint32_t)(((gs >> 1) - 1) & 1), p.status);
                     tc::fence_after();
-                    const uint64_t da = da0 + (uint64_t)s * kBufD;
-                    const uint32_t d = tmem + (uint32_t)s * 128u;
+                    const uint32_t d = tmem + (uint32_t)b * V::NM;
+                    for (int kb = 0; kb < kKb2; kb++, gk++) {
+                        const int st = (int)(gk % V::S2Stages);
+                        tc::mbar_wait(&afull[st], (uint32_t)((gk / V::S2Stages) & 1), p.status);
+                        tc::fence_after();
+                        const uint32_t a = sa0 + (uint32_t)st * V::AStage;
+                        const uint32_t bq = sb0 + (uint32_t)kb * V::BTile;
 #pragma unroll
-                    for (int kb = 0; kb < kS2Kb; kb++)
-#pragma unroll
-                        for (int j = 0; j < 4; j++)
-                            tc::mma_f16(d, da + kb * kKbD + j * kStepA, db0 + kb * kKbD + j * kStepB, kIdesc2,
-                                        (kb > 0 || j > 0) ? 1u : 0u);
-                    tc::mma_commit(&sdone[s]);
+                        for (int j = 0; j < 4; j++) {
+                            const uint32_t acc0 = (kb > 0 || j > 0) ? 1u : 0u;
+                            const uint64_t da = tc::desc(a + j * 2 * kMKs, kMKs, kMMN);
+                            const uint64_t db = tc::desc(bq + j * 2 * kKBytes, kKBytes, kKMN);
+                            tc::mma_f16(d, da, db, kIdesc, acc0);
+                            if constexpr (SP) {
+                                const uint64_t dal = tc::desc(a + kTile16 + j * 2 * kMKs, kMKs, kMMN);
+                                const uint64_t dbl = tc::desc(bq + bbytes + j * 2 * kKBytes, kKBytes, kKMN);
+                                tc::mma_f16(d, da, dbl, kIdesc, 1u);
+                                tc::mma_f16(d, dal, db, kIdesc, 1u);
+                            }
+                        }
+                        tc::mma_commit(&aempty[st]);
+                    }
+                    tc::mma_commit(&dfull[b]);
                 }
+                u += s1 - s0;
             }
         }
-    } else if (warp >= 4) {
-        // epilogue: the N = 64 tile epilogue of the small-grid kernel: thread
-        // row m = (l_x, pol), half h of the 64 l_y
-        const int q = warp & 3, h = (warp - 4) >> 2;
+    } else if (warp >= 2) {
+        // epilogue, warps 2-17: thread row m = (l_x, pol) of TMEM lane
+        // quadrant q, group h of Ly l_y values
+        const int ew = warp - 2, q = warp & 3, h = ew >> 2;
         const int m = 32 * q + lane;
         const int pol = (m >> 4) & 1, kx = (m >> 5) * 16 + (m & 15);
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        constexpr int kLy = 32;
+        constexpr int kLy = V::Ly;
         const size_t NN = (size_t)g.N * g.N;
         float2 acc_a[kLy / 2], acc_x[kLy / 2];
         long long gs = 0;
-        for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
-            const int c = p.c_first + it / per_chan, r = it % per_chan, lxb = r / g.lb2, lyb = r % g.lb2;
+        for (long long u = u0; u < u1;) {
+            const long long it = u / tb;
+            const int s0 = (int)(u % tb), s1 = (int)std::min<long long>(tb, s0 + (u1 - u));
+            const int lyb = (int)(it / per_lyb), rem = (int)(it % per_lyb), c = rem / g.lb2, lxb = rem % g.lb2;
 #pragma unroll
             for (int t = 0; t < kLy / 2; t++) acc_a[t] = acc_x[t] = make_float2(0.f, 0.f);
-            int t0, t1;
-            trange(c, t0, t1);
-            for (int t = t0; t < t1; t++, gs++) {
-                const int s = (int)(gs & 1);
-                tc::mbar_wait(&sdone[s], (uint32_t)((gs >> 1) & 1), p.status);
+            for (int s = s0; s < s1; s++, gs++) {
+                const int b = (int)(gs & 1);
+                tc::mbar_wait(&dfull[b], (uint32_t)((gs >> 1) & 1), p.status);
                 tc::fence_after();
+                // 8 l_y at a time (re and im: 16 registers): the pixel pairs
+                // (2k, 2k + 1) of the cross term stay inside each group
 #pragma unroll
-                for (int cc = 0; cc < 2; cc++) {
-                    const uint32_t col = (uint32_t)s * 128u + (uint32_t)(kLy * h + 16 * cc);
-                    uint32_t rr[16], ri[16];
-                    tc::tmem_ld16(tmem + lane_base + col, rr);
-                    tc::tmem_ld16(tmem + lane_base + col + 64, ri);
+                for (int g8 = 0; g8 < kLy / 8; g8++) {
+                    const uint32_t col = (uint32_t)b * V::NM + (uint32_t)(kLy * h + 8 * g8);
+                    uint32_t rr[8], ri[8];
+                    tc::tmem_ld8(tmem + lane_base + col, rr);
+                    tc::tmem_ld8(tmem + lane_base + col + V::W, ri);
                     tc::tmem_wait_ld();
 #pragma unroll
-                    for (int k = 0; k < 16; k += 2) {
+                    for (int k = 0; k < 8; k += 2) {
                         const float2 fr = make_float2(__uint_as_float(rr[k]), __uint_as_float(rr[k + 1]));
                         const float2 fi = make_float2(__uint_as_float(ri[k]), __uint_as_float(ri[k + 1]));
-                        float2 &a = acc_a[(16 * cc + k) >> 1];
+                        float2 &a = acc_a[(8 * g8 + k) >> 1];
                         a = __ffma2_rn(fr, fr, __ffma2_rn(fi, fi, a));
                     }
 #pragma unroll
-                    for (int k = 0; k < 8; k++) {
+                    for (int k = 0; k < 4; k++) {
                         const float e_r = __uint_as_float(rr[2 * k]), e_i = __uint_as_float(ri[2 * k]);
                         const float o_r = __uint_as_float(rr[2 * k + 1]), o_i = __uint_as_float(ri[2 * k + 1]);
                         const float mr = pol ? o_r : e_r, mi = pol ? o_i : e_i;
                         const float sr = __shfl_xor_sync(0xffffffffu, pol ? e_r : o_r, 16);
                         const float si = __shfl_xor_sync(0xffffffffu, pol ? e_i : o_i, 16);
-                        float2 &a = acc_x[8 * cc + k];
+                        float2 &a = acc_x[4 * g8 + k];
                         a = __ffma2_rn(make_float2(mr, mi), make_float2(sr, sr),
                                        __ffma2_rn(make_float2(mi, -mr), make_float2(si, si), a));
                     }
                 }
                 tc::fence_before();
-                tc::mbar_arrive(&dempty[s]);
+                tc::mbar_arrive(&dempty[b]);
             }
-            // write the pixel tile (image planes XX, YY, Re XY, Im XY of channel c)
-            const bool add = p.accumulate || t0 > 0;
-            float *dst = p.img + (size_t)c * 4 * NN;
-            const int px = lxb * 64 + kx;
+            // the part's pixel tile: planes XX, YY, Re XY, Im XY of channel c,
+            // to the image (the item's first sample is here) or to this CTA's slot
+            const bool head = s0 == 0;
+            float *dst;
+            size_t rs, ps;
+            bool add;
+            if (head) {
+                dst = p.img + (size_t)c * 4 * NN + (size_t)lyb * V::W * g.N + (size_t)lxb * 64;
+                rs = g.N;
+                ps = NN;
+                add = p.add != 0;
+            } else {
+                dst = p.slots + (size_t)blockIdx.x * V::SlotFloats;
+                rs = 64;
+                ps = (size_t)V::W * 64;
+                add = false;
+            }
 #pragma unroll
             for (int t = 0; t < kLy; t++) {
-                const size_t idx = pol * NN + (size_t)(lyb * 64 + kLy * h + t) * g.N + px;
+                float *d = dst + pol * ps + (size_t)(kLy * h + t) * rs + kx;
                 float v = (t & 1) ? acc_a[t >> 1].y : acc_a[t >> 1].x;
-                if (add) v += dst[idx];
-                dst[idx] = v;
+                if (add) v += *d;
+                *d = v;
             }
             const float sgn = pol ? -1.f : 1.f;
 #pragma unroll
             for (int t = 0; t < kLy / 2; t++) {
                 const int ly = kLy * h + 16 * (t >> 3) + 2 * (t & 7) + pol;
-                const size_t idx = 2 * NN + (size_t)(lyb * 64 + ly) * g.N + px;
+                float *d = dst + 2 * ps + (size_t)ly * rs + kx;
                 float vr = acc_x[t].x, vi = sgn * acc_x[t].y;
                 if (add) {
-                    vr += dst[idx];
-                    vi += dst[idx + NN];
+                    vr += d[0];
+                    vi += d[ps];
                 }
-                dst[idx] = vr;
-                dst[idx + NN] = vi;
+                d[0] = vr;
+                d[ps] = vi;
             }
+            u += s1 - s0;
         }
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+    if (warp == 0) tc::tmem_dealloc(tmem, V::TmemCols);
+}
+
+// ------------------------------------------------------------------ fixup
+// Block k: if CTA k's range begins inside an item and CTA k - 1's range does
+// not begin inside the same item, CTA k is that item's first partial: add the
+// slots of k, k + 1, ... (every CTA whose range begins inside the item) to
+// the item's image tile, in CTA order.
+template <int W>
+__global__ void __launch_bounds__(256) big_fixup_kernel(const float *__restrict__ slots, float *__restrict__ img,
+                                                        BigGeo g, int C, int tb, long long units, int G) {
+    const int k = blockIdx.x;
+    auto tail_item = [&](int j) -> long long {            // item whose middle CTA j's range begins in, or -1
+        if (j <= 0 || j >= G) return -1;
+        const long long a = unit_start(units, G, j), b = unit_start(units, G, j + 1);
+        return (a < b && a % tb != 0) ? a / tb : -1;
+    };
+    const long long it = tail_item(k);
+    if (it < 0 || tail_item(k - 1) == it) return;
+    int k1 = k + 1;
+    while (tail_item(k1) == it) k1++;
+    const int per_lyb = C * g.lb2;
+    const int lyb = (int)(it / per_lyb), rem = (int)(it % per_lyb), c = rem / g.lb2, lxb = rem % g.lb2;
+    const size_t NN = (size_t)g.N * g.N;
+    constexpr int kSlot = 4 * W * 64;
+    float *dst = img + (size_t)c * 4 * NN + (size_t)lyb * W * g.N + (size_t)lxb * 64;
+    for (int e = threadIdx.x; e < kSlot; e += blockDim.x) {
+        const int plane = e / (W * 64), r = e % (W * 64), ly = r / 64, lx = r % 64;
+        float s = 0.f;
+        for (int j = k; j < k1; j++) s += slots[(size_t)j * kSlot + e];
+        dst[plane * NN + (size_t)ly * g.N + lx] += s;
+    }
 }
 
 BigGeo big_geo(const hai_layout *L) {
@@ -432,18 +594,22 @@ BigGeo big_geo(const hai_layout *L) {
     g.bx = L->box_w;
     g.by = L->box_h;
     g.kb1 = (2 * g.bx + 63) / 64;
-    g.yb = (g.by + 127) / 128;
-    g.kb2 = g.yb * 4;                                // 2 * by_pad / 64
-    g.lb1 = g.N / 128;
     g.lb2 = g.N / 64;
     return g;
 }
 
 // W'[j][l] = (-1)^j exp(+2 pi i l j / N), FP64, as the K-major operand rows
-// (c_out, l) over K = (j, c_in): [[Wr, -Wi], [Wi, Wr]]
-void dft_operand(int N, int jpad, int lblock, std::vector<uint16_t> &out) {
+// (c_out, l) over K = (j, c_in): [[Wr, -Wi], [Wi, Wr]], in blocks of `lblock`
+// l values, rounded to FP16 or BF16 (part 0) or the remainder after that
+// rounding rounded again (part 1, the lo part of the split operand).
+template <typename H>
+uint16_t bits16(H h) {
+    return *reinterpret_cast<const uint16_t *>(&h);
+}
+
+void dft_operand(int N, int jpad, int lblock, bool bf16, int part, std::vector<uint16_t> &out) {
     const int kb = 2 * jpad / 64, nblk = N / lblock;
-    const uint32_t tile = (uint32_t)(2 * lblock) * 128u;     // rows x 64 K fp16
+    const uint32_t tile = (uint32_t)(2 * lblock) * 128u;     // rows x 64 K x 2 bytes
     out.assign((size_t)nblk * kb * tile / 2, 0);
     for (int b = 0; b < nblk; b++)
         for (int co = 0; co < 2; co++)
@@ -457,11 +623,115 @@ void dft_operand(int N, int jpad, int lblock, std::vector<uint16_t> &out) {
                         const double v = co == 0 ? (ci == 0 ? wr : -wi) : (ci == 0 ? wi : wr);
                         const int k = 2 * j + ci;
                         const size_t off = ((size_t)b * kb + k / 64) * tile + tc::off_kmajor(row, k % 64, kKBytes, kKMN);
-                        const __half h = __float2half_rn((float)v);
-                        out[off / 2] = *reinterpret_cast<const uint16_t *>(&h);
+                        uint16_t h, r;
+                        if (bf16) {
+                            const __nv_bfloat16 hi = __float2bfloat16_rn((float)v);
+                            h = bits16(hi);
+                            r = bits16(__float2bfloat16_rn((float)(v - (double)__bfloat162float(hi))));
+                        } else {
+                            const __half hi = __float2half_rn((float)v);
+                            h = bits16(hi);
+                            r = bits16(__float2half_rn((float)(v - (double)__half2float(hi))));
+                        }
+                        out[off / 2] = part ? r : h;
                     }
                 }
             }
+}
+
+// Index of the (bf16, split) variant: 0 fp16, 1 bf16, 2 fp16 split, 3 bf16 split.
+int variant(hai_precision prec) {
+    switch (prec) {
+        case HAI_PREC_FP16: return 0;
+        case HAI_PREC_BF16: return 1;
+        case HAI_PREC_FP16_SPLIT: return 2;
+        case HAI_PREC_BF16_SPLIT: return 3;
+        default: return -1;
+    }
+}
+
+template <bool BF, bool SP>
+hai_status launch_variant(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
+                          cudaStream_t st) {
+    using V = Var<SP>;
+    hai_ctx *ctx = L->ctx;
+    const BigGeo g = big_geo(L);
+    const int vi = (BF ? 1 : 0) + (SP ? 2 : 0);
+    if (V::S1Smem > (uint32_t)ctx->smem_optin - 1024 || V::S2Smem > (uint32_t)ctx->smem_optin - 1024)
+        return hai_fail(HAI_ERR_UNSUPPORTED, "epic tensor cores (large grid): shared memory");
+    HAI_CUDA_TRY(hai_allow_dyn_smem(big_s1_kernel<BF, SP>, ctx->smem_optin));
+    HAI_CUDA_TRY(hai_allow_dyn_smem(big_s2_kernel<BF, SP>, ctx->smem_optin));
+    // the scratch holds big_batch (channel, sample) pairs of plain operands,
+    // half as many split ones: channels in chunks of at most that many, and
+    // per chunk batches of as many samples of every channel as fit
+    const long long pairs = std::max<long long>(1, L->big_batch / V::Parts);
+    const int cb_max = (int)std::min<long long>(C, pairs);
+    const size_t a1_bytes = (size_t)L->big_batch * g.P * g.kb1 * kTile16;   // plain capacity of A1 (hi + lo when split)
+    uint8_t *a1 = static_cast<uint8_t *>(L->big_a1), *a2 = static_cast<uint8_t *>(L->big_a2);
+    const size_t a1_half = a1_bytes / 2, a2_half = (size_t)L->big_batch * g.lb2 * kKb2 * kTile16 / 2;
+    uint8_t *a1lo = SP ? a1 + a1_half : nullptr, *a2lo = SP ? a2 + a2_half : nullptr;
+    const int G1 = ctx->num_sms, G2 = ctx->num_sms;
+    int launches = 0;
+    const size_t NN = (size_t)g.N * g.N;
+    for (int c0 = 0; c0 < C; c0 += cb_max) {
+    const int Cc = std::min(cb_max, C - c0);
+    const int8_t *vc = volt + (size_t)c0 * T * g.P * L->n_elem * 2;
+    float *ic = img + (size_t)c0 * 4 * NN;
+    const int tb_max = (int)std::max<long long>(1, std::min<long long>(T, pairs / Cc));
+    for (int t0 = 0; t0 < T; t0 += tb_max) {
+        const int tb = std::min(tb_max, T - t0);
+        const long long nfield = (long long)Cc * tb * g.P;
+        const int ncell = (g.kb1 * 32) * 128;
+        big_grid_kernel<BF, SP><<<dim3((ncell + 255) / 256, (unsigned)((nfield + kGridFields - 1) / kGridFields)), 256,
+                                  0, st>>>(vc, L->n_elem, T, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g, t0,
+                                           tb, nfield, a1, a1lo);
+        S1Params p1;
+        p1.a1 = a1;
+        p1.a1lo = a1lo;
+        p1.b1 = static_cast<const uint8_t *>(L->big_b1[vi][0]);
+        p1.b1lo = static_cast<const uint8_t *>(L->big_b1[vi][1]);
+        p1.a2 = a2;
+        p1.a2lo = a2lo;
+        p1.g = g;
+        p1.nfield = nfield;
+        p1.ntiles = nfield * (g.N / V::W);
+        p1.status = ctx->d_status;
+        big_s1_kernel<BF, SP><<<(unsigned)std::min<long long>(p1.ntiles, G1), 384, V::S1Smem, st>>>(p1);
+        S2Params p2;
+        p2.a2 = a2;
+        p2.a2lo = a2lo;
+        p2.b2 = static_cast<const uint8_t *>(L->big_b2[vi][0]);
+        p2.b2lo = static_cast<const uint8_t *>(L->big_b2[vi][1]);
+        p2.img = ic;
+        p2.slots = static_cast<float *>(L->big_slots);
+        p2.g = g;
+        p2.C = Cc;
+        p2.tb = tb;
+        const long long items = (long long)(g.N / V::W) * Cc * g.lb2;
+        p2.units = items * tb;
+        p2.add = (accumulate || t0 > 0) ? 1 : 0;
+        p2.status = ctx->d_status;
+        const int G = (int)std::min<long long>(p2.units, G2);
+        // the profiled (dominant) kernel of this path: every stage-2 launch
+        const int pidx = prof_begin(ctx, st);
+        big_s2_kernel<BF, SP><<<(unsigned)G, 576, V::S2Smem, st>>>(p2);
+        prof_end(ctx, pidx, st);
+        launches += 3;
+        // items split between CTAs: their later parts were left in the slots
+        bool split_items = false;
+        for (int k = 1; k < G && !split_items; k++) {
+            const long long a = unit_start(p2.units, G, k), b = unit_start(p2.units, G, k + 1);
+            split_items = a < b && a % tb != 0;
+        }
+        if (split_items) {
+            big_fixup_kernel<V::W><<<(unsigned)G, 256, 0, st>>>(p2.slots, ic, g, Cc, tb, p2.units, G);
+            launches++;
+        }
+    }
+    }
+    prof_count(ctx, launches);
+    HAI_CUDA_TRY(cudaGetLastError());
+    return HAI_OK;
 }
 
 }  // namespace
@@ -471,81 +741,63 @@ bool epic_big_supported(const hai_layout *L) {
            L->box_h <= std::min(128, L->grid_n / 2);
 }
 
-// Per layout: the two DFT operands and the batch scratch (A1 and A2).
+// Per layout: the DFT operands of every variant (plain W = 128 blocks, split
+// hi and lo W = 64 blocks, FP16 and BF16), the batch scratch (A1 and A2) and
+// the partial-tile slots.
 hai_status epic_big_prepare(hai_layout *L) {
     if (!epic_big_supported(L)) return HAI_OK;
     const BigGeo g = big_geo(L);
-    std::vector<uint16_t> b1, b2;
-    dft_operand(g.N, g.kb1 * 32, 128, b1);
-    dft_operand(g.N, g.yb * 128, 64, b2);
-    const size_t per_ct = (size_t)g.P * g.yb * g.kb1 * kTile16 + (size_t)g.lb2 * g.kb2 * kTile16;
+    std::vector<std::vector<uint16_t>> ops;          // [variant][stage][part]
+    size_t op_bytes = 0;
+    for (int vi = 0; vi < 4; vi++) {
+        const bool bf = vi & 1, sp = vi >= 2;
+        const int w = sp ? 64 : 128;
+        for (int stage = 0; stage < 2; stage++)
+            for (int part = 0; part < 2; part++) {
+                ops.emplace_back();
+                if (part && !sp) continue;
+                dft_operand(g.N, stage == 0 ? g.kb1 * 32 : 128, w, bf, part, ops.back());
+                op_bytes += (ops.back().size() * 2 + 1023) & ~(size_t)1023;
+            }
+    }
+    const size_t per_ct = (size_t)g.P * g.kb1 * kTile16 + (size_t)g.lb2 * kKb2 * kTile16;
     const size_t budget = (size_t)512 << 20;
-    L->big_batch = (long long)std::max<size_t>(1, budget / per_ct);
-    const size_t a1 = (size_t)L->big_batch * g.P * g.yb * g.kb1 * kTile16;
-    const size_t a2 = (size_t)L->big_batch * g.lb2 * g.kb2 * kTile16;
-    cudaError_t e = cudaMalloc(&L->d_big, b1.size() * 2 + b2.size() * 2 + a1 + a2);
-    if (e != cudaSuccess) return hai_cuda_fail(e, "epic fp16 (large grid): scratch");
+    L->big_batch = (long long)std::max<size_t>(2, budget / per_ct) & ~1ll;    // even: halves hold hi and lo
+    const size_t a1 = (size_t)L->big_batch * g.P * g.kb1 * kTile16;
+    const size_t a2 = (size_t)L->big_batch * g.lb2 * kKb2 * kTile16;
+    const size_t slots = (size_t)L->ctx->num_sms * Var<false>::SlotFloats * sizeof(float);
+    cudaError_t e = cudaMalloc(&L->d_big, op_bytes + a1 + a2 + slots);
+    if (e != cudaSuccess) return hai_cuda_fail(e, "epic tensor cores (large grid): scratch");
     uint8_t *base = static_cast<uint8_t *>(L->d_big);
-    L->big_b1 = base;
-    L->big_b2 = base + b1.size() * 2;
-    L->big_a1 = base + b1.size() * 2 + b2.size() * 2;
-    L->big_a2 = static_cast<uint8_t *>(L->big_a1) + a1;
-    e = cudaMemcpy(L->big_b1, b1.data(), b1.size() * 2, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(L->big_b2, b2.data(), b2.size() * 2, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return hai_cuda_fail(e, "epic fp16 (large grid): DFT operands");
+    size_t off = 0;
+    int idx = 0;
+    for (int vi = 0; vi < 4; vi++)
+        for (int stage = 0; stage < 2; stage++)
+            for (int part = 0; part < 2; part++, idx++) {
+                void *&dst = stage == 0 ? L->big_b1[vi][part] : L->big_b2[vi][part];
+                dst = nullptr;
+                if (ops[idx].empty()) continue;
+                dst = base + off;
+                e = cudaMemcpy(dst, ops[idx].data(), ops[idx].size() * 2, cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) return hai_cuda_fail(e, "epic tensor cores (large grid): DFT operands");
+                off += (ops[idx].size() * 2 + 1023) & ~(size_t)1023;
+            }
+    L->big_a1 = base + off;
+    L->big_a2 = base + off + a1;
+    L->big_slots = base + off + a1 + a2;
     return HAI_OK;
 }
 
 hai_status epic_big_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
-                           cudaStream_t st) {
+                           hai_precision prec, cudaStream_t st) {
     if (!epic_big_supported(L) || !L->d_big)
-        return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16: large-grid tensor path needs N = 256 or 512, 2 pols, "
-                                             "a box <= N/2");
-    hai_ctx *ctx = L->ctx;
-    const BigGeo g = big_geo(L);
-    if (g.kb2 != kS2Kb) return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16 (large grid): box taller than 128 cells");
-    const size_t s1_smem = (size_t)kS1Stages * (kTile16 + kTile32);
-    const size_t s2_smem = (size_t)3 * g.kb2 * kTile16;
-    if (s1_smem > (size_t)ctx->smem_optin - 2048 || s2_smem > (size_t)ctx->smem_optin - 2048)
-        return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16 (large grid): shared memory");
-    HAI_CUDA_TRY(cudaFuncSetAttribute(big_s1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1_smem));
-    HAI_CUDA_TRY(cudaFuncSetAttribute(big_s2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2_smem));
-    const long long total = (long long)C * T;
-    const int pidx = prof_begin(ctx, st);
-    for (long long b0 = 0; b0 < total; b0 += L->big_batch) {
-        const long long b1 = std::min(total, b0 + L->big_batch);
-        const long long nfield = (b1 - b0) * g.P;
-        const int ncell = (g.kb1 * 32) * (g.yb * 128);
-        big_grid_kernel<<<dim3((ncell + 255) / 256, (unsigned)((nfield + kGridFields - 1) / kGridFields)), 256, 0,
-                          st>>>(volt, L->n_elem, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g, b0, nfield,
-                                static_cast<uint8_t *>(L->big_a1));
-        S1Params p1;
-        p1.a1 = static_cast<const uint8_t *>(L->big_a1);
-        p1.b1 = static_cast<const uint8_t *>(L->big_b1);
-        p1.a2 = static_cast<uint8_t *>(L->big_a2);
-        p1.g = g;
-        p1.b0 = b0;
-        p1.nfield = nfield;
-        p1.ntiles = nfield * g.yb * g.lb1;
-        p1.status = ctx->d_status;
-        big_s1_kernel<<<(unsigned)std::min<long long>(p1.ntiles, ctx->num_sms), 384, s1_smem, st>>>(p1);
-        S2Params p2;
-        p2.a2 = static_cast<const uint8_t *>(L->big_a2);
-        p2.b2 = static_cast<const uint8_t *>(L->big_b2);
-        p2.img = img;
-        p2.g = g;
-        p2.b0 = b0;
-        p2.b1 = b1;
-        p2.T = T;
-        p2.c_first = (int)(b0 / T);
-        const int c_last = (int)((b1 - 1) / T);
-        p2.n_items = (c_last - p2.c_first + 1) * g.lb2 * g.lb2;
-        p2.accumulate = accumulate;
-        p2.status = ctx->d_status;
-        big_s2_kernel<<<(unsigned)std::min(p2.n_items, ctx->num_sms), kS2Threads, s2_smem, st>>>(p2);
-        prof_count(ctx, 3);
+        return hai_fail(HAI_ERR_UNSUPPORTED, "epic tensor cores: large-grid path needs N = 256 or 512, 2 pols, "
+                                             "a box <= N/2 wide and <= 128 cells high");
+    switch (variant(prec)) {
+        case 0: return launch_variant<false, false>(L, volt, C, T, img, accumulate, st);
+        case 1: return launch_variant<true, false>(L, volt, C, T, img, accumulate, st);
+        case 2: return launch_variant<false, true>(L, volt, C, T, img, accumulate, st);
+        case 3: return launch_variant<true, true>(L, volt, C, T, img, accumulate, st);
+        default: return hai_fail(HAI_ERR_INVALID_ARG, "epic tensor cores (large grid): precision");
     }
-    prof_end(ctx, pidx, st);
-    HAI_CUDA_TRY(cudaGetLastError());
-    return HAI_OK;
 }

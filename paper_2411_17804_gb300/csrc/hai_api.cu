@@ -454,7 +454,8 @@ extern "C" hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *L, const in
     if (C < 0 || T < 0) return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: negative C or T");
     if (accumulate != 0 && accumulate != 1)
         return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: accumulate must be 0 or 1");
-    if (prec != HAI_PREC_FP32 && prec != HAI_PREC_FP16 && prec != HAI_PREC_FP16_SPLIT)
+    if (prec != HAI_PREC_FP32 && prec != HAI_PREC_FP16 && prec != HAI_PREC_FP16_SPLIT && prec != HAI_PREC_BF16 &&
+        prec != HAI_PREC_BF16_SPLIT)
         return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: unknown precision");
     if (C == 0) return HAI_OK;
     if (!img || (T > 0 && !volt)) return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: NULL buffer");
@@ -468,6 +469,8 @@ extern "C" hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *L, const in
         return HAI_OK;
     }
     if (prec == HAI_PREC_FP32) return epic_fp32_launch(L, volt, C, T, img, accumulate, st);
-    if (prec == HAI_PREC_FP16 && L->grid_n >= 256) return epic_big_launch(L, volt, C, T, img, accumulate, st);
+    if (L->grid_n >= 256) return epic_big_launch(L, volt, C, T, img, accumulate, prec, st);
+    if (prec == HAI_PREC_BF16 || prec == HAI_PREC_BF16_SPLIT)
+        return hai_fail(HAI_ERR_UNSUPPORTED, "hai_epic_image: BF16 operands need N = 256 or 512");
     return epic_tc_launch(L, volt, C, T, img, accumulate, st, prec == HAI_PREC_FP16_SPLIT ? 1 : 0);
 }

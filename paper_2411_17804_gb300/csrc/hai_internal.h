@@ -76,7 +76,8 @@ struct hai_layout {
     // tensor-core path of large grids (N = 256, 512): DFT operands and the
     // stage scratch of one batch of (channel, sample) pairs
     void *d_big = nullptr;
-    void *big_b1 = nullptr, *big_b2 = nullptr, *big_a1 = nullptr, *big_a2 = nullptr;
+    void *big_b1[4][2] = {}, *big_b2[4][2] = {};   // [fp16, bf16, fp16 split, bf16 split][hi, lo]
+    void *big_a1 = nullptr, *big_a2 = nullptr, *big_slots = nullptr;
     long long big_batch = 0;
     // XFFT: per grid cell the (pair, K_ab value, mirror) entries landing there,
     // built on the first hai_xfft_image call (layout-only data)
@@ -143,12 +144,13 @@ bool epic_large_supported(int grid_n);
 size_t epic_large_scratch_bytes(int grid_n, int box_h);
 hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
                              cudaStream_t st);
-// FP16 tensor-core EPIC for N = 256, 512 (box <= N/2, box height <= 128):
-// gridding, stage-1 GEMM and stage-2 GEMM + squaring through an HBM scratch.
+// Tensor-core EPIC for N = 256, 512 (box <= N/2, box height <= 128), FP16 or
+// BF16 operands, plain or split: gridding, stage-1 GEMM and stage-2 GEMM +
+// squaring through an HBM scratch.
 bool epic_big_supported(const hai_layout *L);
 hai_status epic_big_prepare(hai_layout *L);
 hai_status epic_big_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
-                           cudaStream_t st);
+                           hai_precision prec, cudaStream_t st);
 
 // ---------------------------------------------------------------- station pairs
 // The inter-station XFFT keeps a pair when the 2x2 bilinear footprint of its

@@ -11,6 +11,7 @@
 // matrices adjacent along M/N.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
 
@@ -48,6 +49,12 @@ __device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t k_stride, uint
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int a_mn_major, int b_mn_major) {
     return (1u << 4) | ((uint32_t)a_mn_major << 15) | ((uint32_t)b_mn_major << 16) |
            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with both A and B in BF16 (A format bits 7-9 and B format bits
+// 10-12 set to 1).  One MMA never mixes FP16 and BF16 operands.
+__host__ __device__ constexpr uint32_t idesc_f16_as(bool bf16, int M, int N, int a_mn_major, int b_mn_major) {
+    return idesc_f16(M, N, a_mn_major, b_mn_major) | (bf16 ? ((1u << 7) | (1u << 10)) : 0u);
 }
 
 // D[tmem] (+)= A * B^T, issued by one thread.
@@ -303,6 +310,34 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t *m, uint32_t parity, 
 __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
     __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<uint32_t *>(&h);
+}
+
+__device__ __forceinline__ uint32_t pack_bf162(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// Two values rounded to the 16-bit operand type (FP16, or BF16 if BF) and
+// packed (a in the low half).
+template <bool BF>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+    if constexpr (BF) return pack_bf162(a, b);
+    else return pack_half2(a, b);
+}
+
+// x rounded to the operand type, as a float.
+template <bool BF>
+__device__ __forceinline__ float round_op(float x) {
+    if constexpr (BF) return __bfloat162float(__float2bfloat16_rn(x));
+    else return __half2float(__float2half_rn(x));
+}
+
+// Split operands: hi = the two values rounded to the operand type, lo = their
+// remainders x - hi rounded to it (hi + lo carries ~2x the type's bits).
+template <bool BF>
+__device__ __forceinline__ void pack2_split(float a, float b, uint32_t &hi, uint32_t &lo) {
+    hi = pack2<BF>(a, b);
+    lo = pack2<BF>(a - round_op<BF>(a), b - round_op<BF>(b));
 }
 
 }  // namespace tc

@@ -22,6 +22,8 @@ STATUS_NAMES = {0: "HAI_OK", 1: "HAI_ERR_INVALID_ARG", 2: "HAI_ERR_OFF_GRID",
 HAI_PREC_FP32 = 0
 HAI_PREC_FP16 = 1
 HAI_PREC_FP16_SPLIT = 2
+HAI_PREC_BF16 = 3
+HAI_PREC_BF16_SPLIT = 4
 
 
 class HaiError(RuntimeError):

@@ -1,0 +1,152 @@
+"""Tensor-core EPIC on the large grids (N = 256, 512) in every operand form:
+FP16, BF16 and their hi/lo splits, against the FP64 oracle.
+
+The dense all-sky lattice (128 x 128 elements at 0.5 lambda on a 512^2 grid,
+1 x 1 unit taps) and the SKA-shaped station on a 256^2 grid.  The cases cover
+several sample batches per call, channel chunks (more channels than the batch
+scratch holds pairs), (item, sample) ranges that split items between CTAs
+(the partial tiles and their fixup), accumulate, determinism and the full
+cadence of 10^4 samples on a sampled channel."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2411_17804_gb300 import inputs as I
+from tests.helpers import (BF16_SPLIT_TOL, BF16_TOL, FP32_TOL, REDUCED_TOL, SPLIT_PIXEL_TOL, frob_err_planes,
+                           pixel_err_planes, rel_err_planes, station)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(hai):
+    c = hai.hai_create(0)
+    yield c
+    hai.hai_destroy(c)
+
+
+def dense():
+    cfg = I.DENSE_ALLSKY_16384
+    pos, anchors, taps = station(cfg)
+    return cfg, pos, anchors, taps
+
+
+def check(hai, prec, got, want):
+    """Each precision against the oracle at its bound (helpers: derivations)."""
+    if prec == hai.HAI_PREC_FP16:
+        assert rel_err_planes(got, want).max() < REDUCED_TOL
+    elif prec == hai.HAI_PREC_BF16:
+        assert rel_err_planes(got, want).max() < BF16_TOL
+    elif prec == hai.HAI_PREC_FP16_SPLIT:
+        assert frob_err_planes(got, want).max() < FP32_TOL
+        assert pixel_err_planes(got, want).max() < SPLIT_PIXEL_TOL
+    elif prec == hai.HAI_PREC_BF16_SPLIT:
+        assert rel_err_planes(got, want).max() < BF16_SPLIT_TOL
+    else:
+        assert rel_err_planes(got, want).max() < FP32_TOL
+
+
+def image(hai, ctx, lay, volt, C, T, prec, n, img=None, accumulate=0):
+    if img is None:
+        img = torch.full((C, 4, n, n), float("nan"), device="cuda")
+    hai.hai_epic_image(ctx, lay, volt, C, T, prec, img, accumulate)
+    hai.hai_sync(ctx)
+    return img
+
+
+PRECS = ["FP16", "BF16", "FP16_SPLIT", "BF16_SPLIT"]
+
+
+@pytest.mark.parametrize("pname", PRECS)
+@pytest.mark.parametrize("case,C,T", [
+    ("n512", 2, 3),           # 64 items x 3 samples on 152 CTAs: items split between CTAs
+    ("n512", 3, 40),
+    ("n256", 2, 7),           # the SKA station (3 x 3 Gaussian taps) on a 256^2 grid
+    ("n256_cplx", 1, 4),      # random complex taps, random anchors over a 100 x 120 box
+])
+def test_every_operand_form_matches_oracle(hai, ctx, pname, case, C, T):
+    prec = getattr(hai, f"HAI_PREC_{pname}")
+    if case == "n512":
+        _, pos, anchors, taps = dense()
+        n = 512
+    elif case == "n256":
+        pos, anchors, taps = station(I.SKA_LOW_STATION_256)
+        n = 256
+    else:
+        rng = np.random.default_rng(3)
+        n, ne, k = 256, 150, 3
+        anchors = np.stack([rng.integers(40, 138, ne), rng.integers(30, 148, ne)], axis=1).astype(np.int32)
+        taps = rng.standard_normal((ne, k, k, 2)).astype(np.float32)
+    volt = I.random_voltages((C, T, 2, len(anchors), 2), seed=C * 7 + T)
+    want = O.epic_image(n, anchors, taps, volt.numpy())
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, 2)
+    try:
+        img = image(hai, ctx, lay, volt.cuda(), C, T, prec, n)
+        got = img.cpu().numpy()
+        check(hai, prec, got, want)
+        # accumulate onto the first result
+        image(hai, ctx, lay, volt.cuda(), C, T, prec, n, img, 1)
+        check(hai, prec, img.cpu().numpy(), 2 * want)
+    finally:
+        hai.hai_layout_destroy(lay)
+
+
+@pytest.mark.parametrize("pname", ["FP16", "BF16_SPLIT"])
+def test_many_channels_go_in_chunks(hai, ctx, pname):
+    """More channels than the batch scratch holds (channel, sample) pairs (819
+    plain, 409 split at 512^2): the channels go in chunks; sampled channels on
+    both sides of every chunk boundary against the oracle."""
+    prec = getattr(hai, f"HAI_PREC_{pname}")
+    _, pos, anchors, taps = dense()
+    C, T, n = 830, 1, 512
+    volt = I.random_voltages((C, T, 2, len(pos), 2), seed=11, device="cuda")
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, 2)
+    try:
+        img = image(hai, ctx, lay, volt, C, T, prec, n)
+        for c in (0, 408, 409, 818, 819, 829):
+            want = O.epic_image(n, anchors, taps, volt[c:c + 1].cpu().numpy())
+            check(hai, prec, img[c:c + 1].cpu().numpy(), want)
+    finally:
+        hai.hai_layout_destroy(lay)
+
+
+def test_results_are_bit_identical_on_repeat(hai, ctx):
+    """Partial tiles are added in a fixed CTA order: repeated calls agree to
+    the bit."""
+    _, pos, anchors, taps = dense()
+    volt = I.random_voltages((3, 17, 2, len(pos), 2), seed=5, device="cuda")
+    lay = hai.hai_layout_create(ctx, anchors, taps, 512, 2)
+    try:
+        for prec in (hai.HAI_PREC_FP16, hai.HAI_PREC_BF16_SPLIT):
+            a = image(hai, ctx, lay, volt, 3, 17, prec, 512).cpu()
+            b = image(hai, ctx, lay, volt, 3, 17, prec, 512).cpu()
+            assert torch.equal(a, b)
+    finally:
+        hai.hai_layout_destroy(lay)
+
+
+@pytest.fixture(scope="module")
+def long_cadence(hai):
+    """The dense all-sky lattice over a cadence of 10^4 samples (the longest of
+    the workload), one sampled channel of the seeded sky: voltages and the
+    oracle's image (FP64, all host cores)."""
+    cfg, pos, anchors, taps = dense()
+    volt = I.station_voltages(cfg, pos, device="cuda", n_chan=1, n_time=10000, chan0=5)
+    want = O.epic_image(cfg.grid_n, anchors, taps, volt.cpu().numpy())
+    return cfg, anchors, taps, volt, want
+
+
+@pytest.mark.parametrize("pname", ["FP32", "FP16", "FP16_SPLIT", "BF16_SPLIT", "BF16"])
+def test_long_cadence_of_ten_thousand_samples(hai, ctx, long_cadence, pname):
+    """T = 10^4: FP32 accumulation over the whole cadence stays within each
+    path's bound (the FP32 path <= 1e-5, the reduced-precision ones within
+    theirs)."""
+    cfg, anchors, taps, volt, want = long_cadence
+    prec = getattr(hai, f"HAI_PREC_{pname}")
+    lay = hai.hai_layout_create(ctx, anchors, taps, cfg.grid_n, 2)
+    try:
+        img = image(hai, ctx, lay, volt, 1, 10000, prec, cfg.grid_n)
+        check(hai, prec, img.cpu().numpy(), want)
+    finally:
+        hai.hai_layout_destroy(lay)
