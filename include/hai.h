@@ -105,6 +105,18 @@ hai_status hai_sync(hai_ctx *ctx, void *stream);
 hai_status hai_check_device_wait(hai_ctx *ctx, long long limit_cycles, void *stream);
 hai_status hai_check_device_wait_result(hai_ctx *ctx, int *gave_up);
 
+/* Peak-rate probe (no counterpart in the paper: a measurement aid for the
+ * roofline fractions).  Launches on `stream` one kernel of 4 CTAs x 256
+ * threads per SM, every thread running independent dependency chains of
+ * `iters` (1 .. 2^24) steps of:
+ *   kind 0  scalar FP32 fused multiply-add (2 FLOP each),
+ *   kind 1  packed FP32 fused multiply-add on pairs, FFMA2 (4 FLOP each),
+ *   kind 2  warp-level int8 MMA, mma.sync m16n8k32 s8 x s8 + s32 (8,192
+ *           integer operations each).
+ * *ops (host) receives the operation count of the launch; time it with
+ * events on `stream`.  HAI_ERR_INVALID_ARG for another kind or iters. */
+hai_status hai_probe_peak(hai_ctx *ctx, int kind, long long iters, double *ops, void *stream);
+
 /* Profiling.  While enabled, every compute call records a pair of CUDA events
  * on the caller's stream around its dominant kernel (the first kernels it
  * launches are the one named in the call's description) and counts every

@@ -76,9 +76,10 @@ extern "C" hai_status hai_create(int device, hai_ctx **out) {
     cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    // word 0: the status word; word 1: outcome of the wait self-check
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 2 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 2 * sizeof(unsigned));
+    // word 0: the status word; word 1: outcome of the wait self-check; word 2:
+    // sink of the peak-rate probes
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 4 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 4 * sizeof(unsigned));
     if (e != cudaSuccess) {
         if (c->d_status) cudaFree(c->d_status);
         delete c;

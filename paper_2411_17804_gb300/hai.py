@@ -93,6 +93,7 @@ def _declare(L):
     L.hai_xfft_station_image.argtypes = [_vp, _vp, _vp, _int, _vp, _vp]
     L.hai_profile_enable.argtypes = [_vp, _int, _int]
     L.hai_check_device_wait.argtypes = [_vp, ctypes.c_longlong, _vp]
+    L.hai_probe_peak.argtypes = [_vp, _int, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), _vp]
     L.hai_check_device_wait_result.argtypes = [_vp, ctypes.POINTER(_int)]
     L.hai_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
@@ -179,6 +180,13 @@ def hai_sync(ctx, stream=None):
 
 def hai_check_device_wait(ctx, limit_cycles: int, stream=None):
     _check(load().hai_check_device_wait(ctx, int(limit_cycles), _stream(stream)), "hai_check_device_wait")
+
+
+def hai_probe_peak(ctx, kind: int, iters: int, stream=None) -> float:
+    """Launch the peak-rate probe; returns the launch's operation count."""
+    ops = ctypes.c_double()
+    _check(load().hai_probe_peak(ctx, kind, int(iters), ctypes.byref(ops), _stream(stream)), "hai_probe_peak")
+    return ops.value
 
 
 def hai_check_device_wait_result(ctx) -> int:
