@@ -147,6 +147,75 @@ __global__ void __launch_bounds__(256) big_grid_kernel(const int8_t *__restrict_
         }
 }
 
+// The same gridding with the field's voltages staged in shared memory: one
+// CTA per field loads its N_e complex int8 voltages with 16-byte loads, then
+// every thread builds whole 16-byte runs of A1 (4 cells of one row: 8 values),
+// eight consecutive threads covering the 128 contiguous bytes of one k group
+// of 8 rows.  Used when the field fits (kGridSmemMax bytes).
+constexpr int kGridThreads = 512;
+constexpr int kGridSmemMax = 96 * 1024;
+
+template <bool BF, bool SP>
+__global__ void __launch_bounds__(kGridThreads) big_grid_smem_kernel(
+    const int8_t *__restrict__ volt, int ne, int T, const int32_t *__restrict__ cell_start,
+    const int32_t *__restrict__ entry_elem, const float2 *__restrict__ entry_w, BigGeo g, int t0, int tb,
+    uint8_t *__restrict__ a1, uint8_t *__restrict__ a1lo) {
+    extern __shared__ __align__(16) char2 sv[];
+    const long long f = blockIdx.x;
+    const long long ct = f / g.P;
+    const int pol = (int)(f % g.P);
+    const long long c = ct / tb, t = t0 + ct % tb;
+    const int8_t *src = volt + ((c * T + t) * g.P + pol) * (long long)ne * 2;
+    const int nbytes = 2 * ne;
+    if (((reinterpret_cast<uintptr_t>(src) | (uintptr_t)nbytes) & 15) == 0) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        uint4 *d4 = reinterpret_cast<uint4 *>(sv);
+        for (int i = threadIdx.x; i < nbytes / 16; i += blockDim.x) d4[i] = __ldg(s4 + i);
+    } else {
+        const char2 *s2 = reinterpret_cast<const char2 *>(src);
+        for (int i = threadIdx.x; i < ne; i += blockDim.x) sv[i] = s2[i];
+    }
+    __syncthreads();
+    const int nkg = g.kb1 * 8;                       // k groups (4 cells each) per row
+    const int nchunk = 128 * nkg;
+    const size_t field_bytes = (size_t)g.kb1 * kTile16;
+    uint8_t *dst = a1 + (size_t)f * field_bytes;
+    uint8_t *dlo = SP ? a1lo + (size_t)f * field_bytes : nullptr;
+    for (int q = threadIdx.x; q < nchunk; q += blockDim.x) {
+        const int y = (q & 7) + 8 * (q / (8 * nkg)), kg = (q >> 3) % nkg;
+        float2 acc[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            acc[i] = make_float2(0.f, 0.f);
+            const int x = 4 * kg + i;
+            if (x < g.bx && y < g.by) {
+                const int cell = y * g.bx + x;
+                for (int k = cell_start[cell]; k < cell_start[cell + 1]; k++) {
+                    const char2 v = sv[entry_elem[k]];
+                    const float2 w = entry_w[k];             // conj(W~)
+                    acc[i].x = fmaf(w.x, (float)v.x, fmaf(-w.y, (float)v.y, acc[i].x));
+                    acc[i].y = fmaf(w.x, (float)v.y, fmaf(w.y, (float)v.x, acc[i].y));
+                }
+            }
+        }
+        const size_t off = (size_t)(kg >> 3) * kTile16 + (size_t)(y >> 3) * kKMN + (size_t)(kg & 7) * kKBytes +
+                           (size_t)(y & 7) * 16;
+        if constexpr (SP) {
+            uint4 hi, lo;
+            tc::pack2_split<BF>(acc[0].x, acc[0].y, hi.x, lo.x);
+            tc::pack2_split<BF>(acc[1].x, acc[1].y, hi.y, lo.y);
+            tc::pack2_split<BF>(acc[2].x, acc[2].y, hi.z, lo.z);
+            tc::pack2_split<BF>(acc[3].x, acc[3].y, hi.w, lo.w);
+            *reinterpret_cast<uint4 *>(dst + off) = hi;
+            *reinterpret_cast<uint4 *>(dlo + off) = lo;
+        } else {
+            *reinterpret_cast<uint4 *>(dst + off) =
+                make_uint4(tc::pack2<BF>(acc[0].x, acc[0].y), tc::pack2<BF>(acc[1].x, acc[1].y),
+                           tc::pack2<BF>(acc[2].x, acc[2].y), tc::pack2<BF>(acc[3].x, acc[3].y));
+        }
+    }
+}
+
 // ------------------------------------------------------------------ stage 1
 struct S1Params {
     const uint8_t *a1, *a1lo;    // A1 (hi, lo)
@@ -557,10 +626,13 @@ __global__ void __launch_bounds__(576, 1) big_s2_kernel(const S2Params p) {
 }
 
 // ------------------------------------------------------------------ fixup
-// Block k: if CTA k's range begins inside an item and CTA k - 1's range does
-// not begin inside the same item, CTA k is that item's first partial: add the
-// slots of k, k + 1, ... (every CTA whose range begins inside the item) to
-// the item's image tile, in CTA order.
+// Block (k, slice): if CTA k's range begins inside an item and CTA k - 1's
+// range does not begin inside the same item, CTA k is that item's first
+// partial: add the slots of k, k + 1, ... (every CTA whose range begins inside
+// the item) to the item's image tile, in CTA order.  Each of kFixSlices blocks
+// takes a slice of the tile, four elements per thread with independent loads.
+constexpr int kFixSlices = 32;
+
 template <int W>
 __global__ void __launch_bounds__(256) big_fixup_kernel(const float *__restrict__ slots, float *__restrict__ img,
                                                         BigGeo g, int C, int tb, long long units, int G) {
@@ -577,14 +649,25 @@ __global__ void __launch_bounds__(256) big_fixup_kernel(const float *__restrict_
     const int per_lyb = C * g.lb2;
     const int lyb = (int)(it / per_lyb), rem = (int)(it % per_lyb), c = rem / g.lb2, lxb = rem % g.lb2;
     const size_t NN = (size_t)g.N * g.N;
-    constexpr int kSlot = 4 * W * 64;
+    constexpr int kSlot = 4 * W * 64, kPer = kSlot / kFixSlices;      // elements per block
+    static_assert(kPer == 4 * 256 || kPer == 2 * 256, "slice = 2 or 4 elements per thread");
+    constexpr int kE = kPer / 256;
     float *dst = img + (size_t)c * 4 * NN + (size_t)lyb * W * g.N + (size_t)lxb * 64;
-    for (int e = threadIdx.x; e < kSlot; e += blockDim.x) {
+    size_t di[kE];
+    float s[kE], v[kE];
+#pragma unroll
+    for (int i = 0; i < kE; i++) {
+        const int e = blockIdx.y * kPer + i * 256 + threadIdx.x;
         const int plane = e / (W * 64), r = e % (W * 64), ly = r / 64, lx = r % 64;
-        float s = 0.f;
-        for (int j = k; j < k1; j++) s += slots[(size_t)j * kSlot + e];
-        dst[plane * NN + (size_t)ly * g.N + lx] += s;
+        di[i] = plane * NN + (size_t)ly * g.N + lx;
+        v[i] = dst[di[i]];
+        s[i] = 0.f;
     }
+    for (int j = k; j < k1; j++)
+#pragma unroll
+        for (int i = 0; i < kE; i++) s[i] += slots[(size_t)j * kSlot + blockIdx.y * kPer + i * 256 + threadIdx.x];
+#pragma unroll
+    for (int i = 0; i < kE; i++) dst[di[i]] = v[i] + s[i];
 }
 
 BigGeo big_geo(const hai_layout *L) {
@@ -659,6 +742,7 @@ hai_status launch_variant(const hai_layout *L, const int8_t *volt, int C, int T,
     const int vi = (BF ? 1 : 0) + (SP ? 2 : 0);
     if (V::S1Smem > (uint32_t)ctx->smem_optin - 1024 || V::S2Smem > (uint32_t)ctx->smem_optin - 1024)
         return hai_fail(HAI_ERR_UNSUPPORTED, "epic tensor cores (large grid): shared memory");
+    HAI_CUDA_TRY(hai_allow_dyn_smem(big_grid_smem_kernel<BF, SP>, ctx->smem_optin));
     HAI_CUDA_TRY(hai_allow_dyn_smem(big_s1_kernel<BF, SP>, ctx->smem_optin));
     HAI_CUDA_TRY(hai_allow_dyn_smem(big_s2_kernel<BF, SP>, ctx->smem_optin));
     // the scratch holds big_batch (channel, sample) pairs of plain operands,
@@ -682,9 +766,14 @@ hai_status launch_variant(const hai_layout *L, const int8_t *volt, int C, int T,
         const int tb = std::min(tb_max, T - t0);
         const long long nfield = (long long)Cc * tb * g.P;
         const int ncell = (g.kb1 * 32) * 128;
-        big_grid_kernel<BF, SP><<<dim3((ncell + 255) / 256, (unsigned)((nfield + kGridFields - 1) / kGridFields)), 256,
-                                  0, st>>>(vc, L->n_elem, T, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g, t0,
-                                           tb, nfield, a1, a1lo);
+        const size_t vbytes = ((size_t)2 * L->n_elem + 15) & ~(size_t)15;
+        if (vbytes <= (size_t)kGridSmemMax)
+            big_grid_smem_kernel<BF, SP><<<(unsigned)nfield, kGridThreads, vbytes, st>>>(
+                vc, L->n_elem, T, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g, t0, tb, a1, a1lo);
+        else
+            big_grid_kernel<BF, SP><<<dim3((ncell + 255) / 256, (unsigned)((nfield + kGridFields - 1) / kGridFields)),
+                                      256, 0, st>>>(vc, L->n_elem, T, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g,
+                                                    t0, tb, nfield, a1, a1lo);
         S1Params p1;
         p1.a1 = a1;
         p1.a1lo = a1lo;
@@ -724,7 +813,7 @@ hai_status launch_variant(const hai_layout *L, const int8_t *volt, int C, int T,
             split_items = a < b && a % tb != 0;
         }
         if (split_items) {
-            big_fixup_kernel<V::W><<<(unsigned)G, 256, 0, st>>>(p2.slots, ic, g, Cc, tb, p2.units, G);
+            big_fixup_kernel<V::W><<<dim3((unsigned)G, kFixSlices), 256, 0, st>>>(p2.slots, ic, g, Cc, tb, p2.units, G);
             launches++;
         }
     }
