@@ -227,8 +227,10 @@ struct S1Params {
     unsigned *status;
 };
 
+constexpr int kS1Threads = 640;             // warp 0 loads, warp 1 MMA, warps 4-19 epilogue
+
 template <bool BF, bool SP>
-__global__ void __launch_bounds__(384, 1) big_s1_kernel(const S1Params p) {
+__global__ void __launch_bounds__(kS1Threads, 1) big_s1_kernel(const S1Params p) {
     using V = Var<SP>;
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t full[V::S1Stages], empty[V::S1Stages], dfull[2], dempty[2], bfull;
@@ -246,7 +248,7 @@ __global__ void __launch_bounds__(384, 1) big_s1_kernel(const S1Params p) {
         }
         for (int b = 0; b < 2; b++) {
             tc::mbar_init(&dfull[b], 1);
-            tc::mbar_init(&dempty[b], 256);
+            tc::mbar_init(&dempty[b], 512);
         }
         tc::mbar_init(&bfull, 1);
         tc::mbar_fence_init();
@@ -278,6 +280,11 @@ __global__ void __launch_bounds__(384, 1) big_s1_kernel(const S1Params p) {
                         tc::bulk_g2s(sB + (size_t)part * kMaxKb1 * V::BTile, src, bpart, &bfull);
                     }
                     cur_lb = lb;
+                }
+                if (tile + 2 < r1) {                      // A1 of the tile two ahead into L2
+                    const size_t pre = (size_t)((tile + 2) % nf) * g.kb1 * kTile16;
+                    tc::bulk_prefetch_l2(p.a1 + pre, (uint32_t)g.kb1 * kTile16);
+                    if constexpr (SP) tc::bulk_prefetch_l2(p.a1lo + pre, (uint32_t)g.kb1 * kTile16);
                 }
                 for (int kb = 0; kb < g.kb1; kb++, gs++) {
                     const int s = (int)(gs % V::S1Stages);
@@ -332,11 +339,12 @@ __global__ void __launch_bounds__(384, 1) big_s1_kernel(const S1Params p) {
             }
         }
     } else if (warp >= 4) {
-        // epilogue, warps 4-11: thread = row y of the tile and one half (h) of
-        // its W1 l_x -> the stage-2 operand rows (l_x, pol), K index 2 y + re/im
+        // epilogue, warps 4-19: thread = row y of the tile and one quarter (h)
+        // of its W1 l_x -> the stage-2 operand rows (l_x, pol), K index 2 y +
+        // re/im
         const int q = warp & 3, y = q * 32 + lane, h = (warp - 4) >> 2;
         const int kb2 = (2 * y) / 64, kk = (2 * y) % 64;   // K of the real part; imag at kk + 1
-        constexpr int kChunks = V::W / 32;                   // 16 l_x per chunk, per half
+        constexpr int kChunks = V::W / 64;                   // 16 l_x per chunk, per quarter
         long long gt = 0;
         for (long long tile = r0; tile < r1; tile++, gt++) {
             const int b = (int)(gt & 1);
@@ -407,6 +415,8 @@ struct S2Params {
     unsigned *status;
 };
 
+constexpr int kAhead = 4;                   // samples of L2 prefetch ahead of the stage-2 loads
+
 // Unit range of CTA k of G over U units: [U k / G, U (k + 1) / G).
 __host__ __device__ __forceinline__ long long unit_start(long long U, int G, int k) { return U * k / G; }
 
@@ -464,6 +474,12 @@ __global__ void __launch_bounds__(576, 1) big_s2_kernel(const S2Params p) {
                 }
                 for (int s = s0; s < s1; s++, gs++) {
                     const size_t base = (((size_t)c * tb + s) * g.lb2 + lxb) * kKb2 * kTile16;
+                    // the operand of a sample kAhead ahead into L2 (the ring holds ~1.5 samples)
+                    if (s + kAhead < s1) {
+                        const size_t pre = base + (size_t)kAhead * g.lb2 * kKb2 * kTile16;
+                        tc::bulk_prefetch_l2(p.a2 + pre, kKb2 * kTile16);
+                        if constexpr (SP) tc::bulk_prefetch_l2(p.a2lo + pre, kKb2 * kTile16);
+                    }
                     for (int kb = 0; kb < kKb2; kb++, gk++) {
                         const int st = (int)(gk % V::S2Stages);
                         if (gk >= V::S2Stages)
@@ -785,7 +801,7 @@ hai_status launch_variant(const hai_layout *L, const int8_t *volt, int C, int T,
         p1.nfield = nfield;
         p1.ntiles = nfield * (g.N / V::W);
         p1.status = ctx->d_status;
-        big_s1_kernel<BF, SP><<<(unsigned)std::min<long long>(p1.ntiles, G1), 384, V::S1Smem, st>>>(p1);
+        big_s1_kernel<BF, SP><<<(unsigned)std::min<long long>(p1.ntiles, G1), kS1Threads, V::S1Smem, st>>>(p1);
         S2Params p2;
         p2.a2 = a2;
         p2.a2lo = a2lo;

@@ -77,8 +77,6 @@ struct Geo {
     static constexpr uint32_t kOffA2 = kOffA1 + 2 * kSet * kA1Bytes;    // A1 [2 buffers][hi, lo]
     static constexpr uint32_t kOffE = kOffA2 + kA2Steps * kTiles * kSet * kA2Bytes;
     static constexpr uint32_t kTmemCols = (4 * kNcol <= 256) ? 256 : 512;
-    static constexpr uint32_t kIdesc1 = tc::idesc_f16(128, kNcol, 0, 0);
-    static constexpr uint32_t kIdesc2 = tc::idesc_f16(128, kNcol, 1, 0);
     static_assert(kTiles == 2, "two stage-2 tiles per step");
 };
 
@@ -100,9 +98,12 @@ struct Params {
 __device__ __forceinline__ void bar_front() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
 __device__ __forceinline__ void bar_epi() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
 
-template <int N, bool SP>
+template <int N, bool SP, bool BF>
 __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
     using G = Geo<N, SP>;
+    // operand type of both MMA operands: FP16, or BF16 when BF
+    constexpr uint32_t kIdesc1 = tc::idesc_f16_as(BF, 128, G::kNcol, 0, 0);
+    constexpr uint32_t kIdesc2 = tc::idesc_f16_as(BF, 128, G::kNcol, 1, 0);
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t mb_v[kStages];
     __shared__ __align__(8) uint64_t mb_a1[2], mb_d1[2], mb_a2[2], mb_full[2], mb_empty[2], mb_a2free;
@@ -270,12 +271,13 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
                     uint8_t *c = A + off;
 #pragma unroll
                     for (int f = 0; f < G::kFields; f++) {
-                        const uint32_t hi = tc::pack_half2(g[f].x, g[f].y);
-                        *reinterpret_cast<uint32_t *>(c + f * G::kImgBytes) = hi;
                         if (SP) {              // the rounding remainder as the lo copy
-                            const float2 back = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
-                            *reinterpret_cast<uint32_t *>(c + G::kA1Bytes + f * G::kImgBytes) =
-                                tc::pack_half2(g[f].x - back.x, g[f].y - back.y);
+                            uint32_t hi, lo;
+                            tc::pack2_split<BF>(g[f].x, g[f].y, hi, lo);
+                            *reinterpret_cast<uint32_t *>(c + f * G::kImgBytes) = hi;
+                            *reinterpret_cast<uint32_t *>(c + G::kA1Bytes + f * G::kImgBytes) = lo;
+                        } else {
+                            *reinterpret_cast<uint32_t *>(c + f * G::kImgBytes) = tc::pack2<BF>(g[f].x, g[f].y);
                         }
                     }
                 }
@@ -306,11 +308,8 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
                         const float x0 = __uint_as_float(r[8 * h + 2 * e]), x1 = __uint_as_float(r[8 * h + 2 * e + 1]);
-                        hv[e] = tc::pack_half2(x0, x1);
-                        if (SP) {
-                            const float2 back = __half22float2(*reinterpret_cast<const __half2 *>(&hv[e]));
-                            lv[e] = tc::pack_half2(x0 - back.x, x1 - back.y);
-                        }
+                        if (SP) tc::pack2_split<BF>(x0, x1, hv[e], lv[e]);
+                        else hv[e] = tc::pack2<BF>(x0, x1);
                     }
                     const uint32_t off = tc::off_mnmajor(m2, kappa, kA2Ks, kA2MNs);
                     *reinterpret_cast<uint4 *>(A2 + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
@@ -384,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
 #pragma unroll
                         for (int s = 0; s < G::kK / 16; s++)
                             tc::mma_f16(d, tc::desc(a + ao + s * 2 * kKs, kKs, G::kMNs),
-                                        tc::desc(b + bo + s * 2 * kKs, kKs, G::kMNs), G::kIdesc1, (pr > 0 || s > 0));
+                                        tc::desc(b + bo + s * 2 * kKs, kKs, G::kMNs), kIdesc1, (pr > 0 || s > 0));
                     }
                     tc::mma_commit(&mb_d1[i & 1]);
                 }
@@ -404,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1) epic_tc_kernel(const Params p) {
 #pragma unroll
                             for (int s = 0; s < G::kK / 16; s++)
                                 tc::mma_f16(d, tc::desc(a + ao + s * 2 * kA2Ks, kA2Ks, kA2MNs),
-                                            tc::desc(b + bo + s * 2 * kKs, kKs, G::kMNs), G::kIdesc2, (pr > 0 || s > 0));
+                                            tc::desc(b + bo + s * 2 * kKs, kKs, G::kMNs), kIdesc2, (pr > 0 || s > 0));
                         }
                         tc::mma_commit(&mb_full[slot]);
                     }
@@ -546,21 +545,21 @@ hai_status raise_limit(hai_ctx *ctx, K kern) {
     return HAI_OK;
 }
 
-template <int N, bool SP>
+template <int N, bool SP, bool BF>
 hai_status run_n(hai_ctx *ctx, const TcLaunch &l, cudaStream_t st) {
     using G = Geo<N, SP>;
     const size_t smem = smem_bytes<N, SP>(l.ne_max, l.table_max);
     if (smem + kStaticSmem > (size_t)ctx->smem_optin)
         return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16: shared memory need exceeds the device limit");
-    const void *dft = epic_tc_dft(ctx, N);
-    if (!dft) return hai_fail(HAI_ERR_INVALID_ARG, "epic fp16: DFT operand not prepared");
+    const void *dft = epic_tc_dft(ctx, N, BF);
+    if (!dft) return hai_fail(HAI_ERR_INVALID_ARG, "epic tensor cores: DFT operand not prepared");
     // the limit is the device's, so launches of any size (and captured graphs) stay valid
     if (!l.no_attr) {
         const hai_status s = epic_tc_set_attr(ctx, N);
         if (s != HAI_OK) return s;
     }
-    if (SP) {
-        const hai_status s = raise_limit(ctx, epic_tc_kernel<N, true>);
+    if (SP || BF) {
+        const hai_status s = raise_limit(ctx, epic_tc_kernel<N, SP, BF>);
         if (s != HAI_OK) return s;
     }
     Params p;
@@ -584,7 +583,7 @@ hai_status run_n(hai_ctx *ctx, const TcLaunch &l, cudaStream_t st) {
     p.partials = l.partials;
     p.status = ctx->d_status;
     const int pidx = prof_begin(ctx, st);
-    epic_tc_kernel<N, SP><<<l.n_cta, kThreads, smem, st>>>(p);
+    epic_tc_kernel<N, SP, BF><<<l.n_cta, kThreads, smem, st>>>(p);
     prof_end(ctx, pidx, st);
     prof_count(ctx, 1);
     HAI_CUDA_TRY(cudaGetLastError());
@@ -608,21 +607,24 @@ size_t epic_tc_smem(hai_ctx *, int N, int ne_max, uint32_t table_max) {
 }
 
 hai_status epic_tc_set_attr(hai_ctx *ctx, int N) {
-    if (N == 32) return raise_limit(ctx, epic_tc_kernel<32, false>);
-    if (N == 64) return raise_limit(ctx, epic_tc_kernel<64, false>);
+    if (N == 32) return raise_limit(ctx, epic_tc_kernel<32, false, false>);
+    if (N == 64) return raise_limit(ctx, epic_tc_kernel<64, false, false>);
     if (N == 128) return epic_tc128_set_attr(ctx);
     return HAI_OK;
 }
 
 hai_status epic_tc_run(hai_ctx *ctx, int N, const TcLaunch &l, cudaStream_t st) {
     if (l.n_cta <= 0) return HAI_OK;
-    if (l.split) {
-        if (N == 32) return run_n<32, true>(ctx, l, st);
-        if (N == 64) return run_n<64, true>(ctx, l, st);
-        return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16 split: this build has the hi/lo variant for N = 32 and 64");
+    if (l.split || l.bf16) {
+        if (N == 32 && l.split) return l.bf16 ? run_n<32, true, true>(ctx, l, st) : run_n<32, true, false>(ctx, l, st);
+        if (N == 64 && l.split) return l.bf16 ? run_n<64, true, true>(ctx, l, st) : run_n<64, true, false>(ctx, l, st);
+        if (N == 32) return run_n<32, false, true>(ctx, l, st);
+        if (N == 64) return run_n<64, false, true>(ctx, l, st);
+        return hai_fail(HAI_ERR_UNSUPPORTED, "epic tensor cores: the hi/lo split and BF16 operands need N = 32, 64, "
+                                             "256 or 512");
     }
-    if (N == 32) return run_n<32, false>(ctx, l, st);
-    if (N == 64) return run_n<64, false>(ctx, l, st);
+    if (N == 32) return run_n<32, false, false>(ctx, l, st);
+    if (N == 64) return run_n<64, false, false>(ctx, l, st);
     if (N == 128) return epic_tc128_run(ctx, l, st);
     return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16: grid size");
 }
@@ -645,23 +647,29 @@ hai_status epic_tc_dft_prepare(hai_ctx *ctx, int N) {
     const int slot = (N == 32) ? 0 : (N == 64) ? 1 : (N == 128) ? 2 : -1;
     if (slot < 0) return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16: grid size");
     if (ctx->d_dft[slot]) return HAI_OK;
-    std::vector<uint8_t> out;
+    std::vector<uint8_t> out, outb;
     auto put = [&](size_t base, uint32_t off, double v) {
         const __half hv = __double2half(v);
         memcpy(&out[base + off], &hv, 2);
     };
     if (N <= 64) {
-        // hi = fp16(W'), then lo = fp16(W' - hi) for the split variant
+        // hi = fp16(W'), then lo = fp16(W' - hi) for the split variant; the
+        // same in BF16 in a second blob
         const int box = N / 2, K = 2 * box;
         const uint32_t mns = (uint32_t)(K / 8) * kKs;
         const size_t half_bytes = (size_t)(2 * N / 8) * mns;
         out.assign(2 * half_bytes, 0);
+        outb.assign(2 * half_bytes, 0);
         for (int n = 0; n < 2 * N; n++)
             for (int kappa = 0; kappa < K; kappa++) {
                 const double v = epic_tc_dft_entry(N, n / N, n % N, kappa >> 1, kappa & 1);
                 const double hi = (double)__half2float(__double2half(v));
                 put(0, tc::off_kmajor(n, kappa, kKs, mns), v);
                 put(half_bytes, tc::off_kmajor(n, kappa, kKs, mns), v - hi);
+                const __nv_bfloat16 bh = __double2bfloat16(v);
+                const __nv_bfloat16 bl = __double2bfloat16(v - (double)__bfloat162float(bh));
+                memcpy(&outb[tc::off_kmajor(n, kappa, kKs, mns)], &bh, 2);
+                memcpy(&outb[half_bytes + tc::off_kmajor(n, kappa, kKs, mns)], &bl, 2);
             }
     } else {
         const uint32_t mns = 16 * kKs;              // K = 128
@@ -686,12 +694,19 @@ hai_status epic_tc_dft_prepare(hai_ctx *ctx, int N) {
     HAI_CUDA_TRY(cudaMalloc(&d, out.size()));
     HAI_CUDA_TRY(cudaMemcpy(d, out.data(), out.size(), cudaMemcpyHostToDevice));
     ctx->d_dft[slot] = d;
+    if (!outb.empty()) {
+        void *db = nullptr;
+        HAI_CUDA_TRY(cudaMalloc(&db, outb.size()));
+        HAI_CUDA_TRY(cudaMemcpy(db, outb.data(), outb.size(), cudaMemcpyHostToDevice));
+        ctx->d_dft[3 + slot] = db;
+    }
     return HAI_OK;
 }
 
-const void *epic_tc_dft(hai_ctx *ctx, int N) {
+const void *epic_tc_dft(hai_ctx *ctx, int N, bool bf16) {
     const int slot = (N == 32) ? 0 : (N == 64) ? 1 : (N == 128) ? 2 : -1;
-    return slot < 0 ? nullptr : ctx->d_dft[slot];
+    if (slot < 0 || (bf16 && slot == 2)) return nullptr;
+    return ctx->d_dft[slot + (bf16 ? 3 : 0)];
 }
 
 void epic_tc_build_gather(int box_w, int box_h, const std::vector<int32_t> &cstart,
@@ -781,7 +796,7 @@ bool epic_tc_supported(const hai_layout *L) {
 }
 
 hai_status epic_tc_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
-                          cudaStream_t st, int split) {
+                          cudaStream_t st, int split, int bf16) {
     if (!epic_tc_supported(L) || !L->d_tc_station)
         return hai_fail(HAI_ERR_UNSUPPORTED,
                         "epic fp16: the tensor-core path needs N = 32, 64 or 128, 2 pols and a kernel box "
@@ -809,6 +824,7 @@ hai_status epic_tc_launch(const hai_layout *L, const int8_t *volt, int C, int T,
     l.partials = L->d_partials;
     l.no_attr = 0;
     l.split = split;
+    l.bf16 = bf16;
     const hai_status s = epic_tc_run(ctx, N, l, st);
     if (s != HAI_OK) return s;
     if (!sp.direct) return epic_reduce_launch(L, sp, C, T, img, accumulate, st);

@@ -152,7 +152,7 @@ double epic_tc_dft_entry(int N, int c_out, int l, int j, int c_in);
 
 // DFT operands of the tensor-core kernels for grid side N (built once per
 // context, device memory owned by the context).
-const void *epic_tc_dft(hai_ctx *ctx, int N);
+const void *epic_tc_dft(hai_ctx *ctx, int N, bool bf16 = false);
 hai_status epic_tc_dft_prepare(hai_ctx *ctx, int N);
 
 // Launchers over a list of stations of one grid side.  cta_begin (device,
@@ -178,6 +178,7 @@ struct TcLaunch {
     float *partials;
     int no_attr;            // 1: the kernel's shared-memory attribute is already set
     int split;              // 1: hi/lo split products (N = 32, 64)
+    int bf16;               // 1: BF16 operands (N = 32, 64)
 };
 // Raises the kernel's dynamic shared-memory limit to the device's.
 hai_status epic_tc_set_attr(hai_ctx *ctx, int N);

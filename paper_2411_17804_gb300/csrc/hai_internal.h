@@ -24,7 +24,7 @@ struct hai_ctx {
     std::vector<cudaEvent_t> prof_ev;   // pairs: [2i] before, [2i+1] after
     size_t prof_used = 0;               // pairs recorded
     long long prof_launches = 0;        // all kernels launched
-    void *d_dft[3] = {nullptr, nullptr, nullptr};   // tensor-core DFT operands, N = 32, 64, 128
+    void *d_dft[6] = {};                // tensor-core DFT operands: FP16 N = 32, 64, 128; BF16 N = 32, 64
     int capturing = 0;                  // a plan is capturing a graph: no profiling events
     void *d_corr_ws = nullptr;          // correlator: fp16 operand images of a batch of channels,
     size_t corr_ws_bytes = 0;           // allocated on the first hai_correlate call
@@ -128,7 +128,7 @@ hai_status epic_fp32_launch(const hai_layout *L, const int8_t *volt, int C, int 
                             int accumulate, cudaStream_t st);
 int epic_fp32_target_ctas(const hai_ctx *ctx, int grid_n);
 hai_status epic_tc_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img,
-                          int accumulate, cudaStream_t st, int split);
+                          int accumulate, cudaStream_t st, int split, int bf16);
 bool epic_tc_supported(const hai_layout *L);
 // Gather table of a layout for the tensor-core kernel of its grid side;
 // shared_bytes = what the kernel keeps in shared memory.

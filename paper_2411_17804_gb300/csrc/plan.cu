@@ -180,6 +180,7 @@ TcLaunch class_launch(const hai_plan *p, const PlanClass &c, const int8_t *volt,
     l.partials = nullptr;
     l.no_attr = 1;
     l.split = 0;
+    l.bf16 = 0;
     return l;
 }
 

@@ -150,3 +150,45 @@ def test_long_cadence_of_ten_thousand_samples(hai, ctx, long_cadence, pname):
         check(hai, prec, img.cpu().numpy(), want)
     finally:
         hai.hai_layout_destroy(lay)
+
+
+# ------------------------------------------------------------------ N = 32, 64
+@pytest.mark.parametrize("pname", ["BF16", "BF16_SPLIT", "FP16_SPLIT", "FP16"])
+@pytest.mark.parametrize("n_elem,C,T,cplx", [(256, 3, 40, False), (256, 2, 301, True), (50, 5, 9, False),
+                                              (300, 1, 1, True)])
+def test_small_grids_every_operand_form(hai, ctx, pname, n_elem, C, T, cplx):
+    """The N = 32 / 64 tensor-core kernel with FP16 or BF16 operands, plain or
+    split, against the oracle at each form's bound; the SKA station (64^2)
+    and stations of the uneven array (32^2), real and complex taps."""
+    prec = getattr(hai, f"HAI_PREC_{pname}")
+    sc = I.SKA_LOW_STATION_256 if n_elem == 256 else I.uneven_station(I.UnevenConfig(), 0, n_elem)
+    pos, anchors, taps = station(sc)
+    if cplx:
+        taps = taps.copy()
+        taps[..., 1] = 0.3 * np.random.default_rng(n_elem).standard_normal(taps.shape[:-1]).astype(np.float32)
+    volt = I.station_voltages(sc, pos, n_chan=C, n_time=T) if not cplx else \
+        I.random_voltages((C, T, 2, len(pos), 2), seed=C + T)
+    want = O.epic_image(sc.grid_n, anchors, taps, volt.numpy())
+    lay = hai.hai_layout_create(ctx, anchors, taps, sc.grid_n, 2)
+    try:
+        img = image(hai, ctx, lay, volt.cuda(), C, T, prec, sc.grid_n)
+        check(hai, prec, img.cpu().numpy(), want)
+        image(hai, ctx, lay, volt.cuda(), C, T, prec, sc.grid_n, img, 1)
+        check(hai, prec, img.cpu().numpy(), 2 * want)
+    finally:
+        hai.hai_layout_destroy(lay)
+
+
+def test_bf16_and_split_unsupported_at_128(hai, ctx):
+    sc = I.uneven_station(I.UnevenConfig(), 0, 700)
+    pos, anchors, taps = station(sc)
+    lay = hai.hai_layout_create(ctx, anchors, taps, 128, 2)
+    volt = torch.zeros((1, 2, 2, len(pos), 2), dtype=torch.int8, device="cuda")
+    img = torch.zeros((1, 4, 128, 128), device="cuda")
+    try:
+        for prec in (hai.HAI_PREC_BF16, hai.HAI_PREC_BF16_SPLIT, hai.HAI_PREC_FP16_SPLIT):
+            with pytest.raises(hai.HaiError) as e:
+                hai.hai_epic_image(ctx, lay, volt, 1, 2, prec, img, 0)
+            assert e.value.status == 4
+    finally:
+        hai.hai_layout_destroy(lay)
