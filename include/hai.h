@@ -153,6 +153,36 @@ typedef struct {
 hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *desc, hai_layout **out);
 void hai_layout_destroy(hai_layout *layout);
 
+/* A layout from element positions with the library's default illumination
+ * kernel (the paper leaves W~ to the user; Section 5.2): element a at
+ * g = pos_m[a] / (lambda_m cell_lambda) + N/2 cells (FP64) gets the K x K cells
+ * around its nearest cell floor(g + 1/2) (anchor = that cell - (K - 1) / 2 per
+ * axis) with real taps exp(-|cell - g|^2 / (2 sigma_cells^2)) normalised to
+ * unit sum.  Then as hai_layout_create (HAI_ERR_OFF_GRID if a tap leaves the
+ * grid).  hai_layout_anchors returns the anchors and taps a layout uses. */
+typedef struct {
+    int n_elem;              /* N_e > 0                                       */
+    const double *pos_m;     /* host [n_elem][2] (x, y) metres, station frame  */
+    double lambda_m;         /* wavelength                                    */
+    double cell_lambda;      /* grid cell in wavelengths                      */
+    int grid_n;              /* N                                             */
+    int ksize;               /* K, 1 .. 15                                    */
+    double sigma_cells;      /* Gaussian width in cells (> 0)                 */
+    int n_pol;               /* P: 1 or 2                                     */
+} hai_position_desc;
+hai_status hai_layout_create_from_positions(hai_ctx *ctx, const hai_position_desc *desc, hai_layout **out);
+
+/* The layout's anchors (host int32 [n_elem][2]) and taps (host float
+ * [n_elem][K][K][2], as given, not conjugated); either may be NULL. */
+hai_status hai_layout_anchors(const hai_layout *layout, int32_t *anchors, float *taps);
+
+/* Device memory held by a layout (gather tables, partial images, the scratch
+ * of its tensor-core and large-grid paths, the XFFT lists once built) or by a
+ * context (status words, DFT operands, and the correlator workspace and host
+ * staging once first used); bytes on the host. */
+hai_status hai_layout_workspace_size(const hai_layout *layout, size_t *bytes);
+hai_status hai_ctx_workspace_size(const hai_ctx *ctx, size_t *bytes);
+
 /* Bounding box of the cells the kernel touches, host int[4] = (x0, y0, x1, y1)
  * half-open. */
 hai_status hai_layout_box(const hai_layout *layout, int *box);
@@ -240,6 +270,11 @@ hai_status hai_plan_run(hai_plan *plan, const int8_t *volt, float *img, void *st
  * re-divide the SMs so that the groups' measured SM-time is balanced.  Runs
  * the kernels on (volt, img), overwriting img.  Synchronises the stream. */
 hai_status hai_plan_autotune(hai_plan *plan, const int8_t *volt, float *img, int rounds, void *stream);
+
+/* Device memory the plan holds (its copies of the gather tables, station
+ * records and per-CTA ranges), bytes on the host.  The run itself allocates
+ * nothing. */
+hai_status hai_workspace_size(const hai_plan *plan, size_t *bytes);
 
 /* Schedule of the plan (host outputs, arrays of length *n_class <= 3):
  * grid side, CTAs and last measured time alone (ms, 0 before autotuning) of

@@ -873,6 +873,7 @@ hai_status epic_big_prepare(hai_layout *L) {
     const size_t slots = (size_t)L->ctx->num_sms * Var<false>::SlotFloats * sizeof(float);
     cudaError_t e = cudaMalloc(&L->d_big, op_bytes + a1 + a2 + slots);
     if (e != cudaSuccess) return hai_cuda_fail(e, "epic tensor cores (large grid): scratch");
+    L->dev_bytes += op_bytes + a1 + a2 + slots;
     uint8_t *base = static_cast<uint8_t *>(L->d_big);
     size_t off = 0;
     int idx = 0;

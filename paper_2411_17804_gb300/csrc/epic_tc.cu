@@ -694,11 +694,13 @@ hai_status epic_tc_dft_prepare(hai_ctx *ctx, int N) {
     HAI_CUDA_TRY(cudaMalloc(&d, out.size()));
     HAI_CUDA_TRY(cudaMemcpy(d, out.data(), out.size(), cudaMemcpyHostToDevice));
     ctx->d_dft[slot] = d;
+    ctx->dev_bytes += out.size();
     if (!outb.empty()) {
         void *db = nullptr;
         HAI_CUDA_TRY(cudaMalloc(&db, outb.size()));
         HAI_CUDA_TRY(cudaMemcpy(db, outb.data(), outb.size(), cudaMemcpyHostToDevice));
         ctx->d_dft[3 + slot] = db;
+        ctx->dev_bytes += outb.size();
     }
     return HAI_OK;
 }

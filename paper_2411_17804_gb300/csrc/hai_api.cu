@@ -79,6 +79,7 @@ extern "C" hai_status hai_create(int device, hai_ctx **out) {
     // word 0: the status word; word 1: outcome of the wait self-check; word 2:
     // sink of the peak-rate probes
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 4 * sizeof(unsigned));
+    if (e == cudaSuccess) c->dev_bytes += 4 * sizeof(unsigned);
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 4 * sizeof(unsigned));
     if (e != cudaSuccess) {
         if (c->d_status) cudaFree(c->d_status);
@@ -303,15 +304,20 @@ extern "C" hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *d, 
             }
 
     cudaError_t e = cudaSetDevice(ctx->device);
-    if (e == cudaSuccess) e = cudaMalloc(&L->d_anchors, sizeof(int32_t) * 2 * ne);
-    if (e == cudaSuccess) e = cudaMalloc(&L->d_taps, sizeof(float2) * (size_t)ne * k * k);
+    auto dmalloc = [&](void **p, size_t bytes) {
+        const cudaError_t r = cudaMalloc(p, bytes);
+        if (r == cudaSuccess) L->dev_bytes += bytes;
+        return r;
+    };
+    if (e == cudaSuccess) e = dmalloc((void **)&L->d_anchors, sizeof(int32_t) * 2 * ne);
+    if (e == cudaSuccess) e = dmalloc((void **)&L->d_taps, sizeof(float2) * (size_t)ne * k * k);
     if (e == cudaSuccess)
         e = cudaMemcpy(L->d_anchors, d->anchors, sizeof(int32_t) * 2 * ne, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(L->d_taps, d->taps, sizeof(float2) * (size_t)ne * k * k, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&L->d_cell_start, sizeof(int32_t) * (ncell + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&L->d_entry_elem, sizeof(int32_t) * std::max(1, L->nnz));
-    if (e == cudaSuccess) e = cudaMalloc(&L->d_entry_w, sizeof(float2) * std::max(1, L->nnz));
+    if (e == cudaSuccess) e = dmalloc((void **)&L->d_cell_start, sizeof(int32_t) * (ncell + 1));
+    if (e == cudaSuccess) e = dmalloc((void **)&L->d_entry_elem, sizeof(int32_t) * std::max(1, L->nnz));
+    if (e == cudaSuccess) e = dmalloc((void **)&L->d_entry_w, sizeof(float2) * std::max(1, L->nnz));
     if (e == cudaSuccess)
         e = cudaMemcpy(L->d_cell_start, count.data(), sizeof(int32_t) * (ncell + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -324,11 +330,11 @@ extern "C" hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *d, 
     if (n <= 128) {
         L->partial_slots = epic_partial_slots(std::max(epic_fp32_target_ctas(ctx, n), ctx->num_sms));
         if (e == cudaSuccess)
-            e = cudaMalloc(&L->d_partials, sizeof(float) * L->partial_slots * Q * (size_t)n * n);
+            e = dmalloc((void **)&L->d_partials, sizeof(float) * L->partial_slots * Q * (size_t)n * n);
     }
     if (n >= 128 && e == cudaSuccess) {
         L->large_scratch_bytes = epic_large_scratch_bytes(n, L->box_h);
-        e = cudaMalloc(&L->d_large_scratch, L->large_scratch_bytes);
+        e = dmalloc(&L->d_large_scratch, L->large_scratch_bytes);
     }
     if (e == cudaSuccess && epic_tc_supported(L)) {   // tensor-core path: gather table, station record
         std::vector<uint8_t> tab;
@@ -338,12 +344,12 @@ extern "C" hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *d, 
                               L->tc_entries);
         L->tc_tables_bytes = shared_bytes;
         L->tc_blob_bytes = tab.size();
-        e = cudaMalloc(&L->d_tc_tables, tab.size());
+        e = dmalloc(&L->d_tc_tables, tab.size());
         if (e == cudaSuccess) e = cudaMemcpy(L->d_tc_tables, tab.data(), tab.size(), cudaMemcpyHostToDevice);
         rec.table = static_cast<const uint8_t *>(L->d_tc_tables);
         rec.ne = ne;
         rec.table_bytes = shared_bytes;
-        if (e == cudaSuccess) e = cudaMalloc(&L->d_tc_station, sizeof(TcStation));
+        if (e == cudaSuccess) e = dmalloc(&L->d_tc_station, sizeof(TcStation));
         if (e == cudaSuccess) e = cudaMemcpy(L->d_tc_station, &rec, sizeof(TcStation), cudaMemcpyHostToDevice);
         if (e == cudaSuccess && epic_tc_dft_prepare(ctx, n) != HAI_OK) e = cudaErrorMemoryAllocation;
         L->tc_groups = n == 128 ? std::min(ctx->num_sms / 4, epic_tc128_max_groups(ctx, ne, shared_bytes))
@@ -419,6 +425,67 @@ extern "C" void hai_layout_destroy(hai_layout *L) {
     if (!L) return;
     cudaSetDevice(L->ctx->device);
     layout_free(L);
+}
+
+// Default illumination kernel (the paper leaves W~ to the user): a real
+// Gaussian of sigma_cells evaluated at the K x K cells around the element's
+// nearest cell floor(g + 1/2), g = pos / (lambda cell) + N/2 in FP64,
+// normalised to unit sum; tap (u, v) on cell (x0 + u, y0 + v).
+extern "C" hai_status hai_layout_create_from_positions(hai_ctx *ctx, const hai_position_desc *d, hai_layout **out) {
+    if (!ctx || !d || !out || !d->pos_m) return hai_fail(HAI_ERR_INVALID_ARG, "hai_layout_create_from_positions: NULL argument");
+    *out = nullptr;
+    if (d->n_elem <= 0 || d->ksize <= 0 || d->ksize > 15 || !(d->lambda_m > 0) || !(d->cell_lambda > 0) ||
+        !(d->sigma_cells > 0))
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_layout_create_from_positions: bad descriptor");
+    const int ne = d->n_elem, k = d->ksize;
+    std::vector<int32_t> anchors(2 * (size_t)ne);
+    std::vector<float> taps(2 * (size_t)ne * k * k, 0.f);
+    std::vector<double> w((size_t)k * k);
+    for (int a = 0; a < ne; a++) {
+        double gc[2];
+        for (int ax = 0; ax < 2; ax++) {
+            gc[ax] = d->pos_m[2 * a + ax] / (d->lambda_m * d->cell_lambda) + d->grid_n / 2.0;
+            if (!std::isfinite(gc[ax]) || std::fabs(gc[ax]) > 1e9)
+                return hai_fail(HAI_ERR_OFF_GRID, "hai_layout_create_from_positions: element position off the grid");
+            anchors[2 * a + ax] = (int32_t)std::floor(gc[ax] + 0.5) - (k - 1) / 2;
+        }
+        double sum = 0;
+        for (int v = 0; v < k; v++)
+            for (int u = 0; u < k; u++) {
+                const double dx = anchors[2 * a] + u - gc[0], dy = anchors[2 * a + 1] + v - gc[1];
+                w[(size_t)v * k + u] = std::exp(-(dx * dx + dy * dy) / (2 * d->sigma_cells * d->sigma_cells));
+                sum += w[(size_t)v * k + u];
+            }
+        for (int i = 0; i < k * k; i++) taps[((size_t)a * k * k + i) * 2] = (float)(w[i] / sum);
+    }
+    hai_layout_desc ld;
+    ld.n_elem = ne;
+    ld.grid_n = d->grid_n;
+    ld.ksize = k;
+    ld.n_pol = d->n_pol;
+    ld.anchors = anchors.data();
+    ld.taps = taps.data();
+    return hai_layout_create(ctx, &ld, out);
+}
+
+extern "C" hai_status hai_layout_anchors(const hai_layout *L, int32_t *anchors, float *taps) {
+    if (!L) return hai_fail(HAI_ERR_INVALID_ARG, "hai_layout_anchors: NULL layout");
+    if (anchors) memcpy(anchors, L->h_anchors.data(), sizeof(int32_t) * L->h_anchors.size());
+    if (taps) memcpy(taps, L->h_taps.data(), sizeof(float) * L->h_taps.size());
+    return HAI_OK;
+}
+
+extern "C" hai_status hai_layout_workspace_size(const hai_layout *L, size_t *bytes) {
+    if (!L || !bytes) return hai_fail(HAI_ERR_INVALID_ARG, "hai_layout_workspace_size: NULL argument");
+    std::lock_guard<std::mutex> g(L->xfft_mu);
+    *bytes = L->dev_bytes;
+    return HAI_OK;
+}
+
+extern "C" hai_status hai_ctx_workspace_size(const hai_ctx *ctx, size_t *bytes) {
+    if (!ctx || !bytes) return hai_fail(HAI_ERR_INVALID_ARG, "hai_ctx_workspace_size: NULL argument");
+    *bytes = ctx->dev_bytes + ctx->corr_ws_bytes + ctx->stage_bytes;
+    return HAI_OK;
 }
 
 extern "C" hai_status hai_layout_box(const hai_layout *L, int *box) {

@@ -33,6 +33,7 @@ struct hai_ctx {
     cudaStream_t copy_stream = nullptr;
     void *d_stage = nullptr;
     size_t stage_bytes = 0;
+    size_t dev_bytes = 0;               // other device memory the context holds (status, DFT operands)
 };
 
 // Operand workspace of the correlator and the XFFT (allocated on first use by
@@ -84,6 +85,7 @@ struct hai_layout {
     mutable int32_t *d_xcell = nullptr, *d_xent = nullptr;
     mutable float2 *d_xk = nullptr;
     mutable std::mutex xfft_mu;
+    mutable size_t dev_bytes = 0;       // device memory the layout holds (guarded by xfft_mu after creation)
 };
 
 // ---------------------------------------------------------------- errors

@@ -32,6 +32,7 @@ struct PlanClass {
     std::vector<TcStation> host_st;
     TcStation *d_st = nullptr;
     long long *d_begin = nullptr;         // per CTA (group) first flat sample, n_cta + 1
+    size_t begin_bytes = 0;
     int n_cta = 0;                        // CTAs, or clusters for N = 128
     int ne_max = 0;
     uint32_t table_max = 0;
@@ -54,6 +55,7 @@ struct hai_plan {
     std::vector<long long> volt_off, img_off;
     long long volt_bytes = 0, img_floats = 0;
     std::vector<void *> tables;            // plan-owned copies of the gather tables
+    size_t table_bytes = 0;                // their total size
     std::vector<PlanClass> cls;
     cudaStream_t cap = nullptr;
     cudaEvent_t fork = nullptr;
@@ -112,6 +114,7 @@ hai_status class_upload_ranges(hai_plan *p, PlanClass &c, int want) {
     cudaFree(c.d_begin);
     c.d_begin = nullptr;
     HAI_CUDA_TRY(cudaMalloc(&c.d_begin, sizeof(long long) * begin.size()));
+    c.begin_bytes = sizeof(long long) * begin.size();
     HAI_CUDA_TRY(cudaMemcpy(c.d_begin, begin.data(), sizeof(long long) * begin.size(), cudaMemcpyHostToDevice));
     return HAI_OK;
 }
@@ -274,6 +277,7 @@ extern "C" hai_status hai_plan_create(hai_ctx *ctx, const hai_layout *const *sta
             const hai_layout *L = stations[s];
             void *tab = nullptr;
             if (e == cudaSuccess) e = cudaMalloc(&tab, L->tc_blob_bytes);
+            if (e == cudaSuccess) p->table_bytes += L->tc_blob_bytes;
             if (e == cudaSuccess)
                 e = cudaMemcpy(tab, L->d_tc_tables, L->tc_blob_bytes, cudaMemcpyDeviceToDevice);
             if (tab) p->tables.push_back(tab);
@@ -331,6 +335,14 @@ extern "C" hai_status hai_plan_layout(const hai_plan *p, int64_t *volt_off, int6
     }
     if (volt_bytes) *volt_bytes = p->volt_bytes;
     if (img_floats) *img_floats = p->img_floats;
+    return HAI_OK;
+}
+
+extern "C" hai_status hai_workspace_size(const hai_plan *p, size_t *bytes) {
+    if (!p || !bytes) return hai_fail(HAI_ERR_INVALID_ARG, "hai_workspace_size: NULL argument");
+    size_t b = p->table_bytes;
+    for (const auto &c : p->cls) b += sizeof(TcStation) * c.host_st.size() + c.begin_bytes;
+    *bytes = b;
     return HAI_OK;
 }
 

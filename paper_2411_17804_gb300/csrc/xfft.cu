@@ -232,6 +232,7 @@ static hai_status ensure_table(const hai_layout *L) {
     L->d_xent = d_ent;
     L->d_xk = d_k;
     L->d_xcell = d_start;
+    L->dev_bytes += sizeof(int32_t) * (start.size() + ent.size()) + sizeof(float2) * kv.size();
     return HAI_OK;
 }
 

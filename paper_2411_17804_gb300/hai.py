@@ -38,6 +38,12 @@ class _LayoutDesc(ctypes.Structure):
                 ("n_pol", ctypes.c_int), ("anchors", ctypes.c_void_p), ("taps", ctypes.c_void_p)]
 
 
+class _PositionDesc(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int), ("pos_m", ctypes.c_void_p), ("lambda_m", ctypes.c_double),
+                ("cell_lambda", ctypes.c_double), ("grid_n", ctypes.c_int), ("ksize", ctypes.c_int),
+                ("sigma_cells", ctypes.c_double), ("n_pol", ctypes.c_int)]
+
+
 class _VisLayoutDesc(ctypes.Structure):
     _fields_ = [("n_station", ctypes.c_int), ("pos_m", ctypes.c_void_p), ("lambda_m", ctypes.c_double),
                 ("cell_m", ctypes.c_double), ("grid_n", ctypes.c_int), ("n_pol", ctypes.c_int),
@@ -93,6 +99,11 @@ def _declare(L):
     L.hai_xfft_station_image.argtypes = [_vp, _vp, _vp, _int, _vp, _vp]
     L.hai_profile_enable.argtypes = [_vp, _int, _int]
     L.hai_check_device_wait.argtypes = [_vp, ctypes.c_longlong, _vp]
+    L.hai_layout_create_from_positions.argtypes = [_vp, ctypes.POINTER(_PositionDesc), ctypes.POINTER(_vp)]
+    L.hai_layout_anchors.argtypes = [_vp, _vp, _vp]
+    L.hai_layout_workspace_size.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.hai_ctx_workspace_size.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.hai_workspace_size.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
     L.hai_probe_peak.argtypes = [_vp, _int, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), _vp]
     L.hai_check_device_wait_result.argtypes = [_vp, ctypes.POINTER(_int)]
     L.hai_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
@@ -232,6 +243,44 @@ def hai_layout_create(ctx, anchors, taps, grid_n: int, n_pol: int) -> Layout:
 
 def hai_layout_destroy(layout: Layout):
     load().hai_layout_destroy(layout.handle)
+
+
+def hai_layout_create_from_positions(ctx, pos_m, lambda_m: float, cell_lambda: float, grid_n: int, ksize: int,
+                                     sigma_cells: float, n_pol: int) -> Layout:
+    pos = np.ascontiguousarray(pos_m, np.float64)
+    if pos.ndim != 2 or pos.shape[1] != 2:
+        raise ValueError("pos_m must be [n][2]")
+    d = _PositionDesc(len(pos), pos.ctypes.data, lambda_m, cell_lambda, grid_n, ksize, sigma_cells, n_pol)
+    h = _vp()
+    _check(load().hai_layout_create_from_positions(ctx, ctypes.byref(d), ctypes.byref(h)),
+           "hai_layout_create_from_positions")
+    return Layout(h, len(pos), grid_n, ksize, n_pol)
+
+
+def hai_layout_anchors(layout: Layout):
+    """(anchors int32 [n][2], taps float32 [n][K][K][2]) the layout uses."""
+    a = np.empty((layout.n_elem, 2), np.int32)
+    t = np.empty((layout.n_elem, layout.ksize, layout.ksize, 2), np.float32)
+    _check(load().hai_layout_anchors(layout.handle, a.ctypes.data, t.ctypes.data), "hai_layout_anchors")
+    return a, t
+
+
+def hai_layout_workspace_size(layout: Layout) -> int:
+    b = ctypes.c_size_t()
+    _check(load().hai_layout_workspace_size(layout.handle, ctypes.byref(b)), "hai_layout_workspace_size")
+    return b.value
+
+
+def hai_ctx_workspace_size(ctx) -> int:
+    b = ctypes.c_size_t()
+    _check(load().hai_ctx_workspace_size(ctx, ctypes.byref(b)), "hai_ctx_workspace_size")
+    return b.value
+
+
+def hai_workspace_size(plan) -> int:
+    b = ctypes.c_size_t()
+    _check(load().hai_workspace_size(plan.handle, ctypes.byref(b)), "hai_workspace_size")
+    return b.value
 
 
 def hai_layout_box(layout: Layout):
