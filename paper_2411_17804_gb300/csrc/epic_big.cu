@@ -316,8 +316,8 @@ __global__ void __launch_bounds__(kS1Threads, 1) big_s1_kernel(const S1Params p)
                 const uint32_t d = tmem + (uint32_t)b * V::NM;
                 for (int kb = 0; kb < g.kb1; kb++, gs++) {
                     const int s = (int)(gs % V::S1Stages);
+                    // bulk-copied stage: no tcgen05 fence needed (see stage 2)
                     tc::mbar_wait(&full[s], (uint32_t)((gs / V::S1Stages) & 1), p.status);
-                    tc::fence_after();
                     const uint32_t a = tc::smem_u32(sA0 + (size_t)s * V::AStage);
                     const uint32_t bq = tc::smem_u32(sB + (size_t)kb * V::BTile);
 #pragma unroll
@@ -381,15 +381,14 @@ __global__ void __launch_bounds__(kS1Threads, 1) big_s1_kernel(const S1Params p)
                             hi[e] = tc::pack2<BF>(b0, b1v);
                         }
                     }
+                    // K values kk (re) and kk + 1 (im) are adjacent 16-byte rows of
+                    // the MN-major tile (kk even): one 32-byte store
                     const int m = m0 + 8 * half;
                     const size_t o_r = toff + tc::off_mnmajor(m, kk, kMKs, kMMN);
-                    const size_t o_i = toff + tc::off_mnmajor(m, kk + 1, kMKs, kMMN);
-                    *reinterpret_cast<uint4 *>(p.a2 + o_r) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-                    *reinterpret_cast<uint4 *>(p.a2 + o_i) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                    if constexpr (SP) {
-                        *reinterpret_cast<uint4 *>(p.a2lo + o_r) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-                        *reinterpret_cast<uint4 *>(p.a2lo + o_i) = make_uint4(li[0], li[1], li[2], li[3]);
-                    }
+                    tc::st_global_v8(p.a2 + o_r, make_uint4(hr[0], hr[1], hr[2], hr[3]), make_uint4(hi[0], hi[1], hi[2], hi[3]));
+                    if constexpr (SP)
+                        tc::st_global_v8(p.a2lo + o_r, make_uint4(lr[0], lr[1], lr[2], lr[3]),
+                                         make_uint4(li[0], li[1], li[2], li[3]));
                 }
             }
             tc::fence_before();
@@ -519,8 +518,10 @@ __global__ void __launch_bounds__(576, 1) big_s2_kernel(const S2Params p) {
                     const uint32_t d = tmem + (uint32_t)b * V::NM;
                     for (int kb = 0; kb < kKb2; kb++, gk++) {
                         const int st = (int)(gk % V::S2Stages);
+                        // a stage filled by bulk copies (async proxy, completed on the
+                        // mbarrier) needs no tcgen05 fence before the MMAs read it; the
+                        // fence above orders them after the epilogue's TMEM reads
                         tc::mbar_wait(&afull[st], (uint32_t)((gk / V::S2Stages) & 1), p.status);
-                        tc::fence_after();
                         const uint32_t a = sa0 + (uint32_t)st * V::AStage;
                         const uint32_t bq = sb0 + (uint32_t)kb * V::BTile;
 #pragma unroll

@@ -212,6 +212,13 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// One 32-byte store to global memory (32-byte aligned address).
+__device__ __forceinline__ void st_global_v8(void *p, uint4 lo, uint4 hi) {
+    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(lo.x), "r"(lo.y), "r"(lo.z),
+                 "r"(lo.w), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w)
+                 : "memory");
+}
+
 // Prefetch `bytes` (multiple of 16, 16-byte aligned) of global memory into L2,
 // so that a later bulk copy of them is an L2 hit.
 __device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
