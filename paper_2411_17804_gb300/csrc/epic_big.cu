@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kS1Threads, 1) big_s1_kernel(const S1Params p)
         }
         for (int b = 0; b < 2; b++) {
             tc::mbar_init(&dfull[b], 1);
-            tc::mbar_init(&dempty[b], 512);
+            tc::mbar_init(&dempty[b], 16);              // one arrival per epilogue warp
         }
         tc::mbar_init(&bfull, 1);
         tc::mbar_fence_init();
@@ -352,7 +352,10 @@ __global__ void __launch_bounds__(kS1Threads, 1) big_s1_kernel(const S1Params p)
             const long long f = tile % nf;
             const int pol = (int)(f % g.P);
             const long long ct = f / g.P;                       // (c, s) of the batch
-            tc::mbar_wait(&dfull[b], (uint32_t)((gt >> 1) & 1), p.status);
+            // one lane of the warp waits, the warp follows (the wait's result
+            // reaches the others through the warp barrier)
+            if (lane == 0) tc::mbar_wait(&dfull[b], (uint32_t)((gt >> 1) & 1), p.status);
+            __syncwarp();
             tc::fence_after();
 #pragma unroll 1
             for (int ch = kChunks * h; ch < kChunks * h + kChunks; ch++) {
@@ -391,8 +394,10 @@ __global__ void __launch_bounds__(kS1Threads, 1) big_s1_kernel(const S1Params p)
                                          make_uint4(li[0], li[1], li[2], li[3]));
                 }
             }
+            // one arrival per warp once all its lanes' TMEM reads are done
             tc::fence_before();
-            tc::mbar_arrive(&dempty[b]);
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&dempty[b]);
         }
     }
     tc::fence_before();
@@ -439,7 +444,7 @@ __global__ void __launch_bounds__(576, 1) big_s2_kernel(const S2Params p) {
         }
         for (int b = 0; b < 2; b++) {
             tc::mbar_init(&dfull[b], 1);
-            tc::mbar_init(&dempty[b], kEpi);
+            tc::mbar_init(&dempty[b], kEpi / 32);       // one arrival per epilogue warp
         }
         tc::mbar_fence_init();
     }
@@ -563,7 +568,8 @@ __global__ void __launch_bounds__(576, 1) big_s2_kernel(const S2Params p) {
             for (int t = 0; t < kLy / 2; t++) acc_a[t] = acc_x[t] = make_float2(0.f, 0.f);
             for (int s = s0; s < s1; s++, gs++) {
                 const int b = (int)(gs & 1);
-                tc::mbar_wait(&dfull[b], (uint32_t)((gs >> 1) & 1), p.status);
+                if (lane == 0) tc::mbar_wait(&dfull[b], (uint32_t)((gs >> 1) & 1), p.status);
+                __syncwarp();
                 tc::fence_after();
                 // 8 l_y at a time (re and im: 16 registers): the pixel pairs
                 // (2k, 2k + 1) of the cross term stay inside each group
@@ -594,7 +600,8 @@ __global__ void __launch_bounds__(576, 1) big_s2_kernel(const S2Params p) {
                     }
                 }
                 tc::fence_before();
-                tc::mbar_arrive(&dempty[b]);
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&dempty[b]);
             }
             // the part's pixel tile: planes XX, YY, Re XY, Im XY of channel c,
             // to the image (the item's first sample is here) or to this CTA's slot
