@@ -147,71 +147,106 @@ __global__ void __launch_bounds__(256) big_grid_kernel(const int8_t *__restrict_
         }
 }
 
-// The same gridding with the field's voltages staged in shared memory: one
-// CTA per field loads its N_e complex int8 voltages with 16-byte loads, then
-// every thread builds whole 16-byte runs of A1 (4 cells of one row: 8 values),
-// eight consecutive threads covering the 128 contiguous bytes of one k group
-// of 8 rows.  Used when the field fits (kGridSmemMax bytes).
+// The same gridding with the voltages staged in shared memory: one CTA per
+// kGridFb consecutive fields (both polarisations of a sample) loads their N_e
+// complex int8 voltages with 16-byte loads, then every thread builds whole
+// 16-byte runs of A1 (4 cells of one row: 8 values) for each field, eight
+// consecutive threads covering the 128 contiguous bytes of one k group of 8
+// rows.  The 4 cells' gather entries are contiguous in the table, read four at
+// a time with independent loads and shared by the CTA's fields.  Used when the
+// fields fit (kGridSmemMax bytes).
 constexpr int kGridThreads = 512;
 constexpr int kGridSmemMax = 96 * 1024;
+constexpr int kGridFb = 2;
 
 template <bool BF, bool SP>
 __global__ void __launch_bounds__(kGridThreads) big_grid_smem_kernel(
     const int8_t *__restrict__ volt, int ne, int T, const int32_t *__restrict__ cell_start,
     const int32_t *__restrict__ entry_elem, const float2 *__restrict__ entry_w, BigGeo g, int t0, int tb,
-    uint8_t *__restrict__ a1, uint8_t *__restrict__ a1lo) {
-    extern __shared__ __align__(16) char2 sv[];
-    const long long f = blockIdx.x;
-    const long long ct = f / g.P;
-    const int pol = (int)(f % g.P);
-    const long long c = ct / tb, t = t0 + ct % tb;
-    const int8_t *src = volt + ((c * T + t) * g.P + pol) * (long long)ne * 2;
+    long long nfield, uint8_t *__restrict__ a1, uint8_t *__restrict__ a1lo) {
+    extern __shared__ __align__(16) char2 sv[];             // [kGridFb][ne]
+    const long long f0 = (long long)blockIdx.x * kGridFb;
+    const int nf = (int)(nfield - f0 < kGridFb ? nfield - f0 : kGridFb);
     const int nbytes = 2 * ne;
-    if (((reinterpret_cast<uintptr_t>(src) | (uintptr_t)nbytes) & 15) == 0) {
-        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-        uint4 *d4 = reinterpret_cast<uint4 *>(sv);
-        for (int i = threadIdx.x; i < nbytes / 16; i += blockDim.x) d4[i] = __ldg(s4 + i);
-    } else {
-        const char2 *s2 = reinterpret_cast<const char2 *>(src);
-        for (int i = threadIdx.x; i < ne; i += blockDim.x) sv[i] = s2[i];
+    for (int j = 0; j < nf; j++) {
+        const long long f = f0 + j;
+        const long long ct = f / g.P;
+        const int pol = (int)(f % g.P);
+        const long long c = ct / tb, t = t0 + ct % tb;
+        const int8_t *src = volt + ((c * T + t) * g.P + pol) * (long long)ne * 2;
+        char2 *dst = sv + (size_t)j * ne;
+        if (((reinterpret_cast<uintptr_t>(src) | (uintptr_t)nbytes) & 15) == 0) {
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+            uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+            for (int i = threadIdx.x; i < nbytes / 16; i += blockDim.x) d4[i] = __ldg(s4 + i);
+        } else {
+            const char2 *s2 = reinterpret_cast<const char2 *>(src);
+            for (int i = threadIdx.x; i < ne; i += blockDim.x) dst[i] = s2[i];
+        }
     }
     __syncthreads();
     const int nkg = g.kb1 * 8;                       // k groups (4 cells each) per row
     const int nchunk = 128 * nkg;
     const size_t field_bytes = (size_t)g.kb1 * kTile16;
-    uint8_t *dst = a1 + (size_t)f * field_bytes;
-    uint8_t *dlo = SP ? a1lo + (size_t)f * field_bytes : nullptr;
     for (int q = threadIdx.x; q < nchunk; q += blockDim.x) {
         const int y = (q & 7) + 8 * (q / (8 * nkg)), kg = (q >> 3) % nkg;
-        float2 acc[4];
+        const int x0 = 4 * kg;
+        float2 acc[kGridFb][4];
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-            acc[i] = make_float2(0.f, 0.f);
-            const int x = 4 * kg + i;
-            if (x < g.bx && y < g.by) {
-                const int cell = y * g.bx + x;
-                for (int k = cell_start[cell]; k < cell_start[cell + 1]; k++) {
-                    const char2 v = sv[entry_elem[k]];
-                    const float2 w = entry_w[k];             // conj(W~)
-                    acc[i].x = fmaf(w.x, (float)v.x, fmaf(-w.y, (float)v.y, acc[i].x));
-                    acc[i].y = fmaf(w.x, (float)v.y, fmaf(w.y, (float)v.x, acc[i].y));
+        for (int j = 0; j < kGridFb; j++)
+#pragma unroll
+            for (int i = 0; i < 4; i++) acc[j][i] = make_float2(0.f, 0.f);
+        if (y < g.by && x0 < g.bx) {
+            // entries of cells x0 .. x0+3 (those inside the box): [cs[0], cs[4])
+            const int cell0 = y * g.bx + x0;
+            int cs[5];
+#pragma unroll
+            for (int i = 0; i < 5; i++) cs[i] = cell_start[cell0 + min(i, g.bx - x0)];
+            for (int k = cs[0]; k < cs[4]; k += 4) {
+                int e[4];
+                float2 w[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const bool ok = k + u < cs[4];
+                    e[u] = ok ? entry_elem[k + u] : 0;
+                    w[u] = ok ? entry_w[k + u] : make_float2(0.f, 0.f);     // conj(W~); 0 past the end
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int kk = k + u;
+                    const int ci = (kk >= cs[1]) + (kk >= cs[2]) + (kk >= cs[3]);
+#pragma unroll
+                    for (int j = 0; j < kGridFb; j++) {
+                        const char2 v = sv[(size_t)j * ne + e[u]];
+#pragma unroll
+                        for (int i = 0; i < 4; i++)
+                            if (i == ci) {
+                                acc[j][i].x = fmaf(w[u].x, (float)v.x, fmaf(-w[u].y, (float)v.y, acc[j][i].x));
+                                acc[j][i].y = fmaf(w[u].x, (float)v.y, fmaf(w[u].y, (float)v.x, acc[j][i].y));
+                            }
+                    }
                 }
             }
         }
         const size_t off = (size_t)(kg >> 3) * kTile16 + (size_t)(y >> 3) * kKMN + (size_t)(kg & 7) * kKBytes +
                            (size_t)(y & 7) * 16;
-        if constexpr (SP) {
-            uint4 hi, lo;
-            tc::pack2_split<BF>(acc[0].x, acc[0].y, hi.x, lo.x);
-            tc::pack2_split<BF>(acc[1].x, acc[1].y, hi.y, lo.y);
-            tc::pack2_split<BF>(acc[2].x, acc[2].y, hi.z, lo.z);
-            tc::pack2_split<BF>(acc[3].x, acc[3].y, hi.w, lo.w);
-            *reinterpret_cast<uint4 *>(dst + off) = hi;
-            *reinterpret_cast<uint4 *>(dlo + off) = lo;
-        } else {
-            *reinterpret_cast<uint4 *>(dst + off) =
-                make_uint4(tc::pack2<BF>(acc[0].x, acc[0].y), tc::pack2<BF>(acc[1].x, acc[1].y),
-                           tc::pack2<BF>(acc[2].x, acc[2].y), tc::pack2<BF>(acc[3].x, acc[3].y));
+#pragma unroll
+        for (int j = 0; j < kGridFb; j++) {
+            if (j >= nf) break;
+            uint8_t *dst = a1 + (size_t)(f0 + j) * field_bytes + off;
+            if constexpr (SP) {
+                uint4 hi, lo;
+                tc::pack2_split<BF>(acc[j][0].x, acc[j][0].y, hi.x, lo.x);
+                tc::pack2_split<BF>(acc[j][1].x, acc[j][1].y, hi.y, lo.y);
+                tc::pack2_split<BF>(acc[j][2].x, acc[j][2].y, hi.z, lo.z);
+                tc::pack2_split<BF>(acc[j][3].x, acc[j][3].y, hi.w, lo.w);
+                *reinterpret_cast<uint4 *>(dst) = hi;
+                *reinterpret_cast<uint4 *>(a1lo + (size_t)(f0 + j) * field_bytes + off) = lo;
+            } else {
+                *reinterpret_cast<uint4 *>(dst) =
+                    make_uint4(tc::pack2<BF>(acc[j][0].x, acc[j][0].y), tc::pack2<BF>(acc[j][1].x, acc[j][1].y),
+                               tc::pack2<BF>(acc[j][2].x, acc[j][2].y), tc::pack2<BF>(acc[j][3].x, acc[j][3].y));
+            }
         }
     }
 }
@@ -790,10 +825,10 @@ hai_status launch_variant(const hai_layout *L, const int8_t *volt, int C, int T,
         const int tb = std::min(tb_max, T - t0);
         const long long nfield = (long long)Cc * tb * g.P;
         const int ncell = (g.kb1 * 32) * 128;
-        const size_t vbytes = ((size_t)2 * L->n_elem + 15) & ~(size_t)15;
+        const size_t vbytes = (size_t)kGridFb * 2 * L->n_elem;
         if (vbytes <= (size_t)kGridSmemMax)
-            big_grid_smem_kernel<BF, SP><<<(unsigned)nfield, kGridThreads, vbytes, st>>>(
-                vc, L->n_elem, T, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g, t0, tb, a1, a1lo);
+            big_grid_smem_kernel<BF, SP><<<(unsigned)((nfield + kGridFb - 1) / kGridFb), kGridThreads, vbytes, st>>>(
+                vc, L->n_elem, T, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g, t0, tb, nfield, a1, a1lo);
         else
             big_grid_kernel<BF, SP><<<dim3((ncell + 255) / 256, (unsigned)((nfield + kGridFields - 1) / kGridFields)),
                                       256, 0, st>>>(vc, L->n_elem, T, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g,
