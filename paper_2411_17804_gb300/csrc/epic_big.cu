@@ -163,28 +163,41 @@ template <bool BF, bool SP>
 __global__ void __launch_bounds__(kGridThreads) big_grid_smem_kernel(
     const int8_t *__restrict__ volt, int ne, int T, const int32_t *__restrict__ cell_start,
     const int32_t *__restrict__ entry_elem, const float2 *__restrict__ entry_w, BigGeo g, int t0, int tb,
-    long long nfield, uint8_t *__restrict__ a1, uint8_t *__restrict__ a1lo) {
+    long long nfield, uint8_t *__restrict__ a1, uint8_t *__restrict__ a1lo, unsigned *status) {
     extern __shared__ __align__(16) char2 sv[];             // [kGridFb][ne]
+    __shared__ __align__(8) uint64_t vfull;
     const long long f0 = (long long)blockIdx.x * kGridFb;
     const int nf = (int)(nfield - f0 < kGridFb ? nfield - f0 : kGridFb);
     const int nbytes = 2 * ne;
+    const int8_t *src[kGridFb];
+    bool aligned = (nbytes & 15) == 0;
     for (int j = 0; j < nf; j++) {
         const long long f = f0 + j;
         const long long ct = f / g.P;
         const int pol = (int)(f % g.P);
         const long long c = ct / tb, t = t0 + ct % tb;
-        const int8_t *src = volt + ((c * T + t) * g.P + pol) * (long long)ne * 2;
-        char2 *dst = sv + (size_t)j * ne;
-        if (((reinterpret_cast<uintptr_t>(src) | (uintptr_t)nbytes) & 15) == 0) {
-            const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-            uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-            for (int i = threadIdx.x; i < nbytes / 16; i += blockDim.x) d4[i] = __ldg(s4 + i);
-        } else {
-            const char2 *s2 = reinterpret_cast<const char2 *>(src);
-            for (int i = threadIdx.x; i < ne; i += blockDim.x) dst[i] = s2[i];
-        }
+        src[j] = volt + ((c * T + t) * g.P + pol) * (long long)ne * 2;
+        aligned = aligned && (reinterpret_cast<uintptr_t>(src[j]) & 15) == 0;
     }
-    __syncthreads();
+    if (aligned) {
+        // one bulk copy per field (TMA), completed on an mbarrier
+        if (threadIdx.x == 0) {
+            tc::mbar_init(&vfull, 1);
+            tc::mbar_fence_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc::mbar_arrive_expect_tx(&vfull, (uint32_t)(nf * nbytes));
+            for (int j = 0; j < nf; j++) tc::bulk_g2s(sv + (size_t)j * ne, src[j], (uint32_t)nbytes, &vfull);
+        }
+        tc::mbar_wait(&vfull, 0u, status);
+    } else {
+        for (int j = 0; j < nf; j++) {
+            const char2 *s2 = reinterpret_cast<const char2 *>(src[j]);
+            for (int i = threadIdx.x; i < ne; i += blockDim.x) sv[(size_t)j * ne + i] = s2[i];
+        }
+        __syncthreads();
+    }
     const int nkg = g.kb1 * 8;                       // k groups (4 cells each) per row
     const int nchunk = 128 * nkg;
     const size_t field_bytes = (size_t)g.kb1 * kTile16;
@@ -828,7 +841,8 @@ hai_status launch_variant(const hai_layout *L, const int8_t *volt, int C, int T,
         const size_t vbytes = (size_t)kGridFb * 2 * L->n_elem;
         if (vbytes <= (size_t)kGridSmemMax)
             big_grid_smem_kernel<BF, SP><<<(unsigned)((nfield + kGridFb - 1) / kGridFb), kGridThreads, vbytes, st>>>(
-                vc, L->n_elem, T, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g, t0, tb, nfield, a1, a1lo);
+                vc, L->n_elem, T, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g, t0, tb, nfield, a1, a1lo,
+                ctx->d_status);
         else
             big_grid_kernel<BF, SP><<<dim3((ncell + 255) / 256, (unsigned)((nfield + kGridFields - 1) / kGridFields)),
                                       256, 0, st>>>(vc, L->n_elem, T, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g,
