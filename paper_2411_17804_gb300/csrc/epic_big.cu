@@ -159,45 +159,64 @@ constexpr int kGridThreads = 512;
 constexpr int kGridSmemMax = 96 * 1024;
 constexpr int kGridFb = 2;
 
+// 32-bit words of one field's voltages in shared memory: ne words hold the
+// 2 ne bytes twice over (one word per element pair, rounded up), plus 2 pad
+// words per 32; kept even so that 8-byte stores stay aligned.
+__host__ __device__ __forceinline__ int gridw_padded(int ne) {
+    const int w = (ne + 1) / 2;
+    return ((w + 2 * ((w + 31) >> 5)) + 1) & ~1;
+}
+
 template <bool BF, bool SP>
 __global__ void __launch_bounds__(kGridThreads) big_grid_smem_kernel(
     const int8_t *__restrict__ volt, int ne, int T, const int32_t *__restrict__ cell_start,
     const int32_t *__restrict__ entry_elem, const float2 *__restrict__ entry_w, BigGeo g, int t0, int tb,
-    long long nfield, uint8_t *__restrict__ a1, uint8_t *__restrict__ a1lo, unsigned *status) {
-    extern __shared__ __align__(16) char2 sv[];             // [kGridFb][ne]
-    __shared__ __align__(8) uint64_t vfull;
+    long long nfield, uint8_t *__restrict__ a1, uint8_t *__restrict__ a1lo) {
+    // voltages in shared memory with 2 pad words after every 32 (word w at
+    // w + 2 (w >> 5)): rows of a lattice 64 words apart then fall on
+    // different banks
+    extern __shared__ __align__(16) uint32_t sw[];          // [kGridFb][padded words]
     const long long f0 = (long long)blockIdx.x * kGridFb;
     const int nf = (int)(nfield - f0 < kGridFb ? nfield - f0 : kGridFb);
-    const int nbytes = 2 * ne;
-    const int8_t *src[kGridFb];
-    bool aligned = (nbytes & 15) == 0;
+    const int nwp = gridw_padded(ne);
     for (int j = 0; j < nf; j++) {
         const long long f = f0 + j;
         const long long ct = f / g.P;
         const int pol = (int)(f % g.P);
         const long long c = ct / tb, t = t0 + ct % tb;
-        src[j] = volt + ((c * T + t) * g.P + pol) * (long long)ne * 2;
-        aligned = aligned && (reinterpret_cast<uintptr_t>(src[j]) & 15) == 0;
+        const int8_t *src = volt + ((c * T + t) * g.P + pol) * (long long)ne * 2;
+        uint32_t *dst = sw + (size_t)j * nwp;
+        if ((reinterpret_cast<uintptr_t>(src) & 7) == 0 && (ne & 3) == 0) {
+            // 8-byte loads (two words), eight in flight per thread
+            const uint2 *s2 = reinterpret_cast<const uint2 *>(src);
+            const int n2 = ne / 4;
+            for (int i0 = threadIdx.x; i0 < n2; i0 += 8 * kGridThreads) {
+                uint2 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const int i = i0 + u * kGridThreads;
+                    v[u] = i < n2 ? __ldg(s2 + i) : make_uint2(0u, 0u);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const int i = i0 + u * kGridThreads;
+                    if (i < n2) {
+                        const int w = 2 * i;
+                        *reinterpret_cast<uint2 *>(dst + w + 2 * (w >> 5)) = v[u];
+                    }
+                }
+            }
+        } else {
+            const char2 *s2 = reinterpret_cast<const char2 *>(src);
+            char2 *d2 = reinterpret_cast<char2 *>(dst);
+            for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+                const int w = e >> 1;
+                d2[2 * (w + 2 * (w >> 5)) + (e & 1)] = s2[e];
+            }
+        }
     }
-    if (aligned) {
-        // one bulk copy per field (TMA), completed on an mbarrier
-        if (threadIdx.x == 0) {
-            tc::mbar_init(&vfull, 1);
-            tc::mbar_fence_init();
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            tc::mbar_arrive_expect_tx(&vfull, (uint32_t)(nf * nbytes));
-            for (int j = 0; j < nf; j++) tc::bulk_g2s(sv + (size_t)j * ne, src[j], (uint32_t)nbytes, &vfull);
-        }
-        tc::mbar_wait(&vfull, 0u, status);
-    } else {
-        for (int j = 0; j < nf; j++) {
-            const char2 *s2 = reinterpret_cast<const char2 *>(src[j]);
-            for (int i = threadIdx.x; i < ne; i += blockDim.x) sv[(size_t)j * ne + i] = s2[i];
-        }
-        __syncthreads();
-    }
+    __syncthreads();
+    const char2 *sv = reinterpret_cast<const char2 *>(sw);
     const int nkg = g.kb1 * 8;                       // k groups (4 cells each) per row
     const int nchunk = 128 * nkg;
     const size_t field_bytes = (size_t)g.kb1 * kTile16;
@@ -229,8 +248,11 @@ __global__ void __launch_bounds__(kGridThreads) big_grid_smem_kernel(
                     const int kk = k + u;
                     const int ci = (kk >= cs[1]) + (kk >= cs[2]) + (kk >= cs[3]);
 #pragma unroll
+                    const int wd = e[u] >> 1;
+                    const int pe = 2 * (wd + 2 * (wd >> 5)) + (e[u] & 1);   // padded char2 index
+#pragma unroll
                     for (int j = 0; j < kGridFb; j++) {
-                        const char2 v = sv[(size_t)j * ne + e[u]];
+                        const char2 v = sv[(size_t)j * 2 * nwp + pe];
 #pragma unroll
                         for (int i = 0; i < 4; i++)
                             if (i == ci) {
@@ -838,11 +860,10 @@ hai_status launch_variant(const hai_layout *L, const int8_t *volt, int C, int T,
         const int tb = std::min(tb_max, T - t0);
         const long long nfield = (long long)Cc * tb * g.P;
         const int ncell = (g.kb1 * 32) * 128;
-        const size_t vbytes = (size_t)kGridFb * 2 * L->n_elem;
+        const size_t vbytes = (size_t)kGridFb * 4 * gridw_padded(L->n_elem);
         if (vbytes <= (size_t)kGridSmemMax)
             big_grid_smem_kernel<BF, SP><<<(unsigned)((nfield + kGridFb - 1) / kGridFb), kGridThreads, vbytes, st>>>(
-                vc, L->n_elem, T, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g, t0, tb, nfield, a1, a1lo,
-                ctx->d_status);
+                vc, L->n_elem, T, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g, t0, tb, nfield, a1, a1lo);
         else
             big_grid_kernel<BF, SP><<<dim3((ncell + 255) / 256, (unsigned)((nfield + kGridFields - 1) / kGridFields)),
                                       256, 0, st>>>(vc, L->n_elem, T, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g,
