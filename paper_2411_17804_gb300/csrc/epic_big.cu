@@ -286,6 +286,101 @@ __global__ void __launch_bounds__(kGridThreads) big_grid_smem_kernel(
     }
 }
 
+// Gridding for layouts whose cells each hold at most one gather entry (a
+// lattice of elements on cells, 1 x 1 taps): a dense per-cell table of the
+// padded box (element or -1, conj(W~)) replaces the CSR walk, so a 4-cell run
+// is three vector loads with no dependent chain.  Voltages staged as above.
+template <bool BF, bool SP>
+__global__ void __launch_bounds__(kGridThreads) big_grid_dense_kernel(
+    const int8_t *__restrict__ volt, int ne, int T, const int4 *__restrict__ cell_elem,
+    const float4 *__restrict__ cell_w, BigGeo g, int t0, int tb, long long nfield, uint8_t *__restrict__ a1,
+    uint8_t *__restrict__ a1lo) {
+    extern __shared__ __align__(16) uint32_t sw[];          // [kGridFb][padded words]
+    const long long f0 = (long long)blockIdx.x * kGridFb;
+    const int nf = (int)(nfield - f0 < kGridFb ? nfield - f0 : kGridFb);
+    const int nwp = gridw_padded(ne);
+    for (int j = 0; j < nf; j++) {
+        const long long f = f0 + j;
+        const long long ct = f / g.P;
+        const int pol = (int)(f % g.P);
+        const long long c = ct / tb, t = t0 + ct % tb;
+        const int8_t *src = volt + ((c * T + t) * g.P + pol) * (long long)ne * 2;
+        uint32_t *dst = sw + (size_t)j * nwp;
+        if ((reinterpret_cast<uintptr_t>(src) & 7) == 0 && (ne & 3) == 0) {
+            const uint2 *s2 = reinterpret_cast<const uint2 *>(src);
+            const int n2 = ne / 4;
+            for (int i0 = threadIdx.x; i0 < n2; i0 += 8 * kGridThreads) {
+                uint2 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const int i = i0 + u * kGridThreads;
+                    v[u] = i < n2 ? __ldg(s2 + i) : make_uint2(0u, 0u);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const int i = i0 + u * kGridThreads;
+                    if (i < n2) {
+                        const int w = 2 * i;
+                        *reinterpret_cast<uint2 *>(dst + w + 2 * (w >> 5)) = v[u];
+                    }
+                }
+            }
+        } else {
+            const char2 *s2 = reinterpret_cast<const char2 *>(src);
+            char2 *d2 = reinterpret_cast<char2 *>(dst);
+            for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+                const int w = e >> 1;
+                d2[2 * (w + 2 * (w >> 5)) + (e & 1)] = s2[e];
+            }
+        }
+    }
+    __syncthreads();
+    const char2 *sv = reinterpret_cast<const char2 *>(sw);
+    const int nkg = g.kb1 * 8;
+    const int nchunk = 128 * nkg;
+    const size_t field_bytes = (size_t)g.kb1 * kTile16;
+    for (int q = threadIdx.x; q < nchunk; q += blockDim.x) {
+        const int y = (q & 7) + 8 * (q / (8 * nkg)), kg = (q >> 3) % nkg;
+        const int run = y * nkg + kg;                        // 4 cells (4 kg .. 4 kg + 3) of row y
+        const int4 el = cell_elem[run];
+        const float4 w01 = cell_w[2 * run], w23 = cell_w[2 * run + 1];
+        const int ev[4] = {el.x, el.y, el.z, el.w};
+        const float2 wv[4] = {make_float2(w01.x, w01.y), make_float2(w01.z, w01.w), make_float2(w23.x, w23.y),
+                              make_float2(w23.z, w23.w)};
+        const size_t off = (size_t)(kg >> 3) * kTile16 + (size_t)(y >> 3) * kKMN + (size_t)(kg & 7) * kKBytes +
+                           (size_t)(y & 7) * 16;
+#pragma unroll
+        for (int j = 0; j < kGridFb; j++) {
+            if (j >= nf) break;
+            float2 acc[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                acc[i] = make_float2(0.f, 0.f);
+                if (ev[i] >= 0) {
+                    const int wd = ev[i] >> 1;
+                    const char2 v = sv[(size_t)j * 2 * nwp + 2 * (wd + 2 * (wd >> 5)) + (ev[i] & 1)];
+                    acc[i].x = fmaf(wv[i].x, (float)v.x, -wv[i].y * (float)v.y);
+                    acc[i].y = fmaf(wv[i].x, (float)v.y, wv[i].y * (float)v.x);
+                }
+            }
+            uint8_t *dst = a1 + (size_t)(f0 + j) * field_bytes + off;
+            if constexpr (SP) {
+                uint4 hi, lo;
+                tc::pack2_split<BF>(acc[0].x, acc[0].y, hi.x, lo.x);
+                tc::pack2_split<BF>(acc[1].x, acc[1].y, hi.y, lo.y);
+                tc::pack2_split<BF>(acc[2].x, acc[2].y, hi.z, lo.z);
+                tc::pack2_split<BF>(acc[3].x, acc[3].y, hi.w, lo.w);
+                *reinterpret_cast<uint4 *>(dst) = hi;
+                *reinterpret_cast<uint4 *>(a1lo + (size_t)(f0 + j) * field_bytes + off) = lo;
+            } else {
+                *reinterpret_cast<uint4 *>(dst) =
+                    make_uint4(tc::pack2<BF>(acc[0].x, acc[0].y), tc::pack2<BF>(acc[1].x, acc[1].y),
+                               tc::pack2<BF>(acc[2].x, acc[2].y), tc::pack2<BF>(acc[3].x, acc[3].y));
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ stage 1
 struct S1Params {
     const uint8_t *a1, *a1lo;    // A1 (hi, lo)
@@ -837,6 +932,7 @@ hai_status launch_variant(const hai_layout *L, const int8_t *volt, int C, int T,
     if (V::S1Smem > (uint32_t)ctx->smem_optin - 1024 || V::S2Smem > (uint32_t)ctx->smem_optin - 1024)
         return hai_fail(HAI_ERR_UNSUPPORTED, "epic tensor cores (large grid): shared memory");
     HAI_CUDA_TRY(hai_allow_dyn_smem(big_grid_smem_kernel<BF, SP>, ctx->smem_optin));
+    HAI_CUDA_TRY(hai_allow_dyn_smem(big_grid_dense_kernel<BF, SP>, ctx->smem_optin));
     HAI_CUDA_TRY(hai_allow_dyn_smem(big_s1_kernel<BF, SP>, ctx->smem_optin));
     HAI_CUDA_TRY(hai_allow_dyn_smem(big_s2_kernel<BF, SP>, ctx->smem_optin));
     // the scratch holds big_batch (channel, sample) pairs of plain operands,
@@ -861,7 +957,12 @@ hai_status launch_variant(const hai_layout *L, const int8_t *volt, int C, int T,
         const long long nfield = (long long)Cc * tb * g.P;
         const int ncell = (g.kb1 * 32) * 128;
         const size_t vbytes = (size_t)kGridFb * 4 * gridw_padded(L->n_elem);
-        if (vbytes <= (size_t)kGridSmemMax)
+        if (vbytes <= (size_t)kGridSmemMax && L->big_cell)
+            big_grid_dense_kernel<BF, SP><<<(unsigned)((nfield + kGridFb - 1) / kGridFb), kGridThreads, vbytes, st>>>(
+                vc, L->n_elem, T, static_cast<const int4 *>(L->big_cell),
+                reinterpret_cast<const float4 *>(static_cast<const uint8_t *>(L->big_cell) + L->big_cell_w_off), g, t0,
+                tb, nfield, a1, a1lo);
+        else if (vbytes <= (size_t)kGridSmemMax)
             big_grid_smem_kernel<BF, SP><<<(unsigned)((nfield + kGridFb - 1) / kGridFb), kGridThreads, vbytes, st>>>(
                 vc, L->n_elem, T, L->d_cell_start, L->d_entry_elem, L->d_entry_w, g, t0, tb, nfield, a1, a1lo);
         else
@@ -943,15 +1044,49 @@ hai_status epic_big_prepare(hai_layout *L) {
                 op_bytes += (ops.back().size() * 2 + 1023) & ~(size_t)1023;
             }
     }
+    // dense per-cell table of the padded box (128 rows x kb1 * 32 cells) when
+    // every cell holds at most one gather entry
+    std::vector<int32_t> cstart(g.bx * g.by + 1);
+    std::vector<int32_t> celem;
+    std::vector<float2> cw;
+    bool dense = true;
+    {
+        cudaError_t e0 = cudaMemcpy(cstart.data(), L->d_cell_start, sizeof(int32_t) * cstart.size(), cudaMemcpyDeviceToHost);
+        if (e0 != cudaSuccess) return hai_cuda_fail(e0, "epic tensor cores (large grid): gather table");
+        for (int i = 0; i < g.bx * g.by && dense; i++) dense = cstart[i + 1] - cstart[i] <= 1;
+        if (dense && L->nnz > 0) {
+            celem.resize(L->nnz);
+            cw.resize(L->nnz);
+            e0 = cudaMemcpy(celem.data(), L->d_entry_elem, sizeof(int32_t) * L->nnz, cudaMemcpyDeviceToHost);
+            if (e0 == cudaSuccess) e0 = cudaMemcpy(cw.data(), L->d_entry_w, sizeof(float2) * L->nnz, cudaMemcpyDeviceToHost);
+            if (e0 != cudaSuccess) return hai_cuda_fail(e0, "epic tensor cores (large grid): gather table");
+        }
+    }
+    const int bxp = g.kb1 * 32, ncellp = bxp * 128;
+    std::vector<int32_t> dense_elem;
+    std::vector<float2> dense_w;
+    if (dense) {
+        dense_elem.assign(ncellp, -1);
+        dense_w.assign(ncellp, make_float2(0.f, 0.f));
+        for (int y = 0; y < g.by; y++)
+            for (int x = 0; x < g.bx; x++) {
+                const int c = y * g.bx + x;
+                if (cstart[c + 1] > cstart[c]) {
+                    dense_elem[y * bxp + x] = celem[cstart[c]];
+                    dense_w[y * bxp + x] = cw[cstart[c]];
+                }
+            }
+    }
+    const size_t dense_bytes = dense ? (size_t)ncellp * (sizeof(int32_t) + sizeof(float2)) : 0;
     const size_t per_ct = (size_t)g.P * g.kb1 * kTile16 + (size_t)g.lb2 * kKb2 * kTile16;
     const size_t budget = (size_t)512 << 20;
     L->big_batch = (long long)std::max<size_t>(2, budget / per_ct) & ~1ll;    // even: halves hold hi and lo
     const size_t a1 = (size_t)L->big_batch * g.P * g.kb1 * kTile16;
     const size_t a2 = (size_t)L->big_batch * g.lb2 * kKb2 * kTile16;
     const size_t slots = (size_t)L->ctx->num_sms * Var<false>::SlotFloats * sizeof(float);
-    cudaError_t e = cudaMalloc(&L->d_big, op_bytes + a1 + a2 + slots);
+    cudaError_t e = cudaMalloc(&L->d_big, op_bytes + a1 + a2 + slots + dense_bytes);
     if (e != cudaSuccess) return hai_cuda_fail(e, "epic tensor cores (large grid): scratch");
-    L->dev_bytes += op_bytes + a1 + a2 + slots;
+    L->dev_bytes += op_bytes + a1 + a2 + slots + dense_bytes;
     uint8_t *base = static_cast<uint8_t *>(L->d_big);
     size_t off = 0;
     int idx = 0;
@@ -969,6 +1104,17 @@ hai_status epic_big_prepare(hai_layout *L) {
     L->big_a1 = base + off;
     L->big_a2 = base + off + a1;
     L->big_slots = base + off + a1 + a2;
+    L->big_cell = nullptr;
+    if (dense) {
+        // [run][4] int32 elements, then [run][4] float2 weights (runs of 4 cells)
+        uint8_t *d = base + off + a1 + a2 + slots;
+        L->big_cell = d;
+        L->big_cell_w_off = sizeof(int32_t) * (size_t)ncellp;
+        e = cudaMemcpy(d, dense_elem.data(), sizeof(int32_t) * ncellp, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(d + L->big_cell_w_off, dense_w.data(), sizeof(float2) * ncellp, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return hai_cuda_fail(e, "epic tensor cores (large grid): cell table");
+    }
     return HAI_OK;
 }
 

@@ -79,6 +79,8 @@ struct hai_layout {
     void *d_big = nullptr;
     void *big_b1[4][2] = {}, *big_b2[4][2] = {};   // [fp16, bf16, fp16 split, bf16 split][hi, lo]
     void *big_a1 = nullptr, *big_a2 = nullptr, *big_slots = nullptr;
+    void *big_cell = nullptr;           // dense per-cell gather table (at most one entry per cell), or NULL
+    size_t big_cell_w_off = 0;          // byte offset of its weights
     long long big_batch = 0;
     // XFFT: per grid cell the (pair, K_ab value, mirror) entries landing there,
     // built on the first hai_xfft_image call (layout-only data)
