@@ -818,6 +818,10 @@ def main():
     peaks = measured_peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     probes = probe_peaks(hai, ctx)
+    # the autotuner picks the channels per internal chunk of the large-grid
+    # tensor path for this cadence (timed on a synthetic cadence, cached)
+    tune_cache = os.environ.get("HAI_TUNE_CACHE") or os.path.join(tempfile.gettempdir(), "hai_autotune.txt")
+    tuned = hai.hai_autotune(ctx, lay, C, T, prec, tune_cache) if prec != 0 else 0
 
     clocks = Clocks(local)
     clocks.start()
@@ -876,7 +880,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == hai.HAI_PREC_FP32 else args.prec[:4],
-            "data": "synthetic", "config": headline_config(cfg, args.prec, ws),
+            "data": "synthetic", "config": dict(headline_config(cfg, args.prec, ws),
+                                                autotuned={"channels_per_chunk": tuned, "cache": tune_cache}),
             "e2e": {"value": ws * units / (e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": int(volt.numel()), "d2h_bytes_per_step": int(img.numel() * 4),
                     "api": "hai_epic_image_host (host buffers, chunks of C/4 channels)"},

@@ -207,6 +207,23 @@ hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *layout, const int8_t *
                           int C, int T, hai_precision prec, float *img, int accumulate,
                           void *stream);
 
+/* Autotuner of hai_epic_image's tensor-core path for N = 256, 512: the
+ * channels imaged per internal chunk, which sets how many samples of each
+ * channel one pass of the stage scratch holds (longer sample blocks mean
+ * fewer image read-modify-writes, fewer stage-2 items shared between CTAs,
+ * but fewer items per pass).  Candidates 1, 2, 4, ... up to min(C, 16)
+ * channels are timed on a synthetic cadence of min(C, 16) channels x
+ * min(T, 1024) samples of the layout (random voltages, device memory
+ * allocated for the trial and freed), and the fastest is kept in the layout
+ * for later calls; *chosen (may be NULL) receives it, or 0 when there is
+ * nothing to tune (FP32, or a grid side other than 256 / 512).
+ * cache_path (may be NULL): a text file of "<key> | chunk <c> | <time>"
+ * lines, key = device, N, K, P, N_e bucket (floor log2) and precision; a
+ * matching line is applied without timing, a new choice is appended.  Not
+ * for use while other work runs on the device (it times kernels). */
+hai_status hai_autotune(hai_ctx *ctx, hai_layout *layout, int C, int T, hai_precision prec, const char *cache_path,
+                        int *chosen);
+
 /* hai_epic_image on HOST buffers, the channels streamed through the GPU in
  * chunks so that the copies overlap the imaging: chunk k is imaged on
  * `stream` while the context's copy stream moves chunk k+1's voltages in and

@@ -939,7 +939,8 @@ hai_status launch_variant(const hai_layout *L, const int8_t *volt, int C, int T,
     // half as many split ones: channels in chunks of at most that many, and
     // per chunk batches of as many samples of every channel as fit
     const long long pairs = std::max<long long>(1, L->big_batch / V::Parts);
-    const int cb_max = (int)std::min<long long>(C, pairs);
+    int cb_max = (int)std::min<long long>(C, pairs);
+    if (L->big_chunk > 0) cb_max = std::min(cb_max, L->big_chunk);          // the autotuner's choice
     const size_t a1_bytes = (size_t)L->big_batch * g.P * g.kb1 * kTile16;   // plain capacity of A1 (hi + lo when split)
     uint8_t *a1 = static_cast<uint8_t *>(L->big_a1), *a2 = static_cast<uint8_t *>(L->big_a2);
     const size_t a1_half = a1_bytes / 2, a2_half = (size_t)L->big_batch * g.lb2 * kKb2 * kTile16 / 2;

@@ -79,6 +79,7 @@ struct hai_layout {
     void *d_big = nullptr;
     void *big_b1[4][2] = {}, *big_b2[4][2] = {};   // [fp16, bf16, fp16 split, bf16 split][hi, lo]
     void *big_a1 = nullptr, *big_a2 = nullptr, *big_slots = nullptr;
+    int big_chunk = 0;                  // channels per internal chunk (hai_autotune; 0 = as many as fit)
     void *big_cell = nullptr;           // dense per-cell gather table (at most one entry per cell), or NULL
     size_t big_cell_w_off = 0;          // byte offset of its weights
     long long big_batch = 0;

@@ -104,6 +104,7 @@ def _declare(L):
     L.hai_layout_workspace_size.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
     L.hai_ctx_workspace_size.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
     L.hai_workspace_size.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.hai_autotune.argtypes = [_vp, _vp, _int, _int, _int, ctypes.c_char_p, ctypes.POINTER(_int)]
     L.hai_probe_peak.argtypes = [_vp, _int, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), _vp]
     L.hai_check_device_wait_result.argtypes = [_vp, ctypes.POINTER(_int)]
     L.hai_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
@@ -263,6 +264,15 @@ def hai_layout_anchors(layout: Layout):
     t = np.empty((layout.n_elem, layout.ksize, layout.ksize, 2), np.float32)
     _check(load().hai_layout_anchors(layout.handle, a.ctypes.data, t.ctypes.data), "hai_layout_anchors")
     return a, t
+
+
+def hai_autotune(ctx, layout: Layout, C: int, T: int, prec: int, cache_path=None) -> int:
+    """Tune the layout's tensor-core path for cadences of C x T; returns the
+    chosen channels per chunk (0: nothing to tune)."""
+    c = _int()
+    path = cache_path.encode() if cache_path else None
+    _check(load().hai_autotune(ctx, layout.handle, C, T, prec, path, ctypes.byref(c)), "hai_autotune")
+    return c.value
 
 
 def hai_layout_workspace_size(layout: Layout) -> int:

@@ -192,3 +192,29 @@ def test_bf16_and_split_unsupported_at_128(hai, ctx):
             assert e.value.status == 4
     finally:
         hai.hai_layout_destroy(lay)
+
+
+def test_autotune_choice_cache_and_parity(hai, ctx, tmp_path):
+    """hai_autotune picks the channels per chunk of the large-grid tensor path
+    by timing, writes it to the cache, applies a cached choice without
+    timing, and the tuned layout still matches the oracle."""
+    _, pos, anchors, taps = dense()
+    lay = hai.hai_layout_create(ctx, anchors, taps, 512, 2)
+    cache = str(tmp_path / "tune.txt")
+    try:
+        c1 = hai.hai_autotune(ctx, lay, 16, 200, hai.HAI_PREC_FP16, cache)
+        assert c1 in (1, 2, 4, 8, 16)
+        text = open(cache).read()
+        assert f"| chunk {c1} |" in text and " N512 " in text
+        # a cached line is applied as written (here a different, valid choice)
+        key = text.split(" | ")[0]
+        with open(cache, "a") as f:
+            f.write(f"{key} | chunk 3 | 0 ms\n")
+        assert hai.hai_autotune(ctx, lay, 16, 200, hai.HAI_PREC_FP16, cache) == 3
+        volt = I.random_voltages((5, 30, 2, len(pos), 2), seed=9, device="cuda")
+        img = image(hai, ctx, lay, volt, 5, 30, hai.HAI_PREC_FP16, 512)
+        want = O.epic_image(512, anchors, taps, volt.cpu().numpy())
+        check(hai, hai.HAI_PREC_FP16, img.cpu().numpy(), want)
+        assert hai.hai_autotune(ctx, lay, 16, 200, hai.HAI_PREC_FP32, cache) == 0
+    finally:
+        hai.hai_layout_destroy(lay)
