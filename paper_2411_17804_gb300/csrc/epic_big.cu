@@ -341,9 +341,10 @@ __global__ void __launch_bounds__(kGridThreads) big_grid_dense_kernel(
     const size_t field_bytes = (size_t)g.kb1 * kTile16;
     for (int q = threadIdx.x; q < nchunk; q += blockDim.x) {
         const int y = (q & 7) + 8 * (q / (8 * nkg)), kg = (q >> 3) % nkg;
-        const int run = y * nkg + kg;                        // 4 cells (4 kg .. 4 kg + 3) of row y
-        const int4 el = cell_elem[run];
-        const float4 w01 = cell_w[2 * run], w23 = cell_w[2 * run + 1];
+        // the table is stored in this loop's run order q (4 cells 4 kg .. 4 kg + 3
+        // of row y): a warp reads it contiguously
+        const int4 el = cell_elem[q];
+        const float4 w01 = cell_w[2 * q], w23 = cell_w[2 * q + 1];
         const int ev[4] = {el.x, el.y, el.z, el.w};
         const float2 wv[4] = {make_float2(w01.x, w01.y), make_float2(w01.z, w01.w), make_float2(w23.x, w23.y),
                               make_float2(w23.z, w23.w)};
@@ -1067,16 +1068,23 @@ hai_status epic_big_prepare(hai_layout *L) {
     std::vector<int32_t> dense_elem;
     std::vector<float2> dense_w;
     if (dense) {
+        // in the gridding kernel's run order: run q = (y & 7) + 8 kg + 8 nkg (y >> 3)
+        // holds cells 4 kg .. 4 kg + 3 of row y
+        const int nkg = g.kb1 * 8;
         dense_elem.assign(ncellp, -1);
         dense_w.assign(ncellp, make_float2(0.f, 0.f));
-        for (int y = 0; y < g.by; y++)
-            for (int x = 0; x < g.bx; x++) {
+        for (int q = 0; q < 128 * nkg; q++) {
+            const int y = (q & 7) + 8 * (q / (8 * nkg)), kg = (q >> 3) % nkg;
+            for (int i = 0; i < 4; i++) {
+                const int x = 4 * kg + i;
+                if (y >= g.by || x >= g.bx) continue;
                 const int c = y * g.bx + x;
                 if (cstart[c + 1] > cstart[c]) {
-                    dense_elem[y * bxp + x] = celem[cstart[c]];
-                    dense_w[y * bxp + x] = cw[cstart[c]];
+                    dense_elem[4 * q + i] = celem[cstart[c]];
+                    dense_w[4 * q + i] = cw[cstart[c]];
                 }
             }
+        }
     }
     const size_t dense_bytes = dense ? (size_t)ncellp * (sizeof(int32_t) + sizeof(float2)) : 0;
     const size_t per_ct = (size_t)g.P * g.kb1 * kTile16 + (size_t)g.lb2 * kKb2 * kTile16;
