@@ -46,7 +46,8 @@ def parse():
                     help="image only this many channels (small cases for profiling)")
     ap.add_argument("--samples", type=int, default=0,
                     help="samples per cadence of the headline workload (default 10^4)")
-    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "xfft", "bf", "xbf", "sxfft", "fc", "big", "big16"], default=None,
+    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "xfft", "bf", "xbf", "sxfft", "fc", "big", "big16", "big2"],
+                    default=None,
                     help="run one small case of a kernel twice, untimed, and exit (for ncu captures)")
     return ap.parse_args()
 
@@ -769,12 +770,12 @@ def run_case(name):
             hai.hai_xfft_station_image(ctx, vl, vis, C, img)
         torch.cuda.synchronize()
         hai.hai_vis_layout_destroy(vl)
-    elif name in ("big", "big16"):        # the dense lattice on tensor cores: 4 ch x 20 samples, or the
-        cfg = I.DENSE_ALLSKY_16384        # benchmark's cadence (16 ch x 100 samples)
-        pos = I.station_layout(cfg)
+    elif name in ("big", "big16", "big2"):   # the dense lattice on tensor cores: 4 ch x 20 samples, 16 ch x
+        cfg = I.DENSE_ALLSKY_16384           # 100, or one batch of the autotuned headline (2 ch x 409 samples:
+        pos = I.station_layout(cfg)          # one launch of each kernel, as in the benchmark's steps)
         an, tp = I.station_kernel(cfg, pos)
         lay = hai.hai_layout_create(ctx, an, tp, 512, 2)
-        C, T = (4, 20) if name == "big" else (16, 100)
+        C, T = {"big": (4, 20), "big16": (16, 100), "big2": (2, 409)}[name]
         v = I.random_voltages((C, T, 2, len(pos), 2), seed=5, device="cuda")
         img = torch.empty((C, 4, 512, 512), device="cuda")
         for _ in range(2):
