@@ -620,8 +620,8 @@ hai_status epic_tc_run(hai_ctx *ctx, int N, const TcLaunch &l, cudaStream_t st) 
         if (N == 64 && l.split) return l.bf16 ? run_n<64, true, true>(ctx, l, st) : run_n<64, true, false>(ctx, l, st);
         if (N == 32) return run_n<32, false, true>(ctx, l, st);
         if (N == 64) return run_n<64, false, true>(ctx, l, st);
-        return hai_fail(HAI_ERR_UNSUPPORTED, "epic tensor cores: the hi/lo split and BF16 operands need N = 32, 64, "
-                                             "256 or 512");
+        if (N == 128 && !l.split) return epic_tc128_run(ctx, l, st);
+        return hai_fail(HAI_ERR_UNSUPPORTED, "epic tensor cores: the hi/lo split needs N = 32, 64, 256 or 512");
     }
     if (N == 32) return run_n<32, false, false>(ctx, l, st);
     if (N == 64) return run_n<64, false, false>(ctx, l, st);
@@ -651,6 +651,10 @@ hai_status epic_tc_dft_prepare(hai_ctx *ctx, int N) {
     auto put = [&](size_t base, uint32_t off, double v) {
         const __half hv = __double2half(v);
         memcpy(&out[base + off], &hv, 2);
+        if (!outb.empty() && N == 128) {          // the BF16 copy of the N = 128 operands
+            const __nv_bfloat16 bv = __double2bfloat16(v);
+            memcpy(&outb[base + off], &bv, 2);
+        }
     };
     if (N <= 64) {
         // hi = fp16(W'), then lo = fp16(W' - hi) for the split variant; the
@@ -675,6 +679,7 @@ hai_status epic_tc_dft_prepare(hai_ctx *ctx, int N) {
         const uint32_t mns = 16 * kKs;              // K = 128
         const size_t qbytes = 8 * (size_t)mns;     // 64 rows
         out.assign(4 * qbytes + 16 * (size_t)mns, 0);
+        outb.assign(out.size(), 0);
         for (int r = 0; r < 4; r++)
             for (int n = 0; n < 64; n++)
                 for (int kappa = 0; kappa < 128; kappa++)
@@ -707,7 +712,7 @@ hai_status epic_tc_dft_prepare(hai_ctx *ctx, int N) {
 
 const void *epic_tc_dft(hai_ctx *ctx, int N, bool bf16) {
     const int slot = (N == 32) ? 0 : (N == 64) ? 1 : (N == 128) ? 2 : -1;
-    if (slot < 0 || (bf16 && slot == 2)) return nullptr;
+    if (slot < 0) return nullptr;
     return ctx->d_dft[slot + (bf16 ? 3 : 0)];
 }
 

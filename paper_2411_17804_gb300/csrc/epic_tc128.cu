@@ -63,8 +63,6 @@ constexpr uint32_t kOffA1 = kOffA2 + kA2Bytes;
 constexpr uint32_t kOffB2 = kOffA1 + 2 * kA1Bytes;
 constexpr uint32_t kOffE = kOffB2 + kB2Bytes;
 constexpr uint32_t kD2Col = 128;             // TMEM: D1 at 0 / 64, D2 at 128 / 256
-constexpr uint32_t kIdesc1 = tc::idesc_f16(128, 64, 0, 0);
-constexpr uint32_t kIdesc2 = tc::idesc_f16(128, 128, 0, 1);
 
 // Header of a station's gather blob (N = 128): per rank the byte offset,
 // size, tiles and entries of its gather table (GatherLayout), and the owner
@@ -95,7 +93,11 @@ struct Params {
 
 __device__ __forceinline__ void bar_front() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
 
+template <bool BF>
 __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) epic_tc128_kernel(const Params p) {
+    // operand type of both MMA operands: FP16, or BF16 when BF
+    constexpr uint32_t kIdesc1 = tc::idesc_f16_as(BF, 128, 64, 0, 0);
+    constexpr uint32_t kIdesc2 = tc::idesc_f16_as(BF, 128, 128, 0, 1);
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t mb_v[kStages];
     __shared__ __align__(8) uint64_t mb_a1[2], mb_a1free[2], mb_d1[2], mb_a2, mb_b2free, mb_full[2], mb_empty[2];
@@ -254,8 +256,8 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
                 for (; q < qe; q += 32) mac(s_w[q], E[s_e[q]]);
                 const uint32_t off = s_cell[t * 32 + lane];
                 if (off != 0xffffffffu) {
-                    *reinterpret_cast<uint32_t *>(A + off) = tc::pack_half2(g0.x, g0.y);
-                    *reinterpret_cast<uint32_t *>(A + off + kPolBytes) = tc::pack_half2(g1.x, g1.y);
+                    *reinterpret_cast<uint32_t *>(A + off) = tc::pack2<BF>(g0.x, g0.y);
+                    *reinterpret_cast<uint32_t *>(A + off + kPolBytes) = tc::pack2<BF>(g1.x, g1.y);
                 }
             }
         };
@@ -310,10 +312,10 @@ __global__ void __cluster_dims__(kRanks, 1, 1) __launch_bounds__(kThreads, 1) ep
                             }
                             const int n2 = pol * 64 + c_out * 32 + 16 * hh + 8 * h;
                             uint4 u;
-                            u.x = tc::pack_half2(v[0], v[1]);
-                            u.y = tc::pack_half2(v[2], v[3]);
-                            u.z = tc::pack_half2(v[4], v[5]);
-                            u.w = tc::pack_half2(v[6], v[7]);
+                            u.x = tc::pack2<BF>(v[0], v[1]);
+                            u.y = tc::pack2<BF>(v[2], v[3]);
+                            u.z = tc::pack2<BF>(v[4], v[5]);
+                            u.w = tc::pack2<BF>(v[6], v[7]);
                             *reinterpret_cast<uint4 *>(sB2 + tc::off_mnmajor(n2, kappa, kB2Ks, kB2MNs)) = u;
                         }
                     }
@@ -565,8 +567,8 @@ hai_status epic_tc128_run(hai_ctx *ctx, const TcLaunch &l, cudaStream_t st) {
     const size_t smem = epic_tc128_smem(l.ne_max, l.table_max);
     if (smem + kStaticSmem > (size_t)ctx->smem_optin)
         return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp16 (N = 128): shared memory need exceeds the device limit");
-    const void *dft = epic_tc_dft(ctx, 128);
-    if (!dft) return hai_fail(HAI_ERR_INVALID_ARG, "epic fp16 (N = 128): DFT operand not prepared");
+    const void *dft = epic_tc_dft(ctx, 128, l.bf16 != 0);
+    if (!dft) return hai_fail(HAI_ERR_INVALID_ARG, "epic tensor cores (N = 128): DFT operand not prepared");
     if (!l.no_attr) {
         const hai_status s = epic_tc128_set_attr(ctx);
         if (s != HAI_OK) return s;
@@ -590,7 +592,8 @@ hai_status epic_tc128_run(hai_ctx *ctx, const TcLaunch &l, cudaStream_t st) {
     p.partials = l.partials;
     p.status = ctx->d_status;
     const int pidx = prof_begin(ctx, st);
-    epic_tc128_kernel<<<l.n_cta * kRanks, kThreads, smem, st>>>(p);
+    if (l.bf16) epic_tc128_kernel<true><<<l.n_cta * kRanks, kThreads, smem, st>>>(p);
+    else epic_tc128_kernel<false><<<l.n_cta * kRanks, kThreads, smem, st>>>(p);
     prof_end(ctx, pidx, st);
     prof_count(ctx, 1);
     HAI_CUDA_TRY(cudaGetLastError());
@@ -598,10 +601,8 @@ hai_status epic_tc128_run(hai_ctx *ctx, const TcLaunch &l, cudaStream_t st) {
 }
 
 hai_status epic_tc128_set_attr(hai_ctx *ctx) {
-    cudaFuncAttributes a;
-    HAI_CUDA_TRY(cudaFuncGetAttributes(&a, epic_tc128_kernel));
-    HAI_CUDA_TRY(cudaFuncSetAttribute(epic_tc128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      ctx->smem_optin - (int)a.sharedSizeBytes));
+    HAI_CUDA_TRY(hai_allow_dyn_smem(epic_tc128_kernel<false>, ctx->smem_optin));
+    HAI_CUDA_TRY(hai_allow_dyn_smem(epic_tc128_kernel<true>, ctx->smem_optin));
     return HAI_OK;
 }
 
@@ -622,6 +623,6 @@ int epic_tc128_max_groups(hai_ctx *ctx, int ne_max, uint32_t table_max) {
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, epic_tc128_kernel, &cfg) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveClusters(&n, epic_tc128_kernel<false>, &cfg) != cudaSuccess) return 0;
     return n;
 }

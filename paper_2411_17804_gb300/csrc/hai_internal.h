@@ -24,7 +24,7 @@ struct hai_ctx {
     std::vector<cudaEvent_t> prof_ev;   // pairs: [2i] before, [2i+1] after
     size_t prof_used = 0;               // pairs recorded
     long long prof_launches = 0;        // all kernels launched
-    void *d_dft[6] = {};                // tensor-core DFT operands: FP16 N = 32, 64, 128; BF16 N = 32, 64
+    void *d_dft[6] = {};                // tensor-core DFT operands: FP16 N = 32, 64, 128; BF16 N = 32, 64, 128
     int capturing = 0;                  // a plan is capturing a graph: no profiling events
     void *d_corr_ws = nullptr;          // correlator: fp16 operand images of a batch of channels,
     size_t corr_ws_bytes = 0;           // allocated on the first hai_correlate call

@@ -179,16 +179,24 @@ def test_small_grids_every_operand_form(hai, ctx, pname, n_elem, C, T, cplx):
         hai.hai_layout_destroy(lay)
 
 
-def test_bf16_and_split_unsupported_at_128(hai, ctx):
+def test_bf16_at_128_and_split_unsupported(hai, ctx):
+    """N = 128 (4-CTA clusters): BF16 operands against the oracle at the BF16
+    bound; the hi/lo split is not built at this grid side."""
     sc = I.uneven_station(I.UnevenConfig(), 0, 700)
     pos, anchors, taps = station(sc)
     lay = hai.hai_layout_create(ctx, anchors, taps, 128, 2)
-    volt = torch.zeros((1, 2, 2, len(pos), 2), dtype=torch.int8, device="cuda")
-    img = torch.zeros((1, 4, 128, 128), device="cuda")
     try:
-        for prec in (hai.HAI_PREC_BF16, hai.HAI_PREC_BF16_SPLIT, hai.HAI_PREC_FP16_SPLIT):
+        volt = I.random_voltages((3, 37, 2, len(pos), 2), seed=17)
+        want = O.epic_image(128, anchors, taps, volt.numpy())
+        img = image(hai, ctx, lay, volt.cuda(), 3, 37, hai.HAI_PREC_BF16, 128)
+        check(hai, hai.HAI_PREC_BF16, img.cpu().numpy(), want)
+        fp16 = image(hai, ctx, lay, volt.cuda(), 3, 37, hai.HAI_PREC_FP16, 128)
+        check(hai, hai.HAI_PREC_FP16, fp16.cpu().numpy(), want)
+        zero = torch.zeros((1, 2, 2, len(pos), 2), dtype=torch.int8, device="cuda")
+        out = torch.zeros((1, 4, 128, 128), device="cuda")
+        for prec in (hai.HAI_PREC_BF16_SPLIT, hai.HAI_PREC_FP16_SPLIT):
             with pytest.raises(hai.HaiError) as e:
-                hai.hai_epic_image(ctx, lay, volt, 1, 2, prec, img, 0)
+                hai.hai_epic_image(ctx, lay, zero, 1, 2, prec, out, 0)
             assert e.value.status == 4
     finally:
         hai.hai_layout_destroy(lay)
