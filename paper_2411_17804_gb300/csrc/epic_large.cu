@@ -164,6 +164,192 @@ __global__ void __launch_bounds__(512) large_cols_kernel(const float2 *__restric
     }
 }
 
+// ------------------------------------------------------------------ N = 512
+// The 512-point transforms of the dense grids in registers: 64 threads per
+// transform, each holding 8 points, in three radix-8 passes (512 = 8 x 8 x 8)
+// with two exchanges through shared memory.  Pass 1: thread tau takes
+// x[tau + 64 m], m < 8, an 8-point DFT over m, twiddle w512^(tau k1); pass 2:
+// thread (k1, t1) the 8 values of k1 at tau = t1 + 8 t2, an 8-point DFT over
+// t2, twiddle w64^(t1 k2); pass 3: thread (k1, k2) the 8 values at t1, an
+// 8-point DFT over t1.  Thread tau ends with X[tau + 64 j], j < 8 (natural
+// order, stride 64).  Exponent + throughout.  The exchange layouts (rows 66
+// apart, then k1 74 + k2 9 + t1) serve every pass's accesses in two
+// shared-memory wavefronts.
+constexpr int kFftBuf = 589;                 // float2 per transform's exchange buffer
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmuli(float2 a) { return make_float2(-a.y, a.x); }          // a * i
+
+// 4-point DFT, exponent +: X_k = sum_m x_m i^(m k), natural order
+__device__ __forceinline__ void dft4(float2 &x0, float2 &x1, float2 &x2, float2 &x3) {
+    const float2 p = cadd(x0, x2), r = csub(x0, x2), q = cadd(x1, x3), s = cmuli(csub(x1, x3));
+    x0 = cadd(p, q);
+    x1 = cadd(r, s);
+    x2 = csub(p, q);
+    x3 = csub(r, s);
+}
+
+// 8-point DFT, exponent +, natural order in and out (decimation in frequency:
+// the even outputs are the 4-point DFT of a_m + a_(m+4), the odd ones that of
+// (a_m - a_(m+4)) w8^m)
+__device__ __forceinline__ void dft8(float2 (&a)[8]) {
+    const float h = 0.70710678118654752f;     // cos(pi / 4)
+    float2 u0 = cadd(a[0], a[4]), u1 = cadd(a[1], a[5]), u2 = cadd(a[2], a[6]), u3 = cadd(a[3], a[7]);
+    float2 v0 = csub(a[0], a[4]), v1 = csub(a[1], a[5]), v2 = csub(a[2], a[6]), v3 = csub(a[3], a[7]);
+    v1 = make_float2(h * (v1.x - v1.y), h * (v1.x + v1.y));          // * e^(+i pi/4)
+    v2 = cmuli(v2);                                                   // * e^(+i pi/2)
+    v3 = make_float2(-h * (v3.x + v3.y), h * (v3.x - v3.y));         // * e^(+3i pi/4)
+    dft4(u0, u1, u2, u3);
+    dft4(v0, v1, v2, v3);
+    a[0] = u0; a[2] = u1; a[4] = u2; a[6] = u3;
+    a[1] = v0; a[3] = v1; a[5] = v2; a[7] = v3;
+}
+
+// a[k] *= w^k for k = 1..7 (w a unit complex number; powers by products)
+__device__ __forceinline__ void twiddle8(float2 (&a)[8], float2 w) {
+    float2 p = w;
+#pragma unroll
+    for (int k = 1; k < 8; k++) {
+        a[k] = cmul(a[k], p);
+        p = cmul(p, w);
+    }
+}
+
+// One 512-point transform by the 64 threads of a group (tau = thread in the
+// group), `buf` its exchange buffer, tw the table w512^n; ends with a[j] =
+// X[tau + 64 j].  bar() synchronises every group of the CTA together.
+template <typename Bar>
+__device__ __forceinline__ void fft512(float2 (&a)[8], int tau, float2 *buf, const float2 *tw, Bar bar) {
+    dft8(a);
+    twiddle8(a, tw[tau]);
+#pragma unroll
+    for (int k = 0; k < 8; k++) buf[k * 66 + tau] = a[k];
+    bar();
+    const int k1 = tau & 7, q = tau >> 3;
+#pragma unroll
+    for (int t2 = 0; t2 < 8; t2++) a[t2] = buf[k1 * 66 + q + 8 * t2];
+    dft8(a);
+    twiddle8(a, tw[8 * q]);
+    bar();
+#pragma unroll
+    for (int k2 = 0; k2 < 8; k2++) buf[k1 * 74 + k2 * 9 + q] = a[k2];
+    bar();
+#pragma unroll
+    for (int t1 = 0; t1 < 8; t1++) a[t1] = buf[k1 * 74 + q * 9 + t1];
+    dft8(a);
+}
+
+// Row pass, N = 512: blockIdx.x = field of the batch, blockIdx.y = group of 8
+// box rows; thread (r = tid / 64, tau): the row's cells x = tau + 64 m
+// gathered from the layout's table, the transform, H[field][y][l] written
+// for every l (coalesced: l = tau + 64 j).
+__global__ void __launch_bounds__(512) large512_rows_kernel(
+    const int8_t *__restrict__ volt, int T, int P, int ne, int box_w, int box_h,
+    const int32_t *__restrict__ cell_start, const int32_t *__restrict__ entry_elem,
+    const float2 *__restrict__ entry_w, Batch bt, float2 *__restrict__ H) {
+    extern __shared__ float2 sm[];
+    float2 *tw = sm;                                    // [512]
+    float2 *bufs = sm + 512;                            // [8][kFftBuf]
+    for (int k = threadIdx.x; k < 512; k += blockDim.x) {
+        float s, c;
+        sincospif((float)k / 256.0f, &s, &c);
+        tw[k] = make_float2(c, s);
+    }
+    const int r = threadIdx.x >> 6, tau = threadIdx.x & 63;
+    const int f = blockIdx.x;
+    const int pol = f % P, tt = (f / P) % bt.tb, cc = f / (P * bt.tb);
+    const int y = blockIdx.y * 8 + r;
+    const char2 *E = reinterpret_cast<const char2 *>(volt) +
+                     ((((size_t)(bt.c0 + cc) * T + (bt.t0 + tt)) * P + pol) * ne);
+    float2 a[8];
+#pragma unroll
+    for (int m = 0; m < 8; m++) {
+        const int x = tau + 64 * m;
+        float2 g = make_float2(0.f, 0.f);
+        if (y < box_h && x < box_w) {
+            const int cell = y * box_w + x;
+            for (int k = cell_start[cell]; k < cell_start[cell + 1]; k++) {
+                const char2 e = E[entry_elem[k]];
+                const float2 w = entry_w[k];            // conj(W~)
+                g.x = fmaf(w.x, (float)e.x, fmaf(-w.y, (float)e.y, g.x));
+                g.y = fmaf(w.x, (float)e.y, fmaf(w.y, (float)e.x, g.y));
+            }
+        }
+        a[m] = g;
+    }
+    __syncthreads();                                    // twiddle table ready
+    fft512(a, tau, bufs + r * kFftBuf, tw, [] { __syncthreads(); });
+    if (y < box_h) {
+        float2 *out = H + ((size_t)f * box_h + y) * 512;
+#pragma unroll
+        for (int j = 0; j < 8; j++) out[tau + 64 * j] = a[j];
+    }
+}
+
+// Column pass, N = 512, two polarisations: blockIdx.x = channel of the batch,
+// blockIdx.y = block of kCols512 columns; thread (c = tid / 64, tau) transforms
+// column l0 + c of both polarisations for every sample of the batch and adds
+// |F_X|^2, |F_Y|^2 and F_X conj(F_Y) at rows l_y = tau + 64 j into 32
+// register accumulators; at the end the image columns are read, added to and
+// written once (output pixel shifted by N/2: the (-1)^j phase centre).
+constexpr int kCols512 = 4;                  // columns per CTA: 256 threads, two CTAs per SM
+
+__global__ void __launch_bounds__(64 * kCols512, 2) large512_cols_kernel(const float2 *__restrict__ H, int box_h,
+                                                                       Batch bt, float *__restrict__ img, int add) {
+    extern __shared__ float2 sm[];
+    float2 *tw = sm;                                    // [512]
+    float2 *bufs = sm + 512;                            // [2 pols][kCols512 columns][kFftBuf]
+    for (int k = threadIdx.x; k < 512; k += blockDim.x) {
+        float s, c;
+        sincospif((float)k / 256.0f, &s, &c);
+        tw[k] = make_float2(c, s);
+    }
+    const int c = threadIdx.x >> 6, tau = threadIdx.x & 63;
+    const int cc = blockIdx.x, l0 = blockIdx.y * kCols512;
+    float acc[4][8];
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) acc[q][j] = 0.f;
+    __syncthreads();
+    for (int tt = 0; tt < bt.tb; tt++) {
+        const size_t fx = ((size_t)cc * bt.tb + tt) * 2;
+        float2 x[8], yv[8];
+#pragma unroll
+        for (int m = 0; m < 8; m++) {
+            const int yy = tau + 64 * m;
+            x[m] = yy < box_h ? H[(fx * box_h + yy) * 512 + l0 + c] : make_float2(0.f, 0.f);
+            yv[m] = yy < box_h ? H[((fx + 1) * box_h + yy) * 512 + l0 + c] : make_float2(0.f, 0.f);
+        }
+        fft512(x, tau, bufs + c * kFftBuf, tw, [] { __syncthreads(); });
+        fft512(yv, tau, bufs + (kCols512 + c) * kFftBuf, tw, [] { __syncthreads(); });
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const float2 a = x[j], b = yv[j];
+            acc[0][j] = fmaf(a.x, a.x, fmaf(a.y, a.y, acc[0][j]));
+            acc[1][j] = fmaf(b.x, b.x, fmaf(b.y, b.y, acc[1][j]));
+            acc[2][j] = fmaf(a.x, b.x, fmaf(a.y, b.y, acc[2][j]));      // Re X conj(Y)
+            acc[3][j] = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc[3][j]));     // Im X conj(Y)
+        }
+        __syncthreads();                                // exchange buffers free for the next sample
+    }
+    const int ch = bt.c0 + cc;
+    const size_t NN = (size_t)512 * 512;
+    const int ox = (l0 + c + 256) & 511;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        float *dst = img + ((size_t)ch * 4 + q) * NN + ox;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int oy = (tau + 64 * j + 256) & 511;
+            float v = acc[q][j];
+            if (add) v += dst[(size_t)oy * 512];
+            dst[(size_t)oy * 512] = v;
+        }
+    }
+}
+
 }  // namespace
 
 bool epic_large_supported(int grid_n) { return grid_n == 128 || grid_n == 256 || grid_n == 512; }
@@ -195,6 +381,35 @@ hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int
         HAI_CUDA_TRY(hai_allow_dyn_smem(large_cols_kernel<1>, L->ctx->smem_optin));
     float2 *H = static_cast<float2 *>(L->d_large_scratch);
     const int pidx = prof_begin(L->ctx, st);
+    if (N == 512 && P == 2) {
+        // register-resident radix-8 transforms; batches of 2 channels x as
+        // many samples as the scratch holds (fewer image read-modify-writes
+        // per sample), 2 x 128 column CTAs of 256 threads (two per SM)
+        const size_t rs_smem = sizeof(float2) * (512 + 8 * (size_t)kFftBuf);
+        const size_t cs_smem = sizeof(float2) * (512 + 2 * kCols512 * (size_t)kFftBuf);
+        HAI_CUDA_TRY(hai_allow_dyn_smem(large512_rows_kernel, L->ctx->smem_optin));
+        HAI_CUDA_TRY(hai_allow_dyn_smem(large512_cols_kernel, L->ctx->smem_optin));
+        const int cb_max = std::min(C, 2);
+        const int tb512 = (int)std::max<long long>(1, std::min<long long>(T, fields_cap / ((long long)cb_max * P)));
+        for (int t0 = 0; t0 < T; t0 += tb512) {
+            const int tb = std::min(tb512, T - t0);
+            for (int c0 = 0; c0 < C; c0 += cb_max) {
+                Batch bt;
+                bt.c0 = c0;
+                bt.cb = std::min(cb_max, C - c0);
+                bt.t0 = t0;
+                bt.tb = tb;
+                large512_rows_kernel<<<dim3(bt.cb * tb * P, (L->box_h + 7) / 8), 512, rs_smem, st>>>(
+                    volt, T, P, L->n_elem, L->box_w, L->box_h, L->d_cell_start, L->d_entry_elem, L->d_entry_w, bt, H);
+                large512_cols_kernel<<<dim3(bt.cb, 512 / kCols512), 64 * kCols512, cs_smem, st>>>(
+                    H, L->box_h, bt, img, (t0 > 0 || accumulate) ? 1 : 0);
+                prof_count(L->ctx, 2);
+            }
+        }
+        prof_end(L->ctx, pidx, st);
+        HAI_CUDA_TRY(cudaGetLastError());
+        return HAI_OK;
+    }
     for (int t0 = 0; t0 < T; t0 += tb_max) {
         const int tb = std::min(tb_max, T - t0);
         const int cb_max = (int)std::max<long long>(1, fields_cap / ((long long)tb * P));
