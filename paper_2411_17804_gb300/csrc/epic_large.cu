@@ -206,23 +206,51 @@ __device__ __forceinline__ void dft8(float2 (&a)[8]) {
     a[1] = v0; a[3] = v1; a[5] = v2; a[7] = v3;
 }
 
-// a[k] *= w^k for k = 1..7 (w a unit complex number; powers by products)
-__device__ __forceinline__ void twiddle8(float2 (&a)[8], float2 w) {
-    float2 p = w;
-#pragma unroll
-    for (int k = 1; k < 8; k++) {
-        a[k] = cmul(a[k], p);
-        p = cmul(p, w);
+// The 8-point DFT when only a[0] and a[1] can be non-zero (the first pass of
+// a transform whose non-zero inputs all lie in its first quarter).
+__device__ __forceinline__ void dft8_first2(float2 (&a)[8]) {
+    const float h = 0.70710678118654752f;
+    const float2 u0 = a[0], u1 = a[1];
+    const float2 v1 = make_float2(h * (u1.x - u1.y), h * (u1.x + u1.y));     // a1 * e^(+i pi/4)
+    a[0] = cadd(u0, u1);
+    a[2] = cadd(u0, cmuli(u1));
+    a[4] = csub(u0, u1);
+    a[6] = csub(u0, cmuli(u1));
+    a[1] = cadd(u0, v1);
+    a[3] = cadd(u0, cmuli(v1));
+    a[5] = csub(u0, v1);
+    a[7] = csub(u0, cmuli(v1));
+}
+
+// Twiddle tables of the 512-point transform in shared memory:
+//   tw[n] = w512^n (n < 512), T1[(k - 1) 64 + tau] = w512^(tau k),
+//   T2[(k - 1) 8 + t1] = w64^(t1 k) (k = 1..7): read by consecutive threads
+//   without bank conflicts (T2 is a broadcast within groups of 8).
+constexpr int kTwFloat2 = 512 + 7 * 64 + 7 * 8;
+
+__device__ __forceinline__ void fill_fft512_tables(float2 *tw) {
+    for (int k = threadIdx.x; k < 512; k += blockDim.x) {
+        float s, c;
+        sincospif((float)k / 256.0f, &s, &c);
+        tw[k] = make_float2(c, s);
     }
+    __syncthreads();
+    float2 *T1 = tw + 512, *T2 = T1 + 7 * 64;
+    for (int i = threadIdx.x; i < 7 * 64; i += blockDim.x) T1[i] = tw[((i & 63) * (1 + (i >> 6))) & 511];
+    for (int i = threadIdx.x; i < 7 * 8; i += blockDim.x) T2[i] = tw[(8 * (i & 7) * (1 + (i >> 3))) & 511];
 }
 
 // One 512-point transform by the 64 threads of a group (tau = thread in the
-// group), `buf` its exchange buffer, tw the table w512^n; ends with a[j] =
-// X[tau + 64 j].  bar() synchronises every group of the CTA together.
-template <typename Bar>
+// group), `buf` its exchange buffer, tw the tables above; ends with a[j] =
+// X[tau + 64 j].  bar() synchronises every group of the CTA together.  Z2:
+// the inputs a[2..7] are zero (skipped in the first pass).
+template <bool Z2, typename Bar>
 __device__ __forceinline__ void fft512(float2 (&a)[8], int tau, float2 *buf, const float2 *tw, Bar bar) {
-    dft8(a);
-    twiddle8(a, tw[tau]);
+    const float2 *T1 = tw + 512, *T2 = T1 + 7 * 64;
+    if (Z2) dft8_first2(a);
+    else dft8(a);
+#pragma unroll
+    for (int k = 1; k < 8; k++) a[k] = cmul(a[k], T1[(k - 1) * 64 + tau]);
 #pragma unroll
     for (int k = 0; k < 8; k++) buf[k * 66 + tau] = a[k];
     bar();
@@ -230,7 +258,8 @@ __device__ __forceinline__ void fft512(float2 (&a)[8], int tau, float2 *buf, con
 #pragma unroll
     for (int t2 = 0; t2 < 8; t2++) a[t2] = buf[k1 * 66 + q + 8 * t2];
     dft8(a);
-    twiddle8(a, tw[8 * q]);
+#pragma unroll
+    for (int k = 1; k < 8; k++) a[k] = cmul(a[k], T2[(k - 1) * 8 + q]);
     bar();
 #pragma unroll
     for (int k2 = 0; k2 < 8; k2++) buf[k1 * 74 + k2 * 9 + q] = a[k2];
@@ -249,13 +278,9 @@ __global__ void __launch_bounds__(512) large512_rows_kernel(
     const int32_t *__restrict__ cell_start, const int32_t *__restrict__ entry_elem,
     const float2 *__restrict__ entry_w, Batch bt, float2 *__restrict__ H) {
     extern __shared__ float2 sm[];
-    float2 *tw = sm;                                    // [512]
-    float2 *bufs = sm + 512;                            // [8][kFftBuf]
-    for (int k = threadIdx.x; k < 512; k += blockDim.x) {
-        float s, c;
-        sincospif((float)k / 256.0f, &s, &c);
-        tw[k] = make_float2(c, s);
-    }
+    float2 *tw = sm;                                    // [kTwFloat2]
+    float2 *bufs = sm + kTwFloat2;                      // [8][kFftBuf]
+    fill_fft512_tables(tw);
     const int r = threadIdx.x >> 6, tau = threadIdx.x & 63;
     const int f = blockIdx.x;
     const int pol = f % P, tt = (f / P) % bt.tb, cc = f / (P * bt.tb);
@@ -278,8 +303,9 @@ __global__ void __launch_bounds__(512) large512_rows_kernel(
         }
         a[m] = g;
     }
-    __syncthreads();                                    // twiddle table ready
-    fft512(a, tau, bufs + r * kFftBuf, tw, [] { __syncthreads(); });
+    __syncthreads();
+    if (box_w <= 128) fft512<true>(a, tau, bufs + r * kFftBuf, tw, [] { __syncthreads(); });
+    else fft512<false>(a, tau, bufs + r * kFftBuf, tw, [] { __syncthreads(); });
     if (y < box_h) {
         float2 *out = H + ((size_t)f * box_h + y) * 512;
 #pragma unroll
@@ -295,16 +321,15 @@ __global__ void __launch_bounds__(512) large512_rows_kernel(
 // written once (output pixel shifted by N/2: the (-1)^j phase centre).
 constexpr int kCols512 = 4;                  // columns per CTA: 256 threads, two CTAs per SM
 
+// Z2: box_h <= 128, so a thread's non-zero inputs are rows tau and tau + 64;
+// those of the next sample are loaded before the current one is transformed.
+template <bool Z2>
 __global__ void __launch_bounds__(64 * kCols512, 2) large512_cols_kernel(const float2 *__restrict__ H, int box_h,
                                                                        Batch bt, float *__restrict__ img, int add) {
     extern __shared__ float2 sm[];
-    float2 *tw = sm;                                    // [512]
-    float2 *bufs = sm + 512;                            // [2 pols][kCols512 columns][kFftBuf]
-    for (int k = threadIdx.x; k < 512; k += blockDim.x) {
-        float s, c;
-        sincospif((float)k / 256.0f, &s, &c);
-        tw[k] = make_float2(c, s);
-    }
+    float2 *tw = sm;                                    // [kTwFloat2]
+    float2 *bufs = sm + kTwFloat2;                      // [2 pols][kCols512 columns][kFftBuf]
+    fill_fft512_tables(tw);
     const int c = threadIdx.x >> 6, tau = threadIdx.x & 63;
     const int cc = blockIdx.x, l0 = blockIdx.y * kCols512;
     float acc[4][8];
@@ -312,18 +337,46 @@ __global__ void __launch_bounds__(64 * kCols512, 2) large512_cols_kernel(const f
     for (int q = 0; q < 4; q++)
 #pragma unroll
         for (int j = 0; j < 8; j++) acc[q][j] = 0.f;
+    // input m (row tau + 64 m) of polarisation p of sample tt of this channel
+    auto in = [&](int tt, int p, int m) -> float2 {
+        const size_t f = ((size_t)cc * bt.tb + tt) * 2 + p;
+        const int yy = tau + 64 * m;
+        return yy < box_h ? H[(f * box_h + yy) * 512 + l0 + c] : make_float2(0.f, 0.f);
+    };
+    float2 nx0 = make_float2(0.f, 0.f), nx1 = nx0, ny0 = nx0, ny1 = nx0;
+    if (Z2) {
+        nx0 = in(0, 0, 0);
+        nx1 = in(0, 0, 1);
+        ny0 = in(0, 1, 0);
+        ny1 = in(0, 1, 1);
+    }
     __syncthreads();
     for (int tt = 0; tt < bt.tb; tt++) {
-        const size_t fx = ((size_t)cc * bt.tb + tt) * 2;
         float2 x[8], yv[8];
+        if (Z2) {
+            x[0] = nx0;
+            x[1] = nx1;
+            yv[0] = ny0;
+            yv[1] = ny1;
 #pragma unroll
-        for (int m = 0; m < 8; m++) {
-            const int yy = tau + 64 * m;
-            x[m] = yy < box_h ? H[(fx * box_h + yy) * 512 + l0 + c] : make_float2(0.f, 0.f);
-            yv[m] = yy < box_h ? H[((fx + 1) * box_h + yy) * 512 + l0 + c] : make_float2(0.f, 0.f);
+            for (int m = 2; m < 8; m++) x[m] = yv[m] = make_float2(0.f, 0.f);
+            if (tt + 1 < bt.tb) {
+                nx0 = in(tt + 1, 0, 0);
+                nx1 = in(tt + 1, 0, 1);
+                ny0 = in(tt + 1, 1, 0);
+                ny1 = in(tt + 1, 1, 1);
+            }
+            fft512<true>(x, tau, bufs + c * kFftBuf, tw, [] { __syncthreads(); });
+            fft512<true>(yv, tau, bufs + (kCols512 + c) * kFftBuf, tw, [] { __syncthreads(); });
+        } else {
+#pragma unroll
+            for (int m = 0; m < 8; m++) {
+                x[m] = in(tt, 0, m);
+                yv[m] = in(tt, 1, m);
+            }
+            fft512<false>(x, tau, bufs + c * kFftBuf, tw, [] { __syncthreads(); });
+            fft512<false>(yv, tau, bufs + (kCols512 + c) * kFftBuf, tw, [] { __syncthreads(); });
         }
-        fft512(x, tau, bufs + c * kFftBuf, tw, [] { __syncthreads(); });
-        fft512(yv, tau, bufs + (kCols512 + c) * kFftBuf, tw, [] { __syncthreads(); });
 #pragma unroll
         for (int j = 0; j < 8; j++) {
             const float2 a = x[j], b = yv[j];
@@ -385,10 +438,11 @@ hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int
         // register-resident radix-8 transforms; batches of 2 channels x as
         // many samples as the scratch holds (fewer image read-modify-writes
         // per sample), 2 x 128 column CTAs of 256 threads (two per SM)
-        const size_t rs_smem = sizeof(float2) * (512 + 8 * (size_t)kFftBuf);
-        const size_t cs_smem = sizeof(float2) * (512 + 2 * kCols512 * (size_t)kFftBuf);
+        const size_t rs_smem = sizeof(float2) * (kTwFloat2 + 8 * (size_t)kFftBuf);
+        const size_t cs_smem = sizeof(float2) * (kTwFloat2 + 2 * kCols512 * (size_t)kFftBuf);
         HAI_CUDA_TRY(hai_allow_dyn_smem(large512_rows_kernel, L->ctx->smem_optin));
-        HAI_CUDA_TRY(hai_allow_dyn_smem(large512_cols_kernel, L->ctx->smem_optin));
+        HAI_CUDA_TRY(hai_allow_dyn_smem(large512_cols_kernel<true>, L->ctx->smem_optin));
+        HAI_CUDA_TRY(hai_allow_dyn_smem(large512_cols_kernel<false>, L->ctx->smem_optin));
         const int cb_max = std::min(C, 2);
         const int tb512 = (int)std::max<long long>(1, std::min<long long>(T, fields_cap / ((long long)cb_max * P)));
         for (int t0 = 0; t0 < T; t0 += tb512) {
@@ -401,8 +455,10 @@ hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int
                 bt.tb = tb;
                 large512_rows_kernel<<<dim3(bt.cb * tb * P, (L->box_h + 7) / 8), 512, rs_smem, st>>>(
                     volt, T, P, L->n_elem, L->box_w, L->box_h, L->d_cell_start, L->d_entry_elem, L->d_entry_w, bt, H);
-                large512_cols_kernel<<<dim3(bt.cb, 512 / kCols512), 64 * kCols512, cs_smem, st>>>(
-                    H, L->box_h, bt, img, (t0 > 0 || accumulate) ? 1 : 0);
+                const dim3 cg(bt.cb, 512 / kCols512);
+                const int add = (t0 > 0 || accumulate) ? 1 : 0;
+                if (L->box_h <= 128) large512_cols_kernel<true><<<cg, 64 * kCols512, cs_smem, st>>>(H, L->box_h, bt, img, add);
+                else large512_cols_kernel<false><<<cg, 64 * kCols512, cs_smem, st>>>(H, L->box_h, bt, img, add);
                 prof_count(L->ctx, 2);
             }
         }
