@@ -319,97 +319,87 @@ __global__ void __launch_bounds__(512) large512_rows_kernel(
 // |F_X|^2, |F_Y|^2 and F_X conj(F_Y) at rows l_y = tau + 64 j into 32
 // register accumulators; at the end the image columns are read, added to and
 // written once (output pixel shifted by N/2: the (-1)^j phase centre).
-constexpr int kCols512 = 4;                  // columns per CTA: 512 threads (column, pol, tau), two CTAs per SM
+constexpr int kCols512 = 4;                  // columns per CTA: 256 threads, two CTAs per SM
 
-// Thread (c, p, tau) transforms column l0 + c of polarisation p for every
-// sample of the batch and accumulates |F_p|^2 at its 8 output rows tau + 64 j;
-// the cross term F_X conj(F_Y) is shared between the pair: after each sample
-// both write their outputs (natural order) to their exchange buffers and the
-// X thread accumulates rows j < 4, the Y thread rows j >= 4, reading the
-// partner's values.  Z2: box_h <= 128 (non-zero inputs at rows tau and
-// tau + 64 only), those of the next sample loaded during the current one.
+// Z2: box_h <= 128, so a thread's non-zero inputs are rows tau and tau + 64;
+// those of the next sample are loaded before the current one is transformed.
 template <bool Z2>
-__global__ void __launch_bounds__(128 * kCols512, 2) large512_cols_kernel(const float2 *__restrict__ H, int box_h,
-                                                                        Batch bt, float *__restrict__ img, int add) {
+__global__ void __launch_bounds__(64 * kCols512, 2) large512_cols_kernel(const float2 *__restrict__ H, int box_h,
+                                                                       Batch bt, float *__restrict__ img, int add) {
     extern __shared__ float2 sm[];
     float2 *tw = sm;                                    // [kTwFloat2]
-    float2 *bufs = sm + kTwFloat2;                      // [kCols512 columns][2 pols][kFftBuf]
+    float2 *bufs = sm + kTwFloat2;                      // [2 pols][kCols512 columns][kFftBuf]
     fill_fft512_tables(tw);
-    const int g = threadIdx.x >> 6, tau = threadIdx.x & 63;
-    const int c = g >> 1, p = g & 1;
+    const int c = threadIdx.x >> 6, tau = threadIdx.x & 63;
     const int cc = blockIdx.x, l0 = blockIdx.y * kCols512;
-    float2 *mine = bufs + (2 * c + p) * kFftBuf, *other = bufs + (2 * c + (p ^ 1)) * kFftBuf;
-    float pw[8];                                        // |F_p|^2 at rows tau + 64 j
-    float2 xy[4];                                       // F_X conj(F_Y) at rows tau + 64 (4 p + i)
+    float acc[4][8];
 #pragma unroll
-    for (int j = 0; j < 8; j++) pw[j] = 0.f;
+    for (int q = 0; q < 4; q++)
 #pragma unroll
-    for (int i = 0; i < 4; i++) xy[i] = make_float2(0.f, 0.f);
-    auto in = [&](int tt, int m) -> float2 {
+        for (int j = 0; j < 8; j++) acc[q][j] = 0.f;
+    // input m (row tau + 64 m) of polarisation p of sample tt of this channel
+    auto in = [&](int tt, int p, int m) -> float2 {
         const size_t f = ((size_t)cc * bt.tb + tt) * 2 + p;
         const int yy = tau + 64 * m;
         return yy < box_h ? H[(f * box_h + yy) * 512 + l0 + c] : make_float2(0.f, 0.f);
     };
-    float2 n0 = make_float2(0.f, 0.f), n1 = n0;
+    float2 nx0 = make_float2(0.f, 0.f), nx1 = nx0, ny0 = nx0, ny1 = nx0;
     if (Z2) {
-        n0 = in(0, 0);
-        n1 = in(0, 1);
+        nx0 = in(0, 0, 0);
+        nx1 = in(0, 0, 1);
+        ny0 = in(0, 1, 0);
+        ny1 = in(0, 1, 1);
     }
     __syncthreads();
     for (int tt = 0; tt < bt.tb; tt++) {
-        float2 a[8];
+        float2 x[8], yv[8];
         if (Z2) {
-            a[0] = n0;
-            a[1] = n1;
+            x[0] = nx0;
+            x[1] = nx1;
+            yv[0] = ny0;
+            yv[1] = ny1;
 #pragma unroll
-            for (int m = 2; m < 8; m++) a[m] = make_float2(0.f, 0.f);
+            for (int m = 2; m < 8; m++) x[m] = yv[m] = make_float2(0.f, 0.f);
             if (tt + 1 < bt.tb) {
-                n0 = in(tt + 1, 0);
-                n1 = in(tt + 1, 1);
+                nx0 = in(tt + 1, 0, 0);
+                nx1 = in(tt + 1, 0, 1);
+                ny0 = in(tt + 1, 1, 0);
+                ny1 = in(tt + 1, 1, 1);
             }
-            fft512<true>(a, tau, mine, tw, [] { __syncthreads(); });
+            fft512<true>(x, tau, bufs + c * kFftBuf, tw, [] { __syncthreads(); });
+            fft512<true>(yv, tau, bufs + (kCols512 + c) * kFftBuf, tw, [] { __syncthreads(); });
         } else {
 #pragma unroll
-            for (int m = 0; m < 8; m++) a[m] = in(tt, m);
-            fft512<false>(a, tau, mine, tw, [] { __syncthreads(); });
+            for (int m = 0; m < 8; m++) {
+                x[m] = in(tt, 0, m);
+                yv[m] = in(tt, 1, m);
+            }
+            fft512<false>(x, tau, bufs + c * kFftBuf, tw, [] { __syncthreads(); });
+            fft512<false>(yv, tau, bufs + (kCols512 + c) * kFftBuf, tw, [] { __syncthreads(); });
         }
 #pragma unroll
-        for (int j = 0; j < 8; j++) pw[j] = fmaf(a[j].x, a[j].x, fmaf(a[j].y, a[j].y, pw[j]));
-        __syncthreads();                                // every pass-3 read of the buffers is done
-#pragma unroll
-        for (int j = 0; j < 8; j++) mine[tau + 64 * j] = a[j];
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int j = 4 * p + i;
-            const float2 o = other[tau + 64 * j];
-            const float2 X = p ? o : a[j], Y = p ? a[j] : o;
-            xy[i].x = fmaf(X.x, Y.x, fmaf(X.y, Y.y, xy[i].x));        // Re X conj(Y)
-            xy[i].y = fmaf(X.y, Y.x, fmaf(-X.x, Y.y, xy[i].y));       // Im X conj(Y)
+        for (int j = 0; j < 8; j++) {
+            const float2 a = x[j], b = yv[j];
+            acc[0][j] = fmaf(a.x, a.x, fmaf(a.y, a.y, acc[0][j]));
+            acc[1][j] = fmaf(b.x, b.x, fmaf(b.y, b.y, acc[1][j]));
+            acc[2][j] = fmaf(a.x, b.x, fmaf(a.y, b.y, acc[2][j]));      // Re X conj(Y)
+            acc[3][j] = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc[3][j]));     // Im X conj(Y)
         }
         __syncthreads();                                // exchange buffers free for the next sample
     }
     const int ch = bt.c0 + cc;
     const size_t NN = (size_t)512 * 512;
     const int ox = (l0 + c + 256) & 511;
-    float *base = img + (size_t)ch * 4 * NN + ox;
 #pragma unroll
-    for (int j = 0; j < 8; j++) {
-        float *d = base + (size_t)p * NN + (size_t)((tau + 64 * j + 256) & 511) * 512;
-        float v = pw[j];
-        if (add) v += *d;
-        *d = v;
-    }
+    for (int q = 0; q < 4; q++) {
+        float *dst = img + ((size_t)ch * 4 + q) * NN + ox;
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        float *d = base + 2 * NN + (size_t)((tau + 64 * (4 * p + i) + 256) & 511) * 512;
-        float vr = xy[i].x, vi = xy[i].y;
-        if (add) {
-            vr += d[0];
-            vi += d[NN];
+        for (int j = 0; j < 8; j++) {
+            const int oy = (tau + 64 * j + 256) & 511;
+            float v = acc[q][j];
+            if (add) v += dst[(size_t)oy * 512];
+            dst[(size_t)oy * 512] = v;
         }
-        d[0] = vr;
-        d[NN] = vi;
     }
 }
 
@@ -447,7 +437,7 @@ hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int
     if (N == 512 && P == 2) {
         // register-resident radix-8 transforms; batches of 2 channels x as
         // many samples as the scratch holds (fewer image read-modify-writes
-        // per sample), 2 x 128 column CTAs of 512 threads (two per SM)
+        // per sample), 2 x 128 column CTAs of 256 threads (two per SM)
         const size_t rs_smem = sizeof(float2) * (kTwFloat2 + 8 * (size_t)kFftBuf);
         const size_t cs_smem = sizeof(float2) * (kTwFloat2 + 2 * kCols512 * (size_t)kFftBuf);
         HAI_CUDA_TRY(hai_allow_dyn_smem(large512_rows_kernel, L->ctx->smem_optin));
@@ -467,8 +457,8 @@ hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int
                     volt, T, P, L->n_elem, L->box_w, L->box_h, L->d_cell_start, L->d_entry_elem, L->d_entry_w, bt, H);
                 const dim3 cg(bt.cb, 512 / kCols512);
                 const int add = (t0 > 0 || accumulate) ? 1 : 0;
-                if (L->box_h <= 128) large512_cols_kernel<true><<<cg, 128 * kCols512, cs_smem, st>>>(H, L->box_h, bt, img, add);
-                else large512_cols_kernel<false><<<cg, 128 * kCols512, cs_smem, st>>>(H, L->box_h, bt, img, add);
+                if (L->box_h <= 128) large512_cols_kernel<true><<<cg, 64 * kCols512, cs_smem, st>>>(H, L->box_h, bt, img, add);
+                else large512_cols_kernel<false><<<cg, 64 * kCols512, cs_smem, st>>>(H, L->box_h, bt, img, add);
                 prof_count(L->ctx, 2);
             }
         }
