@@ -196,18 +196,20 @@ hai_status hai_layout_box(const hai_layout *layout, int *box);
  *   volt  device int8 [C][T][P][N_e][2]
  *   img   device float [C][Q][N][N], Q = 1 (P = 1) or 4 (P = 2); overwritten
  *         (accumulate = 0) or added to (accumulate = 1)
- *   prec  HAI_PREC_FP32 (CUDA-core FFT; N = 16 .. 512), HAI_PREC_FP16
- *         (tensor cores; N = 32, 64, 128, 256 or 512, P = 2 and a kernel box of
- *         at most N/2 x N/2 cells, for N >= 256 at most 128 cells high, else
- *         HAI_ERR_UNSUPPORTED) or HAI_PREC_FP16_SPLIT (tensor cores, hi/lo
- *         split; N = 32 or 64)
+ *   prec  HAI_PREC_FP32 (CUDA-core FFT; N = 16 .. 512), or a tensor-core
+ *         precision (HAI_PREC_FP16, _BF16, _FP16_SPLIT, _BF16_SPLIT; N = 32,
+ *         64, 128, 256 or 512, P = 2 and a kernel box of at most N/2 x N/2
+ *         cells, for N >= 256 at most 128 cells high, else
+ *         HAI_ERR_UNSUPPORTED).  At N = 128 the split precisions run on the
+ *         large-grid kernels (the layout then holds their 64 MB scratch).
  * C >= 0, T >= 0 (C = 0 or T = 0: nothing to image; with accumulate = 0 the
  * image is zeroed). */
 hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *layout, const int8_t *volt,
                           int C, int T, hai_precision prec, float *img, int accumulate,
                           void *stream);
 
-/* Autotuner of hai_epic_image's tensor-core path for N = 256, 512: the
+/* Autotuner of hai_epic_image's large-grid tensor-core path (N = 256, 512,
+ * and the hi/lo split at N = 128): the
  * channels imaged per internal chunk, which sets how many samples of each
  * channel one pass of the stage scratch holds (longer sample blocks mean
  * fewer image read-modify-writes, fewer stage-2 items shared between CTAs,
@@ -216,7 +218,7 @@ hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *layout, const int8_t *
  * min(T, 1024) samples of the layout (random voltages, device memory
  * allocated for the trial and freed), and the fastest is kept in the layout
  * for later calls; *chosen (may be NULL) receives it, or 0 when there is
- * nothing to tune (FP32, or a grid side other than 256 / 512).
+ * nothing to tune (FP32, a grid side below 128, or plain operands at 128).
  * cache_path (may be NULL): a text file of "<key> | chunk <c> | <time>"
  * lines, key = device, N, K, P, N_e bucket (floor log2) and precision; a
  * matching line is applied without timing, a new choice is appended.  Not

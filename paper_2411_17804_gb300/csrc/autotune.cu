@@ -1,6 +1,6 @@
-// Autotuner of the large-grid tensor-core EPIC (N = 256, 512): the channels
-// imaged per internal chunk, which sets the samples per batch of the HBM
-// scratch (the scratch holds a fixed number of (channel, sample) pairs, so
+// Autotuner of the large-grid tensor-core EPIC (N = 256, 512, and the split
+// operands at N = 128): the channels imaged per internal chunk, which sets
+// the samples per batch of the HBM scratch (the scratch holds a fixed number of (channel, sample) pairs, so
 // fewer channels per chunk mean longer sample blocks, fewer image read-modify-
 // writes per sample and fewer items split between CTAs, but fewer stage-2
 // items per batch).  Candidates are timed on a synthetic cadence of the
@@ -69,7 +69,7 @@ extern "C" hai_status hai_autotune(hai_ctx *ctx, hai_layout *L, int C, int T, ha
     if (!ctx || !L || L->ctx != ctx || C <= 0 || T <= 0)
         return hai_fail(HAI_ERR_INVALID_ARG, "hai_autotune: NULL context or layout, or C, T not positive");
     if (chosen) *chosen = 0;
-    if (prec == HAI_PREC_FP32 || !L->d_big) return HAI_OK;        // nothing to tune on this path
+    if (!epic_big_used(L, prec)) return HAI_OK;      // nothing to tune on this precision's path
     const std::string key = cache_key(L, prec);
     int chunk = 0;
     if (cache_path && cache_lookup(cache_path, key, chunk)) {

@@ -1022,17 +1022,26 @@ hai_status launch_variant(const hai_layout *L, const int8_t *volt, int C, int T,
 
 }  // namespace
 
+// N = 128 runs here only with split operands (the 4-CTA cluster kernel
+// holds one operand copy in shared memory); its box (<= 64 rows) is padded
+// to the 128 rows of stage 2's K like every other box.
 bool epic_big_supported(const hai_layout *L) {
-    return (L->grid_n == 256 || L->grid_n == 512) && L->n_pol == 2 && L->box_w <= L->grid_n / 2 &&
-           L->box_h <= std::min(128, L->grid_n / 2);
+    return (L->grid_n == 128 || L->grid_n == 256 || L->grid_n == 512) && L->n_pol == 2 &&
+           L->box_w <= L->grid_n / 2 && L->box_h <= std::min(128, L->grid_n / 2);
+}
+
+bool epic_big_used(const hai_layout *L, hai_precision prec) {
+    if (!epic_big_supported(L) || !L->d_big || prec == HAI_PREC_FP32) return false;
+    return L->grid_n >= 256 || prec == HAI_PREC_FP16_SPLIT || prec == HAI_PREC_BF16_SPLIT;
 }
 
 // Per layout: the DFT operands of every variant (plain W = 128 blocks, split
-// hi and lo W = 64 blocks, FP16 and BF16), the batch scratch (A1 and A2) and
-// the partial-tile slots.
+// hi and lo W = 64 blocks, FP16 and BF16; at N = 128 the split ones only),
+// the batch scratch (A1 and A2) and the partial-tile slots.
 hai_status epic_big_prepare(hai_layout *L) {
     if (!epic_big_supported(L)) return HAI_OK;
     const BigGeo g = big_geo(L);
+    const bool split_only = g.N == 128;
     std::vector<std::vector<uint16_t>> ops;          // [variant][stage][part]
     size_t op_bytes = 0;
     for (int vi = 0; vi < 4; vi++) {
@@ -1041,7 +1050,7 @@ hai_status epic_big_prepare(hai_layout *L) {
         for (int stage = 0; stage < 2; stage++)
             for (int part = 0; part < 2; part++) {
                 ops.emplace_back();
-                if (part && !sp) continue;
+                if ((part && !sp) || (split_only && !sp)) continue;
                 dft_operand(g.N, stage == 0 ? g.kb1 * 32 : 128, w, bf, part, ops.back());
                 op_bytes += (ops.back().size() * 2 + 1023) & ~(size_t)1023;
             }
@@ -1088,11 +1097,14 @@ hai_status epic_big_prepare(hai_layout *L) {
     }
     const size_t dense_bytes = dense ? (size_t)ncellp * (sizeof(int32_t) + sizeof(float2)) : 0;
     const size_t per_ct = (size_t)g.P * g.kb1 * kTile16 + (size_t)g.lb2 * kKb2 * kTile16;
-    const size_t budget = (size_t)512 << 20;
+    // 512 MB of scratch; 64 MB at N = 128 (a batch of ~170 split (channel,
+    // sample) pairs, and the many small stations of an uneven array each hold one)
+    const size_t budget = (size_t)(split_only ? 64 : 512) << 20;
     L->big_batch = (long long)std::max<size_t>(2, budget / per_ct) & ~1ll;    // even: halves hold hi and lo
     const size_t a1 = (size_t)L->big_batch * g.P * g.kb1 * kTile16;
     const size_t a2 = (size_t)L->big_batch * g.lb2 * kKb2 * kTile16;
-    const size_t slots = (size_t)L->ctx->num_sms * Var<false>::SlotFloats * sizeof(float);
+    const size_t slots =
+        (size_t)L->ctx->num_sms * (split_only ? Var<true>::SlotFloats : Var<false>::SlotFloats) * sizeof(float);
     cudaError_t e = cudaMalloc(&L->d_big, op_bytes + a1 + a2 + slots + dense_bytes);
     if (e != cudaSuccess) return hai_cuda_fail(e, "epic tensor cores (large grid): scratch");
     L->dev_bytes += op_bytes + a1 + a2 + slots + dense_bytes;
@@ -1129,9 +1141,9 @@ hai_status epic_big_prepare(hai_layout *L) {
 
 hai_status epic_big_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
                            hai_precision prec, cudaStream_t st) {
-    if (!epic_big_supported(L) || !L->d_big)
-        return hai_fail(HAI_ERR_UNSUPPORTED, "epic tensor cores: large-grid path needs N = 256 or 512, 2 pols, "
-                                             "a box <= N/2 wide and <= 128 cells high");
+    if (!epic_big_used(L, prec))
+        return hai_fail(HAI_ERR_UNSUPPORTED, "epic tensor cores: large-grid path needs N = 256 or 512 (or 128 with "
+                                             "split operands), 2 pols, a box <= N/2 wide and <= 128 cells high");
     switch (variant(prec)) {
         case 0: return launch_variant<false, false>(L, volt, C, T, img, accumulate, st);
         case 1: return launch_variant<true, false>(L, volt, C, T, img, accumulate, st);

@@ -537,7 +537,7 @@ extern "C" hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *L, const in
         return HAI_OK;
     }
     if (prec == HAI_PREC_FP32) return epic_fp32_launch(L, volt, C, T, img, accumulate, st);
-    if (L->grid_n >= 256) return epic_big_launch(L, volt, C, T, img, accumulate, prec, st);
+    if (L->grid_n >= 256 || epic_big_used(L, prec)) return epic_big_launch(L, volt, C, T, img, accumulate, prec, st);
     const int split = (prec == HAI_PREC_FP16_SPLIT || prec == HAI_PREC_BF16_SPLIT) ? 1 : 0;
     const int bf16 = (prec == HAI_PREC_BF16 || prec == HAI_PREC_BF16_SPLIT) ? 1 : 0;
     return epic_tc_launch(L, volt, C, T, img, accumulate, st, split, bf16);

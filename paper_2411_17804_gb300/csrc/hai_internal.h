@@ -153,6 +153,7 @@ hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int
 // BF16 operands, plain or split: gridding, stage-1 GEMM and stage-2 GEMM +
 // squaring through an HBM scratch.
 bool epic_big_supported(const hai_layout *L);
+bool epic_big_used(const hai_layout *L, hai_precision prec);   // this precision runs on the large-grid kernels
 hai_status epic_big_prepare(hai_layout *L);
 hai_status epic_big_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
                            hai_precision prec, cudaStream_t st);

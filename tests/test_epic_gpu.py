@@ -393,13 +393,23 @@ def test_tc_split_recovers_fp32_accuracy(hai, ctx, n_elem, C, T, cplx):
     assert e_split < e_plain / 20, (e_split, e_plain)
 
 
-def test_tc_split_unsupported_at_128(hai, ctx):
-    sc = I.uneven_station(I.UnevenConfig(), 0, 700)
-    pos, anchors, taps = station(sc)
+def test_tc_box_wider_than_half_grid_at_128_is_refused(hai, ctx):
+    """Every tensor-core precision needs the kernel box within N/2 x N/2
+    cells; a 93-cell box at N = 128 is refused (FP32 still images it)."""
+    anchors = np.array([[10, 10], [100, 100], [60, 20]], np.int32)
+    taps = np.zeros((3, 3, 3, 2), np.float32)
+    taps[:, 1, 1, 0] = 1.0
     lay = hai.hai_layout_create(ctx, anchors, taps, 128, 2)
-    volt = torch.zeros((1, 2, 2, len(pos), 2), dtype=torch.int8, device="cuda")
-    img = torch.zeros((1, 4, 128, 128), device="cuda")
-    with pytest.raises(hai.HaiError) as e:
-        hai.hai_epic_image(ctx, lay, volt, 1, 2, hai.HAI_PREC_FP16_SPLIT, img, 0)
-    assert e.value.status == 4
-    hai.hai_layout_destroy(lay)
+    try:
+        volt = I.random_voltages((1, 2, 2, 3, 2), seed=23, device="cuda")
+        img = torch.zeros((1, 4, 128, 128), device="cuda")
+        for prec in (hai.HAI_PREC_FP16, hai.HAI_PREC_BF16, hai.HAI_PREC_FP16_SPLIT, hai.HAI_PREC_BF16_SPLIT):
+            with pytest.raises(hai.HaiError) as e:
+                hai.hai_epic_image(ctx, lay, volt, 1, 2, prec, img, 0)
+            assert e.value.status == 4
+        hai.hai_epic_image(ctx, lay, volt, 1, 2, hai.HAI_PREC_FP32, img, 0)
+        hai.hai_sync(ctx)
+        want = O.epic_image(128, anchors, taps, volt.cpu().numpy())
+        assert rel_err_planes(img.cpu().numpy(), want).max() < FP32_TOL
+    finally:
+        hai.hai_layout_destroy(lay)

@@ -1,5 +1,5 @@
-"""Tensor-core EPIC on the large grids (N = 256, 512) in every operand form:
-FP16, BF16 and their hi/lo splits, against the FP64 oracle.
+"""Tensor-core EPIC on the large grids (N = 256, 512, and 128) in every
+operand form: FP16, BF16 and their hi/lo splits, against the FP64 oracle.
 
 The dense all-sky lattice (128 x 128 elements at 0.5 lambda on a 512^2 grid,
 1 x 1 unit taps) and the SKA-shaped station on a 256^2 grid.  The cases cover
@@ -179,25 +179,42 @@ def test_small_grids_every_operand_form(hai, ctx, pname, n_elem, C, T, cplx):
         hai.hai_layout_destroy(lay)
 
 
-def test_bf16_at_128_and_split_unsupported(hai, ctx):
-    """N = 128 (4-CTA clusters): BF16 operands against the oracle at the BF16
-    bound; the hi/lo split is not built at this grid side."""
+def test_every_form_at_128(hai, ctx):
+    """N = 128: FP16 and BF16 on the 4-CTA cluster kernel, the two splits on
+    the large-grid kernels (64 MB scratch: 170 split (channel, sample) pairs
+    per batch, so 3 x 70 samples take two batches), each against the oracle
+    at its bound, and accumulate."""
     sc = I.uneven_station(I.UnevenConfig(), 0, 700)
     pos, anchors, taps = station(sc)
     lay = hai.hai_layout_create(ctx, anchors, taps, 128, 2)
     try:
-        volt = I.random_voltages((3, 37, 2, len(pos), 2), seed=17)
+        C, T = 3, 70
+        volt = I.random_voltages((C, T, 2, len(pos), 2), seed=17)
         want = O.epic_image(128, anchors, taps, volt.numpy())
-        img = image(hai, ctx, lay, volt.cuda(), 3, 37, hai.HAI_PREC_BF16, 128)
-        check(hai, hai.HAI_PREC_BF16, img.cpu().numpy(), want)
-        fp16 = image(hai, ctx, lay, volt.cuda(), 3, 37, hai.HAI_PREC_FP16, 128)
-        check(hai, hai.HAI_PREC_FP16, fp16.cpu().numpy(), want)
-        zero = torch.zeros((1, 2, 2, len(pos), 2), dtype=torch.int8, device="cuda")
-        out = torch.zeros((1, 4, 128, 128), device="cuda")
-        for prec in (hai.HAI_PREC_BF16_SPLIT, hai.HAI_PREC_FP16_SPLIT):
-            with pytest.raises(hai.HaiError) as e:
-                hai.hai_epic_image(ctx, lay, zero, 1, 2, prec, out, 0)
-            assert e.value.status == 4
+        for pname in PRECS:
+            prec = getattr(hai, f"HAI_PREC_{pname}")
+            img = image(hai, ctx, lay, volt.cuda(), C, T, prec, 128)
+            check(hai, prec, img.cpu().numpy(), want)
+            if "SPLIT" in pname:
+                image(hai, ctx, lay, volt.cuda(), C, T, prec, 128, img, 1)
+                check(hai, prec, img.cpu().numpy(), 2 * want)
+    finally:
+        hai.hai_layout_destroy(lay)
+
+
+def test_split_at_128_channel_chunks(hai, ctx):
+    """More channels than a split batch at N = 128 holds pairs (170): sampled
+    channels on both sides of the chunk boundary against the oracle."""
+    sc = I.uneven_station(I.UnevenConfig(), 0, 700)
+    pos, anchors, taps = station(sc)
+    lay = hai.hai_layout_create(ctx, anchors, taps, 128, 2)
+    try:
+        C = 180
+        volt = I.random_voltages((C, 1, 2, len(pos), 2), seed=19, device="cuda")
+        img = image(hai, ctx, lay, volt, C, 1, hai.HAI_PREC_FP16_SPLIT, 128)
+        for c in (0, 169, 170, 179):
+            want = O.epic_image(128, anchors, taps, volt[c:c + 1].cpu().numpy())
+            check(hai, hai.HAI_PREC_FP16_SPLIT, img[c:c + 1].cpu().numpy(), want)
     finally:
         hai.hai_layout_destroy(lay)
 
