@@ -16,6 +16,10 @@
 //            |F_X|^2, |F_Y|^2 and F_X conj(F_Y) of its row l_y into register
 //            accumulators; at the end of the batch the image columns are
 //            read, added to and written once.
+// N = 512 (the dense all-sky lattice) keeps each 512-point line in registers:
+// the rows as radix-8 transforms over 64 threads, the columns of a box of at
+// most 128 rows as four 128-point transforms per warp (see below), the
+// column data staged through shared memory a few samples ahead.
 // As in the small-grid FP32 kernel the box sits at the transform's origin:
 // the corner shift multiplies F by a phase common to both polarisations that
 // cancels in every product, and the (-1)^(jx+jy) phase-centre factor is an
@@ -23,6 +27,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "hai_internal.h"
 
@@ -313,17 +318,15 @@ __global__ void __launch_bounds__(512) large512_rows_kernel(
     }
 }
 
-// Column pass, N = 512, two polarisations: blockIdx.x = channel of the batch,
-// blockIdx.y = block of kCols512 columns; thread (c = tid / 64, tau) transforms
-// column l0 + c of both polarisations for every sample of the batch and adds
-// |F_X|^2, |F_Y|^2 and F_X conj(F_Y) at rows l_y = tau + 64 j into 32
-// register accumulators; at the end the image columns are read, added to and
-// written once (output pixel shifted by N/2: the (-1)^j phase centre).
+// Column pass, N = 512, two polarisations, boxes taller than 128 rows:
+// blockIdx.x = channel of the batch, blockIdx.y = block of kCols512 columns;
+// thread (c = tid / 64, tau) transforms column l0 + c of both polarisations
+// for every sample of the batch and adds |F_X|^2, |F_Y|^2 and F_X conj(F_Y) at
+// rows l_y = tau + 64 j into 32 register accumulators; at the end the image
+// columns are read, added to and written once (output pixel shifted by N/2:
+// the (-1)^j phase centre).
 constexpr int kCols512 = 4;                  // columns per CTA: 256 threads, two CTAs per SM
 
-// Z2: box_h <= 128, so a thread's non-zero inputs are rows tau and tau + 64;
-// those of the next sample are loaded before the current one is transformed.
-template <bool Z2>
 __global__ void __launch_bounds__(64 * kCols512, 2) large512_cols_kernel(const float2 *__restrict__ H, int box_h,
                                                                        Batch bt, float *__restrict__ img, int add) {
     extern __shared__ float2 sm[];
@@ -343,40 +346,16 @@ __global__ void __launch_bounds__(64 * kCols512, 2) large512_cols_kernel(const f
         const int yy = tau + 64 * m;
         return yy < box_h ? H[(f * box_h + yy) * 512 + l0 + c] : make_float2(0.f, 0.f);
     };
-    float2 nx0 = make_float2(0.f, 0.f), nx1 = nx0, ny0 = nx0, ny1 = nx0;
-    if (Z2) {
-        nx0 = in(0, 0, 0);
-        nx1 = in(0, 0, 1);
-        ny0 = in(0, 1, 0);
-        ny1 = in(0, 1, 1);
-    }
     __syncthreads();
     for (int tt = 0; tt < bt.tb; tt++) {
         float2 x[8], yv[8];
-        if (Z2) {
-            x[0] = nx0;
-            x[1] = nx1;
-            yv[0] = ny0;
-            yv[1] = ny1;
 #pragma unroll
-            for (int m = 2; m < 8; m++) x[m] = yv[m] = make_float2(0.f, 0.f);
-            if (tt + 1 < bt.tb) {
-                nx0 = in(tt + 1, 0, 0);
-                nx1 = in(tt + 1, 0, 1);
-                ny0 = in(tt + 1, 1, 0);
-                ny1 = in(tt + 1, 1, 1);
-            }
-            fft512<true>(x, tau, bufs + c * kFftBuf, tw, [] { __syncthreads(); });
-            fft512<true>(yv, tau, bufs + (kCols512 + c) * kFftBuf, tw, [] { __syncthreads(); });
-        } else {
-#pragma unroll
-            for (int m = 0; m < 8; m++) {
-                x[m] = in(tt, 0, m);
-                yv[m] = in(tt, 1, m);
-            }
-            fft512<false>(x, tau, bufs + c * kFftBuf, tw, [] { __syncthreads(); });
-            fft512<false>(yv, tau, bufs + (kCols512 + c) * kFftBuf, tw, [] { __syncthreads(); });
+        for (int m = 0; m < 8; m++) {
+            x[m] = in(tt, 0, m);
+            yv[m] = in(tt, 1, m);
         }
+        fft512<false>(x, tau, bufs + c * kFftBuf, tw, [] { __syncthreads(); });
+        fft512<false>(yv, tau, bufs + (kCols512 + c) * kFftBuf, tw, [] { __syncthreads(); });
 #pragma unroll
         for (int j = 0; j < 8; j++) {
             const float2 a = x[j], b = yv[j];
@@ -403,14 +382,234 @@ __global__ void __launch_bounds__(64 * kCols512, 2) large512_cols_kernel(const f
     }
 }
 
+// ------------------------------------------------------------------ N = 512, box <= 128 x 128
+// A 512-point transform whose inputs vanish beyond the first 128 (a box of at
+// most 128 cells along the transform) splits by output residue r = k mod 4:
+//   F[4 k + r] = sum_{n < 128} (h[n] w512^(n r)) w128^(n k),  k < 128,
+// four 128-point transforms of pre-twiddled inputs.  One warp computes one
+// such 512-point transform, lane = 8 r + t.  With n = t + 8 m (m < 16) and
+// k = k1 + 16 k2 (k1 < 16, k2 < 8), w128^(n k) = w128^(t k1) w8^(t k2)
+// w16^(m k1): lane (r, t) takes the 16-point DFT over m of its 16
+// pre-twiddled inputs and multiplies output k1 by w128^(t k1); after one
+// exchange through shared memory (within the warp: no block barrier) lane
+// (r, t) takes the 8-point DFTs over t of k1 = t and k1 = t + 8.  It ends with
+// F[4 t + r + 32 h + 64 k2] in v[8 h + k2].  Exponent + throughout.
+//
+// Twiddle tables (built on the host in double precision, rounded once):
+//   Pq[r kPr + 8 m + t] = w512^(r (t + 8 m)), Tq[8 k1 + t] = w128^(t k1).
+// Pq's rows are kPr = 136 apart so that one instruction's 32 lanes touch two
+// wavefronts; the exchange buffer of a warp, kXq float2 per transform, holds
+// value k1 of lane (r, t) at r 152 + 9 k1 + t (writes and reads conflict-free).
+constexpr int kPr = 136;
+constexpr int kTwq = 4 * kPr + 128;          // float2: Pq, then Tq
+constexpr int kXq = 3 * 152 + 15 * 9 + 8;    // float2 per transform's exchange buffer
+constexpr size_t kHBytes = (size_t)64 << 20; // row-pass output of a batch (L2-resident)
+
+// 16-point DFT, exponent +, natural order in and out: m = m1 + 4 m2,
+// k = ka + 4 kb; 4-point DFTs over m2, twiddles w16^(m1 ka), 4-point DFTs
+// over m1.
+__device__ __forceinline__ void dft16(float2 (&a)[16]) {
+    const float c8 = 0.92387953251128674f, s8 = 0.38268343236508978f, h = 0.70710678118654752f;
+#pragma unroll
+    for (int m1 = 0; m1 < 4; m1++) dft4(a[m1], a[m1 + 4], a[m1 + 8], a[m1 + 12]);   // a[m1 + 4 ka]
+    a[5] = cmul(a[5], make_float2(c8, s8));                                         // w16^1
+    a[9] = make_float2(h * (a[9].x - a[9].y), h * (a[9].x + a[9].y));               // w16^2
+    a[13] = cmul(a[13], make_float2(s8, c8));                                       // w16^3
+    a[6] = make_float2(h * (a[6].x - a[6].y), h * (a[6].x + a[6].y));               // w16^2
+    a[10] = cmuli(a[10]);                                                           // w16^4
+    a[14] = make_float2(-h * (a[14].x + a[14].y), h * (a[14].x - a[14].y));         // w16^6
+    a[7] = cmul(a[7], make_float2(s8, c8));                                         // w16^3
+    a[11] = make_float2(-h * (a[11].x + a[11].y), h * (a[11].x - a[11].y));         // w16^6
+    a[15] = cmul(a[15], make_float2(-c8, -s8));                                     // w16^9
+#pragma unroll
+    for (int ka = 0; ka < 4; ka++) dft4(a[4 * ka], a[4 * ka + 1], a[4 * ka + 2], a[4 * ka + 3]);   // a[4 ka + kb]
+    float2 o[16];
+#pragma unroll
+    for (int ka = 0; ka < 4; ka++)
+#pragma unroll
+        for (int kb = 0; kb < 4; kb++) o[ka + 4 * kb] = a[4 * ka + kb];
+#pragma unroll
+    for (int k = 0; k < 16; k++) a[k] = o[k];
+}
+
+// Two 512-point transforms (the two polarisations) by one warp, as above;
+// xb: the warp's two exchange buffers (2 kXq float2), tw: Pq and Tq in shared
+// memory.  Entry: x[m] = h_X[t + 8 m], y[m] = h_Y[t + 8 m].
+__device__ __forceinline__ void fft512q2(float2 (&x)[16], float2 (&y)[16], int r, int t, float2 *xb,
+                                         const float2 *tw) {
+    const float2 *pr = tw + r * kPr + t;
+#pragma unroll
+    for (int m = 0; m < 16; m++) {
+        const float2 w = pr[8 * m];
+        x[m] = cmul(x[m], w);
+        y[m] = cmul(y[m], w);
+    }
+    dft16(x);
+    dft16(y);
+    const float2 *tq = tw + 4 * kPr + t;
+#pragma unroll
+    for (int k = 1; k < 16; k++) {
+        const float2 w = tq[8 * k];
+        x[k] = cmul(x[k], w);
+        y[k] = cmul(y[k], w);
+    }
+    float2 *wx = xb + r * 152 + t, *wy = wx + kXq;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        wx[9 * k] = x[k];
+        wy[9 * k] = y[k];
+    }
+    __syncwarp();
+    const float2 *rx = xb + r * 152 + 9 * t, *ry = rx + kXq;
+    float2 a0[8], a1[8], b0[8], b1[8];
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        a0[s] = rx[s];
+        a1[s] = rx[72 + s];
+        b0[s] = ry[s];
+        b1[s] = ry[72 + s];
+    }
+    __syncwarp();                                        // the buffers are free again
+    dft8(a0);
+    dft8(a1);
+    dft8(b0);
+    dft8(b1);
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        x[k] = a0[k];
+        x[8 + k] = a1[k];
+        y[k] = b0[k];
+        y[8 + k] = b1[k];
+    }
+}
+
+__device__ __forceinline__ void load_twq(float2 *dst, const float2 *__restrict__ src) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    for (int i = threadIdx.x; i < kTwq / 2; i += blockDim.x) d4[i] = s4[i];
+}
+
+// Column pass, boxes of at most 128 rows: one warp per (image column l_x,
+// channel of the batch), four adjacent columns per block.  For each sample
+// the block copies the four columns of both pols (box_h rows of H, 32 bytes
+// per row: whole L2 sectors) into shared memory asynchronously two samples
+// ahead; each warp transforms its column along y and adds |F_X|^2, |F_Y|^2
+// and F_X conj(F_Y) into 64 register accumulators (16 rows l_y per lane); at
+// the end the column is read, added to and written once (output pixel
+// shifted by N/2).  The staged rows are kRowQ float2 apart so that a warp's
+// reads of rows t + 8 m hit distinct banks.
+constexpr int kColsQ = 4;                     // columns (warps) per block
+constexpr int kRowQ = 6;                      // float2 per staged row (4 used)
+constexpr int kPfq = 3;                       // sample stages in flight
+constexpr int kStageQ = 2 * 128 * kRowQ;      // float2 per stage (2 pols x 128 rows)
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
+
+__global__ void __launch_bounds__(32 * kColsQ, 2) large512q_cols_kernel(const float2 *__restrict__ H, int box_h,
+                                                                      const float2 *__restrict__ twq, Batch bt,
+                                                                      float *__restrict__ img, int add) {
+    extern __shared__ float4 smq[];
+    float2 *tw = reinterpret_cast<float2 *>(smq);                 // [kTwq]
+    float2 *pb = tw + kTwq;                                       // [kPfq][2 pols][128 rows][kRowQ]
+    float2 *xb = pb + kPfq * kStageQ;                             // [kColsQ][2 kXq]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, r = lane >> 3, t = lane & 7;
+    const int lx0 = blockIdx.x * kColsQ, lx = lx0 + warp, cc = blockIdx.y;
+    xb += warp * 2 * kXq;
+    load_twq(tw, twq);
+    for (int i = threadIdx.x; i < kPfq * kStageQ; i += blockDim.x) pb[i] = make_float2(0.f, 0.f);
+    __syncthreads();                                              // rows >= box_h stay zero
+    auto issue = [&](int tt) {                                    // two 16-byte copies per (pol, row)
+        const size_t f0 = ((size_t)cc * bt.tb + tt) * 2;
+        float2 *dst = pb + (tt % kPfq) * kStageQ;
+        for (int i = threadIdx.x; i < 2 * 128 * 2; i += blockDim.x) {
+            const int u = i & 1, p = i >> 8, yy = (i >> 1) & 127;
+            if (yy < box_h)
+                cp_async16(dst + (p * 128 + yy) * kRowQ + 2 * u, H + (((f0 + p) * box_h + yy) * 512 + lx0 + 2 * u));
+        }
+    };
+    float acc[4][16];
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+        for (int j = 0; j < 16; j++) acc[q][j] = 0.f;
+    issue(0);
+    cp_async_commit();
+    if (bt.tb > 1) issue(1);
+    cp_async_commit();
+    for (int tt = 0; tt < bt.tb; tt++) {
+        __syncthreads();                                          // the stage refilled next was read last sample
+        if (tt + 2 < bt.tb) issue(tt + 2);
+        cp_async_commit();
+        cp_async_wait2();
+        __syncthreads();                                          // sample tt's copies (every thread's) landed
+        const float2 *src = pb + (tt % kPfq) * kStageQ + t * kRowQ + warp;
+        float2 x[16], yv[16];
+#pragma unroll
+        for (int m = 0; m < 16; m++) {
+            x[m] = src[8 * m * kRowQ];
+            yv[m] = src[(128 + 8 * m) * kRowQ];
+        }
+        fft512q2(x, yv, r, t, xb, tw);
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const float2 a = x[j], b = yv[j];
+            acc[0][j] = fmaf(a.x, a.x, fmaf(a.y, a.y, acc[0][j]));
+            acc[1][j] = fmaf(b.x, b.x, fmaf(b.y, b.y, acc[1][j]));
+            acc[2][j] = fmaf(a.x, b.x, fmaf(a.y, b.y, acc[2][j]));      // Re X conj(Y)
+            acc[3][j] = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc[3][j]));     // Im X conj(Y)
+        }
+    }
+    const int ch = bt.c0 + cc;
+    const size_t NN = (size_t)512 * 512;
+    const int ox = (lx + 256) & 511;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        float *dst = img + ((size_t)ch * 4 + q) * NN + ox;
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int k2 = 0; k2 < 8; k2++) {
+                const int oy = (4 * t + r + 32 * h + 64 * k2 + 256) & 511;
+                float v = acc[q][8 * h + k2];
+                if (add) v += dst[(size_t)oy * 512];
+                dst[(size_t)oy * 512] = v;
+            }
+    }
+}
+
 }  // namespace
 
 bool epic_large_supported(int grid_n) { return grid_n == 128 || grid_n == 256 || grid_n == 512; }
 
+// The row-pass output of a batch (64 MB, kept in L2 between the two passes),
+// and at N = 512 the twiddle tables of the 4 x 128-point transforms after it.
 size_t epic_large_scratch_bytes(int grid_n, int box_h) {
-    (void)grid_n;
     (void)box_h;
-    return (size_t)64 << 20;
+    return kHBytes + (grid_n == 512 ? sizeof(float2) * kTwq : 0);
+}
+
+// Pq and Tq (see the N = 512 transforms above) from FP64 sines and cosines.
+hai_status epic_large_prepare(hai_layout *L) {
+    if (L->grid_n != 512 || !L->d_large_scratch) return HAI_OK;
+    std::vector<float2> tab(kTwq);
+    auto w512 = [](long long j) {
+        const double a = 2.0 * M_PI * (double)(j % 512) / 512.0;
+        return make_float2((float)cos(a), (float)sin(a));
+    };
+    for (int r = 0; r < 4; r++)
+        for (int m = 0; m < 16; m++)
+            for (int t = 0; t < 8; t++) tab[r * kPr + 8 * m + t] = w512((long long)r * (t + 8 * m));
+    for (int k1 = 0; k1 < 16; k1++)
+        for (int t = 0; t < 8; t++) tab[4 * kPr + 8 * k1 + t] = w512(4ll * t * k1);
+    const cudaError_t e = cudaMemcpy(static_cast<uint8_t *>(L->d_large_scratch) + kHBytes, tab.data(),
+                                     sizeof(float2) * kTwq, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return hai_cuda_fail(e, "epic fp32 (large grid): twiddle tables");
+    return HAI_OK;
 }
 
 hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
@@ -421,7 +620,7 @@ hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int
     int log2n = 0;
     while ((1 << log2n) < N) log2n++;
     const size_t field_bytes = sizeof(float2) * (size_t)L->box_h * N;
-    const long long fields_cap = (long long)(L->large_scratch_bytes / field_bytes);
+    const long long fields_cap = (long long)(kHBytes / field_bytes);
     if (fields_cap < P) return hai_fail(HAI_ERR_UNSUPPORTED, "epic fp32: box too large for the row scratch");
     // batch: up to 8 samples of as many channels as the scratch holds
     const int tb_max = (int)std::max<long long>(1, std::min<long long>(8, fields_cap / P));
@@ -435,14 +634,17 @@ hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int
     float2 *H = static_cast<float2 *>(L->d_large_scratch);
     const int pidx = prof_begin(L->ctx, st);
     if (N == 512 && P == 2) {
-        // register-resident radix-8 transforms; batches of 2 channels x as
-        // many samples as the scratch holds (fewer image read-modify-writes
-        // per sample), 2 x 128 column CTAs of 256 threads (two per SM)
+        // rows: register-resident radix-8 transforms; columns: the 4 x 128-point
+        // warp transforms for boxes of at most 128 rows, else radix-8 as the
+        // rows.  Batches of 2 channels x as many samples as the scratch holds
+        // (fewer image read-modify-writes per sample).
+        const float2 *twq = reinterpret_cast<const float2 *>(static_cast<const uint8_t *>(L->d_large_scratch) + kHBytes);
         const size_t rs_smem = sizeof(float2) * (kTwFloat2 + 8 * (size_t)kFftBuf);
         const size_t cs_smem = sizeof(float2) * (kTwFloat2 + 2 * kCols512 * (size_t)kFftBuf);
+        const size_t cq_smem = sizeof(float2) * (kTwq + (size_t)kPfq * kStageQ + (size_t)kColsQ * 2 * kXq);
         HAI_CUDA_TRY(hai_allow_dyn_smem(large512_rows_kernel, L->ctx->smem_optin));
-        HAI_CUDA_TRY(hai_allow_dyn_smem(large512_cols_kernel<true>, L->ctx->smem_optin));
-        HAI_CUDA_TRY(hai_allow_dyn_smem(large512_cols_kernel<false>, L->ctx->smem_optin));
+        HAI_CUDA_TRY(hai_allow_dyn_smem(large512_cols_kernel, L->ctx->smem_optin));
+        HAI_CUDA_TRY(hai_allow_dyn_smem(large512q_cols_kernel, L->ctx->smem_optin));
         const int cb_max = std::min(C, 2);
         const int tb512 = (int)std::max<long long>(1, std::min<long long>(T, fields_cap / ((long long)cb_max * P)));
         for (int t0 = 0; t0 < T; t0 += tb512) {
@@ -455,10 +657,13 @@ hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int
                 bt.tb = tb;
                 large512_rows_kernel<<<dim3(bt.cb * tb * P, (L->box_h + 7) / 8), 512, rs_smem, st>>>(
                     volt, T, P, L->n_elem, L->box_w, L->box_h, L->d_cell_start, L->d_entry_elem, L->d_entry_w, bt, H);
-                const dim3 cg(bt.cb, 512 / kCols512);
                 const int add = (t0 > 0 || accumulate) ? 1 : 0;
-                if (L->box_h <= 128) large512_cols_kernel<true><<<cg, 64 * kCols512, cs_smem, st>>>(H, L->box_h, bt, img, add);
-                else large512_cols_kernel<false><<<cg, 64 * kCols512, cs_smem, st>>>(H, L->box_h, bt, img, add);
+                if (L->box_h <= 128)
+                    large512q_cols_kernel<<<dim3(512 / kColsQ, bt.cb), 32 * kColsQ, cq_smem, st>>>(H, L->box_h, twq, bt,
+                                                                                                   img, add);
+                else
+                    large512_cols_kernel<<<dim3(bt.cb, 512 / kCols512), 64 * kCols512, cs_smem, st>>>(H, L->box_h, bt,
+                                                                                                     img, add);
                 prof_count(L->ctx, 2);
             }
         }

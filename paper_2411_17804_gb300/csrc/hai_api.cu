@@ -335,6 +335,7 @@ extern "C" hai_status hai_layout_create(hai_ctx *ctx, const hai_layout_desc *d, 
     if (n >= 128 && e == cudaSuccess) {
         L->large_scratch_bytes = epic_large_scratch_bytes(n, L->box_h);
         e = dmalloc(&L->d_large_scratch, L->large_scratch_bytes);
+        if (e == cudaSuccess && epic_large_prepare(L) != HAI_OK) e = cudaErrorUnknown;
     }
     if (e == cudaSuccess && epic_tc_supported(L)) {   // tensor-core path: gather table, station record
         std::vector<uint8_t> tab;

@@ -147,6 +147,7 @@ hai_status epic_reduce_launch(const hai_layout *L, const EpicSplit &sp, int C, i
 // squaring and accumulation).
 bool epic_large_supported(int grid_n);
 size_t epic_large_scratch_bytes(int grid_n, int box_h);
+hai_status epic_large_prepare(hai_layout *L);   // constant tables in the scratch's tail
 hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
                              cudaStream_t st);
 // Tensor-core EPIC for N = 256, 512 (box <= N/2, box height <= 128), FP16 or

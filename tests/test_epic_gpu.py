@@ -261,9 +261,19 @@ def _dense(n_side=128):
     ("n512", 2, 3, 2),        # the dense lattice, 128 x 128 box
     ("n512", 1, 2, 1),        # one polarisation
     ("n512", 9, 9, 2),        # two sample batches and two channel blocks of the row scratch
+    ("n512_cplx", 3, 4, 2),   # 3 x 3 complex taps, random anchors: several entries per cell, box < 128
+    ("n512_wide", 2, 3, 2),   # a box wider than 128 cells (the general transforms)
+    ("n512_tall", 2, 3, 2),   # a box taller than 128 cells
 ])
 def test_large_grid_fp32_matches_oracle(hai, ctx, case, C, T, P):
-    if case == "n128":
+    if case.startswith("n512_"):
+        rng = np.random.default_rng(len(case))
+        n, ne, k = 512, 150, 3
+        wx, wy = {"n512_cplx": (100, 120), "n512_wide": (200, 90), "n512_tall": (90, 200)}[case]
+        anchors = np.stack([rng.integers(5, 5 + wx - k, ne), rng.integers(7, 7 + wy - k, ne)], axis=1).astype(np.int32)
+        taps = rng.standard_normal((ne, k, k, 2)).astype(np.float32)
+        volt = I.random_voltages((C, T, P, ne, 2), seed=C + 3 * T)
+    elif case == "n128":
         sc = I.uneven_station(I.UnevenConfig(), 0, 700)
         pos, anchors, taps = station(sc)
         n = 128
