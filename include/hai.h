@@ -300,6 +300,65 @@ hai_status hai_workspace_size(const hai_plan *plan, size_t *bytes);
  * every grid group. */
 hai_status hai_plan_schedule(const hai_plan *plan, int *n_class, int *grid_n, int *ctas, double *measured_ms);
 
+/* Second level of the hierarchy in the same graph launch (Section 6, the
+ * two-stage architectures: station-synthesised fields imaged between
+ * stations).  Set once per plan; hai_plan_run_hier then runs, as ONE graph
+ * launch per cadence, the station EPIC images of hai_plan_run and after them
+ *   1. K voltage beams of every station (Eq. intra-station BF, diagonal pol:
+ *      B^p_{s,k} = sum_a conj(w^p_{s,k,a}) E^p_{s,a}; exact int32 sums, then
+ *      |x| / 2^shift rounded half away from zero and clamped to 127, as
+ *      hai_beamform's requantised output),
+ *   2. their inter-station order (hai_beams_to_corr),
+ *   3. the inter-station correlator + XFFT dirty image of every beam (Eq.
+ *      inter-station visibilities and XFFT; hai_correlate with the K*C
+ *      (beam, channel) pairs as channels, then hai_xfft_station_image) when
+ *      `xfft` is set, and/or
+ *   4. the inter-station EPIC image of every beam (Eq. inter-station EPIC:
+ *      hai_epic_image of beam k's block with epic[k], a layout from
+ *      hai_station_epic_layout_create) when `epic` is set. */
+typedef struct hai_vis_layout hai_vis_layout;   /* declared with its functions below */
+typedef struct {
+    int n_beam;                     /* K, 1..64 */
+    const int8_t *weights;          /* device int8: station s's weights [K][2][N_e,s][2]
+                                       start at byte weight_off[s] (even) */
+    const int64_t *weight_off;      /* host [S] */
+    int requant_shift;              /* 0..30 */
+    const hai_vis_layout *xfft;     /* S stations, K directions; or NULL */
+    const hai_layout *const *epic;  /* host array of K layouts (S elements, 2 pols); or NULL */
+    hai_precision epic_prec;        /* precision of the inter-station EPIC */
+} hai_plan_hier_desc;
+/* The plan keeps the weights pointer and the layouts (not copies): they must
+ * outlive the plan or the next hai_plan_set_hierarchy.  At least one of xfft
+ * and epic; HAI_ERR_UNSUPPORTED if 4 K (S + 1) bytes exceed 48 KB. */
+hai_status hai_plan_set_hierarchy(hai_plan *plan, const hai_plan_hier_desc *desc);
+
+/* Sizes of the second level's buffers (host outputs, NULL for any not
+ * wanted): beams and their reorder, bytes each; visibilities, int32 count;
+ * the XFFT and EPIC images, float counts (0 when that stage is not set). */
+hai_status hai_plan_hier_sizes(const hai_plan *plan, int64_t *beam_bytes, int64_t *vis_ints, int64_t *xfft_floats,
+                               int64_t *epic_floats);
+
+/* Device buffers of the second level, owned by the caller, 16-byte aligned:
+ *   beams     int8 [S][C][T][K][2][2] (station beams, hai_beamform's layout)
+ *   corr      int8 [K][C][T][2][S][2] (their inter-station order)
+ *   vis       int32 [K][C][S(S+1)/2][2][2][2] (with xfft; else may be NULL)
+ *   xfft_img  float [K][C][4][N_A][N_A] (with xfft; else may be NULL)
+ *   epic_img  float: beam k's images [C][4][N_k][N_k] one after another
+ *             (with epic; else may be NULL)
+ *   n_saturated  device int64 count of clamped beam components (or NULL) */
+typedef struct {
+    int8_t *beams;
+    int8_t *corr;
+    int32_t *vis;
+    float *xfft_img;
+    float *epic_img;
+    long long *n_saturated;
+} hai_plan_hier_buffers;
+/* As hai_plan_run, plus the second level into `buffers`; the graph is
+ * captured again when any pointer changes. */
+hai_status hai_plan_run_hier(hai_plan *plan, const int8_t *volt, float *img, const hai_plan_hier_buffers *buffers,
+                             void *stream);
+
 /* ---------------------------------------------------------------------------
  * Correlator (Eq. intra-station visibilities): for every element pair a >= b
  * (autos included) and polarisation pair (p, q),

@@ -154,6 +154,7 @@ hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int
 // BF16 operands, plain or split: gridding, stage-1 GEMM and stage-2 GEMM +
 // squaring through an HBM scratch.
 bool epic_big_supported(const hai_layout *L);
+void vis_layout_dims(const hai_vis_layout *L, int *S, int *N, int *K);   // stations, grid side, directions
 bool epic_big_used(const hai_layout *L, hai_precision prec);   // this precision runs on the large-grid kernels
 hai_status epic_big_prepare(hai_layout *L);
 hai_status epic_big_launch(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,

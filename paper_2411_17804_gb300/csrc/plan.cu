@@ -13,6 +13,12 @@
 // Cost model of one sample of a station, in SM cycles: a fixed part for the
 // two DFT stages and the epilogue plus a part per gather entry of the
 // gridding step (entries of the largest rank for N = 128).
+//
+// Second level (hai_plan_set_hierarchy, Section 6): after the station images
+// the same graph beamforms every station (int8 weights, exact int32 sums,
+// requantised to int8), reorders the beams for the inter-station stage and
+// images them with the inter-station correlator + XFFT and/or the
+// inter-station EPIC of every beam.
 #include <math.h>
 #include <string.h>
 
@@ -62,6 +68,15 @@ struct hai_plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const void *g_volt = nullptr, *g_img = nullptr;
+    // second level
+    int hK = 0, hshift = 0;
+    const int8_t *hw = nullptr;                  // caller's weights (device)
+    void *d_hst = nullptr;                       // per station: voltage and weight offsets, elements
+    const hai_vis_layout *hx = nullptr;          // inter-station XFFT (or NULL)
+    std::vector<const hai_layout *> he;          // inter-station EPIC layouts, one per beam (or none)
+    hai_precision hprec = HAI_PREC_FP16;
+    bool g_hier = false;                         // the captured graph holds the second level
+    hai_plan_hier_buffers gb = {};               // with these buffers
 };
 
 namespace {
@@ -78,6 +93,7 @@ void plan_free(hai_plan *p) {
         if (c.done) cudaEventDestroy(c.done);
     }
     for (void *t : p->tables) cudaFree(t);
+    cudaFree(p->d_hst);
     if (p->cap) cudaStreamDestroy(p->cap);
     if (p->fork) cudaEventDestroy(p->fork);
     delete p;
@@ -193,9 +209,116 @@ void drop_graph(hai_plan *p) {
     p->exec = nullptr;
     p->graph = nullptr;
     p->g_volt = p->g_img = nullptr;
+    p->g_hier = false;
 }
 
-hai_status capture(hai_plan *p, const int8_t *volt, float *img) {
+// ------------------------------------------------------------------ station beams
+// Eq. intra-station BF with diagonal polarisation weights, for stations of
+// any element count: block (station s, channel c, 16 samples), thread
+// (sample t, beam k) sums conj(w^p_k,a) E^p_a(t) for both pols in int32 over
+// the station's elements (exact: |sum| <= 2^15 N_e), staged through shared
+// memory 256 elements at a time; the sums are requantised as hai_beamform
+// does (|x| / 2^shift rounded half away from zero, clamped to 127) into
+// beams [S][C][T][K][2][2].
+struct HierStation {
+    long long volt_off, w_off;   // bytes into the plan's voltage buffer / the weights
+    int ne, pad;
+};
+constexpr int kBfT = 16;           // samples per block
+constexpr int kBfChunk = 256;      // elements per shared-memory pass
+constexpr int kBfWRow = kBfChunk + 1;   // padded weight row (char2): rows k fall in distinct banks
+
+__device__ __forceinline__ int bf_requant(int x, int shift, int &sat) {
+    int m = x < 0 ? -x : x;
+    if (shift > 0) m = (m + (1 << (shift - 1))) >> shift;
+    if (m > 127) {
+        m = 127;
+        sat++;
+    }
+    return x < 0 ? -m : m;
+}
+
+__global__ void __launch_bounds__(1024) plan_bf_kernel(const int8_t *__restrict__ volt, const int8_t *__restrict__ w,
+                                                       const HierStation *__restrict__ hst, int C, int T, int K,
+                                                       int shift, int8_t *__restrict__ beams,
+                                                       unsigned long long *__restrict__ n_sat) {
+    extern __shared__ char2 sb[];
+    char2 *sE = sb;                                   // [kBfT][2][kBfChunk]
+    char2 *sW = sb + kBfT * 2 * kBfChunk;             // [K][2][kBfWRow]
+    const int s = blockIdx.x, c = blockIdx.y, t0 = blockIdx.z * kBfT;
+    const HierStation h = hst[s];
+    const int ne = h.ne, nt = min(kBfT, T - t0);
+    const int t = threadIdx.x / K, k = threadIdx.x % K;
+    const char2 *E = reinterpret_cast<const char2 *>(volt + h.volt_off) + ((size_t)c * T + t0) * 2 * ne;
+    const char2 *W = reinterpret_cast<const char2 *>(w + h.w_off);
+    int xr = 0, xi = 0, yr = 0, yi = 0;
+    for (int a0 = 0; a0 < ne; a0 += kBfChunk) {
+        const int cn = min(kBfChunk, ne - a0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nt * 2 * cn; i += blockDim.x) {
+            const int a = i % cn, row = i / cn;       // row = (sample, pol)
+            sE[row * kBfChunk + a] = E[(size_t)row * ne + a0 + a];
+        }
+        for (int i = threadIdx.x; i < K * 2 * cn; i += blockDim.x) {
+            const int a = i % cn, row = i / cn;       // row = (beam, pol)
+            sW[row * kBfWRow + a] = W[(size_t)row * ne + a0 + a];
+        }
+        __syncthreads();
+        if (t < nt) {
+            const char2 *ex = sE + (2 * t) * kBfChunk, *ey = ex + kBfChunk;
+            const char2 *wx = sW + (2 * k) * kBfWRow, *wy = wx + kBfWRow;
+            for (int a = 0; a < cn; a++) {
+                const char2 e0 = ex[a], e1 = ey[a], g0 = wx[a], g1 = wy[a];
+                xr += g0.x * e0.x + g0.y * e0.y;      // Re conj(w) E
+                xi += g0.x * e0.y - g0.y * e0.x;      // Im conj(w) E
+                yr += g1.x * e1.x + g1.y * e1.y;
+                yi += g1.x * e1.y - g1.y * e1.x;
+            }
+        }
+    }
+    int sat = 0;
+    if (t < nt) {
+        const int b0 = bf_requant(xr, shift, sat), b1 = bf_requant(xi, shift, sat);
+        const int b2 = bf_requant(yr, shift, sat), b3 = bf_requant(yi, shift, sat);
+        char4 v = make_char4((signed char)b0, (signed char)b1, (signed char)b2, (signed char)b3);
+        reinterpret_cast<char4 *>(beams)[(((size_t)s * C + c) * T + t0 + t) * K + k] = v;
+    }
+    if (n_sat) {
+        for (int o = 16; o > 0; o >>= 1) sat += __shfl_xor_sync(0xffffffffu, sat, o);
+        if ((threadIdx.x & 31) == 0 && sat) atomicAdd(n_sat, (unsigned long long)sat);
+    }
+}
+
+size_t bf_smem(int K) { return sizeof(char2) * ((size_t)kBfT * 2 * kBfChunk + (size_t)K * 2 * kBfWRow); }
+
+// The second level on stream st (inside the capture): beams, their
+// inter-station order, then the correlator + XFFT and/or the EPIC of every beam.
+hai_status run_second_level(hai_plan *p, const int8_t *volt, const hai_plan_hier_buffers *b, cudaStream_t st) {
+    hai_ctx *ctx = p->ctx;
+    const int S = p->S, C = p->C, T = p->T, K = p->hK;
+    if (b->n_saturated) HAI_CUDA_TRY(cudaMemsetAsync(b->n_saturated, 0, sizeof(long long), st));
+    plan_bf_kernel<<<dim3((unsigned)S, (unsigned)C, (unsigned)((T + kBfT - 1) / kBfT)), kBfT * K, bf_smem(K), st>>>(
+        volt, p->hw, static_cast<const HierStation *>(p->d_hst), C, T, K, p->hshift, b->beams,
+        reinterpret_cast<unsigned long long *>(b->n_saturated));
+    HAI_CUDA_TRY(cudaGetLastError());
+    hai_status s = hai_beams_to_corr(ctx, b->beams, S, C, T, K, 2, b->corr, st);
+    if (s != HAI_OK) return s;
+    if (p->hx) {
+        s = hai_correlate(ctx, b->corr, K * C, T, S, 2, b->vis, 0, st);
+        if (s == HAI_OK) s = hai_xfft_station_image(ctx, p->hx, b->vis, C, b->xfft_img, st);
+        if (s != HAI_OK) return s;
+    }
+    const size_t beam_block = (size_t)C * T * 2 * S * 2;
+    for (int k = 0; k < (int)p->he.size(); k++) {
+        const hai_layout *L = p->he[k];
+        s = hai_epic_image(ctx, L, b->corr + (size_t)k * beam_block, C, T, p->hprec,
+                           b->epic_img + (size_t)k * C * 4 * L->grid_n * L->grid_n, 0, st);
+        if (s != HAI_OK) return s;
+    }
+    return HAI_OK;
+}
+
+hai_status capture(hai_plan *p, const int8_t *volt, float *img, const hai_plan_hier_buffers *hb) {
     drop_graph(p);
     hai_ctx *ctx = p->ctx;
     HAI_CUDA_TRY(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
@@ -209,6 +332,7 @@ hai_status capture(hai_plan *p, const int8_t *volt, float *img) {
         if (e == cudaSuccess && s == HAI_OK) e = cudaEventRecord(c.done, c.stream);
         if (e == cudaSuccess && s == HAI_OK) e = cudaStreamWaitEvent(p->cap, c.done, 0);
     }
+    if (hb && e == cudaSuccess && s == HAI_OK) s = run_second_level(p, volt, hb, p->cap);
     ctx->capturing = 0;
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(p->cap, &g);
@@ -225,6 +349,8 @@ hai_status capture(hai_plan *p, const int8_t *volt, float *img) {
     HAI_CUDA_TRY(cudaGraphInstantiate(&p->exec, g, 0));
     p->g_volt = volt;
     p->g_img = img;
+    p->g_hier = hb != nullptr;
+    if (hb) p->gb = *hb;
     return HAI_OK;
 }
 
@@ -363,8 +489,8 @@ extern "C" hai_status hai_plan_run(hai_plan *p, const int8_t *volt, float *img, 
         return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_run: buffers must be 16-byte aligned");
     if (hai_fault_injected("launch")) return hai_fail(HAI_ERR_CUDA, "hai_plan_run: injected launch failure");
     HAI_CUDA_TRY(cudaSetDevice(p->ctx->device));
-    if (!p->exec || p->g_volt != volt || p->g_img != img) {
-        const hai_status s = capture(p, volt, img);
+    if (!p->exec || p->g_volt != volt || p->g_img != img || p->g_hier) {
+        const hai_status s = capture(p, volt, img, nullptr);
         if (s != HAI_OK) return s;
     }
     const int pidx = prof_begin(p->ctx, (cudaStream_t)stream);
@@ -408,4 +534,109 @@ extern "C" hai_status hai_plan_autotune(hai_plan *p, const int8_t *volt, float *
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     return s;
+}
+
+extern "C" hai_status hai_plan_set_hierarchy(hai_plan *p, const hai_plan_hier_desc *d) {
+    if (!p || !d) return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_set_hierarchy: NULL argument");
+    const int K = d->n_beam, S = p->S;
+    if (K < 1 || K > 64 || !d->weights || !d->weight_off || d->requant_shift < 0 || d->requant_shift > 30)
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_set_hierarchy: n_beam in 1..64, weights, offsets and a "
+                                             "shift in 0..30 are needed");
+    if (!d->xfft && !d->epic)
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_set_hierarchy: no inter-station stage (xfft or epic)");
+    if (d->xfft) {
+        int vs = 0, vn = 0, vk = 0;
+        vis_layout_dims(d->xfft, &vs, &vn, &vk);
+        if (vs != S || vk != K) return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_set_hierarchy: the XFFT layout needs "
+                                                                     "the plan's S stations and n_beam directions");
+    }
+    if (d->epic) {
+        for (int k = 0; k < K; k++) {
+            const hai_layout *L = d->epic[k];
+            if (!L || L->ctx != p->ctx || L->n_elem != S || L->n_pol != 2)
+                return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_set_hierarchy: EPIC layout " + std::to_string(k) +
+                                                         " must have the plan's S stations as elements and 2 pols");
+        }
+        if (d->epic_prec < HAI_PREC_FP32 || d->epic_prec > HAI_PREC_BF16_SPLIT)
+            return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_set_hierarchy: EPIC precision");
+    }
+    if (2 * K * 2 * (S + 1) > 48 * 1024)
+        return hai_fail(HAI_ERR_UNSUPPORTED, "hai_plan_set_hierarchy: S x n_beam too large for the beam reorder");
+    std::vector<HierStation> hs(S);
+    for (int s = 0; s < S; s++) {
+        if (d->weight_off[s] < 0 || (d->weight_off[s] & 1))
+            return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_set_hierarchy: weight offsets must be even and >= 0");
+        hs[s].volt_off = p->volt_off[s];
+        hs[s].w_off = d->weight_off[s];
+        hs[s].ne = p->ne[s];
+        hs[s].pad = 0;
+    }
+    HAI_CUDA_TRY(cudaSetDevice(p->ctx->device));
+    if (d->xfft) {
+        const hai_status ws = hai_workspace(p->ctx);         // the correlator's operand workspace, before any capture
+        if (ws != HAI_OK) return ws;
+    }
+    HAI_CUDA_TRY(hai_allow_dyn_smem(plan_bf_kernel, p->ctx->smem_optin));
+    if (bf_smem(K) > (size_t)p->ctx->smem_optin)
+        return hai_fail(HAI_ERR_UNSUPPORTED, "hai_plan_set_hierarchy: n_beam too large for shared memory");
+    void *d_hst = nullptr;
+    HAI_CUDA_TRY(cudaMalloc(&d_hst, sizeof(HierStation) * S));
+    const cudaError_t e = cudaMemcpy(d_hst, hs.data(), sizeof(HierStation) * S, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d_hst);
+        return hai_cuda_fail(e, "hai_plan_set_hierarchy: station records");
+    }
+    cudaFree(p->d_hst);
+    p->d_hst = d_hst;
+    p->hK = K;
+    p->hshift = d->requant_shift;
+    p->hw = d->weights;
+    p->hx = d->xfft;
+    p->he.clear();
+    if (d->epic) p->he.assign(d->epic, d->epic + K);
+    p->hprec = d->epic_prec;
+    drop_graph(p);
+    return HAI_OK;
+}
+
+extern "C" hai_status hai_plan_hier_sizes(const hai_plan *p, int64_t *beam_bytes, int64_t *vis_ints,
+                                          int64_t *xfft_floats, int64_t *epic_floats) {
+    if (!p) return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_hier_sizes: NULL plan");
+    if (p->hK == 0) return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_hier_sizes: no hierarchy set");
+    const long long S = p->S, K = p->hK;
+    if (beam_bytes) *beam_bytes = S * p->C * p->T * K * 4;
+    if (vis_ints) *vis_ints = p->hx ? K * p->C * (S * (S + 1) / 2) * 8 : 0;
+    if (xfft_floats) {
+        int vs = 0, vn = 0, vk = 0;
+        if (p->hx) vis_layout_dims(p->hx, &vs, &vn, &vk);
+        *xfft_floats = p->hx ? K * p->C * 4ll * vn * vn : 0;
+    }
+    if (epic_floats) {
+        long long f = 0;
+        for (const hai_layout *L : p->he) f += (long long)p->C * 4 * L->grid_n * L->grid_n;
+        *epic_floats = p->he.empty() ? 0 : f;
+    }
+    return HAI_OK;
+}
+
+extern "C" hai_status hai_plan_run_hier(hai_plan *p, const int8_t *volt, float *img, const hai_plan_hier_buffers *b,
+                                        void *stream) {
+    if (!p || !volt || !img || !b) return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_run_hier: NULL argument");
+    if (p->hK == 0) return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_run_hier: no hierarchy set");
+    if (!b->beams || !b->corr || (p->hx && (!b->vis || !b->xfft_img)) || (!p->he.empty() && !b->epic_img))
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_run_hier: a buffer of the second level is NULL");
+    const uintptr_t al = (uintptr_t)volt | (uintptr_t)img | (uintptr_t)b->beams | (uintptr_t)b->corr |
+                         (uintptr_t)b->vis | (uintptr_t)b->xfft_img | (uintptr_t)b->epic_img;
+    if (al & 15) return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_run_hier: buffers must be 16-byte aligned");
+    if (hai_fault_injected("launch")) return hai_fail(HAI_ERR_CUDA, "hai_plan_run_hier: injected launch failure");
+    HAI_CUDA_TRY(cudaSetDevice(p->ctx->device));
+    if (!p->exec || p->g_volt != volt || p->g_img != img || !p->g_hier ||
+        memcmp(&p->gb, b, sizeof(hai_plan_hier_buffers)) != 0) {
+        const hai_status s = capture(p, volt, img, b);
+        if (s != HAI_OK) return s;
+    }
+    const int pidx = prof_begin(p->ctx, (cudaStream_t)stream);
+    HAI_CUDA_TRY(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
+    prof_end(p->ctx, pidx, (cudaStream_t)stream);
+    return HAI_OK;
 }

@@ -78,7 +78,8 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 }
 
 // Adds the 2x2 footprint with lower corner (du, dv) (window cells) to the
-// cells that fall inside this CTA's tile [tu0, tu0 + tw) x [tv0, tv0 + th).
+// cells that fall inside this CTA's tile [tu0, tu0 + tw) x [tv0, tv0 + th)
+// (tw, th: the tile's own extent; shared rows are tw apart).
 __device__ __forceinline__ void add_footprint(float *wre, float *wim, int tu0, int tv0, int tw, int th, int du, int dv,
                                               float fu, float fv, float2 g) {
     const float w[4] = {(1.f - fu) * (1.f - fv), fu * (1.f - fv), (1.f - fu) * fv, fu * fv};
@@ -141,8 +142,8 @@ __global__ void __launch_bounds__(kThreads) station_grid_kernel(
         const int u = win_u0 + tu0 + cu, v = win_v0 + tv0 + cv;
         const int x = (u + N) % N, y = (v + N) % N;
         const float sgn = ((u + v) & 1) ? -1.f : 1.f;
-        pre[(size_t)y * N + x] = sgn * wre[cv * tw + cu];
-        pim[(size_t)y * N + x] = sgn * wim[cv * tw + cu];
+        pre[(size_t)y * N + x] = sgn * wre[cv * tw_eff + cu];     // rows tw_eff apart, as add_footprint wrote them
+        pim[(size_t)y * N + x] = sgn * wim[cv * tw_eff + cu];
     }
 }
 
@@ -301,6 +302,12 @@ struct hai_vis_layout {
     float2 *d_phasor = nullptr;
     int32_t *d_tile_start = nullptr, *d_tile_pairs = nullptr;
 };
+
+void vis_layout_dims(const hai_vis_layout *L, int *S, int *N, int *K) {
+    *S = L->S;
+    *N = L->N;
+    *K = L->K;
+}
 
 static void vis_layout_free(hai_vis_layout *L) {
     if (!L) return;

@@ -50,6 +50,17 @@ class _VisLayoutDesc(ctypes.Structure):
                 ("n_dir", ctypes.c_int), ("dir", ctypes.c_void_p)]
 
 
+class _PlanHierDesc(ctypes.Structure):
+    _fields_ = [("n_beam", ctypes.c_int), ("weights", ctypes.c_void_p), ("weight_off", ctypes.c_void_p),
+                ("requant_shift", ctypes.c_int), ("xfft", ctypes.c_void_p), ("epic", ctypes.c_void_p),
+                ("epic_prec", ctypes.c_int)]
+
+
+class _PlanHierBuffers(ctypes.Structure):
+    _fields_ = [("beams", ctypes.c_void_p), ("corr", ctypes.c_void_p), ("vis", ctypes.c_void_p),
+                ("xfft_img", ctypes.c_void_p), ("epic_img", ctypes.c_void_p), ("n_saturated", ctypes.c_void_p)]
+
+
 _lib = None
 _lock = threading.Lock()
 _vp = ctypes.c_void_p
@@ -84,6 +95,9 @@ def _declare(L):
     L.hai_plan_run.argtypes = [_vp, _vp, _vp, _vp]
     L.hai_plan_autotune.argtypes = [_vp, _vp, _vp, _int, _vp]
     L.hai_plan_schedule.argtypes = [_vp, ctypes.POINTER(_int), _vp, _vp, _vp]
+    L.hai_plan_set_hierarchy.argtypes = [_vp, ctypes.POINTER(_PlanHierDesc)]
+    L.hai_plan_hier_sizes.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_int64)] * 4
+    L.hai_plan_run_hier.argtypes = [_vp, _vp, _vp, ctypes.POINTER(_PlanHierBuffers), _vp]
     L.hai_beams_to_corr.argtypes = [_vp, _vp, _int, _int, _int, _int, _int, _vp, _vp]
     L.hai_vis_layout_create.argtypes = [_vp, ctypes.POINTER(_VisLayoutDesc), ctypes.POINTER(_vp)]
     L.hai_vis_layout_destroy.argtypes = [_vp]
@@ -433,6 +447,52 @@ def hai_plan_schedule(plan: Plan):
     m = (ctypes.c_double * 3)()
     _check(load().hai_plan_schedule(plan.handle, ctypes.byref(n), g, c, m), "hai_plan_schedule")
     return [(g[k], c[k], m[k]) for k in range(n.value)]
+
+
+def hai_plan_set_hierarchy(plan: Plan, n_beam: int, weights, weight_off, requant_shift: int, xfft=None,
+                           epic=None, epic_prec: int = HAI_PREC_FP16):
+    """Attach the second level: station beams (weights: device int8 holding
+    station s's [K][2][N_e,s][2] at byte weight_off[s]) imaged by the
+    inter-station XFFT (a VisLayout) and/or EPIC (K Layouts).  The plan keeps
+    references to the weights and layouts."""
+    import torch
+    if not (isinstance(weights, torch.Tensor) and weights.is_cuda and weights.dtype == torch.int8):
+        raise ValueError("weights must be a CUDA int8 tensor")
+    off = np.ascontiguousarray(weight_off, np.int64)
+    if off.shape != (plan.S,):
+        raise ValueError("weight_off must hold one offset per station")
+    arr = None
+    if epic is not None:
+        if len(epic) != n_beam:
+            raise ValueError("one EPIC layout per beam")
+        arr = (_vp * n_beam)(*[ly.handle for ly in epic])
+    desc = _PlanHierDesc(n_beam, weights.data_ptr(), off.ctypes.data, requant_shift,
+                         None if xfft is None else xfft.handle, None if arr is None else ctypes.addressof(arr),
+                         epic_prec)
+    _check(load().hai_plan_set_hierarchy(plan.handle, ctypes.byref(desc)), "hai_plan_set_hierarchy")
+    plan.hier = (n_beam, weights, off, xfft, list(epic) if epic is not None else None)   # keep them alive
+
+
+def hai_plan_hier_sizes(plan: Plan):
+    """(beam bytes, visibility int32s, XFFT image floats, EPIC image floats)."""
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(load().hai_plan_hier_sizes(plan.handle, *[ctypes.byref(x) for x in v]), "hai_plan_hier_sizes")
+    return tuple(x.value for x in v)
+
+
+def hai_plan_run_hier(plan: Plan, volt, img, beams, corr, vis=None, xfft_img=None, epic_img=None,
+                      n_saturated=None, stream=None):
+    import torch
+    nb, nv, nx, ne = hai_plan_hier_sizes(plan)
+    bufs = _PlanHierBuffers(
+        _dev_ptr(beams, torch.int8, "beams", nb), _dev_ptr(corr, torch.int8, "corr", nb),
+        _dev_ptr(vis, torch.int32, "vis", nv) if vis is not None else None,
+        _dev_ptr(xfft_img, torch.float32, "xfft_img", nx) if xfft_img is not None else None,
+        _dev_ptr(epic_img, torch.float32, "epic_img", ne) if epic_img is not None else None,
+        _dev_ptr(n_saturated, torch.int64, "n_saturated", 1) if n_saturated is not None else None)
+    vp = _dev_ptr(volt, torch.int8, "volt", plan.volt_bytes)
+    ip = _dev_ptr(img, torch.float32, "img", plan.img_floats)
+    _check(load().hai_plan_run_hier(plan.handle, vp, ip, ctypes.byref(bufs), _stream(stream)), "hai_plan_run_hier")
 
 
 # ------------------------------------------------------------------ inter-station stage

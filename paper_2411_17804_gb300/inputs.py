@@ -105,6 +105,15 @@ class UnevenConfig:
     cell_lambda: float = 0.5
     ksize: int = 3
     ref_diameter_m: float = 38.0   # diameter of a 256-element station
+    # second level: the stations in a compact core, K beams each, imaged
+    # between stations (XFFT on an N_A grid, EPIC on an N_E grid)
+    core_diameter_m: float = 3000.0
+    n_beam: int = 4
+    requant_shift: int = 12
+    xfft_grid_n: int = 256
+    xfft_cell_m: float = 38.0
+    epic_grid_n: int = 128
+    epic_cell_m: float = 76.0
     seed: int = SEED0 + 4
 
 
@@ -354,3 +363,27 @@ def uneven_station(cfg: UnevenConfig, index: int, n_elem: int | None = None) -> 
         min_spacing_m=1.5, lam_m=cfg.lam_m, n_chan=cfg.n_chan, n_pol=cfg.n_pol,
         n_time=cfg.n_time, grid_n=uneven_grid_side(ne, cfg), cell_lambda=cfg.cell_lambda,
         ksize=cfg.ksize, n_src=20, seed=cfg.seed * 7919 + index)
+
+
+def uneven_centres(cfg: UnevenConfig, n_station: int | None = None) -> np.ndarray:
+    """Station centres of the uneven array: a disk of the core diameter with
+    a minimum spacing of the largest station's diameter."""
+    S = cfg.n_station if n_station is None else n_station
+    rng = np.random.default_rng(cfg.seed + 17)
+    return disk_layout(S, cfg.core_diameter_m, uneven_diameter(cfg.n_max, cfg), rng)
+
+
+def uneven_beam_weights(cfg: UnevenConfig, positions, dirs: np.ndarray):
+    """Beam weights of every station (bf_weights towards dirs, both pols)
+    packed one station after another; returns (int8 buffer, byte offsets)."""
+    blocks = [bf_weights(np.asarray(pos), cfg.lam_m, dirs, 2).reshape(-1) for pos in positions]
+    off = np.zeros(len(blocks), np.int64)
+    o = 0
+    for s, b in enumerate(blocks):
+        off[s] = o
+        o += (b.size + 15) & ~15
+    buf = np.zeros(max(o, 16), np.int8)
+    for s, b in enumerate(blocks):
+        buf[off[s]:off[s] + b.size] = b
+    return buf, off
+

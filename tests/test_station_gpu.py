@@ -56,8 +56,10 @@ def station_case(S, n, cell, seed, tail=0):
     return pos
 
 
-@pytest.mark.parametrize("S,K,C,n,tail", [(12, 2, 3, 32, 0), (30, 3, 2, 64, 4), (9, 1, 1, 16, 2)])
+@pytest.mark.parametrize("S,K,C,n,tail", [(12, 2, 3, 32, 0), (30, 3, 2, 64, 4), (9, 1, 1, 16, 2), (40, 2, 2, 256, 0)])
 def test_station_xfft_matches_oracle(hai, ctx, S, K, C, n, tail):
+    """The last case's uv window (~200 cells) takes two gridding tiles per
+    axis, the last one narrower than the first."""
     cell, lam = 19.0, 3.0
     pos = station_case(S, n, cell, S * n, tail)
     dirs = np.random.default_rng(K).uniform(-0.1, 0.1, (K, 2))
