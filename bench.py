@@ -480,6 +480,8 @@ def plan_component(hai, ctx, flush, peaks, steps):
         ih.copy_(img, non_blocking=True)
     torch.cuda.synchronize()
     e_ms = (time.perf_counter() - e0) * 1e3 / 3
+    hier = plan_hierarchy(hai, ctx, plan, cfg, volt, img, flush, steps, ms,
+                          sum(n * n for n in grids) * C * 2 * T)
     out = {"workload": cfg.name, "stations": cfg.n_station, "channels": C, "samples": T,
            "grid_classes": {str(n): grids.count(n) for n in sorted(set(grids))},
            "ms": ms, "units_per_s": units / (ms * 1e-3), "unit": UNIT,
@@ -489,10 +491,72 @@ def plan_component(hai, ctx, flush, peaks, steps):
            "roofline": {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                         "peak_source": "of measured bf16_tflops (fp16 nominal ratio 1)"},
            "e2e": {"value": units / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(volt.numel()),
-                   "d2h_bytes_per_step": int(img.numel() * 4)}}
+                   "d2h_bytes_per_step": int(img.numel() * 4)},
+           "hierarchy": hier}
     hai.hai_plan_destroy(plan)
     del volt, img, vh, ih
     return out
+
+
+def plan_hierarchy(hai, ctx, plan, cfg, volt, img, flush, steps, plan_ms, units):
+    """The second level in the same graph launch: K beams per station
+    (int8 weights towards a 2 x 2 lattice of directions), then the
+    inter-station correlator + XFFT (256^2, 38 m cells) and the inter-station
+    EPIC (128^2, 76 m cells, FP16) of every beam, for the 512 stations in a
+    3 km core."""
+    import torch
+    from paper_2411_17804_gb300 import inputs as I
+    K, S = cfg.n_beam, cfg.n_station
+    pos = [I.station_layout(I.uneven_station(cfg, i)) for i in range(S)]
+    dirs = I.beam_directions(K, cfg.lam_m, cfg.ref_diameter_m)
+    wbuf, woff = I.uneven_beam_weights(cfg, pos, dirs)
+    centres = I.uneven_centres(cfg)
+    vl = hai.hai_vis_layout_create(ctx, centres, cfg.lam_m, cfg.xfft_cell_m, cfg.xfft_grid_n, dirs)
+    el = [hai.hai_station_epic_layout_create(ctx, centres, cfg.lam_m, cfg.epic_cell_m, cfg.epic_grid_n, dirs, k)[0]
+          for k in range(K)]
+    w = torch.from_numpy(wbuf).cuda()
+    hai.hai_plan_set_hierarchy(plan, K, w, woff, cfg.requant_shift, xfft=vl, epic=el, epic_prec=hai.HAI_PREC_FP16)
+    nb, nv, nx, ne = hai.hai_plan_hier_sizes(plan)
+    beams = torch.empty(nb, dtype=torch.int8, device="cuda")
+    corr = torch.empty(nb, dtype=torch.int8, device="cuda")
+    vis = torch.empty(nv, dtype=torch.int32, device="cuda")
+    ximg = torch.empty(nx, device="cuda")
+    eimg = torch.empty(ne, device="cuda")
+    nsat = torch.zeros(1, dtype=torch.int64, device="cuda")
+    run = lambda st: hai.hai_plan_run_hier(plan, volt, img, beams, corr, vis, ximg, eimg, nsat, st)
+    ms = time_call(run, steps, 3, flush)
+    # end to end: pinned voltages in; station images and both inter-station images out
+    vh = torch.empty(volt.shape, dtype=torch.int8).pin_memory()
+    outs = [(img, torch.empty(img.shape, dtype=torch.float32).pin_memory()),
+            (ximg, torch.empty(ximg.shape, dtype=torch.float32).pin_memory()),
+            (eimg, torch.empty(eimg.shape, dtype=torch.float32).pin_memory())]
+    st = torch.cuda.current_stream()
+
+    def cadence():
+        volt.copy_(vh, non_blocking=True)
+        run(st)
+        for d, h in outs:
+            h.copy_(d, non_blocking=True)
+    for _ in range(2):
+        cadence()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(3):
+        cadence()
+    torch.cuda.synchronize()
+    e_ms = (time.perf_counter() - e0) * 1e3 / 3
+    res = {"what": "station EPIC images + station beams -> inter-station correlator + XFFT and EPIC, one graph",
+           "beams": K, "requant_shift": cfg.requant_shift, "ms": ms, "second_level_ms": ms - plan_ms,
+           "xfft_grid": cfg.xfft_grid_n, "epic_grid": cfg.epic_grid_n, "epic_prec": "fp16",
+           "saturated_beam_components": int(nsat.item()),
+           "e2e": {"value": units / (e_ms * 1e-3), "unit": UNIT, "ms": e_ms,
+                   "h2d_bytes_per_step": int(volt.numel()),
+                   "d2h_bytes_per_step": int(sum(d.numel() * 4 for d, _ in outs))}}
+    del beams, corr, vis, ximg, eimg, vh, outs
+    hai.hai_vis_layout_destroy(vl)
+    for ly in el:
+        hai.hai_layout_destroy(ly)
+    return res
 
 
 def fft_correlator_component(hai, ctx, img, C, n, P, flush, peaks):
