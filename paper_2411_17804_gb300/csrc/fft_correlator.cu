@@ -16,8 +16,12 @@
 //   columns: one CTA per (channel, product, 16 columns), one warp per
 //            column: FFT along y, times (-1)^(dx+dy) / N^2, written back; the
 //            XY CTA also writes YX[-d] = conj(XY[d]) (I_YX = conj(I_XY)).
+// N = 512 keeps each line in registers instead: 64 threads per line, three
+// radix-8 passes and two shared-memory exchanges (fft512.cuh), the inverse
+// transform taken as conj(FFT(conj(x))); 8 lines per CTA in both passes.
 #include <algorithm>
 
+#include "fft512.cuh"
 #include "hai_internal.h"
 
 namespace {
@@ -125,6 +129,90 @@ __global__ void __launch_bounds__(kThreads) fc_cols_kernel(int N, int log2n, int
     }
 }
 
+// N = 512, rows: CTA = 8 rows of one (channel, product), thread (r, tau).
+__global__ void __launch_bounds__(512) fc512_rows_kernel(const float *__restrict__ img, int P,
+                                                         float2 *__restrict__ out) {
+    constexpr int N = 512;
+    extern __shared__ float2 sm[];
+    float2 *tw = sm;                                          // [kTwFloat2]
+    float2 *bufs = sm + hai_fft512::kTwFloat2;                // [8][kFftBuf]
+    hai_fft512::fill_fft512_tables(tw);
+    const int r = threadIdx.x >> 6, tau = threadIdx.x & 63;
+    const int np = (P == 2) ? 3 : 1, Q = (P == 2) ? 4 : 1;
+    const int c = blockIdx.x / np, pr = blockIdx.x % np;
+    const int y = blockIdx.y * 8 + r;
+    const size_t NN = (size_t)N * N;
+    const float *re = img + ((size_t)c * Q + (pr == 2 ? 2 : pr)) * NN + (size_t)y * N;
+    float2 a[8];
+#pragma unroll
+    for (int m = 0; m < 8; m++)                               // conj of the input: exponent -
+        a[m] = make_float2(__ldg(re + tau + 64 * m), pr == 2 ? -__ldg(re + NN + tau + 64 * m) : 0.f);
+    __syncthreads();
+    hai_fft512::fft512<false>(a, tau, bufs + r * hai_fft512::kFftBuf, tw, [] { __syncthreads(); });
+    float2 *dst = out + ((size_t)c * P * P + out_plane(pr, P)) * NN + (size_t)y * N;
+#pragma unroll
+    for (int j = 0; j < 8; j++) dst[tau + 64 * j] = make_float2(a[j].x, -a[j].y);
+}
+
+// N = 512, columns: CTA = 8 adjacent columns of one (channel, product).  The
+// columns move between HBM and the registers through a shared tile [8][kTs]
+// (which shares its memory with the exchange buffers): loads and stores of
+// whole 64-byte row segments (a warp: 4 rows x 8 columns), and tile reads and
+// writes of one column's rows by consecutive threads, both free of bank
+// conflicts (kTs = 514: columns 4 banks apart).  Thread (col, tau) transforms
+// its column; times (-1)^(dx+dy) / N^2; the XY CTA also writes the YX mirror.
+constexpr int kTs = 514;
+
+__global__ void __launch_bounds__(512) fc512_cols_kernel(int P, float2 *__restrict__ out) {
+    constexpr int N = 512;
+    extern __shared__ float2 sm[];
+    float2 *tw = sm;
+    float2 *bufs = sm + hai_fft512::kTwFloat2;                // exchange buffers, and the column tile
+    float2 *tile = bufs;
+    static_assert(8 * kTs <= 8 * hai_fft512::kFftBuf, "tile inside the exchange buffers");
+    hai_fft512::fill_fft512_tables(tw);
+    const int col = threadIdx.x >> 6, tau = threadIdx.x & 63;
+    const int lc = threadIdx.x & 7, lr = threadIdx.x >> 3;     // row-segment mapping: column, row of 64
+    const int np = (P == 2) ? 3 : 1;
+    const int c = blockIdx.x / np, pr = blockIdx.x % np;
+    const int x0 = blockIdx.y * 8;
+    const size_t NN = (size_t)N * N;
+    float2 *plane = out + ((size_t)c * P * P + out_plane(pr, P)) * NN;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const int y = lr + 64 * k;
+        tile[lc * kTs + y] = plane[(size_t)y * N + x0 + lc];
+    }
+    __syncthreads();
+    float2 a[8];
+#pragma unroll
+    for (int m = 0; m < 8; m++) {                             // conj of the input: exponent -
+        const float2 v = tile[col * kTs + tau + 64 * m];
+        a[m] = make_float2(v.x, -v.y);
+    }
+    __syncthreads();
+    hai_fft512::fft512<false>(a, tau, bufs + col * hai_fft512::kFftBuf, tw, [] { __syncthreads(); });
+    __syncthreads();                                          // exchange buffers free: the tile again
+    const float inv = 1.0f / (float)NN;
+    const int dx = x0 + col;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const int dy = tau + 64 * j;
+        const float s = ((dx + dy) & 1) ? -inv : inv;
+        tile[col * kTs + dy] = make_float2(a[j].x * s, -a[j].y * s);
+    }
+    __syncthreads();
+    float2 *mirror = (pr == 2) ? out + ((size_t)c * P * P + 2) * NN : nullptr;   // YX
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const int dy = lr + 64 * k;
+        const float2 v = tile[lc * kTs + dy];
+        plane[(size_t)dy * N + x0 + lc] = v;
+        if (mirror)
+            mirror[(size_t)((N - dy) & (N - 1)) * N + ((N - x0 - lc) & (N - 1))] = make_float2(v.x, -v.y);
+    }
+}
+
 }  // namespace
 
 extern "C" hai_status hai_fft_correlate(hai_ctx *ctx, const float *img, int C, int N, int P, float *grid,
@@ -147,6 +235,18 @@ extern "C" hai_status hai_fft_correlate(hai_ctx *ctx, const float *img, int C, i
     HAI_CUDA_TRY(hai_allow_dyn_smem(fc_rows_kernel, ctx->smem_optin));
     HAI_CUDA_TRY(hai_allow_dyn_smem(fc_cols_kernel, ctx->smem_optin));
     float2 *out = reinterpret_cast<float2 *>(grid);
+    if (N == 512) {
+        const size_t smem512 = sizeof(float2) * (hai_fft512::kTwFloat2 + 8 * (size_t)hai_fft512::kFftBuf);
+        HAI_CUDA_TRY(hai_allow_dyn_smem(fc512_rows_kernel, ctx->smem_optin));
+        HAI_CUDA_TRY(hai_allow_dyn_smem(fc512_cols_kernel, ctx->smem_optin));
+        const int pidx = prof_begin(ctx, st);
+        fc512_rows_kernel<<<dim3(C * np, N / 8), 512, smem512, st>>>(img, P, out);
+        fc512_cols_kernel<<<dim3(C * np, N / 8), 512, smem512, st>>>(P, out);
+        prof_end(ctx, pidx, st);
+        prof_count(ctx, 2);
+        HAI_CUDA_TRY(cudaGetLastError());
+        return HAI_OK;
+    }
     const int pidx = prof_begin(ctx, st);
     fc_rows_kernel<<<dim3(C * np, (N + kThreads / 32 - 1) / (kThreads / 32)), kThreads, smem, st>>>(img, N, log2n,
                                                                                                      P, out);

@@ -53,7 +53,7 @@ def epic(hai, ctx, anchors, taps, n, volt, prec):
     return img
 
 
-@pytest.mark.parametrize("N,P,C", [(16, 2, 3), (32, 1, 2), (64, 2, 2), (128, 2, 1), (256, 1, 2), (512, 2, 1)])
+@pytest.mark.parametrize("N,P,C", [(16, 2, 3), (32, 1, 2), (64, 2, 2), (128, 2, 1), (256, 1, 2), (512, 2, 1), (512, 1, 2)])
 def test_inverse_transform_matches_oracle(hai, ctx, N, P, C):
     Q = 4 if P == 2 else 1
     planes = torch.from_numpy(np.random.default_rng(N + P).standard_normal((C, Q, N, N)).astype(np.float32))
