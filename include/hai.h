@@ -327,9 +327,11 @@ typedef struct {
     const hai_layout *const *epic;  /* host array of K layouts (S elements, 2 pols); or NULL */
     hai_precision epic_prec;        /* precision of the inter-station EPIC */
 } hai_plan_hier_desc;
-/* The plan keeps the weights pointer and the layouts (not copies): they must
- * outlive the plan or the next hai_plan_set_hierarchy.  At least one of xfft
- * and epic; HAI_ERR_UNSUPPORTED if 4 K (S + 1) bytes exceed 48 KB. */
+/* The plan re-packs the weights into its own device memory (the caller's
+ * buffer may be freed after the call, which synchronises the device) and
+ * keeps the layouts (not copies): they must outlive the plan or the next
+ * hai_plan_set_hierarchy.  At least one of xfft and epic;
+ * HAI_ERR_UNSUPPORTED if 4 K (S + 1) bytes exceed 48 KB. */
 hai_status hai_plan_set_hierarchy(hai_plan *plan, const hai_plan_hier_desc *desc);
 
 /* Sizes of the second level's buffers (host outputs, NULL for any not

@@ -70,8 +70,8 @@ struct hai_plan {
     const void *g_volt = nullptr, *g_img = nullptr;
     // second level
     int hK = 0, hshift = 0;
-    const int8_t *hw = nullptr;                  // caller's weights (device)
     void *d_hst = nullptr;                       // per station: voltage and weight offsets, elements
+    void *d_pw = nullptr;                        // the weights re-packed for the integer dot products
     const hai_vis_layout *hx = nullptr;          // inter-station XFFT (or NULL)
     std::vector<const hai_layout *> he;          // inter-station EPIC layouts, one per beam (or none)
     hai_precision hprec = HAI_PREC_FP16;
@@ -94,6 +94,7 @@ void plan_free(hai_plan *p) {
     }
     for (void *t : p->tables) cudaFree(t);
     cudaFree(p->d_hst);
+    cudaFree(p->d_pw);
     if (p->cap) cudaStreamDestroy(p->cap);
     if (p->fork) cudaEventDestroy(p->fork);
     delete p;
@@ -214,19 +215,47 @@ void drop_graph(hai_plan *p) {
 
 // ------------------------------------------------------------------ station beams
 // Eq. intra-station BF with diagonal polarisation weights, for stations of
-// any element count: block (station s, channel c, 16 samples), thread
-// (sample t, beam k) sums conj(w^p_k,a) E^p_a(t) for both pols in int32 over
-// the station's elements (exact: |sum| <= 2^15 N_e), staged through shared
-// memory 256 elements at a time; the sums are requantised as hai_beamform
-// does (|x| / 2^shift rounded half away from zero, clamped to 127) into
-// beams [S][C][T][K][2][2].
+// any element count, in exact integer dot products:
+//   Re conj(w) E = w.re E.re + w.im E.im  -> __dp4a over two elements' (re, im)
+//   Im conj(w) E = w.re E.im - w.im E.re  -> __dp2a of (w.re, -w.im) as int16
+//                                            with (E.im, E.re)
+// The weights are re-packed once (hai_plan_set_hierarchy) into both forms:
+// per station WP[k][p][pair] (4 int8: two elements' re, im) then
+// WQ[k][p][element] (2 int16: re, -im), odd element counts padded with a zero
+// element.  Block (station s, channel c, 32 samples), thread (sample t, beam
+// pair kp): the two beams' sums of both pols in int32 (exact: |sum| <= 2^15
+// N_e), the voltages staged through shared memory 128 elements at a time;
+// the sums are requantised as hai_beamform does (|x| / 2^shift rounded half
+// away from zero, clamped to 127) into beams [S][C][T][K][2][2].
 struct HierStation {
-    long long volt_off, w_off;   // bytes into the plan's voltage buffer / the weights
-    int ne, pad;
+    long long volt_off, w_off;   // bytes into the plan's voltage buffer / the caller's weights
+    long long pw_off;            // 32-bit words into the packed weights
+    int ne, ne2;                 // elements, element pairs
 };
-constexpr int kBfT = 16;           // samples per block
-constexpr int kBfChunk = 256;      // elements per shared-memory pass
-constexpr int kBfWRow = kBfChunk + 1;   // padded weight row (char2): rows k fall in distinct banks
+constexpr int kBfT = 32;                 // samples per block
+constexpr int kBfPairs = 64;             // element pairs per shared-memory pass
+constexpr int kBfERow = kBfPairs + 1;    // words per staged (sample, pol) row: rows t fall in distinct banks
+constexpr int kBfWRow = kBfPairs + 1;    // words per staged WP row
+constexpr int kBfQRow = 2 * kBfPairs + 2;   // words per staged WQ row (8-byte aligned, rows 4 banks apart)
+
+__global__ void plan_bf_pack_kernel(const int8_t *__restrict__ w, const HierStation *__restrict__ hst, int K,
+                                    uint32_t *__restrict__ pw) {
+    const HierStation h = hst[blockIdx.x];
+    const char2 *W = reinterpret_cast<const char2 *>(w + h.w_off);      // [K][2][ne]
+    uint32_t *wp = pw + h.pw_off, *wq = wp + (size_t)K * 2 * h.ne2;
+    for (int i = threadIdx.x; i < K * 2 * h.ne2; i += blockDim.x) {
+        const int row = i / h.ne2, j = i % h.ne2, a = 2 * j;
+        const char2 g0 = W[(size_t)row * h.ne + a];
+        const char2 g1 = a + 1 < h.ne ? W[(size_t)row * h.ne + a + 1] : make_char2(0, 0);
+        wp[i] = (uint32_t)(uint8_t)g0.x | ((uint32_t)(uint8_t)g0.y << 8) | ((uint32_t)(uint8_t)g1.x << 16) |
+                ((uint32_t)(uint8_t)g1.y << 24);
+    }
+    for (int i = threadIdx.x; i < K * 2 * 2 * h.ne2; i += blockDim.x) {
+        const int row = i / (2 * h.ne2), a = i % (2 * h.ne2);
+        const char2 g = a < h.ne ? W[(size_t)row * h.ne + a] : make_char2(0, 0);
+        wq[i] = (uint32_t)(uint16_t)(int16_t)g.x | ((uint32_t)(uint16_t)(int16_t)(-(int)g.y) << 16);
+    }
+}
 
 __device__ __forceinline__ int bf_requant(int x, int shift, int &sat) {
     int m = x < 0 ? -x : x;
@@ -238,50 +267,75 @@ __device__ __forceinline__ int bf_requant(int x, int shift, int &sat) {
     return x < 0 ? -m : m;
 }
 
-__global__ void __launch_bounds__(1024) plan_bf_kernel(const int8_t *__restrict__ volt, const int8_t *__restrict__ w,
+__global__ void __launch_bounds__(1024) plan_bf_kernel(const int8_t *__restrict__ volt,
+                                                       const uint32_t *__restrict__ pw,
                                                        const HierStation *__restrict__ hst, int C, int T, int K,
                                                        int shift, int8_t *__restrict__ beams,
                                                        unsigned long long *__restrict__ n_sat) {
-    extern __shared__ char2 sb[];
-    char2 *sE = sb;                                   // [kBfT][2][kBfChunk]
-    char2 *sW = sb + kBfT * 2 * kBfChunk;             // [K][2][kBfWRow]
+    extern __shared__ uint32_t sbw[];
+    const int KP = (K + 1) / 2;
+    uint32_t *sE = sbw;                                   // [kBfT][2][kBfERow]
+    uint32_t *sP = sE + kBfT * 2 * kBfERow;               // [2 KP][2][kBfWRow] (a padded odd beam reads zeros)
+    uint32_t *sQ = sP + 2 * KP * 2 * kBfWRow;             // [2 KP][2][kBfQRow]
     const int s = blockIdx.x, c = blockIdx.y, t0 = blockIdx.z * kBfT;
     const HierStation h = hst[s];
-    const int ne = h.ne, nt = min(kBfT, T - t0);
-    const int t = threadIdx.x / K, k = threadIdx.x % K;
+    const int ne = h.ne, ne2 = h.ne2, nt = min(kBfT, T - t0);
+    const int t = threadIdx.x / KP, kp = threadIdx.x % KP;
     const char2 *E = reinterpret_cast<const char2 *>(volt + h.volt_off) + ((size_t)c * T + t0) * 2 * ne;
-    const char2 *W = reinterpret_cast<const char2 *>(w + h.w_off);
-    int xr = 0, xi = 0, yr = 0, yi = 0;
-    for (int a0 = 0; a0 < ne; a0 += kBfChunk) {
-        const int cn = min(kBfChunk, ne - a0);
+    const uint32_t *WP = pw + h.pw_off, *WQ = WP + (size_t)K * 2 * ne2;
+    for (int i = threadIdx.x; i < 2 * KP * 2 * (kBfWRow + kBfQRow); i += blockDim.x) sP[i] = 0u;   // beam K (odd K)
+    int acc[2][2][2] = {};                                // [beam of the pair][pol][re, im]
+    for (int j0 = 0; j0 < ne2; j0 += kBfPairs) {
+        const int np = min(kBfPairs, ne2 - j0);
         __syncthreads();
-        for (int i = threadIdx.x; i < nt * 2 * cn; i += blockDim.x) {
-            const int a = i % cn, row = i / cn;       // row = (sample, pol)
-            sE[row * kBfChunk + a] = E[(size_t)row * ne + a0 + a];
+        for (int i = threadIdx.x; i < nt * 2 * np; i += blockDim.x) {
+            const int j = i % np, row = i / np;            // row = (sample, pol)
+            const int a = 2 * (j0 + j);
+            const char2 e0 = E[(size_t)row * ne + a];
+            const char2 e1 = a + 1 < ne ? E[(size_t)row * ne + a + 1] : make_char2(0, 0);
+            sE[row * kBfERow + j] = (uint32_t)(uint8_t)e0.x | ((uint32_t)(uint8_t)e0.y << 8) |
+                                    ((uint32_t)(uint8_t)e1.x << 16) | ((uint32_t)(uint8_t)e1.y << 24);
         }
-        for (int i = threadIdx.x; i < K * 2 * cn; i += blockDim.x) {
-            const int a = i % cn, row = i / cn;       // row = (beam, pol)
-            sW[row * kBfWRow + a] = W[(size_t)row * ne + a0 + a];
+        for (int i = threadIdx.x; i < K * 2 * np; i += blockDim.x) {
+            const int j = i % np, row = i / np;            // row = (beam, pol)
+            sP[row * kBfWRow + j] = WP[(size_t)row * ne2 + j0 + j];
+        }
+        for (int i = threadIdx.x; i < K * 2 * 2 * np; i += blockDim.x) {
+            const int a = i % (2 * np), row = i / (2 * np);
+            sQ[row * kBfQRow + a] = WQ[(size_t)row * 2 * ne2 + 2 * j0 + a];
         }
         __syncthreads();
         if (t < nt) {
-            const char2 *ex = sE + (2 * t) * kBfChunk, *ey = ex + kBfChunk;
-            const char2 *wx = sW + (2 * k) * kBfWRow, *wy = wx + kBfWRow;
-            for (int a = 0; a < cn; a++) {
-                const char2 e0 = ex[a], e1 = ey[a], g0 = wx[a], g1 = wy[a];
-                xr += g0.x * e0.x + g0.y * e0.y;      // Re conj(w) E
-                xi += g0.x * e0.y - g0.y * e0.x;      // Im conj(w) E
-                yr += g1.x * e1.x + g1.y * e1.y;
-                yi += g1.x * e1.y - g1.y * e1.x;
+#pragma unroll 2
+            for (int j = 0; j < np; j++) {
+#pragma unroll
+                for (int pol = 0; pol < 2; pol++) {
+                    const int e = (int)sE[(2 * t + pol) * kBfERow + j];
+                    const int es = (int)__byte_perm((uint32_t)e, 0u, 0x2301);   // (im, re) of both elements
+#pragma unroll
+                    for (int b = 0; b < 2; b++) {
+                        const int row = (2 * kp + b) * 2 + pol;
+                        const int wp = (int)sP[row * kBfWRow + j];
+                        const uint2 wq = *reinterpret_cast<const uint2 *>(sQ + row * kBfQRow + 2 * j);
+                        acc[b][pol][0] = __dp4a(wp, e, acc[b][pol][0]);
+                        acc[b][pol][1] = __dp2a_lo((int)wq.x, es, acc[b][pol][1]);
+                        acc[b][pol][1] = __dp2a_hi((int)wq.y, es, acc[b][pol][1]);
+                    }
+                }
             }
         }
     }
     int sat = 0;
     if (t < nt) {
-        const int b0 = bf_requant(xr, shift, sat), b1 = bf_requant(xi, shift, sat);
-        const int b2 = bf_requant(yr, shift, sat), b3 = bf_requant(yi, shift, sat);
-        char4 v = make_char4((signed char)b0, (signed char)b1, (signed char)b2, (signed char)b3);
-        reinterpret_cast<char4 *>(beams)[(((size_t)s * C + c) * T + t0 + t) * K + k] = v;
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const int k = 2 * kp + b;
+            if (k >= K) break;
+            const int b0 = bf_requant(acc[b][0][0], shift, sat), b1 = bf_requant(acc[b][0][1], shift, sat);
+            const int b2 = bf_requant(acc[b][1][0], shift, sat), b3 = bf_requant(acc[b][1][1], shift, sat);
+            const char4 v = make_char4((signed char)b0, (signed char)b1, (signed char)b2, (signed char)b3);
+            reinterpret_cast<char4 *>(beams)[(((size_t)s * C + c) * T + t0 + t) * K + k] = v;
+        }
     }
     if (n_sat) {
         for (int o = 16; o > 0; o >>= 1) sat += __shfl_xor_sync(0xffffffffu, sat, o);
@@ -289,7 +343,10 @@ __global__ void __launch_bounds__(1024) plan_bf_kernel(const int8_t *__restrict_
     }
 }
 
-size_t bf_smem(int K) { return sizeof(char2) * ((size_t)kBfT * 2 * kBfChunk + (size_t)K * 2 * kBfWRow); }
+size_t bf_smem(int K) {
+    const int KP = (K + 1) / 2;
+    return sizeof(uint32_t) * ((size_t)kBfT * 2 * kBfERow + (size_t)2 * KP * 2 * (kBfWRow + kBfQRow));
+}
 
 // The second level on stream st (inside the capture): beams, their
 // inter-station order, then the correlator + XFFT and/or the EPIC of every beam.
@@ -297,9 +354,9 @@ hai_status run_second_level(hai_plan *p, const int8_t *volt, const hai_plan_hier
     hai_ctx *ctx = p->ctx;
     const int S = p->S, C = p->C, T = p->T, K = p->hK;
     if (b->n_saturated) HAI_CUDA_TRY(cudaMemsetAsync(b->n_saturated, 0, sizeof(long long), st));
-    plan_bf_kernel<<<dim3((unsigned)S, (unsigned)C, (unsigned)((T + kBfT - 1) / kBfT)), kBfT * K, bf_smem(K), st>>>(
-        volt, p->hw, static_cast<const HierStation *>(p->d_hst), C, T, K, p->hshift, b->beams,
-        reinterpret_cast<unsigned long long *>(b->n_saturated));
+    plan_bf_kernel<<<dim3((unsigned)S, (unsigned)C, (unsigned)((T + kBfT - 1) / kBfT)), kBfT * ((K + 1) / 2), bf_smem(K),
+                     st>>>(volt, static_cast<const uint32_t *>(p->d_pw), static_cast<const HierStation *>(p->d_hst), C,
+                           T, K, p->hshift, b->beams, reinterpret_cast<unsigned long long *>(b->n_saturated));
     HAI_CUDA_TRY(cudaGetLastError());
     hai_status s = hai_beams_to_corr(ctx, b->beams, S, C, T, K, 2, b->corr, st);
     if (s != HAI_OK) return s;
@@ -563,13 +620,16 @@ extern "C" hai_status hai_plan_set_hierarchy(hai_plan *p, const hai_plan_hier_de
     if (2 * K * 2 * (S + 1) > 48 * 1024)
         return hai_fail(HAI_ERR_UNSUPPORTED, "hai_plan_set_hierarchy: S x n_beam too large for the beam reorder");
     std::vector<HierStation> hs(S);
+    long long pw_words = 0;
     for (int s = 0; s < S; s++) {
         if (d->weight_off[s] < 0 || (d->weight_off[s] & 1))
             return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_set_hierarchy: weight offsets must be even and >= 0");
         hs[s].volt_off = p->volt_off[s];
         hs[s].w_off = d->weight_off[s];
         hs[s].ne = p->ne[s];
-        hs[s].pad = 0;
+        hs[s].ne2 = (p->ne[s] + 1) / 2;
+        hs[s].pw_off = pw_words;
+        pw_words += 3ll * K * 2 * hs[s].ne2;             // WP (K 2 ne2 words) then WQ (K 2 2 ne2)
     }
     HAI_CUDA_TRY(cudaSetDevice(p->ctx->device));
     if (d->xfft) {
@@ -579,18 +639,27 @@ extern "C" hai_status hai_plan_set_hierarchy(hai_plan *p, const hai_plan_hier_de
     HAI_CUDA_TRY(hai_allow_dyn_smem(plan_bf_kernel, p->ctx->smem_optin));
     if (bf_smem(K) > (size_t)p->ctx->smem_optin)
         return hai_fail(HAI_ERR_UNSUPPORTED, "hai_plan_set_hierarchy: n_beam too large for shared memory");
-    void *d_hst = nullptr;
-    HAI_CUDA_TRY(cudaMalloc(&d_hst, sizeof(HierStation) * S));
-    const cudaError_t e = cudaMemcpy(d_hst, hs.data(), sizeof(HierStation) * S, cudaMemcpyHostToDevice);
+    void *d_hst = nullptr, *d_pw = nullptr;
+    cudaError_t e = cudaMalloc(&d_hst, sizeof(HierStation) * S);
+    if (e == cudaSuccess) e = cudaMalloc(&d_pw, sizeof(uint32_t) * (size_t)pw_words);
+    if (e == cudaSuccess) e = cudaMemcpy(d_hst, hs.data(), sizeof(HierStation) * S, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        plan_bf_pack_kernel<<<(unsigned)S, 256>>>(d->weights, static_cast<const HierStation *>(d_hst), K,
+                                                 static_cast<uint32_t *>(d_pw));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaFree(d_hst);
-        return hai_cuda_fail(e, "hai_plan_set_hierarchy: station records");
+        cudaFree(d_pw);
+        return hai_cuda_fail(e, "hai_plan_set_hierarchy: station records and packed weights");
     }
     cudaFree(p->d_hst);
+    cudaFree(p->d_pw);
     p->d_hst = d_hst;
+    p->d_pw = d_pw;
     p->hK = K;
     p->hshift = d->requant_shift;
-    p->hw = d->weights;
     p->hx = d->xfft;
     p->he.clear();
     if (d->epic) p->he.assign(d->epic, d->epic + K);

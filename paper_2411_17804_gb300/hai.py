@@ -452,9 +452,9 @@ def hai_plan_schedule(plan: Plan):
 def hai_plan_set_hierarchy(plan: Plan, n_beam: int, weights, weight_off, requant_shift: int, xfft=None,
                            epic=None, epic_prec: int = HAI_PREC_FP16):
     """Attach the second level: station beams (weights: device int8 holding
-    station s's [K][2][N_e,s][2] at byte weight_off[s]) imaged by the
-    inter-station XFFT (a VisLayout) and/or EPIC (K Layouts).  The plan keeps
-    references to the weights and layouts."""
+    station s's [K][2][N_e,s][2] at byte weight_off[s], re-packed by the
+    plan) imaged by the inter-station XFFT (a VisLayout) and/or EPIC (K
+    Layouts).  The plan keeps references to the layouts."""
     import torch
     if not (isinstance(weights, torch.Tensor) and weights.is_cuda and weights.dtype == torch.int8):
         raise ValueError("weights must be a CUDA int8 tensor")
@@ -470,7 +470,7 @@ def hai_plan_set_hierarchy(plan: Plan, n_beam: int, weights, weight_off, requant
                          None if xfft is None else xfft.handle, None if arr is None else ctypes.addressof(arr),
                          epic_prec)
     _check(load().hai_plan_set_hierarchy(plan.handle, ctypes.byref(desc)), "hai_plan_set_hierarchy")
-    plan.hier = (n_beam, weights, off, xfft, list(epic) if epic is not None else None)   # keep them alive
+    plan.hier = (xfft, list(epic) if epic is not None else None)   # keep the layouts alive
 
 
 def hai_plan_hier_sizes(plan: Plan):
