@@ -177,3 +177,85 @@ def test_hierarchy_arguments(hai, ctx):
         assert e.value.status == 1
     finally:
         release(hai, plan, vl, el)
+
+
+def test_full_cadence_sampled(hai, ctx):
+    """The uneven array at full size in the benchmark's launch configuration
+    (512 stations, 128 channels x 64 samples, plan autotuned, 4 beams, both
+    inter-station stages; random int8 voltages made on the device): sampled
+    station images, beams of sampled stations (bit-exact), the visibilities
+    and both inter-station images of sampled (beam, channel) pairs against
+    the oracle."""
+    C, T, K = U.n_chan, U.n_time, U.n_beam
+    S = U.n_station
+    stations = [I.uneven_station(U, i) for i in range(S)]
+    pos, lays, kern = [], [], []
+    for sc in stations:
+        p, anchors, taps = station(sc)
+        pos.append(p)
+        kern.append((anchors, taps))
+        lays.append(hai.hai_layout_create(ctx, anchors, taps, sc.grid_n, 2))
+    plan = hai.hai_plan_create(ctx, lays, C, T)
+    for ly in lays:
+        hai.hai_layout_destroy(ly)
+    g = torch.Generator(device="cuda").manual_seed(12)
+    volt = torch.randint(-128, 128, (plan.volt_bytes,), dtype=torch.int8, device="cuda", generator=g)
+    img = torch.empty((plan.img_floats,), device="cuda")
+    hai.hai_plan_autotune(plan, volt, img, 2)
+    dirs = I.beam_directions(K, U.lam_m, U.ref_diameter_m)
+    wbuf, woff = I.uneven_beam_weights(U, pos, dirs)
+    centres = I.uneven_centres(U)
+    vl = hai.hai_vis_layout_create(ctx, centres, U.lam_m, U.xfft_cell_m, U.xfft_grid_n, dirs)
+    el = [hai.hai_station_epic_layout_create(ctx, centres, U.lam_m, U.epic_cell_m, U.epic_grid_n, dirs, k)[0]
+          for k in range(K)]
+    try:
+        hai.hai_plan_set_hierarchy(plan, K, torch.from_numpy(wbuf).cuda(), woff, U.requant_shift, xfft=vl, epic=el,
+                                   epic_prec=hai.HAI_PREC_FP16)
+        nb, nv, nx, ne = hai.hai_plan_hier_sizes(plan)
+        beams = torch.empty(nb, dtype=torch.int8, device="cuda")
+        corr = torch.empty(nb, dtype=torch.int8, device="cuda")
+        vis = torch.empty(nv, dtype=torch.int32, device="cuda")
+        ximg = torch.empty(nx, device="cuda")
+        eimg = torch.empty(ne, device="cuda")
+        hai.hai_plan_run_hier(plan, volt, img, beams, corr, vis, ximg, eimg)
+        hai.hai_sync(ctx)
+        v = volt.cpu().numpy()
+        # station images of sampled (station, channel) blocks
+        imgs = img.cpu().numpy()
+        for s, c in ((0, 0), (97, 127), (255, 64), (400, 3), (511, 100)):
+            sc, (anchors, taps) = stations[s], kern[s]
+            n, nel = sc.grid_n, sc.n_elem
+            blk = v[plan.volt_off[s]: plan.volt_off[s] + C * T * 2 * nel * 2].reshape(C, T, 2, nel, 2)
+            want = O.epic_image(n, anchors, taps, blk[c:c + 1])
+            got = imgs[plan.img_off[s] + c * 4 * n * n: plan.img_off[s] + (c + 1) * 4 * n * n].reshape(1, 4, n, n)
+            assert rel_err_planes(got, want).max() < REDUCED_TOL, (s, c)
+        # beams of sampled stations, every channel and sample: bit-exact
+        got_b = beams.cpu().numpy().reshape(S, C, T, K, 2, 2)
+        for s in (1, 200, 511):
+            nel = stations[s].n_elem
+            vs = v[plan.volt_off[s]: plan.volt_off[s] + C * T * 2 * nel * 2].reshape(1, C, T, 2, nel, 2)
+            ws = wbuf[woff[s]: woff[s] + K * 2 * nel * 2].reshape(1, K, 2, nel, 2)
+            q, _ = O.requant(O.beamform(vs, ws), U.requant_shift)
+            assert np.array_equal(got_b[s], q[0]), s
+        # second level for sampled (beam, channel) pairs, from the beams the plan made
+        cin_all = corr.cpu().numpy().reshape(K, C, T, 2, S, 2)
+        assert np.array_equal(cin_all, got_b.transpose(3, 1, 2, 4, 0, 5))
+        nbl = S * (S + 1) // 2
+        vis_all = vis.cpu().numpy().reshape(K, C, nbl, 2, 2, 2)
+        x_all = ximg.cpu().numpy().reshape(K, C, 4, U.xfft_grid_n, U.xfft_grid_n)
+        e_all = eimg.cpu().numpy().reshape(K, C, 4, U.epic_grid_n, U.epic_grid_n)
+        for k, c in ((0, 0), (3, 127), (1, 50)):
+            cin = cin_all[k:k + 1, c:c + 1]
+            want_v = O.correlate(cin.reshape(1, T, 2, S, 2))
+            assert np.array_equal(vis_all[k, c], want_v[0]), (k, c)
+            want_x, dropped = O.station_xfft(U.xfft_grid_n, centres, U.lam_m, U.xfft_cell_m, dirs[k:k + 1],
+                                             want_v.reshape(1, 1, nbl, 2, 2, 2))
+            assert dropped == 0
+            assert rel_err_planes(x_all[k, c][None], planes(want_x)).max() < FP32_TOL, (k, c)
+            want_e, _ = O.station_epic(U.epic_grid_n, centres, U.lam_m, U.epic_cell_m, dirs[k:k + 1], cin)
+            assert rel_err_planes(e_all[k, c][None], want_e[0]).max() < REDUCED_TOL, (k, c)
+    finally:
+        hai.hai_plan_destroy(plan)
+        hai.hai_vis_layout_destroy(vl)
+        for ly in el:
+            hai.hai_layout_destroy(ly)
