@@ -25,6 +25,7 @@
 // cancels in every product, and the (-1)^(jx+jy) phase-centre factor is an
 // output shift by N/2.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(512) large_cols_kernel(const float2 *__restric
 __global__ void __launch_bounds__(512) large512_rows_kernel(
     const int8_t *__restrict__ volt, int T, int P, int ne, int box_w, int box_h,
     const int32_t *__restrict__ cell_start, const int32_t *__restrict__ entry_elem,
-    const float2 *__restrict__ entry_w, Batch bt, float2 *__restrict__ H) {
+    const float2 *__restrict__ entry_w, const int4 *__restrict__ cell_tab, Batch bt, float2 *__restrict__ H) {
     extern __shared__ float2 sm[];
     float2 *tw = sm;                                    // [kTwFloat2]
     float2 *bufs = sm + kTwFloat2;                      // [8][kFftBuf]
@@ -197,11 +198,21 @@ __global__ void __launch_bounds__(512) large512_rows_kernel(
         float2 g = make_float2(0.f, 0.f);
         if (y < box_h && x < box_w) {
             const int cell = y * box_w + x;
-            for (int k = cell_start[cell]; k < cell_start[cell + 1]; k++) {
-                const char2 e = E[entry_elem[k]];
-                const float2 w = entry_w[k];            // conj(W~)
-                g.x = fmaf(w.x, (float)e.x, fmaf(-w.y, (float)e.y, g.x));
-                g.y = fmaf(w.x, (float)e.y, fmaf(w.y, (float)e.x, g.y));
+            if (cell_tab) {                             // one entry at most: element and weight in one load
+                const int4 d = cell_tab[cell];
+                if (d.x >= 0) {
+                    const char2 e = E[d.x];
+                    const float2 w = make_float2(__int_as_float(d.y), __int_as_float(d.z));
+                    g.x = fmaf(w.x, (float)e.x, -w.y * (float)e.y);
+                    g.y = fmaf(w.x, (float)e.y, w.y * (float)e.x);
+                }
+            } else {
+                for (int k = cell_start[cell]; k < cell_start[cell + 1]; k++) {
+                    const char2 e = E[entry_elem[k]];
+                    const float2 w = entry_w[k];        // conj(W~)
+                    g.x = fmaf(w.x, (float)e.x, fmaf(-w.y, (float)e.y, g.x));
+                    g.y = fmaf(w.x, (float)e.y, fmaf(w.y, (float)e.x, g.y));
+                }
             }
         }
         a[m] = g;
@@ -504,9 +515,39 @@ hai_status epic_large_prepare(hai_layout *L) {
             for (int t = 0; t < 8; t++) tab[r * kPr + 8 * m + t] = w512((long long)r * (t + 8 * m));
     for (int k1 = 0; k1 < 16; k1++)
         for (int t = 0; t < 8; t++) tab[4 * kPr + 8 * k1 + t] = w512(4ll * t * k1);
-    const cudaError_t e = cudaMemcpy(static_cast<uint8_t *>(L->d_large_scratch) + kHBytes, tab.data(),
-                                     sizeof(float2) * kTwq, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(static_cast<uint8_t *>(L->d_large_scratch) + kHBytes, tab.data(),
+                               sizeof(float2) * kTwq, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return hai_cuda_fail(e, "epic fp32 (large grid): twiddle tables");
+    // per-cell table of the box when no cell holds more than one gather entry
+    // (the row pass then reads element and weight in one 16-byte load)
+    const int ncell = L->box_w * L->box_h;
+    std::vector<int32_t> cstart(ncell + 1);
+    e = cudaMemcpy(cstart.data(), L->d_cell_start, sizeof(int32_t) * (ncell + 1), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return hai_cuda_fail(e, "epic fp32 (large grid): gather table");
+    for (int c = 0; c < ncell; c++)
+        if (cstart[c + 1] - cstart[c] > 1) return HAI_OK;
+    std::vector<int32_t> elem(std::max(1, L->nnz));
+    std::vector<float2> w(std::max(1, L->nnz));
+    if (L->nnz > 0) {
+        e = cudaMemcpy(elem.data(), L->d_entry_elem, sizeof(int32_t) * L->nnz, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(w.data(), L->d_entry_w, sizeof(float2) * L->nnz, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return hai_cuda_fail(e, "epic fp32 (large grid): gather table");
+    }
+    std::vector<int4> cells(std::max(1, ncell));
+    for (int c = 0; c < ncell; c++) {
+        const bool has = cstart[c + 1] > cstart[c];
+        const int k = cstart[c];
+        int32_t wx = 0, wy = 0;
+        if (has) {
+            memcpy(&wx, &w[k].x, sizeof(wx));
+            memcpy(&wy, &w[k].y, sizeof(wy));
+        }
+        cells[c] = has ? make_int4(elem[k], wx, wy, 0) : make_int4(-1, 0, 0, 0);
+    }
+    e = cudaMalloc(&L->d_large_cell, sizeof(int4) * cells.size());
+    if (e == cudaSuccess) e = cudaMemcpy(L->d_large_cell, cells.data(), sizeof(int4) * cells.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return hai_cuda_fail(e, "epic fp32 (large grid): cell table");
+    L->dev_bytes += sizeof(int4) * cells.size();
     return HAI_OK;
 }
 
@@ -554,7 +595,8 @@ hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int
                 bt.t0 = t0;
                 bt.tb = tb;
                 large512_rows_kernel<<<dim3(bt.cb * tb * P, (L->box_h + 7) / 8), 512, rs_smem, st>>>(
-                    volt, T, P, L->n_elem, L->box_w, L->box_h, L->d_cell_start, L->d_entry_elem, L->d_entry_w, bt, H);
+                    volt, T, P, L->n_elem, L->box_w, L->box_h, L->d_cell_start, L->d_entry_elem, L->d_entry_w,
+                    static_cast<const int4 *>(L->d_large_cell), bt, H);
                 const int add = (t0 > 0 || accumulate) ? 1 : 0;
                 if (L->box_h <= 128)
                     large512q_cols_kernel<<<dim3(512 / kColsQ, bt.cb), 32 * kColsQ, cq_smem, st>>>(H, L->box_h, twq, bt,

@@ -236,6 +236,7 @@ static void layout_free(hai_layout *L) {
     cudaFree(L->d_tc_tables);
     cudaFree(L->d_tc_station);
     cudaFree(L->d_large_scratch);
+    cudaFree(L->d_large_cell);
     cudaFree(L->d_big);
     cudaFree(L->d_xcell);
     cudaFree(L->d_xent);

@@ -73,6 +73,7 @@ struct hai_layout {
     // FP32 path of large grids (N >= 128): L2-resident row-transform scratch
     void *d_large_scratch = nullptr;
     size_t large_scratch_bytes = 0;
+    void *d_large_cell = nullptr;       // N = 512, at most one entry per cell: int4 {element, conj(W~)} per box cell
     void *d_tc_station = nullptr;
     // tensor-core path of large grids (N = 256, 512): DFT operands and the
     // stage scratch of one batch of (channel, sample) pairs
