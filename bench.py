@@ -305,6 +305,17 @@ def cpu_baseline(cfg, anchors, taps, volt_host, gpu_imgs=None, min_s=10.0):
     units = cfg.grid_n ** 2 * n_chan * cfg.n_pol * T * reps
     out = {"value": units / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
            "sample": f"{n_chan} of {cfg.n_chan} channels x all {T} samples of the cadence, x {reps} ({dt:.1f} s)"}
+    # the same oracle on one core, over the first 128 samples of the first channel
+    all_threads = O.num_threads()
+    O.set_threads(1)
+    try:
+        t1 = time.perf_counter()
+        O.epic_image(cfg.grid_n, anchors, taps, volt_host[:1, :128])
+        d1 = time.perf_counter() - t1
+    finally:
+        O.set_threads(all_threads)
+    out["one_core"] = {"value": cfg.grid_n ** 2 * cfg.n_pol * min(T, 128) / d1, "unit": UNIT, "cores": 1,
+                       "sample": f"1 channel x {min(T, 128)} samples ({d1:.1f} s)"}
     errs = {k: image_error(v, want) for k, v in (gpu_imgs or {}).items()}
     return out, errs
 

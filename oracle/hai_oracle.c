@@ -63,6 +63,18 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the following parallel regions (timing on one core); n <= 0
+ * leaves the count unchanged.  Returns the count in force. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------------- */
 /* FFT: textbook iterative radix-2 Cooley-Tukey, X[k] = sum_n x[n] e^{+2 pi i nk/n} */
 /* ------------------------------------------------------------------------- */

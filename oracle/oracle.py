@@ -47,6 +47,8 @@ def lib():
             L = ctypes.CDLL(build())
             c_int, c_long = ctypes.c_int, ctypes.c_long
             L.orc_num_threads.restype = c_int
+            L.orc_set_threads.argtypes = [c_int]
+            L.orc_set_threads.restype = c_int
             L.orc_fft1d.argtypes = [c_int, _f64p, _f64p, c_long]
             L.orc_fft2d.argtypes = [c_int, _f64p, _f64p]
             L.orc_grid.argtypes = [c_int, c_int, c_int, _i32p, _f32p, _i8p, _f64p, _f64p]
@@ -79,6 +81,12 @@ def lib():
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's later calls (n <= 0: unchanged);
+    returns the count in force."""
+    return lib().orc_set_threads(n)
 
 
 def _check(rc: int, what: str):
