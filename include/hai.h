@@ -372,7 +372,8 @@ hai_status hai_plan_run_hier(hai_plan *plan, const int8_t *volt, float *img, con
  * FP32 over blocks of at most 512 samples (every partial sum is an integer
  * below 2^24) and the blocks in int32.  V^{qp}_{ba} = conj(V^{pq}_{ab}) gives
  * the upper triangle.  HAI_ERR_OVERFLOW_RISK if T > 65535 (|V| could exceed
- * 2^31 - 1); HAI_ERR_UNSUPPORTED if N > 65535.  vis must be 8-byte aligned.
+ * 2^31 - 1); HAI_ERR_UNSUPPORTED if N > 65535.  vis must be 8-byte aligned and volt
+ * 2-byte aligned (one complex int8 value).
  * The fp16 operands are staged in the context's 512 MB workspace (allocated
  * by the first call), so calls on one context must not run concurrently on
  * different streams. */

@@ -343,6 +343,7 @@ extern "C" hai_status hai_correlate(hai_ctx *ctx, const int8_t *volt, int C, int
         return HAI_OK;
     }
     if (((uintptr_t)vis) & 7) return hai_fail(HAI_ERR_INVALID_ARG, "hai_correlate: vis must be 8-byte aligned");
+    if (((uintptr_t)volt) & 1) return hai_fail(HAI_ERR_INVALID_ARG, "hai_correlate: volt must be 2-byte aligned");
     const hai_status wst = hai_workspace(ctx);
     if (wst != HAI_OK) return wst;
     int tpc = 0;
