@@ -21,7 +21,9 @@
  *     launched and hai_last_error() returns a message (thread-local).
  *   - Data buffers are owned by the caller and are DEVICE pointers (for
  *     example torch tensors' data_ptr()) on the context's device, unless a
- *     parameter says "host".  Opaque objects (context, layout) are owned by
+ *     parameter says "host".  Voltage buffers are at least 2-byte aligned
+ *     (one complex int8 value), float buffers 4-byte aligned; an entry point
+ *     that needs more says so (HAI_ERR_INVALID_ARG otherwise).  Opaque objects (context, layout) are owned by
  *     the library and released with their destroy function.
  *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
  *     stream.  Work is asynchronous on that stream; errors of the kernels

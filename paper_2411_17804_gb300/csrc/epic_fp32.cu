@@ -412,6 +412,8 @@ extern "C" hai_status hai_epic_image_fp32_static(int device, const hai_layout_de
     }
     if (C == 0) return HAI_OK;
     if (!img || (T > 0 && !volt)) return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image_fp32_static: NULL buffer");
+    if ((((uintptr_t)volt) & 1) || (((uintptr_t)img) & 3))
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image_fp32_static: volt must be 2-byte and img 4-byte aligned");
     HAI_CUDA_TRY(cudaSetDevice(device));
     cudaStream_t st = (cudaStream_t)stream;
     const int Q = (d->n_pol == 2) ? 4 : 1;

@@ -529,6 +529,8 @@ extern "C" hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *L, const in
         return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: unknown precision");
     if (C == 0) return HAI_OK;
     if (!img || (T > 0 && !volt)) return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: NULL buffer");
+    if ((((uintptr_t)volt) & 1) || (((uintptr_t)img) & 3))
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_epic_image: volt must be 2-byte and img 4-byte aligned");
     if (hai_fault_injected("launch")) return hai_fail(HAI_ERR_CUDA, "hai_epic_image: injected launch failure");
     HAI_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;

@@ -423,3 +423,26 @@ def test_tc_box_wider_than_half_grid_at_128_is_refused(hai, ctx):
         assert rel_err_planes(img.cpu().numpy(), want).max() < FP32_TOL
     finally:
         hai.hai_layout_destroy(lay)
+
+
+def test_misaligned_buffers_are_refused(hai, ctx):
+    """A voltage pointer on an odd byte (half a complex value) or an image
+    pointer off 4 bytes is refused before any launch."""
+    cfg = I.SKA_LOW_STATION_256
+    pos, anchors, taps = station(cfg)
+    lay = hai.hai_layout_create(ctx, anchors, taps, cfg.grid_n, 2)
+    try:
+        ne, n = len(pos), cfg.grid_n
+        raw = torch.zeros(2 * 2 * ne * 2 + 16, dtype=torch.int8, device="cuda")
+        img = torch.zeros((1, 4, n, n), device="cuda")
+        L = hai.load()
+        for prec in (hai.HAI_PREC_FP32, hai.HAI_PREC_FP16):
+            rc = L.hai_epic_image(ctx, lay.handle, raw.data_ptr() + 1, 1, 2, prec, img.data_ptr(), 0, None)
+            assert rc == 1 and "aligned" in hai.hai_last_error()
+            rc = L.hai_epic_image(ctx, lay.handle, raw.data_ptr(), 1, 2, prec, img.data_ptr() + 2, 0, None)
+            assert rc == 1
+        vis = torch.zeros((1, ne * (ne + 1) // 2, 2, 2, 2), dtype=torch.int32, device="cuda")
+        rc = L.hai_correlate(ctx, raw.data_ptr() + 1, 1, 2, ne, 2, vis.data_ptr(), 0, None)
+        assert rc == 1 and "aligned" in hai.hai_last_error()
+    finally:
+        hai.hai_layout_destroy(lay)
