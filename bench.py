@@ -468,7 +468,8 @@ def plan_component(hai, ctx, flush, peaks, steps):
     g = torch.Generator(device="cuda").manual_seed(12)
     volt = torch.randint(-128, 128, (plan.volt_bytes,), dtype=torch.int8, device="cuda", generator=g)
     img = torch.empty((plan.img_floats,), device="cuda")
-    hai.hai_plan_autotune(plan, volt, img, 2)
+    plan_cache = os.environ.get("HAI_PLAN_TUNE_CACHE") or os.path.join(tempfile.gettempdir(), "hai_plan_autotune.txt")
+    from_cache = hai.hai_plan_autotune_cached(plan, volt, img, plan_cache, 2)
     sched = hai.hai_plan_schedule(plan)
     ms = time_call(lambda st: hai.hai_plan_run(plan, volt, img, st), steps, 3, flush)
     units = sum(n * n for n in grids) * C * 2 * T
@@ -498,6 +499,7 @@ def plan_component(hai, ctx, flush, peaks, steps):
            "ms": ms, "units_per_s": units / (ms * 1e-3), "unit": UNIT,
            "graph_launches_per_cadence": 1, "kernels_per_cadence": len(sched),
            "schedule": [{"grid": n, "ctas": c, "alone_ms": m} for n, c, m in sched],
+           "autotune": {"cache": plan_cache, "from_cache": from_cache},
            "setup_s": setup_s,
            "roofline": {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                         "peak_source": "of measured bf16_tflops (fp16 nominal ratio 1)"},

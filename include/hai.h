@@ -292,6 +292,15 @@ hai_status hai_plan_run(hai_plan *plan, const int8_t *volt, float *img, void *st
  * the kernels on (volt, img), overwriting img.  Synchronises the stream. */
 hai_status hai_plan_autotune(hai_plan *plan, const int8_t *volt, float *img, int rounds, void *stream);
 
+/* hai_plan_autotune with a cache: cache_path is a text file of
+ * "<key> | units <u_0> ... | <time>" lines, key = device, C, T and per grid
+ * class its side, station count and modelled cost.  A matching line (the
+ * last one) sets the classes' shares (CTAs, clusters at N = 128) without
+ * timing and *from_cache (may be NULL) is set to 1; otherwise the plan is
+ * autotuned as hai_plan_autotune does and a line is appended. */
+hai_status hai_plan_autotune_cached(hai_plan *plan, const int8_t *volt, float *img, int rounds, const char *cache_path,
+                                    int *from_cache, void *stream);
+
 /* Device memory the plan holds (its copies of the gather tables, station
  * records and per-CTA ranges), bytes on the host.  The run itself allocates
  * nothing. */

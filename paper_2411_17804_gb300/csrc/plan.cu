@@ -20,10 +20,12 @@
 // images them with the inter-station correlator + XFFT and/or the
 // inter-station EPIC of every beam.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "epic_tc.cuh"
@@ -707,5 +709,74 @@ extern "C" hai_status hai_plan_run_hier(hai_plan *p, const int8_t *volt, float *
     const int pidx = prof_begin(p->ctx, (cudaStream_t)stream);
     HAI_CUDA_TRY(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
     prof_end(p->ctx, pidx, (cudaStream_t)stream);
+    return HAI_OK;
+}
+
+// Key of a plan in the autotune cache: the device and, per grid class, its
+// side, stations, modelled cost (rounded) and the cadence shape.
+static std::string plan_cache_key(const hai_plan *p) {
+    cudaDeviceProp prop;
+    std::string key = "unknown";
+    if (cudaGetDeviceProperties(&prop, p->ctx->device) == cudaSuccess)
+        key = "sm" + std::to_string(prop.major) + std::to_string(prop.minor) + "x" + std::to_string(prop.multiProcessorCount);
+    key += " plan C" + std::to_string(p->C) + " T" + std::to_string(p->T);
+    for (const auto &c : p->cls) {
+        const double cost = std::accumulate(c.cost.begin(), c.cost.end(), 0.0);
+        key += " N" + std::to_string(c.N) + ":" + std::to_string(c.stations.size()) + ":" +
+               std::to_string((long long)llround(cost));
+    }
+    return key;
+}
+
+extern "C" hai_status hai_plan_autotune_cached(hai_plan *p, const int8_t *volt, float *img, int rounds,
+                                               const char *cache_path, int *from_cache, void *stream) {
+    if (!p || !volt || !img || rounds < 0 || !cache_path)
+        return hai_fail(HAI_ERR_INVALID_ARG, "hai_plan_autotune_cached: bad argument");
+    if (from_cache) *from_cache = 0;
+    const std::string key = plan_cache_key(p);
+    // "<key> | units <u_0> <u_1> ... | <ms>": the last matching line wins
+    std::vector<int> units;
+    if (FILE *f = fopen(cache_path, "r")) {
+        char line[1024];
+        while (fgets(line, sizeof(line), f)) {
+            const char *bar = strstr(line, " | units ");
+            if (!bar || std::string(line, bar - line) != key) continue;
+            std::vector<int> u;
+            const char *q = bar + 9;
+            for (size_t k = 0; k < p->cls.size(); k++) {
+                int v = 0, n = 0;
+                if (sscanf(q, "%d%n", &v, &n) != 1 || v <= 0) {
+                    u.clear();
+                    break;
+                }
+                u.push_back(v);
+                q += n;
+            }
+            if (u.size() == p->cls.size()) units = u;
+        }
+        fclose(f);
+    }
+    HAI_CUDA_TRY(cudaSetDevice(p->ctx->device));
+    if (!units.empty()) {
+        for (size_t k = 0; k < p->cls.size(); k++) {
+            const hai_status st = class_upload_ranges(p, p->cls[k], std::min(units[k], p->cls[k].max_units));
+            if (st != HAI_OK) return st;
+        }
+        drop_graph(p);
+        if (from_cache) *from_cache = 1;
+        return HAI_OK;
+    }
+    const hai_status st = hai_plan_autotune(p, volt, img, rounds, stream);
+    if (st != HAI_OK) return st;
+    if (FILE *f = fopen(cache_path, "a")) {
+        fprintf(f, "%s | units", key.c_str());
+        double worst = 0.0;
+        for (const auto &c : p->cls) {
+            fprintf(f, " %d", c.n_cta);
+            worst = std::max(worst, c.measured_ms);
+        }
+        fprintf(f, " | %.3f ms slowest class alone\n", worst);
+        fclose(f);
+    }
     return HAI_OK;
 }

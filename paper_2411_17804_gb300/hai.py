@@ -94,6 +94,7 @@ def _declare(L):
     L.hai_plan_layout.argtypes = [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.hai_plan_run.argtypes = [_vp, _vp, _vp, _vp]
     L.hai_plan_autotune.argtypes = [_vp, _vp, _vp, _int, _vp]
+    L.hai_plan_autotune_cached.argtypes = [_vp, _vp, _vp, _int, ctypes.c_char_p, ctypes.POINTER(_int), _vp]
     L.hai_plan_schedule.argtypes = [_vp, ctypes.POINTER(_int), _vp, _vp, _vp]
     L.hai_plan_set_hierarchy.argtypes = [_vp, ctypes.POINTER(_PlanHierDesc)]
     L.hai_plan_hier_sizes.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_int64)] * 4
@@ -437,6 +438,17 @@ def hai_plan_autotune(plan: Plan, volt, img, rounds: int = 2, stream=None):
     vp = _dev_ptr(volt, torch.int8, "volt", plan.volt_bytes)
     ip = _dev_ptr(img, torch.float32, "img", plan.img_floats)
     _check(load().hai_plan_autotune(plan.handle, vp, ip, rounds, _stream(stream)), "hai_plan_autotune")
+
+
+def hai_plan_autotune_cached(plan: Plan, volt, img, cache_path: str, rounds: int = 2, stream=None) -> bool:
+    """Autotune with a text cache; True when the shares came from the cache."""
+    import torch
+    vp = _dev_ptr(volt, torch.int8, "volt", plan.volt_bytes)
+    ip = _dev_ptr(img, torch.float32, "img", plan.img_floats)
+    hit = _int()
+    _check(load().hai_plan_autotune_cached(plan.handle, vp, ip, rounds, cache_path.encode(), ctypes.byref(hit),
+                                           _stream(stream)), "hai_plan_autotune_cached")
+    return bool(hit.value)
 
 
 def hai_plan_schedule(plan: Plan):

@@ -143,6 +143,34 @@ def test_plan_full_array_sampled_stations(hai, ctx):
     hai.hai_plan_destroy(plan)
 
 
+def test_plan_autotune_cache(hai, ctx, tmp_path):
+    """The cached autotuner times a plan once and writes its shares; a second
+    plan of the same shape takes them from the cache without timing, gets the
+    same schedule, and images bit-identically."""
+    C, T = 3, 9
+    sizes = [30, 90, 250, 700]
+    arr = make_array(hai, ctx, range(len(sizes)), C, T, sizes, random=True)
+    cache = str(tmp_path / "plan_tune.txt")
+    plans = [hai.hai_plan_create(ctx, [a[4] for a in arr], C, T) for _ in range(2)]
+    try:
+        vbuf = pack(plans[0], arr)
+        imgs = [torch.empty((p.img_floats,), device="cuda") for p in plans]
+        assert not hai.hai_plan_autotune_cached(plans[0], vbuf, imgs[0], cache, 1)
+        assert " | units " in open(cache).read()
+        assert hai.hai_plan_autotune_cached(plans[1], vbuf, imgs[1], cache, 1)
+        s0, s1 = hai.hai_plan_schedule(plans[0]), hai.hai_plan_schedule(plans[1])
+        assert [(g, c) for g, c, _ in s0] == [(g, c) for g, c, _ in s1]
+        for p, im in zip(plans, imgs):
+            hai.hai_plan_run(p, vbuf, im)
+        hai.hai_sync(ctx)
+        assert torch.equal(imgs[0].cpu(), imgs[1].cpu())
+    finally:
+        for p in plans:
+            hai.hai_plan_destroy(p)
+        for a in arr:
+            hai.hai_layout_destroy(a[4])
+
+
 def test_plan_rejects_unsupported_input(hai, ctx):
     sc = I.uneven_station(UNEVEN, 0, 50)
     pos, anchors, taps = station(sc)
