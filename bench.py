@@ -46,7 +46,8 @@ def parse():
                     help="image only this many channels (small cases for profiling)")
     ap.add_argument("--samples", type=int, default=0,
                     help="samples per cadence of the headline workload (default 10^4)")
-    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "xfft", "bf", "xbf", "sxfft", "fc", "big", "big16", "big2"],
+    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "xfft", "bf", "xbf", "sxfft", "fc", "big", "big16", "big2",
+                                       "plan_hier"],
                     default=None,
                     help="run one small case of a kernel twice, untimed, and exit (for ncu captures)")
     return ap.parse_args()
@@ -770,7 +771,24 @@ def run_case(name):
     import torch
     from paper_2411_17804_gb300 import hai, inputs as I
     ctx = hai.hai_create(0)
-    if name == "bf":                      # 16 stations of the hierarchical shape: 525 MB of voltages
+    if name == "plan_hier":               # the uneven array's plan with its second level, two cadences
+        cfg = I.UnevenConfig()
+        lays = []
+        for i in range(cfg.n_station):
+            sc = I.uneven_station(cfg, i)
+            an, tp = I.station_kernel(sc, I.station_layout(sc))
+            lays.append(hai.hai_layout_create(ctx, an, tp, sc.grid_n, 2))
+        plan = hai.hai_plan_create(ctx, lays, cfg.n_chan, cfg.n_time)
+        for ly in lays:
+            hai.hai_layout_destroy(ly)
+        g = torch.Generator(device="cuda").manual_seed(12)
+        volt = torch.randint(-128, 128, (plan.volt_bytes,), dtype=torch.int8, device="cuda", generator=g)
+        img = torch.empty((plan.img_floats,), device="cuda")
+        flush = torch.empty(64 << 20, device="cuda")
+        hai.hai_plan_autotune(plan, volt, img, 1)
+        plan_hierarchy(hai, ctx, plan, cfg, volt, img, flush, 2, 0.0, 1)
+        hai.hai_plan_destroy(plan)
+    elif name == "bf":                    # 16 stations of the hierarchical shape: 525 MB of voltages
         S, C, T, K, N, P = 16, 32, 1000, 16, 256, 2
         g = torch.Generator(device="cuda").manual_seed(1)
         v = torch.randint(-128, 128, (S, C, T, P, N, 2), dtype=torch.int8, device="cuda", generator=g)
