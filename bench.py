@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--samples", type=int, default=0,
                     help="samples per cadence of the headline workload (default 10^4)")
     ap.add_argument("--case", choices=["tc64", "tc128", "corr", "xfft", "bf", "xbf", "sxfft", "fc", "big", "big16", "big2",
-                                       "plan_hier"],
+                                       "plan_hier", "plan_hier128"],
                     default=None,
                     help="run one small case of a kernel twice, untimed, and exit (for ncu captures)")
     return ap.parse_args()
@@ -771,8 +771,10 @@ def run_case(name):
     import torch
     from paper_2411_17804_gb300 import hai, inputs as I
     ctx = hai.hai_create(0)
-    if name == "plan_hier":               # the uneven array's plan with its second level, two cadences
-        cfg = I.UnevenConfig()
+    if name in ("plan_hier", "plan_hier128"):   # the uneven array's plan with its second level (all stations,
+        cfg = I.UnevenConfig()                   # or the first 128 for full captures: ~1 GB of voltages)
+        if name == "plan_hier128":
+            cfg.n_station = 128
         lays = []
         for i in range(cfg.n_station):
             sc = I.uneven_station(cfg, i)

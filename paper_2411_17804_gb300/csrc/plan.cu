@@ -224,9 +224,10 @@ void drop_graph(hai_plan *p) {
 // The weights are re-packed once (hai_plan_set_hierarchy) into both forms:
 // per station WP[k][p][pair] (4 int8: two elements' re, im) then
 // WQ[k][p][element] (2 int16: re, -im), odd element counts padded with a zero
-// element.  Block (station s, channel c, 32 samples), thread (sample t, beam
-// pair kp): the two beams' sums of both pols in int32 (exact: |sum| <= 2^15
-// N_e), the voltages staged through shared memory 128 elements at a time;
+// element.  Block (station s, channel c, 64 samples, or 32 with more than 16
+// beam pairs), thread (sample t, beam pair kp): the two beams' sums of both
+// pols in int32 (exact: |sum| <= 2^15 N_e), the voltages staged through
+// shared memory 128 elements at a time;
 // the sums are requantised as hai_beamform does (|x| / 2^shift rounded half
 // away from zero, clamped to 127) into beams [S][C][T][K][2][2].
 struct HierStation {
@@ -234,7 +235,8 @@ struct HierStation {
     long long pw_off;            // 32-bit words into the packed weights
     int ne, ne2;                 // elements, element pairs
 };
-constexpr int kBfT = 32;                 // samples per block
+constexpr int kBfTMax = 64;              // samples per block: 64, or 32 for more than 16 beam pairs
+__host__ __device__ __forceinline__ int bf_samples(int K) { return (K + 1) / 2 > 16 ? 32 : kBfTMax; }
 constexpr int kBfPairs = 64;             // element pairs per shared-memory pass
 constexpr int kBfERow = kBfPairs + 1;    // words per staged (sample, pol) row: rows t fall in distinct banks
 constexpr int kBfWRow = kBfPairs + 1;    // words per staged WP row
@@ -276,12 +278,13 @@ __global__ void __launch_bounds__(1024) plan_bf_kernel(const int8_t *__restrict_
                                                        unsigned long long *__restrict__ n_sat) {
     extern __shared__ uint32_t sbw[];
     const int KP = (K + 1) / 2;
-    uint32_t *sE = sbw;                                   // [kBfT][2][kBfERow]
-    uint32_t *sP = sE + kBfT * 2 * kBfERow;               // [2 KP][2][kBfWRow] (a padded odd beam reads zeros)
+    const int TB = bf_samples(K);
+    uint32_t *sE = sbw;                                   // [TB][2][kBfERow]
+    uint32_t *sP = sE + TB * 2 * kBfERow;                 // [2 KP][2][kBfWRow] (a padded odd beam reads zeros)
     uint32_t *sQ = sP + 2 * KP * 2 * kBfWRow;             // [2 KP][2][kBfQRow]
-    const int s = blockIdx.x, c = blockIdx.y, t0 = blockIdx.z * kBfT;
+    const int s = blockIdx.x, c = blockIdx.y, t0 = blockIdx.z * TB;
     const HierStation h = hst[s];
-    const int ne = h.ne, ne2 = h.ne2, nt = min(kBfT, T - t0);
+    const int ne = h.ne, ne2 = h.ne2, nt = min(TB, T - t0);
     const int t = threadIdx.x / KP, kp = threadIdx.x % KP;
     const char2 *E = reinterpret_cast<const char2 *>(volt + h.volt_off) + ((size_t)c * T + t0) * 2 * ne;
     const uint32_t *WP = pw + h.pw_off, *WQ = WP + (size_t)K * 2 * ne2;
@@ -290,6 +293,7 @@ __global__ void __launch_bounds__(1024) plan_bf_kernel(const int8_t *__restrict_
     for (int j0 = 0; j0 < ne2; j0 += kBfPairs) {
         const int np = min(kBfPairs, ne2 - j0);
         __syncthreads();
+#pragma unroll 4
         for (int i = threadIdx.x; i < nt * 2 * np; i += blockDim.x) {
             const int j = i % np, row = i / np;            // row = (sample, pol)
             const int a = 2 * (j0 + j);
@@ -347,7 +351,7 @@ __global__ void __launch_bounds__(1024) plan_bf_kernel(const int8_t *__restrict_
 
 size_t bf_smem(int K) {
     const int KP = (K + 1) / 2;
-    return sizeof(uint32_t) * ((size_t)kBfT * 2 * kBfERow + (size_t)2 * KP * 2 * (kBfWRow + kBfQRow));
+    return sizeof(uint32_t) * ((size_t)bf_samples(K) * 2 * kBfERow + (size_t)2 * KP * 2 * (kBfWRow + kBfQRow));
 }
 
 // The second level on stream st (inside the capture): beams, their
@@ -356,7 +360,8 @@ hai_status run_second_level(hai_plan *p, const int8_t *volt, const hai_plan_hier
     hai_ctx *ctx = p->ctx;
     const int S = p->S, C = p->C, T = p->T, K = p->hK;
     if (b->n_saturated) HAI_CUDA_TRY(cudaMemsetAsync(b->n_saturated, 0, sizeof(long long), st));
-    plan_bf_kernel<<<dim3((unsigned)S, (unsigned)C, (unsigned)((T + kBfT - 1) / kBfT)), kBfT * ((K + 1) / 2), bf_smem(K),
+    const int TB = bf_samples(K);
+    plan_bf_kernel<<<dim3((unsigned)S, (unsigned)C, (unsigned)((T + TB - 1) / TB)), TB * ((K + 1) / 2), bf_smem(K),
                      st>>>(volt, static_cast<const uint32_t *>(p->d_pw), static_cast<const HierStation *>(p->d_hst), C,
                            T, K, p->hshift, b->beams, reinterpret_cast<unsigned long long *>(b->n_saturated));
     HAI_CUDA_TRY(cudaGetLastError());

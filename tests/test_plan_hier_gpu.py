@@ -161,6 +161,30 @@ def test_one_stage_only_and_recapture(hai, ctx):
         release(hai, plan, vl, el)
 
 
+@pytest.mark.parametrize("K", [9, 36])
+def test_beam_counts(hai, ctx, K):
+    """An odd beam count (a padded beam pair) and 18 beam pairs (32-sample
+    blocks): beams bit-exact, visibilities bit-exact."""
+    S, C, T = 5, 1, 40
+    plan, stations, volt, wbuf, woff, dirs, centres, vl, el = build(hai, ctx, S, C, T, K, epic=False)
+    try:
+        nb, nv, nx, ne = hai.hai_plan_hier_sizes(plan)
+        beams = torch.zeros(nb, dtype=torch.int8, device="cuda")
+        corr = torch.zeros(nb, dtype=torch.int8, device="cuda")
+        vis = torch.zeros(nv, dtype=torch.int32, device="cuda")
+        ximg = torch.zeros(nx, device="cuda")
+        img = torch.zeros(plan.img_floats, device="cuda")
+        hai.hai_plan_run_hier(plan, volt.cuda(), img, beams, corr, vis, ximg)
+        hai.hai_sync(ctx)
+        want_b, _ = oracle_beams(plan, stations, volt, wbuf, woff, C, T, K)
+        assert np.array_equal(beams.cpu().numpy().reshape(want_b.shape), want_b)
+        cin = want_b.transpose(3, 1, 2, 4, 0, 5)
+        want_v = O.correlate(cin.reshape(K * C, T, 2, S, 2))
+        assert np.array_equal(vis.cpu().numpy().reshape(want_v.shape), want_v)
+    finally:
+        release(hai, plan, vl, el)
+
+
 def test_hierarchy_arguments(hai, ctx):
     S, C, T, K = 3, 1, 4, 4
     plan, stations, volt, wbuf, woff, dirs, centres, vl, el = build(hai, ctx, S, C, T, K, epic=False)
