@@ -179,7 +179,8 @@ hai_status hai_layout_create_from_positions(hai_ctx *ctx, const hai_position_des
 hai_status hai_layout_anchors(const hai_layout *layout, int32_t *anchors, float *taps);
 
 /* Device memory held by a layout (gather tables, partial images, the scratch
- * of its tensor-core and large-grid paths, the XFFT lists once built) or by a
+ * of its tensor-core and large-grid paths, the XFFT lists once built; an
+ * N = 512 layout holds two 1 GB row scratches of the FP32 path) or by a
  * context (status words, DFT operands, and the correlator workspace and host
  * staging once first used); bytes on the host. */
 hai_status hai_layout_workspace_size(const hai_layout *layout, size_t *bytes);

@@ -19,7 +19,10 @@
 // N = 512 (the dense all-sky lattice) keeps each 512-point line in registers:
 // the rows as radix-8 transforms over 64 threads, the columns of a box of at
 // most 128 rows as four 128-point transforms per warp (see below), the
-// column data staged through shared memory a few samples ahead.
+// column data staged through shared memory a few samples ahead.  There the
+// batches are large (2 channels x 512 samples at a 128-row box, 1 GB of row
+// output) and alternate between two scratches in HBM: the row pass of one
+// batch runs on a second stream beside the column pass of the previous one.
 // As in the small-grid FP32 kernel the box sits at the transform's origin:
 // the corner shift multiplies F by a phase common to both polarisations that
 // cancels in every product, and the (-1)^(jx+jy) phase-centre factor is an
@@ -173,22 +176,27 @@ __global__ void __launch_bounds__(512) large_cols_kernel(const float2 *__restric
 // ------------------------------------------------------------------ N = 512
 // The 512-point transforms of the dense grids in registers: fft512.cuh.
 
-// Row pass, N = 512: blockIdx.x = field of the batch, blockIdx.y = group of 8
-// box rows; thread (r = tid / 64, tau): the row's cells x = tau + 64 m
+// Row pass, N = 512: blockIdx.x = field of the batch, blockIdx.y = group of
+// RPC box rows; thread (r = tid / 64, tau): the row's cells x = tau + 64 m
 // gathered from the layout's table, the transform, H[field][y][l] written
-// for every l (coalesced: l = tau + 64 j).
-__global__ void __launch_bounds__(512) large512_rows_kernel(
+// for every l (coalesced: l = tau + 64 j).  The twiddle tables come from
+// tw_g (built on the host) into shared memory.
+template <int RPC>
+__global__ void __launch_bounds__(64 * RPC) large512_rows_kernel(
     const int8_t *__restrict__ volt, int T, int P, int ne, int box_w, int box_h,
     const int32_t *__restrict__ cell_start, const int32_t *__restrict__ entry_elem,
-    const float2 *__restrict__ entry_w, const int4 *__restrict__ cell_tab, Batch bt, float2 *__restrict__ H) {
-    extern __shared__ float2 sm[];
-    float2 *tw = sm;                                    // [kTwFloat2]
-    float2 *bufs = sm + kTwFloat2;                      // [8][kFftBuf]
-    fill_fft512_tables(tw);
+    const float2 *__restrict__ entry_w, const int4 *__restrict__ cell_tab, const float2 *__restrict__ tw_g, Batch bt,
+    float2 *__restrict__ H) {
+    extern __shared__ float4 sm4[];
+    float2 *tw = reinterpret_cast<float2 *>(sm4);      // [kTwFloat2]
+    float2 *bufs = tw + kTwFloat2;                      // [RPC][kFftBuf]
+    static_assert(kTwFloat2 % 2 == 0, "tables copied as float4");
+    for (int i = threadIdx.x; i < kTwFloat2 / 2; i += blockDim.x)
+        sm4[i] = reinterpret_cast<const float4 *>(tw_g)[i];
     const int r = threadIdx.x >> 6, tau = threadIdx.x & 63;
     const int f = blockIdx.x;
     const int pol = f % P, tt = (f / P) % bt.tb, cc = f / (P * bt.tb);
-    const int y = blockIdx.y * 8 + r;
+    const int y = blockIdx.y * RPC + r;
     const char2 *E = reinterpret_cast<const char2 *>(volt) +
                      ((((size_t)(bt.c0 + cc) * T + (bt.t0 + tt)) * P + pol) * ne);
     float2 a[8];
@@ -312,7 +320,8 @@ __global__ void __launch_bounds__(64 * kCols512, 2) large512_cols_kernel(const f
 constexpr int kPr = 136;
 constexpr int kTwq = 4 * kPr + 128;          // float2: Pq, then Tq
 constexpr int kXq = 3 * 152 + 15 * 9 + 8;    // float2 per transform's exchange buffer
-constexpr size_t kHBytes = (size_t)64 << 20; // row-pass output of a batch (L2-resident)
+constexpr size_t kHBytes = (size_t)64 << 20;     // row-pass output of a batch, N = 128, 256 (L2-resident)
+constexpr size_t kH512Bytes = (size_t)1 << 30;   // each of the two row scratches at N = 512
 
 // 16-point DFT, exponent +, natural order in and out: m = m1 + 4 m2,
 // k = ka + 4 kb; 4-point DFTs over m2, twiddles w16^(m1 ka), 4-point DFTs
@@ -495,11 +504,13 @@ __global__ void __launch_bounds__(32 * kColsQ, 2) large512q_cols_kernel(const fl
 
 bool epic_large_supported(int grid_n) { return grid_n == 128 || grid_n == 256 || grid_n == 512; }
 
-// The row-pass output of a batch (64 MB, kept in L2 between the two passes),
-// and at N = 512 the twiddle tables of the 4 x 128-point transforms after it.
+// N = 128, 256: the row-pass output of a batch (64 MB, kept in L2 between the
+// two passes).  N = 512: two row scratches of 1 GB (the row pass of one batch
+// overlaps the column pass of the previous one, through HBM) and the twiddle
+// tables after them.
 size_t epic_large_scratch_bytes(int grid_n, int box_h) {
     (void)box_h;
-    return kHBytes + (grid_n == 512 ? sizeof(float2) * kTwq : 0);
+    return grid_n == 512 ? 2 * kH512Bytes + sizeof(float2) * (kTwq + kTwFloat2) : kHBytes;
 }
 
 // Pq and Tq (see the N = 512 transforms above) from FP64 sines and cosines.
@@ -515,9 +526,20 @@ hai_status epic_large_prepare(hai_layout *L) {
             for (int t = 0; t < 8; t++) tab[r * kPr + 8 * m + t] = w512((long long)r * (t + 8 * m));
     for (int k1 = 0; k1 < 16; k1++)
         for (int t = 0; t < 8; t++) tab[4 * kPr + 8 * k1 + t] = w512(4ll * t * k1);
-    cudaError_t e = cudaMemcpy(static_cast<uint8_t *>(L->d_large_scratch) + kHBytes, tab.data(),
-                               sizeof(float2) * kTwq, cudaMemcpyHostToDevice);
+    // the radix-8 transforms' tables: w512^n, w512^(tau k), w64^(t1 k) (k = 1..7)
+    tab.resize(kTwq + kTwFloat2);
+    float2 *t8 = tab.data() + kTwq;
+    for (int n = 0; n < 512; n++) t8[n] = w512(n);
+    for (int i = 0; i < 7 * 64; i++) t8[512 + i] = w512((long long)(i & 63) * (1 + (i >> 6)));
+    for (int i = 0; i < 7 * 8; i++) t8[512 + 7 * 64 + i] = w512(8ll * (i & 7) * (1 + (i >> 3)));
+    cudaError_t e = cudaMemcpy(static_cast<uint8_t *>(L->d_large_scratch) + 2 * kH512Bytes, tab.data(),
+                               sizeof(float2) * tab.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return hai_cuda_fail(e, "epic fp32 (large grid): twiddle tables");
+    // the second stream and events that overlap the row pass of one batch with
+    // the column pass of the previous one
+    e = cudaStreamCreateWithFlags(&L->large_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 5 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&L->large_ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return hai_cuda_fail(e, "epic fp32 (large grid): stream");
     // per-cell table of the box when no cell holds more than one gather entry
     // (the row pass then reads element and weight in one 16-byte load)
     const int ncell = L->box_w * L->box_h;
@@ -573,40 +595,64 @@ hai_status epic_large_launch(const hai_layout *L, const int8_t *volt, int C, int
     float2 *H = static_cast<float2 *>(L->d_large_scratch);
     const int pidx = prof_begin(L->ctx, st);
     if (N == 512 && P == 2) {
-        // rows: register-resident radix-8 transforms; columns: the 4 x 128-point
-        // warp transforms for boxes of at most 128 rows, else radix-8 as the
-        // rows.  Batches of 2 channels x as many samples as the scratch holds
-        // (fewer image read-modify-writes per sample).
-        const float2 *twq = reinterpret_cast<const float2 *>(static_cast<const uint8_t *>(L->d_large_scratch) + kHBytes);
-        const size_t rs_smem = sizeof(float2) * (kTwFloat2 + 8 * (size_t)kFftBuf);
+        // rows: register-resident radix-8 transforms, 8 rows per CTA, on the
+        // layout's second stream into one of two row scratches, so that the
+        // row pass of batch i overlaps the column pass of batch i - 1; columns:
+        // the 4 x 128-point warp transforms for boxes of at most 128 rows, else
+        // radix-8 as the rows.  Batches of 2 channels x as many samples as a
+        // scratch holds (512 at a 128-row box): the column pass reads and
+        // writes its image columns once per batch, and the two streams meet
+        // once per batch.
+        constexpr int kRpc = 8;
+        constexpr int kCb = 2;
+        const uint8_t *tabs = static_cast<const uint8_t *>(L->d_large_scratch) + 2 * kH512Bytes;
+        const float2 *twq = reinterpret_cast<const float2 *>(tabs);
+        const float2 *tw8 = twq + kTwq;
+        const size_t rs_smem = sizeof(float2) * (kTwFloat2 + kRpc * (size_t)kFftBuf);
         const size_t cs_smem = sizeof(float2) * (kTwFloat2 + 2 * kCols512 * (size_t)kFftBuf);
         const size_t cq_smem = sizeof(float2) * (kTwq + (size_t)kPfq * kStageQ + (size_t)kColsQ * 2 * kXq);
-        HAI_CUDA_TRY(hai_allow_dyn_smem(large512_rows_kernel, L->ctx->smem_optin));
+        HAI_CUDA_TRY(hai_allow_dyn_smem(large512_rows_kernel<kRpc>, L->ctx->smem_optin));
         HAI_CUDA_TRY(hai_allow_dyn_smem(large512_cols_kernel, L->ctx->smem_optin));
         HAI_CUDA_TRY(hai_allow_dyn_smem(large512q_cols_kernel, L->ctx->smem_optin));
-        const int cb_max = std::min(C, 2);
-        const int tb512 = (int)std::max<long long>(1, std::min<long long>(T, fields_cap / ((long long)cb_max * P)));
+        cudaStream_t rst = L->large_stream;
+        cudaEvent_t const *ev = L->large_ev;            // 0, 1: rows done (scratch 0, 1); 2, 3: columns done; 4: fork / join
+        HAI_CUDA_TRY(cudaEventRecord(ev[4], st));
+        HAI_CUDA_TRY(cudaStreamWaitEvent(rst, ev[4], 0));
+        const int cb_max = std::min(C, kCb);
+        const long long fields512 = (long long)(kH512Bytes / field_bytes);
+        const int tb512 = (int)std::max<long long>(1, std::min<long long>(T, fields512 / ((long long)cb_max * P)));
+        int i = 0;
         for (int t0 = 0; t0 < T; t0 += tb512) {
             const int tb = std::min(tb512, T - t0);
-            for (int c0 = 0; c0 < C; c0 += cb_max) {
+            for (int c0 = 0; c0 < C; c0 += cb_max, i++) {
+                const int buf = i & 1;
+                float2 *Hb = reinterpret_cast<float2 *>(static_cast<uint8_t *>(L->d_large_scratch) + buf * kH512Bytes);
                 Batch bt;
                 bt.c0 = c0;
                 bt.cb = std::min(cb_max, C - c0);
                 bt.t0 = t0;
                 bt.tb = tb;
-                large512_rows_kernel<<<dim3(bt.cb * tb * P, (L->box_h + 7) / 8), 512, rs_smem, st>>>(
-                    volt, T, P, L->n_elem, L->box_w, L->box_h, L->d_cell_start, L->d_entry_elem, L->d_entry_w,
-                    static_cast<const int4 *>(L->d_large_cell), bt, H);
+                if (i >= 2) HAI_CUDA_TRY(cudaStreamWaitEvent(rst, ev[2 + buf], 0));   // columns of batch i - 2 done
+                large512_rows_kernel<kRpc><<<dim3(bt.cb * tb * P, (L->box_h + kRpc - 1) / kRpc), 64 * kRpc, rs_smem,
+                                             rst>>>(volt, T, P, L->n_elem, L->box_w, L->box_h, L->d_cell_start,
+                                                    L->d_entry_elem, L->d_entry_w,
+                                                    static_cast<const int4 *>(L->d_large_cell), tw8, bt, Hb);
+                HAI_CUDA_TRY(cudaEventRecord(ev[buf], rst));
+                HAI_CUDA_TRY(cudaStreamWaitEvent(st, ev[buf], 0));
                 const int add = (t0 > 0 || accumulate) ? 1 : 0;
                 if (L->box_h <= 128)
-                    large512q_cols_kernel<<<dim3(512 / kColsQ, bt.cb), 32 * kColsQ, cq_smem, st>>>(H, L->box_h, twq, bt,
+                    large512q_cols_kernel<<<dim3(512 / kColsQ, bt.cb), 32 * kColsQ, cq_smem, st>>>(Hb, L->box_h, twq, bt,
                                                                                                    img, add);
                 else
-                    large512_cols_kernel<<<dim3(bt.cb, 512 / kCols512), 64 * kCols512, cs_smem, st>>>(H, L->box_h, bt,
+                    large512_cols_kernel<<<dim3(bt.cb, 512 / kCols512), 64 * kCols512, cs_smem, st>>>(Hb, L->box_h, bt,
                                                                                                      img, add);
+                HAI_CUDA_TRY(cudaEventRecord(ev[2 + buf], st));
                 prof_count(L->ctx, 2);
             }
         }
+        // join: the caller's stream after the second stream's last work
+        HAI_CUDA_TRY(cudaEventRecord(ev[4], rst));
+        HAI_CUDA_TRY(cudaStreamWaitEvent(st, ev[4], 0));
         prof_end(L->ctx, pidx, st);
         HAI_CUDA_TRY(cudaGetLastError());
         return HAI_OK;

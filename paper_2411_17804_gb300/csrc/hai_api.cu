@@ -237,6 +237,9 @@ static void layout_free(hai_layout *L) {
     cudaFree(L->d_tc_station);
     cudaFree(L->d_large_scratch);
     cudaFree(L->d_large_cell);
+    if (L->large_stream) cudaStreamDestroy(L->large_stream);
+    for (cudaEvent_t ev : L->large_ev)
+        if (ev) cudaEventDestroy(ev);
     cudaFree(L->d_big);
     cudaFree(L->d_xcell);
     cudaFree(L->d_xent);

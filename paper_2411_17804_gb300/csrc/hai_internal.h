@@ -74,6 +74,8 @@ struct hai_layout {
     void *d_large_scratch = nullptr;
     size_t large_scratch_bytes = 0;
     void *d_large_cell = nullptr;       // N = 512, at most one entry per cell: int4 {element, conj(W~)} per box cell
+    cudaStream_t large_stream = nullptr;   // N = 512: the row pass's stream
+    cudaEvent_t large_ev[5] = {};          // rows done (2), columns done (2), fork / join
     void *d_tc_station = nullptr;
     // tensor-core path of large grids (N = 256, 512): DFT operands and the
     // stage scratch of one batch of (channel, sample) pairs
