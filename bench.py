@@ -46,7 +46,7 @@ def parse():
                     help="image only this many channels (small cases for profiling)")
     ap.add_argument("--samples", type=int, default=0,
                     help="samples per cadence of the headline workload (default 10^4)")
-    ap.add_argument("--case", choices=["tc64", "tc128", "corr", "xfft", "bf", "xbf", "sxfft", "fc", "big", "big16", "big2",
+    ap.add_argument("--case", choices=["tc64", "fp32_64", "tc128", "corr", "xfft", "bf", "xbf", "sxfft", "fc", "big", "big16", "big2",
                                        "plan_hier", "plan_hier128"],
                     default=None,
                     help="run one small case of a kernel twice, untimed, and exit (for ncu captures)")
@@ -798,17 +798,18 @@ def run_case(name):
         out = torch.empty((S, C, T, K, P, 2), dtype=torch.int8, device="cuda")
         for _ in range(2):
             hai.hai_beamform(ctx, v, w, S, C, T, K, N, P, 11, out)
-    elif name in ("tc64", "corr"):        # the SKA-low station: 16 channels (33.6 MB) for tc64, 64 for corr
-        cfg = I.SKA_LOW_STATION_256
+    elif name in ("tc64", "fp32_64", "corr"):   # the SKA-low station: 16 channels (33.6 MB) for the EPIC
+        cfg = I.SKA_LOW_STATION_256               # cases (tensor cores, FP32), 64 for corr
         pos = I.station_layout(cfg)
         an, tp = I.station_kernel(cfg, pos)
-        C = 16 if name == "tc64" else cfg.n_chan
+        C = cfg.n_chan if name == "corr" else 16
         v = I.station_voltages(cfg, pos, device="cuda", n_chan=C)
-        if name == "tc64":
+        if name != "corr":
+            prec = hai.HAI_PREC_FP16 if name == "tc64" else hai.HAI_PREC_FP32
             lay = hai.hai_layout_create(ctx, an, tp, 64, 2)
             img = torch.empty((C, 4, 64, 64), device="cuda")
             for _ in range(2):
-                hai.hai_epic_image(ctx, lay, v, C, cfg.n_time, hai.HAI_PREC_FP16, img, 0)
+                hai.hai_epic_image(ctx, lay, v, C, cfg.n_time, prec, img, 0)
         else:
             N = cfg.n_elem
             vis = torch.empty((C, N * (N + 1) // 2, 2, 2, 2), dtype=torch.int32, device="cuda")

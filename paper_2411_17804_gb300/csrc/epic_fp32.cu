@@ -19,6 +19,7 @@
 
 #include <algorithm>
 
+#include "fft512.cuh"
 #include "hai_internal.h"
 
 namespace {
@@ -220,6 +221,320 @@ epic_fp32_kernel(const int8_t *__restrict__ volt, int C, int T, int ne, long lon
     if (s1 > s0) flush(cur_c, seg);
 }
 
+// ------------------------------------------------------------------ N = 64
+// The 64 x 64 grid with every 64-point line in registers: a group of 8 lanes
+// per line, lane t holding points t + 8 m (m < 8).  With k = k1 + 8 k2,
+// w64^((t + 8 m) k) = w64^(t k1) w8^(t k2) w8^(m k1): lane t takes the
+// 8-point DFT over m (only m < 4 when the box spans at most 32 cells along
+// the line), multiplies output k1 by w64^(t k1), and after one exchange
+// through the group's shared scratch (within the warp) lane j takes the
+// 8-point DFT over t of the values of k1 = j, ending with X[j + 8 k2] in
+// a[k2].  Exponent + throughout.
+//
+// Per sample: row pass (a group per (box row, pol): gather, transform along
+// x, row written to H), then column pass (a group per column, both pols:
+// transform along y, then |F_X|^2, |F_Y|^2 and F_X conj(F_Y) of its 8 pixels
+// into register accumulators).  The row pass of sample i and the column pass
+// of sample i - 1 share one phase (H and the staged voltages double-buffered),
+// so a sample costs one block barrier.
+//
+// Shared layouts, all accesses in the minimum two wavefronts per 8-byte
+// access: H[p][y][(k + 2 (y & 7)) & 63] with planes 8 (mod 16) float2 apart
+// (a half-warp writes both pols of one row, or rows y and y + 4 with one
+// pol, and reads rows t + 8 m of two adjacent columns); the exchange scratch
+// of a group holds value k of lane t at 9 k + t, groups 8 (mod 16) apart.
+constexpr int k64Threads = 512;                  // 64 groups of 8 lanes
+constexpr int k64Xs = 72;                        // float2 of exchange scratch per group (one pol at a time)
+
+__device__ __forceinline__ void dft8_first4(float2 (&a)[8]) {
+    // inputs a[4..7] zero: the even outputs are the 4-point DFT of a[0..3],
+    // the odd ones that of a[m] w8^m
+    const float h = 0.70710678118654752f;
+    float2 v0 = a[0], v1 = a[1], v2 = a[2], v3 = a[3];
+    v1 = make_float2(h * (v1.x - v1.y), h * (v1.x + v1.y));          // * e^(+i pi/4)
+    v2 = hai_fft512::cmuli(v2);                                       // * e^(+i pi/2)
+    v3 = make_float2(-h * (v3.x + v3.y), h * (v3.x - v3.y));         // * e^(+3i pi/4)
+    float2 u0 = a[0], u1 = a[1], u2 = a[2], u3 = a[3];
+    hai_fft512::dft4(u0, u1, u2, u3);
+    hai_fft512::dft4(v0, v1, v2, v3);
+    a[0] = u0; a[2] = u1; a[4] = u2; a[6] = u3;
+    a[1] = v0; a[3] = v1; a[5] = v2; a[7] = v3;
+}
+
+__device__ __forceinline__ void cp_async16_64(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// Shared memory of the N = 64 kernel.  SP samples per phase (2 when the box
+// is at most 32 rows and shared memory allows, else 1); sample si of a phase
+// and pol p keep their H plane at si SO + p PO, SO = 8 (mod 16) too, so that
+// a half-warp writing one row of two samples stays within two wavefronts.
+// TS: the gather table (cell starts, then {element, conj(W~)} as int4 per
+// entry) is copied into shared memory at the start.
+template <int P, bool PX, bool PY, int SP, bool TS>
+struct Epic64Smem {
+    static constexpr int HR = PY ? 32 : 64;                  // rows of H
+    static constexpr int PO = HR * 64 + 8;                   // pol plane stride (float2)
+    static constexpr int SO = (P * PO + 15) / 16 * 16 + 8;   // sample stride
+    static constexpr int HB = SP * SO;                        // one of the two H buffers
+    static constexpr size_t fixed = sizeof(float2) * (2 * (size_t)HB + 64 * (size_t)k64Xs);
+    __host__ __device__ static size_t vbuf(int ne) { return ((size_t)SP * P * ne * 2 + 15) / 16 * 16; }
+    __host__ __device__ static size_t cbytes(int ncell) { return TS ? ((size_t)(ncell + 1) * 4 + 15) / 16 * 16 : 0; }
+    __host__ __device__ static size_t bytes(int ne, int ncell, int nnz) {
+        return fixed + 2 * vbuf(ne) + cbytes(ncell) + (TS ? (size_t)nnz * 16 : 0);
+    }
+};
+
+// Same arguments and outputs as epic_fp32_kernel<64, P> (nnz = the table's
+// entry count); PX / PY: the box spans at most 32 cells along x / y.  The
+// int8 voltages of the next phase are copied into shared memory (16-byte
+// cp.async when vec16) while the current one is imaged.
+//
+// Row tasks: warp w takes rows w and 31 - w (+ 32), so that the rows beyond a
+// box of fewer than 32 spread over the four schedulers.  SP = 2: group g
+// takes its row of sample g & 1 of the phase, both pols (one walk of the
+// gather table for both); SP = 1, P = 2: pol g & 1; P = 1: rows g and g + 4
+// paired in a half-warp.  The exchanges go one pol at a time.
+template <int P, bool PX, bool PY, int SP, bool TS>
+__global__ void __launch_bounds__(k64Threads, 1)
+epic64_kernel(const int8_t *__restrict__ volt, int C, int T, int ne, long long len, int box_w, int box_h,
+              const int32_t *__restrict__ cstart_g, const int32_t *__restrict__ celem,
+              const float2 *__restrict__ cw, int nnz, float *__restrict__ out, int direct, int accumulate,
+              int vec16) {
+    constexpr int Q = (P == 2) ? 4 : 1;
+    using S = Epic64Smem<P, PX, PY, SP, TS>;
+    constexpr int PO = S::PO, SO = S::SO, HB = S::HB;
+    constexpr int RP = (SP == 2) ? P : 1;                    // pols per row task
+    constexpr int RR = (SP == 2 || P == 2) && !PY ? 2 : 1;   // row tasks per group
+    static_assert(SP == 1 || PY, "two samples per phase need a box of at most 32 rows");
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *Hs = reinterpret_cast<float2 *>(smem);                        // [2][HB]
+    float2 *xs = Hs + 2 * HB + (threadIdx.x >> 3) * k64Xs;                // this group's scratch
+    unsigned char *vs = smem + S::fixed;                                  // [2][vstride]
+    const int vbytes = P * ne * 2;                                        // one sample
+    const int vstride = (int)S::vbuf(ne);
+    const int ncell = box_w * box_h;
+    int32_t *cs_s = reinterpret_cast<int32_t *>(vs + 2 * (size_t)vstride);
+    int4 *ent_s = reinterpret_cast<int4 *>(reinterpret_cast<unsigned char *>(cs_s) + S::cbytes(ncell));
+
+    const int tid = threadIdx.x, t = tid & 7, g = tid >> 3;
+    const long long total = (long long)C * T;
+    const long long s0 = (long long)blockIdx.x * len;
+    const long long s1 = min(total, s0 + len);
+    if (s0 >= s1) return;
+    const int n = (int)(s1 - s0);
+    const int nph = (n + SP - 1) / SP;
+
+    if (TS) {
+        for (int i = tid; i <= ncell; i += k64Threads) cs_s[i] = __ldg(cstart_g + i);
+        for (int i = tid; i < nnz; i += k64Threads) {
+            const float2 w = __ldg(cw + i);
+            ent_s[i] = make_int4(__ldg(celem + i), __float_as_int(w.x), __float_as_int(w.y), 0);
+        }
+    }
+    const int32_t *cstart = TS ? cs_s : cstart_g;
+
+    // w64^(t k), k = 1..7, from the table of w64^m, m < 32
+    float2 tw[8];
+#pragma unroll
+    for (int k = 1; k < 8; k++) {
+        const int m = t * k;
+        const float2 v = c_tw[m & 31];
+        tw[k] = m < 32 ? v : make_float2(-v.x, -v.y);
+    }
+
+    auto load = [&](int ph, int b) {
+        const int bytes = min(SP, n - SP * ph) * vbytes;
+        const int8_t *src = volt + (size_t)(s0 + (long long)SP * ph) * vbytes;
+        unsigned char *dst = vs + (size_t)b * vstride;
+        if (vec16) {
+            for (int i = tid; i < bytes / 16; i += k64Threads) cp_async16_64(dst + 16 * i, src + 16 * i);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        } else {
+            const char2 *s2 = reinterpret_cast<const char2 *>(src);
+            char2 *d2 = reinterpret_cast<char2 *>(dst);
+            for (int i = tid; i < bytes / 2; i += k64Threads) d2[i] = s2[i];
+        }
+    };
+
+    float acc[8][Q];
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+#pragma unroll
+        for (int q = 0; q < Q; q++) acc[k][q] = 0.f;
+    const int col = g;                                   // column pass: column of this group
+    int cur_c = (int)(s0 / T), seg = 0;
+    auto flush = [&](int c, int sgm) {
+        float *dst = direct ? out + (size_t)c * Q * 4096 : out + ((size_t)blockIdx.x * 2 + sgm) * Q * 4096;
+        const int lx = (col + 32) & 63;
+#pragma unroll
+        for (int k2 = 0; k2 < 8; k2++) {
+            const int pix = ((t + 8 * k2 + 32) & 63) * 64 + lx;
+#pragma unroll
+            for (int q = 0; q < Q; q++) {
+                float v = acc[k2][q];
+                if (direct && accumulate) v += dst[(size_t)q * 4096 + pix];
+                dst[(size_t)q * 4096 + pix] = v;
+                acc[k2][q] = 0.f;
+            }
+        }
+    };
+    // second half of a 64-point line: a[k1] (twiddled) of lane t in, X[t + 8 k2] in a[k2] out
+    auto finish = [&](float2 (&a)[8]) {
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) xs[9 * k + t] = a[k];
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < 8; u++) a[u] = xs[9 * t + u];
+        hai_fft512::dft8(a);
+    };
+
+    load(0, 0);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    for (int it = 0; it <= nph; it++) {
+        if (it + 1 < nph) load(it + 1, (it + 1) & 1);
+        if (it < nph) {
+            // row pass of phase it
+            const unsigned char *V = vs + (size_t)(it & 1) * vstride;
+            float2 *H = Hs + (size_t)(it & 1) * HB;
+            const int ns = min(SP, n - SP * it);
+#pragma unroll
+            for (int r = 0; r < RR; r++) {
+                int y, p0, si;
+                const int w = g >> 2, yw = ((g & 2) ? 31 - w : w) + 32 * r;
+                if (SP == 2) {
+                    si = g & 1;
+                    p0 = 0;
+                    y = yw;
+                } else if (P == 2) {
+                    si = 0;
+                    p0 = g & 1;
+                    y = yw;
+                } else {
+                    si = 0;
+                    p0 = 0;
+                    y = (g & ~7) | ((g & 1) << 2) | ((g >> 1) & 3);
+                }
+                const bool live = y < box_h && si < ns;
+                if (!__any_sync(0xffffffffu, live)) continue;             // warp-uniform
+                float2 a[RP][8];
+#pragma unroll
+                for (int q = 0; q < RP; q++)
+#pragma unroll
+                    for (int m = 0; m < 8; m++) a[q][m] = make_float2(0.f, 0.f);
+                if (live) {
+                    const char2 *E = reinterpret_cast<const char2 *>(V + (size_t)si * vbytes) + (size_t)p0 * ne;
+                    constexpr int MX = PX ? 4 : 8;
+                    int cb[MX], ce[MX];                                   // the cells' entry ranges, loaded first
+#pragma unroll
+                    for (int m = 0; m < MX; m++) {
+                        const int x = t + 8 * m;
+                        cb[m] = ce[m] = 0;
+                        if (x < box_w) {
+                            cb[m] = cstart[y * box_w + x];
+                            ce[m] = cstart[y * box_w + x + 1];
+                        }
+                    }
+#pragma unroll
+                    for (int m = 0; m < MX; m++) {
+                        float2 acg[RP];
+#pragma unroll
+                        for (int q = 0; q < RP; q++) acg[q] = make_float2(0.f, 0.f);
+                        for (int i = cb[m]; i < ce[m]; i++) {
+                            int el;
+                            float2 wv;                                    // conj(W~)
+                            if (TS) {
+                                const int4 d = ent_s[i];
+                                el = d.x;
+                                wv = make_float2(__int_as_float(d.y), __int_as_float(d.z));
+                            } else {
+                                el = __ldg(celem + i);
+                                wv = __ldg(cw + i);
+                            }
+#pragma unroll
+                            for (int q = 0; q < RP; q++) {
+                                const char2 v = E[q * ne + el];
+                                const float er = (float)v.x, ei = (float)v.y;
+                                acg[q].x = fmaf(wv.x, er, fmaf(-wv.y, ei, acg[q].x));
+                                acg[q].y = fmaf(wv.x, ei, fmaf(wv.y, er, acg[q].y));
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < RP; q++) a[q][m] = acg[q];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < RP; q++) {
+                    if (PX) dft8_first4(a[q]);
+                    else hai_fft512::dft8(a[q]);
+#pragma unroll
+                    for (int k = 1; k < 8; k++) a[q][k] = hai_fft512::cmul(a[q][k], tw[k]);
+                    finish(a[q]);
+                }
+                if (live) {
+                    const int sw = 2 * (y & 7);
+#pragma unroll
+                    for (int q = 0; q < RP; q++) {
+                        float2 *row = H + (size_t)si * SO + (size_t)(p0 + q) * PO + (size_t)y * 64;
+#pragma unroll
+                        for (int k2 = 0; k2 < 8; k2++) row[(t + 8 * k2 + sw) & 63] = a[q][k2];
+                    }
+                }
+            }
+        }
+        if (it >= 1) {
+            // column pass of phase it - 1, sample by sample
+            const float2 *Hp = Hs + (size_t)((it - 1) & 1) * HB;
+            const int ns = min(SP, n - SP * (it - 1));
+            const int pos = (col + 2 * t) & 63;                           // row y = t + 8 m: y & 7 = t
+#pragma unroll
+            for (int si = 0; si < SP; si++) {
+                if (si >= ns) break;                                      // CTA-uniform
+                const int c = (int)((s0 + (long long)SP * (it - 1) + si) / T);
+                if (c != cur_c) {
+                    flush(cur_c, seg);
+                    seg++;
+                    cur_c = c;
+                }
+                const float2 *H = Hp + (size_t)si * SO;
+                float2 f[P][8];
+#pragma unroll
+                for (int p = 0; p < P; p++) {
+#pragma unroll
+                    for (int m = 0; m < 8; m++) {
+                        const int y = t + 8 * m;
+                        f[p][m] = (m < (PY ? 4 : 8) && y < box_h) ? H[(size_t)p * PO + (size_t)y * 64 + pos]
+                                                                  : make_float2(0.f, 0.f);
+                    }
+                    if (PY) dft8_first4(f[p]);
+                    else hai_fft512::dft8(f[p]);
+#pragma unroll
+                    for (int k = 1; k < 8; k++) f[p][k] = hai_fft512::cmul(f[p][k], tw[k]);
+                }
+#pragma unroll
+                for (int p = 0; p < P; p++) finish(f[p]);
+#pragma unroll
+                for (int k2 = 0; k2 < 8; k2++) {
+                    const float2 fx = f[0][k2];
+                    acc[k2][0] = fmaf(fx.x, fx.x, fmaf(fx.y, fx.y, acc[k2][0]));
+                    if (P == 2) {
+                        const float2 fy = f[P - 1][k2];
+                        acc[k2][Q > 1 ? 1 : 0] = fmaf(fy.x, fy.x, fmaf(fy.y, fy.y, acc[k2][Q > 1 ? 1 : 0]));
+                        acc[k2][Q > 2 ? 2 : 0] = fmaf(fx.x, fy.x, fmaf(fx.y, fy.y, acc[k2][Q > 2 ? 2 : 0]));
+                        acc[k2][Q > 3 ? 3 : 0] = fmaf(fx.y, fy.x, fmaf(-fx.x, fy.y, acc[k2][Q > 3 ? 3 : 0]));
+                    }
+                }
+            }
+        }
+        if (vec16) asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncthreads();
+    }
+    flush(cur_c, seg);
+}
+
 // img[c] = (accumulate ? img[c] : 0) + sum of the partials of channel c, in
 // CTA order.  CTA b covers samples [b*len, (b+1)*len) of the flat index.
 __global__ void epic_reduce_kernel(const float *__restrict__ part, float *__restrict__ img, int C,
@@ -239,9 +554,113 @@ __global__ void epic_reduce_kernel(const float *__restrict__ part, float *__rest
     img[i] = accumulate ? img[i] + s : s;
 }
 
+// The N = 64 kernel in the form the box and the shared memory allow:
+// *launched = false if even the smallest form does not fit (the caller keeps
+// the general kernel).
+template <int P, bool PX, bool PY, int SP, bool TS>
+void launch64_form(const int8_t *volt, int C, int T, int ne, const EpicSplit &sp, int box_w, int box_h,
+                   const int32_t *cstart, const int32_t *celem, const float2 *cw, int nnz, float *dst,
+                   int accumulate, size_t smem, cudaStream_t st) {
+    const int vec16 = ((((uintptr_t)volt) & 15) == 0 && ((size_t)P * ne * 2) % 16 == 0) ? 1 : 0;
+    epic64_kernel<P, PX, PY, SP, TS><<<sp.n_cta, k64Threads, smem, st>>>(
+        volt, C, T, ne, sp.len, box_w, box_h, cstart, celem, cw, nnz, dst, sp.direct, accumulate, vec16);
+}
+
+template <int P, bool PX, bool PY, int SP, bool TS>
+hai_status try64(const int8_t *volt, int C, int T, int ne, const EpicSplit &sp, int box_w, int box_h,
+                 const int32_t *cstart, const int32_t *celem, const float2 *cw, int nnz, float *dst, int accumulate,
+                 int smem_optin, cudaStream_t st, bool *launched) {
+    const size_t smem = Epic64Smem<P, PX, PY, SP, TS>::bytes(ne, box_w * box_h, nnz);
+    if (*launched || smem > (size_t)smem_optin) return HAI_OK;
+    auto kern = epic64_kernel<P, PX, PY, SP, TS>;
+    HAI_CUDA_TRY(hai_allow_dyn_smem(kern, smem_optin));
+    launch64_form<P, PX, PY, SP, TS>(volt, C, T, ne, sp, box_w, box_h, cstart, celem, cw, nnz, dst, accumulate,
+                                     smem, st);
+    HAI_CUDA_TRY(cudaGetLastError());
+    *launched = true;
+    return HAI_OK;
+}
+
+// Forms in order of preference: two samples per phase (boxes of at most 32
+// rows) with the table in shared memory, then without it; one sample with the
+// table (taller boxes); one sample.  One pol: one sample, table in global
+// memory.
+template <int P, bool PX, bool PY>
+hai_status launch64_box(const int8_t *volt, int C, int T, int ne, const EpicSplit &sp, int box_w, int box_h,
+                        const int32_t *cstart, const int32_t *celem, const float2 *cw, int nnz, float *dst,
+                        int accumulate, int smem_optin, cudaStream_t st, bool *launched) {
+    *launched = false;
+    if constexpr (P == 1) {       // one pol: the plain forms only
+        return try64<P, PX, PY, 1, false>(volt, C, T, ne, sp, box_w, box_h, cstart, celem, cw, nnz, dst, accumulate,
+                                          smem_optin, st, launched);
+    } else {
+#define HAI_TRY64(SPV, TSV)                                                                                    \
+    {                                                                                                          \
+        const hai_status s_ = try64<P, PX, PY, SPV, TSV>(volt, C, T, ne, sp, box_w, box_h, cstart, celem, cw,  \
+                                                         nnz, dst, accumulate, smem_optin, st, launched);      \
+        if (s_ != HAI_OK) return s_;                                                                           \
+    }
+        if constexpr (PY) {
+            HAI_TRY64(2, true);
+            HAI_TRY64(2, false);
+        } else {
+            HAI_TRY64(1, true);
+        }
+        HAI_TRY64(1, false);
+#undef HAI_TRY64
+        return HAI_OK;
+    }
+}
+
+template <int P>
+size_t epic64_bytes(int ne, int box_w, int box_h) {
+    // the smallest form (one sample per phase, table in global memory)
+    const bool px = box_w <= 32, py = box_h <= 32;
+    if (px && py) return Epic64Smem<P, true, true, 1, false>::bytes(ne, 0, 0);
+    if (px) return Epic64Smem<P, true, false, 1, false>::bytes(ne, 0, 0);
+    if (py) return Epic64Smem<P, false, true, 1, false>::bytes(ne, 0, 0);
+    return Epic64Smem<P, false, false, 1, false>::bytes(ne, 0, 0);
+}
+
+template <int P>
+hai_status launch64(const int8_t *volt, int C, int T, int ne, const EpicSplit &sp, int box_w, int box_h,
+                    const int32_t *cstart, const int32_t *celem, const float2 *cw, int nnz, float *dst,
+                    int accumulate, int smem_optin, cudaStream_t st, bool *launched) {
+    const bool px = box_w <= 32, py = box_h <= 32;
+    if (px && py)
+        return launch64_box<P, true, true>(volt, C, T, ne, sp, box_w, box_h, cstart, celem, cw, nnz, dst, accumulate,
+                                           smem_optin, st, launched);
+    if (px)
+        return launch64_box<P, true, false>(volt, C, T, ne, sp, box_w, box_h, cstart, celem, cw, nnz, dst,
+                                            accumulate, smem_optin, st, launched);
+    if (py)
+        return launch64_box<P, false, true>(volt, C, T, ne, sp, box_w, box_h, cstart, celem, cw, nnz, dst,
+                                            accumulate, smem_optin, st, launched);
+    return launch64_box<P, false, false>(volt, C, T, ne, sp, box_w, box_h, cstart, celem, cw, nnz, dst, accumulate,
+                                         smem_optin, st, launched);
+}
+
 template <int N, int P>
 hai_status launch_n(const hai_layout *L, const int8_t *volt, int C, int T, float *img, int accumulate,
                     cudaStream_t st) {
+    if (N == 64) {
+        const EpicSplit sp = epic_make_split(C, T, epic_fp32_target_ctas(L->ctx, N));
+        if (!sp.direct && (size_t)sp.n_cta * 2 > L->partial_slots)
+            return hai_fail(HAI_ERR_INVALID_ARG, "epic fp32: partial buffer too small");
+        float *dst = sp.direct ? img : L->d_partials;
+        bool launched = false;
+        if (epic64_bytes<P>(L->n_elem, L->box_w, L->box_h) <= (size_t)L->ctx->smem_optin) {
+            const int pidx = prof_begin(L->ctx, st);
+            hai_status s = launch64<P>(volt, C, T, L->n_elem, sp, L->box_w, L->box_h, L->d_cell_start,
+                                       L->d_entry_elem, L->d_entry_w, L->nnz, dst, accumulate, L->ctx->smem_optin,
+                                       st, &launched);
+            if (s != HAI_OK) return s;
+            prof_end(L->ctx, pidx, st);
+            prof_count(L->ctx, 1);
+            if (!sp.direct) return epic_reduce_launch(L, sp, C, T, img, accumulate, st);
+            return HAI_OK;
+        }
+    }
     const size_t smem = sizeof(float2) * EpicSmem<N, P>::kBuf +
                         ((size_t)kSamples * P * L->n_elem * 2 + 15) / 16 * 16;
     if (smem > (size_t)L->ctx->smem_optin)
@@ -360,19 +779,28 @@ hai_status static_scratch(int device, float **out) {
 template <int N, int P>
 hai_status launch_static(float *scratch, int ne, int box_w, int box_h, int ncell, int nnz, const int8_t *volt,
                          int C, int T, float *img, int accumulate, int sms, int smem_optin, cudaStream_t st) {
-    const size_t smem = sizeof(float2) * EpicSmem<N, P>::kBuf + ((size_t)kSamples * P * ne * 2 + 15) / 16 * 16;
-    if (smem > (size_t)smem_optin)
-        return hai_fail(HAI_ERR_UNSUPPORTED, "hai_epic_image_fp32_static: shared memory need exceeds the device limit");
-    auto kern = epic_fp32_kernel<N, P>;
-    HAI_CUDA_TRY(hai_allow_dyn_smem(kern, smem_optin));
     const EpicSplit sp = epic_make_split(C, T, std::min(sms, kStaticCtas));
     const int32_t *cstart = reinterpret_cast<const int32_t *>(scratch);
     const int32_t *celem = cstart + (ncell + 1);
     const float2 *cw = reinterpret_cast<const float2 *>(cstart + static_taps_word(ncell, nnz));
     float *partials = scratch + kStaticTableWords;
-    kern<<<sp.n_cta, kThreads, smem, st>>>(volt, C, T, ne, sp.len, box_w, box_h, cstart, celem, cw,
-                                           sp.direct ? img : partials, sp.direct, accumulate);
-    HAI_CUDA_TRY(cudaGetLastError());
+    bool launched = false;
+    if (N == 64) {
+        hai_status s = launch64<P>(volt, C, T, ne, sp, box_w, box_h, cstart, celem, cw, nnz,
+                                   sp.direct ? img : partials, accumulate, smem_optin, st, &launched);
+        if (s != HAI_OK) return s;
+    }
+    if (!launched) {
+        const size_t smem = sizeof(float2) * EpicSmem<N, P>::kBuf + ((size_t)kSamples * P * ne * 2 + 15) / 16 * 16;
+        if (smem > (size_t)smem_optin)
+            return hai_fail(HAI_ERR_UNSUPPORTED,
+                            "hai_epic_image_fp32_static: shared memory need exceeds the device limit");
+        auto kern = epic_fp32_kernel<N, P>;
+        HAI_CUDA_TRY(hai_allow_dyn_smem(kern, smem_optin));
+        kern<<<sp.n_cta, kThreads, smem, st>>>(volt, C, T, ne, sp.len, box_w, box_h, cstart, celem, cw,
+                                               sp.direct ? img : partials, sp.direct, accumulate);
+        HAI_CUDA_TRY(cudaGetLastError());
+    }
     if (!sp.direct) {
         const int Q = (P == 2) ? 4 : 1;
         const int plane = Q * N * N;

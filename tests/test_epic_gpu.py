@@ -64,6 +64,45 @@ def test_grid_sizes_pols_and_element_counts(hai, ctx, n, P, ne):
     assert rel_err_planes(got, want).max() < FP32_TOL
 
 
+@pytest.mark.parametrize("P,bw,bh,ne,C,T", [
+    (2, 20, 48, 64, 3, 41),     # box at most 32 cells wide, taller than 32
+    (2, 48, 20, 64, 2, 17),     # wider than 32, at most 32 tall
+    (2, 64, 64, 200, 2, 9),     # the whole grid
+    (1, 30, 30, 7, 3, 23),      # one pol, 14-byte samples (plain voltage loads)
+    (1, 50, 40, 9, 2, 10),      # one pol, box over 32 both ways
+    (2, 33, 31, 5, 2, 12),      # one cell over half the grid along x; 20-byte samples
+    (2, 29, 28, 256, 160, 2),   # more channels than CTAs: one CTA per channel
+])
+def test_fp32_64_box_forms(hai, ctx, P, bw, bh, ne, C, T):
+    """The N = 64 FP32 kernel's box forms (at most 32 cells, or more, along x
+    and along y), one and two pols, samples that do or do not fill whole
+    16-byte copies, the time split, and one CTA per channel with accumulate."""
+    n, k = 64, 3
+    rng = np.random.default_rng(bw * 1000 + bh * 10 + ne)
+    x0, y0 = (n - bw) // 2, n - bh
+    ax = rng.integers(x0, x0 + bw - k + 1, ne)
+    ay = rng.integers(y0, y0 + bh - k + 1, ne)
+    ax[0], ay[0] = x0, y0
+    ax[-1], ay[-1] = x0 + bw - k, y0 + bh - k
+    anchors = np.stack([ax, ay], 1).astype(np.int32)
+    taps = rng.standard_normal((ne, k, k, 2)).astype(np.float32)
+    volt = I.random_voltages((C, T, P, ne, 2), seed=bw + bh + ne)
+    lay = hai.hai_layout_create(ctx, anchors, taps, n, P)
+    try:
+        assert list(hai.hai_layout_box(lay)) == [x0, y0, x0 + bw, y0 + bh]
+        v = volt.cuda().contiguous()
+        img = torch.full((C, lay.n_planes, n, n), float("nan"), device="cuda")
+        hai.hai_epic_image(ctx, lay, v, C, T, hai.HAI_PREC_FP32, img, 0)
+        hai.hai_sync(ctx)
+        want = O.epic_image(n, anchors, taps, volt.numpy())
+        assert rel_err_planes(img.cpu().numpy(), want).max() < FP32_TOL
+        hai.hai_epic_image(ctx, lay, v, C, T, hai.HAI_PREC_FP32, img, 1)
+        hai.hai_sync(ctx)
+        assert rel_err_planes(img.cpu().numpy(), 2 * want).max() < FP32_TOL
+    finally:
+        hai.hai_layout_destroy(lay)
+
+
 def test_adversarial_extreme_voltages(hai, ctx):
     cfg = I.SKA_LOW_STATION_256
     pos, anchors, taps = station(cfg)
