@@ -590,13 +590,14 @@ def fft_correlator_component(hai, ctx, img, C, n, P, flush, peaks):
                          "algorithmic_bytes": fc_bytes}}
 
 
-def ska_component(hai, ctx, flush, peaks, sms, steps):
+def ska_component(hai, ctx, flush, peaks, sms, steps, fp32_peak=None):
     """The SKA-low-shaped station (256 elements in a 38 m disk, 3 x 3 Gaussian
     taps, 64^2 grid, 64 channels x 2 pols x 2048 samples): EPIC on tensor
     cores (fp16, and the hi/lo split), on CUDA cores (FP32), end to end through
     host buffers, and the correlator + XFFT comparison path on the same
     cadence.  The tensor-core roofline counts the pruned DFT of the layout's
-    own kernel box (8 (R N C + N^2 R) per field)."""
+    own kernel box (8 (R N C + N^2 R) per field); the FP32 one the
+    FFT-equivalent work per unit against the probed FP32 FMA peak."""
     import torch
     from paper_2411_17804_gb300 import inputs as I
     cfg = I.SKA_LOW_STATION_256
@@ -625,6 +626,13 @@ def ska_component(hai, ctx, flush, peaks, sms, steps):
             e["roofline"] = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                              "kernel": "epic_tc_kernel", "flop_per_field": pruned_dft_flop(n, R, Cnz),
                              "basis": f"pruned DFT of the {Cnz} x {R} kernel box, 8 (R N C + N^2 R) per field"}
+        elif fp32_peak:
+            fpu = epic_flops_per_unit(cfg)
+            ach = fpu * units / (dom * 1e-3) / 1e12
+            e["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                             "frac": ach / fp32_peak, "kernel": "epic64_kernel", "flop_per_unit": fpu,
+                             "basis": "FFT-equivalent work 5 log2(N^2) + gridding + squaring per unit over the "
+                                      "kernel's event time; peak measured by hai_probe_peak"}
         out[name] = e
     out["tc_over_fp32"] = out["fp32"]["ms"] / out["fp16"]["ms"]
     # end to end through the C ABI with host buffers (pinned)
@@ -1013,7 +1021,8 @@ def main():
         line["components"] = {"fft_correlator": fft_correlator_component(hai, ctx, img, C, n, P, flush, peaks)}
         del volt, vh, ih
         torch.cuda.empty_cache()
-        line["components"]["ska_station"] = ska_component(hai, ctx, flush, peaks, sms, 20)
+        line["components"]["ska_station"] = ska_component(hai, ctx, flush, peaks, sms, 20,
+                                                          probes.get("fp32_tflops"))
         line["components"]["beamformer"] = bf_component(hai, ctx, flush, peaks)
         line["components"]["batched_uneven"] = plan_component(hai, ctx, flush, peaks, 10)
         line["components"]["hierarchical"] = hierarchy_component(hai, ctx, flush, peaks)
