@@ -11,14 +11,16 @@
 // sums 2 N_e of them, so for N_e <= 512 every FP32 partial sum is an integer
 // below 2^24: exact.
 //
-// CTA = 12 warps, persistent over a contiguous range of (s, c, tile) units:
-//   warps 0-6  producers: cp.async 16-byte copies of the voltage rows of a
+// CTA = 13 warps, persistent over a contiguous range of (s, c, tile) units:
+//   warps 0-7  producers: cp.async 16-byte copies of the voltage rows of a
 //              64-element chunk (zero-filled past T) into a 5-deep int8 ring
 //              (4 chunks, 64 KB, in flight per SM to cover HBM latency), then
-//              fp16 widening into a 2-deep K-major A ring; the station's
-//              weights are widened into B when the station changes;
-//   warp 7     one thread issues the MMAs (8 per chunk);
-//   warps 8-11 epilogue: TMEM -> int32, optional requantisation; each thread
+//              fp16 widening into a 2-deep K-major A ring; every thread owns
+//              four fixed (row, 16-byte group) items of a chunk for the copies
+//              and four for the widening, their offsets computed once; the
+//              station's weights are widened into B when the station changes;
+//   warp 8     one thread issues the MMAs (8 per chunk);
+//   warps 9-12 epilogue: TMEM -> int32, optional requantisation; each thread
 //              assembles its sample's [k][p][re, im] row from both pols and
 //              writes it with 16-byte stores (rows are contiguous per unit).
 #include "hai_internal.h"
@@ -26,10 +28,11 @@
 
 namespace {
 
-constexpr int kThreads = 384;
-constexpr int kProd = 224;             // warps 0-6
-constexpr int kMmaWarp = 7;
-constexpr int kEpi = 128;              // warps 8-11
+constexpr int kThreads = 416;
+constexpr int kProd = 256;             // warps 0-7
+constexpr int kMmaWarp = 8;
+constexpr int kEpi = 128;              // warps 9-12
+constexpr int kItems = 4;              // (row, 16-byte group) items per producer thread and chunk
 constexpr int kTile = 128;             // samples per unit (MMA M)
 constexpr int kChunkE = 64;            // elements per K chunk (128 real K)
 constexpr int kI8Stages = 5;           // int8 landing ring: 4 chunks in flight
@@ -60,7 +63,7 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-__device__ __forceinline__ void bar_prod() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
+__device__ __forceinline__ void bar_prod() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 // 16 int8 -> 16 fp16 (two 8-value K groups), exact: bits 0x6400 + (x ^ 0x80) minus 1152
 __device__ __forceinline__ void widen16(const int4 raw, uint4 &lo, uint4 &hi) {
@@ -163,19 +166,29 @@ __global__ void __launch_bounds__(kThreads, 1) bf_kernel(const BfParams p) {
         Walk wi, wc;
         walk_init(wi);
         walk_init(wc);
+        static_assert(kTile * 8 == kItems * kProd, "items per chunk");
+        // copy items: row tc0 + 32 j, group gc (16 bytes of row t stored at
+        // group g ^ (t & 7): conflict-free reads below)
+        const int tc0 = tid >> 3, gc = tid & 7;
+        const uint32_t src0 = (uint32_t)tc0 * t_stride + (uint32_t)gc * 16;
+        const uint32_t dst0 = (uint32_t)tc0 * 128 + (uint32_t)((gc ^ (tc0 & 7)) * 16);
+        // widening items: row tw0 + 32 j, group gw
+        const int tw0 = (tid & 7) + 8 * (tid >> 6), gw = (tid >> 3) & 7;
+        const uint32_t rd0 = (uint32_t)tw0 * 128 + (uint32_t)((gw ^ (tw0 & 7)) * 16);
+        const uint32_t wr0 = (uint32_t)(tw0 >> 3) * kAMNs + (uint32_t)(tw0 & 7) * 16 + (uint32_t)(2 * gw) * kAKs;
         auto issue = [&](long long q) {                        // cp.async of chunk q into its int8 stage
             if (q < nq) {
                 const int t0 = wi.tile * kTile;
                 const int8_t *base = p.volt + ((((size_t)wi.s * p.C + wi.c) * p.T + t0) * p.P + wi.pol) * row_bytes +
                                      (size_t)wi.kc * kChunkE * 2;
-                uint8_t *dst = sI8 + (q % kI8Stages) * kI8Bytes;
-                const int t_valid = p.T - t0, a_left = p.ne - wi.kc * kChunkE;
-                for (int it = tid; it < kTile * 8; it += kProd) {      // 128 rows x 8 x 16 B
-                    const int t = it >> 3, g = it & 7;
-                    const bool ok = (t < t_valid) && (g * 8 < a_left);
-                    const int8_t *src = ok ? base + (uint32_t)t * t_stride + g * 16 : p.volt;
-                    // 16-byte group g of row t stored at g ^ (t & 7): conflict-free reads below
-                    cp_async16(dst + t * 128 + ((g ^ (t & 7)) * 16), src, ok ? 16u : 0u);
+                uint8_t *dst = sI8 + (q % kI8Stages) * kI8Bytes + dst0;
+                const int t_valid = p.T - t0 - tc0;
+                const bool g_ok = gc * 8 < p.ne - wi.kc * kChunkE;
+#pragma unroll
+                for (int j = 0; j < kItems; j++) {
+                    const bool ok = g_ok && 32 * j < t_valid;
+                    const int8_t *src = ok ? base + src0 + (size_t)(32 * j) * t_stride : p.volt;
+                    cp_async16(dst + 32 * 128 * j, src, ok ? 16u : 0u);
                 }
                 walk_next(wi);
             }
@@ -211,16 +224,15 @@ __global__ void __launch_bounds__(kThreads, 1) bf_kernel(const BfParams p) {
                 cur_s = s;
             }
             bar_prod();                                        // int8 stage landed for all threads
-            const uint8_t *src = sI8 + (q % kI8Stages) * kI8Bytes;
-            uint8_t *A = sA + slot * kABytes;
-            for (int it = tid; it < kTile * 8; it += kProd) {  // (row t, 16-byte group g)
-                const int t = (it & 7) | ((it >> 6) << 3), g = (it >> 3) & 7;
-                const int4 raw = *reinterpret_cast<const int4 *>(src + t * 128 + ((g ^ (t & 7)) * 16));
+            const uint8_t *src = sI8 + (q % kI8Stages) * kI8Bytes + rd0;
+            uint8_t *A = sA + slot * kABytes + wr0;
+#pragma unroll
+            for (int j = 0; j < kItems; j++) {                 // rows tw0 + 32 j: A row groups + 4 j
+                const int4 raw = *reinterpret_cast<const int4 *>(src + 32 * 128 * j);
                 uint4 lo, hi;
                 widen16(raw, lo, hi);
-                uint8_t *row = A + (t >> 3) * kAMNs + (t & 7) * 16;
-                *reinterpret_cast<uint4 *>(row + (2 * g) * kAKs) = lo;
-                *reinterpret_cast<uint4 *>(row + (2 * g + 1) * kAKs) = hi;
+                *reinterpret_cast<uint4 *>(A + 4 * kAMNs * j) = lo;
+                *reinterpret_cast<uint4 *>(A + 4 * kAMNs * j + kAKs) = hi;
             }
             tc::fence_proxy_async();
             tc::mbar_arrive(&mb_full[slot]);
