@@ -74,6 +74,11 @@ struct hai_plan {
     int hK = 0, hshift = 0;
     void *d_hst = nullptr;                       // per station: voltage and weight offsets, elements
     void *d_pw = nullptr;                        // the weights re-packed for the integer dot products
+    // the persistent beam kernel (when its shared memory fits): weights per
+    // (beam, pair) in 32 bytes, item starts per station, CTA item ranges
+    void *d_pw2 = nullptr, *d_hitem = nullptr, *d_order = nullptr, *d_next = nullptr;
+    int bf2_grid = 0;                            // 0: the per-block kernel instead
+    size_t bf2_w = 0, bf2_raw = 0, bf2_smem = 0;
     const hai_vis_layout *hx = nullptr;          // inter-station XFFT (or NULL)
     std::vector<const hai_layout *> he;          // inter-station EPIC layouts, one per beam (or none)
     hai_precision hprec = HAI_PREC_FP16;
@@ -97,6 +102,10 @@ void plan_free(hai_plan *p) {
     for (void *t : p->tables) cudaFree(t);
     cudaFree(p->d_hst);
     cudaFree(p->d_pw);
+    cudaFree(p->d_pw2);
+    cudaFree(p->d_hitem);
+    cudaFree(p->d_order);
+    cudaFree(p->d_next);
     if (p->cap) cudaStreamDestroy(p->cap);
     if (p->fork) cudaEventDestroy(p->fork);
     delete p;
@@ -233,7 +242,9 @@ void drop_graph(hai_plan *p) {
 struct HierStation {
     long long volt_off, w_off;   // bytes into the plan's voltage buffer / the caller's weights
     long long pw_off;            // 32-bit words into the packed weights
+    long long pw2_off;           // 16-byte units into the persistent kernel's weights
     int ne, ne2;                 // elements, element pairs
+    int tb, nblk;                // persistent kernel: samples per item, items per channel
 };
 constexpr int kBfTMax = 64;              // samples per block: 64, or 32 for more than 16 beam pairs
 __host__ __device__ __forceinline__ int bf_samples(int K) { return (K + 1) / 2 > 16 ? 32 : kBfTMax; }
@@ -243,9 +254,27 @@ constexpr int kBfWRow = kBfPairs + 1;    // words per staged WP row
 constexpr int kBfQRow = 2 * kBfPairs + 2;   // words per staged WQ row (8-byte aligned, rows 4 banks apart)
 
 __global__ void plan_bf_pack_kernel(const int8_t *__restrict__ w, const HierStation *__restrict__ hst, int K,
-                                    uint32_t *__restrict__ pw) {
+                                    uint32_t *__restrict__ pw, uint4 *__restrict__ pw2) {
     const HierStation h = hst[blockIdx.x];
     const char2 *W = reinterpret_cast<const char2 *>(w + h.w_off);      // [K][2][ne]
+    if (pw2) {
+        // per (beam k, pair j): {WP_0, WQ_0[2j], WQ_0[2j+1], WP_1} {WQ_1[2j], WQ_1[2j+1], 0, 0}
+        auto pk = [&](int k, int p, int a) {
+            return a < h.ne ? W[(size_t)(k * 2 + p) * h.ne + a] : make_char2(0, 0);
+        };
+        auto wpw = [](char2 g0, char2 g1) {
+            return (uint32_t)(uint8_t)g0.x | ((uint32_t)(uint8_t)g0.y << 8) | ((uint32_t)(uint8_t)g1.x << 16) |
+                   ((uint32_t)(uint8_t)g1.y << 24);
+        };
+        auto wqw = [](char2 g) { return (uint32_t)(uint16_t)(int16_t)g.x | ((uint32_t)(uint16_t)(int16_t)(-(int)g.y) << 16); };
+        uint4 *o = pw2 + h.pw2_off;
+        for (int i = threadIdx.x; i < K * h.ne2; i += blockDim.x) {
+            const int k = i / h.ne2, j = i % h.ne2;
+            const char2 a0 = pk(k, 0, 2 * j), a1 = pk(k, 0, 2 * j + 1), b0 = pk(k, 1, 2 * j), b1 = pk(k, 1, 2 * j + 1);
+            o[2 * i] = make_uint4(wpw(a0, a1), wqw(a0), wqw(a1), wpw(b0, b1));
+            o[2 * i + 1] = make_uint4(wqw(b0), wqw(b1), 0u, 0u);
+        }
+    }
     uint32_t *wp = pw + h.pw_off, *wq = wp + (size_t)K * 2 * h.ne2;
     for (int i = threadIdx.x; i < K * 2 * h.ne2; i += blockDim.x) {
         const int row = i / h.ne2, j = i % h.ne2, a = 2 * j;
@@ -354,16 +383,209 @@ size_t bf_smem(int K) {
     return sizeof(uint32_t) * ((size_t)bf_samples(K) * 2 * kBfERow + (size_t)2 * KP * 2 * (kBfWRow + kBfQRow));
 }
 
+// The same beams from a persistent kernel, one CTA per SM taking items
+// (station, block of tb consecutive (channel, sample) rows of its flat C T
+// rows; a block may cross channels) from an atomic counter, the largest
+// stations' items first so that the small ones even out the end:
+//   - the item's voltages are one contiguous run of tb x 2 pols x N_e
+//     complex int8 ([C][T][2][N_e][2] per station): copied by 16-byte
+//     cp.async from the enclosing 16-byte-aligned span (the plan leaves 16
+//     spare bytes around each station) while the previous item is summed;
+//   - the run is re-laid into rows of element pairs (one 32-bit word per two
+//     elements, odd element counts completed with a zero element) with an odd
+//     row stride, pols in separate planes, so that 32 consecutive samples read
+//     32 distinct banks;
+//   - the station's weights stay in shared memory while its items last, per
+//     (beam, pair) two 16-byte words that every lane of a warp reads at once;
+//   - a group of spl lanes per (beam, 4 rows) (one row where an item has too
+//     few rows to fill the CTA; spl = 1, 2, 4 or 8, the largest that keeps the
+//     item's groups within the CTA): each lane sums its share of the element
+//     pairs for both pols' Re and Im in int32, reading a pair's weights once
+//     for its rows; shuffles join the shares, and the sums are requantised on
+//     the way out exactly as by the per-block kernel.
+constexpr int kBf2Threads = 512;
+
+__device__ __forceinline__ void bf2_cp16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+// The sums of one item: task (beam k, rows t + r S1, r < R; S1 = ceil(nt / R))
+// by a group of spl lanes, each over its share of the element pairs; the
+// weights of (k, pair) are read once for the R rows.  Returns the saturations.
+template <int R>
+__device__ __forceinline__ int bf2_sum(const uint32_t *__restrict__ sE, const uint4 *__restrict__ sW,
+                                       int8_t *__restrict__ beams, int tid, int RS, int m, int tb, int nt, int K,
+                                       int shift, size_t row0) {
+    const int S1 = (nt + R - 1) / R, tasks = S1 * K;
+    int spl = 1;
+    while (spl < 8 && tasks * spl * 2 <= kBf2Threads) spl *= 2;
+    const int part = tid & (spl - 1), mp = (m + spl - 1) / spl;
+    const int jb = min(m, part * mp), je = min(m, jb + mp);
+    int sat = 0;
+    for (int q0 = 0; q0 < tasks; q0 += kBf2Threads / spl) {                // CTA-uniform trip count
+        const int q = q0 + tid / spl;
+        const bool live = q < tasks;
+        const int k = live ? q / S1 : 0, t = live ? q - k * S1 : 0;
+        const uint4 *wk = sW + (size_t)k * m * 2;
+        int acc[R][4];
+#pragma unroll
+        for (int r = 0; r < R; r++) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0;
+#pragma unroll 2
+        for (int j = jb; j < (live ? je : jb); j++) {
+            const uint4 wa = wk[2 * j], wb = wk[2 * j + 1];
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int tr = min(t + r * S1, nt - 1);                    // rows past nt: read, not written
+                const int e0 = (int)sE[(size_t)tr * RS + j], e1 = (int)sE[((size_t)tb + tr) * RS + j];
+                const int es0 = (int)__byte_perm((uint32_t)e0, 0u, 0x2301);
+                const int es1 = (int)__byte_perm((uint32_t)e1, 0u, 0x2301);
+                acc[r][0] = __dp4a((int)wa.x, e0, acc[r][0]);
+                acc[r][1] = __dp2a_lo((int)wa.y, es0, acc[r][1]);
+                acc[r][1] = __dp2a_hi((int)wa.z, es0, acc[r][1]);
+                acc[r][2] = __dp4a((int)wa.w, e1, acc[r][2]);
+                acc[r][3] = __dp2a_lo((int)wb.x, es1, acc[r][3]);
+                acc[r][3] = __dp2a_hi((int)wb.y, es1, acc[r][3]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            for (int o = 1; o < spl; o <<= 1)
+#pragma unroll
+                for (int v = 0; v < 4; v++) acc[r][v] += __shfl_xor_sync(0xffffffffu, acc[r][v], o);
+            const int tr = t + r * S1;
+            if (live && part == 0 && tr < nt) {
+                const int b0 = bf_requant(acc[r][0], shift, sat), b1 = bf_requant(acc[r][1], shift, sat);
+                const int b2 = bf_requant(acc[r][2], shift, sat), b3 = bf_requant(acc[r][3], shift, sat);
+                reinterpret_cast<char4 *>(beams)[(row0 + tr) * K + k] =
+                    make_char4((signed char)b0, (signed char)b1, (signed char)b2, (signed char)b3);
+            }
+        }
+    }
+    return sat;
+}
+
+__global__ void __launch_bounds__(kBf2Threads, 1) plan_bf2_kernel(
+    const int8_t *__restrict__ volt, const uint4 *__restrict__ pw2, const HierStation *__restrict__ hst,
+    const long long *__restrict__ hitem, const int *__restrict__ order, unsigned long long *__restrict__ next_item,
+    int S, int C, int T, int K, int shift, int w_bytes, int raw_bytes, int8_t *__restrict__ beams,
+    unsigned long long *__restrict__ n_sat) {
+    extern __shared__ __align__(16) uint8_t sm2[];
+    __shared__ long long s_item;
+    uint4 *sW = reinterpret_cast<uint4 *>(sm2);                          // [K][ne2][2]
+    uint8_t *raw = sm2 + w_bytes;                                         // the item's voltage run
+    uint32_t *sE = reinterpret_cast<uint32_t *>(raw + raw_bytes);        // [2][tb][RS]
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int CT = C * T;                                                 // rows (channel, sample) of a station
+    const long long n_items = hitem[S];
+    // item -> (station, block): items run over the stations in the order
+    // given (largest first, so that the small ones fill the end)
+    auto locate = [&](long long item, int &st, int &blk) {
+        int lo = 0, hi = S - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (hitem[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        st = order[lo];
+        blk = (int)(item - hitem[lo]);
+    };
+    auto issue = [&](const HierStation &hh, int bb) {                     // returns the run's word offset
+        const int t0 = bb * hh.tb, nt = min(hh.tb, CT - t0);
+        const long long start = hh.volt_off + (long long)t0 * 4ll * hh.ne;
+        const long long a0 = start & ~15ll, a1 = (start + (long long)nt * 4 * hh.ne + 15) & ~15ll;
+        const int n16 = (int)((a1 - a0) >> 4);
+        for (int i = tid; i < n16; i += kBf2Threads) bf2_cp16(raw + 16 * i, volt + a0 + 16 * i);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        return (int)((start - a0) >> 2);
+    };
+    if (tid == 0) s_item = (long long)atomicAdd(next_item, 1ull);
+    __syncthreads();
+    long long cur = s_item;
+    if (cur >= n_items) return;
+    int s, blk;
+    locate(cur, s, blk);
+    HierStation h = hst[s];
+    int off = issue(h, blk);
+    int cur_w = -1, sat = 0;
+    for (;;) {
+        if (tid == 0) s_item = (long long)atomicAdd(next_item, 1ull);
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncthreads();                                   // the run has landed; the previous item is summed
+        const long long nxt = s_item;
+        if (s != cur_w) {                                  // this station's weights
+            const int n16 = K * h.ne2 * 2;
+            for (int i = tid; i < n16; i += kBf2Threads) bf2_cp16(sW + i, pw2 + h.pw2_off + i);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            cur_w = s;
+        }
+        const int m = h.ne2, ne = h.ne, tb = h.tb, t0 = blk * tb, nt = min(tb, CT - t0);
+        const int RS = m | 1;                              // odd row stride (words)
+        {
+            // word w = r m + j of the item (row r = (sample r >> 1, pol r & 1)),
+            // lanes over consecutive words, (r, j) carried along
+            const int nw = 2 * nt * m;
+            int r = tid / m, j = tid - r * m;
+            const int dr = kBf2Threads / m, dj = kBf2Threads - dr * m;
+            for (int w = tid; w < nw; w += kBf2Threads) {
+                uint32_t v;
+                if (!(ne & 1)) {
+                    v = reinterpret_cast<const uint32_t *>(raw)[off + w];
+                } else {
+                    const uint16_t *src = reinterpret_cast<const uint16_t *>(raw) + 2 * off + (size_t)r * ne;
+                    const uint32_t lo = src[2 * j], hi = (2 * j + 1 < ne) ? src[2 * j + 1] : 0u;
+                    v = lo | (hi << 16);
+                }
+                sE[((size_t)(r & 1) * tb + (r >> 1)) * RS + j] = v;
+                r += dr;
+                j += dj;
+                if (j >= m) {
+                    j -= m;
+                    r++;
+                }
+            }
+        }
+        __syncthreads();                                   // rows ready, the run buffer free
+        // the next item's run, in flight while this one is summed
+        const int cs = s;
+        if (nxt < n_items) {
+            locate(nxt, s, blk);
+            if (s != cs) h = hst[s];
+            off = issue(h, blk);
+        }
+        if (4 * 128 <= nt * K)
+            sat += bf2_sum<4>(sE, sW, beams, tid, RS, m, tb, nt, K, shift, (size_t)cs * CT + t0);
+        else
+            sat += bf2_sum<1>(sE, sW, beams, tid, RS, m, tb, nt, K, shift, (size_t)cs * CT + t0);
+        if (nxt >= n_items) break;
+    }
+    if (n_sat) {
+        for (int o = 16; o > 0; o >>= 1) sat += __shfl_xor_sync(0xffffffffu, sat, o);
+        if (lane == 0 && sat) atomicAdd(n_sat, (unsigned long long)sat);
+    }
+}
+
 // The second level on stream st (inside the capture): beams, their
 // inter-station order, then the correlator + XFFT and/or the EPIC of every beam.
 hai_status run_second_level(hai_plan *p, const int8_t *volt, const hai_plan_hier_buffers *b, cudaStream_t st) {
     hai_ctx *ctx = p->ctx;
     const int S = p->S, C = p->C, T = p->T, K = p->hK;
     if (b->n_saturated) HAI_CUDA_TRY(cudaMemsetAsync(b->n_saturated, 0, sizeof(long long), st));
-    const int TB = bf_samples(K);
-    plan_bf_kernel<<<dim3((unsigned)S, (unsigned)C, (unsigned)((T + TB - 1) / TB)), TB * ((K + 1) / 2), bf_smem(K),
-                     st>>>(volt, static_cast<const uint32_t *>(p->d_pw), static_cast<const HierStation *>(p->d_hst), C,
-                           T, K, p->hshift, b->beams, reinterpret_cast<unsigned long long *>(b->n_saturated));
+    if (p->bf2_grid > 0) {
+        HAI_CUDA_TRY(cudaMemsetAsync(p->d_next, 0, sizeof(unsigned long long), st));
+        plan_bf2_kernel<<<(unsigned)p->bf2_grid, kBf2Threads, p->bf2_smem, st>>>(
+            volt, static_cast<const uint4 *>(p->d_pw2), static_cast<const HierStation *>(p->d_hst),
+            static_cast<const long long *>(p->d_hitem), static_cast<const int *>(p->d_order),
+            static_cast<unsigned long long *>(p->d_next), S, C, T, K, p->hshift, (int)p->bf2_w, (int)p->bf2_raw,
+            b->beams, reinterpret_cast<unsigned long long *>(b->n_saturated));
+    } else {
+        const int TB = bf_samples(K);
+        plan_bf_kernel<<<dim3((unsigned)S, (unsigned)C, (unsigned)((T + TB - 1) / TB)), TB * ((K + 1) / 2), bf_smem(K),
+                         st>>>(volt, static_cast<const uint32_t *>(p->d_pw), static_cast<const HierStation *>(p->d_hst),
+                               C, T, K, p->hshift, b->beams, reinterpret_cast<unsigned long long *>(b->n_saturated));
+    }
     HAI_CUDA_TRY(cudaGetLastError());
     hai_status s = hai_beams_to_corr(ctx, b->beams, S, C, T, K, 2, b->corr, st);
     if (s != HAI_OK) return s;
@@ -646,25 +868,86 @@ extern "C" hai_status hai_plan_set_hierarchy(hai_plan *p, const hai_plan_hier_de
     HAI_CUDA_TRY(hai_allow_dyn_smem(plan_bf_kernel, p->ctx->smem_optin));
     if (bf_smem(K) > (size_t)p->ctx->smem_optin)
         return hai_fail(HAI_ERR_UNSUPPORTED, "hai_plan_set_hierarchy: n_beam too large for shared memory");
-    void *d_hst = nullptr, *d_pw = nullptr;
+    // the persistent beam kernel: each station's weights (K ne2 x 32 bytes),
+    // one voltage run and its re-laid rows share the SM; samples per item so
+    // that the run and the rows take at most half of the rest each
+    const int C = p->C, T = p->T;
+    int m_max = 1;
+    for (int st = 0; st < S; st++) m_max = std::max(m_max, hs[st].ne2);
+    const size_t w_bytes = (size_t)K * m_max * 32;
+    const long long budget = (long long)p->ctx->smem_optin - (long long)w_bytes - 1024;
+    int bf2_grid = 0;
+    size_t raw_bytes = 0, se_bytes = 0;
+    std::vector<long long> hitem(S + 1, 0);                // item starts, in the order below
+    std::vector<int> order(S);                             // stations, most elements first
+    long long pw2_units = 0;
+    if (budget > 0) {
+        const long long cap = budget / 2;
+        bool ok = true;
+        for (int st = 0; st < S && ok; st++) {
+            const long long rs = hs[st].ne2 | 1;
+            const long long tb = std::min<long long>({(long long)C * T, (cap - 48) / (4ll * hs[st].ne), cap / (8 * rs)});
+            if (tb < 1) ok = false;
+            hs[st].tb = (int)std::max<long long>(tb, 1);
+            hs[st].nblk = (int)(((long long)C * T + hs[st].tb - 1) / hs[st].tb);
+            hs[st].pw2_off = pw2_units;
+            pw2_units += 2ll * K * hs[st].ne2;
+            raw_bytes = std::max(raw_bytes, (size_t)hs[st].tb * 4 * (size_t)hs[st].ne + 32);
+            se_bytes = std::max(se_bytes, (size_t)(2ll * hs[st].tb * rs * 4));
+        }
+        raw_bytes = (raw_bytes + 15) / 16 * 16;
+        for (int st = 0; st < S; st++) order[st] = st;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hs[x].ne > hs[y].ne; });
+        for (int i = 0; i < S; i++) hitem[i + 1] = hitem[i] + hs[order[i]].nblk;
+        if (ok && w_bytes + raw_bytes + se_bytes <= (size_t)p->ctx->smem_optin && hitem[S] > 0)
+            bf2_grid = (int)std::min<long long>(p->ctx->num_sms, hitem[S]);
+    }
+    void *d_hst = nullptr, *d_pw = nullptr, *d_pw2 = nullptr, *d_hitem = nullptr, *d_order = nullptr,
+         *d_next = nullptr;
     cudaError_t e = cudaMalloc(&d_hst, sizeof(HierStation) * S);
     if (e == cudaSuccess) e = cudaMalloc(&d_pw, sizeof(uint32_t) * (size_t)pw_words);
+    if (e == cudaSuccess && bf2_grid > 0) {
+        e = cudaMalloc(&d_pw2, sizeof(uint4) * (size_t)pw2_units);
+        if (e == cudaSuccess) e = cudaMalloc(&d_hitem, sizeof(long long) * (S + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&d_order, sizeof(int) * S);
+        if (e == cudaSuccess) e = cudaMalloc(&d_next, sizeof(unsigned long long));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(d_hitem, hitem.data(), sizeof(long long) * (S + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_order, order.data(), sizeof(int) * S, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = hai_allow_dyn_smem(plan_bf2_kernel, p->ctx->smem_optin);
+    }
     if (e == cudaSuccess) e = cudaMemcpy(d_hst, hs.data(), sizeof(HierStation) * S, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         plan_bf_pack_kernel<<<(unsigned)S, 256>>>(d->weights, static_cast<const HierStation *>(d_hst), K,
-                                                 static_cast<uint32_t *>(d_pw));
+                                                 static_cast<uint32_t *>(d_pw), static_cast<uint4 *>(d_pw2));
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaFree(d_hst);
         cudaFree(d_pw);
+        cudaFree(d_pw2);
+        cudaFree(d_hitem);
+        cudaFree(d_order);
+        cudaFree(d_next);
         return hai_cuda_fail(e, "hai_plan_set_hierarchy: station records and packed weights");
     }
     cudaFree(p->d_hst);
     cudaFree(p->d_pw);
+    cudaFree(p->d_pw2);
+    cudaFree(p->d_hitem);
+    cudaFree(p->d_order);
+    cudaFree(p->d_next);
     p->d_hst = d_hst;
     p->d_pw = d_pw;
+    p->d_pw2 = d_pw2;
+    p->d_hitem = d_hitem;
+    p->d_order = d_order;
+    p->d_next = d_next;
+    p->bf2_grid = bf2_grid;
+    p->bf2_w = w_bytes;
+    p->bf2_raw = raw_bytes;
+    p->bf2_smem = w_bytes + raw_bytes + se_bytes;
     p->hK = K;
     p->hshift = d->requant_shift;
     p->hx = d->xfft;
