@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(kBf2Threads, 1) plan_bf2_kernel(
             if (s != cs) h = hst[s];
             off = issue(h, blk);
         }
-        if (4 * 128 <= nt * K)
+        if (nt >= 16)
             sat += bf2_sum<4>(sE, sW, beams, tid, RS, m, tb, nt, K, shift, (size_t)cs * CT + t0);
         else
             sat += bf2_sum<1>(sE, sW, beams, tid, RS, m, tb, nt, K, shift, (size_t)cs * CT + t0);
