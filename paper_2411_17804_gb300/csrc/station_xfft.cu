@@ -38,7 +38,7 @@
 namespace {
 
 constexpr int kThreads = 512;
-constexpr int kTileCells = 112;        // uv tile side: 2 x 112^2 floats = 98 KB of shared memory
+constexpr int kTileCells = 56;         // uv tile side: 2 x 56^2 floats = 24.5 KB of shared memory
 
 // Gridding record of one stored pair (m >= n): the 2x2 footprints of the pair
 // and of its mirror, as window-relative cell of the lower corner and
