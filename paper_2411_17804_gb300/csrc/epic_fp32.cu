@@ -1,8 +1,12 @@
 // EPIC direct imager, FP32 on CUDA cores (Eq. intra-station EPIC followed by
-// the squaring and temporal sum of Eq. intra-station squaring).
+// the squaring and temporal sum of Eq. intra-station squaring), for grids of
+// N = 16, 32, 64 (larger grids: epic_large.cu).
 //
-// One CTA sums a contiguous range of the flattened (channel, sample) index.
-// Per group of kSamples samples it
+// In both kernels here one CTA sums a contiguous range of the flattened
+// (channel, sample) index.  At N = 64 the 64-point lines are held in
+// registers by groups of 8 lanes (epic64_kernel, described below); for
+// N = 16 and 32, and as the fallback when that kernel's shared memory does not
+// fit, epic_fp32_kernel does, per group of kSamples samples:
 //   1. stages the int8 voltages of the group in shared memory;
 //   2. row pass: one thread per (sample, pol, box row) gathers the gridded
 //      row sum_a conj(W~) E_a from the layout's gather table and transforms
@@ -231,18 +235,20 @@ epic_fp32_kernel(const int8_t *__restrict__ volt, int C, int T, int ne, long lon
 // 8-point DFT over t of the values of k1 = j, ending with X[j + 8 k2] in
 // a[k2].  Exponent + throughout.
 //
-// Per sample: row pass (a group per (box row, pol): gather, transform along
-// x, row written to H), then column pass (a group per column, both pols:
-// transform along y, then |F_X|^2, |F_Y|^2 and F_X conj(F_Y) of its 8 pixels
-// into register accumulators).  The row pass of sample i and the column pass
-// of sample i - 1 share one phase (H and the staged voltages double-buffered),
-// so a sample costs one block barrier.
+// Per phase of one or two samples: row pass (a group per box row and sample,
+// or per (box row, pol): gather, transform along x, row written to H), then
+// column pass (a group per column, both pols, sample by sample: transform
+// along y, then |F_X|^2, |F_Y|^2 and F_X conj(F_Y) of its 8 pixels into
+// register accumulators).  The row pass of phase i and the column pass of
+// phase i - 1 run together (H and the staged voltages double-buffered), so a
+// phase costs one block barrier.
 //
 // Shared layouts, all accesses in the minimum two wavefronts per 8-byte
-// access: H[p][y][(k + 2 (y & 7)) & 63] with planes 8 (mod 16) float2 apart
-// (a half-warp writes both pols of one row, or rows y and y + 4 with one
-// pol, and reads rows t + 8 m of two adjacent columns); the exchange scratch
-// of a group holds value k of lane t at 9 k + t, groups 8 (mod 16) apart.
+// access: H[sample][p][y][(k + 2 (y & 7)) & 63] with pol and sample planes
+// 8 (mod 16) float2 apart (a half-warp writes one row of both samples, or of
+// both pols, or rows y and y + 4 of one pol, and reads rows t + 8 m of two
+// adjacent columns); the exchange scratch of a group holds value k of lane t
+// at 9 k + t, groups 72 float2 (8 mod 16) apart, one pol at a time.
 constexpr int k64Threads = 512;                  // 64 groups of 8 lanes
 constexpr int k64Xs = 72;                        // float2 of exchange scratch per group (one pol at a time)
 
