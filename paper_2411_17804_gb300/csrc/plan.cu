@@ -244,7 +244,7 @@ struct HierStation {
     long long pw_off;            // 32-bit words into the packed weights
     long long pw2_off;           // 16-byte units into the persistent kernel's weights
     int ne, ne2;                 // elements, element pairs
-    int tb, nblk;                // persistent kernel: samples per item, items per channel
+    int tb, nblk;                // persistent kernel: (channel, sample) rows per item, items of the station
 };
 constexpr int kBfTMax = 64;              // samples per block: 64, or 32 for more than 16 beam pairs
 __host__ __device__ __forceinline__ int bf_samples(int K) { return (K + 1) / 2 > 16 ? 32 : kBfTMax; }
@@ -869,7 +869,7 @@ extern "C" hai_status hai_plan_set_hierarchy(hai_plan *p, const hai_plan_hier_de
     if (bf_smem(K) > (size_t)p->ctx->smem_optin)
         return hai_fail(HAI_ERR_UNSUPPORTED, "hai_plan_set_hierarchy: n_beam too large for shared memory");
     // the persistent beam kernel: each station's weights (K ne2 x 32 bytes),
-    // one voltage run and its re-laid rows share the SM; samples per item so
+    // one voltage run and its re-laid rows share the SM; rows per item so
     // that the run and the rows take at most half of the rest each
     const int C = p->C, T = p->T;
     int m_max = 1;
