@@ -185,6 +185,33 @@ def test_beam_counts(hai, ctx, K):
         release(hai, plan, vl, el)
 
 
+def test_beams_small_odd_and_split_stations(hai, ctx):
+    """The persistent beam kernel's edge cases: stations of 1, 2 and 3
+    elements, odd and even element counts (element pairs straddling 32-bit
+    words, a padded last pair), and a 700-element station whose flat
+    (channel, sample) rows take several items crossing channel boundaries;
+    a loud input for saturations.  Beams and the clamp count bit-exact."""
+    S, C, T, K = 6, 3, 13, 4
+    sizes = [1, 2, 3, 17, 64, 700]
+    plan, stations, volt, wbuf, woff, dirs, centres, vl, el = build(hai, ctx, S, C, T, K, sizes=sizes, epic=False,
+                                                                     vrange=127)
+    try:
+        nb, nv, nx, ne = hai.hai_plan_hier_sizes(plan)
+        beams = torch.zeros(nb, dtype=torch.int8, device="cuda")
+        corr = torch.zeros(nb, dtype=torch.int8, device="cuda")
+        vis = torch.zeros(nv, dtype=torch.int32, device="cuda")
+        ximg = torch.zeros(nx, device="cuda")
+        nsat = torch.zeros(1, dtype=torch.int64, device="cuda")
+        img = torch.zeros(plan.img_floats, device="cuda")
+        hai.hai_plan_run_hier(plan, volt.cuda(), img, beams, corr, vis, ximg, None, nsat)
+        hai.hai_sync(ctx)
+        want_b, want_sat = oracle_beams(plan, stations, volt, wbuf, woff, C, T, K)
+        assert np.array_equal(beams.cpu().numpy().reshape(want_b.shape), want_b)
+        assert int(nsat.item()) == want_sat
+    finally:
+        release(hai, plan, vl, el)
+
+
 def test_hierarchy_arguments(hai, ctx):
     S, C, T, K = 3, 1, 4, 4
     plan, stations, volt, wbuf, woff, dirs, centres, vl, el = build(hai, ctx, S, C, T, K, epic=False)
