@@ -206,7 +206,11 @@ hai_status hai_layout_box(const hai_layout *layout, int *box);
  *         HAI_ERR_UNSUPPORTED).  At N = 128 the split precisions run on the
  *         large-grid kernels (the layout then holds their 64 MB scratch).
  * C >= 0, T >= 0 (C = 0 or T = 0: nothing to image; with accumulate = 0 the
- * image is zeroed). */
+ * image is zeroed).  A layout's scratch (partial images, the large-grid batch
+ * and row scratches, and at N = 512 the FP32 path's second stream, joined to
+ * `stream` by events) serves one call at a time: calls with the same layout
+ * must be ordered on the device (one stream, or events between streams);
+ * calls with different layouts may overlap. */
 hai_status hai_epic_image(hai_ctx *ctx, const hai_layout *layout, const int8_t *volt,
                           int C, int T, hai_precision prec, float *img, int accumulate,
                           void *stream);
