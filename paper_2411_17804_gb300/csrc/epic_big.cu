@@ -948,6 +948,10 @@ hai_status launch_variant(const hai_layout *L, const int8_t *volt, int C, int T,
     uint8_t *a1lo = SP ? a1 + a1_half : nullptr, *a2lo = SP ? a2 + a2_half : nullptr;
     const int G1 = ctx->num_sms, G2 = ctx->num_sms;
     int launches = 0;
+    // the fixup of a batch runs on the layout's second stream beside the next
+    // batch's gridding and stage 1; the next stage 2 (which rewrites the
+    // slots and adds to the image tiles) and the return wait for it
+    bool fix_pending = false;
     const size_t NN = (size_t)g.N * g.N;
     for (int c0 = 0; c0 < C; c0 += cb_max) {
     const int Cc = std::min(cb_max, C - c0);
@@ -998,6 +1002,7 @@ hai_status launch_variant(const hai_layout *L, const int8_t *volt, int C, int T,
         p2.add = (accumulate || t0 > 0) ? 1 : 0;
         p2.status = ctx->d_status;
         const int G = (int)std::min<long long>(p2.units, G2);
+        if (fix_pending) HAI_CUDA_TRY(cudaStreamWaitEvent(st, L->big_ev[1], 0));
         // the profiled (dominant) kernel of this path: every stage-2 launch
         const int pidx = prof_begin(ctx, st);
         big_s2_kernel<BF, SP><<<(unsigned)G, 576, V::S2Smem, st>>>(p2);
@@ -1010,11 +1015,17 @@ hai_status launch_variant(const hai_layout *L, const int8_t *volt, int C, int T,
             split_items = a < b && a % tb != 0;
         }
         if (split_items) {
-            big_fixup_kernel<V::W><<<dim3((unsigned)G, kFixSlices), 256, 0, st>>>(p2.slots, ic, g, Cc, tb, p2.units, G);
+            HAI_CUDA_TRY(cudaEventRecord(L->big_ev[0], st));
+            HAI_CUDA_TRY(cudaStreamWaitEvent(L->big_stream, L->big_ev[0], 0));
+            big_fixup_kernel<V::W><<<dim3((unsigned)G, kFixSlices), 256, 0, L->big_stream>>>(p2.slots, ic, g, Cc, tb,
+                                                                                          p2.units, G);
+            HAI_CUDA_TRY(cudaEventRecord(L->big_ev[1], L->big_stream));
+            fix_pending = true;
             launches++;
         }
     }
     }
+    if (fix_pending) HAI_CUDA_TRY(cudaStreamWaitEvent(st, L->big_ev[1], 0));
     prof_count(ctx, launches);
     HAI_CUDA_TRY(cudaGetLastError());
     return HAI_OK;
@@ -1136,6 +1147,9 @@ hai_status epic_big_prepare(hai_layout *L) {
             e = cudaMemcpy(d + L->big_cell_w_off, dense_w.data(), sizeof(float2) * ncellp, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return hai_cuda_fail(e, "epic tensor cores (large grid): cell table");
     }
+    e = cudaStreamCreateWithFlags(&L->big_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&L->big_ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return hai_cuda_fail(e, "epic tensor cores (large grid): fixup stream");
     return HAI_OK;
 }
 

@@ -241,6 +241,9 @@ static void layout_free(hai_layout *L) {
     for (cudaEvent_t ev : L->large_ev)
         if (ev) cudaEventDestroy(ev);
     cudaFree(L->d_big);
+    if (L->big_stream) cudaStreamDestroy(L->big_stream);
+    for (cudaEvent_t ev : L->big_ev)
+        if (ev) cudaEventDestroy(ev);
     cudaFree(L->d_xcell);
     cudaFree(L->d_xent);
     cudaFree(L->d_xk);

@@ -86,6 +86,8 @@ struct hai_layout {
     void *big_cell = nullptr;           // dense per-cell gather table (at most one entry per cell), or NULL
     size_t big_cell_w_off = 0;          // byte offset of its weights
     long long big_batch = 0;
+    cudaStream_t big_stream = nullptr;  // the fixup of batch i beside batch i + 1's gridding and stage 1
+    cudaEvent_t big_ev[2] = {};         // stage 2 done, fixup done
     // XFFT: per grid cell the (pair, K_ab value, mirror) entries landing there,
     // built on the first hai_xfft_image call (layout-only data)
     mutable int32_t *d_xcell = nullptr, *d_xent = nullptr;
