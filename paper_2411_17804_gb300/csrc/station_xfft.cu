@@ -38,7 +38,9 @@
 namespace {
 
 constexpr int kThreads = 512;
-constexpr int kTileCells = 56;         // uv tile side: 2 x 56^2 floats = 24.5 KB of shared memory
+constexpr int kTileCells = 112;        // uv tile side: 2 x 112^2 floats = 98 KB of shared memory
+constexpr int kTileSmall = 56;         // the smaller side, for layouts with many pairs per tile
+constexpr size_t kTilePairsMin = 4096; // pairs per tile (average) that the smaller side needs
 
 // Gridding record of one stored pair (m >= n): the 2x2 footprints of the pair
 // and of its mirror, as window-relative cell of the lower corner and
@@ -370,11 +372,6 @@ extern "C" hai_status hai_vis_layout_create(hai_ctx *ctx, const hai_vis_layout_d
     L->win_v0 = (int)vmin;
     L->ww = (int)(umax - umin + 1);
     L->wh = (int)(vmax - vmin + 1);
-    // tiles of at most kTileCells^2 cells (2 x 4 bytes each in shared memory)
-    L->ntx = (L->ww + kTileCells - 1) / kTileCells;
-    L->nty = (L->wh + kTileCells - 1) / kTileCells;
-    L->tw = (L->ww + L->ntx - 1) / L->ntx;
-    L->th = (L->wh + L->nty - 1) / L->nty;
     for (int m = 0, bl = 0; m < S; m++)
         for (int n = 0; n <= m; n++, bl++) {
             PairRec &r = rec[bl];
@@ -392,25 +389,41 @@ extern "C" hai_status hai_vis_layout_create(hai_ctx *ctx, const hai_vis_layout_d
             r.mfu = mfu[bl];
             r.mfv = mfv[bl];
         }
-    // pairs per tile: every tile that the pair's footprint or its mirror's touches
-    const int ntile = L->ntx * L->nty;
-    std::vector<std::vector<int32_t>> lists(ntile);
-    for (long long bl = 0; bl < nbl; bl++) {
-        const PairRec &r = rec[bl];
-        if (r.du < 0) continue;
-        int seen[8], ns = 0;
-        auto touch = [&](int du, int dv) {
-            for (int t = 0; t < 4; t++) {
-                const int tx = (du + (t & 1)) / L->tw, ty = (dv + (t >> 1)) / L->th;
-                const int id = ty * L->ntx + tx;
-                bool dup = false;
-                for (int j = 0; j < ns; j++) dup |= seen[j] == id;
-                if (!dup) seen[ns++] = id;
-            }
-        };
-        touch(r.du, r.dv);
-        if (r.mu >= 0) touch(r.mu, r.mv);
-        for (int j = 0; j < ns; j++) lists[seen[j]].push_back((int32_t)bl);
+    // tiles of at most side^2 cells (2 x 4 bytes each in shared memory); pairs
+    // per tile: every tile that the pair's footprint or its mirror's touches.
+    // The time follows the tiles that hold the densest cells (short
+    // baselines near the window's centre): the smaller side spreads them over
+    // more CTAs, which pays where the tiles stay well filled (measured: 512
+    // stations in a 3 km core 6.1 -> 4.9 ms, 256 stations 0.91 -> 1.17 ms)
+    std::vector<std::vector<int32_t>> lists;
+    int ntile = 0;
+    for (int side : {kTileSmall, kTileCells}) {
+        L->ntx = (L->ww + side - 1) / side;
+        L->nty = (L->wh + side - 1) / side;
+        L->tw = (L->ww + L->ntx - 1) / L->ntx;
+        L->th = (L->wh + L->nty - 1) / L->nty;
+        ntile = L->ntx * L->nty;
+        lists.assign(ntile, {});
+        size_t binned = 0;
+        for (long long bl = 0; bl < nbl; bl++) {
+            const PairRec &r = rec[bl];
+            if (r.du < 0) continue;
+            int seen[8], ns = 0;
+            auto touch = [&](int du, int dv) {
+                for (int t = 0; t < 4; t++) {
+                    const int tx = (du + (t & 1)) / L->tw, ty = (dv + (t >> 1)) / L->th;
+                    const int id = ty * L->ntx + tx;
+                    bool dup = false;
+                    for (int j = 0; j < ns; j++) dup |= seen[j] == id;
+                    if (!dup) seen[ns++] = id;
+                }
+            };
+            touch(r.du, r.dv);
+            if (r.mu >= 0) touch(r.mu, r.mv);
+            for (int j = 0; j < ns; j++) lists[seen[j]].push_back((int32_t)bl);
+            binned += ns;
+        }
+        if (side == kTileCells || binned >= kTilePairsMin * (size_t)ntile) break;
     }
     std::vector<int32_t> tstart(ntile + 1, 0), tpairs;
     for (int t = 0; t < ntile; t++) {
